@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark: effective TFLOPS and seconds per 2^k-amplitude batch of the sliced contraction.
+
+One step = one tn_contract over all 16 slices of the 30-qubit 5x6-grid 14-cycle Sycamore-shaped
+circuit (10 open qubits: one batch of 1024 amplitudes), inputs resident in HBM.  Effective
+TFLOPS = sum over slices and steps of T_cc (8 flops per complex multiply-add, Eq. T_cc) / time.
+The headline runs the FP16-scaled tensor-core path; the complex64 CUDA-core path is timed in the
+same run for comparison ("mixed vs c64").
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode M]
+
+Under torchrun every rank contracts its own amplitude batch (the same circuit with different
+seeded closed bits: same work, weak scaling); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective TFLOPS & s per 2^k-amplitude batch, mixed vs c64, at XEB err ≤1e-3"
+WORKLOAD = "sycamore_5x6_c14_open10_s4"
+GOLDEN = os.path.join(ROOT, "tests", "golden", WORKLOAD + ".amps.txt")
+TC_SOURCE = os.path.join(ROOT, "paper_2310_03978_gb300", "csrc", "tn_gemm_tc.cu")
+SIMT_SOURCE = os.path.join(ROOT, "paper_2310_03978_gb300", "csrc", "tn_gemm_simt.cu")
+PROFILE_SUMMARY = {"gemm_tc": os.path.join(ROOT, "profiles", "gemm_tc_" + WORKLOAD + ".md"),
+                   "gemm_simt": os.path.join(ROOT, "profiles", "gemm_simt_" + WORKLOAD + ".md")}
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fp16_scaled")
+    ap.add_argument("--c64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------------------------- workload
+def rank_network(wl, rank):
+    """The bench circuit with rank-specific seeded closed bits (same structure and path)."""
+    from paper_2310_03978_gb300 import workload as W
+    if rank == 0:
+        return wl.network
+    net = wl.network
+    rng = W.Xoshiro256ss(W.BASE_SEED + 1 + 7919 * rank)
+    closed = {q: rng.below(2) for q in net.closed_bits}
+    return W.build_network(wl.circuit, net.open_qubits, closed)
+
+
+def dominant_step(wl):
+    from paper_2310_03978_gb300 import workload as W
+    steps = W.replay_path(wl.network.labels, wl.network.open_labels, wl.path, wl.sliced)
+    return max(range(len(steps)), key=lambda i: steps[i].tcc), steps
+
+
+# ---------------------------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, seconds):
+    """Time the CPU oracle on a bounded sample of the workload: the dominant contraction step
+    (random operands with its labels) restricted to a sub-block of its output by fixing all but
+    `keep` of the free labels of A and B, with `keep` grown until the sample takes about
+    `seconds`."""
+    from oracle import oracle as O
+    di, steps = dominant_step(wl)
+    st = steps[di]
+    rng = np.random.default_rng(12345)
+    lk = len(st.k_labels)
+    fa = [l for l in st.labels_a if l not in st.k_labels]
+    fb = [l for l in st.labels_b if l not in st.k_labels]
+    order = [x for pair in zip(fa, fb) for x in pair] + fa[len(fb):] + fb[len(fa):]
+
+    def run(keep):
+        kept = set(order[:keep])
+        la = [l for l in st.labels_a if l in kept or l in st.k_labels]
+        lb = [l for l in st.labels_b if l in kept or l in st.k_labels]
+        A = rng.standard_normal((2,) * len(la)) + 1j * rng.standard_normal((2,) * len(la))
+        B = rng.standard_normal((2,) * len(lb)) + 1j * rng.standard_normal((2,) * len(lb))
+        out = [l for l in st.labels_out if l in kept]
+        t0 = time.perf_counter()
+        O.einsum_pair(A, la, B, lb, out)
+        dt = time.perf_counter() - t0
+        return dt, 8.0 * 2 ** len(out) * 2 ** lk, 2 ** len(out)
+
+    keep = 3
+    dt, fl, outs = run(keep)
+    while dt < 0.5 and keep < len(order):
+        keep += 1
+        dt, fl, outs = run(keep)
+    rate = fl / dt
+    while keep < len(order) and fl * 2 / rate <= seconds:
+        keep += 1
+        fl *= 2
+    dt, fl, outs = run(keep)
+    rate = fl / dt
+    return {"seconds": dt, "flops": fl, "rate": rate, "outputs": outs,
+            "fixed_labels": len(order) - keep, "step": di, "threads": O.num_threads(),
+            "shape": "m=2^%d n=2^%d k=2^%d" % (len(st.m_labels), len(st.n_labels), lk)}
+
+
+# ---------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------- helpers
+def profile_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = PROFILE_SUMMARY.get(kernel)
+    src = TC_SOURCE if kernel == "gemm_tc" else SIMT_SOURCE
+    if not path or not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    traffic, src_sha = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("source_sha256_16:"):
+            src_sha = line.split(":", 1)[1].strip()
+    return traffic if src_sha == sha else None
+
+
+def read_golden():
+    if not os.path.exists(GOLDEN):
+        return None
+    rows = np.loadtxt(GOLDEN, comments="#")
+    return rows[:, 0] + 1j * rows[:, 1]
+
+
+def time_contract(torch, plan, amps, steps, stream):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        plan.contract(amps, stream=stream)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end)
+
+
+def kernel_roofline(plan, step_index, before, slices_per_launch, tcc, peak, bound, unit,
+                    traffic):
+    after = plan.step_info(step_index)
+    n = after["launches"] - before["launches"]
+    t = after["time_ms"] - before["time_ms"]
+    if n <= 0 or t <= 0:
+        return None
+    avg_s = t / n / 1e3
+    achieved = tcc * slices_per_launch / avg_s / 1e12
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": traffic, "kernel": after["kernel_name"],
+            "avg_launch_ms": avg_s * 1e3, "launches": n,
+            "flops_per_launch": tcc * slices_per_launch}
+
+
+# ---------------------------------------------------------------------------------- arms
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from oracle import oracle as O
+    from paper_2310_03978_gb300 import tn, workload as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    wl = W.bench_workload()
+    net_w = rank_network(wl, rank)
+    n_open = len(net_w.open_labels)
+    pk = peaks()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    net = tn.Network.from_workload(net_w)
+
+    def measure(mode, steps, warmup, clocks=False):
+        plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True)
+        info = plan.info()
+        amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
+        # correctness pass (not timed)
+        plan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        result = amps.cpu().numpy().copy()
+        for _ in range(warmup):
+            plan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        kinds = [plan.step_info(i) for i in range(info["num_steps"])]
+        dom = max((i for i in range(len(kinds)) if kinds[i]["kernel_name"] in
+                   ("gemm_tc", "gemm_simt")), key=lambda i: kinds[i]["tcc"])
+        before = plan.step_info(dom)
+        launches0 = plan.info()["kernel_launches"]
+        sampler = ClockSampler(local_rank) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.5)
+        barrier()
+        torch.cuda.synchronize()
+        ms = time_contract(torch, plan, amps, steps, stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = sampler.stop() if sampler else None
+        ms = max_over_ranks(ms)
+        launches = plan.info()["kernel_launches"] - launches0
+        flops = info["tcc_per_slice"] * info["num_slices"] + info["tcc_invariant"]
+        kname = kinds[dom]["kernel_name"]
+        if kname == "gemm_tc":
+            peak, bound, unit = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s"
+        else:
+            peak = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+            bound, unit = "alu", "TFLOP/s"
+        roof = kernel_roofline(plan, dom, before, info["slices_in_flight"], kinds[dom]["tcc"],
+                               peak, bound, unit, profile_traffic(kname))
+        plan.close()
+        return {"ms": ms / steps, "flops": flops, "info": info, "result": result,
+                "roofline": roof, "launches": launches // steps, "clocks": clk, "steps": steps}
+
+    head = measure(args.mode, args.steps, args.warmup, clocks=True)
+    c64 = measure("c64", args.c64_steps, 1) if args.c64_steps > 0 else None
+
+    # end to end through the host-buffer entry points: set the network's numbers (H2D) and
+    # contract into a host array (D2H), every step
+    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode)
+    host_out = np.zeros(1 << n_open, dtype=np.complex128)
+    plan.contract_host(out=host_out)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        net.set_data(net_w.tensors)
+        plan.contract_host(out=host_out, stream=stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0) / args.e2e_steps
+    plan.close()
+
+    golden = read_golden() if rank == 0 else None
+    acc = {}
+    if golden is not None:
+        for name, r in (("head", head), ("c64", c64)):
+            if r is None:
+                continue
+            x_ref = O.readout(golden, wl.circuit.n_qubits)[3]
+            x_got = O.readout(r["result"], wl.circuit.n_qubits)[3]
+            acc[name] = {"amp_rel_l2": O.rel_l2(r["result"], golden),
+                         "eps_l2sq": O.eps_l2sq(r["result"], golden),
+                         "xeb_ideal_rel_err": abs(x_got - x_ref) / abs(x_ref)}
+    if rank != 0:
+        return
+    tflops = world * head["flops"] / (head["ms"] / 1e3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": tflops,
+        "unit": "TFLOPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms"],
+        "s_per_batch": head["ms"] / 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp16_scaled": "f16", "bf16_scaled": "bf16", "c64": "f32"}.get(args.mode,
+                                                                                  args.mode),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "qubits": wl.circuit.n_qubits, "cycles": 14,
+                   "open_qubits": n_open, "slices": head["info"]["num_slices"],
+                   "slices_in_flight": head["info"]["slices_in_flight"],
+                   "max_intermediate_log2": head["info"]["max_log2_size"], "mode": args.mode,
+                   "flops_per_batch": head["flops"],
+                   "l2": "inputs larger than L2 (largest intermediate 2^28 x 8 B per slice)"},
+        "roofline": head["roofline"],
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "e2e": {"value": world * head["flops"] / e2e_s / 1e12, "unit": "TFLOPS",
+                "s_per_batch": e2e_s, "h2d_bytes_per_step": net.data_bytes,
+                "d2h_bytes_per_step": (1 << n_open) * 16},
+        "accuracy": acc,
+    }
+    if c64 is not None:
+        line["c64"] = {"value": world * c64["flops"] / (c64["ms"] / 1e3) / 1e12,
+                       "unit": "TFLOPS", "ms_per_step": c64["ms"], "steps": c64["steps"],
+                       "roofline": c64["roofline"]}
+        line["mixed_over_c64"] = c64["ms"] / head["ms"]
+    if world == 1 and not args.no_cpu_baseline:
+        smp = oracle_sample(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": smp["rate"] / 1e12, "unit": "TFLOPS", "cores": smp["threads"],
+            "kind": "oracle",
+            "sample": "oracle einsum of the dominant step (%s) on %d output elements "
+                      "(%d free labels fixed), %.1f s; s per batch extrapolated %.1f"
+                      % (smp["shape"], smp["outputs"], smp["fixed_labels"], smp["seconds"],
+                         head["flops"] / smp["rate"])}
+    print(json.dumps(line))
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
+    if rank != 0:
+        return
+    from paper_2310_03978_gb300 import workload as W
+    wl = W.bench_workload()
+    per = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(wl, per / 4)
+    rates, secs = [], []
+    smp = None
+    for _ in range(args.steps):
+        smp = oracle_sample(wl, per)
+        rates.append(smp["rate"])
+        secs.append(smp["seconds"])
+    _, steps = dominant_step(wl)
+    flops = sum(s.tcc for s in steps) * wl.num_slices
+    rate = statistics.median(rates)
+    line = {
+        "metric": METRIC, "impl": "reference", "value": rate / 1e12, "unit": "TFLOPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(secs), "s_per_batch": flops / rate,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": "oracle complex128"},
+        "cpu_baseline": {"value": rate / 1e12, "unit": "TFLOPS", "cores": smp["threads"],
+                         "kind": "oracle",
+                         "sample": "dominant step (%s), %d output elements per step"
+                                   % (smp["shape"], smp["outputs"])},
+        "e2e": {"value": rate / 1e12, "unit": "TFLOPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        from oracle import oracle as O
+        O.build()
+        run_reference(args, rank, world)
+        return
+    from paper_2310_03978_gb300 import tn
+    if not os.path.exists(tn.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    from oracle import oracle as O
+    O.build()
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

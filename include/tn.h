@@ -1,0 +1,207 @@
+/*
+ * tn.h - C ABI of the GB300 sliced tensor-network contraction engine (libtn.so).
+ *
+ * The engine computes amplitudes of a quantum circuit by contracting its tensor network
+ * (Sec. 2.1 of "Efficient Quantum Circuit Simulation by Tensor Network Methods on Modern GPUs")
+ * in pairwise steps along a given path (Sec. 3.1), each step being the einsum of Sec. 2.4,
+ * Eq. (chap2_einsum), run as a (permuted) complex GEMM on the GPU (Sec. 4.1).  The network may
+ * be cut on a set of bonds (slicing, Sec. 3.2); every slice is an independent sub-task and the
+ * amplitudes are the sum of the slice results.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a tn_status; nothing is thrown across the ABI.  On failure a message is
+ *     kept per thread and can be read with tn_last_error_detail().
+ *   - Host pointers are read during the call only; the caller keeps ownership.
+ *   - Device pointers are raw CUDA device addresses on the device current at tn_plan() time.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream); all device
+ *     work of a call is ordered on it.
+ *   - Tensors are row-major over their label list (the last label varies fastest).  Every
+ *     label has dimension 2 (qubit bonds); other dimensions give TN_ERR_UNSUPPORTED.
+ *   - Complex numbers are interleaved (re, im) doubles on the host and in the amplitude buffer.
+ */
+#ifndef TN_H_
+#define TN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TN_OK = 0,
+    TN_ERR_INVALID_ARG = 1,  /* NULL pointer, negative size, out-of-range id or label      */
+    TN_ERR_SHAPE = 2,        /* a label used with inconsistent dims, a dangling label       */
+    TN_ERR_PATH = 3,         /* path reuses a retired id or does not reduce to the output   */
+    TN_ERR_OOM = 4,          /* device memory (or the workspace limit) exhausted            */
+    TN_ERR_CUDA = 5,         /* a CUDA runtime/driver call failed; see the detail message   */
+    TN_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                          */
+    TN_ERR_UNSUPPORTED = 7,  /* valid input this build does not handle (e.g. dim != 2)     */
+    TN_ERR_NUMERIC = 8       /* scaled low-precision storage overflowed                     */
+} tn_status;
+
+/* Arithmetic of the contraction steps (Sec. 4.2-4.3).  Storage between steps is complex64
+ * unless a step runs on the tensor cores, whose operands are then stored as planar 16-bit
+ * numbers with one power-of-two exponent per tensor and slice.  Accumulation is FP32 in every
+ * mode; the cross-slice sum and the readout are FP64. */
+typedef enum {
+    TN_PREC_C64 = 0,          /* complex64 storage, FP32 FMA arithmetic on CUDA cores        */
+    TN_PREC_TF32 = 1,         /* reserved: TF32 tensor-core steps                            */
+    TN_PREC_SPLIT_TF32 = 2,   /* reserved: 3xTF32 (Eq. 3xTF32)                               */
+    TN_PREC_FP16_SCALED = 3,  /* dense steps: FP16 tensor cores, per-tensor 2^e scaling     */
+    TN_PREC_BF16_SCALED = 4,  /* dense steps: BF16 tensor cores, per-tensor 2^e scaling     */
+    TN_PREC_SPLIT_BF16 = 5,   /* reserved: 3xBF16 (Sec. 4.2 extension of Eq. 3xTF32)         */
+    TN_PREC_SPLIT_FP16 = 6,   /* reserved: 3xFP16                                            */
+    TN_PREC_MIXED = 7         /* per-step choice (Sec. 4.3): tensor cores on the dense steps */
+} tn_precision;
+
+/* Complex GEMM form for the tensor-core steps: 4M = four real products, 3M = three. */
+typedef enum { TN_GEMM_AUTO = 0, TN_GEMM_4M = 1, TN_GEMM_3M = 2 } tn_gemm_form;
+
+typedef struct tn_network tn_network_t;
+typedef struct tn_plan tn_plan_t;
+
+typedef struct {
+    int64_t max_slices_in_flight;  /* slices contracted together per launch; 0 = as many as
+                                      the workspace limit allows                            */
+    int64_t workspace_limit;       /* bytes of device workspace the plan may use; 0 = 60% of
+                                      the free device memory at tn_plan() time               */
+    void *workspace;               /* optional caller-owned device buffer of workspace_limit
+                                      bytes; NULL = the plan allocates (cudaMalloc) and frees */
+    int32_t gemm_form;             /* tn_gemm_form                                           */
+    int32_t sync_each_call;        /* 1 = tn_contract synchronises its stream and reports
+                                      asynchronous errors itself                             */
+    int32_t use_graph;             /* 1 = replay the step sequence as a captured CUDA graph  */
+    int32_t profile;               /* 1 = time every tensor-core and GEMM step with CUDA events
+                                      on the contraction stream (read by
+                                      tn_plan_get_step_info after the stream is synchronised) */
+    int32_t reserved[8];
+} tn_plan_options;
+
+typedef struct {
+    int64_t num_steps;             /* pairwise steps of the path                             */
+    int64_t num_slices;            /* 2^(number of sliced labels)                            */
+    int64_t slices_in_flight;      /* slices per launch chosen by the plan                   */
+    int64_t workspace_bytes;       /* device workspace used                                  */
+    int32_t num_open;              /* open labels = log2(number of amplitudes)               */
+    int32_t max_log2_size;         /* largest intermediate (log2 elements, per slice)        */
+    double tcc_per_slice;          /* sum of T_cc (Eq. T_cc, 8 flops per complex MAC) of the
+                                      slice-dependent steps, per slice                        */
+    double tcc_invariant;          /* T_cc of the slice-independent steps (run once per call) */
+    double tmc_per_slice;          /* sum of T_mc (Eq. T_mc) of the slice-dependent steps,
+                                      in bytes of complex64                                  */
+    int32_t num_tc_steps;          /* steps routed to the tcgen05 GEMM                       */
+    int32_t num_gemm_steps;        /* steps routed to the CUDA-core GEMM                     */
+    int32_t num_stream_steps;      /* steps routed to the streaming (thin-operand) kernel    */
+    int32_t num_generic_steps;     /* steps routed to the element-wise kernel                */
+    int64_t kernel_launches;       /* kernels this plan has launched so far (all calls)      */
+    int32_t reserved[6];
+} tn_plan_info;
+
+typedef struct {
+    int32_t kernel;                /* 0 generic, 1 stream, 2 CUDA-core GEMM, 3 tcgen05 GEMM  */
+    int32_t slice_dependent;       /* 0 = computed once per call and shared by all slices    */
+    int32_t log2_m, log2_n, log2_k, log2_batch;  /* GEMM extents of the step (Sec. A.2)    */
+    int32_t log2_a, log2_b, log2_c;              /* operand and result sizes               */
+    int32_t gemm_form;             /* tn_gemm_form actually used                              */
+    double tcc;                    /* Eq. T_cc of one slice of this step                     */
+    double time_ms;                /* profile mode: summed CUDA-event time of its launches   */
+    int64_t launches;              /* profile mode: launches timed                           */
+    int32_t reserved[2];
+} tn_step_info;
+
+/*
+ * Load a tensor network (Sec. 2.1; D1 of the paper's pipeline).
+ *   num_tensors       number of tensors (>= 1)
+ *   ranks[i]          rank of tensor i (0..62)
+ *   labels[i][r]      label of axis r of tensor i; labels are ints in [0, 2^20)
+ *   dims[i][r]        dimension of that axis; must be 2
+ *   data[i]           2 * prod(dims) doubles: interleaved complex128, row-major
+ *   num_open          number of open (output) labels
+ *   open_labels[j]    output order: open_labels[0] is the most significant bit of the
+ *                     amplitude index
+ * A label must appear on exactly two tensors, or on one tensor and in open_labels; a label on
+ * three or more tensors is a hyperedge (allowed; it becomes a batch index where two of its
+ * tensors meet).  The data are copied to the device; the caller may free them on return.
+ * Errors: TN_ERR_INVALID_ARG, TN_ERR_SHAPE, TN_ERR_UNSUPPORTED (dim != 2), TN_ERR_CUDA.
+ */
+tn_status tn_network_load(int32_t num_tensors, const int32_t *ranks,
+                          const int32_t *const *labels, const int64_t *const *dims,
+                          const double *const *data, int32_t num_open,
+                          const int32_t *open_labels, tn_network_t **out);
+
+/*
+ * Replace the numbers of a loaded network (same structure), e.g. new gate parameters.
+ * data[i] as in tn_network_load.  Synchronous with respect to the host buffers.
+ */
+tn_status tn_network_set_data(tn_network_t *net, const double *const *data);
+
+/*
+ * Build an execution plan.
+ *   path              path_len = num_tensors - 1 pairs (a, b): tensor a becomes the
+ *                     contraction of a and b and id b is retired (Sec. 3.1)
+ *   sliced_labels     bonds cut by slicing (Sec. 3.2); bit j of a slice id fixes
+ *                     sliced_labels[j]; open labels cannot be sliced
+ *   mode              tn_precision
+ *   opts              may be NULL (defaults)
+ * The plan decides the memory order of every intermediate so that each dense step reads its
+ * operands as GEMM matrices and each producer writes in its consumer's order (Sec. 4.1), routes
+ * every step to a kernel, and sizes its device workspace.  The network must outlive the plan.
+ * Errors: TN_ERR_INVALID_ARG, TN_ERR_PATH, TN_ERR_OOM, TN_ERR_UNSUPPORTED, TN_ERR_CUDA.
+ */
+tn_status tn_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
+                  int32_t num_sliced, const int32_t *sliced_labels, tn_precision mode,
+                  const tn_plan_options *opts, tn_plan_t **out);
+
+/* Plan statistics (host memory out). */
+tn_status tn_plan_get_info(const tn_plan_t *plan, tn_plan_info *out);
+
+/* Per-step statistics, step in [0, num_steps) in path order (host memory out).  In profile
+ * mode this waits for the step's recorded events; synchronise the stream first. */
+tn_status tn_plan_get_step_info(const tn_plan_t *plan, int64_t step, tn_step_info *out);
+
+/*
+ * Contract slices [slice_begin, slice_end) and ADD their sum into amps_dev (Sec. 3.2: the
+ * answer is the sum of the sub-task results).
+ *   amps_dev          device buffer of 2^num_open complex128 (interleaved doubles), caller
+ *                     owned and caller zeroed; results are accumulated (+=) in FP64, slices in
+ *                     increasing order.  Splitting a range into sub-ranges gives the same sum
+ *                     up to FP64 rounding.
+ * Device work is asynchronous on `stream`; an asynchronous failure is reported by this call
+ * when opts.sync_each_call was set, otherwise by the next call on the plan.
+ * Errors: TN_ERR_INVALID_ARG (range), TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_NUMERIC.
+ */
+tn_status tn_contract(tn_plan_t *plan, int64_t slice_begin, int64_t slice_end, void *amps_dev,
+                      void *stream);
+
+/*
+ * Host-buffer convenience: zero a device accumulator, contract [slice_begin, slice_end), copy
+ * the 2^num_open complex128 amplitudes to amps_host and synchronise `stream`.
+ */
+tn_status tn_contract_host(tn_plan_t *plan, int64_t slice_begin, int64_t slice_end,
+                           double *amps_host, void *stream);
+
+/*
+ * FP64 readout of m = 2^num_open amplitudes on the device (Eq. lxeb_2, Eq. lxeb_as_l2):
+ *   out[0] = sum |a|^2, out[1] = sum |a|^4, out[2] = F_l = 2^n_qubits * out[0] / m - 1,
+ *   out[3] = 2^n_qubits * out[1] / out[0] - 1  (XEB of ideal samples from these amplitudes).
+ * out is host memory; the call synchronises `stream`.
+ */
+tn_status tn_readout(const tn_plan_t *plan, const void *amps_dev, int32_t n_qubits,
+                     double out[4], void *stream);
+
+/* Free a network or a plan (NULL is a no-op).  Destroy plans before their network. */
+void tn_destroy(void *handle);
+
+/* Static description of a status code. */
+const char *tn_status_string(tn_status s);
+
+/* Copy this thread's last error message into buf (always NUL-terminated when len > 0). */
+tn_status tn_last_error_detail(char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TN_H_ */

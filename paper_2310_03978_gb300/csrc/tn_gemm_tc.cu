@@ -1,0 +1,366 @@
+// Complex GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// C[m, n] = 2^(eA + eB) * sum_k A[m, k] * B[n, k] for one slice per grid row, where A and B are
+// stored as planar 16-bit numbers (a real plane and an imaginary plane, FP16 or BF16) scaled by
+// per-slice powers of two (the dynamic scaling that Sec. 4.2 proposes, made exact by using
+// powers of two), and the sum runs in FP32 in tensor memory.  The complex product is formed from
+// four real products (4M):
+//     Cre = Are*Bre - Aim*Bim,   Cim = Are*Bim + Aim*Bre,
+// with the minus sign taken by the instruction descriptor's negate-A bit.
+//
+// One CTA computes a 128 x 128 output tile: warp 0 lane 0 issues TMA loads (128-byte swizzle)
+// into a 3-stage shared-memory ring, warp 1 lane 0 issues tcgen05.mma into two TMEM
+// accumulators (re, im; 256 columns), and all four warps drain TMEM through tcgen05.ld, apply the
+// exponent and scatter the complex64 result into the consumer's memory order (Sec. 4.1 index
+// reordering, done at the producer's store).  Every mbarrier wait gives up after a device-time
+// limit, records a timeout in a status word and lets the CTA release its TMEM and exit.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
+constexpr int TILE_A = BM * BK * 2;                  // bytes of one 16-bit plane tile
+constexpr int TILE_B = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // re and im planes of A and B
+constexpr int TMEM_COLS = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + BN * 8 /*col offsets*/ + 256;
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s
+
+__device__ unsigned int g_tc_status;  // bit 0: an mbarrier wait timed out
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the status word set) once the deadline has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long deadline) {
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() > deadline) {
+            atomicOr(&g_tc_status, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte swizzle:
+// rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                    // descriptor version of tcgen05
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16 with FP32 accumulation, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N, bool neg_a) {
+    return (1u << 4)                          // D format: F32
+           | ((bf16 ? 1u : 0u) << 7)          // A format: F16 / BF16
+           | ((bf16 ? 1u : 0u) << 10)         // B format
+           | ((neg_a ? 1u : 0u) << 13)        // negate A
+           | ((uint32_t)(N >> 3) << 17)       // N / 8
+           | ((uint32_t)(M >> 4) << 24);      // M / 16
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos) {
+    uint64_t r = 0;
+    for (int i = 0; i < n; ++i)
+        if ((x >> i) & 1ull) r |= 1ull << pos[i];
+    return r;
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGemmDesc d,
+                                                    int64_t tiles_n) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *coloff = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + BN * 8);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = blockIdx.y;
+    // grouped raster: 16 m-tiles share a group so that concurrent CTAs reuse A and B in L2
+    const int64_t tile = blockIdx.x;
+    const int64_t tiles_m = (1ll << d.lm) / BM;
+    const int64_t group = 16;
+    const int64_t per_group = group * tiles_n;
+    const int64_t g = tile / per_group;
+    const int64_t first_m = g * group;
+    const int64_t gsize = (tiles_m - first_m) < group ? (tiles_m - first_m) : group;
+    const int64_t mt = first_m + (tile % per_group) % gsize;
+    const int64_t nt = (tile % per_group) / gsize;
+    const int m0 = (int)(mt * BM), n0 = (int)(nt * BN);
+    const int num_kb = (1 << d.lk) / BK;
+    const int sa = d.a_sliced ? (int)s : 0, sbi = d.b_sliced ? (int)s : 0;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmA))
+                     : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmB))
+                     : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (int j = threadIdx.x; j < BN; j += blockDim.x)
+        coloff[j] = deposit((uint64_t)(n0 + j), d.ln, d.posC_n);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const unsigned long long deadline = globaltimer() + kWaitLimitNs;
+
+    int issued = 0;  // k blocks whose loads the producer issued
+    if (threadIdx.x == 0) {
+        // TMA producer
+        for (int kb = 0; kb < num_kb; ++kb) {
+            const int st = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (kb >= STAGES && !mbar_wait(&empty[st], ph ^ 1u, deadline)) break;
+            uint8_t *base = smem + st * STAGE_BYTES;
+            mbar_expect_tx(&full[st], STAGE_BYTES);
+            const int k0 = kb * BK;
+            tma_load_3d(base, &d.tmA, &full[st], k0, m0, sa);
+            tma_load_3d(base + TILE_A, &d.tmA, &full[st], k0, m0, (int)d.slices_a + sa);
+            tma_load_3d(base + 2 * TILE_A, &d.tmB, &full[st], k0, n0, sbi);
+            tma_load_3d(base + 2 * TILE_A + TILE_B, &d.tmB, &full[st], k0, n0,
+                        (int)d.slices_b + sbi);
+            issued = kb + 1;
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer: four real products per k step into the re and im accumulators
+        const uint32_t id_pos = idesc_f16(d.bf16 != 0, BM, BN, false);
+        const uint32_t id_neg = idesc_f16(d.bf16 != 0, BM, BN, true);
+        const uint32_t t_re = tmem, t_im = tmem + BN;
+        bool ok = true;
+        for (int kb = 0; kb < num_kb && ok; ++kb) {
+            const int st = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&full[st], ph, deadline)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+            const uint64_t a_re = sdesc_sw128(base), a_im = sdesc_sw128(base + TILE_A);
+            const uint64_t b_re = sdesc_sw128(base + 2 * TILE_A);
+            const uint64_t b_im = sdesc_sw128(base + 2 * TILE_A + TILE_B);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
+                const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+                umma_f16(t_re, a_re + adv, b_re + adv, id_pos, first);
+                umma_f16(t_re, a_im + adv, b_im + adv, id_neg, 1u);
+                umma_f16(t_im, a_re + adv, b_im + adv, id_pos, first);
+                umma_f16(t_im, a_im + adv, b_re + adv, id_pos, 1u);
+            }
+            umma_commit(&empty[st]);
+        }
+        umma_commit(done);
+    }
+    __syncwarp();
+
+    // epilogue: every warp drains its 32 TMEM lanes (rows); the wait result is made
+    // warp-uniform because tcgen05.ld is a warp-collective instruction
+    bool have = false;
+    if (lane == 0) have = mbar_wait(done, 0, deadline);
+    have = __shfl_sync(0xffffffffu, have ? 1 : 0, 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (have) {
+        const int e = d.expA[sa] + d.expB[sbi];
+        const int row = warp * 32 + lane;
+        const uint64_t roff = deposit((uint64_t)(m0 + row), d.lm, d.posC_m);
+        float2 *C = d.C + s * d.sC;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t re[16], im[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)c0, re);
+            tmem_ld16(tmem + lane_base + (uint32_t)(BN + c0), im);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float vr = ldexpf(__uint_as_float(re[j]), e);
+                const float vi = ldexpf(__uint_as_float(im[j]), e);
+                C[roff | coloff[c0 + j]] = make_float2(vr, vi);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        // every load this CTA issued must have landed before its shared memory is released;
+        // after a normal run the MMA warp consumed them all and these waits return at once
+        const unsigned long long drain = globaltimer() + kWaitLimitNs;
+        for (int st = 0; st < STAGES && st < issued; ++st) {
+            const int last = ((issued - 1 - st) / STAGES) * STAGES + st;
+            mbar_wait(&full[st], (uint32_t)(last / STAGES) & 1u, drain);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+}
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+bool tc_available() {
+    int dev = 0, major = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+        return false;
+    if (major != 10) return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_gemm_tc) != cudaSuccess) return false;
+    return get_encode() != nullptr;
+}
+
+int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
+                         int64_t depth, int bf16) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return -1;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || K % BK != 0) return -2;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
+    cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2)};
+    cuuint32_t box[3] = {BK, 128, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap *>(tmap_host),
+                     bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                     const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (d.lm < 7 || d.ln < 7 || d.lk < 6 || slices > 65535) return cudaErrorInvalidValue;
+    const int64_t tiles_n = (1ll << d.ln) / BN;
+    const int64_t tiles = ((1ll << d.lm) / BM) * tiles_n;
+    if (tiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    k_gemm_tc<<<dim3((unsigned)tiles, (unsigned)slices), 128, SMEM_BYTES, st>>>(d, tiles_n);
+    return cudaGetLastError();
+}
+
+unsigned int tc_status_read_and_clear() {
+    unsigned int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_status, sizeof v) != cudaSuccess) return 0xffffffffu;
+    if (v) cudaMemcpyToSymbol(g_tc_status, &z, sizeof z);
+    return v;
+}
+
+}  // namespace tn

@@ -1,0 +1,1021 @@
+// Host runtime and C ABI of the contraction engine (declared in include/tn.h).
+//
+// tn_plan() turns (network, path, sliced bonds, precision) into a list of device operations:
+//   1. replay of the path (Sec. 3.1: pairs (a, b), the result keeps id a) with the sliced labels
+//      removed (Sec. 3.2), giving for every step its contracted (K), free (M, N) and batch
+//      labels (Sec. 2.4, Eq. chap2_einsum) and its T_cc / T_mc (Eq. T_cc, Eq. T_mc);
+//   2. routing of every step to a kernel (tensor-core GEMM, CUDA-core GEMM, element-wise) by
+//      its GEMM extents, following the balanced-index thresholds of App. A.2;
+//   3. a layout pass from the root back to the leaves (Sec. 4.1, index reordering): each operand
+//      of a step is stored as [its free labels in the order of the step's result][the contracted
+//      labels], so every step reads its operands as GEMM matrices and every producer writes
+//      directly in its consumer's order; no separate transpose pass exists;
+//   4. slice-independent steps are hoisted into a prologue that runs once per tn_contract call;
+//   5. a liveness-based first-fit placement of every tensor in one device workspace, with as
+//      many slices per launch as the workspace allows.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tn.h"
+#include "tn_internal.h"
+
+namespace {
+
+constexpr uint32_t kNetMagic = 0x544e4e54u;   // "TNNT"
+constexpr uint32_t kPlanMagic = 0x544e504cu;  // "TNPL"
+constexpr int kMaxLabel = 1 << 20;
+constexpr int kMaxRank = 62;
+
+thread_local std::string g_err;
+
+tn_status fail(tn_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define TN_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? TN_ERR_OOM : TN_ERR_CUDA,            \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+    } while (0)
+
+}  // namespace
+
+struct tn_network {
+    uint32_t magic = kNetMagic;
+    int device = 0;
+    std::vector<std::vector<int>> labels;  // per tensor, row-major order
+    std::vector<int64_t> offset;           // complex128 element offset of each tensor
+    std::vector<int> open;
+    int64_t total = 0;                     // complex128 elements
+    double2 *data = nullptr;               // device copy
+};
+
+namespace {
+
+enum Kernel { K_GENERIC = 0, K_STREAM = 1, K_GEMM = 2, K_TC = 3 };
+
+struct Tensor {
+    std::vector<int> order;  // memory order of the labels, most significant first
+    bool dep = false;        // depends on the slice id
+    int producer = -1;       // step index, or -1 for a leaf
+    int leaf = -1;           // network tensor index for a leaf
+    int64_t off = -1;        // complex64 element offset in the arena
+    int t0 = 0, t1 = 0;      // lifetime on the op timeline
+    int rank() const { return (int)order.size(); }
+    int pos(int label) const {  // bit position of a label in this tensor's memory index
+        for (int i = 0; i < rank(); ++i)
+            if (order[i] == label) return rank() - 1 - i;
+        return -1;
+    }
+};
+
+struct Planar {              // planar 16-bit copy of a tensor feeding a tensor-core step
+    int tensor = -1;
+    int64_t off = -1;        // byte offset in the arena
+    int64_t bytes_per_slice = 0;
+    int t = 0;               // time of the consuming step
+    int meta = -1;           // index of its (amax, exps) block
+};
+
+struct Step {
+    int a = -1, b = -1, c = -1;  // tensor indices
+    std::vector<int> la, lb, lc; // replayed label lists (before layout)
+    std::vector<int> K, M, N, batch;
+    int kernel = K_GENERIC;
+    bool dep = false;
+    double tcc = 0, tmc = 0;
+    int t = 0;                   // op time
+    int pa = -1, pb = -1;        // planar copies for K_TC
+    int form = TN_GEMM_4M;
+    // profile mode: recorded (start, stop) event pairs not yet read, and the running totals
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double time_ms = 0;
+    int64_t timed = 0;
+};
+
+struct Op {
+    int kind;   // 0 bind invariant, 1 step, 2 bind sliced, 3 convert, 4 accumulate
+    int index;  // step or planar index
+};
+
+}  // namespace
+
+struct tn_plan {
+    uint32_t magic = kPlanMagic;
+    const tn_network *net = nullptr;
+    int device = 0;
+    tn_precision mode = TN_PREC_C64;
+    tn_plan_options opts{};
+    std::vector<int> sliced;
+    std::vector<Tensor> tensors;
+    std::vector<Step> steps;
+    std::vector<Planar> planars;
+    int root = -1;
+    int64_t num_slices = 1;
+    int64_t sb = 1;              // slices per launch
+    int64_t arena_elems = 0;     // complex64 elements
+    int64_t arena_bytes = 0;
+    char *arena = nullptr;
+    bool own_arena = false;
+    std::vector<tn::BindItem> bind_inv, bind_sl;
+    tn::BindItem *bind_inv_dev = nullptr, *bind_sl_dev = nullptr;
+    int max_rank_inv = 0, max_rank_sl = 0;
+    unsigned int *meta = nullptr;  // per planar: amax[sb] then exps[sb]
+    double *partial = nullptr;     // readout partials
+    double2 *amps_tmp = nullptr;   // tn_contract_host accumulator
+    int n_partial = 64;
+    int max_log = 0;
+    bool tc_ok = false;
+    std::vector<tn::TcGemmDesc> tc_desc;  // per step (only K_TC entries used)
+    int64_t launches = 0;                 // kernels launched by this plan
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
+};
+
+namespace {
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+tn_status check_net(const tn_network *n) {
+    if (!n || n->magic != kNetMagic) return fail(TN_ERR_INVALID_ARG, "not a tn network handle");
+    return TN_OK;
+}
+
+tn_status check_plan(const tn_plan_t *p) {
+    if (!p || p->magic != kPlanMagic) return fail(TN_ERR_INVALID_ARG, "not a tn plan handle");
+    return TN_OK;
+}
+
+// Pick the kernel of a step from its GEMM extents (log2).  Dense steps go to the tensor cores
+// when the mode asks for them; the thresholds follow App. A.2 (k >= 64, m, n >= 32 keep the
+// tensor cores busy) rounded up to the tcgen05 tile (M 128, N 128, K 64).
+int route(const Step &s, tn_precision mode, bool tc_ok) {
+    const int lm = (int)s.M.size(), ln = (int)s.N.size(), lk = (int)s.K.size();
+    const bool tc_mode = mode == TN_PREC_FP16_SCALED || mode == TN_PREC_BF16_SCALED ||
+                         mode == TN_PREC_MIXED;
+    if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 6) return K_TC;
+    if (s.batch.empty() && lm >= 5 && ln >= 5 && lk >= 3) return K_GEMM;
+    return K_GENERIC;
+}
+
+void fill_pos(int8_t *dst, int n, int value) {
+    for (int i = 0; i < n; ++i) dst[i] = (int8_t)value;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tn_status_string(tn_status s) {
+    switch (s) {
+        case TN_OK: return "ok";
+        case TN_ERR_INVALID_ARG: return "invalid argument";
+        case TN_ERR_SHAPE: return "inconsistent shape or labels";
+        case TN_ERR_PATH: return "invalid contraction path";
+        case TN_ERR_OOM: return "out of device memory";
+        case TN_ERR_CUDA: return "CUDA error";
+        case TN_ERR_TIMEOUT: return "device wait timed out";
+        case TN_ERR_UNSUPPORTED: return "unsupported input";
+        case TN_ERR_NUMERIC: return "scaled storage overflow";
+    }
+    return "unknown status";
+}
+
+tn_status tn_last_error_detail(char *buf, size_t len) {
+    if (!buf || len == 0) return TN_ERR_INVALID_ARG;
+    size_t n = std::min(len - 1, g_err.size());
+    memcpy(buf, g_err.data(), n);
+    buf[n] = 0;
+    return TN_OK;
+}
+
+tn_status tn_network_load(int32_t num_tensors, const int32_t *ranks,
+                          const int32_t *const *labels, const int64_t *const *dims,
+                          const double *const *data, int32_t num_open,
+                          const int32_t *open_labels, tn_network_t **out) {
+    g_err.clear();
+    if (!out) return fail(TN_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (num_tensors < 1 || !ranks || !labels || !dims || !data)
+        return fail(TN_ERR_INVALID_ARG, "need at least one tensor and non-NULL arrays");
+    if (num_open < 0 || (num_open > 0 && !open_labels))
+        return fail(TN_ERR_INVALID_ARG, "bad open labels");
+    if (num_open > 40) return fail(TN_ERR_UNSUPPORTED, "at most 40 open labels");
+    std::map<int, int> count;
+    auto *net = new tn_network();
+    for (int i = 0; i < num_tensors; ++i) {
+        if (ranks[i] < 0 || ranks[i] > kMaxRank) {
+            delete net;
+            return fail(TN_ERR_INVALID_ARG, "tensor %d: rank %d out of range", i, ranks[i]);
+        }
+        if (ranks[i] > 0 && (!labels[i] || !dims[i])) {
+            delete net;
+            return fail(TN_ERR_INVALID_ARG, "tensor %d: NULL labels or dims", i);
+        }
+        if (!data[i]) {
+            delete net;
+            return fail(TN_ERR_INVALID_ARG, "tensor %d: NULL data", i);
+        }
+        std::vector<int> ls;
+        for (int r = 0; r < ranks[i]; ++r) {
+            int l = labels[i][r];
+            if (l < 0 || l >= kMaxLabel) {
+                delete net;
+                return fail(TN_ERR_INVALID_ARG, "tensor %d: label %d out of range", i, l);
+            }
+            if (dims[i][r] != 2) {
+                delete net;
+                return fail(TN_ERR_UNSUPPORTED, "tensor %d: dim %lld (only 2 is supported)", i,
+                            (long long)dims[i][r]);
+            }
+            if (std::find(ls.begin(), ls.end(), l) != ls.end()) {
+                delete net;
+                return fail(TN_ERR_SHAPE, "tensor %d: label %d repeated", i, l);
+            }
+            ls.push_back(l);
+            count[l]++;
+        }
+        net->labels.push_back(ls);
+        net->offset.push_back(net->total);
+        net->total += (int64_t)1 << ranks[i];
+    }
+    for (int j = 0; j < num_open; ++j) {
+        int l = open_labels[j];
+        if (count.find(l) == count.end()) {
+            delete net;
+            return fail(TN_ERR_SHAPE, "open label %d is on no tensor", l);
+        }
+        if (std::find(net->open.begin(), net->open.end(), l) != net->open.end()) {
+            delete net;
+            return fail(TN_ERR_SHAPE, "open label %d repeated", l);
+        }
+        net->open.push_back(l);
+        count[l]++;
+    }
+    for (auto &kv : count)
+        if (kv.second < 2) {
+            delete net;
+            return fail(TN_ERR_SHAPE, "label %d is on one tensor only and not open", kv.first);
+        }
+    if (cudaGetDevice(&net->device) != cudaSuccess) {
+        delete net;
+        return fail(TN_ERR_CUDA, "no CUDA device");
+    }
+    cudaError_t e = cudaMalloc(&net->data, sizeof(double2) * (size_t)net->total);
+    if (e != cudaSuccess) {
+        delete net;
+        return fail(e == cudaErrorMemoryAllocation ? TN_ERR_OOM : TN_ERR_CUDA,
+                    "cudaMalloc network: %s", cudaGetErrorString(e));
+    }
+    *out = net;
+    tn_status s = tn_network_set_data(net, data);
+    if (s != TN_OK) {
+        tn_destroy(net);
+        *out = nullptr;
+    }
+    return s;
+}
+
+tn_status tn_network_set_data(tn_network_t *net, const double *const *data) {
+    if (check_net(net) != TN_OK) return TN_ERR_INVALID_ARG;
+    if (!data) return fail(TN_ERR_INVALID_ARG, "data is NULL");
+    std::vector<double2> host((size_t)net->total);
+    for (size_t i = 0; i < net->labels.size(); ++i) {
+        if (!data[i]) return fail(TN_ERR_INVALID_ARG, "tensor %d: NULL data", (int)i);
+        memcpy(&host[(size_t)net->offset[i]], data[i],
+               sizeof(double2) * ((size_t)1 << net->labels[i].size()));
+    }
+    TN_CUDA(cudaMemcpy(net->data, host.data(), sizeof(double2) * host.size(),
+                       cudaMemcpyHostToDevice));
+    return TN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// First-fit placement of intervals [t0, t1] with sizes, returns the peak (in units).
+int64_t place(std::vector<std::pair<int64_t, std::pair<int, int>>> items,
+              std::vector<int64_t> &offsets) {
+    // items: (size, (t0, t1)); offsets out in input order
+    struct Live { int64_t off, size; int t0, t1; };
+    std::vector<Live> placed;
+    std::vector<int> order(items.size());
+    for (size_t i = 0; i < items.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (items[x].second.first != items[y].second.first)
+            return items[x].second.first < items[y].second.first;
+        return items[x].first > items[y].first;
+    });
+    offsets.assign(items.size(), 0);
+    int64_t peak = 0;
+    for (int idx : order) {
+        const int64_t sz = items[idx].first;
+        const int t0 = items[idx].second.first, t1 = items[idx].second.second;
+        std::vector<std::pair<int64_t, int64_t>> busy;
+        for (auto &p : placed)
+            if (!(p.t1 < t0 || p.t0 > t1)) busy.push_back({p.off, p.off + p.size});
+        std::sort(busy.begin(), busy.end());
+        int64_t cand = 0;
+        for (auto &bz : busy) {
+            if (cand + sz <= bz.first) break;
+            cand = std::max(cand, bz.second);
+        }
+        offsets[idx] = cand;
+        placed.push_back({cand, sz, t0, t1});
+        peak = std::max(peak, cand + sz);
+    }
+    return peak;
+}
+
+// Layout, allocation and descriptors for a given number of slices per launch.
+int64_t layout_bytes(tn_plan_t *p, int64_t sb, bool commit) {
+    std::vector<std::pair<int64_t, std::pair<int, int>>> items;
+    std::vector<int> who;  // >= 0 tensor, < 0: -(planar + 1)
+    for (size_t i = 0; i < p->tensors.size(); ++i) {
+        const Tensor &t = p->tensors[i];
+        int64_t bytes = (int64_t)8 << t.rank();
+        if (t.dep) bytes *= sb;
+        items.push_back({align_up(bytes, 256), {t.t0, t.t1}});
+        who.push_back((int)i);
+    }
+    for (size_t i = 0; i < p->planars.size(); ++i) {
+        const Planar &q = p->planars[i];
+        const Tensor &t = p->tensors[q.tensor];
+        int64_t bytes = q.bytes_per_slice * (t.dep ? sb : 1);
+        items.push_back({align_up(bytes, 1024), {q.t - 2, q.t}});
+        who.push_back(-(int)i - 1);
+    }
+    std::vector<int64_t> offs;
+    int64_t peak = place(items, offs);
+    if (commit) {
+        for (size_t i = 0; i < who.size(); ++i) {
+            if (who[i] >= 0) p->tensors[who[i]].off = offs[i] / 8;
+            else p->planars[-who[i] - 1].off = offs[i];
+        }
+    }
+    return align_up(peak, 1024);
+}
+
+tn_status build_descriptors(tn_plan_t *p);
+
+}  // namespace
+
+extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
+                             int32_t num_sliced, const int32_t *sliced_labels, tn_precision mode,
+                             const tn_plan_options *opts, tn_plan_t **out) {
+    g_err.clear();
+    if (!out) return fail(TN_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (check_net(net) != TN_OK) return TN_ERR_INVALID_ARG;
+    const int nt = (int)net->labels.size();
+    if (path_len != nt - 1) return fail(TN_ERR_PATH, "path has %d pairs, need %d", path_len, nt - 1);
+    if (path_len > 0 && !path) return fail(TN_ERR_INVALID_ARG, "path is NULL");
+    if (num_sliced < 0 || num_sliced > 40 || (num_sliced > 0 && !sliced_labels))
+        return fail(TN_ERR_INVALID_ARG, "bad sliced labels");
+    if ((int)mode < 0 || (int)mode > (int)TN_PREC_MIXED)
+        return fail(TN_ERR_INVALID_ARG, "bad precision mode");
+    if (mode == TN_PREC_TF32 || mode == TN_PREC_SPLIT_TF32 || mode == TN_PREC_SPLIT_BF16 ||
+        mode == TN_PREC_SPLIT_FP16)
+        return fail(TN_ERR_UNSUPPORTED, "precision mode %d is not implemented", (int)mode);
+
+    auto *p = new tn_plan_t();
+    p->net = net;
+    p->mode = mode;
+    p->device = net->device;
+    if (opts) p->opts = *opts;
+    p->tc_ok = tn::tc_available();
+
+    std::map<int, int> cnt;  // holders of each label (tensors + output)
+    for (auto &ls : net->labels)
+        for (int l : ls) cnt[l]++;
+    for (int l : net->open) cnt[l]++;
+    for (int j = 0; j < num_sliced; ++j) {
+        int l = sliced_labels[j];
+        if (cnt.find(l) == cnt.end()) {
+            delete p;
+            return fail(TN_ERR_INVALID_ARG, "sliced label %d is not in the network", l);
+        }
+        if (std::find(net->open.begin(), net->open.end(), l) != net->open.end()) {
+            delete p;
+            return fail(TN_ERR_INVALID_ARG, "open label %d cannot be sliced", l);
+        }
+        if (std::find(p->sliced.begin(), p->sliced.end(), l) != p->sliced.end()) {
+            delete p;
+            return fail(TN_ERR_INVALID_ARG, "sliced label %d repeated", l);
+        }
+        p->sliced.push_back(l);
+    }
+    p->num_slices = (int64_t)1 << num_sliced;
+    auto is_sliced = [&](int l) {
+        return std::find(p->sliced.begin(), p->sliced.end(), l) != p->sliced.end();
+    };
+    for (int l : p->sliced) cnt[l] = 0;
+
+    // leaves, with sliced labels removed
+    std::vector<int> cur(nt);
+    std::vector<std::vector<int>> lab(nt);
+    for (int i = 0; i < nt; ++i) {
+        Tensor t;
+        t.leaf = i;
+        for (int l : net->labels[i]) {
+            if (is_sliced(l)) t.dep = true;
+            else lab[i].push_back(l);
+        }
+        if (num_sliced == 0) t.dep = true;  // one slice: everything runs in the slice loop
+        p->tensors.push_back(t);
+        cur[i] = i;
+    }
+    std::vector<bool> alive(nt, true);
+    // 1. replay
+    for (int s = 0; s < path_len; ++s) {
+        int a = path[2 * s], b = path[2 * s + 1];
+        if (a < 0 || a >= nt || b < 0 || b >= nt || a == b || !alive[a] || !alive[b]) {
+            delete p;
+            return fail(TN_ERR_PATH, "step %d: pair (%d, %d) invalid or retired", s, a, b);
+        }
+        Step st;
+        st.a = cur[a];
+        st.b = cur[b];
+        st.la = lab[a];
+        st.lb = lab[b];
+        auto inb = [&](int l) { return std::find(st.lb.begin(), st.lb.end(), l) != st.lb.end(); };
+        auto ina = [&](int l) { return std::find(st.la.begin(), st.la.end(), l) != st.la.end(); };
+        for (int l : st.la) {
+            if (inb(l)) {
+                if (cnt[l] > 2) { st.batch.push_back(l); st.lc.push_back(l); }
+                else st.K.push_back(l);
+            } else {
+                st.M.push_back(l);
+                st.lc.push_back(l);
+            }
+        }
+        for (int l : st.lb)
+            if (!ina(l)) { st.N.push_back(l); st.lc.push_back(l); }
+        if ((int)st.lc.size() > kMaxRank || (int)st.lc.size() > TN_MAXR - 1) {
+            delete p;
+            return fail(TN_ERR_UNSUPPORTED, "step %d: result rank %d too large", s,
+                        (int)st.lc.size());
+        }
+        for (int l : st.batch) cnt[l]--;
+        for (int l : st.K) cnt[l] = 0;
+        const double la_ = (double)st.la.size(), lb_ = (double)st.lb.size();
+        st.tcc = 8.0 * std::ldexp(1.0, (int)(la_ + lb_) - (int)st.K.size());
+        st.tmc = 8.0 * (std::ldexp(1.0, (int)la_) + std::ldexp(1.0, (int)lb_) +
+                        std::ldexp(1.0, (int)st.lc.size()));
+        Tensor t;
+        t.producer = s;
+        t.dep = p->tensors[st.a].dep || p->tensors[st.b].dep;
+        st.dep = t.dep;
+        st.c = (int)p->tensors.size();
+        p->tensors.push_back(t);
+        cur[a] = st.c;
+        lab[a] = st.lc;
+        alive[b] = false;
+        p->max_log = std::max(p->max_log, (int)st.lc.size());
+        p->steps.push_back(st);
+    }
+    int root_id = -1;
+    for (int i = 0; i < nt; ++i)
+        if (alive[i]) { root_id = i; break; }
+    p->root = cur[root_id];
+    {
+        std::vector<int> rl = lab[root_id], ol = net->open;
+        std::sort(rl.begin(), rl.end());
+        std::sort(ol.begin(), ol.end());
+        if (rl != ol) {
+            delete p;
+            return fail(TN_ERR_PATH, "the path does not reduce to a tensor of the open labels");
+        }
+    }
+    for (int i = 0; i < nt; ++i) p->max_log = std::max(p->max_log, (int)lab[i].size());
+
+    // 2. routing
+    for (auto &st : p->steps) {
+        st.kernel = route(st, mode, p->tc_ok);
+        // slice-independent steps run once per call; they stay on the CUDA cores
+        if (!st.dep && st.kernel == K_TC) st.kernel = K_GEMM;
+        st.form = (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
+    }
+
+    // 3. layout: root first, then every step's operands from its result's order
+    p->tensors[p->root].order = net->open;
+    for (int s = path_len - 1; s >= 0; --s) {
+        Step &st = p->steps[s];
+        const std::vector<int> &co = p->tensors[st.c].order;
+        auto pos_in = [&](const std::vector<int> &v, int l) {
+            return (int)(std::find(v.begin(), v.end(), l) - v.begin());
+        };
+        std::vector<int> oa, ob;
+        for (int l : co) {
+            if (std::find(st.la.begin(), st.la.end(), l) != st.la.end()) oa.push_back(l);
+            if (std::find(st.lb.begin(), st.lb.end(), l) != st.lb.end()) ob.push_back(l);
+        }
+        for (int l : st.K) { oa.push_back(l); ob.push_back(l); }
+        // M and N in the order of the result (used by the GEMM descriptors)
+        std::sort(st.M.begin(), st.M.end(), [&](int x, int y) { return pos_in(co, x) < pos_in(co, y); });
+        std::sort(st.N.begin(), st.N.end(), [&](int x, int y) { return pos_in(co, x) < pos_in(co, y); });
+        p->tensors[st.a].order = oa;
+        p->tensors[st.b].order = ob;
+    }
+    if (path_len == 0) p->tensors[p->root].order = net->open;
+
+    // 4. op timeline: invariant leaves, invariant steps, sliced leaves, dependent steps, accumulate
+    std::vector<Op> ops;
+    ops.push_back({0, -1});
+    for (int s = 0; s < path_len; ++s)
+        if (!p->steps[s].dep) ops.push_back({1, s});
+    ops.push_back({2, -1});
+    for (int s = 0; s < path_len; ++s)
+        if (p->steps[s].dep) {
+            Step &st = p->steps[s];
+            if (st.kernel == K_TC) {
+                for (int side = 0; side < 2; ++side) {
+                    Planar q;
+                    q.tensor = side ? st.b : st.a;
+                    q.bytes_per_slice = (int64_t)4 << p->tensors[q.tensor].rank();
+                    q.meta = (int)p->planars.size();
+                    (side ? st.pb : st.pa) = (int)p->planars.size();
+                    p->planars.push_back(q);
+                    ops.push_back({3, (int)p->planars.size() - 1});
+                }
+            }
+            ops.push_back({1, s});
+        }
+    ops.push_back({4, -1});
+    const int tend = (int)ops.size() - 1;
+    for (int t = 0; t < (int)ops.size(); ++t) {
+        const Op &op = ops[t];
+        if (op.kind == 0 || op.kind == 2) {
+            for (auto &x : p->tensors)
+                if (x.producer < 0 && x.dep == (op.kind == 2)) x.t0 = x.t1 = t;
+        } else if (op.kind == 1) {
+            Step &st = p->steps[op.index];
+            st.t = t;
+            p->tensors[st.c].t0 = p->tensors[st.c].t1 = t;
+            p->tensors[st.a].t1 = t;
+            p->tensors[st.b].t1 = t;
+        } else if (op.kind == 3) {
+            p->planars[op.index].t = t + 1;
+        }
+    }
+    for (auto &st : p->steps) {
+        if (st.kernel == K_TC) {
+            // both planar copies are written by the two convert ops just before the step
+            p->planars[st.pa].t = st.t;
+            p->planars[st.pb].t = st.t;
+        }
+    }
+    // invariant tensors read by the slice loop stay live through all batches
+    for (auto &st : p->steps)
+        if (st.dep) {
+            if (!p->tensors[st.a].dep) p->tensors[st.a].t1 = tend;
+            if (!p->tensors[st.b].dep) p->tensors[st.b].t1 = tend;
+        }
+    p->tensors[p->root].t1 = tend;
+
+    // 5. slices per launch under the workspace limit
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete p;
+        return fail(TN_ERR_CUDA, "cudaMemGetInfo failed");
+    }
+    int64_t limit = p->opts.workspace_limit > 0 ? p->opts.workspace_limit
+                                                : (int64_t)((double)free_b * 0.6);
+    int64_t sb = p->num_slices;
+    if (p->opts.max_slices_in_flight > 0) sb = std::min(sb, p->opts.max_slices_in_flight);
+    sb = std::min<int64_t>(sb, 65535);
+    while (sb > 1 && layout_bytes(p, sb, false) > limit) sb = (sb + 1) / 2;
+    const int64_t need = layout_bytes(p, sb, true);
+    if (need > limit) {
+        delete p;
+        return fail(TN_ERR_OOM, "workspace needs %lld bytes for one slice, limit %lld",
+                    (long long)need, (long long)limit);
+    }
+    p->sb = sb;
+    p->arena_bytes = need;
+    if (p->opts.workspace) {
+        p->arena = (char *)p->opts.workspace;
+    } else {
+        cudaError_t e = cudaMalloc(&p->arena, (size_t)need);
+        if (e != cudaSuccess) {
+            delete p;
+            return fail(TN_ERR_OOM, "cudaMalloc workspace (%lld bytes): %s", (long long)need,
+                        cudaGetErrorString(e));
+        }
+        p->own_arena = true;
+    }
+    tn_status s = build_descriptors(p);
+    if (s != TN_OK) {
+        tn_destroy(p);
+        return s;
+    }
+    *out = p;
+    return TN_OK;
+}
+
+namespace {
+
+tn::BindItem make_bind(const tn_plan_t *p, const Tensor &t) {
+    tn::BindItem it{};
+    const std::vector<int> &src = p->net->labels[t.leaf];
+    it.dst_off = t.off;
+    it.dst_sstride = t.dep ? ((int64_t)1 << t.rank()) : 0;
+    if (p->sliced.empty()) it.dst_sstride = 0;
+    it.src_off = p->net->offset[t.leaf];
+    it.rank = t.rank();
+    const int rs = (int)src.size();
+    fill_pos(it.pos_src, TN_MAXR, -1);
+    for (int i = 0; i < t.rank(); ++i) {
+        const int l = t.order[t.rank() - 1 - i];
+        const int j = (int)(std::find(src.begin(), src.end(), l) - src.begin());
+        it.pos_src[i] = (int8_t)(rs - 1 - j);
+    }
+    it.nsl = 0;
+    for (int j = 0; j < (int)p->sliced.size(); ++j) {
+        auto f = std::find(src.begin(), src.end(), p->sliced[j]);
+        if (f == src.end()) continue;
+        it.sl_bit[it.nsl] = (int8_t)j;
+        it.sl_pos[it.nsl] = (int8_t)(rs - 1 - (int)(f - src.begin()));
+        it.nsl++;
+    }
+    return it;
+}
+
+tn_status build_descriptors(tn_plan_t *p) {
+    for (auto &t : p->tensors) {
+        if (t.leaf < 0) continue;
+        if (t.rank() > TN_MAXR - 1) return fail(TN_ERR_UNSUPPORTED, "leaf rank too large");
+        int nsl = 0;
+        for (int l : p->net->labels[t.leaf])
+            if (std::find(p->sliced.begin(), p->sliced.end(), l) != p->sliced.end()) nsl++;
+        if (nsl > 8) return fail(TN_ERR_UNSUPPORTED, "a leaf carries more than 8 sliced labels");
+        tn::BindItem it = make_bind(p, t);
+        if (t.dep) {
+            p->bind_sl.push_back(it);
+            p->max_rank_sl = std::max(p->max_rank_sl, t.rank());
+        } else {
+            p->bind_inv.push_back(it);
+            p->max_rank_inv = std::max(p->max_rank_inv, t.rank());
+        }
+    }
+    auto upload = [&](std::vector<tn::BindItem> &v, tn::BindItem **dst) -> tn_status {
+        if (v.empty()) return TN_OK;
+        TN_CUDA(cudaMalloc(dst, sizeof(tn::BindItem) * v.size()));
+        TN_CUDA(cudaMemcpy(*dst, v.data(), sizeof(tn::BindItem) * v.size(),
+                           cudaMemcpyHostToDevice));
+        return TN_OK;
+    };
+    tn_status s = upload(p->bind_inv, &p->bind_inv_dev);
+    if (s != TN_OK) return s;
+    s = upload(p->bind_sl, &p->bind_sl_dev);
+    if (s != TN_OK) return s;
+    if (!p->planars.empty())
+        TN_CUDA(cudaMalloc(&p->meta, sizeof(unsigned int) * 2 * p->sb * p->planars.size()));
+    TN_CUDA(cudaMalloc(&p->partial, sizeof(double) * 2 * p->n_partial));
+    TN_CUDA(cudaMalloc(&p->amps_tmp, sizeof(double2) << p->net->open.size()));
+
+    p->tc_desc.resize(p->steps.size());
+    for (auto &st : p->steps) {
+        if (st.kernel != K_TC) continue;
+        tn::TcGemmDesc &d = p->tc_desc[&st - &p->steps[0]];
+        memset(&d, 0, sizeof d);
+        const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
+        const int bf = p->mode == TN_PREC_BF16_SCALED;
+        const int64_t Kx = (int64_t)1 << st.K.size();
+        const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
+        const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
+        if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx,
+                                     (int64_t)1 << st.M.size(), 2 * sa, bf) != 0 ||
+            tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx,
+                                     (int64_t)1 << st.N.size(), 2 * sbb, bf) != 0)
+            return fail(TN_ERR_CUDA, "cuTensorMapEncodeTiled failed for step %d",
+                        (int)(&st - &p->steps[0]));
+        d.C = reinterpret_cast<float2 *>(p->arena) + C.off;
+        d.sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
+        d.lm = (int)st.M.size();
+        d.ln = (int)st.N.size();
+        d.lk = (int)st.K.size();
+        d.a_sliced = A.dep ? 1 : 0;
+        d.b_sliced = B.dep ? 1 : 0;
+        d.slices_a = sa;
+        d.slices_b = sbb;
+        d.expA = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qa.meta + p->sb);
+        d.expB = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qb.meta + p->sb);
+        d.form = st.form;
+        d.bf16 = bf;
+        fill_pos(d.posC_m, TN_MAXR, -1);
+        fill_pos(d.posC_n, TN_MAXR, -1);
+        for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
+        for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
+    }
+    return TN_OK;
+}
+
+tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStream_t stream,
+                         const std::pair<cudaEvent_t, cudaEvent_t> *ev);
+
+// Launch one step; in profile mode the GEMM launch of a tensor-core or CUDA-core GEMM step is
+// bracketed by a pair of CUDA events on the contraction stream.
+tn_status run_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stream) {
+    const bool prof = p->opts.profile && (st.kernel == K_TC || st.kernel == K_GEMM);
+    if (!prof) return run_step_inner(p, st, slices, stream, nullptr);
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!p->event_pool.empty()) {
+        ev = p->event_pool.back();
+        p->event_pool.pop_back();
+    } else {
+        TN_CUDA(cudaEventCreate(&ev.first));
+        TN_CUDA(cudaEventCreate(&ev.second));
+    }
+    tn_status s = run_step_inner(p, st, slices, stream, &ev);
+    st.pending.push_back(ev);
+    return s;
+}
+
+tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStream_t stream,
+                         const std::pair<cudaEvent_t, cudaEvent_t> *ev) {
+    const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
+    float2 *arena = reinterpret_cast<float2 *>(p->arena);
+    const int64_t sA = A.dep ? ((int64_t)1 << A.rank()) : 0;
+    const int64_t sB = B.dep ? ((int64_t)1 << B.rank()) : 0;
+    const int64_t sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
+    cudaError_t e = cudaSuccess;
+    if (st.kernel == K_TC) {
+        const int si = (int)(&st - &p->steps[0]);
+        for (int side = 0; side < 2; ++side) {
+            const Planar &q = p->planars[side ? st.pb : st.pa];
+            const Tensor &X = side ? B : A;
+            tn::ConvertDesc cd{};
+            cd.src = arena + X.off;
+            cd.dst = p->arena + q.off;
+            cd.n = (int64_t)1 << X.rank();
+            cd.src_sstride = X.dep ? cd.n : 0;
+            const int64_t sx = X.dep ? slices : 1;
+            cd.plane_stride = cd.n * (X.dep ? p->sb : 1);
+            cd.dst_sstride = cd.n;
+            cd.amax = p->meta + 2 * p->sb * q.meta;
+            cd.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
+            cd.bf16 = p->mode == TN_PREC_BF16_SCALED;
+            TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
+            TN_CUDA(tn::launch_amax(cd, sx, stream));
+            TN_CUDA(tn::launch_convert16(cd, sx, stream));
+        }
+        if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
+        e = tn::launch_gemm_tc(p->tc_desc[si], slices, stream);
+        if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
+        p->launches += 2 * 2 + 1;  // amax + convert per operand, then the GEMM
+    } else if (st.kernel == K_GEMM) {
+        tn::GemmDesc d{};
+        d.A = arena + A.off;
+        d.B = arena + B.off;
+        d.C = arena + C.off;
+        d.sA = sA;
+        d.sB = sB;
+        d.sC = sC;
+        d.lm = (int)st.M.size();
+        d.ln = (int)st.N.size();
+        d.lk = (int)st.K.size();
+        fill_pos(d.posC_m, TN_MAXR, -1);
+        fill_pos(d.posC_n, TN_MAXR, -1);
+        for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
+        for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
+        if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
+        e = tn::launch_gemm_simt(d, slices, stream);
+        if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
+        p->launches += 1;
+    } else {
+        tn::GenericDesc d{};
+        d.A = arena + A.off;
+        d.B = arena + B.off;
+        d.C = arena + C.off;
+        d.sA = sA;
+        d.sB = sB;
+        d.sC = sC;
+        d.rank_c = C.rank();
+        d.nk = (int)st.K.size();
+        fill_pos(d.posA_c, TN_MAXR, -1);
+        fill_pos(d.posB_c, TN_MAXR, -1);
+        fill_pos(d.posA_k, TN_MAXR, -1);
+        fill_pos(d.posB_k, TN_MAXR, -1);
+        for (int i = 0; i < C.rank(); ++i) {
+            const int l = C.order[C.rank() - 1 - i];
+            d.posA_c[i] = (int8_t)A.pos(l);
+            d.posB_c[i] = (int8_t)B.pos(l);
+        }
+        const int nk = (int)st.K.size();
+        for (int j = 0; j < nk; ++j) {
+            const int l = st.K[nk - 1 - j];
+            d.posA_k[j] = (int8_t)A.pos(l);
+            d.posB_k[j] = (int8_t)B.pos(l);
+        }
+        e = tn::launch_generic(d, slices, stream);
+        p->launches += 1;
+    }
+    if (e != cudaSuccess)
+        return fail(TN_ERR_CUDA, "step %d launch: %s", (int)(&st - &p->steps[0]),
+                    cudaGetErrorString(e));
+    return TN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tn_status tn_plan_get_info(const tn_plan_t *p, tn_plan_info *out) {
+    if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
+    if (!out) return fail(TN_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof *out);
+    out->num_steps = (int64_t)p->steps.size();
+    out->num_slices = p->num_slices;
+    out->slices_in_flight = p->sb;
+    out->workspace_bytes = p->arena_bytes;
+    out->num_open = (int32_t)p->net->open.size();
+    out->max_log2_size = p->max_log;
+    for (auto &st : p->steps) {
+        if (st.dep) {
+            out->tcc_per_slice += st.tcc;
+            out->tmc_per_slice += st.tmc;
+        } else {
+            out->tcc_invariant += st.tcc;
+        }
+        switch (st.kernel) {
+            case K_TC: out->num_tc_steps++; break;
+            case K_GEMM: out->num_gemm_steps++; break;
+            case K_STREAM: out->num_stream_steps++; break;
+            default: out->num_generic_steps++; break;
+        }
+    }
+    out->kernel_launches = p->launches;
+    return TN_OK;
+}
+
+tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *out) {
+    if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
+    if (!out || step < 0 || step >= (int64_t)p->steps.size())
+        return fail(TN_ERR_INVALID_ARG, "bad step index");
+    const Step &st = p->steps[(size_t)step];
+    memset(out, 0, sizeof *out);
+    out->kernel = st.kernel;
+    out->slice_dependent = st.dep ? 1 : 0;
+    out->log2_m = (int)st.M.size();
+    out->log2_n = (int)st.N.size();
+    out->log2_k = (int)st.K.size();
+    out->log2_batch = (int)st.batch.size();
+    out->log2_a = (int)st.la.size();
+    out->log2_b = (int)st.lb.size();
+    out->log2_c = (int)st.lc.size();
+    out->gemm_form = st.kernel == K_TC ? st.form : 0;
+    out->tcc = st.tcc;
+    Step &ms = const_cast<Step &>(st);
+    tn_plan_t *mp = const_cast<tn_plan_t *>(p);
+    for (auto &ev : ms.pending) {
+        float ms_ = 0.f;
+        TN_CUDA(cudaEventSynchronize(ev.second));
+        TN_CUDA(cudaEventElapsedTime(&ms_, ev.first, ev.second));
+        ms.time_ms += ms_;
+        ms.timed += 1;
+        mp->event_pool.push_back(ev);
+    }
+    ms.pending.clear();
+    out->time_ms = st.time_ms;
+    out->launches = st.timed;
+    return TN_OK;
+}
+
+tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void *amps_dev,
+                      void *stream_) {
+    g_err.clear();
+    if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
+    if (!amps_dev) return fail(TN_ERR_INVALID_ARG, "amps_dev is NULL");
+    if (slice_begin < 0 || slice_end > p->num_slices || slice_begin > slice_end)
+        return fail(TN_ERR_INVALID_ARG, "slice range [%lld, %lld) outside [0, %lld)",
+                    (long long)slice_begin, (long long)slice_end, (long long)p->num_slices);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    {
+        cudaError_t pending = cudaPeekAtLastError();
+        if (pending != cudaSuccess)
+            return fail(TN_ERR_CUDA, "pending CUDA error: %s", cudaGetErrorString(pending));
+    }
+    if (slice_begin == slice_end) return TN_OK;
+    int dev = 0;
+    TN_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) TN_CUDA(cudaSetDevice(p->device));
+    float2 *arena = reinterpret_cast<float2 *>(p->arena);
+    const double2 *src = p->net->data;
+    // prologue: slice-independent leaves and steps, once per call
+    TN_CUDA(tn::launch_bind(p->bind_inv_dev, (int32_t)p->bind_inv.size(), src, arena, 0, 1,
+                            p->max_rank_inv, stream));
+    if (!p->bind_inv.empty()) p->launches++;
+    for (auto &st : p->steps)
+        if (!st.dep) {
+            tn_status s = run_step(p, st, 1, stream);
+            if (s != TN_OK) return s;
+        }
+    const Tensor &R = p->tensors[p->root];
+    const int64_t nout = (int64_t)1 << R.rank();
+    for (int64_t s0 = slice_begin; s0 < slice_end; s0 += p->sb) {
+        const int64_t ns = std::min(p->sb, slice_end - s0);
+        TN_CUDA(tn::launch_bind(p->bind_sl_dev, (int32_t)p->bind_sl.size(), src, arena, s0, ns,
+                                p->max_rank_sl, stream));
+        if (!p->bind_sl.empty()) p->launches++;
+        for (auto &st : p->steps)
+            if (st.dep) {
+                tn_status s = run_step(p, st, ns, stream);
+                if (s != TN_OK) return s;
+            }
+        TN_CUDA(tn::launch_accumulate(arena + R.off, R.dep ? nout : 0, nout, R.dep ? ns : 1,
+                                      reinterpret_cast<double2 *>(amps_dev), stream));
+        p->launches++;
+    }
+    if (p->opts.sync_each_call) {
+        TN_CUDA(cudaStreamSynchronize(stream));
+        if (!p->planars.empty() && tn::tc_status_read_and_clear() != 0)
+            return fail(TN_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+    }
+    if (dev != p->device) cudaSetDevice(dev);
+    return TN_OK;
+}
+
+tn_status tn_contract_host(tn_plan_t *p, int64_t slice_begin, int64_t slice_end,
+                           double *amps_host, void *stream_) {
+    if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
+    if (!amps_host) return fail(TN_ERR_INVALID_ARG, "amps_host is NULL");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int64_t n = (int64_t)1 << p->net->open.size();
+    TN_CUDA(tn::launch_zero_f64(p->amps_tmp, n, stream));
+    tn_status s = tn_contract(p, slice_begin, slice_end, p->amps_tmp, stream_);
+    if (s != TN_OK) return s;
+    TN_CUDA(cudaMemcpyAsync(amps_host, p->amps_tmp, sizeof(double2) * (size_t)n,
+                            cudaMemcpyDeviceToHost, stream));
+    TN_CUDA(cudaStreamSynchronize(stream));
+    if (!p->planars.empty() && tn::tc_status_read_and_clear() != 0)
+        return fail(TN_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
+    return TN_OK;
+}
+
+tn_status tn_readout(const tn_plan_t *p, const void *amps_dev, int32_t n_qubits, double out[4],
+                     void *stream_) {
+    g_err.clear();
+    if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
+    if (!amps_dev || !out || n_qubits < 0 || n_qubits > 1000)
+        return fail(TN_ERR_INVALID_ARG, "bad readout arguments");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int64_t m = (int64_t)1 << p->net->open.size();
+    TN_CUDA(tn::launch_readout(reinterpret_cast<const double2 *>(amps_dev), m, p->partial,
+                               p->n_partial, stream));
+    double h[2];
+    TN_CUDA(cudaMemcpyAsync(h, p->partial, sizeof h, cudaMemcpyDeviceToHost, stream));
+    TN_CUDA(cudaStreamSynchronize(stream));
+    const double D = std::ldexp(1.0, n_qubits);
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = D * h[0] / (double)m - 1.0;
+    out[3] = h[0] > 0.0 ? D * h[1] / h[0] - 1.0 : 0.0;
+    return TN_OK;
+}
+
+void tn_destroy(void *handle) {
+    if (!handle) return;
+    const uint32_t magic = *reinterpret_cast<const uint32_t *>(handle);
+    if (magic == kNetMagic) {
+        auto *n = reinterpret_cast<tn_network *>(handle);
+        if (n->data) cudaFree(n->data);
+        n->magic = 0;
+        delete n;
+    } else if (magic == kPlanMagic) {
+        auto *p = reinterpret_cast<tn_plan_t *>(handle);
+        if (p->own_arena && p->arena) cudaFree(p->arena);
+        if (p->bind_inv_dev) cudaFree(p->bind_inv_dev);
+        if (p->bind_sl_dev) cudaFree(p->bind_sl_dev);
+        if (p->meta) cudaFree(p->meta);
+        if (p->partial) cudaFree(p->partial);
+        if (p->amps_tmp) cudaFree(p->amps_tmp);
+        for (auto &st : p->steps)
+            for (auto &ev : st.pending) p->event_pool.push_back(ev);
+        for (auto &ev : p->event_pool) {
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        p->magic = 0;
+        delete p;
+    }
+}
+
+}  // extern "C"

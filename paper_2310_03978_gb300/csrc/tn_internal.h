@@ -1,0 +1,106 @@
+// Internal declarations shared by the host runtime and the CUDA kernels of libtn.so.
+//
+// Every tensor is a "bit tensor": each label has dimension 2, so an element index is a word of
+// bits and a label is a bit position.  Bit 0 of a tensor's memory index is its last label.
+// A step C = sum_K A * B (Sec. 2.4, Eq. chap2_einsum) is described by where each bit of the
+// output index and of the contracted index lands in the operands' memory indices.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define TN_MAXR 48  // largest rank handled by a kernel descriptor
+
+namespace tn {
+
+// Element-wise contraction: one thread per output element (any memory orders).
+struct GenericDesc {
+    const float2 *A;
+    const float2 *B;
+    float2 *C;
+    int64_t sA, sB, sC;        // slice strides in elements (0 = shared by all slices)
+    int32_t rank_c;            // output bits
+    int32_t nk;                // contracted bits
+    int8_t posA_c[TN_MAXR];    // output bit i -> bit of A's index (-1: label not in A)
+    int8_t posB_c[TN_MAXR];
+    int8_t posA_k[TN_MAXR];    // contracted bit j -> bit of A's index
+    int8_t posB_k[TN_MAXR];
+};
+
+// Complex GEMM C[m, n] = sum_k A[m, k] * B[n, k] with A = [M][K] and B = [N][K] row-major per
+// slice and C written at pdep(m -> posC_m) | pdep(n -> posC_n), i.e. in the consumer's order.
+struct GemmDesc {
+    const float2 *A;
+    const float2 *B;
+    float2 *C;
+    int64_t sA, sB, sC;
+    int32_t lm, ln, lk;        // log2 of M, N, K
+    int8_t posC_m[TN_MAXR];    // bit i of m (0 = least significant) -> bit of C's index
+    int8_t posC_n[TN_MAXR];
+};
+
+// Slice binding and conversion of a leaf (Sec. 3.2): dst[s][i] (complex64, plan order) =
+// src[sum_j bit_j(i) << posS[j] + sum_t bit_t(slice) << posSl[t]] (complex128, network order).
+struct BindItem {
+    int64_t dst_off;           // element offset of the destination (complex64) in the arena
+    int64_t dst_sstride;       // slice stride of the destination (0 = invariant leaf)
+    int64_t src_off;           // complex128 element offset in the network buffer
+    int32_t rank;              // bits of the bound (destination) tensor
+    int32_t nsl;               // sliced labels of this leaf
+    int8_t pos_src[TN_MAXR];   // destination bit i -> source bit
+    int8_t sl_bit[8];          // which bit of the slice id fixes sliced label t
+    int8_t sl_pos[8];          // source bit of sliced label t
+};
+
+// Kernel launchers (stream-ordered; return the launch error).
+cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
+cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st);
+cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double2 *src,
+                        float2 *arena, int64_t slice_begin, int64_t slices, int32_t max_rank,
+                        cudaStream_t st);
+cudaError_t launch_accumulate(const float2 *root, int64_t root_sstride, int64_t n, int64_t slices,
+                              double2 *amps, cudaStream_t st);
+cudaError_t launch_readout(const double2 *amps, int64_t n, double *partial, int32_t n_partial,
+                           cudaStream_t st);
+cudaError_t launch_zero_f64(double2 *p, int64_t n, cudaStream_t st);
+
+// Tensor-core path: planar 16-bit operands with one power-of-two exponent per slice.
+struct ConvertDesc {
+    const float2 *src;         // complex64 source, [slices][n]
+    void *dst;                 // planar: re plane [slices][n] then im plane at +plane_stride
+    int64_t n;                 // elements per slice
+    int64_t src_sstride;
+    int64_t plane_stride;      // elements between the re and the im plane
+    int64_t dst_sstride;       // elements between slices inside one plane
+    unsigned int *amax;        // per slice, float bits of max(|re|, |im|)
+    int32_t *exps;             // per slice exponent e: stored = value * 2^-e
+    int32_t bf16;              // 0 = fp16, 1 = bf16
+};
+cudaError_t launch_amax(const ConvertDesc &d, int64_t slices, cudaStream_t st);
+cudaError_t launch_convert16(const ConvertDesc &d, int64_t slices, cudaStream_t st);
+
+struct TcGemmDesc {
+    CUtensorMap tmA;           // planar 16-bit A: [2 * slices_a][M][K], re planes then im planes
+    CUtensorMap tmB;           // planar 16-bit B: [2 * slices_b][N][K]
+    float2 *C;
+    int64_t sC;
+    int32_t lm, ln, lk;
+    int32_t a_sliced, b_sliced;  // 0: operand shared by all slices
+    int64_t slices_a, slices_b;  // slices stored per plane (1 when shared)
+    const int32_t *expA;       // per slice exponents of A and B (index 0 if shared)
+    const int32_t *expB;
+    int32_t form;              // 1 = 4M, 2 = 3M
+    int32_t bf16;
+    int8_t posC_m[TN_MAXR];
+    int8_t posC_n[TN_MAXR];
+};
+bool tc_available();
+cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st);
+// Device status word of the tensor-core kernel (bit 0: a bounded wait timed out); cleared.
+unsigned int tc_status_read_and_clear();
+// Encode a 3-D tensor map over planar 16-bit data [planes*slices][rows][K] (K contiguous).
+int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
+                         int64_t depth, int bf16);
+
+}  // namespace tn

@@ -1,0 +1,250 @@
+// CUDA-core kernels of the contraction engine: element-wise contraction of small steps, slice
+// binding of the leaves (Sec. 3.2), FP64 cross-slice accumulation and readout (Eq. lxeb_2), and
+// the per-tensor power-of-two scaling into planar 16-bit storage (Sec. 4.2, dynamic scaling).
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+__device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos) {
+    uint64_t r = 0;
+    for (int i = 0; i < n; ++i)
+        if (((x >> i) & 1ull) && pos[i] >= 0) r |= 1ull << pos[i];
+    return r;
+}
+
+// One thread per output element of C (C's own memory order), summing over the contracted
+// bits in increasing order.  Used for small and irregular steps.
+__global__ void __launch_bounds__(256) k_generic(GenericDesc d, int64_t total) {
+    __shared__ uint64_t koffA[1024], koffB[1024];
+    const int nk = d.nk;
+    const bool table = nk <= 10;
+    if (table) {
+        for (int k = threadIdx.x; k < (1 << nk); k += blockDim.x) {
+            koffA[k] = deposit((uint64_t)k, nk, d.posA_k);
+            koffB[k] = deposit((uint64_t)k, nk, d.posB_k);
+        }
+        __syncthreads();
+    }
+    const uint64_t cmask = (d.rank_c >= 63) ? ~0ull : ((1ull << d.rank_c) - 1);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = idx >> d.rank_c;
+        const uint64_t c = (uint64_t)idx & cmask;
+        const float2 *A = d.A + s * d.sA + deposit(c, d.rank_c, d.posA_c);
+        const float2 *B = d.B + s * d.sB + deposit(c, d.rank_c, d.posB_c);
+        float re = 0.f, im = 0.f;
+        const int64_t K = 1ll << nk;
+        for (int64_t k = 0; k < K; ++k) {
+            uint64_t oa, ob;
+            if (table) {
+                oa = koffA[k];
+                ob = koffB[k];
+            } else {
+                oa = deposit((uint64_t)k, nk, d.posA_k);
+                ob = deposit((uint64_t)k, nk, d.posB_k);
+            }
+            const float2 a = A[oa], b = B[ob];
+            re = fmaf(a.x, b.x, re);
+            re = fmaf(-a.y, b.y, re);
+            im = fmaf(a.x, b.y, im);
+            im = fmaf(a.y, b.x, im);
+        }
+        d.C[s * d.sC + (int64_t)c] = make_float2(re, im);
+    }
+}
+
+// Leaf binding: grid (item, slice); each block fills one bound leaf of one slice.
+__global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
+                       int64_t slice_begin) {
+    const BindItem it = items[blockIdx.x];
+    const int64_t s = blockIdx.y;
+    const uint64_t sigma = (uint64_t)(slice_begin + s);
+    uint64_t soff = 0;
+    for (int t = 0; t < it.nsl; ++t)
+        if ((sigma >> it.sl_bit[t]) & 1ull) soff |= 1ull << it.sl_pos[t];
+    const int64_t n = 1ll << it.rank;
+    float2 *dst = arena + it.dst_off + s * it.dst_sstride;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t so = deposit((uint64_t)i, it.rank, it.pos_src) | soff;
+        const double2 v = src[it.src_off + (int64_t)so];
+        dst[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// amps[x] += sum over slices s (in increasing order) of root[s][x], in FP64.
+__global__ void k_accumulate(const float2 *root, int64_t sstride, int64_t n, int64_t slices,
+                             double2 *amps) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc = amps[x];
+        for (int64_t s = 0; s < slices; ++s) {
+            const float2 v = root[s * sstride + x];
+            acc.x += (double)v.x;
+            acc.y += (double)v.y;
+        }
+        amps[x] = acc;
+    }
+}
+
+// FP64 readout, pass 1: block partial sums of p = |a|^2 and p^2 (fixed order per block).
+__global__ void __launch_bounds__(256) k_readout_partial(const double2 *amps, int64_t n,
+                                                         double *partial) {
+    __shared__ double s1[256], s2[256];
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = amps[x];
+        const double p = v.x * v.x + v.y * v.y;
+        a1 += p;
+        a2 += p * p;
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s1[0];
+        partial[2 * blockIdx.x + 1] = s2[0];
+    }
+}
+
+// Pass 2: one thread sums the block partials in block order.
+__global__ void k_readout_final(double *partial, int32_t n_partial) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a1 = 0.0, a2 = 0.0;
+    for (int i = 0; i < n_partial; ++i) {
+        a1 += partial[2 * i];
+        a2 += partial[2 * i + 1];
+    }
+    partial[0] = a1;
+    partial[1] = a2;
+}
+
+__global__ void k_zero_f64(double2 *p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = make_double2(0.0, 0.0);
+}
+
+// max(|re|, |im|) per slice, as float bits (non-negative floats order like unsigned ints).
+__global__ void __launch_bounds__(256) k_amax(ConvertDesc d) {
+    const int64_t s = blockIdx.y;
+    const float4 *src = reinterpret_cast<const float4 *>(d.src + s * d.src_sstride);
+    const int64_t n2 = d.n >> 1;  // two complex numbers per float4
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = src[i];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    if ((d.n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const float2 v = d.src[s * d.src_sstride + d.n - 1];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(d.amax + s, __float_as_uint(m));
+}
+
+__device__ __forceinline__ int scale_exponent(unsigned int amax_bits) {
+    const float a = __uint_as_float(amax_bits);
+    if (!(a > 0.f) || !isfinite(a)) return 0;
+    return ilogbf(a) - 14;  // stored max lands in [2^14, 2^15): inside FP16's range
+}
+
+// complex64 -> planar 16-bit: stored = value * 2^-e (exact power-of-two scaling).
+__global__ void __launch_bounds__(256) k_convert16(ConvertDesc d) {
+    const int64_t s = blockIdx.y;
+    const int e = scale_exponent(d.amax[s]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.exps[s] = e;
+    const float2 *src = d.src + s * d.src_sstride;
+    const int64_t base = s * d.dst_sstride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (d.n >> 1);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = reinterpret_cast<const float4 *>(src)[i];
+        const float r0 = ldexpf(v.x, -e), i0 = ldexpf(v.y, -e);
+        const float r1 = ldexpf(v.z, -e), i1 = ldexpf(v.w, -e);
+        if (d.bf16) {
+            __nv_bfloat16 *re = reinterpret_cast<__nv_bfloat16 *>(d.dst) + base;
+            __nv_bfloat16 *imp = re + d.plane_stride;
+            reinterpret_cast<__nv_bfloat162 *>(re)[i] = __floats2bfloat162_rn(r0, r1);
+            reinterpret_cast<__nv_bfloat162 *>(imp)[i] = __floats2bfloat162_rn(i0, i1);
+        } else {
+            __half *re = reinterpret_cast<__half *>(d.dst) + base;
+            __half *imp = re + d.plane_stride;
+            reinterpret_cast<__half2 *>(re)[i] = __floats2half2_rn(r0, r1);
+            reinterpret_cast<__half2 *>(imp)[i] = __floats2half2_rn(i0, i1);
+        }
+    }
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st) {
+    const int64_t total = slices << d.rank_c;
+    k_generic<<<grid_for(total, 256), 256, 0, st>>>(d, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double2 *src,
+                        float2 *arena, int64_t slice_begin, int64_t slices, int32_t max_rank,
+                        cudaStream_t st) {
+    if (n_items == 0 || slices == 0) return cudaSuccess;
+    const int threads = max_rank >= 8 ? 256 : (max_rank >= 6 ? 64 : 32);
+    k_bind<<<dim3((unsigned)n_items, (unsigned)slices), threads, 0, st>>>(items_dev, src, arena,
+                                                                          slice_begin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const float2 *root, int64_t root_sstride, int64_t n, int64_t slices,
+                              double2 *amps, cudaStream_t st) {
+    k_accumulate<<<grid_for(n, 256), 256, 0, st>>>(root, root_sstride, n, slices, amps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_readout(const double2 *amps, int64_t n, double *partial, int32_t n_partial,
+                           cudaStream_t st) {
+    k_readout_partial<<<n_partial, 256, 0, st>>>(amps, n, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_readout_final<<<1, 32, 0, st>>>(partial, n_partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_f64(double2 *p, int64_t n, cudaStream_t st) {
+    k_zero_f64<<<grid_for(n, 256), 256, 0, st>>>(p, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amax(const ConvertDesc &d, int64_t slices, cudaStream_t st) {
+    const int gx = grid_for((d.n + 1) / 2, 256);
+    const int g = gx > 1024 ? 1024 : gx;
+    k_amax<<<dim3((unsigned)g, (unsigned)slices), 256, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert16(const ConvertDesc &d, int64_t slices, cudaStream_t st) {
+    const int gx = grid_for(d.n / 2, 256);
+    const int g = gx > 2048 ? 2048 : gx;
+    k_convert16<<<dim3((unsigned)g, (unsigned)slices), 256, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+}  // namespace tn

@@ -1,0 +1,226 @@
+"""Python binding of the C ABI in ``include/tn.h`` (libtn.so): argument marshalling only.
+
+Every step of the contraction runs in libtn.so's CUDA kernels.  PyTorch supplies device memory
+(amplitude buffers, optional workspace) and streams.  If libtn.so is missing this module raises;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtn.so")
+
+TN_OK = 0
+STATUS = {0: "TN_OK", 1: "TN_ERR_INVALID_ARG", 2: "TN_ERR_SHAPE", 3: "TN_ERR_PATH",
+          4: "TN_ERR_OOM", 5: "TN_ERR_CUDA", 6: "TN_ERR_TIMEOUT", 7: "TN_ERR_UNSUPPORTED",
+          8: "TN_ERR_NUMERIC"}
+PRECISION = {"c64": 0, "tf32": 1, "split_tf32": 2, "fp16_scaled": 3, "bf16_scaled": 4,
+             "split_bf16": 5, "split_fp16": 6, "mixed": 7}
+GEMM_FORM = {"auto": 0, "4m": 1, "3m": 2}
+KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc"}
+
+# Every symbol declared in include/tn.h.
+EXPORTS = ("tn_network_load", "tn_network_set_data", "tn_plan", "tn_plan_get_info",
+           "tn_plan_get_step_info", "tn_contract", "tn_contract_host", "tn_readout",
+           "tn_destroy", "tn_status_string", "tn_last_error_detail")
+
+
+class PlanOptions(C.Structure):
+    _fields_ = [("max_slices_in_flight", C.c_int64), ("workspace_limit", C.c_int64),
+                ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
+                ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
+                ("profile", C.c_int32), ("reserved", C.c_int32 * 8)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("num_steps", C.c_int64), ("num_slices", C.c_int64),
+                ("slices_in_flight", C.c_int64), ("workspace_bytes", C.c_int64),
+                ("num_open", C.c_int32), ("max_log2_size", C.c_int32),
+                ("tcc_per_slice", C.c_double), ("tcc_invariant", C.c_double),
+                ("tmc_per_slice", C.c_double), ("num_tc_steps", C.c_int32),
+                ("num_gemm_steps", C.c_int32), ("num_stream_steps", C.c_int32),
+                ("num_generic_steps", C.c_int32), ("kernel_launches", C.c_int64),
+                ("reserved", C.c_int32 * 6)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("slice_dependent", C.c_int32), ("log2_m", C.c_int32),
+                ("log2_n", C.c_int32), ("log2_k", C.c_int32), ("log2_batch", C.c_int32),
+                ("log2_a", C.c_int32), ("log2_b", C.c_int32), ("log2_c", C.c_int32),
+                ("gemm_form", C.c_int32), ("tcc", C.c_double), ("time_ms", C.c_double),
+                ("launches", C.c_int64), ("reserved", C.c_int32 * 2)]
+
+
+class TnError(RuntimeError):
+    def __init__(self, status, detail):
+        super().__init__("%s: %s" % (STATUS.get(status, status), detail))
+        self.status = status
+        self.detail = detail
+
+
+_lib = None
+
+
+def lib():
+    """Load libtn.so (built by ``__graft_entry__.build()``); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtn.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.tn_network_load.argtypes = [i32, vp, vp, vp, vp, i32, vp, C.POINTER(vp)]
+        L.tn_network_set_data.argtypes = [vp, vp]
+        L.tn_plan.argtypes = [vp, i32, vp, i32, vp, C.c_int, C.POINTER(PlanOptions),
+                              C.POINTER(vp)]
+        L.tn_plan_get_info.argtypes = [vp, C.POINTER(PlanInfo)]
+        L.tn_plan_get_step_info.argtypes = [vp, i64, C.POINTER(StepInfo)]
+        L.tn_contract.argtypes = [vp, i64, i64, vp, vp]
+        L.tn_contract_host.argtypes = [vp, i64, i64, vp, vp]
+        L.tn_readout.argtypes = [vp, vp, i32, vp, vp]
+        L.tn_destroy.argtypes = [vp]
+        L.tn_destroy.restype = None
+        L.tn_status_string.argtypes = [C.c_int]
+        L.tn_status_string.restype = C.c_char_p
+        L.tn_last_error_detail.argtypes = [vp, C.c_size_t]
+        for name in EXPORTS:
+            if name not in ("tn_destroy", "tn_status_string"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != TN_OK:
+        buf = C.create_string_buffer(1024)
+        lib().tn_last_error_detail(buf, 1024)
+        raise TnError(status, buf.value.decode(errors="replace"))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Network:
+    """A tensor network on the device (tn_network_load)."""
+
+    def __init__(self, tensors, labels, open_labels):
+        self._keep = []
+        n = len(tensors)
+        arrs = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+        ranks = np.array([a.ndim for a in arrs], dtype=np.int32)
+        labs = [np.ascontiguousarray(np.asarray(l, dtype=np.int32)) for l in labels]
+        dims = [np.ascontiguousarray(np.asarray(a.shape, dtype=np.int64)) for a in arrs]
+        lab_p = (C.c_void_p * n)(*[l.ctypes.data for l in labs])
+        dim_p = (C.c_void_p * n)(*[d.ctypes.data for d in dims])
+        dat_p = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
+        op = np.ascontiguousarray(np.asarray(open_labels, dtype=np.int32))
+        h = C.c_void_p()
+        _check(lib().tn_network_load(n, ranks.ctypes.data, lab_p, dim_p, dat_p, len(op),
+                                     op.ctypes.data if len(op) else None, C.byref(h)))
+        self.handle = h
+        self.num_tensors = n
+        self.num_open = len(op)
+        self.data_bytes = sum(a.nbytes for a in arrs)
+
+    @classmethod
+    def from_workload(cls, net):
+        return cls(net.tensors, net.labels, net.open_labels)
+
+    def set_data(self, tensors):
+        arrs = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+        dat_p = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        _check(lib().tn_network_set_data(self.handle, dat_p))
+
+    def close(self):
+        if self.handle:
+            lib().tn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """An execution plan (tn_plan) over a Network."""
+
+    def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
+                 workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
+                 profile=False, use_graph=False):
+        self.network = network
+        opts = PlanOptions()
+        opts.max_slices_in_flight = int(max_slices_in_flight)
+        opts.workspace_limit = int(workspace_limit)
+        self._workspace = workspace  # a torch tensor kept alive by the plan
+        if workspace is not None:
+            opts.workspace = C.c_void_p(workspace.data_ptr())
+            opts.workspace_limit = int(workspace.numel() * workspace.element_size())
+        opts.gemm_form = GEMM_FORM[gemm_form]
+        opts.sync_each_call = 1 if sync_each_call else 0
+        opts.profile = 1 if profile else 0
+        opts.use_graph = 1 if use_graph else 0
+        pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
+        sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
+        h = C.c_void_p()
+        _check(lib().tn_plan(network.handle, len(path), pp.ctypes.data if pp.size else None,
+                             len(sl), sl.ctypes.data if sl.size else None, PRECISION[mode],
+                             C.byref(opts), C.byref(h)))
+        self.handle = h
+        self.mode = mode
+
+    def info(self) -> dict:
+        i = PlanInfo()
+        _check(lib().tn_plan_get_info(self.handle, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
+
+    def step_info(self, step: int) -> dict:
+        s = StepInfo()
+        _check(lib().tn_plan_get_step_info(self.handle, int(step), C.byref(s)))
+        d = {f: getattr(s, f) for f, _ in StepInfo._fields_ if f != "reserved"}
+        d["kernel_name"] = KERNELS.get(d["kernel"], "?")
+        return d
+
+    def contract(self, amps, slice_begin=0, slice_end=None, stream=None):
+        """amps: torch complex128 CUDA tensor of 2^num_open entries; results are added."""
+        if slice_end is None:
+            slice_end = self.info()["num_slices"]
+        _check(lib().tn_contract(self.handle, int(slice_begin), int(slice_end),
+                                 C.c_void_p(amps.data_ptr()), _stream_ptr(stream)))
+
+    def contract_host(self, slice_begin=0, slice_end=None, stream=None, out=None):
+        """Contract into a host complex128 numpy array (synchronises)."""
+        if slice_end is None:
+            slice_end = self.info()["num_slices"]
+        n = 1 << self.network.num_open
+        if out is None:
+            out = np.zeros(n, dtype=np.complex128)
+        _check(lib().tn_contract_host(self.handle, int(slice_begin), int(slice_end),
+                                      C.c_void_p(out.ctypes.data), _stream_ptr(stream)))
+        return out
+
+    def readout(self, amps, n_qubits, stream=None):
+        out = np.zeros(4, dtype=np.float64)
+        _check(lib().tn_readout(self.handle, C.c_void_p(amps.data_ptr()), int(n_qubits),
+                                C.c_void_p(out.ctypes.data), _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().tn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

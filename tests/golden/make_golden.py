@@ -1,0 +1,50 @@
+"""Write the stored expected amplitudes of the named workloads.
+
+Every value here comes from the CPU oracle's state-vector simulator (oracle.statevector, a
+brute-force application of every gate matrix to the full 2^n state), read at the workload's open
+subspace.  Nothing here touches the GPU path.
+
+    python tests/golden/make_golden.py [small|bench ...]
+"""
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from oracle import oracle as O  # noqa: E402
+from paper_2310_03978_gb300 import workload as W  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def write(name, wl):
+    t0 = time.time()
+    net = wl.network
+    sv = O.statevector(wl.circuit.n_qubits, wl.circuit.gates)
+    idx = [W.full_index(net.n_qubits, net.open_qubits, net.closed_bits, x)
+           for x in range(1 << len(net.open_qubits))]
+    amps = sv[idx]
+    norm = float(np.sum(np.abs(sv) ** 2))
+    del sv
+    path = os.path.join(HERE, name + ".amps.txt")
+    with open(path, "w") as f:
+        f.write("# %s: %d qubits, open qubits %s, closed bits seeded; amplitudes from the\n"
+                % (wl.name, net.n_qubits, net.open_qubits))
+        f.write("# oracle state vector (qubit 0 = MSB), index = open bits, first open qubit = MSB\n")
+        f.write("# full-state norm %.17g, oracle threads %d, %.1f s\n"
+                % (norm, O.num_threads(), time.time() - t0))
+        for a in amps:
+            f.write("%.17e %.17e\n" % (a.real, a.imag))
+    print("wrote", path, "in %.1f s" % (time.time() - t0))
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["small", "bench"]
+    if "small" in which:
+        write("sycamore_3x4_c8_open6", W.small_workload())
+    if "bench" in which:
+        write("sycamore_5x6_c14_open10_s4", W.bench_workload())

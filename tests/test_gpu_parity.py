@@ -1,0 +1,236 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (amplitude relative L2 error against FP64):
+  complex64 path            <= 1e-5
+  FP16 / BF16 scaled path   <= 5e-3 (FP16), 1e-2 (BF16: 8-bit significand on the dense steps)
+and for the full-size circuit the ideal-sample XEB (2^n sum p^2 / sum p - 1) within 1e-3
+relative of the state-vector value.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2310_03978_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = {"c64": 1e-5, "fp16_scaled": 5e-3, "bf16_scaled": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def tn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_03978_gb300 import tn as T
+    T.lib()
+    return T
+
+
+def crandn(rng, rank, scale=1.0):
+    shape = (2,) * rank
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * scale
+
+
+def gpu_amps(tn, tensors, labels, open_labels, path, sliced=(), mode="c64", s0=0, s1=None,
+             **kw):
+    net = tn.Network(tensors, labels, open_labels)
+    plan = tn.Plan(net, path, sliced, mode=mode, sync_each_call=True, **kw)
+    amps = torch.zeros(1 << len(open_labels), dtype=torch.complex128, device="cuda")
+    plan.contract(amps, s0, s1)
+    torch.cuda.synchronize()
+    out = amps.cpu().numpy()
+    info = plan.info()
+    kernels = [plan.step_info(i)["kernel_name"] for i in range(info["num_steps"])]
+    plan.close()
+    net.close()
+    return out, info, kernels
+
+
+def read_golden(name):
+    rows = np.loadtxt(os.path.join(HERE, "golden", name + ".amps.txt"), comments="#")
+    return rows[:, 0] + 1j * rows[:, 1]
+
+
+def check(got, ref, tol):
+    err = O.rel_l2(got, ref)
+    assert err <= tol, "rel L2 %.3e > %.1e" % (err, tol)
+    return err
+
+
+# ------------------------------------------------------------------ whole circuits
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled", "bf16_scaled"])
+def test_small_circuit_vs_oracle_and_statevector(tn, mode):
+    wl = W.small_workload()
+    net = wl.network
+    ref = O.contract_network(net, wl.path)
+    got, info, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path, mode=mode)
+    check(got, ref, TOL[mode])
+    check(got, read_golden("sycamore_3x4_c8_open6"), TOL[mode])
+    assert info["num_slices"] == 1
+
+
+def test_closed_forms(tn):
+    n = 10
+    net = W.build_network(W.hadamard_circuit(n), list(range(n)), {})
+    got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels,
+                         W.greedy_path(net.labels, net.open_labels))
+    np.testing.assert_allclose(got, np.full(1 << n, 2 ** (-n / 2)), atol=1e-7)
+    net = W.build_network(W.ghz_circuit(n), list(range(n)), {})
+    got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels,
+                         W.greedy_path(net.labels, net.open_labels))
+    ref = np.zeros(1 << n, dtype=complex)
+    ref[0] = ref[-1] = 2 ** -0.5
+    np.testing.assert_allclose(got, ref, atol=1e-7)
+    circ = W.mirrored_circuit(W.random_circuit(3, 3, 5, seed=4))
+    net = W.build_network(circ, list(range(9)), {})
+    got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels,
+                         W.greedy_path(net.labels, net.open_labels))
+    ref = np.zeros(1 << 9, dtype=complex)
+    ref[0] = 1
+    np.testing.assert_allclose(got, ref, atol=1e-6)
+
+
+def test_slices_sum_to_unsliced_and_ranges_split(tn):
+    wl = W.small_workload()
+    net = wl.network
+    sl = W.greedy_slices(net.labels, net.open_labels, wl.path, 3)
+    ref = O.contract_network(net, wl.path)
+    full, info, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path, sl)
+    assert info["num_slices"] == 8
+    check(full, ref, 1e-5)
+    a, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path, sl, s0=0, s1=3)
+    b, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path, sl, s0=3, s1=8)
+    check(a + b, ref, 1e-5)
+    check(a, O.contract_network(net, wl.path, sl, 0, 3), 1e-5)
+    # one slice per launch gives the same sum
+    one, info1, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path, sl,
+                             max_slices_in_flight=1)
+    assert info1["slices_in_flight"] == 1
+    check(one, full, 1e-6)
+
+
+def test_all_open_norm_and_readout(tn):
+    circ = W.random_circuit(3, 4, 10, seed=8)
+    net = W.build_network(circ, list(range(12)), {})
+    path = W.greedy_path(net.labels, net.open_labels)
+    ref = O.statevector(12, circ.gates)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.Plan(tnet, path, (), mode="c64", sync_each_call=True)
+    amps = torch.zeros(1 << 12, dtype=torch.complex128, device="cuda")
+    plan.contract(amps)
+    got = amps.cpu().numpy()
+    check(got, ref, 1e-5)
+    r_gpu = plan.readout(amps, 12)
+    r_cpu = O.readout(got, 12)
+    np.testing.assert_allclose(r_gpu, r_cpu, rtol=1e-12, atol=1e-12)
+    assert abs(r_gpu[0] - 1) < 1e-5
+    plan.close()
+    tnet.close()
+
+
+# ------------------------------------------------------------------ single steps per kernel
+def single_step(rng, lm, ln, lk, scale=1.0, scramble=True):
+    M = list(range(0, lm))
+    N = list(range(100, 100 + ln))
+    K = list(range(200, 200 + lk))
+    la = list(rng.permutation(M + K))
+    lb = list(rng.permutation(N + K))
+    out = M + N
+    if scramble:
+        out = list(rng.permutation(out))
+    A = crandn(rng, lm + lk, scale)
+    B = crandn(rng, ln + lk, scale)
+    return [A, B], [[int(x) for x in la], [int(x) for x in lb]], [int(x) for x in out]
+
+
+@pytest.mark.parametrize("shape,kernel", [((3, 2, 2), "generic"), ((6, 5, 4), "gemm_simt"),
+                                          ((7, 6, 9), "gemm_simt"), ((5, 9, 3), "gemm_simt")])
+def test_single_step_cuda_core_kernels(tn, shape, kernel):
+    rng = np.random.default_rng(sum(shape))
+    tensors, labels, out = single_step(rng, *shape)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)])
+    assert kernels == [kernel]
+    check(got, ref, 1e-5)
+
+
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled"])
+@pytest.mark.parametrize("shape", [(7, 7, 6), (9, 8, 7), (8, 10, 8)])
+def test_single_step_tensor_core(tn, mode, shape):
+    rng = np.random.default_rng(7 + sum(shape))
+    tensors, labels, out = single_step(rng, *shape)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode=mode)
+    assert kernels == ["gemm_tc"]
+    check(got, ref, TOL[mode])
+
+
+def test_tensor_core_scaling_keeps_tiny_magnitudes(tn):
+    # amplitude-like magnitudes (2^-40) would flush to zero in FP16 without the 2^e scaling
+    rng = np.random.default_rng(3)
+    tensors, labels, out = single_step(rng, 8, 8, 7, scale=2.0 ** -20)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode="fp16_scaled")
+    assert kernels == ["gemm_tc"]
+    check(got, ref, TOL["fp16_scaled"])
+
+
+def test_tensor_core_step_with_slices_in_flight(tn):
+    # the dense step depends on the sliced bond x; 2 slices run in one launch
+    rng = np.random.default_rng(11)
+    A = crandn(rng, 16)
+    B = crandn(rng, 15)
+    v = crandn(rng, 1)
+    la = [500] + list(range(0, 8)) + list(range(200, 207))
+    lb = list(range(100, 108)) + list(range(200, 207))
+    out = list(rng.permutation(list(range(100, 108)) + list(range(0, 8))))
+    out = [int(x) for x in out]
+    tensors, labels, path = [A, B, v], [la, lb, [500]], [(0, 1), (0, 2)]
+    ref = O.contract(tensors, labels, out, path)
+    for mode in ("c64", "fp16_scaled"):
+        got, info, kernels = gpu_amps(tn, tensors, labels, out, path, [500], mode=mode)
+        assert info["slices_in_flight"] == 2
+        assert kernels[0] == ("gemm_tc" if mode == "fp16_scaled" else "gemm_simt")
+        check(got, ref, TOL[mode])
+
+
+def test_host_entry_points_and_set_data(tn):
+    wl = W.small_workload()
+    net = wl.network
+    tnet = tn.Network.from_workload(net)
+    plan = tn.Plan(tnet, wl.path, (), mode="c64")
+    got = plan.contract_host()
+    check(got, O.contract_network(net, wl.path), 1e-5)
+    # new numbers, same structure: conjugated tensors give the conjugate circuit
+    tnet.set_data([np.conj(t) for t in net.tensors])
+    got2 = plan.contract_host()
+    check(got2, np.conj(O.contract_network(net, wl.path)), 1e-5)
+    with pytest.raises(tn.TnError):
+        plan.contract_host(0, 2)  # one slice only
+    plan.close()
+    tnet.close()
+
+
+# ------------------------------------------------------------------ the full-size circuit
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+def test_bench_circuit_full_size(tn, mode):
+    golden = os.path.join(HERE, "golden", "sycamore_5x6_c14_open10_s4.amps.txt")
+    if not os.path.exists(golden):
+        pytest.skip("golden amplitudes not generated")
+    wl = W.bench_workload()
+    net = wl.network
+    ref = read_golden("sycamore_5x6_c14_open10_s4")
+    got, info, kernels = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path,
+                                  wl.sliced, mode=mode)
+    assert info["num_slices"] == 16 and info["max_log2_size"] <= 28
+    check(got, ref, TOL[mode])
+    n = wl.circuit.n_qubits
+    x_ref = O.readout(ref, n)[3]
+    x_got = O.readout(got, n)[3]
+    assert abs(x_got - x_ref) / abs(x_ref) <= 1e-3
+    if mode == "fp16_scaled":
+        assert "gemm_tc" in kernels
