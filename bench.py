@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--step", default=None,
+                    help="single-step microbench 'lm,ln,lk' (log2 of m, n, k) instead of the "
+                         "circuit: one random dense contraction with shuffled label orders")
     return ap.parse_args()
 
 
@@ -365,6 +368,50 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
+def run_step_bench(args):
+    """Single-step microbench: C[M,N] = sum_K A[M,K] B[N,K] on random complex tensors with all
+    dims 2 and seeded random label orders, timed through the C ABI (one launch per step)."""
+    import torch
+    from oracle import oracle as O
+    from paper_2310_03978_gb300 import tn
+    lm, ln, lk = (int(x) for x in args.step.split(","))
+    rng = np.random.default_rng(1000 + 37 * lm + 5 * ln + lk)
+    M, N, K = list(range(lm)), list(range(100, 100 + ln)), list(range(200, 200 + lk))
+    la = [int(x) for x in rng.permutation(M + K)]
+    lb = [int(x) for x in rng.permutation(N + K)]
+    out = [int(x) for x in rng.permutation(M + N)]
+    ra, rb = lm + lk, ln + lk
+    scale = 2.0 ** (-(ra + rb) / 4)  # amplitude-like magnitudes
+    A = (rng.standard_normal((2,) * ra) + 1j * rng.standard_normal((2,) * ra)) * scale
+    B = (rng.standard_normal((2,) * rb) + 1j * rng.standard_normal((2,) * rb)) * scale
+    net = tn.Network([A, B], [la, lb], out)
+    plan = tn.Plan(net, [(0, 1)], (), mode=args.mode, profile=True)
+    amps = torch.zeros(1 << (lm + ln), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.contract(amps, stream=stream)
+    torch.cuda.synchronize()
+    before = plan.step_info(0)
+    ms = time_contract(torch, plan, amps, args.steps, stream) / args.steps
+    si = plan.step_info(0)
+    kern_ms = (si["time_ms"] - before["time_ms"]) / max(1, si["launches"] - before["launches"])
+    tcc = si["tcc"]
+    check = None
+    if lm + ln + lk <= 22:
+        amps.zero_()
+        plan.contract(amps, stream=stream)
+        ref = O.contract([A, B], [la, lb], out, [(0, 1)])
+        check = O.rel_l2(amps.cpu().numpy(), ref)
+    print(json.dumps({"metric": "single-step effective TFLOPS", "value": tcc / (ms / 1e3) / 1e12,
+                      "unit": "TFLOPS", "kernel": si["kernel_name"], "kernel_ms": kern_ms,
+                      "kernel_tflops": tcc / (kern_ms / 1e3) / 1e12, "ms_per_step": ms,
+                      "prep_ms": (si["prep_ms"] - before["prep_ms"]) / max(1, args.steps),
+                      "config": {"lm": lm, "ln": ln, "lk": lk, "mode": args.mode},
+                      "rel_l2_vs_oracle": check}))
+    plan.close()
+    net.close()
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
     if rank != 0:
@@ -416,6 +463,9 @@ def main():
         __graft_entry__.build()
     from oracle import oracle as O
     O.build()
+    if args.step:
+        run_step_bench(args)
+        return
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

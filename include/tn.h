@@ -73,9 +73,9 @@ typedef struct {
     int32_t sync_each_call;        /* 1 = tn_contract synchronises its stream and reports
                                       asynchronous errors itself                             */
     int32_t use_graph;             /* 1 = replay the step sequence as a captured CUDA graph  */
-    int32_t profile;               /* 1 = time every tensor-core and GEMM step with CUDA events
-                                      on the contraction stream (read by
-                                      tn_plan_get_step_info after the stream is synchronised) */
+    int32_t profile;               /* 1 = time every step with CUDA events on the contraction
+                                      stream (read by tn_plan_get_step_info after the stream is
+                                      synchronised)                                           */
     int32_t reserved[8];
 } tn_plan_options;
 
@@ -106,9 +106,10 @@ typedef struct {
     int32_t log2_a, log2_b, log2_c;              /* operand and result sizes               */
     int32_t gemm_form;             /* tn_gemm_form actually used                              */
     double tcc;                    /* Eq. T_cc of one slice of this step                     */
-    double time_ms;                /* profile mode: summed CUDA-event time of its launches   */
+    double time_ms;                /* profile mode: summed CUDA-event time of its main kernel */
     int64_t launches;              /* profile mode: launches timed                           */
-    int32_t reserved[2];
+    double prep_ms;                /* profile mode: time of its operand conversions (tensor-
+                                      core steps: amax + planar 16-bit copies)               */
 } tn_step_info;
 
 /*

@@ -2,6 +2,11 @@
 // C[m, n] = sum_k A[m, k] * B[n, k] per slice, A = [M][K] and B = [N][K] row-major, the result
 // scattered into the consumer's memory order (the index reordering of Sec. 4.1 applied at the
 // producer's store, so no separate transpose pass is needed).
+//
+// Steps with few outputs and a long contraction (e.g. the last step of a circuit, which sums two
+// large halves into the amplitudes) are split along K: CTA z sums its K range into a partial
+// tile, and a second kernel adds the partials in increasing z (a fixed order, so results do not
+// depend on scheduling) and scatters the sums.
 #include "tn_internal.h"
 
 namespace tn {
@@ -24,9 +29,12 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     const int64_t s = blockIdx.y;
     const int64_t tile = blockIdx.x;
     const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-    const int64_t M = 1ll << d.lm, N = 1ll << d.ln, K = 1ll << d.lk;
-    const float2 *A = d.A + s * d.sA;
-    const float2 *B = d.B + s * d.sB;
+    const int64_t M = 1ll << d.lm, N = 1ll << d.ln;
+    const int64_t Kfull = 1ll << d.lk;
+    const int64_t K = Kfull / d.splits;  // this CTA's K range: [z * K, (z + 1) * K)
+    const int64_t kz = (int64_t)blockIdx.z * K;
+    const float2 *A = d.A + s * d.sA + kz;
+    const float2 *B = d.B + s * d.sB + kz;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
     // global -> shared mapping: 64 rows x 16 k; thread loads row (tid >> 2), k (tid & 3) * 4..+3
@@ -37,8 +45,8 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t gk = k0 + lk + q;
-            ra[q] = (gm < M && gk < K) ? A[gm * K + gk] : make_float2(0.f, 0.f);
-            rb[q] = (gn < N && gk < K) ? B[gn * K + gk] : make_float2(0.f, 0.f);
+            ra[q] = (gm < M && gk < K) ? A[gm * Kfull + gk] : make_float2(0.f, 0.f);
+            rb[q] = (gn < N && gk < K) ? B[gn * Kfull + gk] : make_float2(0.f, 0.f);
         }
     };
     auto store = [&](int buf) {
@@ -83,6 +91,20 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
         __syncthreads();
     }
 
+    if (d.splits > 1) {
+        float2 *P = d.partial + ((int64_t)blockIdx.z * gridDim.y + s) * M * N;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gm = m0 + ty + 16 * i;
+            if (gm >= M) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t gn = n0 + tx + 16 * j;
+                if (gn < N) P[gm * N + gn] = make_float2(cr[i][j], ci[i][j]);
+            }
+        }
+        return;
+    }
     float2 *C = d.C + s * d.sC;
     uint64_t coff[TN];
 #pragma unroll
@@ -100,14 +122,54 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     }
 }
 
+// Sum of the split-K partials in increasing split order, scattered into C's order.
+__global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
+    const int64_t MN = 1ll << (d.lm + d.ln);
+    const int64_t total = slices * MN;
+    const uint64_t nmask = (1ull << d.ln) - 1;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = idx / MN, e = idx % MN;
+        float re = 0.f, im = 0.f;
+        for (int z = 0; z < d.splits; ++z) {
+            const float2 v = d.partial[((int64_t)z * slices + s) * MN + e];
+            re += v.x;
+            im += v.y;
+        }
+        const uint64_t m = (uint64_t)e >> d.ln, n = (uint64_t)e & nmask;
+        d.C[s * d.sC + (int64_t)(deposit(m, d.lm, d.posC_m) | deposit(n, d.ln, d.posC_n))] =
+            make_float2(re, im);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st) {
     const int64_t M = 1ll << d.lm, N = 1ll << d.ln;
     const int64_t tm = (M + BM - 1) / BM, tn_ = (N + BN - 1) / BN;
-    if (tm * tn_ > 0x7fffffffll || slices > 65535) return cudaErrorInvalidConfiguration;
-    k_gemm_simt<<<dim3((unsigned)(tm * tn_), (unsigned)slices), 256, 0, st>>>(d, tn_);
+    if (tm * tn_ > 0x7fffffffll || slices > 65535 || d.splits < 1 || d.splits > 65535 ||
+        ((1ll << d.lk) % d.splits) != 0 || (d.splits > 1 && !d.partial))
+        return cudaErrorInvalidConfiguration;
+    k_gemm_simt<<<dim3((unsigned)(tm * tn_), (unsigned)slices, (unsigned)d.splits), 256, 0, st>>>(
+        d, tn_);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || d.splits == 1) return e;
+    const int64_t total = slices << (d.lm + d.ln);
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_splitk_reduce<<<(unsigned)blocks, 256, 0, st>>>(d, slices);
     return cudaGetLastError();
+}
+
+// Number of K splits for a CUDA-core GEMM step: enough CTAs to fill the GPU a few times when
+// the output tiles alone cannot, with at least 256 contracted elements per split.
+int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {
+    const int64_t tiles = ((1ll << lm) + BM - 1) / BM * (((1ll << ln) + BN - 1) / BN) * slices;
+    int splits = 1;
+    while (tiles * splits < 4 * 152 && (lk - 8) > 0 && (1ll << lk) / (splits * 2) >= 256 &&
+           splits < 4096)
+        splits *= 2;
+    return splits;
 }
 
 }  // namespace tn

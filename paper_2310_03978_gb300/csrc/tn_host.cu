@@ -104,9 +104,11 @@ struct Step {
     int t = 0;                   // op time
     int pa = -1, pb = -1;        // planar copies for K_TC
     int form = TN_GEMM_4M;
+    int splits = 1;              // K_GEMM split-K factor
+    int64_t part_off = -1;       // K_GEMM split-K partials (byte offset in the arena)
     // profile mode: recorded (start, stop) event pairs not yet read, and the running totals
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
-    double time_ms = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pending_prep;
+    double time_ms = 0, prep_ms = 0;
     int64_t timed = 0;
 };
 
@@ -170,7 +172,9 @@ int route(const Step &s, tn_precision mode, bool tc_ok) {
     const bool tc_mode = mode == TN_PREC_FP16_SCALED || mode == TN_PREC_BF16_SCALED ||
                          mode == TN_PREC_MIXED;
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 6) return K_TC;
-    if (s.batch.empty() && lm >= 5 && ln >= 5 && lk >= 3) return K_GEMM;
+    // register-tiled GEMM (split along K when the output is small); a contraction of fewer than
+    // 16 elements is cheaper as an element-wise pass with coalesced stores
+    if (s.batch.empty() && lk >= 4 && lm >= 3 && ln >= 3 && lm + ln + lk >= 14) return K_GEMM;
     return K_GENERIC;
 }
 
@@ -362,12 +366,26 @@ int64_t layout_bytes(tn_plan_t *p, int64_t sb, bool commit) {
         items.push_back({align_up(bytes, 1024), {q.t - 2, q.t}});
         who.push_back(-(int)i - 1);
     }
+    const int npl = (int)p->planars.size();
+    for (size_t i = 0; i < p->steps.size(); ++i) {
+        Step &st = p->steps[i];
+        if (st.kernel != K_GEMM) continue;
+        const int64_t sl = st.dep ? sb : 1;
+        const int sp = tn::gemm_simt_splits((int)st.M.size(), (int)st.N.size(),
+                                            (int)st.K.size(), sl);
+        if (commit) st.splits = sp;
+        if (sp <= 1) continue;
+        const int64_t bytes = (int64_t)sp * sl * ((int64_t)8 << (st.M.size() + st.N.size()));
+        items.push_back({align_up(bytes, 256), {st.t, st.t}});
+        who.push_back(-(npl + (int)i) - 1);
+    }
     std::vector<int64_t> offs;
     int64_t peak = place(items, offs);
     if (commit) {
         for (size_t i = 0; i < who.size(); ++i) {
             if (who[i] >= 0) p->tensors[who[i]].off = offs[i] / 8;
-            else p->planars[-who[i] - 1].off = offs[i];
+            else if (-who[i] - 1 < npl) p->planars[-who[i] - 1].off = offs[i];
+            else p->steps[-who[i] - 1 - npl].part_off = offs[i];
         }
     }
     return align_up(peak, 1024);
@@ -522,6 +540,19 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         auto pos_in = [&](const std::vector<int> &v, int l) {
             return (int)(std::find(v.begin(), v.end(), l) - v.begin());
         };
+        // Operand roles of a GEMM step: the tensor-core epilogue maps consecutive lanes to
+        // consecutive rows (m), the CUDA-core one maps them to consecutive columns (n); give the
+        // label at bit 0 of the result to the side whose stores are then contiguous.
+        if ((st.kernel == K_TC || st.kernel == K_GEMM) && !co.empty()) {
+            const int low = co.back();
+            const bool low_in_m = std::find(st.M.begin(), st.M.end(), low) != st.M.end();
+            const bool want_m = st.kernel == K_TC;
+            if (low_in_m != want_m) {
+                std::swap(st.a, st.b);
+                std::swap(st.la, st.lb);
+                std::swap(st.M, st.N);
+            }
+        }
         std::vector<int> oa, ob;
         for (int l : co) {
             if (std::find(st.la.begin(), st.la.end(), l) != st.la.end()) oa.push_back(l);
@@ -728,29 +759,41 @@ tn_status build_descriptors(tn_plan_t *p) {
     return TN_OK;
 }
 
-tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStream_t stream,
-                         const std::pair<cudaEvent_t, cudaEvent_t> *ev);
+using EventPair = std::pair<cudaEvent_t, cudaEvent_t>;
 
-// Launch one step; in profile mode the GEMM launch of a tensor-core or CUDA-core GEMM step is
-// bracketed by a pair of CUDA events on the contraction stream.
-tn_status run_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stream) {
-    const bool prof = p->opts.profile && (st.kernel == K_TC || st.kernel == K_GEMM);
-    if (!prof) return run_step_inner(p, st, slices, stream, nullptr);
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStream_t stream,
+                         const EventPair *ev, const EventPair *prep);
+
+tn_status take_events(tn_plan_t *p, EventPair &ev) {
     if (!p->event_pool.empty()) {
         ev = p->event_pool.back();
         p->event_pool.pop_back();
-    } else {
-        TN_CUDA(cudaEventCreate(&ev.first));
-        TN_CUDA(cudaEventCreate(&ev.second));
+        return TN_OK;
     }
-    tn_status s = run_step_inner(p, st, slices, stream, &ev);
+    TN_CUDA(cudaEventCreate(&ev.first));
+    TN_CUDA(cudaEventCreate(&ev.second));
+    return TN_OK;
+}
+
+// Launch one step; in profile mode its main kernel (and, for a tensor-core step, its operand
+// conversions) are bracketed by CUDA events on the contraction stream.
+tn_status run_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stream) {
+    if (!p->opts.profile) return run_step_inner(p, st, slices, stream, nullptr, nullptr);
+    EventPair ev{nullptr, nullptr}, prep{nullptr, nullptr};
+    tn_status s = take_events(p, ev);
+    if (s != TN_OK) return s;
+    if (st.kernel == K_TC) {
+        s = take_events(p, prep);
+        if (s != TN_OK) return s;
+    }
+    s = run_step_inner(p, st, slices, stream, &ev, st.kernel == K_TC ? &prep : nullptr);
     st.pending.push_back(ev);
+    if (st.kernel == K_TC) st.pending_prep.push_back(prep);
     return s;
 }
 
 tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStream_t stream,
-                         const std::pair<cudaEvent_t, cudaEvent_t> *ev) {
+                         const EventPair *ev, const EventPair *prep) {
     const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
     float2 *arena = reinterpret_cast<float2 *>(p->arena);
     const int64_t sA = A.dep ? ((int64_t)1 << A.rank()) : 0;
@@ -759,6 +802,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
     cudaError_t e = cudaSuccess;
     if (st.kernel == K_TC) {
         const int si = (int)(&st - &p->steps[0]);
+        if (prep) TN_CUDA(cudaEventRecord(prep->first, stream));
         for (int side = 0; side < 2; ++side) {
             const Planar &q = p->planars[side ? st.pb : st.pa];
             const Tensor &X = side ? B : A;
@@ -777,6 +821,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             TN_CUDA(tn::launch_amax(cd, sx, stream));
             TN_CUDA(tn::launch_convert16(cd, sx, stream));
         }
+        if (prep) TN_CUDA(cudaEventRecord(prep->second, stream));
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_gemm_tc(p->tc_desc[si], slices, stream);
         if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
@@ -792,12 +837,15 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         d.lm = (int)st.M.size();
         d.ln = (int)st.N.size();
         d.lk = (int)st.K.size();
+        d.splits = st.splits;
+        d.partial = st.part_off >= 0 ? reinterpret_cast<float2 *>(p->arena + st.part_off) : nullptr;
         fill_pos(d.posC_m, TN_MAXR, -1);
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
         for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_gemm_simt(d, slices, stream);
+        if (st.splits > 1) p->launches += 1;
         if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
         p->launches += 1;
     } else {
@@ -825,7 +873,9 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             d.posA_k[j] = (int8_t)A.pos(l);
             d.posB_k[j] = (int8_t)B.pos(l);
         }
+        if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_generic(d, slices, stream);
+        if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
         p->launches += 1;
     }
     if (e != cudaSuccess)
@@ -894,8 +944,17 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
         mp->event_pool.push_back(ev);
     }
     ms.pending.clear();
+    for (auto &ev : ms.pending_prep) {
+        float ms_ = 0.f;
+        TN_CUDA(cudaEventSynchronize(ev.second));
+        TN_CUDA(cudaEventElapsedTime(&ms_, ev.first, ev.second));
+        ms.prep_ms += ms_;
+        mp->event_pool.push_back(ev);
+    }
+    ms.pending_prep.clear();
     out->time_ms = st.time_ms;
     out->launches = st.timed;
+    out->prep_ms = st.prep_ms;
     return TN_OK;
 }
 
@@ -1007,8 +1066,10 @@ void tn_destroy(void *handle) {
         if (p->meta) cudaFree(p->meta);
         if (p->partial) cudaFree(p->partial);
         if (p->amps_tmp) cudaFree(p->amps_tmp);
-        for (auto &st : p->steps)
+        for (auto &st : p->steps) {
             for (auto &ev : st.pending) p->event_pool.push_back(ev);
+            for (auto &ev : st.pending_prep) p->event_pool.push_back(ev);
+        }
         for (auto &ev : p->event_pool) {
             cudaEventDestroy(ev.first);
             cudaEventDestroy(ev.second);

@@ -36,6 +36,8 @@ struct GemmDesc {
     float2 *C;
     int64_t sA, sB, sC;
     int32_t lm, ln, lk;        // log2 of M, N, K
+    int32_t splits;            // > 1: split-K; CTA z sums K range z and writes partial[z][s]
+    float2 *partial;           // split-K partial tiles, [splits][slices][M][N] row-major
     int8_t posC_m[TN_MAXR];    // bit i of m (0 = least significant) -> bit of C's index
     int8_t posC_n[TN_MAXR];
 };
@@ -56,6 +58,7 @@ struct BindItem {
 // Kernel launchers (stream-ordered; return the launch error).
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st);
+int gemm_simt_splits(int lm, int ln, int lk, int64_t slices);
 cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double2 *src,
                         float2 *arena, int64_t slice_begin, int64_t slices, int32_t max_rank,
                         cudaStream_t st);

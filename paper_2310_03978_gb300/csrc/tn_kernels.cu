@@ -17,48 +17,64 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
     return r;
 }
 
-// One thread per output element of C (C's own memory order), summing over the contracted
-// bits in increasing order.  Used for small and irregular steps.
+// One thread per output element of C (in C's own memory order, so stores are coalesced),
+// summing over the contracted bits in increasing order.  A block walks chunks of 2^LB
+// consecutive outputs; the operand offsets of the chunk's low LB bits come from shared-memory
+// tables built once per block, those of the high bits are computed once per chunk.
 __global__ void __launch_bounds__(256) k_generic(GenericDesc d, int64_t total) {
     __shared__ uint64_t koffA[1024], koffB[1024];
+    __shared__ uint64_t loA[1024], loB[1024];
     const int nk = d.nk;
     const bool table = nk <= 10;
+    const int lb = d.rank_c < 10 ? d.rank_c : 10;
+    for (int j = threadIdx.x; j < (1 << lb); j += blockDim.x) {
+        loA[j] = deposit((uint64_t)j, lb, d.posA_c);
+        loB[j] = deposit((uint64_t)j, lb, d.posB_c);
+    }
     if (table) {
         for (int k = threadIdx.x; k < (1 << nk); k += blockDim.x) {
             koffA[k] = deposit((uint64_t)k, nk, d.posA_k);
             koffB[k] = deposit((uint64_t)k, nk, d.posB_k);
         }
-        __syncthreads();
     }
+    __syncthreads();
     const uint64_t cmask = (d.rank_c >= 63) ? ~0ull : ((1ull << d.rank_c) - 1);
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = idx >> d.rank_c;
-        const uint64_t c = (uint64_t)idx & cmask;
-        const float2 *A = d.A + s * d.sA + deposit(c, d.rank_c, d.posA_c);
-        const float2 *B = d.B + s * d.sB + deposit(c, d.rank_c, d.posB_c);
-        float re = 0.f, im = 0.f;
-        const int64_t K = 1ll << nk;
-        for (int64_t k = 0; k < K; ++k) {
-            uint64_t oa, ob;
-            if (table) {
-                oa = koffA[k];
-                ob = koffB[k];
-            } else {
-                oa = deposit((uint64_t)k, nk, d.posA_k);
-                ob = deposit((uint64_t)k, nk, d.posB_k);
+    const int64_t nchunks = total >> lb;
+    const int64_t K = 1ll << nk;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = ch << lb;
+        const int64_t s = base >> d.rank_c;
+        const uint64_t c0 = (uint64_t)base & cmask;
+        const uint64_t hA = deposit(c0 >> lb, d.rank_c - lb, d.posA_c + lb);
+        const uint64_t hB = deposit(c0 >> lb, d.rank_c - lb, d.posB_c + lb);
+        const float2 *Ab = d.A + s * d.sA + hA;
+        const float2 *Bb = d.B + s * d.sB + hB;
+        float2 *Cb = d.C + s * d.sC + (int64_t)c0;
+        for (int j = threadIdx.x; j < (1 << lb); j += blockDim.x) {
+            const float2 *A = Ab + loA[j];
+            const float2 *B = Bb + loB[j];
+            float re = 0.f, im = 0.f;
+            for (int64_t k = 0; k < K; ++k) {
+                uint64_t oa, ob;
+                if (table) {
+                    oa = koffA[k];
+                    ob = koffB[k];
+                } else {
+                    oa = deposit((uint64_t)k, nk, d.posA_k);
+                    ob = deposit((uint64_t)k, nk, d.posB_k);
+                }
+                const float2 a = A[oa], b = B[ob];
+                re = fmaf(a.x, b.x, re);
+                re = fmaf(-a.y, b.y, re);
+                im = fmaf(a.x, b.y, im);
+                im = fmaf(a.y, b.x, im);
             }
-            const float2 a = A[oa], b = B[ob];
-            re = fmaf(a.x, b.x, re);
-            re = fmaf(-a.y, b.y, re);
-            im = fmaf(a.x, b.y, im);
-            im = fmaf(a.y, b.x, im);
+            Cb[j] = make_float2(re, im);
         }
-        d.C[s * d.sC + (int64_t)c] = make_float2(re, im);
     }
 }
 
-// Leaf binding: grid (item, slice); each block fills one bound leaf of one slice.
+// Leaf binding: grid (item, slice, chunk); the blocks of one (item, slice) share its elements.
 __global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
                        int64_t slice_begin) {
     const BindItem it = items[blockIdx.x];
@@ -69,7 +85,8 @@ __global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
         if ((sigma >> it.sl_bit[t]) & 1ull) soff |= 1ull << it.sl_pos[t];
     const int64_t n = 1ll << it.rank;
     float2 *dst = arena + it.dst_off + s * it.dst_sstride;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = blockIdx.z * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.z * blockDim.x) {
         const uint64_t so = deposit((uint64_t)i, it.rank, it.pos_src) | soff;
         const double2 v = src[it.src_off + (int64_t)so];
         dst[i] = make_float2((float)v.x, (float)v.y);
@@ -199,7 +216,10 @@ int grid_for(int64_t work, int threads) {
 
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st) {
     const int64_t total = slices << d.rank_c;
-    k_generic<<<grid_for(total, 256), 256, 0, st>>>(d, total);
+    const int lb = d.rank_c < 10 ? d.rank_c : 10;
+    int64_t blocks = total >> lb;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_generic<<<(unsigned)blocks, 256, 0, st>>>(d, total);
     return cudaGetLastError();
 }
 
@@ -208,8 +228,11 @@ cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double
                         cudaStream_t st) {
     if (n_items == 0 || slices == 0) return cudaSuccess;
     const int threads = max_rank >= 8 ? 256 : (max_rank >= 6 ? 64 : 32);
-    k_bind<<<dim3((unsigned)n_items, (unsigned)slices), threads, 0, st>>>(items_dev, src, arena,
-                                                                          slice_begin);
+    int64_t chunks = ((1ll << max_rank) + threads * 8 - 1) / (threads * 8);
+    if (chunks > 1024) chunks = 1024;
+    if (chunks < 1) chunks = 1;
+    k_bind<<<dim3((unsigned)n_items, (unsigned)slices, (unsigned)chunks), threads, 0, st>>>(
+        items_dev, src, arena, slice_begin);
     return cudaGetLastError();
 }
 

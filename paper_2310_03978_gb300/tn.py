@@ -52,7 +52,7 @@ class StepInfo(C.Structure):
                 ("log2_n", C.c_int32), ("log2_k", C.c_int32), ("log2_batch", C.c_int32),
                 ("log2_a", C.c_int32), ("log2_b", C.c_int32), ("log2_c", C.c_int32),
                 ("gemm_form", C.c_int32), ("tcc", C.c_double), ("time_ms", C.c_double),
-                ("launches", C.c_int64), ("reserved", C.c_int32 * 2)]
+                ("launches", C.c_int64), ("prep_ms", C.c_double)]
 
 
 class TnError(RuntimeError):

@@ -78,20 +78,20 @@ def test_closed_forms(tn):
     net = W.build_network(W.hadamard_circuit(n), list(range(n)), {})
     got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels,
                          W.greedy_path(net.labels, net.open_labels))
-    np.testing.assert_allclose(got, np.full(1 << n, 2 ** (-n / 2)), atol=1e-7)
+    check(got, np.full(1 << n, 2 ** (-n / 2)), TOL["c64"])
     net = W.build_network(W.ghz_circuit(n), list(range(n)), {})
     got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels,
                          W.greedy_path(net.labels, net.open_labels))
     ref = np.zeros(1 << n, dtype=complex)
     ref[0] = ref[-1] = 2 ** -0.5
-    np.testing.assert_allclose(got, ref, atol=1e-7)
+    check(got, ref, TOL["c64"])
     circ = W.mirrored_circuit(W.random_circuit(3, 3, 5, seed=4))
     net = W.build_network(circ, list(range(9)), {})
     got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels,
                          W.greedy_path(net.labels, net.open_labels))
     ref = np.zeros(1 << 9, dtype=complex)
     ref[0] = 1
-    np.testing.assert_allclose(got, ref, atol=1e-6)
+    check(got, ref, TOL["c64"])
 
 
 def test_slices_sum_to_unsliced_and_ranges_split(tn):
@@ -147,8 +147,16 @@ def single_step(rng, lm, ln, lk, scale=1.0, scramble=True):
     return [A, B], [[int(x) for x in la], [int(x) for x in lb]], [int(x) for x in out]
 
 
-@pytest.mark.parametrize("shape,kernel", [((3, 2, 2), "generic"), ((6, 5, 4), "gemm_simt"),
-                                          ((7, 6, 9), "gemm_simt"), ((5, 9, 3), "gemm_simt")])
+@pytest.mark.parametrize("shape,kernel", [
+    ((3, 2, 2), "generic"),      # tiny
+    ((9, 9, 2), "generic"),      # outer-product-like: 2^18 outputs, k = 4
+    ((2, 2, 11), "generic"),     # k > 2^10: offsets computed without the shared table
+    ((6, 5, 4), "gemm_simt"),
+    ((7, 6, 9), "gemm_simt"),
+    ((5, 9, 4), "gemm_simt"),
+    ((6, 4, 14), "gemm_simt"),   # few outputs, long contraction: split along K
+    ((3, 3, 13), "gemm_simt"),
+])
 def test_single_step_cuda_core_kernels(tn, shape, kernel):
     rng = np.random.default_rng(sum(shape))
     tensors, labels, out = single_step(rng, *shape)
@@ -156,6 +164,15 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
     got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)])
     assert kernels == [kernel]
     check(got, ref, 1e-5)
+    # the same step with 4 slices in flight (a sliced bond on a rank-1 factor of A)
+    A, B = tensors
+    v = crandn(rng, 1)
+    t2 = [A[None] * v.reshape(2, *([1] * A.ndim)), B, np.ones(2, complex)]
+    l2 = [[900] + labels[0], labels[1], [900]]
+    ref2 = O.contract(t2, l2, out, [(0, 1), (0, 2)])
+    got2, info, _ = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900])
+    assert info["slices_in_flight"] == 2
+    check(got2, ref2, 1e-5)
 
 
 @pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled"])
