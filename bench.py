@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fp16_scaled")
+    ap.add_argument("--gemm-form", default="auto", choices=["auto", "4m", "3m"])
+    ap.add_argument("--tc-bk", type=int, default=0, choices=[0, 32, 64])
     ap.add_argument("--c64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -385,7 +387,8 @@ def run_step_bench(args):
     A = (rng.standard_normal((2,) * ra) + 1j * rng.standard_normal((2,) * ra)) * scale
     B = (rng.standard_normal((2,) * rb) + 1j * rng.standard_normal((2,) * rb)) * scale
     net = tn.Network([A, B], [la, lb], out)
-    plan = tn.Plan(net, [(0, 1)], (), mode=args.mode, profile=True)
+    plan = tn.Plan(net, [(0, 1)], (), mode=args.mode, profile=True, gemm_form=args.gemm_form,
+                   tc_bk=args.tc_bk)
     amps = torch.zeros(1 << (lm + ln), dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -406,7 +409,8 @@ def run_step_bench(args):
                       "unit": "TFLOPS", "kernel": si["kernel_name"], "kernel_ms": kern_ms,
                       "kernel_tflops": tcc / (kern_ms / 1e3) / 1e12, "ms_per_step": ms,
                       "prep_ms": (si["prep_ms"] - before["prep_ms"]) / max(1, args.steps),
-                      "config": {"lm": lm, "ln": ln, "lk": lk, "mode": args.mode},
+                      "config": {"lm": lm, "ln": ln, "lk": lk, "mode": args.mode,
+                                 "gemm_form": args.gemm_form, "tc_bk": args.tc_bk},
                       "rel_l2_vs_oracle": check}))
     plan.close()
     net.close()

@@ -3,6 +3,12 @@
 // scattered into the consumer's memory order (the index reordering of Sec. 4.1 applied at the
 // producer's store, so no separate transpose pass is needed).
 //
+// Accumulation is blocked: each 16-wide K tile is summed in fresh registers and then added to the
+// running sum, which keeps the FP32 rounding error of a length-K sum near sqrt(K/16 + 16) units
+// instead of sqrt(K).  The finished 64 x 64 tile is staged in shared memory and written out in
+// the order of the consumer's memory index (tile bits sorted by their position in C), so the
+// stores are contiguous whenever C's low bits fall inside the tile.
+//
 // Steps with few outputs and a long contraction (e.g. the last step of a circuit, which sums two
 // large halves into the amplitudes) are split along K: CTA z sums its K range into a partial
 // tile, and a second kernel adds the partials in increasing z (a fixed order, so results do not
@@ -24,8 +30,11 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
 
 // 256 threads as 16 x 16; each thread owns rows ty + 16*i and columns tx + 16*j (i, j < 4).
 __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) {
-    __shared__ float2 As[2][BK][BM + 1];
-    __shared__ float2 Bs[2][BK][BN + 1];
+    constexpr int AS = 2 * BK * (BM + 1), BS = 2 * BK * (BN + 1);
+    static_assert(AS + BS >= BM * BN, "staging tile must fit in the operand buffers");
+    __shared__ __align__(16) float2 sbuf[AS + BS];
+    auto As = reinterpret_cast<float2(*)[BK][BM + 1]>(sbuf);
+    auto Bs = reinterpret_cast<float2(*)[BK][BN + 1]>(sbuf + AS);
     const int64_t s = blockIdx.y;
     const int64_t tile = blockIdx.x;
     const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
@@ -70,6 +79,11 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     for (int64_t kt = 0; kt < ktiles; ++kt) {
         const int buf = kt & 1;
         if (kt + 1 < ktiles) load((kt + 1) * BK);
+        float tr[TM][TN], ti[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) tr[i][j] = ti[i][j] = 0.f;
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             float2 a[TM], b[TN];
@@ -81,12 +95,19 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) {
-                    cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
-                    cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
-                    ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
-                    ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
+                    tr[i][j] = fmaf(a[i].x, b[j].x, tr[i][j]);
+                    tr[i][j] = fmaf(-a[i].y, b[j].y, tr[i][j]);
+                    ti[i][j] = fmaf(a[i].x, b[j].y, ti[i][j]);
+                    ti[i][j] = fmaf(a[i].y, b[j].x, ti[i][j]);
                 }
         }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                cr[i][j] += tr[i][j];
+                ci[i][j] += ti[i][j];
+            }
         if (kt + 1 < ktiles) store(buf ^ 1);
         __syncthreads();
     }
@@ -105,20 +126,39 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
         }
         return;
     }
-    float2 *C = d.C + s * d.sC;
-    uint64_t coff[TN];
+    // stage the tile (row-major 64 x 64) and write it out in C's memory order
+    float2 *stage = sbuf;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) coff[j] = deposit((uint64_t)(n0 + tx + 16 * j), d.ln, d.posC_n);
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int64_t gm = m0 + ty + 16 * i;
-        if (gm >= M) continue;
-        const uint64_t roff = deposit((uint64_t)gm, d.lm, d.posC_m);
-#pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int64_t gn = n0 + tx + 16 * j;
-            if (gn < N) C[roff | coff[j]] = make_float2(cr[i][j], ci[i][j]);
+        for (int j = 0; j < TN; ++j)
+            stage[(ty + 16 * i) * BN + tx + 16 * j] = make_float2(cr[i][j], ci[i][j]);
+    // element t of the tile in C order: its low 8 bits come from the thread index, the high
+    // bits from the iteration; the sorted tile bits were computed on the host
+    const int nb = d.tile_bits;
+    __syncthreads();
+    int wlo = 0;
+    uint64_t olo = 0;
+    for (int q = 0; q < 8 && q < nb; ++q)
+        if ((threadIdx.x >> q) & 1) {
+            wlo |= 1 << d.tb_src[q];
+            olo |= 1ull << d.tb_pos[q];
         }
+    float2 *C = d.C + s * d.sC +
+                (deposit((uint64_t)m0, d.lm, d.posC_m) | deposit((uint64_t)n0, d.ln, d.posC_n));
+    if (nb < 8) {
+        if ((int)threadIdx.x < (1 << nb)) C[olo] = stage[wlo];
+        return;
+    }
+    for (int it = 0; it < (1 << (nb - 8)); ++it) {
+        int w = wlo;
+        uint64_t off = olo;
+        for (int q = 8; q < nb; ++q)
+            if ((it >> (q - 8)) & 1) {
+                w |= 1 << d.tb_src[q];
+                off |= 1ull << d.tb_pos[q];
+            }
+        C[off] = stage[w];
     }
 }
 
@@ -159,6 +199,22 @@ cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st)
     if (blocks > 152 * 32) blocks = 152 * 32;
     k_splitk_reduce<<<(unsigned)blocks, 256, 0, st>>>(d, slices);
     return cudaGetLastError();
+}
+
+void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
+                    int8_t *src, int8_t *pos) {
+    int s_[32], p_[32], n = 0;
+    for (int j = 0; j < tn; ++j) { s_[n] = j; p_[n] = posC_n[j]; ++n; }
+    for (int i = 0; i < tm; ++i) { s_[n] = row_tag | i; p_[n] = posC_m[i]; ++n; }
+    for (int a = 1; a < n; ++a)
+        for (int b = a; b > 0 && p_[b - 1] > p_[b]; --b) {
+            int t = p_[b]; p_[b] = p_[b - 1]; p_[b - 1] = t;
+            t = s_[b]; s_[b] = s_[b - 1]; s_[b - 1] = t;
+        }
+    for (int q = 0; q < n; ++q) {
+        src[q] = (int8_t)s_[q];
+        pos[q] = (int8_t)p_[q];
+    }
 }
 
 // Number of K splits for a CUDA-core GEMM step: enough CTAs to fill the GPU a few times when

@@ -6,14 +6,18 @@
 // powers of two), and the sum runs in FP32 in tensor memory.  The complex product is formed from
 // four real products (4M):
 //     Cre = Are*Bre - Aim*Bim,   Cim = Are*Bim + Aim*Bre,
-// with the minus sign taken by the instruction descriptor's negate-A bit.
+// with the minus sign taken by the instruction descriptor's negate-A bit, or from three (3M,
+// Gauss's product):
+//     P1 = Are*Bre, P2 = Aim*Bim, P3 = (Are+Aim)*(Bre+Bim);  Cre = P1 - P2, Cim = P3 - P1 - P2,
+// where the sum planes Are+Aim and Bre+Bim are rounded once from FP32 by the conversion kernel.
 //
 // One CTA computes a 128 x 128 output tile: warp 0 lane 0 issues TMA loads (128-byte swizzle)
-// into a 3-stage shared-memory ring, warp 1 lane 0 issues tcgen05.mma into two TMEM
-// accumulators (re, im; 256 columns), and all four warps drain TMEM through tcgen05.ld, apply the
-// exponent and scatter the complex64 result into the consumer's memory order (Sec. 4.1 index
-// reordering, done at the producer's store).  Every mbarrier wait gives up after a device-time
-// limit, records a timeout in a status word and lets the CTA release its TMEM and exit.
+// into a shared-memory ring (3 stages for 4M, 2 for 3M), warp 1 lane 0 issues tcgen05.mma into
+// the TMEM accumulators (2 or 3 of 128 columns), and all four warps drain TMEM through
+// tcgen05.ld, apply the exponent and scatter the complex64 result into the consumer's memory
+// order (Sec. 4.1 index reordering, done at the producer's store).  Every mbarrier wait gives up
+// after a device-time limit, records a timeout in a status word and lets the CTA release its
+// TMEM and exit.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -23,12 +27,22 @@ namespace tn {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
-constexpr int TILE_A = BM * BK * 2;                  // bytes of one 16-bit plane tile
-constexpr int TILE_B = BN * BK * 2;
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // re and im planes of A and B
-constexpr int TMEM_COLS = 256;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + BN * 8 /*col offsets*/ + 256;
+constexpr int BM = 128, BN = 128;
+
+// NPL planes per operand (2: 4M, 3: 3M) and a K tile of BKT 16-bit elements per row (64: rows
+// of 128 bytes with the 128-byte swizzle, 32: rows of 64 bytes with the 64-byte swizzle).
+template <int NPL, int BKT>
+struct Form {
+    static constexpr int TILE_A = BM * BKT * 2;
+    static constexpr int TILE_B = BN * BKT * 2;
+    static constexpr int STAGE_BYTES = NPL * (TILE_A + TILE_B);
+    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+    static constexpr int TMEM_COLS = NPL == 2 ? 256 : 512;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + BN * 8 + 256;
+    static constexpr int SBO = 8 * BKT * 2;          // bytes between 8-row groups
+    static constexpr uint64_t LAYOUT = BKT == 64 ? 2 : 4;  // 128-byte / 64-byte swizzle
+};
+
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s
 
 __device__ unsigned int g_tc_status;  // bit 0: an mbarrier wait timed out
@@ -88,15 +102,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major tile written by TMA with the 128-byte swizzle:
-// rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major tile written by TMA with a 128- or 64-byte
+// swizzle: rows of 128 (64) bytes, 8-row groups 1024 (512) bytes apart.
+template <int SBO, uint64_t LAYOUT>
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address (16-byte units)
-    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for these layouts)
+    d |= (uint64_t)(SBO >> 4) << 32;           // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;                    // descriptor version of tcgen05
-    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    d |= LAYOUT << 61;                         // swizzle mode
     return d;
 }
 
@@ -145,8 +160,16 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
     return r;
 }
 
+template <int NPL, int BKT>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGemmDesc d,
                                                     int64_t tiles_n) {
+    using F = Form<NPL, BKT>;
+    constexpr int STAGES = F::STAGES;
+    constexpr int STAGE_BYTES = F::STAGE_BYTES;
+    constexpr int TMEM_COLS = F::TMEM_COLS;
+    constexpr int TILE_A = F::TILE_A, TILE_B = F::TILE_B;
+    constexpr int BK = BKT;
+    auto sdesc = [](uint32_t a) { return sdesc_sw<F::SBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -190,8 +213,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int j = threadIdx.x; j < BN; j += blockDim.x)
-        coloff[j] = deposit((uint64_t)(n0 + j), d.ln, d.posC_n);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -208,18 +229,20 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
             uint8_t *base = smem + st * STAGE_BYTES;
             mbar_expect_tx(&full[st], STAGE_BYTES);
             const int k0 = kb * BK;
-            tma_load_3d(base, &d.tmA, &full[st], k0, m0, sa);
-            tma_load_3d(base + TILE_A, &d.tmA, &full[st], k0, m0, (int)d.slices_a + sa);
-            tma_load_3d(base + 2 * TILE_A, &d.tmB, &full[st], k0, n0, sbi);
-            tma_load_3d(base + 2 * TILE_A + TILE_B, &d.tmB, &full[st], k0, n0,
-                        (int)d.slices_b + sbi);
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+                tma_load_3d(base + pl * TILE_A, &d.tmA, &full[st], k0, m0,
+                            pl * (int)d.slices_a + sa);
+                tma_load_3d(base + NPL * TILE_A + pl * TILE_B, &d.tmB, &full[st], k0, n0,
+                            pl * (int)d.slices_b + sbi);
+            }
             issued = kb + 1;
         }
     } else if (threadIdx.x == 32) {
-        // MMA issuer: four real products per k step into the re and im accumulators
+        // MMA issuer: 4M = four real products into the re and im accumulators,
+        // 3M = three products into three accumulators
         const uint32_t id_pos = idesc_f16(d.bf16 != 0, BM, BN, false);
         const uint32_t id_neg = idesc_f16(d.bf16 != 0, BM, BN, true);
-        const uint32_t t_re = tmem, t_im = tmem + BN;
         bool ok = true;
         for (int kb = 0; kb < num_kb && ok; ++kb) {
             const int st = kb % STAGES;
@@ -230,17 +253,26 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-            const uint64_t a_re = sdesc_sw128(base), a_im = sdesc_sw128(base + TILE_A);
-            const uint64_t b_re = sdesc_sw128(base + 2 * TILE_A);
-            const uint64_t b_im = sdesc_sw128(base + 2 * TILE_A + TILE_B);
+            const uint64_t a_re = sdesc(base), a_im = sdesc(base + TILE_A);
+            const uint64_t b_re = sdesc(base + NPL * TILE_A);
+            const uint64_t b_im = sdesc(base + NPL * TILE_A + TILE_B);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
+                const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes,
+                                                                 // inside one swizzled row
                 const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
-                umma_f16(t_re, a_re + adv, b_re + adv, id_pos, first);
-                umma_f16(t_re, a_im + adv, b_im + adv, id_neg, 1u);
-                umma_f16(t_im, a_re + adv, b_im + adv, id_pos, first);
-                umma_f16(t_im, a_im + adv, b_re + adv, id_pos, 1u);
+                if constexpr (NPL == 2) {
+                    umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
+                    umma_f16(tmem, a_im + adv, b_im + adv, id_neg, 1u);
+                    umma_f16(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
+                    umma_f16(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                } else {
+                    const uint64_t a_sm = sdesc(base + 2 * TILE_A);
+                    const uint64_t b_sm = sdesc(base + NPL * TILE_A + 2 * TILE_B);
+                    umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
+                    umma_f16(tmem + BN, a_im + adv, b_im + adv, id_pos, first);
+                    umma_f16(tmem + 2 * BN, a_sm + adv, b_sm + adv, id_pos, first);
+                }
             }
             umma_commit(&empty[st]);
         }
@@ -248,40 +280,93 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
     }
     __syncwarp();
 
-    // epilogue: every warp drains its 32 TMEM lanes (rows); the wait result is made
-    // warp-uniform because tcgen05.ld is a warp-collective instruction
+    // epilogue: every warp drains its 32 TMEM lanes (rows) into a shared-memory tile (the idle
+    // pipeline buffers), which is then written out in the order of C's memory index: the 14 tile
+    // bits are sorted by their position in C, so consecutive threads store consecutive addresses
+    // whenever C's low bits fall inside the tile.  The wait result is made warp-uniform because
+    // tcgen05.ld is a warp-collective instruction.
     bool have = false;
     if (lane == 0) have = mbar_wait(done, 0, deadline);
     have = __shfl_sync(0xffffffffu, have ? 1 : 0, 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (have) {
-        const int e = d.expA[sa] + d.expB[sbi];
-        const int row = warp * 32 + lane;
-        const uint64_t roff = deposit((uint64_t)(m0 + row), d.lm, d.posC_m);
-        float2 *C = d.C + s * d.sC;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t re[16], im[16];
-            tmem_ld16(tmem + lane_base + (uint32_t)c0, re);
-            tmem_ld16(tmem + lane_base + (uint32_t)(BN + c0), im);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float vr = ldexpf(__uint_as_float(re[j]), e);
-                const float vi = ldexpf(__uint_as_float(im[j]), e);
-                C[roff | coloff[c0 + j]] = make_float2(vr, vi);
-            }
-        }
-    }
     if (threadIdx.x == 0) {
-        // every load this CTA issued must have landed before its shared memory is released;
-        // after a normal run the MMA warp consumed them all and these waits return at once
+        // every load this CTA issued must have landed before its shared memory is reused or
+        // released; after a normal run the MMA warp consumed them all and these waits return
         const unsigned long long drain = globaltimer() + kWaitLimitNs;
         for (int st = 0; st < STAGES && st < issued; ++st) {
             const int last = ((issued - 1 - st) / STAGES) * STAGES + st;
             mbar_wait(&full[st], (uint32_t)(last / STAGES) & 1u, drain);
         }
+    }
+    have = __syncthreads_and(have ? 1 : 0) != 0;
+    if (have) {
+        constexpr int LD = BN + 1;  // padded row stride of the staging tile (float2)
+        static_assert(BM * LD * 8 + 64 + 128 * 12 <= STAGES * STAGE_BYTES,
+                      "staging tile exceeds the ring");
+        float2 *stage = reinterpret_cast<float2 *>(smem);
+        const int e = d.expA[sa] + d.expB[sbi];
+        const int row = warp * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r0[16], r1[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)c0, r0);
+            tmem_ld16(tmem + lane_base + (uint32_t)(BN + c0), r1);
+            if constexpr (NPL == 2) {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    stage[row * LD + c0 + j] = make_float2(ldexpf(__uint_as_float(r0[j]), e),
+                                                           ldexpf(__uint_as_float(r1[j]), e));
+            } else {
+                uint32_t r2[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)(2 * BN + c0), r2);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float p1 = __uint_as_float(r0[j]), p2 = __uint_as_float(r1[j]);
+                    const float p3 = __uint_as_float(r2[j]);
+                    stage[row * LD + c0 + j] =
+                        make_float2(ldexpf(p1 - p2, e), ldexpf(p3 - p1 - p2, e));
+                }
+            }
+        }
+        // tile element t in C order: low 7 bits from the thread index, high 7 from the
+        // iteration (the sorted tile bits were computed on the host)
+        __syncthreads();
+        int mlo = 0, nlo = 0;
+        uint64_t olo = 0;
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+            if ((threadIdx.x >> q) & 1) {
+                const int sq = d.tb_src[q];
+                if (sq & 128) mlo |= 1 << (sq & 127);
+                else nlo |= 1 << sq;
+                olo |= 1ull << d.tb_pos[q];
+            }
+        // per-iteration parts, 128 entries built once by the 128 threads
+        uint64_t *hi_off = reinterpret_cast<uint64_t *>(smem + BM * LD * 8 + 64);
+        int *hi_w = reinterpret_cast<int *>(hi_off + 128);
+        {
+            int mi = 0, ni = 0;
+            uint64_t off = 0;
+#pragma unroll
+            for (int q = 7; q < 14; ++q)
+                if ((threadIdx.x >> (q - 7)) & 1) {
+                    const int sq = d.tb_src[q];
+                    if (sq & 128) mi |= 1 << (sq & 127);
+                    else ni |= 1 << sq;
+                    off |= 1ull << d.tb_pos[q];
+                }
+            hi_off[threadIdx.x] = off;
+            hi_w[threadIdx.x] = mi * LD + ni;
+        }
+        __syncthreads();
+        const int wlo = mlo * LD + nlo;
+        float2 *C = d.C + s * d.sC +
+                    (deposit((uint64_t)m0, d.lm, d.posC_m) | deposit((uint64_t)n0, d.ln, d.posC_n));
+#pragma unroll 4
+        for (int it = 0; it < (BM * BN) / 128; ++it) C[olo | hi_off[it]] = stage[wlo + hi_w[it]];
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -319,41 +404,65 @@ bool tc_available() {
         return false;
     if (major != 10) return false;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_gemm_tc) != cudaSuccess) return false;
+    if (cudaFuncGetAttributes(&fa, k_gemm_tc<2, 64>) != cudaSuccess) return false;
     return get_encode() != nullptr;
 }
 
 int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
-                         int64_t depth, int bf16) {
+                         int64_t depth, int bf16, int bk) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return -1;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || K % BK != 0) return -2;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bk != 32 && bk != 64) || K % bk != 0)
+        return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
     cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2)};
-    cuuint32_t box[3] = {BK, 128, 1};
+    cuuint32_t box[3] = {(cuuint32_t)bk, 128, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(reinterpret_cast<CUtensorMap *>(tmap_host),
                      bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                      const_cast<void *>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -3;
 }
 
-cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    if (d.lm < 7 || d.ln < 7 || d.lk < 6 || slices > 65535) return cudaErrorInvalidValue;
+namespace {
+
+template <int NPL, int BKT>
+cudaError_t configure_form() {
+    return cudaFuncSetAttribute(k_gemm_tc<NPL, BKT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Form<NPL, BKT>::SMEM_BYTES);
+}
+
+template <int NPL, int BKT>
+cudaError_t launch_form(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     const int64_t tiles_n = (1ll << d.ln) / BN;
     const int64_t tiles = ((1ll << d.lm) / BM) * tiles_n;
     if (tiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    k_gemm_tc<<<dim3((unsigned)tiles, (unsigned)slices), 128, SMEM_BYTES, st>>>(d, tiles_n);
+    k_gemm_tc<NPL, BKT><<<dim3((unsigned)tiles, (unsigned)slices), 128,
+                          Form<NPL, BKT>::SMEM_BYTES, st>>>(d, tiles_n);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_prepare() {
+    cudaError_t e = configure_form<2, 64>();
+    if (e == cudaSuccess) e = configure_form<2, 32>();
+    if (e == cudaSuccess) e = configure_form<3, 64>();
+    if (e == cudaSuccess) e = configure_form<3, 32>();
+    return e;
+}
+
+int tc_default_bk(int form) { return form == 2 ? 32 : 64; }
+
+cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
+    if (d.lm < 7 || d.ln < 7 || d.lk < 6 || slices > 65535) return cudaErrorInvalidValue;
+    if (d.bk != 32 && d.bk != 64) return cudaErrorInvalidValue;
+    if (d.form == 2) return d.bk == 32 ? launch_form<3, 32>(d, slices, st)
+                                       : launch_form<3, 64>(d, slices, st);
+    return d.bk == 32 ? launch_form<2, 32>(d, slices, st) : launch_form<2, 64>(d, slices, st);
 }
 
 unsigned int tc_status_read_and_clear() {

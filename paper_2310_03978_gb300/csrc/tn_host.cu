@@ -88,6 +88,7 @@ struct Tensor {
 
 struct Planar {              // planar 16-bit copy of a tensor feeding a tensor-core step
     int tensor = -1;
+    int planes = 2;          // re, im (4M) or re, im, re + im (3M)
     int64_t off = -1;        // byte offset in the arena
     int64_t bytes_per_slice = 0;
     int t = 0;               // time of the consuming step
@@ -148,6 +149,11 @@ struct tn_plan {
     std::vector<tn::TcGemmDesc> tc_desc;  // per step (only K_TC entries used)
     int64_t launches = 0;                 // kernels launched by this plan
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
+    // CUDA graph of the slice-dependent steps of one full batch (use_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;           // kernels inside one replay
 };
 
 namespace {
@@ -174,7 +180,7 @@ int route(const Step &s, tn_precision mode, bool tc_ok) {
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 6) return K_TC;
     // register-tiled GEMM (split along K when the output is small); a contraction of fewer than
     // 16 elements is cheaper as an element-wise pass with coalesced stores
-    if (s.batch.empty() && lk >= 4 && lm >= 3 && ln >= 3 && lm + ln + lk >= 14) return K_GEMM;
+    if (s.batch.empty() && lk >= 2 && lm >= 3 && ln >= 3 && lm + ln + lk >= 14) return K_GEMM;
     return K_GENERIC;
 }
 
@@ -418,7 +424,7 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
     p->mode = mode;
     p->device = net->device;
     if (opts) p->opts = *opts;
-    p->tc_ok = tn::tc_available();
+    p->tc_ok = tn::tc_available() && tn::tc_prepare() == cudaSuccess;
 
     std::map<int, int> cnt;  // holders of each label (tensors + output)
     for (auto &ls : net->labels)
@@ -580,7 +586,8 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
                 for (int side = 0; side < 2; ++side) {
                     Planar q;
                     q.tensor = side ? st.b : st.a;
-                    q.bytes_per_slice = (int64_t)4 << p->tensors[q.tensor].rank();
+                    q.planes = st.form == TN_GEMM_3M ? 3 : 2;
+                    q.bytes_per_slice = (int64_t)(2 * q.planes) << p->tensors[q.tensor].rank();
                     q.meta = (int)p->planars.size();
                     (side ? st.pb : st.pa) = (int)p->planars.size();
                     p->planars.push_back(q);
@@ -732,10 +739,13 @@ tn_status build_descriptors(tn_plan_t *p) {
         const int64_t Kx = (int64_t)1 << st.K.size();
         const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
         const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
+        d.bk = p->opts.tc_bk == 32 || p->opts.tc_bk == 64 ? p->opts.tc_bk
+                                                          : tn::tc_default_bk(st.form);
+        if (Kx < d.bk) d.bk = 32;
         if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx,
-                                     (int64_t)1 << st.M.size(), 2 * sa, bf) != 0 ||
+                                     (int64_t)1 << st.M.size(), qa.planes * sa, bf, d.bk) != 0 ||
             tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx,
-                                     (int64_t)1 << st.N.size(), 2 * sbb, bf) != 0)
+                                     (int64_t)1 << st.N.size(), qb.planes * sbb, bf, d.bk) != 0)
             return fail(TN_ERR_CUDA, "cuTensorMapEncodeTiled failed for step %d",
                         (int)(&st - &p->steps[0]));
         d.C = reinterpret_cast<float2 *>(p->arena) + C.off;
@@ -755,6 +765,7 @@ tn_status build_descriptors(tn_plan_t *p) {
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
         for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
+        tn::sort_tile_bits(7, 7, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
     }
     return TN_OK;
 }
@@ -817,6 +828,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             cd.amax = p->meta + 2 * p->sb * q.meta;
             cd.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
             cd.bf16 = p->mode == TN_PREC_BF16_SCALED;
+            cd.planes = q.planes;
             TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
             TN_CUDA(tn::launch_amax(cd, sx, stream));
             TN_CUDA(tn::launch_convert16(cd, sx, stream));
@@ -843,6 +855,14 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
         for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
+        {
+            const int tm = std::min(d.lm, 6), tnb = std::min(d.ln, 6);
+            d.tile_bits = tm + tnb;
+            tn::sort_tile_bits(tm, tnb, d.posC_m, d.posC_n, 64, d.tb_src, d.tb_pos);
+            // the staging index of row i, column j is 64 * i + j: row bit i is index bit 6 + i
+            for (int q = 0; q < d.tile_bits; ++q)
+                if (d.tb_src[q] & 64) d.tb_src[q] = (int8_t)(6 + (d.tb_src[q] & 63));
+        }
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_gemm_simt(d, slices, stream);
         if (st.splits > 1) p->launches += 1;
@@ -994,11 +1014,38 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
         TN_CUDA(tn::launch_bind(p->bind_sl_dev, (int32_t)p->bind_sl.size(), src, arena, s0, ns,
                                 p->max_rank_sl, stream));
         if (!p->bind_sl.empty()) p->launches++;
-        for (auto &st : p->steps)
-            if (st.dep) {
-                tn_status s = run_step(p, st, ns, stream);
-                if (s != TN_OK) return s;
+        const bool graph = p->opts.use_graph && !p->opts.profile && ns == p->sb;
+        if (graph && !p->graph_exec) {
+            // capture the dependent steps once, on a plan-owned stream
+            if (!p->cap_stream)
+                TN_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+            const int64_t l0 = p->launches;
+            TN_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+            tn_status cs = TN_OK;
+            for (auto &st : p->steps)
+                if (st.dep && cs == TN_OK) cs = run_step(p, st, ns, p->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+            if (cs != TN_OK) {
+                if (g) cudaGraphDestroy(g);
+                return cs;
             }
+            if (ce != cudaSuccess) return fail(TN_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            p->graph = g;
+            TN_CUDA(cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
+            p->graph_launches = p->launches - l0;
+            p->launches = l0;
+        }
+        if (graph) {
+            TN_CUDA(cudaGraphLaunch(p->graph_exec, stream));
+            p->launches += p->graph_launches;
+        } else {
+            for (auto &st : p->steps)
+                if (st.dep) {
+                    tn_status s = run_step(p, st, ns, stream);
+                    if (s != TN_OK) return s;
+                }
+        }
         TN_CUDA(tn::launch_accumulate(arena + R.off, R.dep ? nout : 0, nout, R.dep ? ns : 1,
                                       reinterpret_cast<double2 *>(amps_dev), stream));
         p->launches++;
@@ -1074,6 +1121,9 @@ void tn_destroy(void *handle) {
             cudaEventDestroy(ev.first);
             cudaEventDestroy(ev.second);
         }
+        if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
         p->magic = 0;
         delete p;
     }

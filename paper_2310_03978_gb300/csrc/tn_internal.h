@@ -38,6 +38,9 @@ struct GemmDesc {
     int32_t lm, ln, lk;        // log2 of M, N, K
     int32_t splits;            // > 1: split-K; CTA z sums K range z and writes partial[z][s]
     float2 *partial;           // split-K partial tiles, [splits][slices][M][N] row-major
+    int32_t tile_bits;         // valid bits of a 64 x 64 tile (min(lm,6) + min(ln,6))
+    int8_t tb_src[16];         // tile bits sorted by position in C: bit of the staging index
+    int8_t tb_pos[16];         //   (n: 0..5, m: 6..11) and its position in C
     int8_t posC_m[TN_MAXR];    // bit i of m (0 = least significant) -> bit of C's index
     int8_t posC_n[TN_MAXR];
 };
@@ -54,6 +57,11 @@ struct BindItem {
     int8_t sl_bit[8];          // which bit of the slice id fixes sliced label t
     int8_t sl_pos[8];          // source bit of sliced label t
 };
+
+// Sort the bits of an output tile (tm row bits, tn column bits) by their position in C:
+// src[q] = row_tag | i for row bit i, or j for column bit j; pos[q] = position in C.
+void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
+                    int8_t *src, int8_t *pos);
 
 // Kernel launchers (stream-ordered; return the launch error).
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
@@ -79,13 +87,14 @@ struct ConvertDesc {
     unsigned int *amax;        // per slice, float bits of max(|re|, |im|)
     int32_t *exps;             // per slice exponent e: stored = value * 2^-e
     int32_t bf16;              // 0 = fp16, 1 = bf16
+    int32_t planes;            // 2: re, im; 3: re, im, re + im (for the 3M product)
 };
 cudaError_t launch_amax(const ConvertDesc &d, int64_t slices, cudaStream_t st);
 cudaError_t launch_convert16(const ConvertDesc &d, int64_t slices, cudaStream_t st);
 
 struct TcGemmDesc {
-    CUtensorMap tmA;           // planar 16-bit A: [2 * slices_a][M][K], re planes then im planes
-    CUtensorMap tmB;           // planar 16-bit B: [2 * slices_b][N][K]
+    CUtensorMap tmA;           // planar 16-bit A: [planes * slices_a][M][K]: re, im (, re+im)
+    CUtensorMap tmB;           // planar 16-bit B: [planes * slices_b][N][K]
     float2 *C;
     int64_t sC;
     int32_t lm, ln, lk;
@@ -95,15 +104,23 @@ struct TcGemmDesc {
     const int32_t *expB;
     int32_t form;              // 1 = 4M, 2 = 3M
     int32_t bf16;
+    int32_t bk;                // K tile: 64 (128-byte swizzle) or 32 (64-byte swizzle)
+    int8_t tb_src[16];         // the 14 bits of a 128 x 128 tile sorted by position in C:
+    int8_t tb_pos[16];         //   (is_row << 7) | bit index, and its position in C
     int8_t posC_m[TN_MAXR];
     int8_t posC_n[TN_MAXR];
 };
 bool tc_available();
+// Set the kernels' shared-memory limits (once per device, outside any stream capture).
+cudaError_t tc_prepare();
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st);
 // Device status word of the tensor-core kernel (bit 0: a bounded wait timed out); cleared.
 unsigned int tc_status_read_and_clear();
-// Encode a 3-D tensor map over planar 16-bit data [planes*slices][rows][K] (K contiguous).
+// Encode a 3-D tensor map over planar 16-bit data [planes*slices][rows][K] (K contiguous),
+// box {bk, 128, 1} with the 128-byte (bk 64) or 64-byte (bk 32) swizzle.
 int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
-                         int64_t depth, int bf16);
+                         int64_t depth, int bf16, int bk);
+// Default K tile of a complex form (1 = 4M, 2 = 3M).
+int tc_default_bk(int form);
 
 }  // namespace tn

@@ -179,30 +179,44 @@ __device__ __forceinline__ int scale_exponent(unsigned int amax_bits) {
     return ilogbf(a) - 14;  // stored max lands in [2^14, 2^15): inside FP16's range
 }
 
-// complex64 -> planar 16-bit: stored = value * 2^-e (exact power-of-two scaling).
-__global__ void __launch_bounds__(256) k_convert16(ConvertDesc d) {
-    const int64_t s = blockIdx.y;
-    const int e = scale_exponent(d.amax[s]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.exps[s] = e;
+// complex64 -> planar 16-bit: stored = value * 2^-e (exact power-of-two scaling).  With three
+// planes the third holds re + im, summed in FP32 and rounded once.
+template <typename T2>
+__device__ __forceinline__ T2 pack2(float a, float b);
+template <>
+__device__ __forceinline__ __half2 pack2<__half2>(float a, float b) {
+    return __floats2half2_rn(a, b);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat162>(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+}
+
+template <typename T2>
+__device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, int e) {
     const float2 *src = d.src + s * d.src_sstride;
-    const int64_t base = s * d.dst_sstride;
+    T2 *re = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) + s * d.dst_sstride);
+    T2 *im = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) + s * d.dst_sstride +
+                                    d.plane_stride);
+    T2 *sm = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) + s * d.dst_sstride +
+                                    2 * d.plane_stride);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (d.n >> 1);
          i += (int64_t)gridDim.x * blockDim.x) {
         const float4 v = reinterpret_cast<const float4 *>(src)[i];
         const float r0 = ldexpf(v.x, -e), i0 = ldexpf(v.y, -e);
         const float r1 = ldexpf(v.z, -e), i1 = ldexpf(v.w, -e);
-        if (d.bf16) {
-            __nv_bfloat16 *re = reinterpret_cast<__nv_bfloat16 *>(d.dst) + base;
-            __nv_bfloat16 *imp = re + d.plane_stride;
-            reinterpret_cast<__nv_bfloat162 *>(re)[i] = __floats2bfloat162_rn(r0, r1);
-            reinterpret_cast<__nv_bfloat162 *>(imp)[i] = __floats2bfloat162_rn(i0, i1);
-        } else {
-            __half *re = reinterpret_cast<__half *>(d.dst) + base;
-            __half *imp = re + d.plane_stride;
-            reinterpret_cast<__half2 *>(re)[i] = __floats2half2_rn(r0, r1);
-            reinterpret_cast<__half2 *>(imp)[i] = __floats2half2_rn(i0, i1);
-        }
+        re[i] = pack2<T2>(r0, r1);
+        im[i] = pack2<T2>(i0, i1);
+        if (d.planes == 3) sm[i] = pack2<T2>(r0 + i0, r1 + i1);
     }
+}
+
+__global__ void __launch_bounds__(256) k_convert16(ConvertDesc d) {
+    const int64_t s = blockIdx.y;
+    const int e = scale_exponent(d.amax[s]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.exps[s] = e;
+    if (d.bf16) convert_body<__nv_bfloat162>(d, s, e);
+    else convert_body<__half2>(d, s, e);
 }
 
 int grid_for(int64_t work, int threads) {

@@ -33,7 +33,7 @@ class PlanOptions(C.Structure):
     _fields_ = [("max_slices_in_flight", C.c_int64), ("workspace_limit", C.c_int64),
                 ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
                 ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
-                ("profile", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("profile", C.c_int32), ("tc_bk", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class PlanInfo(C.Structure):
@@ -156,7 +156,7 @@ class Plan:
 
     def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
                  workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
-                 profile=False, use_graph=False):
+                 profile=False, use_graph=False, tc_bk=0):
         self.network = network
         opts = PlanOptions()
         opts.max_slices_in_flight = int(max_slices_in_flight)
@@ -169,6 +169,7 @@ class Plan:
         opts.sync_each_call = 1 if sync_each_call else 0
         opts.profile = 1 if profile else 0
         opts.use_graph = 1 if use_graph else 0
+        opts.tc_bk = int(tc_bk)
         pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
         sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
         h = C.c_void_p()

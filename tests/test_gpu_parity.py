@@ -149,7 +149,8 @@ def single_step(rng, lm, ln, lk, scale=1.0, scramble=True):
 
 @pytest.mark.parametrize("shape,kernel", [
     ((3, 2, 2), "generic"),      # tiny
-    ((9, 9, 2), "generic"),      # outer-product-like: 2^18 outputs, k = 4
+    ((9, 9, 1), "generic"),      # outer-product-like: 2^18 outputs, k = 2
+    ((9, 9, 2), "gemm_simt"),    # k = 4: register-tiled, zero-padded K tile
     ((2, 2, 11), "generic"),     # k > 2^10: offsets computed without the shared table
     ((6, 5, 4), "gemm_simt"),
     ((7, 6, 9), "gemm_simt"),
@@ -175,13 +176,15 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
     check(got2, ref2, 1e-5)
 
 
+@pytest.mark.parametrize("form,bk", [("4m", 64), ("4m", 32), ("3m", 32), ("3m", 64)])
 @pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled"])
 @pytest.mark.parametrize("shape", [(7, 7, 6), (9, 8, 7), (8, 10, 8)])
-def test_single_step_tensor_core(tn, mode, shape):
+def test_single_step_tensor_core(tn, mode, shape, form, bk):
     rng = np.random.default_rng(7 + sum(shape))
     tensors, labels, out = single_step(rng, *shape)
     ref = O.contract(tensors, labels, out, [(0, 1)])
-    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode=mode)
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode=mode, gemm_form=form,
+                               tc_bk=bk)
     assert kernels == ["gemm_tc"]
     check(got, ref, TOL[mode])
 
@@ -215,6 +218,25 @@ def test_tensor_core_step_with_slices_in_flight(tn):
         check(got, ref, TOL[mode])
 
 
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+def test_graph_replay_matches_direct_launches(tn, mode):
+    wl = W.small_workload()
+    net = wl.network
+    sl = W.greedy_slices(net.labels, net.open_labels, wl.path, 2)
+    tnet = tn.Network.from_workload(net)
+    direct = tn.Plan(tnet, wl.path, sl, mode=mode)
+    graph = tn.Plan(tnet, wl.path, sl, mode=mode, use_graph=True, max_slices_in_flight=2)
+    ref = direct.contract_host()
+    for _ in range(3):  # capture on first use, then replays
+        got = graph.contract_host()
+        check(got, ref, 1e-6)
+    part = graph.contract_host(1, 4)   # a partial batch runs without the graph
+    check(part, O.contract_network(net, wl.path, sl, 1, 4), TOL[mode])
+    direct.close()
+    graph.close()
+    tnet.close()
+
+
 def test_host_entry_points_and_set_data(tn):
     wl = W.small_workload()
     net = wl.network
@@ -233,8 +255,9 @@ def test_host_entry_points_and_set_data(tn):
 
 
 # ------------------------------------------------------------------ the full-size circuit
-@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
-def test_bench_circuit_full_size(tn, mode):
+@pytest.mark.parametrize("mode,form", [("c64", "auto"), ("fp16_scaled", "4m"),
+                                       ("fp16_scaled", "3m")])
+def test_bench_circuit_full_size(tn, mode, form):
     golden = os.path.join(HERE, "golden", "sycamore_5x6_c14_open10_s4.amps.txt")
     if not os.path.exists(golden):
         pytest.skip("golden amplitudes not generated")
@@ -242,7 +265,7 @@ def test_bench_circuit_full_size(tn, mode):
     net = wl.network
     ref = read_golden("sycamore_5x6_c14_open10_s4")
     got, info, kernels = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path,
-                                  wl.sliced, mode=mode)
+                                  wl.sliced, mode=mode, gemm_form=form)
     assert info["num_slices"] == 16 and info["max_log2_size"] <= 28
     check(got, ref, TOL[mode])
     n = wl.circuit.n_qubits
