@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--mode", default="fp16_scaled")
     ap.add_argument("--gemm-form", default="auto", choices=["auto", "4m", "3m"])
     ap.add_argument("--tc-bk", type=int, default=0, choices=[0, 32, 64])
+    ap.add_argument("--tc-bn", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--c64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -388,7 +389,7 @@ def run_step_bench(args):
     B = (rng.standard_normal((2,) * rb) + 1j * rng.standard_normal((2,) * rb)) * scale
     net = tn.Network([A, B], [la, lb], out)
     plan = tn.Plan(net, [(0, 1)], (), mode=args.mode, profile=True, gemm_form=args.gemm_form,
-                   tc_bk=args.tc_bk)
+                   tc_bk=args.tc_bk, tc_bn=args.tc_bn)
     amps = torch.zeros(1 << (lm + ln), dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -410,7 +411,8 @@ def run_step_bench(args):
                       "kernel_tflops": tcc / (kern_ms / 1e3) / 1e12, "ms_per_step": ms,
                       "prep_ms": (si["prep_ms"] - before["prep_ms"]) / max(1, args.steps),
                       "config": {"lm": lm, "ln": ln, "lk": lk, "mode": args.mode,
-                                 "gemm_form": args.gemm_form, "tc_bk": args.tc_bk},
+                                 "gemm_form": args.gemm_form, "tc_bk": args.tc_bk,
+                                 "tc_bn": args.tc_bn},
                       "rel_l2_vs_oracle": check}))
     plan.close()
     net.close()

@@ -76,9 +76,9 @@ typedef struct {
     int32_t profile;               /* 1 = time every step with CUDA events on the contraction
                                       stream (read by tn_plan_get_step_info after the stream is
                                       synchronised)                                           */
-    int32_t tc_bk;                 /* tensor-core K tile: 0 = default (64 for 4M, 32 for 3M),
-                                      32 or 64                                               */
-    int32_t reserved[7];
+    int32_t tc_bk;                 /* tensor-core K tile preference: 0 = automatic, 32 or 64  */
+    int32_t tc_bn;                 /* tensor-core N tile preference: 0 = automatic, 128, 256  */
+    int32_t reserved[6];
 } tn_plan_options;
 
 typedef struct {

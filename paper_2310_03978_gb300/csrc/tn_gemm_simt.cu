@@ -19,7 +19,7 @@ namespace tn {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
 
 __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos) {
     uint64_t r = 0;
@@ -29,8 +29,11 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
 }
 
 // 256 threads as 16 x 16; each thread owns rows ty + 16*i and columns tx + 16*j (i, j < 4).
+// BK is the K tile (16, or 8 for contractions of at most 8 elements, which would otherwise
+// multiply half a tile of zero padding).
+template <int BK>
 __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) {
-    constexpr int AS = 2 * BK * (BM + 1), BS = 2 * BK * (BN + 1);
+    constexpr int AS = 2 * 16 * (BM + 1), BS = 2 * 16 * (BN + 1);
     static_assert(AS + BS >= BM * BN, "staging tile must fit in the operand buffers");
     __shared__ __align__(16) float2 sbuf[AS + BS];
     auto As = reinterpret_cast<float2(*)[BK][BM + 1]>(sbuf);
@@ -46,13 +49,14 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     const float2 *B = d.B + s * d.sB + kz;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
-    // global -> shared mapping: 64 rows x 16 k; thread loads row (tid >> 2), k (tid & 3) * 4..+3
-    const int lr = tid >> 2, lk = (tid & 3) * 4;
-    float2 ra[4], rb[4];
+    // global -> shared mapping: 64 rows x BK k; thread loads row (tid >> 2), k lk..lk+BK/4-1
+    constexpr int KQ = BK / 4;
+    const int lr = tid >> 2, lk = (tid & 3) * KQ;
+    float2 ra[KQ], rb[KQ];
     auto load = [&](int64_t k0) {
         const int64_t gm = m0 + lr, gn = n0 + lr;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < KQ; ++q) {
             const int64_t gk = k0 + lk + q;
             ra[q] = (gm < M && gk < K) ? A[gm * Kfull + gk] : make_float2(0.f, 0.f);
             rb[q] = (gn < N && gk < K) ? B[gn * Kfull + gk] : make_float2(0.f, 0.f);
@@ -60,7 +64,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     };
     auto store = [&](int buf) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < KQ; ++q) {
             As[buf][lk + q][lr] = ra[q];
             Bs[buf][lk + q][lr] = rb[q];
         }
@@ -146,20 +150,28 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
         }
     float2 *C = d.C + s * d.sC +
                 (deposit((uint64_t)m0, d.lm, d.posC_m) | deposit((uint64_t)n0, d.ln, d.posC_n));
+    float amx = 0.f;
     if (nb < 8) {
-        if ((int)threadIdx.x < (1 << nb)) C[olo] = stage[wlo];
-        return;
+        if ((int)threadIdx.x < (1 << nb)) {
+            const float2 v = stage[wlo];
+            C[olo] = v;
+            amx = fmaxf(fabsf(v.x), fabsf(v.y));
+        }
+    } else {
+        for (int it = 0; it < (1 << (nb - 8)); ++it) {
+            int w = wlo;
+            uint64_t off = olo;
+            for (int q = 8; q < nb; ++q)
+                if ((it >> (q - 8)) & 1) {
+                    w |= 1 << d.tb_src[q];
+                    off |= 1ull << d.tb_pos[q];
+                }
+            const float2 v = stage[w];
+            C[off] = v;
+            amx = fmaxf(amx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
     }
-    for (int it = 0; it < (1 << (nb - 8)); ++it) {
-        int w = wlo;
-        uint64_t off = olo;
-        for (int q = 8; q < nb; ++q)
-            if ((it >> (q - 8)) & 1) {
-                w |= 1 << d.tb_src[q];
-                off |= 1ull << d.tb_pos[q];
-            }
-        C[off] = stage[w];
-    }
+    if (d.amax_out) amax_publish(d.amax_out + s, amx);
 }
 
 // Sum of the split-K partials in increasing split order, scattered into C's order.
@@ -179,6 +191,7 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
         const uint64_t m = (uint64_t)e >> d.ln, n = (uint64_t)e & nmask;
         d.C[s * d.sC + (int64_t)(deposit(m, d.lm, d.posC_m) | deposit(n, d.ln, d.posC_n))] =
             make_float2(re, im);
+        if (d.amax_out) atomicMax(d.amax_out + s, __float_as_uint(fmaxf(fabsf(re), fabsf(im))));
     }
 }
 
@@ -190,8 +203,11 @@ cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st)
     if (tm * tn_ > 0x7fffffffll || slices > 65535 || d.splits < 1 || d.splits > 65535 ||
         ((1ll << d.lk) % d.splits) != 0 || (d.splits > 1 && !d.partial))
         return cudaErrorInvalidConfiguration;
-    k_gemm_simt<<<dim3((unsigned)(tm * tn_), (unsigned)slices, (unsigned)d.splits), 256, 0, st>>>(
-        d, tn_);
+    const dim3 grid((unsigned)(tm * tn_), (unsigned)slices, (unsigned)d.splits);
+    if (d.lk - (d.splits > 1 ? __builtin_ctz((unsigned)d.splits) : 0) <= 3)
+        k_gemm_simt<8><<<grid, 256, 0, st>>>(d, tn_);
+    else
+        k_gemm_simt<16><<<grid, 256, 0, st>>>(d, tn_);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || d.splits == 1) return e;
     const int64_t total = slices << (d.lm + d.ln);

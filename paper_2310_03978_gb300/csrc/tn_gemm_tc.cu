@@ -27,20 +27,29 @@ namespace tn {
 
 namespace {
 
-constexpr int BM = 128, BN = 128;
+constexpr int BM = 128;
+constexpr int CW = 64;       // epilogue column chunk
+constexpr int SLD = CW + 1;  // padded row stride of the epilogue staging tile (float2)
 
-// NPL planes per operand (2: 4M, 3: 3M) and a K tile of BKT 16-bit elements per row (64: rows
-// of 128 bytes with the 128-byte swizzle, 32: rows of 64 bytes with the 64-byte swizzle).
-template <int NPL, int BKT>
-struct Form {
+// NPL planes per operand (2: 4M, 3: 3M); a K tile of BKT 16-bit elements per row (64: rows of
+// 128 bytes with the 128-byte swizzle, 32: rows of 64 bytes with the 64-byte swizzle); an N
+// tile of BNT columns; STG pipeline stages; MINB CTAs per SM.
+template <int NPL, int BKT, int BNT, int STG, int MINB>
+struct Cfg {
     static constexpr int TILE_A = BM * BKT * 2;
-    static constexpr int TILE_B = BN * BKT * 2;
+    static constexpr int TILE_B = BNT * BKT * 2;
     static constexpr int STAGE_BYTES = NPL * (TILE_A + TILE_B);
-    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
-    static constexpr int TMEM_COLS = NPL == 2 ? 256 : 512;
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + BN * 8 + 256;
-    static constexpr int SBO = 8 * BKT * 2;          // bytes between 8-row groups
-    static constexpr uint64_t LAYOUT = BKT == 64 ? 2 : 4;  // 128-byte / 64-byte swizzle
+    static constexpr int RING = STG * STAGE_BYTES;
+    static constexpr int STAGING = BM * SLD * 8 + 64 * 12;  // tile chunk + per-iteration tables
+    static constexpr int BODY = RING > STAGING ? RING : STAGING;
+    static constexpr int BODY_MIN = MINB == 2 ? 80 * 1024 : 0;  // at most 2 CTAs per SM
+    static constexpr int SMEM_BYTES = (BODY > BODY_MIN ? BODY : BODY_MIN) + 1024 + 256;
+    static constexpr int ACC = NPL == 2 ? 2 * BNT : 3 * BNT;
+    static constexpr int TMEM_COLS = ACC <= 256 ? 256 : 512;
+    static constexpr int SBO = 8 * BKT * 2;                 // bytes between 8-row groups
+    static constexpr uint64_t LAYOUT = BKT == 64 ? 2 : 4;   // 128-byte / 64-byte swizzle
+    static_assert(ACC <= 512, "accumulators exceed tensor memory");
+    static_assert(MINB * TMEM_COLS <= 512, "co-resident CTAs exceed tensor memory");
 };
 
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s
@@ -160,21 +169,20 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
     return r;
 }
 
-template <int NPL, int BKT>
-__global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGemmDesc d,
-                                                    int64_t tiles_n) {
-    using F = Form<NPL, BKT>;
-    constexpr int STAGES = F::STAGES;
+template <int NPL, int BKT, int BNT, int STG, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ TcGemmDesc d,
+                                                       int64_t tiles_n) {
+    using F = Cfg<NPL, BKT, BNT, STG, MINB>;
+    constexpr int STAGES = STG;
     constexpr int STAGE_BYTES = F::STAGE_BYTES;
     constexpr int TMEM_COLS = F::TMEM_COLS;
     constexpr int TILE_A = F::TILE_A, TILE_B = F::TILE_B;
-    constexpr int BK = BKT;
+    constexpr int BK = BKT, BN = BNT;
     auto sdesc = [](uint32_t a) { return sdesc_sw<F::SBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t *coloff = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES + BN * 8);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY);
     uint64_t *empty = full + STAGES;
     uint64_t *done = empty + STAGES;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
@@ -241,8 +249,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
     } else if (threadIdx.x == 32) {
         // MMA issuer: 4M = four real products into the re and im accumulators,
         // 3M = three products into three accumulators
-        const uint32_t id_pos = idesc_f16(d.bf16 != 0, BM, BN, false);
-        const uint32_t id_neg = idesc_f16(d.bf16 != 0, BM, BN, true);
+        const uint32_t id_pos = idesc_f16(d.bf16 != 0, BM, BNT, false);
+        const uint32_t id_neg = idesc_f16(d.bf16 != 0, BM, BNT, true);
         bool ok = true;
         for (int kb = 0; kb < num_kb && ok; ++kb) {
             const int st = kb % STAGES;
@@ -300,40 +308,18 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
     }
     have = __syncthreads_and(have ? 1 : 0) != 0;
     if (have) {
-        constexpr int LD = BN + 1;  // padded row stride of the staging tile (float2)
-        static_assert(BM * LD * 8 + 64 + 128 * 12 <= STAGES * STAGE_BYTES,
-                      "staging tile exceeds the ring");
+        // The tile is written in chunks of CW = 64 columns: each chunk is staged in shared
+        // memory and written out in the order of C's memory index.  A chunk has 13 bits (7 row,
+        // 6 column), sorted on the host by their position in C; element t of the chunk in that
+        // order takes its low 7 bits from the thread index and its high 6 from the iteration.
+        // C's positions 0..5 always belong to a chunk, so each warp store covers >= 64
+        // consecutive elements.
         float2 *stage = reinterpret_cast<float2 *>(smem);
+        uint64_t *hi_off = reinterpret_cast<uint64_t *>(smem + BM * SLD * 8);
+        int *hi_w = reinterpret_cast<int *>(hi_off + 64);
         const int e = d.expA[sa] + d.expB[sbi];
         const int row = warp * 32 + lane;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r0[16], r1[16];
-            tmem_ld16(tmem + lane_base + (uint32_t)c0, r0);
-            tmem_ld16(tmem + lane_base + (uint32_t)(BN + c0), r1);
-            if constexpr (NPL == 2) {
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    stage[row * LD + c0 + j] = make_float2(ldexpf(__uint_as_float(r0[j]), e),
-                                                           ldexpf(__uint_as_float(r1[j]), e));
-            } else {
-                uint32_t r2[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(2 * BN + c0), r2);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float p1 = __uint_as_float(r0[j]), p2 = __uint_as_float(r1[j]);
-                    const float p3 = __uint_as_float(r2[j]);
-                    stage[row * LD + c0 + j] =
-                        make_float2(ldexpf(p1 - p2, e), ldexpf(p3 - p1 - p2, e));
-                }
-            }
-        }
-        // tile element t in C order: low 7 bits from the thread index, high 7 from the
-        // iteration (the sorted tile bits were computed on the host)
-        __syncthreads();
         int mlo = 0, nlo = 0;
         uint64_t olo = 0;
 #pragma unroll
@@ -344,14 +330,12 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
-        // per-iteration parts, 128 entries built once by the 128 threads
-        uint64_t *hi_off = reinterpret_cast<uint64_t *>(smem + BM * LD * 8 + 64);
-        int *hi_w = reinterpret_cast<int *>(hi_off + 128);
-        {
+        const int wlo = mlo * SLD + nlo;
+        if (threadIdx.x < 64) {
             int mi = 0, ni = 0;
             uint64_t off = 0;
 #pragma unroll
-            for (int q = 7; q < 14; ++q)
+            for (int q = 7; q < 13; ++q)
                 if ((threadIdx.x >> (q - 7)) & 1) {
                     const int sq = d.tb_src[q];
                     if (sq & 128) mi |= 1 << (sq & 127);
@@ -359,14 +343,49 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(const __grid_constant__ TcGe
                     off |= 1ull << d.tb_pos[q];
                 }
             hi_off[threadIdx.x] = off;
-            hi_w[threadIdx.x] = mi * LD + ni;
+            hi_w[threadIdx.x] = mi * SLD + ni;
         }
-        __syncthreads();
-        const int wlo = mlo * LD + nlo;
-        float2 *C = d.C + s * d.sC +
-                    (deposit((uint64_t)m0, d.lm, d.posC_m) | deposit((uint64_t)n0, d.ln, d.posC_n));
+        const uint64_t mbase = deposit((uint64_t)m0, d.lm, d.posC_m);
+        float amx = 0.f;
+#pragma unroll 1
+        for (int cb = 0; cb < BN; cb += CW) {
+#pragma unroll 1
+            for (int c0 = cb; c0 < cb + CW; c0 += 16) {
+                uint32_t r0[16], r1[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)c0, r0);
+                tmem_ld16(tmem + lane_base + (uint32_t)(BN + c0), r1);
+                if constexpr (NPL == 2) {
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        stage[row * SLD + (c0 - cb) + j] =
+                            make_float2(ldexpf(__uint_as_float(r0[j]), e),
+                                        ldexpf(__uint_as_float(r1[j]), e));
+                } else {
+                    uint32_t r2[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(2 * BN + c0), r2);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float p1 = __uint_as_float(r0[j]), p2 = __uint_as_float(r1[j]);
+                        const float p3 = __uint_as_float(r2[j]);
+                        stage[row * SLD + (c0 - cb) + j] =
+                            make_float2(ldexpf(p1 - p2, e), ldexpf(p3 - p1 - p2, e));
+                    }
+                }
+            }
+            __syncthreads();
+            float2 *C = d.C + s * d.sC +
+                        (mbase | deposit((uint64_t)(n0 + cb), d.ln, d.posC_n));
 #pragma unroll 4
-        for (int it = 0; it < (BM * BN) / 128; ++it) C[olo | hi_off[it]] = stage[wlo + hi_w[it]];
+            for (int it = 0; it < (BM * CW) / 128; ++it) {
+                const float2 v = stage[wlo + hi_w[it]];
+                C[olo | hi_off[it]] = v;
+                amx = fmaxf(amx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+            __syncthreads();
+        }
+        if (d.amax_out) amax_publish(d.amax_out + s, amx);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -404,19 +423,20 @@ bool tc_available() {
         return false;
     if (major != 10) return false;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_gemm_tc<2, 64>) != cudaSuccess) return false;
+    if (cudaFuncGetAttributes(&fa, k_gemm_tc<2, 64, 128, 3, 1>) != cudaSuccess) return false;
     return get_encode() != nullptr;
 }
 
 int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
-                         int64_t depth, int bf16, int bk) {
+                         int64_t depth, int bf16, int bk, int box_rows) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return -1;
     if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bk != 32 && bk != 64) || K % bk != 0)
         return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
     cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)bk, 128, 1};
+    if (box_rows != 128 && box_rows != 256) return -2;
+    cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(reinterpret_cast<CUtensorMap *>(tmap_host),
                      bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
@@ -429,40 +449,87 @@ int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t r
 
 namespace {
 
-template <int NPL, int BKT>
-cudaError_t configure_form() {
-    return cudaFuncSetAttribute(k_gemm_tc<NPL, BKT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Form<NPL, BKT>::SMEM_BYTES);
+// The kernel variants, indexed by TcGemmDesc::variant.
+#define TN_TC_VARIANTS(X)          \
+    X(0, 2, 64, 128, 3, 1) /* 4M, long K (default)                  */ \
+    X(1, 2, 32, 256, 4, 1) /* 4M, N tile 256                         */ \
+    X(2, 2, 32, 128, 2, 2) /* 4M, short K: small ring, 2 CTAs per SM */ \
+    X(3, 3, 32, 128, 4, 1) /* 3M                                     */ \
+    X(4, 3, 64, 128, 2, 1) /* 3M, 128-byte swizzle                   */ \
+    X(5, 2, 32, 128, 6, 1) /* 4M, 64-byte swizzle, 6 stages          */
+
+template <int NPL, int BKT, int BNT, int STG, int MINB>
+cudaError_t configure_variant() {
+    return cudaFuncSetAttribute(k_gemm_tc<NPL, BKT, BNT, STG, MINB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<NPL, BKT, BNT, STG, MINB>::SMEM_BYTES);
 }
 
-template <int NPL, int BKT>
-cudaError_t launch_form(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    const int64_t tiles_n = (1ll << d.ln) / BN;
+template <int NPL, int BKT, int BNT, int STG, int MINB>
+cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
+    if (d.ln < (BNT == 256 ? 8 : 7) || d.lk < (BKT == 64 ? 6 : 5))
+        return cudaErrorInvalidValue;
+    const int64_t tiles_n = (1ll << d.ln) / BNT;
     const int64_t tiles = ((1ll << d.lm) / BM) * tiles_n;
     if (tiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    k_gemm_tc<NPL, BKT><<<dim3((unsigned)tiles, (unsigned)slices), 128,
-                          Form<NPL, BKT>::SMEM_BYTES, st>>>(d, tiles_n);
+    k_gemm_tc<NPL, BKT, BNT, STG, MINB>
+        <<<dim3((unsigned)tiles, (unsigned)slices), 128, Cfg<NPL, BKT, BNT, STG, MINB>::SMEM_BYTES,
+           st>>>(d, tiles_n);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t tc_prepare() {
-    cudaError_t e = configure_form<2, 64>();
-    if (e == cudaSuccess) e = configure_form<2, 32>();
-    if (e == cudaSuccess) e = configure_form<3, 64>();
-    if (e == cudaSuccess) e = configure_form<3, 32>();
+    cudaError_t e = cudaSuccess;
+#define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb) \
+    if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb>();
+    TN_TC_VARIANTS(TN_TC_CONFIGURE)
+#undef TN_TC_CONFIGURE
     return e;
 }
 
-int tc_default_bk(int form) { return form == 2 ? 32 : 64; }
+int tc_variant_bk(int variant) {
+    switch (variant) {
+#define TN_TC_BK(id, npl, bk, bn, stg, minb) \
+    case id: return bk;
+        TN_TC_VARIANTS(TN_TC_BK)
+#undef TN_TC_BK
+    }
+    return 0;
+}
+
+int tc_variant_bn(int variant) {
+    switch (variant) {
+#define TN_TC_BN(id, npl, bk, bn, stg, minb) \
+    case id: return bn;
+        TN_TC_VARIANTS(TN_TC_BN)
+#undef TN_TC_BN
+    }
+    return 0;
+}
+
+// Variant choice (measured on GB300): short contractions (K <= 512) are epilogue-bound and run
+// two CTAs per SM; long ones use the 128 x 256 tile (1.98 PFLOP/s on m=2^13, n=2^14, k=2^14
+// against 1.79 for 128 x 128), or 128 x 128 when N < 256.
+int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref) {
+    if (form == 2) return bk_pref == 64 ? 4 : 3;
+    if (bn_pref == 256 && ln >= 8) return 1;
+    if (bk_pref == 32) return lk <= 9 ? 2 : 5;
+    if (bk_pref == 64 || bn_pref == 128) return lk <= 9 && bk_pref != 64 ? 2 : 0;
+    if (lk <= 9) return 2;
+    return ln >= 8 ? 1 : 0;
+}
 
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    if (d.lm < 7 || d.ln < 7 || d.lk < 6 || slices > 65535) return cudaErrorInvalidValue;
-    if (d.bk != 32 && d.bk != 64) return cudaErrorInvalidValue;
-    if (d.form == 2) return d.bk == 32 ? launch_form<3, 32>(d, slices, st)
-                                       : launch_form<3, 64>(d, slices, st);
-    return d.bk == 32 ? launch_form<2, 32>(d, slices, st) : launch_form<2, 64>(d, slices, st);
+    if (d.lm < 7 || slices > 65535) return cudaErrorInvalidValue;
+    switch (d.variant) {
+#define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb) \
+    case id: return launch_variant<npl, bk, bn, stg, minb>(d, slices, st);
+        TN_TC_VARIANTS(TN_TC_LAUNCH)
+#undef TN_TC_LAUNCH
+    }
+    return cudaErrorInvalidValue;
 }
 
 unsigned int tc_status_read_and_clear() {

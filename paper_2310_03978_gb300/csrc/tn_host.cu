@@ -89,6 +89,7 @@ struct Tensor {
 struct Planar {              // planar 16-bit copy of a tensor feeding a tensor-core step
     int tensor = -1;
     int planes = 2;          // re, im (4M) or re, im, re + im (3M)
+    bool fused_amax = false; // its producer's epilogue records the per-slice max-abs
     int64_t off = -1;        // byte offset in the arena
     int64_t bytes_per_slice = 0;
     int t = 0;               // time of the consuming step
@@ -106,6 +107,7 @@ struct Step {
     int pa = -1, pb = -1;        // planar copies for K_TC
     int form = TN_GEMM_4M;
     int splits = 1;              // K_GEMM split-K factor
+    int amax_planar = -1;        // planar copy whose max-abs this step's epilogue records
     int64_t part_off = -1;       // K_GEMM split-K partials (byte offset in the arena)
     // profile mode: recorded (start, stop) event pairs not yet read, and the running totals
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pending_prep;
@@ -729,6 +731,16 @@ tn_status build_descriptors(tn_plan_t *p) {
     TN_CUDA(cudaMalloc(&p->partial, sizeof(double) * 2 * p->n_partial));
     TN_CUDA(cudaMalloc(&p->amps_tmp, sizeof(double2) << p->net->open.size()));
 
+    // a tensor-core operand produced by a step gets its max-abs from that step's epilogue
+    for (size_t i = 0; i < p->planars.size(); ++i) {
+        Planar &q = p->planars[i];
+        const Tensor &t = p->tensors[q.tensor];
+        if (t.producer < 0) continue;
+        Step &pr = p->steps[t.producer];
+        if (pr.amax_planar >= 0) continue;
+        pr.amax_planar = (int)i;
+        q.fused_amax = true;
+    }
     p->tc_desc.resize(p->steps.size());
     for (auto &st : p->steps) {
         if (st.kernel != K_TC) continue;
@@ -739,13 +751,14 @@ tn_status build_descriptors(tn_plan_t *p) {
         const int64_t Kx = (int64_t)1 << st.K.size();
         const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
         const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
-        d.bk = p->opts.tc_bk == 32 || p->opts.tc_bk == 64 ? p->opts.tc_bk
-                                                          : tn::tc_default_bk(st.form);
-        if (Kx < d.bk) d.bk = 32;
-        if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx,
-                                     (int64_t)1 << st.M.size(), qa.planes * sa, bf, d.bk) != 0 ||
-            tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx,
-                                     (int64_t)1 << st.N.size(), qb.planes * sbb, bf, d.bk) != 0)
+        d.variant = tn::tc_pick_variant(st.form == TN_GEMM_3M ? 2 : 1, (int)st.K.size(),
+                                        (int)st.N.size(), p->opts.tc_bk, p->opts.tc_bn);
+        d.bk = tn::tc_variant_bk(d.variant);
+        const int bn = tn::tc_variant_bn(d.variant);
+        if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx, (int64_t)1 << st.M.size(),
+                                     qa.planes * sa, bf, d.bk, 128) != 0 ||
+            tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx, (int64_t)1 << st.N.size(),
+                                     qb.planes * sbb, bf, d.bk, bn) != 0)
             return fail(TN_ERR_CUDA, "cuTensorMapEncodeTiled failed for step %d",
                         (int)(&st - &p->steps[0]));
         d.C = reinterpret_cast<float2 *>(p->arena) + C.off;
@@ -761,11 +774,14 @@ tn_status build_descriptors(tn_plan_t *p) {
         d.expB = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qb.meta + p->sb);
         d.form = st.form;
         d.bf16 = bf;
+        d.amax_out = st.amax_planar >= 0 ? p->meta + 2 * p->sb * p->planars[st.amax_planar].meta
+                                         : nullptr;
         fill_pos(d.posC_m, TN_MAXR, -1);
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
         for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
-        tn::sort_tile_bits(7, 7, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+        // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C
+        tn::sort_tile_bits(7, 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
     }
     return TN_OK;
 }
@@ -811,6 +827,12 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
     const int64_t sB = B.dep ? ((int64_t)1 << B.rank()) : 0;
     const int64_t sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
     cudaError_t e = cudaSuccess;
+    unsigned int *amax_out = nullptr;
+    if (st.amax_planar >= 0) {
+        amax_out = p->meta + 2 * p->sb * p->planars[st.amax_planar].meta;
+        TN_CUDA(cudaMemsetAsync(amax_out, 0, sizeof(unsigned int) * (C.dep ? slices : 1),
+                                stream));
+    }
     if (st.kernel == K_TC) {
         const int si = (int)(&st - &p->steps[0]);
         if (prep) TN_CUDA(cudaEventRecord(prep->first, stream));
@@ -829,15 +851,19 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             cd.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
             cd.bf16 = p->mode == TN_PREC_BF16_SCALED;
             cd.planes = q.planes;
-            TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
-            TN_CUDA(tn::launch_amax(cd, sx, stream));
+            if (!q.fused_amax) {
+                TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
+                TN_CUDA(tn::launch_amax(cd, sx, stream));
+                p->launches += 1;
+            }
             TN_CUDA(tn::launch_convert16(cd, sx, stream));
+            p->launches += 1;
         }
         if (prep) TN_CUDA(cudaEventRecord(prep->second, stream));
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_gemm_tc(p->tc_desc[si], slices, stream);
         if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
-        p->launches += 2 * 2 + 1;  // amax + convert per operand, then the GEMM
+        p->launches += 1;
     } else if (st.kernel == K_GEMM) {
         tn::GemmDesc d{};
         d.A = arena + A.off;
@@ -851,6 +877,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         d.lk = (int)st.K.size();
         d.splits = st.splits;
         d.partial = st.part_off >= 0 ? reinterpret_cast<float2 *>(p->arena + st.part_off) : nullptr;
+        d.amax_out = amax_out;
         fill_pos(d.posC_m, TN_MAXR, -1);
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
@@ -878,6 +905,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         d.sC = sC;
         d.rank_c = C.rank();
         d.nk = (int)st.K.size();
+        d.amax_out = amax_out;
         fill_pos(d.posA_c, TN_MAXR, -1);
         fill_pos(d.posB_c, TN_MAXR, -1);
         fill_pos(d.posA_k, TN_MAXR, -1);

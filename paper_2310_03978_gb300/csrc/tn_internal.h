@@ -22,6 +22,7 @@ struct GenericDesc {
     int64_t sA, sB, sC;        // slice strides in elements (0 = shared by all slices)
     int32_t rank_c;            // output bits
     int32_t nk;                // contracted bits
+    unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
     int8_t posA_c[TN_MAXR];    // output bit i -> bit of A's index (-1: label not in A)
     int8_t posB_c[TN_MAXR];
     int8_t posA_k[TN_MAXR];    // contracted bit j -> bit of A's index
@@ -39,6 +40,7 @@ struct GemmDesc {
     int32_t splits;            // > 1: split-K; CTA z sums K range z and writes partial[z][s]
     float2 *partial;           // split-K partial tiles, [splits][slices][M][N] row-major
     int32_t tile_bits;         // valid bits of a 64 x 64 tile (min(lm,6) + min(ln,6))
+    unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
     int8_t tb_src[16];         // tile bits sorted by position in C: bit of the staging index
     int8_t tb_pos[16];         //   (n: 0..5, m: 6..11) and its position in C
     int8_t posC_m[TN_MAXR];    // bit i of m (0 = least significant) -> bit of C's index
@@ -62,6 +64,12 @@ struct BindItem {
 // src[q] = row_tag | i for row bit i, or j for column bit j; pos[q] = position in C.
 void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
                     int8_t *src, int8_t *pos);
+
+// Warp-reduced atomicMax of a non-negative float into *slot (float bits order like unsigned).
+__device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, __float_as_uint(m));
+}
 
 // Kernel launchers (stream-ordered; return the launch error).
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
@@ -105,6 +113,8 @@ struct TcGemmDesc {
     int32_t form;              // 1 = 4M, 2 = 3M
     int32_t bf16;
     int32_t bk;                // K tile: 64 (128-byte swizzle) or 32 (64-byte swizzle)
+    int32_t variant;           // kernel variant (tile shape, stages, CTAs per SM)
+    unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
     int8_t tb_src[16];         // the 14 bits of a 128 x 128 tile sorted by position in C:
     int8_t tb_pos[16];         //   (is_row << 7) | bit index, and its position in C
     int8_t posC_m[TN_MAXR];
@@ -119,8 +129,11 @@ unsigned int tc_status_read_and_clear();
 // Encode a 3-D tensor map over planar 16-bit data [planes*slices][rows][K] (K contiguous),
 // box {bk, 128, 1} with the 128-byte (bk 64) or 64-byte (bk 32) swizzle.
 int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
-                         int64_t depth, int bf16, int bk);
-// Default K tile of a complex form (1 = 4M, 2 = 3M).
-int tc_default_bk(int form);
+                         int64_t depth, int bf16, int bk, int box_rows);
+// Tensor-core kernel variants: pick one for a step (form 1 = 4M, 2 = 3M; preferences 0 = any),
+// and read its K tile and N tile.
+int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref);
+int tc_variant_bk(int variant);
+int tc_variant_bn(int variant);
 
 }  // namespace tn

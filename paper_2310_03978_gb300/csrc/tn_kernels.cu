@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) k_generic(GenericDesc d, int64_t total) {
         const float2 *Ab = d.A + s * d.sA + hA;
         const float2 *Bb = d.B + s * d.sB + hB;
         float2 *Cb = d.C + s * d.sC + (int64_t)c0;
+        float amx = 0.f;
         for (int j = threadIdx.x; j < (1 << lb); j += blockDim.x) {
             const float2 *A = Ab + loA[j];
             const float2 *B = Bb + loB[j];
@@ -70,7 +71,9 @@ __global__ void __launch_bounds__(256) k_generic(GenericDesc d, int64_t total) {
                 im = fmaf(a.y, b.x, im);
             }
             Cb[j] = make_float2(re, im);
+            amx = fmaxf(amx, fmaxf(fabsf(re), fabsf(im)));
         }
+        if (d.amax_out) amax_publish(d.amax_out + s, amx);
     }
 }
 

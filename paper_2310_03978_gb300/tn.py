@@ -33,7 +33,8 @@ class PlanOptions(C.Structure):
     _fields_ = [("max_slices_in_flight", C.c_int64), ("workspace_limit", C.c_int64),
                 ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
                 ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
-                ("profile", C.c_int32), ("tc_bk", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("profile", C.c_int32), ("tc_bk", C.c_int32), ("tc_bn", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class PlanInfo(C.Structure):
@@ -156,7 +157,7 @@ class Plan:
 
     def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
                  workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
-                 profile=False, use_graph=False, tc_bk=0):
+                 profile=False, use_graph=False, tc_bk=0, tc_bn=0):
         self.network = network
         opts = PlanOptions()
         opts.max_slices_in_flight = int(max_slices_in_flight)
@@ -170,6 +171,7 @@ class Plan:
         opts.profile = 1 if profile else 0
         opts.use_graph = 1 if use_graph else 0
         opts.tc_bk = int(tc_bk)
+        opts.tc_bn = int(tc_bn)
         pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
         sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
         h = C.c_void_p()

@@ -176,15 +176,20 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
     check(got2, ref2, 1e-5)
 
 
-@pytest.mark.parametrize("form,bk", [("4m", 64), ("4m", 32), ("3m", 32), ("3m", 64)])
+# (form, K-tile preference, N-tile preference): every tensor-core kernel variant
+TC_VARIANTS = [("4m", 0, 0), ("4m", 64, 0), ("4m", 32, 0), ("4m", 0, 256), ("3m", 32, 0),
+               ("3m", 64, 0)]
+
+
+@pytest.mark.parametrize("form,bk,bn", TC_VARIANTS)
 @pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled"])
-@pytest.mark.parametrize("shape", [(7, 7, 6), (9, 8, 7), (8, 10, 8)])
-def test_single_step_tensor_core(tn, mode, shape, form, bk):
+@pytest.mark.parametrize("shape", [(7, 7, 6), (9, 8, 7), (8, 10, 8), (8, 8, 10)])
+def test_single_step_tensor_core(tn, mode, shape, form, bk, bn):
     rng = np.random.default_rng(7 + sum(shape))
     tensors, labels, out = single_step(rng, *shape)
     ref = O.contract(tensors, labels, out, [(0, 1)])
     got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode=mode, gemm_form=form,
-                               tc_bk=bk)
+                               tc_bk=bk, tc_bn=bn)
     assert kernels == ["gemm_tc"]
     check(got, ref, TOL[mode])
 
@@ -235,6 +240,26 @@ def test_graph_replay_matches_direct_launches(tn, mode):
     direct.close()
     graph.close()
     tnet.close()
+
+
+@pytest.mark.parametrize("lk1,first", [(7, "gemm_tc"), (5, "gemm_simt")])
+def test_chained_steps_feed_the_tensor_cores(tn, lk1, first):
+    # step 1 produces the operand of a tensor-core step 2; its epilogue records the max-abs
+    # that step 2's 16-bit conversion uses
+    rng = np.random.default_rng(40 + lk1)
+    a, k1, b, c = (list(range(o, o + w)) for o, w in ((0, 8), (100, lk1), (200, 8), (300, 8)))
+    T0 = crandn(rng, 8 + lk1, 2.0 ** -6)
+    T1 = crandn(rng, lk1 + 8, 2.0 ** -6)
+    T2 = crandn(rng, 16, 2.0 ** -4)
+    tensors, labels = [T0, T1, T2], [a + k1, k1 + b, b + c]
+    out = [int(x) for x in rng.permutation(a + c)]
+    path = [(0, 1), (0, 2)]
+    ref = O.contract(tensors, labels, out, path)
+    for form in ("4m", "3m"):
+        got, _, kernels = gpu_amps(tn, tensors, labels, out, path, mode="fp16_scaled",
+                                   gemm_form=form)
+        assert kernels == [first, "gemm_tc"]
+        check(got, ref, TOL["fp16_scaled"])
 
 
 def test_host_entry_points_and_set_data(tn):
