@@ -194,6 +194,25 @@ tn_status tn_contract_host(tn_plan_t *plan, int64_t slice_begin, int64_t slice_e
 tn_status tn_readout(const tn_plan_t *plan, const void *amps_dev, int32_t n_qubits,
                      double out[4], void *stream);
 
+/*
+ * FP64 readout of `num_amps` complex128 amplitudes at amps_dev, with no plan and no device
+ * allocation; out[0..3] as in tn_readout with m = num_amps.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory, such as a process whose GPU memory is held
+ * by another allocator (a caching allocator keeps freed blocks reserved, so a cudaMalloc from
+ * this library can fail although the caller has memory to spare) or one that runs under a fixed
+ * budget where every allocation must come from its own pool.
+ *   - Scratch: a fixed 64 KiB device array inside libtn.so (on every GPU that loads the library,
+ *     until the process exits); the call allocates and frees nothing.
+ *   - Limit: num_amps <= 2^28 (4096 block sums of 65536 amplitudes); larger -> TN_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's partial sums; calls whose work
+ *     overlaps on the GPU (e.g. on two streams) race.  The call synchronises `stream`.
+ * Errors: TN_ERR_INVALID_ARG, TN_ERR_CUDA.
+ */
+tn_status tn_readout_noalloc(const void *amps_dev, int64_t num_amps, int32_t n_qubits,
+                             double out[4], void *stream);
+
 /* Free a network or a plan (NULL is a no-op).  Destroy plans before their network. */
 void tn_destroy(void *handle);
 

@@ -57,6 +57,8 @@ tn_status fail(tn_status s, const char *fmt, ...) {
 
 }  // namespace
 
+tn_status tn::report(tn_status s, const char *msg) { return fail(s, "%s", msg); }
+
 struct tn_network {
     uint32_t magic = kNetMagic;
     int device = 0;

@@ -12,7 +12,12 @@
 
 #define TN_MAXR 48  // largest rank handled by a kernel descriptor
 
+#include "../../include/tn.h"
+
 namespace tn {
+
+// Record `msg` as this thread's error detail (tn_last_error_detail) and return `s`.
+tn_status report(tn_status s, const char *msg);
 
 // Element-wise contraction: one thread per output element (any memory orders).
 struct GenericDesc {

@@ -26,7 +26,7 @@ KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc"}
 # Every symbol declared in include/tn.h.
 EXPORTS = ("tn_network_load", "tn_network_set_data", "tn_plan", "tn_plan_get_info",
            "tn_plan_get_step_info", "tn_contract", "tn_contract_host", "tn_readout",
-           "tn_destroy", "tn_status_string", "tn_last_error_detail")
+           "tn_readout_noalloc", "tn_destroy", "tn_status_string", "tn_last_error_detail")
 
 
 class PlanOptions(C.Structure):
@@ -83,6 +83,7 @@ def lib():
         L.tn_contract.argtypes = [vp, i64, i64, vp, vp]
         L.tn_contract_host.argtypes = [vp, i64, i64, vp, vp]
         L.tn_readout.argtypes = [vp, vp, i32, vp, vp]
+        L.tn_readout_noalloc.argtypes = [vp, i64, i32, vp, vp]
         L.tn_destroy.argtypes = [vp]
         L.tn_destroy.restype = None
         L.tn_status_string.argtypes = [C.c_int]
@@ -107,6 +108,16 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+def readout_noalloc(amps, n_qubits, stream=None):
+    """FP64 readout of a complex128 CUDA tensor without a plan and without device allocation
+    (tn_readout_noalloc): [sum p, sum p^2, F_l, ideal-sample XEB]."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(lib().tn_readout_noalloc(C.c_void_p(amps.data_ptr()), int(amps.numel()),
+                                    int(n_qubits), C.c_void_p(out.ctypes.data),
+                                    _stream_ptr(stream)))
+    return out
 
 
 class Network:
