@@ -14,6 +14,7 @@
 // tile, and a second kernel adds the partials in increasing z (a fixed order, so results do not
 // depend on scheduling) and scatters the sums.
 #include "tn_internal.h"
+#include "tn_planar_out.cuh"
 
 namespace tn {
 
@@ -137,38 +138,47 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
 #pragma unroll
         for (int j = 0; j < TN; ++j)
             stage[(ty + 16 * i) * BN + tx + 16 * j] = make_float2(cr[i][j], ci[i][j]);
-    // element t of the tile in C order: its low 8 bits come from the thread index, the high
-    // bits from the iteration; the sorted tile bits were computed on the host
+    // element pairs of the tile in C order: sorted tile bit 0 is C's position 0 (the pair),
+    // bits 1..8 come from the thread index and the rest from the iteration; the sorted tile bits
+    // were computed on the host
     const int nb = d.tile_bits;
     __syncthreads();
+    const int dpair = 1 << d.tb_src[0];
     int wlo = 0;
     uint64_t olo = 0;
-    for (int q = 0; q < 8 && q < nb; ++q)
-        if ((threadIdx.x >> q) & 1) {
+    for (int q = 1; q < 9 && q < nb; ++q)
+        if ((threadIdx.x >> (q - 1)) & 1) {
             wlo |= 1 << d.tb_src[q];
             olo |= 1ull << d.tb_pos[q];
         }
-    float2 *C = d.C + s * d.sC +
-                (deposit((uint64_t)m0, d.lm, d.posC_m) | deposit((uint64_t)n0, d.ln, d.posC_n));
+    const uint64_t cbase =
+        deposit((uint64_t)m0, d.lm, d.posC_m) | deposit((uint64_t)n0, d.ln, d.posC_n);
+    float2 *C = d.C + s * d.sC + cbase;
+    const int eo = d.planar_out ? planar_out_exponent(d.pout, s) : 0;
+    if (d.planar_out && blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+        d.pout.exps[s] = eo;
     float amx = 0.f;
-    if (nb < 8) {
-        if ((int)threadIdx.x < (1 << nb)) {
-            const float2 v = stage[wlo];
-            C[olo] = v;
-            amx = fmaxf(fabsf(v.x), fabsf(v.y));
+    auto put = [&](uint64_t off, int w) {
+        const float2 v0 = stage[w], v1 = stage[w + dpair];
+        if (d.planar_out) {
+            planar_out_store2(d.pout, s, cbase | off, v0, v1, eo);
+        } else {
+            *reinterpret_cast<float4 *>(C + off) = make_float4(v0.x, v0.y, v1.x, v1.y);
         }
+        amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v1.x), fabsf(v1.y))));
+    };
+    if (nb - 1 <= 8) {
+        if ((int)threadIdx.x < (1 << (nb - 1))) put(olo, wlo);
     } else {
-        for (int it = 0; it < (1 << (nb - 8)); ++it) {
+        for (int it = 0; it < (1 << (nb - 9)); ++it) {
             int w = wlo;
             uint64_t off = olo;
-            for (int q = 8; q < nb; ++q)
-                if ((it >> (q - 8)) & 1) {
+            for (int q = 9; q < nb; ++q)
+                if ((it >> (q - 9)) & 1) {
                     w |= 1 << d.tb_src[q];
                     off |= 1ull << d.tb_pos[q];
                 }
-            const float2 v = stage[w];
-            C[off] = v;
-            amx = fmaxf(amx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            put(off, w);
         }
     }
     if (d.amax_out) amax_publish(d.amax_out + s, amx);

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "tn_internal.h"
+#include "tn_planar_out.cuh"
 
 namespace tn {
 
@@ -320,23 +321,27 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
         const int e = d.expA[sa] + d.expB[sbi];
         const int row = warp * 32 + lane;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // sorted chunk bit 0 is C's position 0, so each thread writes an adjacent pair: bit 0
+        // is the pair, bits 1..7 come from the thread index and bits 8..12 from the iteration
+        const int sq0 = d.tb_src[0];
+        const int dpair = (sq0 & 128) ? (1 << (sq0 & 127)) * SLD : (1 << sq0);
         int mlo = 0, nlo = 0;
         uint64_t olo = 0;
 #pragma unroll
-        for (int q = 0; q < 7; ++q)
-            if ((threadIdx.x >> q) & 1) {
+        for (int q = 1; q < 8; ++q)
+            if ((threadIdx.x >> (q - 1)) & 1) {
                 const int sq = d.tb_src[q];
                 if (sq & 128) mlo |= 1 << (sq & 127);
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
         const int wlo = mlo * SLD + nlo;
-        if (threadIdx.x < 64) {
+        if (threadIdx.x < 32) {
             int mi = 0, ni = 0;
             uint64_t off = 0;
 #pragma unroll
-            for (int q = 7; q < 13; ++q)
-                if ((threadIdx.x >> (q - 7)) & 1) {
+            for (int q = 8; q < 13; ++q)
+                if ((threadIdx.x >> (q - 8)) & 1) {
                     const int sq = d.tb_src[q];
                     if (sq & 128) mi |= 1 << (sq & 127);
                     else ni |= 1 << sq;
@@ -346,6 +351,8 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             hi_w[threadIdx.x] = mi * SLD + ni;
         }
         const uint64_t mbase = deposit((uint64_t)m0, d.lm, d.posC_m);
+        const int eo = d.planar_out ? planar_out_exponent(d.pout, s) : 0;
+        if (d.planar_out && blockIdx.x == 0 && threadIdx.x == 0) d.pout.exps[s] = eo;
         float amx = 0.f;
 #pragma unroll 1
         for (int cb = 0; cb < BN; cb += CW) {
@@ -375,13 +382,27 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
                 }
             }
             __syncthreads();
-            float2 *C = d.C + s * d.sC +
-                        (mbase | deposit((uint64_t)(n0 + cb), d.ln, d.posC_n));
+            const uint64_t cbase = mbase | deposit((uint64_t)(n0 + cb), d.ln, d.posC_n);
+            if (d.planar_out) {
 #pragma unroll 4
-            for (int it = 0; it < (BM * CW) / 128; ++it) {
-                const float2 v = stage[wlo + hi_w[it]];
-                C[olo | hi_off[it]] = v;
-                amx = fmaxf(amx, fmaxf(fabsf(v.x), fabsf(v.y)));
+                for (int it = 0; it < (BM * CW) / 256; ++it) {
+                    const int w = wlo + hi_w[it];
+                    const float2 v0 = stage[w], v1 = stage[w + dpair];
+                    planar_out_store2(d.pout, s, cbase | olo | hi_off[it], v0, v1, eo);
+                    amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
+                                           fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                }
+            } else {
+                float2 *C = d.C + s * d.sC + cbase;
+#pragma unroll 4
+                for (int it = 0; it < (BM * CW) / 256; ++it) {
+                    const int w = wlo + hi_w[it];
+                    const float2 v0 = stage[w], v1 = stage[w + dpair];
+                    *reinterpret_cast<float4 *>(C + (olo | hi_off[it])) =
+                        make_float4(v0.x, v0.y, v1.x, v1.y);
+                    amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
+                                           fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                }
             }
             __syncthreads();
         }

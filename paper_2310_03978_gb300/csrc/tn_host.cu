@@ -80,6 +80,8 @@ struct Tensor {
     int leaf = -1;           // network tensor index for a leaf
     int64_t off = -1;        // complex64 element offset in the arena
     int t0 = 0, t1 = 0;      // lifetime on the op timeline
+    int meta = -1;           // block of per-slice (max-abs, exponent) if some step needs them
+    bool direct = false;     // produced directly as a planar 16-bit copy (no complex64 storage)
     int rank() const { return (int)order.size(); }
     int pos(int label) const {  // bit position of a label in this tensor's memory index
         for (int i = 0; i < rank(); ++i)
@@ -91,11 +93,12 @@ struct Tensor {
 struct Planar {              // planar 16-bit copy of a tensor feeding a tensor-core step
     int tensor = -1;
     int planes = 2;          // re, im (4M) or re, im, re + im (3M)
-    bool fused_amax = false; // its producer's epilogue records the per-slice max-abs
+    bool direct = false;     // written by its producer's epilogue (no conversion pass)
     int64_t off = -1;        // byte offset in the arena
     int64_t bytes_per_slice = 0;
     int t = 0;               // time of the consuming step
     int meta = -1;           // index of its (amax, exps) block
+    int t0 = 0;              // first op that writes it
 };
 
 struct Step {
@@ -109,7 +112,8 @@ struct Step {
     int pa = -1, pb = -1;        // planar copies for K_TC
     int form = TN_GEMM_4M;
     int splits = 1;              // K_GEMM split-K factor
-    int amax_planar = -1;        // planar copy whose max-abs this step's epilogue records
+    int out_meta = -1;           // meta block whose per-slice max-abs this step's epilogue records
+    int direct_planar = -1;      // planar copy this step writes directly instead of complex64
     int64_t part_off = -1;       // K_GEMM split-K partials (byte offset in the arena)
     // profile mode: recorded (start, stop) event pairs not yet read, and the running totals
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pending_prep;
@@ -144,7 +148,8 @@ struct tn_plan {
     std::vector<tn::BindItem> bind_inv, bind_sl;
     tn::BindItem *bind_inv_dev = nullptr, *bind_sl_dev = nullptr;
     int max_rank_inv = 0, max_rank_sl = 0;
-    unsigned int *meta = nullptr;  // per planar: amax[sb] then exps[sb]
+    unsigned int *meta = nullptr;  // per meta block: amax[sb] then exps[sb]
+    int nmeta = 0;
     double *partial = nullptr;     // readout partials
     double2 *amps_tmp = nullptr;   // tn_contract_host accumulator
     int n_partial = 64;
@@ -364,6 +369,7 @@ int64_t layout_bytes(tn_plan_t *p, int64_t sb, bool commit) {
     std::vector<int> who;  // >= 0 tensor, < 0: -(planar + 1)
     for (size_t i = 0; i < p->tensors.size(); ++i) {
         const Tensor &t = p->tensors[i];
+        if (t.direct) continue;  // lives only as its planar copy
         int64_t bytes = (int64_t)8 << t.rank();
         if (t.dep) bytes *= sb;
         items.push_back({align_up(bytes, 256), {t.t0, t.t1}});
@@ -373,7 +379,7 @@ int64_t layout_bytes(tn_plan_t *p, int64_t sb, bool commit) {
         const Planar &q = p->planars[i];
         const Tensor &t = p->tensors[q.tensor];
         int64_t bytes = q.bytes_per_slice * (t.dep ? sb : 1);
-        items.push_back({align_up(bytes, 1024), {q.t - 2, q.t}});
+        items.push_back({align_up(bytes, 1024), {q.t0, q.t}});
         who.push_back(-(int)i - 1);
     }
     const int npl = (int)p->planars.size();
@@ -381,8 +387,10 @@ int64_t layout_bytes(tn_plan_t *p, int64_t sb, bool commit) {
         Step &st = p->steps[i];
         if (st.kernel != K_GEMM) continue;
         const int64_t sl = st.dep ? sb : 1;
-        const int sp = tn::gemm_simt_splits((int)st.M.size(), (int)st.N.size(),
-                                            (int)st.K.size(), sl);
+        const int sp = st.direct_planar >= 0
+                           ? 1
+                           : tn::gemm_simt_splits((int)st.M.size(), (int)st.N.size(),
+                                                  (int)st.K.size(), sl);
         if (commit) st.splits = sp;
         if (sp <= 1) continue;
         const int64_t bytes = (int64_t)sp * sl * ((int64_t)8 << (st.M.size() + st.N.size()));
@@ -577,7 +585,57 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
     }
     if (path_len == 0) p->tensors[p->root].order = net->open;
 
-    // 4. op timeline: invariant leaves, invariant steps, sliced leaves, dependent steps, accumulate
+    // 4. tensor-core operands get planar 16-bit copies.  When the operand's producer is a GEMM
+    //    step of the slice loop (with whole 64 x 64 tiles to spare), that producer writes the
+    //    copy directly, with an exponent bounded from its own inputs' max-abs; otherwise a
+    //    conversion pass makes it from complex64 just before the step.
+    for (int s = 0; s < path_len; ++s) {
+        Step &st = p->steps[s];
+        if (!st.dep || st.kernel != K_TC) continue;
+        for (int side = 0; side < 2; ++side) {
+            Planar q;
+            q.tensor = side ? st.b : st.a;
+            q.planes = st.form == TN_GEMM_3M ? 3 : 2;
+            q.bytes_per_slice = (int64_t)(2 * q.planes) << p->tensors[q.tensor].rank();
+            const Tensor &X = p->tensors[q.tensor];
+            if (X.producer >= 0) {
+                // a CUDA-core producer writes directly only with whole 64 x 64 tiles, and then
+                // never splits K (its epilogue must hold final sums)
+                const Step &pr = p->steps[X.producer];
+                q.direct = pr.dep && (pr.kernel == K_TC ||
+                                      (pr.kernel == K_GEMM && pr.M.size() >= 6 &&
+                                       pr.N.size() >= 6));
+            }
+            (side ? st.pb : st.pa) = (int)p->planars.size();
+            p->planars.push_back(q);
+        }
+    }
+    {
+        auto need_meta = [&](int ti) {
+            if (p->tensors[ti].meta < 0) p->tensors[ti].meta = p->nmeta++;
+        };
+        for (auto &q : p->planars) need_meta(q.tensor);
+        for (auto &q : p->planars)
+            if (q.direct) {
+                const Step &pr = p->steps[p->tensors[q.tensor].producer];
+                if (pr.kernel == K_GEMM) {
+                    need_meta(pr.a);
+                    need_meta(pr.b);
+                }
+            }
+        for (auto &q : p->planars) {
+            q.meta = p->tensors[q.tensor].meta;
+            if (q.direct) {
+                p->tensors[q.tensor].direct = true;
+                p->steps[p->tensors[q.tensor].producer].direct_planar = (int)(&q - &p->planars[0]);
+            }
+        }
+        // a tensor's max-abs is recorded by its producer's epilogue; leaves get an amax pass
+        for (auto &x : p->tensors)
+            if (x.meta >= 0 && x.producer >= 0) p->steps[x.producer].out_meta = x.meta;
+    }
+    // op timeline: invariant leaves, invariant steps, sliced leaves, dependent steps (each
+    // tensor-core step preceded by its conversions), accumulate
     std::vector<Op> ops;
     ops.push_back({0, -1});
     for (int s = 0; s < path_len; ++s)
@@ -587,16 +645,8 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         if (p->steps[s].dep) {
             Step &st = p->steps[s];
             if (st.kernel == K_TC) {
-                for (int side = 0; side < 2; ++side) {
-                    Planar q;
-                    q.tensor = side ? st.b : st.a;
-                    q.planes = st.form == TN_GEMM_3M ? 3 : 2;
-                    q.bytes_per_slice = (int64_t)(2 * q.planes) << p->tensors[q.tensor].rank();
-                    q.meta = (int)p->planars.size();
-                    (side ? st.pb : st.pa) = (int)p->planars.size();
-                    p->planars.push_back(q);
-                    ops.push_back({3, (int)p->planars.size() - 1});
-                }
+                ops.push_back({3, st.pa});
+                ops.push_back({3, st.pb});
             }
             ops.push_back({1, s});
         }
@@ -613,15 +663,14 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
             p->tensors[st.c].t0 = p->tensors[st.c].t1 = t;
             p->tensors[st.a].t1 = t;
             p->tensors[st.b].t1 = t;
-        } else if (op.kind == 3) {
-            p->planars[op.index].t = t + 1;
         }
     }
     for (auto &st : p->steps) {
-        if (st.kernel == K_TC) {
-            // both planar copies are written by the two convert ops just before the step
-            p->planars[st.pa].t = st.t;
-            p->planars[st.pb].t = st.t;
+        if (st.kernel != K_TC) continue;
+        for (int side = 0; side < 2; ++side) {
+            Planar &q = p->planars[side ? st.pb : st.pa];
+            q.t = st.t;  // last use
+            q.t0 = q.direct ? p->steps[p->tensors[q.tensor].producer].t : st.t - 2;
         }
     }
     // invariant tensors read by the slice loop stay live through all batches
@@ -700,6 +749,25 @@ tn::BindItem make_bind(const tn_plan_t *p, const Tensor &t) {
     return it;
 }
 
+// Direct planar output of step st (see tn::PlanarOut): the consumer's planar buffer, the
+// exponents of its meta block, and the max-abs of st's inputs for the bound.
+void fill_planar_out(const tn_plan_t *p, const Step &st, tn::PlanarOut &o) {
+    const Planar &q = p->planars[st.direct_planar];
+    const Tensor &C = p->tensors[st.c], &A = p->tensors[st.a], &B = p->tensors[st.b];
+    const int64_t n = (int64_t)1 << C.rank();
+    o.base = p->arena + q.off;
+    o.sstride = C.dep ? n : 0;
+    o.plane_stride = n * (C.dep ? p->sb : 1);
+    o.planes = q.planes;
+    o.bf16 = p->mode == TN_PREC_BF16_SCALED;
+    o.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
+    o.amax_a = p->meta + 2 * p->sb * A.meta;
+    o.amax_b = p->meta + 2 * p->sb * B.meta;
+    o.a_sliced = A.dep ? 1 : 0;
+    o.b_sliced = B.dep ? 1 : 0;
+    o.log2_k = (int)st.K.size();
+}
+
 tn_status build_descriptors(tn_plan_t *p) {
     for (auto &t : p->tensors) {
         if (t.leaf < 0) continue;
@@ -728,21 +796,11 @@ tn_status build_descriptors(tn_plan_t *p) {
     if (s != TN_OK) return s;
     s = upload(p->bind_sl, &p->bind_sl_dev);
     if (s != TN_OK) return s;
-    if (!p->planars.empty())
-        TN_CUDA(cudaMalloc(&p->meta, sizeof(unsigned int) * 2 * p->sb * p->planars.size()));
+    if (p->nmeta > 0)
+        TN_CUDA(cudaMalloc(&p->meta, sizeof(unsigned int) * 2 * p->sb * p->nmeta));
     TN_CUDA(cudaMalloc(&p->partial, sizeof(double) * 2 * p->n_partial));
     TN_CUDA(cudaMalloc(&p->amps_tmp, sizeof(double2) << p->net->open.size()));
 
-    // a tensor-core operand produced by a step gets its max-abs from that step's epilogue
-    for (size_t i = 0; i < p->planars.size(); ++i) {
-        Planar &q = p->planars[i];
-        const Tensor &t = p->tensors[q.tensor];
-        if (t.producer < 0) continue;
-        Step &pr = p->steps[t.producer];
-        if (pr.amax_planar >= 0) continue;
-        pr.amax_planar = (int)i;
-        q.fused_amax = true;
-    }
     p->tc_desc.resize(p->steps.size());
     for (auto &st : p->steps) {
         if (st.kernel != K_TC) continue;
@@ -776,14 +834,22 @@ tn_status build_descriptors(tn_plan_t *p) {
         d.expB = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qb.meta + p->sb);
         d.form = st.form;
         d.bf16 = bf;
-        d.amax_out = st.amax_planar >= 0 ? p->meta + 2 * p->sb * p->planars[st.amax_planar].meta
-                                         : nullptr;
+        d.amax_out = st.out_meta >= 0 ? p->meta + 2 * p->sb * st.out_meta : nullptr;
+        if (st.direct_planar >= 0) {
+            d.planar_out = 1;
+            fill_planar_out(p, st, d.pout);
+        }
         fill_pos(d.posC_m, TN_MAXR, -1);
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
         for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
-        // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C
+        // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C; the first is
+        // always position 0 (the lowest label of C is the lowest of its side), which the
+        // epilogue's pair stores rely on
         tn::sort_tile_bits(7, 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+        if (d.tb_pos[0] != 0)
+            return fail(TN_ERR_UNSUPPORTED, "step %d: result bit 0 outside the epilogue chunk",
+                        (int)(&st - &p->steps[0]));
     }
     return TN_OK;
 }
@@ -830,10 +896,27 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
     const int64_t sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
     cudaError_t e = cudaSuccess;
     unsigned int *amax_out = nullptr;
-    if (st.amax_planar >= 0) {
-        amax_out = p->meta + 2 * p->sb * p->planars[st.amax_planar].meta;
+    if (st.out_meta >= 0) {
+        amax_out = p->meta + 2 * p->sb * st.out_meta;
         TN_CUDA(cudaMemsetAsync(amax_out, 0, sizeof(unsigned int) * (C.dep ? slices : 1),
                                 stream));
+    }
+    // a direct CUDA-core producer bounds its output from its inputs' max-abs; inputs that are
+    // leaves (no producer epilogue records it) get an amax pass here
+    if (st.kernel == K_GEMM && st.direct_planar >= 0) {
+        for (int side = 0; side < 2; ++side) {
+            const Tensor &X = side ? B : A;
+            if (X.producer >= 0) continue;
+            tn::ConvertDesc cd{};
+            cd.src = arena + X.off;
+            cd.n = (int64_t)1 << X.rank();
+            cd.src_sstride = X.dep ? cd.n : 0;
+            cd.amax = p->meta + 2 * p->sb * X.meta;
+            const int64_t sx = X.dep ? slices : 1;
+            TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
+            TN_CUDA(tn::launch_amax(cd, sx, stream));
+            p->launches += 1;
+        }
     }
     if (st.kernel == K_TC) {
         const int si = (int)(&st - &p->steps[0]);
@@ -841,6 +924,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         for (int side = 0; side < 2; ++side) {
             const Planar &q = p->planars[side ? st.pb : st.pa];
             const Tensor &X = side ? B : A;
+            if (q.direct) continue;  // written by its producer
             tn::ConvertDesc cd{};
             cd.src = arena + X.off;
             cd.dst = p->arena + q.off;
@@ -853,7 +937,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             cd.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
             cd.bf16 = p->mode == TN_PREC_BF16_SCALED;
             cd.planes = q.planes;
-            if (!q.fused_amax) {
+            if (X.producer < 0) {  // a leaf: no producer epilogue recorded its max-abs
                 TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
                 TN_CUDA(tn::launch_amax(cd, sx, stream));
                 p->launches += 1;
@@ -880,6 +964,10 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         d.splits = st.splits;
         d.partial = st.part_off >= 0 ? reinterpret_cast<float2 *>(p->arena + st.part_off) : nullptr;
         d.amax_out = amax_out;
+        if (st.direct_planar >= 0) {
+            d.planar_out = 1;
+            fill_planar_out(p, st, d.pout);
+        }
         fill_pos(d.posC_m, TN_MAXR, -1);
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
@@ -891,6 +979,9 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             // the staging index of row i, column j is 64 * i + j: row bit i is index bit 6 + i
             for (int q = 0; q < d.tile_bits; ++q)
                 if (d.tb_src[q] & 64) d.tb_src[q] = (int8_t)(6 + (d.tb_src[q] & 63));
+            if (d.tb_pos[0] != 0)
+                return fail(TN_ERR_UNSUPPORTED, "step %d: result bit 0 outside the GEMM tile",
+                            (int)(&st - &p->steps[0]));
         }
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_gemm_simt(d, slices, stream);

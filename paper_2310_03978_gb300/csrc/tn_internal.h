@@ -19,6 +19,38 @@ namespace tn {
 // Record `msg` as this thread's error detail (tn_last_error_detail) and return `s`.
 tn_status report(tn_status s, const char *msg);
 
+// Direct planar 16-bit output of a GEMM whose result feeds a tensor-core step: the producer
+// writes stored = value * 2^-e into the consumer's planar buffer (re, im, and for the 3M form
+// re + im planes), with e chosen before the GEMM runs from the bound
+//     max(|Re c|, |Im c|) <= 2 K max|a| max|b|,   max|x| = max over x of max(|Re x|, |Im x|),
+// evaluated from the inputs' measured per-slice max-abs, so that |stored| < 2^15 (inside FP16's
+// range) and no overflow is possible.  The exponent of slice s is written to exps[s].
+struct PlanarOut {
+    void *base;                     // plane p, slice s: base + p * plane_stride + s * sstride
+    int64_t plane_stride;           // elements
+    int64_t sstride;                // elements
+    int32_t planes;                 // 2, or 3 with the re + im plane
+    int32_t bf16;
+    int32_t *exps;                  // per slice exponent (written by the producer)
+    const unsigned int *amax_a;     // inputs' per-slice max-abs, float bits, true scale
+    const unsigned int *amax_b;
+    int32_t a_sliced, b_sliced;     // 0: the input is shared by all slices (index 0)
+    int32_t log2_k;
+};
+
+#ifdef __CUDACC__
+// Exponent e of the direct planar output of slice s (see PlanarOut).
+__device__ __forceinline__ int planar_out_exponent(const PlanarOut &o, int64_t s) {
+    const float a = __uint_as_float(o.amax_a[o.a_sliced ? s : 0]);
+    const float b = __uint_as_float(o.amax_b[o.b_sliced ? s : 0]);
+    if (!(a > 0.f) || !(b > 0.f) || !isfinite(a) || !isfinite(b)) return 0;
+    int ea, eb;
+    frexpf(a, &ea);  // a < 2^ea
+    frexpf(b, &eb);
+    return ea + eb + 1 + o.log2_k - 15;  // 2 K a b < 2^(e + 15)
+}
+#endif
+
 // Element-wise contraction: one thread per output element (any memory orders).
 struct GenericDesc {
     const float2 *A;
@@ -46,6 +78,8 @@ struct GemmDesc {
     float2 *partial;           // split-K partial tiles, [splits][slices][M][N] row-major
     int32_t tile_bits;         // valid bits of a 64 x 64 tile (min(lm,6) + min(ln,6))
     unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
+    int32_t planar_out;        // 1: write C as PlanarOut `pout` instead of complex64
+    PlanarOut pout;
     int8_t tb_src[16];         // tile bits sorted by position in C: bit of the staging index
     int8_t tb_pos[16];         //   (n: 0..5, m: 6..11) and its position in C
     int8_t posC_m[TN_MAXR];    // bit i of m (0 = least significant) -> bit of C's index
@@ -69,6 +103,7 @@ struct BindItem {
 // src[q] = row_tag | i for row bit i, or j for column bit j; pos[q] = position in C.
 void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
                     int8_t *src, int8_t *pos);
+
 
 // Warp-reduced atomicMax of a non-negative float into *slot (float bits order like unsigned).
 __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {
@@ -120,6 +155,8 @@ struct TcGemmDesc {
     int32_t bk;                // K tile: 64 (128-byte swizzle) or 32 (64-byte swizzle)
     int32_t variant;           // kernel variant (tile shape, stages, CTAs per SM)
     unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
+    int32_t planar_out;        // 1: write C as PlanarOut `pout` instead of complex64
+    PlanarOut pout;
     int8_t tb_src[16];         // the 14 bits of a 128 x 128 tile sorted by position in C:
     int8_t tb_pos[16];         //   (is_row << 7) | bit index, and its position in C
     int8_t posC_m[TN_MAXR];

@@ -242,10 +242,11 @@ def test_graph_replay_matches_direct_launches(tn, mode):
     tnet.close()
 
 
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled"])
 @pytest.mark.parametrize("lk1,first", [(7, "gemm_tc"), (5, "gemm_simt")])
-def test_chained_steps_feed_the_tensor_cores(tn, lk1, first):
-    # step 1 produces the operand of a tensor-core step 2; its epilogue records the max-abs
-    # that step 2's 16-bit conversion uses
+def test_chained_steps_feed_the_tensor_cores(tn, lk1, first, mode):
+    # step 1 writes the operand of tensor-core step 2 directly as planar 16-bit numbers, with an
+    # exponent bounded from its own inputs' max-abs (the tensor-core and CUDA-core epilogues)
     rng = np.random.default_rng(40 + lk1)
     a, k1, b, c = (list(range(o, o + w)) for o, w in ((0, 8), (100, lk1), (200, 8), (300, 8)))
     T0 = crandn(rng, 8 + lk1, 2.0 ** -6)
@@ -256,10 +257,9 @@ def test_chained_steps_feed_the_tensor_cores(tn, lk1, first):
     path = [(0, 1), (0, 2)]
     ref = O.contract(tensors, labels, out, path)
     for form in ("4m", "3m"):
-        got, _, kernels = gpu_amps(tn, tensors, labels, out, path, mode="fp16_scaled",
-                                   gemm_form=form)
+        got, _, kernels = gpu_amps(tn, tensors, labels, out, path, mode=mode, gemm_form=form)
         assert kernels == [first, "gemm_tc"]
-        check(got, ref, TOL["fp16_scaled"])
+        check(got, ref, TOL[mode])
 
 
 def test_host_entry_points_and_set_data(tn):
