@@ -213,6 +213,15 @@ tn_status tn_readout(const tn_plan_t *plan, const void *amps_dev, int32_t n_qubi
 tn_status tn_readout_noalloc(const void *amps_dev, int64_t num_amps, int32_t n_qubits,
                              double out[4], void *stream);
 
+/*
+ * Failure-detection self-test of the tensor-core kernel's bounded waits: launches one CTA whose
+ * producer issues no copies, so its MMA warp's wait gives up after limit_ms (1..10000); the CTA
+ * records the timeout, frees its tensor memory and exits without writing results.  Returns
+ * TN_ERR_TIMEOUT when the wait ran out as designed (the CUDA context stays usable), TN_OK if it
+ * did not, TN_ERR_UNSUPPORTED without a tcgen05 device.  Synchronises `stream`.
+ */
+tn_status tn_selftest_wait_timeout(int32_t limit_ms, void *stream);
+
 /* Free a network or a plan (NULL is a no-op).  Destroy plans before their network. */
 void tn_destroy(void *handle);
 

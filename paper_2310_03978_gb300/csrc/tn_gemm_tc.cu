@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "tn_internal.h"
 #include "tn_planar_out.cuh"
 
@@ -53,7 +55,7 @@ struct Cfg {
     static_assert(MINB * TMEM_COLS <= 512, "co-resident CTAs exceed tensor memory");
 };
 
-constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // default bound of every wait: 4 s
 
 __device__ unsigned int g_tc_status;  // bit 0: an mbarrier wait timed out
 
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
     uint64_t *empty = full + STAGES;
     uint64_t *done = empty + STAGES;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    int *aborted = reinterpret_cast<int *>(tmem_slot + 1);  // set when a wait gave up
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = blockIdx.y;
@@ -201,7 +204,8 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
     const int64_t mt = first_m + (tile % per_group) % gsize;
     const int64_t nt = (tile % per_group) / gsize;
     const int m0 = (int)(mt * BM), n0 = (int)(nt * BN);
-    const int num_kb = (1 << d.lk) / BK;
+    // K below the K tile: one block, the tensor map zero-fills the columns past K
+    const int num_kb = ((1 << d.lk) + BK - 1) / BK;
     const int sa = d.a_sliced ? (int)s : 0, sbi = d.b_sliced ? (int)s : 0;
 
     if (threadIdx.x == 0) {
@@ -210,6 +214,7 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             mbar_init(&empty[i], 1);
         }
         mbar_init(done, 1);
+        *aborted = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmA))
                      : "memory");
@@ -226,7 +231,8 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const unsigned long long deadline = globaltimer() + kWaitLimitNs;
+    const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
+    const unsigned long long deadline = globaltimer() + limit;
 
     int issued = 0;  // k blocks whose loads the producer issued
     if (threadIdx.x == 0) {
@@ -234,7 +240,11 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
         for (int kb = 0; kb < num_kb; ++kb) {
             const int st = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (kb >= STAGES && !mbar_wait(&empty[st], ph ^ 1u, deadline)) break;
+            if (kb >= STAGES && !mbar_wait(&empty[st], ph ^ 1u, deadline)) {
+                *aborted = 1;
+                break;
+            }
+            if (d.selftest_no_loads) break;  // nothing will arrive on full[]
             uint8_t *base = smem + st * STAGE_BYTES;
             mbar_expect_tx(&full[st], STAGE_BYTES);
             const int k0 = kb * BK;
@@ -258,6 +268,7 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
             if (!mbar_wait(&full[st], ph, deadline)) {
                 ok = false;
+                *aborted = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -295,19 +306,19 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
     // whenever C's low bits fall inside the tile.  The wait result is made warp-uniform because
     // tcgen05.ld is a warp-collective instruction.
     bool have = false;
-    if (lane == 0) have = mbar_wait(done, 0, deadline);
+    if (lane == 0) have = mbar_wait(done, 0, deadline) && *(volatile int *)aborted == 0;
     have = __shfl_sync(0xffffffffu, have ? 1 : 0, 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (threadIdx.x == 0) {
         // every load this CTA issued must have landed before its shared memory is reused or
         // released; after a normal run the MMA warp consumed them all and these waits return
-        const unsigned long long drain = globaltimer() + kWaitLimitNs;
+        const unsigned long long drain = globaltimer() + limit;
         for (int st = 0; st < STAGES && st < issued; ++st) {
             const int last = ((issued - 1 - st) / STAGES) * STAGES + st;
             mbar_wait(&full[st], (uint32_t)(last / STAGES) & 1u, drain);
         }
     }
-    have = __syncthreads_and(have ? 1 : 0) != 0;
+    have = __syncthreads_and(have && *(volatile int *)aborted == 0 ? 1 : 0) != 0;
     if (have) {
         // The tile is written in chunks of CW = 64 columns: each chunk is staged in shared
         // memory and written out in the order of C's memory index.  A chunk has 13 bits (7 row,
@@ -452,7 +463,9 @@ int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t r
                          int64_t depth, int bf16, int bk, int box_rows) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return -1;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bk != 32 && bk != 64) || K % bk != 0)
+    // K must fill whole 16-byte rows; a K below the tile is zero-filled by the tensor map
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bk != 32 && bk != 64) || K % 8 != 0 ||
+        (K > bk && K % bk != 0))
         return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
     cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2)};
@@ -488,7 +501,7 @@ cudaError_t configure_variant() {
 
 template <int NPL, int BKT, int BNT, int STG, int MINB>
 cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    if (d.ln < (BNT == 256 ? 8 : 7) || d.lk < (BKT == 64 ? 6 : 5))
+    if (d.ln < (BNT == 256 ? 8 : 7) || d.lk < 3 || (BKT == 64 && d.lk < 6))
         return cudaErrorInvalidValue;
     const int64_t tiles_n = (1ll << d.ln) / BNT;
     const int64_t tiles = ((1ll << d.lm) / BM) * tiles_n;
@@ -551,6 +564,43 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 #undef TN_TC_LAUNCH
     }
     return cudaErrorInvalidValue;
+}
+
+// One CTA whose producer issues no loads: the MMA warp's wait on the first stage runs out after
+// limit_ms, the CTA records the timeout in the status word, skips its epilogue, frees its tensor
+// memory and exits.  Returns TN_ERR_TIMEOUT when that happened, TN_OK when the wait did not run out.
+tn_status tc_selftest_wait_timeout(int32_t limit_ms, cudaStream_t st) {
+    if (limit_ms < 1 || limit_ms > 10000) return report(TN_ERR_INVALID_ARG, "limit_ms out of range");
+    if (!tc_available()) return report(TN_ERR_UNSUPPORTED, "no tcgen05 device");
+    tc_status_read_and_clear();
+    float2 *buf = nullptr;  // a valid tile-sized target; the self-test never writes it
+    if (cudaMalloc(&buf, sizeof(float2) * 128 * 128 + 64) != cudaSuccess)
+        return report(TN_ERR_OOM, "self-test buffer");
+    TcGemmDesc d;
+    memset(&d, 0, sizeof d);
+    int32_t *exps = reinterpret_cast<int32_t *>(buf + 128 * 128);
+    if (encode_tmap_planar16(&d.tmA, buf, 64, 128, 2, 0, 64, 128) != 0 ||
+        encode_tmap_planar16(&d.tmB, buf, 64, 128, 2, 0, 64, 128) != 0) {
+        cudaFree(buf);
+        return report(TN_ERR_CUDA, "self-test tensor maps");
+    }
+    d.C = buf;
+    d.lm = 7;
+    d.ln = 7;
+    d.lk = 6;
+    d.slices_a = d.slices_b = 1;
+    d.expA = d.expB = exps;
+    d.form = 1;
+    d.bk = 64;
+    d.variant = 0;
+    d.wait_limit_ns = (uint64_t)limit_ms * 1000000ull;
+    d.selftest_no_loads = 1;
+    cudaError_t e = launch_gemm_tc(d, 1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return report(TN_ERR_CUDA, "self-test launch failed");
+    return tc_status_read_and_clear() & 1u ? report(TN_ERR_TIMEOUT, "bounded wait ran out")
+                                           : TN_OK;
 }
 
 unsigned int tc_status_read_and_clear() {

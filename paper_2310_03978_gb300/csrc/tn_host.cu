@@ -187,6 +187,10 @@ int route(const Step &s, tn_precision mode, bool tc_ok) {
     const bool tc_mode = mode == TN_PREC_FP16_SCALED || mode == TN_PREC_BF16_SCALED ||
                          mode == TN_PREC_MIXED;
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 6) return K_TC;
+    // large outputs of short contractions (8 <= k < 64) also go to the tensor cores: the short-K
+    // variant's tensor map zero-fills the K tile past k, and its epilogue writes 2 CTAs per SM
+    if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 3 && lm + ln >= 20)
+        return K_TC;
     // register-tiled GEMM (split along K when the output is small); a contraction of fewer than
     // 16 elements is cheaper as an element-wise pass with coalesced stores
     if (s.batch.empty() && lk >= 2 && lm >= 3 && ln >= 3 && lm + ln + lk >= 14) return K_GEMM;
@@ -1195,6 +1199,11 @@ tn_status tn_contract_host(tn_plan_t *p, int64_t slice_begin, int64_t slice_end,
     if (!p->planars.empty() && tn::tc_status_read_and_clear() != 0)
         return fail(TN_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait");
     return TN_OK;
+}
+
+tn_status tn_selftest_wait_timeout(int32_t limit_ms, void *stream) {
+    g_err.clear();
+    return tn::tc_selftest_wait_timeout(limit_ms, (cudaStream_t)stream);
 }
 
 tn_status tn_readout(const tn_plan_t *p, const void *amps_dev, int32_t n_qubits, double out[4],

@@ -157,8 +157,10 @@ struct TcGemmDesc {
     unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
     int32_t planar_out;        // 1: write C as PlanarOut `pout` instead of complex64
     PlanarOut pout;
-    int8_t tb_src[16];         // the 14 bits of a 128 x 128 tile sorted by position in C:
-    int8_t tb_pos[16];         //   (is_row << 7) | bit index, and its position in C
+    uint64_t wait_limit_ns;    // bound of every mbarrier wait (0 = 4 s)
+    int32_t selftest_no_loads; // self-test of the bounded waits: the producer issues no loads
+    int8_t tb_src[16];         // the 13 bits of a 128 x 64 epilogue chunk sorted by position in
+    int8_t tb_pos[16];         //   C: (is_row << 7) | bit index, and its position in C
     int8_t posC_m[TN_MAXR];
     int8_t posC_n[TN_MAXR];
 };
@@ -168,6 +170,8 @@ cudaError_t tc_prepare();
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st);
 // Device status word of the tensor-core kernel (bit 0: a bounded wait timed out); cleared.
 unsigned int tc_status_read_and_clear();
+// Self-test of the bounded waits (see tn_selftest_wait_timeout in tn.h).
+tn_status tc_selftest_wait_timeout(int32_t limit_ms, cudaStream_t st);
 // Encode a 3-D tensor map over planar 16-bit data [planes*slices][rows][K] (K contiguous),
 // box {bk, 128, 1} with the 128-byte (bk 64) or 64-byte (bk 32) swizzle.
 int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,

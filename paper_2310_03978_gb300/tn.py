@@ -26,7 +26,8 @@ KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc"}
 # Every symbol declared in include/tn.h.
 EXPORTS = ("tn_network_load", "tn_network_set_data", "tn_plan", "tn_plan_get_info",
            "tn_plan_get_step_info", "tn_contract", "tn_contract_host", "tn_readout",
-           "tn_readout_noalloc", "tn_destroy", "tn_status_string", "tn_last_error_detail")
+           "tn_readout_noalloc", "tn_selftest_wait_timeout", "tn_destroy", "tn_status_string",
+           "tn_last_error_detail")
 
 
 class PlanOptions(C.Structure):
@@ -84,6 +85,7 @@ def lib():
         L.tn_contract_host.argtypes = [vp, i64, i64, vp, vp]
         L.tn_readout.argtypes = [vp, vp, i32, vp, vp]
         L.tn_readout_noalloc.argtypes = [vp, i64, i32, vp, vp]
+        L.tn_selftest_wait_timeout.argtypes = [i32, vp]
         L.tn_destroy.argtypes = [vp]
         L.tn_destroy.restype = None
         L.tn_status_string.argtypes = [C.c_int]

@@ -194,6 +194,30 @@ def test_single_step_tensor_core(tn, mode, shape, form, bk, bn):
     check(got, ref, TOL[mode])
 
 
+@pytest.mark.parametrize("shape", [(10, 10, 3), (11, 9, 4), (7, 13, 5)])
+def test_short_contraction_on_tensor_cores(tn, shape):
+    # k = 8..32 with a large output: the K tile is zero-filled past k by the tensor map
+    rng = np.random.default_rng(70 + sum(shape))
+    tensors, labels, out = single_step(rng, *shape)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    for mode in ("fp16_scaled", "bf16_scaled"):
+        got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode=mode)
+        assert kernels == ["gemm_tc"]
+        check(got, ref, TOL[mode])
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(tn):
+    # a tensor-core CTA whose producer issues no copies: its MMA warp's wait runs out after
+    # 200 ms, the kernel records the timeout and exits; the context stays usable
+    status = tn.lib().tn_selftest_wait_timeout(200, None)
+    assert status == 6  # TN_ERR_TIMEOUT
+    wl = W.small_workload()
+    net = wl.network
+    got, _, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path,
+                         mode="fp16_scaled")
+    check(got, O.contract_network(net, wl.path), TOL["fp16_scaled"])
+
+
 def test_tensor_core_scaling_keeps_tiny_magnitudes(tn):
     # amplitude-like magnitudes (2^-40) would flush to zero in FP16 without the 2^e scaling
     rng = np.random.default_rng(3)
