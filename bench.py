@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--tc-bk", type=int, default=0, choices=[0, 32, 64])
     ap.add_argument("--tc-bn", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--c64-steps", type=int, default=2)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: each rank contracts its own amplitude batch; strong: the ranks "
+                         "split one batch's slices and sum-reduce the amplitudes (FP64)")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: time the headline steps as CUDA-graph replays and measure the "
                          "dominant kernel in a separate profiled pass of the same steps")
@@ -68,17 +71,6 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------------- workload
-def rank_network(wl, rank):
-    """The bench circuit with rank-specific seeded closed bits (same structure and path)."""
-    from paper_2310_03978_gb300 import workload as W
-    if rank == 0:
-        return wl.network
-    net = wl.network
-    rng = W.Xoshiro256ss(W.BASE_SEED + 1 + 7919 * rank)
-    closed = {q: rng.below(2) for q in net.closed_bits}
-    return W.build_network(wl.circuit, net.open_qubits, closed)
-
-
 def dominant_step(wl):
     from paper_2310_03978_gb300 import workload as W
     steps = W.replay_path(wl.network.labels, wl.network.open_labels, wl.path, wl.sliced)
@@ -203,15 +195,19 @@ def read_golden():
     return rows[:, 0] + 1j * rows[:, 1]
 
 
-def time_contract(torch, plan, amps, steps, stream):
+def time_steps(torch, step, steps, stream):
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for _ in range(steps):
-        plan.contract(amps, stream=stream)
+        step()
     end.record(stream)
     end.synchronize()
     return start.elapsed_time(end)
+
+
+def time_contract(torch, plan, amps, steps, stream):
+    return time_steps(torch, lambda: plan.contract(amps, stream=stream), steps, stream)
 
 
 def kernel_roofline(plan, step_index, before, slices_per_launch, tcc, peak, bound, unit,
@@ -233,13 +229,15 @@ def kernel_roofline(plan, step_index, before, slices_per_launch, tcc, peak, boun
 def run_ours(args, rank, world, local_rank):
     import torch
     from oracle import oracle as O
-    from paper_2310_03978_gb300 import tn, workload as W
+    from paper_2310_03978_gb300 import shard, tn, workload as W
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     wl = W.bench_workload()
-    net_w = rank_network(wl, rank)
+    strong = args.scaling == "strong"
+    net_w = wl.network if strong else shard.rank_network(wl, rank)
+    s_begin, s_end = shard.slice_range(wl.num_slices, rank, world) if strong else (0, None)
     n_open = len(net_w.open_labels)
     pk = peaks()
 
@@ -248,11 +246,14 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(x, device=dev)
+
+    def contract(plan, amps):
+        # one step: this rank's slices (all of its own batch, or its range of the shared
+        # batch followed by the FP64 sum-reduce of the amplitudes)
+        plan.contract(amps, s_begin, s_end, stream=stream)
+        if strong:
+            shard.reduce_amplitudes(amps)
 
     net = tn.Network.from_workload(net_w)
 
@@ -263,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
             gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True)
             amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
             for _ in range(warmup):
-                gplan.contract(amps, stream=stream)
+                contract(gplan, amps)
             torch.cuda.synchronize()
             launches0 = gplan.info()["kernel_launches"]
             sampler = ClockSampler(local_rank) if clocks else None
@@ -272,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
                 time.sleep(0.5)
             barrier()
             torch.cuda.synchronize()
-            gms = time_contract(torch, gplan, amps, steps, stream)
+            gms = time_steps(torch, lambda: contract(gplan, amps), steps, stream)
             torch.cuda.synchronize()
             barrier()
             gclk = sampler.stop() if sampler else None
@@ -290,11 +291,11 @@ def run_ours(args, rank, world, local_rank):
         info = plan.info()
         amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
         # correctness pass (not timed)
-        plan.contract(amps, stream=stream)
+        contract(plan, amps)
         torch.cuda.synchronize()
         result = amps.cpu().numpy().copy()
         for _ in range(warmup):
-            plan.contract(amps, stream=stream)
+            contract(plan, amps)
         torch.cuda.synchronize()
         kinds = [plan.step_info(i) for i in range(info["num_steps"])]
         dom = max((i for i in range(len(kinds)) if kinds[i]["kernel_name"] in
@@ -307,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
             time.sleep(0.5)
         barrier()
         torch.cuda.synchronize()
-        ms = time_contract(torch, plan, amps, steps, stream)
+        ms = time_steps(torch, lambda: contract(plan, amps), steps, stream)
         torch.cuda.synchronize()
         barrier()
         clk = sampler.stop() if sampler else None
@@ -334,13 +335,19 @@ def run_ours(args, rank, world, local_rank):
     # contract into a host array (D2H), every step
     plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode)
     host_out = np.zeros(1 << n_open, dtype=np.complex128)
-    plan.contract_host(out=host_out)
+    plan.contract_host(s_begin, s_end, out=host_out)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         net.set_data(net_w.tensors)
-        plan.contract_host(out=host_out, stream=stream)
+        plan.contract_host(s_begin, s_end, out=host_out, stream=stream)
+        if strong:
+            red = torch.from_numpy(host_out)
+            if world > 1:
+                red = red.to(dev)
+                shard.reduce_amplitudes(red)
+                host_out[:] = red.cpu().numpy()
     e2e_s = max_over_ranks(time.perf_counter() - t0) / args.e2e_steps
     plan.close()
 
@@ -357,7 +364,8 @@ def run_ours(args, rank, world, local_rank):
                          "xeb_ideal_rel_err": abs(x_got - x_ref) / abs(x_ref)}
     if rank != 0:
         return
-    tflops = world * head["flops"] / (head["ms"] / 1e3) / 1e12
+    batches = 1 if strong else world
+    tflops = batches * head["flops"] / (head["ms"] / 1e3) / 1e12
     line = {
         "metric": METRIC,
         "value": tflops,
@@ -368,7 +376,7 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": head["ms"],
         "s_per_batch": head["ms"] / 1e3,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": args.scaling,
         "vs_baseline": None,
         "dtype": {"fp16_scaled": "f16", "bf16_scaled": "bf16", "c64": "f32"}.get(args.mode,
                                                                                   args.mode),
@@ -384,13 +392,13 @@ def run_ours(args, rank, world, local_rank):
         "roofline": head["roofline"],
         "gpu_launches": head["launches"],
         "clocks": head["clocks"],
-        "e2e": {"value": world * head["flops"] / e2e_s / 1e12, "unit": "TFLOPS",
+        "e2e": {"value": batches * head["flops"] / e2e_s / 1e12, "unit": "TFLOPS",
                 "s_per_batch": e2e_s, "h2d_bytes_per_step": net.data_bytes,
                 "d2h_bytes_per_step": (1 << n_open) * 16},
         "accuracy": acc,
     }
     if c64 is not None:
-        line["c64"] = {"value": world * c64["flops"] / (c64["ms"] / 1e3) / 1e12,
+        line["c64"] = {"value": batches * c64["flops"] / (c64["ms"] / 1e3) / 1e12,
                        "unit": "TFLOPS", "ms_per_step": c64["ms"], "steps": c64["steps"],
                        "roofline": c64["roofline"]}
         line["mixed_over_c64"] = c64["ms"] / head["ms"]
