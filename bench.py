@@ -261,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
         if graph:
             # headline: graph replays, no per-kernel events; the roofline comes from a profiled
             # pass of the same number of steps right after
-            gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True)
+            gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True, autotune=True)
             amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
             for _ in range(warmup):
                 contract(gplan, amps)
@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
             res["launches"] = glaunch
             res["graph"] = True
             return res
-        plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True)
+        plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True, autotune=True)
         info = plan.info()
         amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
         # correctness pass (not timed)
@@ -298,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
             contract(plan, amps)
         torch.cuda.synchronize()
         kinds = [plan.step_info(i) for i in range(info["num_steps"])]
+        variants = {i: k["tc_variant"] for i, k in enumerate(kinds) if k["tc_variant"] >= 0}
         dom = max((i for i in range(len(kinds)) if kinds[i]["kernel_name"] in
                    ("gemm_tc", "gemm_simt")), key=lambda i: kinds[i]["tcc"])
         before = plan.step_info(dom)
@@ -326,7 +327,7 @@ def run_ours(args, rank, world, local_rank):
         plan.close()
         return {"ms": ms / steps, "flops": flops, "info": info, "result": result,
                 "roofline": roof, "launches": launches // steps, "clocks": clk, "steps": steps,
-                "graph": False}
+                "graph": False, "variants": variants}
 
     head = measure(args.mode, args.steps, args.warmup, clocks=True, graph=bool(args.graph))
     c64 = measure("c64", args.c64_steps, 1) if args.c64_steps > 0 else None
@@ -388,6 +389,7 @@ def run_ours(args, rank, world, local_rank):
                    "flops_per_batch": head["flops"],
                    "l2": "inputs larger than L2 (largest intermediate 2^28 x 8 B per slice)",
                    "cuda_graph": head["graph"],
+                   "tc_variants_by_step": head.get("variants"),
                    "ms_per_step_without_graph": head.get("ms_profiled")},
         "roofline": head["roofline"],
         "gpu_launches": head["launches"],

@@ -78,7 +78,10 @@ typedef struct {
                                       synchronised)                                           */
     int32_t tc_bk;                 /* tensor-core K tile preference: 0 = automatic, 32 or 64  */
     int32_t tc_bn;                 /* tensor-core N tile preference: 0 = automatic, 128, 256  */
-    int32_t reserved[6];
+    int32_t autotune;              /* 1 = during the first full batch, time every applicable
+                                      tensor-core kernel variant (tile shape, 4M / 3M) per step
+                                      and keep the fastest                                    */
+    int32_t reserved[5];
 } tn_plan_options;
 
 typedef struct {
@@ -112,6 +115,8 @@ typedef struct {
     int64_t launches;              /* profile mode: launches timed                           */
     double prep_ms;                /* profile mode: time of its operand conversions (tensor-
                                       core steps: amax + planar 16-bit copies)               */
+    int32_t tc_variant;            /* tensor-core kernel variant in use (-1 otherwise)       */
+    int32_t reserved2;
 } tn_step_info;
 
 /*

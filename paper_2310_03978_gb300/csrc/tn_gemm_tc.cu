@@ -546,6 +546,26 @@ int tc_variant_bn(int variant) {
 // Variant choice (measured on GB300): short contractions (K <= 512) are epilogue-bound and run
 // two CTAs per SM; long ones use the 128 x 256 tile (1.98 PFLOP/s on m=2^13, n=2^14, k=2^14
 // against 1.79 for 128 x 128), or 128 x 128 when N < 256.
+int tc_variant_form(int variant) {
+    switch (variant) {
+#define TN_TC_FORM(id, npl, bk, bn, stg, minb) \
+    case id: return npl == 3 ? 2 : 1;
+        TN_TC_VARIANTS(TN_TC_FORM)
+#undef TN_TC_FORM
+    }
+    return 0;
+}
+
+int tc_num_variants() { return 6; }
+
+bool tc_variant_fits(int variant, int lk, int ln) {
+    const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
+    if (bk == 0) return false;
+    if (bk == 64 && lk < 6) return false;
+    if (lk < 3) return false;
+    return ln >= (bn == 256 ? 8 : 7);
+}
+
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref) {
     if (form == 2) return bk_pref == 64 ? 4 : 3;
     if (bn_pref == 256 && ln >= 8) return 1;

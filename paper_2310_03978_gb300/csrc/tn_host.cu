@@ -92,7 +92,8 @@ struct Tensor {
 
 struct Planar {              // planar 16-bit copy of a tensor feeding a tensor-core step
     int tensor = -1;
-    int planes = 2;          // re, im (4M) or re, im, re + im (3M)
+    int planes = 2;          // planes written: re, im (4M) or re, im, re + im (3M)
+    int cap_planes = 2;      // planes allocated (3 while the autotuner may still pick 3M)
     bool direct = false;     // written by its producer's epilogue (no conversion pass)
     int64_t off = -1;        // byte offset in the arena
     int64_t bytes_per_slice = 0;
@@ -112,6 +113,8 @@ struct Step {
     int pa = -1, pb = -1;        // planar copies for K_TC
     int form = TN_GEMM_4M;
     int splits = 1;              // K_GEMM split-K factor
+    bool tune_form = false;      // autotune: 3M is still a candidate for this K_TC step
+    int variant = -1;            // K_TC kernel variant
     int out_meta = -1;           // meta block whose per-slice max-abs this step's epilogue records
     int direct_planar = -1;      // planar copy this step writes directly instead of complex64
     int64_t part_off = -1;       // K_GEMM split-K partials (byte offset in the arena)
@@ -158,6 +161,7 @@ struct tn_plan {
     std::vector<tn::TcGemmDesc> tc_desc;  // per step (only K_TC entries used)
     int64_t launches = 0;                 // kernels launched by this plan
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
+    bool tuned = false;                   // autotune done (first full batch)
     // CUDA graph of the slice-dependent steps of one full batch (use_graph)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -552,6 +556,7 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         // slice-independent steps run once per call; they stay on the CUDA cores
         if (!st.dep && st.kernel == K_TC) st.kernel = K_GEMM;
         st.form = (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
+        st.tune_form = p->opts.autotune && p->opts.gemm_form == TN_GEMM_AUTO && st.kernel == K_TC;
     }
 
     // 3. layout: root first, then every step's operands from its result's order
@@ -600,7 +605,9 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
             Planar q;
             q.tensor = side ? st.b : st.a;
             q.planes = st.form == TN_GEMM_3M ? 3 : 2;
-            q.bytes_per_slice = (int64_t)(2 * q.planes) << p->tensors[q.tensor].rank();
+            if (st.tune_form) q.planes = 3;  // the tuner may pick 3M for this step
+            q.cap_planes = q.planes;
+            q.bytes_per_slice = (int64_t)(2 * q.cap_planes) << p->tensors[q.tensor].rank();
             const Tensor &X = p->tensors[q.tensor];
             if (X.producer >= 0) {
                 // a CUDA-core producer writes directly only with whole 64 x 64 tiles, and then
@@ -772,6 +779,57 @@ void fill_planar_out(const tn_plan_t *p, const Step &st, tn::PlanarOut &o) {
     o.log2_k = (int)st.K.size();
 }
 
+// Descriptor of tensor-core step st with kernel variant `variant` (tile shape and form).
+tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGemmDesc &d) {
+    memset(&d, 0, sizeof d);
+    const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
+    const int bf = p->mode == TN_PREC_BF16_SCALED;
+    const int64_t Kx = (int64_t)1 << st.K.size();
+    const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
+    const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
+    d.variant = variant;
+    d.bk = tn::tc_variant_bk(variant);
+    d.form = tn::tc_variant_form(variant);
+    if (d.form == 2 && (qa.planes < 3 || qb.planes < 3))
+        return fail(TN_ERR_UNSUPPORTED, "3M needs the operands' sum planes");
+    const int bn = tn::tc_variant_bn(variant);
+    if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx, (int64_t)1 << st.M.size(),
+                                 qa.cap_planes * sa, bf, d.bk, 128) != 0 ||
+        tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx, (int64_t)1 << st.N.size(),
+                                 qb.cap_planes * sbb, bf, d.bk, bn) != 0)
+        return fail(TN_ERR_CUDA, "cuTensorMapEncodeTiled failed for step %d",
+                    (int)(&st - &p->steps[0]));
+    d.C = reinterpret_cast<float2 *>(p->arena) + C.off;
+    d.sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
+    d.lm = (int)st.M.size();
+    d.ln = (int)st.N.size();
+    d.lk = (int)st.K.size();
+    d.a_sliced = A.dep ? 1 : 0;
+    d.b_sliced = B.dep ? 1 : 0;
+    d.slices_a = sa;
+    d.slices_b = sbb;
+    d.expA = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qa.meta + p->sb);
+    d.expB = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qb.meta + p->sb);
+    d.bf16 = bf;
+    d.amax_out = st.out_meta >= 0 ? p->meta + 2 * p->sb * st.out_meta : nullptr;
+    if (st.direct_planar >= 0) {
+        d.planar_out = 1;
+        fill_planar_out(p, st, d.pout);
+    }
+    fill_pos(d.posC_m, TN_MAXR, -1);
+    fill_pos(d.posC_n, TN_MAXR, -1);
+    for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
+    for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
+    // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C; the first is
+    // always position 0 (the lowest label of C is the lowest of its side), which the
+    // epilogue's pair stores rely on
+    tn::sort_tile_bits(7, 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+    if (d.tb_pos[0] != 0)
+        return fail(TN_ERR_UNSUPPORTED, "step %d: result bit 0 outside the epilogue chunk",
+                    (int)(&st - &p->steps[0]));
+    return TN_OK;
+}
+
 tn_status build_descriptors(tn_plan_t *p) {
     for (auto &t : p->tensors) {
         if (t.leaf < 0) continue;
@@ -808,52 +866,10 @@ tn_status build_descriptors(tn_plan_t *p) {
     p->tc_desc.resize(p->steps.size());
     for (auto &st : p->steps) {
         if (st.kernel != K_TC) continue;
-        tn::TcGemmDesc &d = p->tc_desc[&st - &p->steps[0]];
-        memset(&d, 0, sizeof d);
-        const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
-        const int bf = p->mode == TN_PREC_BF16_SCALED;
-        const int64_t Kx = (int64_t)1 << st.K.size();
-        const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
-        const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
-        d.variant = tn::tc_pick_variant(st.form == TN_GEMM_3M ? 2 : 1, (int)st.K.size(),
-                                        (int)st.N.size(), p->opts.tc_bk, p->opts.tc_bn);
-        d.bk = tn::tc_variant_bk(d.variant);
-        const int bn = tn::tc_variant_bn(d.variant);
-        if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx, (int64_t)1 << st.M.size(),
-                                     qa.planes * sa, bf, d.bk, 128) != 0 ||
-            tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx, (int64_t)1 << st.N.size(),
-                                     qb.planes * sbb, bf, d.bk, bn) != 0)
-            return fail(TN_ERR_CUDA, "cuTensorMapEncodeTiled failed for step %d",
-                        (int)(&st - &p->steps[0]));
-        d.C = reinterpret_cast<float2 *>(p->arena) + C.off;
-        d.sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
-        d.lm = (int)st.M.size();
-        d.ln = (int)st.N.size();
-        d.lk = (int)st.K.size();
-        d.a_sliced = A.dep ? 1 : 0;
-        d.b_sliced = B.dep ? 1 : 0;
-        d.slices_a = sa;
-        d.slices_b = sbb;
-        d.expA = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qa.meta + p->sb);
-        d.expB = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qb.meta + p->sb);
-        d.form = st.form;
-        d.bf16 = bf;
-        d.amax_out = st.out_meta >= 0 ? p->meta + 2 * p->sb * st.out_meta : nullptr;
-        if (st.direct_planar >= 0) {
-            d.planar_out = 1;
-            fill_planar_out(p, st, d.pout);
-        }
-        fill_pos(d.posC_m, TN_MAXR, -1);
-        fill_pos(d.posC_n, TN_MAXR, -1);
-        for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
-        for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
-        // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C; the first is
-        // always position 0 (the lowest label of C is the lowest of its side), which the
-        // epilogue's pair stores rely on
-        tn::sort_tile_bits(7, 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
-        if (d.tb_pos[0] != 0)
-            return fail(TN_ERR_UNSUPPORTED, "step %d: result bit 0 outside the epilogue chunk",
-                        (int)(&st - &p->steps[0]));
+        st.variant = tn::tc_pick_variant(st.form == TN_GEMM_3M ? 2 : 1, (int)st.K.size(),
+                                         (int)st.N.size(), p->opts.tc_bk, p->opts.tc_bn);
+        tn_status s = make_tc_desc(p, st, st.variant, p->tc_desc[&st - &p->steps[0]]);
+        if (s != TN_OK) return s;
     }
     return TN_OK;
 }
@@ -871,6 +887,74 @@ tn_status take_events(tn_plan_t *p, EventPair &ev) {
     }
     TN_CUDA(cudaEventCreate(&ev.first));
     TN_CUDA(cudaEventCreate(&ev.second));
+    return TN_OK;
+}
+
+tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGemmDesc &d);
+
+// Autotune a tensor-core step (first full batch): run it once as planned, then launch every
+// applicable kernel variant (tile shape, K tile, 4M or 3M) between CUDA events and keep the
+// fastest.  All variants compute the same result; when 4M wins, the operands' sum planes are
+// no longer written.
+tn_status tune_tc_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stream) {
+    const int si = (int)(&st - &p->steps[0]);
+    tn_status s = run_step_inner(p, st, slices, stream, nullptr, nullptr);
+    if (s != TN_OK) return s;
+    const int lk = (int)st.K.size(), ln = (int)st.N.size();
+    const bool three_planes = p->planars[st.pa].planes == 3 && p->planars[st.pb].planes == 3;
+    std::vector<int> cands;
+    std::vector<tn::TcGemmDesc> descs;
+    std::vector<EventPair> evs;
+    for (int v = 0; v < tn::tc_num_variants(); ++v) {
+        if (!tn::tc_variant_fits(v, lk, ln)) continue;
+        const int form = tn::tc_variant_form(v);
+        if (form == 2 && !three_planes) continue;
+        if (p->opts.gemm_form == TN_GEMM_4M && form != 1) continue;
+        if (p->opts.gemm_form == TN_GEMM_3M && form != 2) continue;
+        tn::TcGemmDesc d;
+        s = make_tc_desc(p, st, v, d);
+        if (s != TN_OK) return s;
+        EventPair ev;
+        TN_CUDA(cudaEventCreate(&ev.first));
+        TN_CUDA(cudaEventCreate(&ev.second));
+        cands.push_back(v);
+        descs.push_back(d);
+        evs.push_back(ev);
+    }
+    for (size_t i = 0; i < cands.size(); ++i) {
+        TN_CUDA(cudaEventRecord(evs[i].first, stream));
+        TN_CUDA(tn::launch_gemm_tc(descs[i], slices, stream));
+        TN_CUDA(cudaEventRecord(evs[i].second, stream));
+        p->launches += 1;
+    }
+    TN_CUDA(cudaStreamSynchronize(stream));
+    int best = -1;
+    float best_ms = 0.f;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        float ms = 0.f;
+        TN_CUDA(cudaEventElapsedTime(&ms, evs[i].first, evs[i].second));
+        if (best < 0 || ms < best_ms) {
+            best = (int)i;
+            best_ms = ms;
+        }
+        cudaEventDestroy(evs[i].first);
+        cudaEventDestroy(evs[i].second);
+    }
+    if (best < 0) return TN_OK;
+    st.variant = cands[best];
+    st.form = tn::tc_variant_form(st.variant) == 2 ? TN_GEMM_3M : TN_GEMM_4M;
+    p->tc_desc[si] = descs[best];
+    if (st.form == TN_GEMM_4M && st.tune_form) {
+        // the sum planes are not read: their producers stop writing them
+        for (int side = 0; side < 2; ++side) {
+            Planar &q = p->planars[side ? st.pb : st.pa];
+            q.planes = 2;
+            const Tensor &X = p->tensors[q.tensor];
+            if (q.direct && p->steps[X.producer].kernel == K_TC)
+                p->tc_desc[X.producer].pout.planes = 2;
+        }
+    }
+    st.tune_form = false;
     return TN_OK;
 }
 
@@ -1077,6 +1161,7 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
     out->log2_b = (int)st.lb.size();
     out->log2_c = (int)st.lc.size();
     out->gemm_form = st.kernel == K_TC ? st.form : 0;
+    out->tc_variant = st.kernel == K_TC ? st.variant : -1;
     out->tcc = st.tcc;
     Step &ms = const_cast<Step &>(st);
     tn_plan_t *mp = const_cast<tn_plan_t *>(p);
@@ -1139,6 +1224,20 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
         TN_CUDA(tn::launch_bind(p->bind_sl_dev, (int32_t)p->bind_sl.size(), src, arena, s0, ns,
                                 p->max_rank_sl, stream));
         if (!p->bind_sl.empty()) p->launches++;
+        if (p->opts.autotune && !p->tuned && ns == p->sb) {
+            // first full batch: tune the tensor-core steps while running it
+            for (auto &st : p->steps)
+                if (st.dep) {
+                    tn_status s = st.kernel == K_TC ? tune_tc_step(p, st, ns, stream)
+                                                    : run_step(p, st, ns, stream);
+                    if (s != TN_OK) return s;
+                }
+            p->tuned = true;
+            TN_CUDA(tn::launch_accumulate(arena + R.off, R.dep ? nout : 0, nout, R.dep ? ns : 1,
+                                          reinterpret_cast<double2 *>(amps_dev), stream));
+            p->launches++;
+            continue;
+        }
         const bool graph = p->opts.use_graph && !p->opts.profile && ns == p->sb;
         if (graph && !p->graph_exec) {
             // capture the dependent steps once, on a plan-owned stream

@@ -181,5 +181,8 @@ int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t r
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref);
 int tc_variant_bk(int variant);
 int tc_variant_bn(int variant);
+int tc_variant_form(int variant);  // 1 = 4M, 2 = 3M
+int tc_num_variants();
+bool tc_variant_fits(int variant, int lk, int ln);
 
 }  // namespace tn

@@ -35,7 +35,7 @@ class PlanOptions(C.Structure):
                 ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
                 ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
                 ("profile", C.c_int32), ("tc_bk", C.c_int32), ("tc_bn", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("autotune", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class PlanInfo(C.Structure):
@@ -54,7 +54,8 @@ class StepInfo(C.Structure):
                 ("log2_n", C.c_int32), ("log2_k", C.c_int32), ("log2_batch", C.c_int32),
                 ("log2_a", C.c_int32), ("log2_b", C.c_int32), ("log2_c", C.c_int32),
                 ("gemm_form", C.c_int32), ("tcc", C.c_double), ("time_ms", C.c_double),
-                ("launches", C.c_int64), ("prep_ms", C.c_double)]
+                ("launches", C.c_int64), ("prep_ms", C.c_double), ("tc_variant", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 class TnError(RuntimeError):
@@ -170,7 +171,7 @@ class Plan:
 
     def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
                  workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
-                 profile=False, use_graph=False, tc_bk=0, tc_bn=0):
+                 profile=False, use_graph=False, tc_bk=0, tc_bn=0, autotune=False):
         self.network = network
         opts = PlanOptions()
         opts.max_slices_in_flight = int(max_slices_in_flight)
@@ -185,6 +186,7 @@ class Plan:
         opts.use_graph = 1 if use_graph else 0
         opts.tc_bk = int(tc_bk)
         opts.tc_bn = int(tc_bn)
+        opts.autotune = 1 if autotune else 0
         pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
         sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
         h = C.c_void_p()
@@ -202,7 +204,7 @@ class Plan:
     def step_info(self, step: int) -> dict:
         s = StepInfo()
         _check(lib().tn_plan_get_step_info(self.handle, int(step), C.byref(s)))
-        d = {f: getattr(s, f) for f, _ in StepInfo._fields_ if f != "reserved"}
+        d = {f: getattr(s, f) for f, _ in StepInfo._fields_ if not f.startswith("reserved")}
         d["kernel_name"] = KERNELS.get(d["kernel"], "?")
         return d
 

@@ -286,6 +286,32 @@ def test_chained_steps_feed_the_tensor_cores(tn, lk1, first, mode):
         check(got, ref, TOL[mode])
 
 
+@pytest.mark.parametrize("form", ["auto", "4m", "3m"])
+def test_autotuned_plan_matches_oracle(tn, form):
+    # the first full batch times every applicable tensor-core variant per step; results before
+    # and after tuning agree with the oracle
+    rng = np.random.default_rng(90)
+    a, k1, b, c = (list(range(o, o + w)) for o, w in ((0, 9), (100, 7), (200, 8), (300, 8)))
+    tensors = [crandn(rng, 16, 2.0 ** -6), crandn(rng, 15, 2.0 ** -6), crandn(rng, 16)]
+    labels = [a + k1, k1 + b, b + c]
+    out = [int(x) for x in rng.permutation(a + c)]
+    path = [(0, 1), (0, 2)]
+    ref = O.contract(tensors, labels, out, path)
+    net = tn.Network(tensors, labels, out)
+    plan = tn.Plan(net, path, (), mode="fp16_scaled", gemm_form=form, autotune=True)
+    for _ in range(3):
+        check(plan.contract_host(), ref, TOL["fp16_scaled"])
+    variants = [plan.step_info(i)["tc_variant"] for i in range(2)]
+    assert all(v >= 0 for v in variants)
+    forms = [plan.step_info(i)["gemm_form"] for i in range(2)]
+    if form == "4m":
+        assert forms == [1, 1]
+    if form == "3m":
+        assert forms == [2, 2]
+    plan.close()
+    net.close()
+
+
 def test_host_entry_points_and_set_data(tn):
     wl = W.small_workload()
     net = wl.network
@@ -314,7 +340,8 @@ def test_bench_circuit_full_size(tn, mode, form):
     net = wl.network
     ref = read_golden("sycamore_5x6_c14_open10_s4")
     got, info, kernels = gpu_amps(tn, net.tensors, net.labels, net.open_labels, wl.path,
-                                  wl.sliced, mode=mode, gemm_form=form)
+                                  wl.sliced, mode=mode, gemm_form=form,
+                                  autotune=mode != "c64")
     assert info["num_slices"] == 16 and info["max_log2_size"] <= 28
     check(got, ref, TOL[mode])
     n = wl.circuit.n_qubits
