@@ -51,9 +51,11 @@ typedef enum {
     TN_PREC_SPLIT_TF32 = 2,   /* reserved: 3xTF32 (Eq. 3xTF32)                               */
     TN_PREC_FP16_SCALED = 3,  /* dense steps: FP16 tensor cores, per-tensor 2^e scaling     */
     TN_PREC_BF16_SCALED = 4,  /* dense steps: BF16 tensor cores, per-tensor 2^e scaling     */
-    TN_PREC_SPLIT_BF16 = 5,   /* reserved: 3xBF16 (Sec. 4.2 extension of Eq. 3xTF32)         */
-    TN_PREC_SPLIT_FP16 = 6,   /* reserved: 3xFP16                                            */
-    TN_PREC_MIXED = 7         /* per-step choice (Sec. 4.3): tensor cores on the dense steps */
+    TN_PREC_SPLIT_BF16 = 5,   /* dense steps: compensated BF16 products (3xBF16, Sec. 4.2)   */
+    TN_PREC_SPLIT_FP16 = 6,   /* dense steps: compensated FP16 products (3xFP16, Sec. 4.2):
+                                 x = hi + lo, xy ~ hi hi + hi lo + lo hi, near-FP32 accuracy  */
+    TN_PREC_MIXED = 7         /* Sec. 4.3: the mixed_topk largest-T_cc dense steps single-pass
+                                 FP16, the other dense steps compensated FP16                */
 } tn_precision;
 
 /* Complex GEMM form for the tensor-core steps: 4M = four real products, 3M = three. */
@@ -81,7 +83,10 @@ typedef struct {
     int32_t autotune;              /* 1 = during the first full batch, time every applicable
                                       tensor-core kernel variant (tile shape, 4M / 3M) per step
                                       and keep the fastest                                    */
-    int32_t reserved[5];
+    int32_t mixed_topk;            /* TN_PREC_MIXED: how many tensor-core steps, largest T_cc
+                                      first, run single-pass FP16 (0 = 1); the others use
+                                      compensated hi/lo products                             */
+    int32_t reserved[4];
 } tn_plan_options;
 
 typedef struct {
@@ -109,7 +114,7 @@ typedef struct {
     int32_t slice_dependent;       /* 0 = computed once per call and shared by all slices    */
     int32_t log2_m, log2_n, log2_k, log2_batch;  /* GEMM extents of the step (Sec. A.2)    */
     int32_t log2_a, log2_b, log2_c;              /* operand and result sizes               */
-    int32_t gemm_form;             /* tn_gemm_form actually used                              */
+    int32_t gemm_form;             /* 1 = 4M, 2 = 3M, 3 = 4M with compensated hi/lo planes   */
     double tcc;                    /* Eq. T_cc of one slice of this step                     */
     double time_ms;                /* profile mode: summed CUDA-event time of its main kernel */
     int64_t launches;              /* profile mode: launches timed                           */

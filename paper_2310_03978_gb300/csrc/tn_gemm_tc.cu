@@ -34,7 +34,8 @@ constexpr int BM = 128;
 constexpr int CW = 64;       // epilogue column chunk
 constexpr int SLD = CW + 1;  // padded row stride of the epilogue staging tile (float2)
 
-// NPL planes per operand (2: 4M, 3: 3M); a K tile of BKT 16-bit elements per row (64: rows of
+// NPL planes per operand (2: 4M; 3: 3M; 4: split 4M with hi and lo planes); a K tile of BKT
+// 16-bit elements per row (64: rows of
 // 128 bytes with the 128-byte swizzle, 32: rows of 64 bytes with the 64-byte swizzle); an N
 // tile of BNT columns; STG pipeline stages; MINB CTAs per SM.
 template <int NPL, int BKT, int BNT, int STG, int MINB>
@@ -47,7 +48,8 @@ struct Cfg {
     static constexpr int BODY = RING > STAGING ? RING : STAGING;
     static constexpr int BODY_MIN = MINB == 2 ? 80 * 1024 : 0;  // at most 2 CTAs per SM
     static constexpr int SMEM_BYTES = (BODY > BODY_MIN ? BODY : BODY_MIN) + 1024 + 256;
-    static constexpr int ACC = NPL == 2 ? 2 * BNT : 3 * BNT;
+    // accumulators: 4M 2 (re, im), 3M 3, split 4M 2 plus 2 running sums for the promotion
+    static constexpr int ACC = NPL == 3 ? 3 * BNT : (NPL == 4 ? 4 * BNT : 2 * BNT);
     static constexpr int TMEM_COLS = ACC <= 256 ? 256 : 512;
     static constexpr int SBO = 8 * BKT * 2;                 // bytes between 8-row groups
     static constexpr uint64_t LAYOUT = BKT == 64 ? 2 : 4;   // 128-byte / 64-byte swizzle
@@ -165,6 +167,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos) {
     uint64_t r = 0;
     for (int i = 0; i < n; ++i)
@@ -172,10 +187,20 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
     return r;
 }
 
+// Compensated (split) products restart their TMEM accumulator every kPromoteK elements of K and
+// four warps fold each chunk into a running FP32 sum (round to nearest) kept in the other half
+// of tensor memory: the tensor core's own accumulation over a long K loses low-order bits at
+// every step, which shows as an error growing linearly with K and would swamp the ~2^-22
+// accuracy of hi + lo operands.
+constexpr int kPromoteK = 512;
+
 template <int NPL, int BKT, int BNT, int STG, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ TcGemmDesc d,
-                                                       int64_t tiles_n) {
+__global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
+    k_gemm_tc(const __grid_constant__ TcGemmDesc d, int64_t tiles_n) {
     using F = Cfg<NPL, BKT, BNT, STG, MINB>;
+    // split 4M: warps 2..5 fold chunk accumulators into the running sums and write the result
+    constexpr bool PROMOTE = NPL == 4;
+    constexpr int CHUNK_KB = kPromoteK / BKT;
     constexpr int STAGES = STG;
     constexpr int STAGE_BYTES = F::STAGE_BYTES;
     constexpr int TMEM_COLS = F::TMEM_COLS;
@@ -188,7 +213,9 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY);
     uint64_t *empty = full + STAGES;
     uint64_t *done = empty + STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *chunk_full = done + 1;   // MMA -> fold warps: a chunk accumulator is complete
+    uint64_t *chunk_free = done + 2;   // fold warps -> MMA: the chunk accumulator was folded
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 3);
     int *aborted = reinterpret_cast<int *>(tmem_slot + 1);  // set when a wait gave up
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,6 +241,8 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             mbar_init(&empty[i], 1);
         }
         mbar_init(done, 1);
+        mbar_init(chunk_full, 1);
+        mbar_init(chunk_free, 4);
         *aborted = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmA))
@@ -266,6 +295,16 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
         for (int kb = 0; kb < num_kb && ok; ++kb) {
             const int st = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            const int chunk = kb / CHUNK_KB, kc = kb % CHUNK_KB;
+            if (PROMOTE && kc == 0 && chunk > 0) {
+                // the previous chunk must be folded before its accumulator is restarted
+                if (!mbar_wait(chunk_free, (uint32_t)(chunk - 1) & 1u, deadline)) {
+                    ok = false;
+                    *aborted = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
             if (!mbar_wait(&full[st], ph, deadline)) {
                 ok = false;
                 *aborted = 1;
@@ -280,12 +319,29 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes,
                                                                  // inside one swizzled row
-                const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+                const uint32_t first = ((PROMOTE ? kc : kb) > 0 || kk > 0) ? 1u : 0u;
                 if constexpr (NPL == 2) {
                     umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
                     umma_f16(tmem, a_im + adv, b_im + adv, id_neg, 1u);
                     umma_f16(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
                     umma_f16(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                } else if constexpr (NPL == 4) {
+                    // compensated products: x = x_hi + x_lo, xy ~ x_hi y_hi + x_hi y_lo + x_lo y_hi
+                    const uint64_t a_rl = sdesc(base + 2 * TILE_A), a_il = sdesc(base + 3 * TILE_A);
+                    const uint64_t b_rl = sdesc(base + NPL * TILE_A + 2 * TILE_B);
+                    const uint64_t b_il = sdesc(base + NPL * TILE_A + 3 * TILE_B);
+                    umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
+                    umma_f16(tmem, a_im + adv, b_im + adv, id_neg, 1u);
+                    umma_f16(tmem, a_re + adv, b_rl + adv, id_pos, 1u);
+                    umma_f16(tmem, a_im + adv, b_il + adv, id_neg, 1u);
+                    umma_f16(tmem, a_rl + adv, b_re + adv, id_pos, 1u);
+                    umma_f16(tmem, a_il + adv, b_im + adv, id_neg, 1u);
+                    umma_f16(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
+                    umma_f16(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                    umma_f16(tmem + BN, a_re + adv, b_il + adv, id_pos, 1u);
+                    umma_f16(tmem + BN, a_im + adv, b_rl + adv, id_pos, 1u);
+                    umma_f16(tmem + BN, a_rl + adv, b_im + adv, id_pos, 1u);
+                    umma_f16(tmem + BN, a_il + adv, b_re + adv, id_pos, 1u);
                 } else {
                     const uint64_t a_sm = sdesc(base + 2 * TILE_A);
                     const uint64_t b_sm = sdesc(base + NPL * TILE_A + 2 * TILE_B);
@@ -295,8 +351,44 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
                 }
             }
             umma_commit(&empty[st]);
+            if (PROMOTE && (kc == CHUNK_KB - 1 || kb == num_kb - 1)) umma_commit(chunk_full);
         }
         umma_commit(done);
+    } else if (PROMOTE && warp >= 2) {
+        // fold warps: running sum (columns 2BN..4BN) += chunk accumulator (columns 0..2BN)
+        const uint32_t lb = (uint32_t)((warp & 3) * 32) << 16;
+        const int nchunks = (num_kb + CHUNK_KB - 1) / CHUNK_KB;
+        for (int c = 0; c < nchunks; ++c) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(chunk_full, (uint32_t)c & 1u, deadline);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) *aborted = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int col = 0; col < 2 * BN; col += 16) {
+                uint32_t a[16], r[16];
+                tmem_ld16(tmem + lb + (uint32_t)col, a);
+                if (c > 0) {
+                    tmem_ld16(tmem + lb + (uint32_t)(2 * BN + col), r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(a[j]));
+                } else {
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) r[j] = a[j];
+                }
+                tmem_st16(tmem + lb + (uint32_t)(2 * BN + col), r);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(chunk_free);
+        }
     }
     __syncwarp();
 
@@ -330,8 +422,13 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
         uint64_t *hi_off = reinterpret_cast<uint64_t *>(smem + BM * SLD * 8);
         int *hi_w = reinterpret_cast<int *>(hi_off + 64);
         const int e = d.expA[sa] + d.expB[sbi];
-        const int row = warp * 32 + lane;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // epilogue threads: all four warps, or the four fold warps (the running sums) when
+        // promoting; et is the epilogue thread index 0..127
+        const bool epi = !PROMOTE || warp >= 2;
+        const int et = PROMOTE ? (int)threadIdx.x - 64 : (int)threadIdx.x;
+        const int row = (warp & 3) * 32 + lane;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t src = PROMOTE ? 2 * BN : 0;  // accumulator columns to read
         // sorted chunk bit 0 is C's position 0, so each thread writes an adjacent pair: bit 0
         // is the pair, bits 1..7 come from the thread index and bits 8..12 from the iteration
         const int sq0 = d.tb_src[0];
@@ -340,26 +437,26 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
         uint64_t olo = 0;
 #pragma unroll
         for (int q = 1; q < 8; ++q)
-            if ((threadIdx.x >> (q - 1)) & 1) {
+            if ((et >> (q - 1)) & 1) {
                 const int sq = d.tb_src[q];
                 if (sq & 128) mlo |= 1 << (sq & 127);
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
         const int wlo = mlo * SLD + nlo;
-        if (threadIdx.x < 32) {
+        if (epi && et < 32) {
             int mi = 0, ni = 0;
             uint64_t off = 0;
 #pragma unroll
             for (int q = 8; q < 13; ++q)
-                if ((threadIdx.x >> (q - 8)) & 1) {
+                if ((et >> (q - 8)) & 1) {
                     const int sq = d.tb_src[q];
                     if (sq & 128) mi |= 1 << (sq & 127);
                     else ni |= 1 << sq;
                     off |= 1ull << d.tb_pos[q];
                 }
-            hi_off[threadIdx.x] = off;
-            hi_w[threadIdx.x] = mi * SLD + ni;
+            hi_off[et] = off;
+            hi_w[et] = mi * SLD + ni;
         }
         const uint64_t mbase = deposit((uint64_t)m0, d.lm, d.posC_m);
         const int eo = d.planar_out ? planar_out_exponent(d.pout, s) : 0;
@@ -368,11 +465,11 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
 #pragma unroll 1
         for (int cb = 0; cb < BN; cb += CW) {
 #pragma unroll 1
-            for (int c0 = cb; c0 < cb + CW; c0 += 16) {
+            for (int c0 = cb; c0 < cb + CW && epi; c0 += 16) {
                 uint32_t r0[16], r1[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)c0, r0);
-                tmem_ld16(tmem + lane_base + (uint32_t)(BN + c0), r1);
-                if constexpr (NPL == 2) {
+                tmem_ld16(tmem + lane_base + src + (uint32_t)c0, r0);
+                tmem_ld16(tmem + lane_base + src + (uint32_t)(BN + c0), r1);
+                if constexpr (NPL != 3) {
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
@@ -394,7 +491,9 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             }
             __syncthreads();
             const uint64_t cbase = mbase | deposit((uint64_t)(n0 + cb), d.ln, d.posC_n);
-            if (d.planar_out) {
+            if (!epi) {
+                // producer and MMA warps only join the barriers
+            } else if (d.planar_out) {
 #pragma unroll 4
                 for (int it = 0; it < (BM * CW) / 256; ++it) {
                     const int w = wlo + hi_w[it];
@@ -417,7 +516,7 @@ __global__ void __launch_bounds__(128, MINB) k_gemm_tc(const __grid_constant__ T
             }
             __syncthreads();
         }
-        if (d.amax_out) amax_publish(d.amax_out + s, amx);
+        if (d.amax_out && epi) amax_publish(d.amax_out + s, amx);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -490,7 +589,8 @@ namespace {
     X(2, 2, 32, 128, 2, 2) /* 4M, short K: small ring, 2 CTAs per SM */ \
     X(3, 3, 32, 128, 4, 1) /* 3M                                     */ \
     X(4, 3, 64, 128, 2, 1) /* 3M, 128-byte swizzle                   */ \
-    X(5, 2, 32, 128, 6, 1) /* 4M, 64-byte swizzle, 6 stages          */
+    X(5, 2, 32, 128, 6, 1) /* 4M, 64-byte swizzle, 6 stages          */ \
+    X(6, 4, 32, 128, 3, 1) /* split 4M (hi/lo planes), promoted      */
 
 template <int NPL, int BKT, int BNT, int STG, int MINB>
 cudaError_t configure_variant() {
@@ -507,8 +607,8 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
     const int64_t tiles = ((1ll << d.lm) / BM) * tiles_n;
     if (tiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     k_gemm_tc<NPL, BKT, BNT, STG, MINB>
-        <<<dim3((unsigned)tiles, (unsigned)slices), 128, Cfg<NPL, BKT, BNT, STG, MINB>::SMEM_BYTES,
-           st>>>(d, tiles_n);
+        <<<dim3((unsigned)tiles, (unsigned)slices), NPL == 4 ? 192 : 128,
+           Cfg<NPL, BKT, BNT, STG, MINB>::SMEM_BYTES, st>>>(d, tiles_n);
     return cudaGetLastError();
 }
 
@@ -549,14 +649,14 @@ int tc_variant_bn(int variant) {
 int tc_variant_form(int variant) {
     switch (variant) {
 #define TN_TC_FORM(id, npl, bk, bn, stg, minb) \
-    case id: return npl == 3 ? 2 : 1;
+    case id: return npl == 3 ? 2 : (npl == 4 ? 3 : 1);
         TN_TC_VARIANTS(TN_TC_FORM)
 #undef TN_TC_FORM
     }
     return 0;
 }
 
-int tc_num_variants() { return 6; }
+int tc_num_variants() { return 7; }
 
 bool tc_variant_fits(int variant, int lk, int ln) {
     const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
@@ -567,6 +667,7 @@ bool tc_variant_fits(int variant, int lk, int ln) {
 }
 
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref) {
+    if (form == 3) return 6;
     if (form == 2) return bk_pref == 64 ? 4 : 3;
     if (bn_pref == 256 && ln >= 8) return 1;
     if (bk_pref == 32) return lk <= 9 ? 2 : 5;

@@ -73,6 +73,14 @@ namespace {
 
 enum Kernel { K_GENERIC = 0, K_STREAM = 1, K_GEMM = 2, K_TC = 3 };
 
+// Complex form of a tensor-core step: TN_GEMM_4M, TN_GEMM_3M, or 4M with compensated hi/lo
+// operand planes (Sec. 4.2: x = hi + lo, xy ~ hi hi + hi lo + lo hi).
+constexpr int kFormSplit = 3;
+
+bool bf16_mode(tn_precision m) {
+    return m == TN_PREC_BF16_SCALED || m == TN_PREC_SPLIT_BF16;
+}
+
 struct Tensor {
     std::vector<int> order;  // memory order of the labels, most significant first
     bool dep = false;        // depends on the slice id
@@ -189,6 +197,7 @@ tn_status check_plan(const tn_plan_t *p) {
 int route(const Step &s, tn_precision mode, bool tc_ok) {
     const int lm = (int)s.M.size(), ln = (int)s.N.size(), lk = (int)s.K.size();
     const bool tc_mode = mode == TN_PREC_FP16_SCALED || mode == TN_PREC_BF16_SCALED ||
+                         mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 ||
                          mode == TN_PREC_MIXED;
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 6) return K_TC;
     // large outputs of short contractions (8 <= k < 64) also go to the tensor cores: the short-K
@@ -435,8 +444,7 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         return fail(TN_ERR_INVALID_ARG, "bad sliced labels");
     if ((int)mode < 0 || (int)mode > (int)TN_PREC_MIXED)
         return fail(TN_ERR_INVALID_ARG, "bad precision mode");
-    if (mode == TN_PREC_TF32 || mode == TN_PREC_SPLIT_TF32 || mode == TN_PREC_SPLIT_BF16 ||
-        mode == TN_PREC_SPLIT_FP16)
+    if (mode == TN_PREC_TF32 || mode == TN_PREC_SPLIT_TF32)
         return fail(TN_ERR_UNSUPPORTED, "precision mode %d is not implemented", (int)mode);
 
     auto *p = new tn_plan_t();
@@ -555,8 +563,25 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         st.kernel = route(st, mode, p->tc_ok);
         // slice-independent steps run once per call; they stay on the CUDA cores
         if (!st.dep && st.kernel == K_TC) st.kernel = K_GEMM;
-        st.form = (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
-        st.tune_form = p->opts.autotune && p->opts.gemm_form == TN_GEMM_AUTO && st.kernel == K_TC;
+        if (mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 || mode == TN_PREC_MIXED)
+            st.form = kFormSplit;
+        else
+            st.form = (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
+        st.tune_form = p->opts.autotune && p->opts.gemm_form == TN_GEMM_AUTO &&
+                       st.kernel == K_TC && st.form != kFormSplit;
+    }
+
+    if (mode == TN_PREC_MIXED) {
+        // Sec. 4.3: the steps with the largest T_cc run single-pass (FP16), the others with
+        // compensated hi/lo products
+        std::vector<int> tc;
+        for (int s = 0; s < path_len; ++s)
+            if (p->steps[s].kernel == K_TC && p->steps[s].dep) tc.push_back(s);
+        std::stable_sort(tc.begin(), tc.end(), [&](int x, int y) {
+            return p->steps[x].tcc > p->steps[y].tcc;
+        });
+        const int topk = p->opts.mixed_topk > 0 ? p->opts.mixed_topk : 1;
+        for (int i = 0; i < (int)tc.size() && i < topk; ++i) p->steps[tc[i]].form = TN_GEMM_4M;
     }
 
     // 3. layout: root first, then every step's operands from its result's order
@@ -604,14 +629,19 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         for (int side = 0; side < 2; ++side) {
             Planar q;
             q.tensor = side ? st.b : st.a;
-            q.planes = st.form == TN_GEMM_3M ? 3 : 2;
+            q.planes = st.form == TN_GEMM_3M ? 3 : (st.form == kFormSplit ? 4 : 2);
             if (st.tune_form) q.planes = 3;  // the tuner may pick 3M for this step
             q.cap_planes = q.planes;
             q.bytes_per_slice = (int64_t)(2 * q.cap_planes) << p->tensors[q.tensor].rank();
             const Tensor &X = p->tensors[q.tensor];
-            if (X.producer >= 0) {
-                // a CUDA-core producer writes directly only with whole 64 x 64 tiles, and then
-                // never splits K (its epilogue must hold final sums)
+            if (X.producer >= 0 && st.form != kFormSplit) {
+                // A producer's direct output takes its exponent from a bound (2 K max|a| max|b|)
+                // that can exceed the true maximum by many binades, which leaves the stored
+                // values low in FP16's range; single-pass operands keep their 11 significant
+                // bits there, but the lo planes of compensated operands would fall into the
+                // subnormals, so those are split from complex64 with their measured max-abs.
+                // A CUDA-core producer writes directly only with whole 64 x 64 tiles, and then
+                // never splits K (its epilogue must hold final sums).
                 const Step &pr = p->steps[X.producer];
                 q.direct = pr.dep && (pr.kernel == K_TC ||
                                       (pr.kernel == K_GEMM && pr.M.size() >= 6 &&
@@ -770,7 +800,7 @@ void fill_planar_out(const tn_plan_t *p, const Step &st, tn::PlanarOut &o) {
     o.sstride = C.dep ? n : 0;
     o.plane_stride = n * (C.dep ? p->sb : 1);
     o.planes = q.planes;
-    o.bf16 = p->mode == TN_PREC_BF16_SCALED;
+    o.bf16 = bf16_mode(p->mode);
     o.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
     o.amax_a = p->meta + 2 * p->sb * A.meta;
     o.amax_b = p->meta + 2 * p->sb * B.meta;
@@ -783,15 +813,17 @@ void fill_planar_out(const tn_plan_t *p, const Step &st, tn::PlanarOut &o) {
 tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGemmDesc &d) {
     memset(&d, 0, sizeof d);
     const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
-    const int bf = p->mode == TN_PREC_BF16_SCALED;
+    const int bf = bf16_mode(p->mode);
     const int64_t Kx = (int64_t)1 << st.K.size();
     const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
     const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
     d.variant = variant;
     d.bk = tn::tc_variant_bk(variant);
     d.form = tn::tc_variant_form(variant);
-    if (d.form == 2 && (qa.planes < 3 || qb.planes < 3))
+    if (d.form == 2 && (qa.planes != 3 || qb.planes != 3))
         return fail(TN_ERR_UNSUPPORTED, "3M needs the operands' sum planes");
+    if (d.form == 3 && (qa.planes != 4 || qb.planes != 4))
+        return fail(TN_ERR_UNSUPPORTED, "compensated products need the operands' lo planes");
     const int bn = tn::tc_variant_bn(variant);
     if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx, (int64_t)1 << st.M.size(),
                                  qa.cap_planes * sa, bf, d.bk, 128) != 0 ||
@@ -866,8 +898,9 @@ tn_status build_descriptors(tn_plan_t *p) {
     p->tc_desc.resize(p->steps.size());
     for (auto &st : p->steps) {
         if (st.kernel != K_TC) continue;
-        st.variant = tn::tc_pick_variant(st.form == TN_GEMM_3M ? 2 : 1, (int)st.K.size(),
-                                         (int)st.N.size(), p->opts.tc_bk, p->opts.tc_bn);
+        st.variant = tn::tc_pick_variant(st.form == TN_GEMM_3M ? 2 : (st.form == kFormSplit ? 3 : 1),
+                                         (int)st.K.size(), (int)st.N.size(), p->opts.tc_bk,
+                                         p->opts.tc_bn);
         tn_status s = make_tc_desc(p, st, st.variant, p->tc_desc[&st - &p->steps[0]]);
         if (s != TN_OK) return s;
     }
@@ -908,9 +941,10 @@ tn_status tune_tc_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stre
     for (int v = 0; v < tn::tc_num_variants(); ++v) {
         if (!tn::tc_variant_fits(v, lk, ln)) continue;
         const int form = tn::tc_variant_form(v);
+        if ((st.form == kFormSplit) != (form == 3)) continue;  // split steps stay split
         if (form == 2 && !three_planes) continue;
-        if (p->opts.gemm_form == TN_GEMM_4M && form != 1) continue;
-        if (p->opts.gemm_form == TN_GEMM_3M && form != 2) continue;
+        if (p->opts.gemm_form == TN_GEMM_4M && form == 2) continue;
+        if (p->opts.gemm_form == TN_GEMM_3M && form == 1) continue;
         tn::TcGemmDesc d;
         s = make_tc_desc(p, st, v, d);
         if (s != TN_OK) return s;
@@ -942,7 +976,10 @@ tn_status tune_tc_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stre
     }
     if (best < 0) return TN_OK;
     st.variant = cands[best];
-    st.form = tn::tc_variant_form(st.variant) == 2 ? TN_GEMM_3M : TN_GEMM_4M;
+    {
+        const int f = tn::tc_variant_form(st.variant);
+        st.form = f == 2 ? TN_GEMM_3M : (f == 3 ? kFormSplit : TN_GEMM_4M);
+    }
     p->tc_desc[si] = descs[best];
     if (st.form == TN_GEMM_4M && st.tune_form) {
         // the sum planes are not read: their producers stop writing them
@@ -1023,7 +1060,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             cd.dst_sstride = cd.n;
             cd.amax = p->meta + 2 * p->sb * q.meta;
             cd.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
-            cd.bf16 = p->mode == TN_PREC_BF16_SCALED;
+            cd.bf16 = bf16_mode(p->mode);
             cd.planes = q.planes;
             if (X.producer < 0) {  // a leaf: no producer epilogue recorded its max-abs
                 TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));

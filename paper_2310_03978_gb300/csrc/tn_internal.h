@@ -29,7 +29,7 @@ struct PlanarOut {
     void *base;                     // plane p, slice s: base + p * plane_stride + s * sstride
     int64_t plane_stride;           // elements
     int64_t sstride;                // elements
-    int32_t planes;                 // 2, or 3 with the re + im plane
+    int32_t planes;                 // 2; 3 with the re + im plane; 4 with re_lo, im_lo planes
     int32_t bf16;
     int32_t *exps;                  // per slice exponent (written by the producer)
     const unsigned int *amax_a;     // inputs' per-slice max-abs, float bits, true scale
@@ -135,7 +135,7 @@ struct ConvertDesc {
     unsigned int *amax;        // per slice, float bits of max(|re|, |im|)
     int32_t *exps;             // per slice exponent e: stored = value * 2^-e
     int32_t bf16;              // 0 = fp16, 1 = bf16
-    int32_t planes;            // 2: re, im; 3: re, im, re + im (for the 3M product)
+    int32_t planes;            // 2: re, im; 3: re, im, re + im (3M); 4: re, im, re_lo, im_lo
 };
 cudaError_t launch_amax(const ConvertDesc &d, int64_t slices, cudaStream_t st);
 cudaError_t launch_convert16(const ConvertDesc &d, int64_t slices, cudaStream_t st);
@@ -181,7 +181,7 @@ int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t r
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref);
 int tc_variant_bk(int variant);
 int tc_variant_bn(int variant);
-int tc_variant_form(int variant);  // 1 = 4M, 2 = 3M
+int tc_variant_form(int variant);  // 1 = 4M, 2 = 3M, 3 = split 4M (hi/lo planes)
 int tc_num_variants();
 bool tc_variant_fits(int variant, int lk, int ln);
 

@@ -183,7 +183,8 @@ __device__ __forceinline__ int scale_exponent(unsigned int amax_bits) {
 }
 
 // complex64 -> planar 16-bit: stored = value * 2^-e (exact power-of-two scaling).  With three
-// planes the third holds re + im, summed in FP32 and rounded once.
+// planes the third holds re + im, summed in FP32 and rounded once; with four, planes 2 and 3 hold
+// the residuals re - hi(re) and im - hi(im) (the "lo" halves of a compensated product).
 template <typename T2>
 __device__ __forceinline__ T2 pack2(float a, float b);
 template <>
@@ -194,6 +195,9 @@ template <>
 __device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat162>(float a, float b) {
     return __floats2bfloat162_rn(a, b);
 }
+
+__device__ __forceinline__ float2 unpack2(__half2 h) { return __half22float2(h); }
+__device__ __forceinline__ float2 unpack2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
 
 template <typename T2>
 __device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, int e) {
@@ -208,9 +212,18 @@ __device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, in
         const float4 v = reinterpret_cast<const float4 *>(src)[i];
         const float r0 = ldexpf(v.x, -e), i0 = ldexpf(v.y, -e);
         const float r1 = ldexpf(v.z, -e), i1 = ldexpf(v.w, -e);
-        re[i] = pack2<T2>(r0, r1);
-        im[i] = pack2<T2>(i0, i1);
+        const T2 rh = pack2<T2>(r0, r1), ih = pack2<T2>(i0, i1);
+        re[i] = rh;
+        im[i] = ih;
         if (d.planes == 3) sm[i] = pack2<T2>(r0 + i0, r1 + i1);
+        if (d.planes == 4) {
+            // lo planes: the rounding residuals x - hi (exact in FP32), rounded again
+            const float2 rf = unpack2(rh), jf = unpack2(ih);
+            sm[i] = pack2<T2>(r0 - rf.x, r1 - rf.y);
+            T2 *iml = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) +
+                                             s * d.dst_sstride + 3 * d.plane_stride);
+            iml[i] = pack2<T2>(i0 - jf.x, i1 - jf.y);
+        }
     }
 }
 

@@ -35,7 +35,7 @@ class PlanOptions(C.Structure):
                 ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
                 ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
                 ("profile", C.c_int32), ("tc_bk", C.c_int32), ("tc_bn", C.c_int32),
-                ("autotune", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("autotune", C.c_int32), ("mixed_topk", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class PlanInfo(C.Structure):
@@ -171,7 +171,8 @@ class Plan:
 
     def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
                  workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
-                 profile=False, use_graph=False, tc_bk=0, tc_bn=0, autotune=False):
+                 profile=False, use_graph=False, tc_bk=0, tc_bn=0, autotune=False,
+                 mixed_topk=0):
         self.network = network
         opts = PlanOptions()
         opts.max_slices_in_flight = int(max_slices_in_flight)
@@ -187,6 +188,7 @@ class Plan:
         opts.tc_bk = int(tc_bk)
         opts.tc_bn = int(tc_bn)
         opts.autotune = 1 if autotune else 0
+        opts.mixed_topk = int(mixed_topk)
         pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
         sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
         h = C.c_void_p()
