@@ -50,6 +50,10 @@ def parse_args():
     ap.add_argument("--tc-bk", type=int, default=0, choices=[0, 32, 64])
     ap.add_argument("--tc-bn", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--c64-steps", type=int, default=2)
+    ap.add_argument("--split-steps", type=int, default=2,
+                    help="steps of the compensated FP16 (3xFP16) tensor-core arm; 0 = skip")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: plans time every tensor-core variant on their first batch")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak: each rank contracts its own amplitude batch; strong: the ranks "
                          "split one batch's slices and sum-reduce the amplitudes (FP64)")
@@ -261,7 +265,8 @@ def run_ours(args, rank, world, local_rank):
         if graph:
             # headline: graph replays, no per-kernel events; the roofline comes from a profiled
             # pass of the same number of steps right after
-            gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True, autotune=True)
+            gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True,
+                            autotune=bool(args.autotune))
             amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
             for _ in range(warmup):
                 contract(gplan, amps)
@@ -287,7 +292,8 @@ def run_ours(args, rank, world, local_rank):
             res["launches"] = glaunch
             res["graph"] = True
             return res
-        plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True, autotune=True)
+        plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True,
+                       autotune=bool(args.autotune))
         info = plan.info()
         amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
         # correctness pass (not timed)
@@ -331,6 +337,7 @@ def run_ours(args, rank, world, local_rank):
 
     head = measure(args.mode, args.steps, args.warmup, clocks=True, graph=bool(args.graph))
     c64 = measure("c64", args.c64_steps, 1) if args.c64_steps > 0 else None
+    split = measure("split_fp16", args.split_steps, 1) if args.split_steps > 0 else None
 
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
     # contract into a host array (D2H), every step
@@ -340,7 +347,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e_steps = max(1, args.e2e_steps)
+    for _ in range(e2e_steps):
         net.set_data(net_w.tensors)
         plan.contract_host(s_begin, s_end, out=host_out, stream=stream)
         if strong:
@@ -349,13 +357,13 @@ def run_ours(args, rank, world, local_rank):
                 red = red.to(dev)
                 shard.reduce_amplitudes(red)
                 host_out[:] = red.cpu().numpy()
-    e2e_s = max_over_ranks(time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks(time.perf_counter() - t0) / e2e_steps
     plan.close()
 
     golden = read_golden() if rank == 0 else None
     acc = {}
     if golden is not None:
-        for name, r in (("head", head), ("c64", c64)):
+        for name, r in (("head", head), ("c64", c64), ("split_fp16", split)):
             if r is None:
                 continue
             x_ref = O.readout(golden, wl.circuit.n_qubits)[3]
@@ -404,6 +412,10 @@ def run_ours(args, rank, world, local_rank):
                        "unit": "TFLOPS", "ms_per_step": c64["ms"], "steps": c64["steps"],
                        "roofline": c64["roofline"]}
         line["mixed_over_c64"] = c64["ms"] / head["ms"]
+    if split is not None:
+        line["split_fp16"] = {"value": batches * split["flops"] / (split["ms"] / 1e3) / 1e12,
+                              "unit": "TFLOPS", "ms_per_step": split["ms"],
+                              "steps": split["steps"], "roofline": split["roofline"]}
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {
