@@ -46,9 +46,12 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fp16_scaled")
-    ap.add_argument("--gemm-form", default="auto", choices=["auto", "4m", "3m"])
+    ap.add_argument("--gemm-form", default="auto",
+                    help="auto, 4m or 3m (the single-step microbench takes a comma list)")
     ap.add_argument("--tc-bk", type=int, default=0, choices=[0, 32, 64])
     ap.add_argument("--tc-bn", type=int, default=0, choices=[0, 128, 256])
+    ap.add_argument("--mixed-topk", type=int, default=0,
+                    help="mode mixed: tensor-core steps (largest T_cc first) kept single-pass FP16")
     ap.add_argument("--c64-steps", type=int, default=2)
     ap.add_argument("--split-steps", type=int, default=2,
                     help="steps of the compensated FP16 (3xFP16) tensor-core arm; 0 = skip")
@@ -266,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
             # headline: graph replays, no per-kernel events; the roofline comes from a profiled
             # pass of the same number of steps right after
             gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True,
-                            autotune=bool(args.autotune))
+                            autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
             amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
             for _ in range(warmup):
                 contract(gplan, amps)
@@ -293,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
             res["graph"] = True
             return res
         plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True,
-                       autotune=bool(args.autotune))
+                       autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
         info = plan.info()
         amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
         # correctness pass (not timed)
@@ -341,7 +344,7 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
     # contract into a host array (D2H), every step
-    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode)
+    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, mixed_topk=args.mixed_topk)
     host_out = np.zeros(1 << n_open, dtype=np.complex128)
     plan.contract_host(s_begin, s_end, out=host_out)
     barrier()
@@ -394,6 +397,7 @@ def run_ours(args, rank, world, local_rank):
                    "open_qubits": n_open, "slices": head["info"]["num_slices"],
                    "slices_in_flight": head["info"]["slices_in_flight"],
                    "max_intermediate_log2": head["info"]["max_log2_size"], "mode": args.mode,
+                   **({"mixed_topk": max(1, args.mixed_topk)} if args.mode == "mixed" else {}),
                    "flops_per_batch": head["flops"],
                    "l2": "inputs larger than L2 (largest intermediate 2^28 x 8 B per slice)",
                    "cuda_graph": head["graph"],
@@ -430,7 +434,11 @@ def run_ours(args, rank, world, local_rank):
 
 def run_step_bench(args):
     """Single-step microbench: C[M,N] = sum_K A[M,K] B[N,K] on random complex tensors with all
-    dims 2 and seeded random label orders, timed through the C ABI (one launch per step)."""
+    dims 2 and seeded random label orders, timed through the C ABI.  `--mode` and `--gemm-form`
+    may list several values (comma-separated); one JSON line per combination.  Each line splits
+    the call into the GEMM kernel, the operand conversions (tensor-core steps) and the leaf
+    binding (the permutation of both leaves into GEMM order, complex128 -> complex64), and gives
+    the binding's bandwidth against the measured HBM copy peak and the GEMM's against its own."""
     import torch
     from oracle import oracle as O
     from paper_2310_03978_gb300 import tn
@@ -445,33 +453,48 @@ def run_step_bench(args):
     A = (rng.standard_normal((2,) * ra) + 1j * rng.standard_normal((2,) * ra)) * scale
     B = (rng.standard_normal((2,) * rb) + 1j * rng.standard_normal((2,) * rb)) * scale
     net = tn.Network([A, B], [la, lb], out)
-    plan = tn.Plan(net, [(0, 1)], (), mode=args.mode, profile=True, gemm_form=args.gemm_form,
-                   tc_bk=args.tc_bk, tc_bn=args.tc_bn)
+    ref = O.contract([A, B], [la, lb], out, [(0, 1)]) if lm + ln + lk <= 22 else None
+    pk = peaks()
+    bind_bytes = 24.0 * ((1 << ra) + (1 << rb))  # complex128 read + complex64 written
     amps = torch.zeros(1 << (lm + ln), dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        plan.contract(amps, stream=stream)
-    torch.cuda.synchronize()
-    before = plan.step_info(0)
-    ms = time_contract(torch, plan, amps, args.steps, stream) / args.steps
-    si = plan.step_info(0)
-    kern_ms = (si["time_ms"] - before["time_ms"]) / max(1, si["launches"] - before["launches"])
-    tcc = si["tcc"]
-    check = None
-    if lm + ln + lk <= 22:
-        amps.zero_()
-        plan.contract(amps, stream=stream)
-        ref = O.contract([A, B], [la, lb], out, [(0, 1)])
-        check = O.rel_l2(amps.cpu().numpy(), ref)
-    print(json.dumps({"metric": "single-step effective TFLOPS", "value": tcc / (ms / 1e3) / 1e12,
-                      "unit": "TFLOPS", "kernel": si["kernel_name"], "kernel_ms": kern_ms,
-                      "kernel_tflops": tcc / (kern_ms / 1e3) / 1e12, "ms_per_step": ms,
-                      "prep_ms": (si["prep_ms"] - before["prep_ms"]) / max(1, args.steps),
-                      "config": {"lm": lm, "ln": ln, "lk": lk, "mode": args.mode,
-                                 "gemm_form": args.gemm_form, "tc_bk": args.tc_bk,
-                                 "tc_bn": args.tc_bn},
-                      "rel_l2_vs_oracle": check}))
-    plan.close()
+    for mode in args.mode.split(","):
+        for form in args.gemm_form.split(","):
+            plan = tn.Plan(net, [(0, 1)], (), mode=mode, profile=True, gemm_form=form,
+                           tc_bk=args.tc_bk, tc_bn=args.tc_bn, autotune=bool(args.autotune))
+            for _ in range(args.warmup):
+                plan.contract(amps, stream=stream)
+            torch.cuda.synchronize()
+            before, ib = plan.step_info(0), plan.info()
+            ms = time_contract(torch, plan, amps, args.steps, stream) / args.steps
+            si, ia = plan.step_info(0), plan.info()
+            nl = max(1, si["launches"] - before["launches"])
+            kern_ms = (si["time_ms"] - before["time_ms"]) / nl
+            bind_ms = (ia["bind_ms"] - ib["bind_ms"]) / max(1, ia["bind_launches"] -
+                                                             ib["bind_launches"])
+            tcc = si["tcc"]
+            check = None
+            if ref is not None:
+                amps.zero_()
+                plan.contract(amps, stream=stream)
+                check = O.rel_l2(amps.cpu().numpy(), ref)
+            tc = si["kernel_name"] == "gemm_tc"
+            kpeak = pk["bf16_tflops"] if tc else 80.54784
+            print(json.dumps({
+                "metric": "single-step effective TFLOPS", "value": tcc / (ms / 1e3) / 1e12,
+                "unit": "TFLOPS", "kernel": si["kernel_name"], "tc_variant": si["tc_variant"],
+                "ms_per_step": ms, "kernel_ms": kern_ms,
+                "kernel_tflops": tcc / (kern_ms / 1e3) / 1e12,
+                "kernel_frac": tcc / (kern_ms / 1e3) / 1e12 / kpeak,
+                "kernel_peak": "bf16 burst (measured)" if tc else "FP32 ALU",
+                "prep_ms": (si["prep_ms"] - before["prep_ms"]) / max(1, args.steps),
+                "bind_ms": bind_ms, "bind_gbs": bind_bytes / (bind_ms / 1e3) / 1e9,
+                "bind_frac_hbm": bind_bytes / (bind_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                "config": {"lm": lm, "ln": ln, "lk": lk, "rank_a": ra, "rank_b": rb,
+                           "mode": mode, "gemm_form": form, "tc_bk": args.tc_bk,
+                           "tc_bn": args.tc_bn, "autotune": args.autotune},
+                "rel_l2_vs_oracle": check}))
+            plan.close()
     net.close()
 
 

@@ -42,13 +42,15 @@ typedef enum {
 } tn_status;
 
 /* Arithmetic of the contraction steps (Sec. 4.2-4.3).  Storage between steps is complex64
- * unless a step runs on the tensor cores, whose operands are then stored as planar 16-bit
- * numbers with one power-of-two exponent per tensor and slice.  Accumulation is FP32 in every
- * mode; the cross-slice sum and the readout are FP64. */
+ * unless a step runs on the tensor cores, whose operands are then stored as planar numbers
+ * (16-bit, or FP32 rounded to TF32) with one power-of-two exponent per tensor and slice.
+ * Accumulation is FP32 in every mode; the cross-slice sum and the readout are FP64. */
 typedef enum {
     TN_PREC_C64 = 0,          /* complex64 storage, FP32 FMA arithmetic on CUDA cores        */
-    TN_PREC_TF32 = 1,         /* reserved: TF32 tensor-core steps                            */
-    TN_PREC_SPLIT_TF32 = 2,   /* reserved: 3xTF32 (Eq. 3xTF32)                               */
+    TN_PREC_TF32 = 1,         /* dense steps: TF32 tensor cores (kind::tf32), operands
+                                 rounded to nearest TF32 (Sec. 4.2, Table 2's TF32)         */
+    TN_PREC_SPLIT_TF32 = 2,   /* dense steps: 3xTF32 compensated products (Sec. 4.2):
+                                 hi = TF32(x), lo = TF32(x - hi), three products            */
     TN_PREC_FP16_SCALED = 3,  /* dense steps: FP16 tensor cores, per-tensor 2^e scaling     */
     TN_PREC_BF16_SCALED = 4,  /* dense steps: BF16 tensor cores, per-tensor 2^e scaling     */
     TN_PREC_SPLIT_BF16 = 5,   /* dense steps: compensated BF16 products (3xBF16, Sec. 4.2)   */
@@ -70,7 +72,8 @@ typedef struct {
     int64_t workspace_limit;       /* bytes of device workspace the plan may use; 0 = 60% of
                                       the free device memory at tn_plan() time               */
     void *workspace;               /* optional caller-owned device buffer of workspace_limit
-                                      bytes; NULL = the plan allocates (cudaMalloc) and frees */
+                                      bytes, 256-byte aligned (else TN_ERR_INVALID_ARG); NULL =
+                                      the plan allocates (cudaMalloc) and frees              */
     int32_t gemm_form;             /* tn_gemm_form                                           */
     int32_t sync_each_call;        /* 1 = tn_contract synchronises its stream and reports
                                       asynchronous errors itself                             */
@@ -106,7 +109,11 @@ typedef struct {
     int32_t num_stream_steps;      /* steps routed to the streaming (thin-operand) kernel    */
     int32_t num_generic_steps;     /* steps routed to the element-wise kernel                */
     int64_t kernel_launches;       /* kernels this plan has launched so far (all calls)      */
-    int32_t reserved[6];
+    double bind_ms;                /* profile mode: summed CUDA-event time of the leaf binding
+                                      (slice fixing + permutation into plan order + complex64
+                                      conversion, Sec. 3.2 / 4.1)                            */
+    int64_t bind_launches;         /* profile mode: binding passes timed                     */
+    int32_t reserved[2];
 } tn_plan_info;
 
 typedef struct {

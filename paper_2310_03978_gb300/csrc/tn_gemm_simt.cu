@@ -205,6 +205,119 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
     }
 }
 
+// Thin steps (the low-intensity contractions of App. A.2): C[m, n] = sum_k A[m, k] B[n, k] with
+// few columns (N = NT <= 16) and a short contraction (K <= 64).  One thread owns one row m of A
+// and all NT outputs of that row.  B is held in shared memory as [K][NT] and read as broadcast
+// 16-byte pairs; the block's 256 rows of A are staged through shared memory in chunks of 16 of
+// K with coalesced 16-byte loads.  A step whose small operand is A runs with the roles swapped
+// (the complex product commutes).  The tile (256 x NT) is staged and written in C's order with
+// 8 consecutive elements per thread, as in the other epilogues.
+constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
+
+template <int NT>
+__global__ void __launch_bounds__(256) k_gemm_thin(GemmDesc d) {
+    __shared__ __align__(16) float2 sA[kThinRows * kThinLd];
+    __shared__ __align__(16) float2 sB[64 * (NT < 2 ? 2 : NT)];
+    constexpr int NB = NT < 2 ? 2 : NT;  // row stride of sB (pairs stay 16-byte aligned)
+    const int64_t s = blockIdx.y;
+    const int64_t m0 = (int64_t)blockIdx.x * kThinRows;
+    const int K = 1 << d.lk;
+    const float2 *A = d.A + s * d.sA + m0 * K;
+    const float2 *B = d.B + s * d.sB;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NT * K; e += 256) {
+        const int n = e / K, k = e % K;
+        sB[k * NB + n] = B[e];
+    }
+    float cr[NT], ci[NT];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
+    for (int kc = 0; kc < K; kc += kThinKC) {
+        const int kw = K - kc < kThinKC ? K - kc : kThinKC;  // a power of two >= 2
+        const int hp = kw >> 1;                               // 16-byte pairs per row
+        __syncthreads();
+        for (int e = tid; e < kThinRows * hp; e += 256) {
+            const int r = e / hp, q = e % hp;
+            const float4 v = *reinterpret_cast<const float4 *>(A + (int64_t)r * K + kc + 2 * q);
+            sA[r * kThinLd + 2 * q] = make_float2(v.x, v.y);
+            sA[r * kThinLd + 2 * q + 1] = make_float2(v.z, v.w);
+        }
+        __syncthreads();
+        float tr[NT], ti[NT];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) tr[n] = ti[n] = 0.f;
+        for (int k = 0; k < kw; ++k) {
+            const float2 a = sA[tid * kThinLd + k];
+            const float2 *bk = sB + (kc + k) * NB;
+#pragma unroll
+            for (int n = 0; n < NT; n += 2) {
+                float2 b0, b1;
+                if (NT >= 2) {
+                    const float4 bb = *reinterpret_cast<const float4 *>(bk + n);
+                    b0 = make_float2(bb.x, bb.y);
+                    b1 = make_float2(bb.z, bb.w);
+                } else {
+                    b0 = bk[0];
+                    b1 = b0;
+                }
+                tr[n] = fmaf(a.x, b0.x, tr[n]);
+                tr[n] = fmaf(-a.y, b0.y, tr[n]);
+                ti[n] = fmaf(a.x, b0.y, ti[n]);
+                ti[n] = fmaf(a.y, b0.x, ti[n]);
+                if (n + 1 < NT) {
+                    tr[n + 1] = fmaf(a.x, b1.x, tr[n + 1]);
+                    tr[n + 1] = fmaf(-a.y, b1.y, tr[n + 1]);
+                    ti[n + 1] = fmaf(a.x, b1.y, ti[n + 1]);
+                    ti[n + 1] = fmaf(a.y, b1.x, ti[n + 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            cr[n] += tr[n];
+            ci[n] += ti[n];
+        }
+    }
+    __syncthreads();
+    // stage rows with stride NT + 1 and write 8 consecutive elements of C per task
+    constexpr int LD = NT + 1;
+    float2 *stage = sA;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
+    __syncthreads();
+    auto soff = [&](int sq) { return (sq & 128) ? (LD << (sq & 127)) : (1 << sq); };
+    int w8[8];
+    {
+        const int d0 = soff(d.tb_src[0]), d1 = soff(d.tb_src[1]), d2 = soff(d.tb_src[2]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
+    }
+    const int nb = d.tile_bits;
+    float2 *C = d.C + s * d.sC + deposit((uint64_t)m0, d.lm, d.posC_m);
+    float amx = 0.f;
+    for (int task = tid; task < (1 << (nb - 3)); task += 256) {
+        int w = 0;
+        uint64_t off = 0;
+        for (int q = 3; q < nb; ++q)
+            if ((task >> (q - 3)) & 1) {
+                w += soff(d.tb_src[q]);
+                off |= 1ull << d.tb_pos[q];
+            }
+        float2 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = stage[w + w8[j]];
+            amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+        }
+        float4 *c4 = reinterpret_cast<float4 *>(C + off);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+    }
+    if (d.amax_out) amax_publish(d.amax_out + s, amx);
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st) {
@@ -252,6 +365,21 @@ int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {
            splits < 4096)
         splits *= 2;
     return splits;
+}
+
+cudaError_t launch_gemm_thin(const GemmDesc &d, int64_t slices, cudaStream_t st) {
+    if (d.lm < 8 || d.ln < 0 || d.ln > 4 || d.lk < 1 || d.lk > 6 || slices > 65535 ||
+        d.tile_bits != 8 + d.ln || d.tile_bits < 3 || d.planar_out)
+        return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)((1ll << d.lm) / kThinRows), (unsigned)slices);
+    switch (d.ln) {
+        case 0: k_gemm_thin<1><<<grid, 256, 0, st>>>(d); break;
+        case 1: k_gemm_thin<2><<<grid, 256, 0, st>>>(d); break;
+        case 2: k_gemm_thin<4><<<grid, 256, 0, st>>>(d); break;
+        case 3: k_gemm_thin<8><<<grid, 256, 0, st>>>(d); break;
+        default: k_gemm_thin<16><<<grid, 256, 0, st>>>(d); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace tn

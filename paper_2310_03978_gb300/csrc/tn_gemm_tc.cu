@@ -34,12 +34,15 @@ constexpr int BM = 128;
 constexpr int CW = 64;       // epilogue column chunk
 constexpr int SLD = CW + 1;  // padded row stride of the epilogue staging tile (float2)
 
-// NPL planes per operand (2: 4M; 3: 3M; 4: split 4M with hi and lo planes); a K tile of BKT
-// 16-bit elements per row (64: rows of
-// 128 bytes with the 128-byte swizzle, 32: rows of 64 bytes with the 64-byte swizzle); an N
-// tile of BNT columns; STG pipeline stages; MINB CTAs per SM.
-template <int NPL, int BKT, int BNT, int STG, int MINB>
+// NPL planes per operand (2: 4M; 3: 3M; 4: split 4M with hi and lo planes); shared-memory rows
+// of 2 * BKT bytes (BKT = 64: 128-byte rows with the 128-byte swizzle, 32: 64-byte rows with the
+// 64-byte swizzle), which hold KEL = 2 * BKT / ESZ elements of K (ESZ = 2: FP16 / BF16 with
+// kind::f16, ESZ = 4: FP32 storage read as TF32 with kind::tf32); an N tile of BNT columns; STG
+// pipeline stages; MINB CTAs per SM.  One MMA consumes 32 bytes of K per row in both kinds
+// (16 16-bit or 8 TF32 elements), so the shared-memory geometry depends on BKT alone.
+template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 struct Cfg {
+    static constexpr int KEL = 2 * BKT / ESZ;
     static constexpr int TILE_A = BM * BKT * 2;
     static constexpr int TILE_B = BNT * BKT * 2;
     static constexpr int STAGE_BYTES = NPL * (TILE_A + TILE_B);
@@ -55,6 +58,7 @@ struct Cfg {
     static constexpr uint64_t LAYOUT = BKT == 64 ? 2 : 4;   // 128-byte / 64-byte swizzle
     static_assert(ACC <= 512, "accumulators exceed tensor memory");
     static_assert(MINB * TMEM_COLS <= 512, "co-resident CTAs exceed tensor memory");
+    static_assert(ESZ == 2 || ESZ == 4, "16-bit or TF32 operands");
 };
 
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // default bound of every wait: 4 s
@@ -129,25 +133,37 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor of kind::f16 with FP32 accumulation, both operands K-major.
-__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N, bool neg_a) {
+// Instruction descriptor of kind::f16 (fmt 0 = F16, 1 = BF16) or kind::tf32 (fmt 2 = TF32)
+// with FP32 accumulation, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_mma(uint32_t fmt, int M, int N, bool neg_a) {
     return (1u << 4)                          // D format: F32
-           | ((bf16 ? 1u : 0u) << 7)          // A format: F16 / BF16
-           | ((bf16 ? 1u : 0u) << 10)         // B format
+           | (fmt << 7)                       // A format
+           | (fmt << 10)                      // B format
            | ((neg_a ? 1u : 0u) << 13)        // negate A
            | ((uint32_t)(N >> 3) << 17)       // N / 8
            | ((uint32_t)(M >> 4) << 24);      // M / 16
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+template <int ESZ>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if constexpr (ESZ == 2) {
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -194,18 +210,18 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, int n, const int8_t *pos
 // accuracy of hi + lo operands.
 constexpr int kPromoteK = 512;
 
-template <int NPL, int BKT, int BNT, int STG, int MINB>
+template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
     k_gemm_tc(const __grid_constant__ TcGemmDesc d, int64_t tiles_n) {
-    using F = Cfg<NPL, BKT, BNT, STG, MINB>;
+    using F = Cfg<NPL, BKT, BNT, STG, MINB, ESZ>;
     // split 4M: warps 2..5 fold chunk accumulators into the running sums and write the result
     constexpr bool PROMOTE = NPL == 4;
-    constexpr int CHUNK_KB = kPromoteK / BKT;
+    constexpr int CHUNK_KB = kPromoteK / F::KEL;
     constexpr int STAGES = STG;
     constexpr int STAGE_BYTES = F::STAGE_BYTES;
     constexpr int TMEM_COLS = F::TMEM_COLS;
     constexpr int TILE_A = F::TILE_A, TILE_B = F::TILE_B;
-    constexpr int BK = BKT, BN = BNT;
+    constexpr int BK = F::KEL, BN = BNT;  // K elements per stage, N tile
     auto sdesc = [](uint32_t a) { return sdesc_sw<F::SBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -289,8 +305,9 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
     } else if (threadIdx.x == 32) {
         // MMA issuer: 4M = four real products into the re and im accumulators,
         // 3M = three products into three accumulators
-        const uint32_t id_pos = idesc_f16(d.bf16 != 0, BM, BNT, false);
-        const uint32_t id_neg = idesc_f16(d.bf16 != 0, BM, BNT, true);
+        const uint32_t fmt = ESZ == 4 ? 2u : (d.dtype == 1 ? 1u : 0u);
+        const uint32_t id_pos = idesc_mma(fmt, BM, BNT, false);
+        const uint32_t id_neg = idesc_mma(fmt, BM, BNT, true);
         bool ok = true;
         for (int kb = 0; kb < num_kb && ok; ++kb) {
             const int st = kb % STAGES;
@@ -316,38 +333,38 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
             const uint64_t b_re = sdesc(base + NPL * TILE_A);
             const uint64_t b_im = sdesc(base + NPL * TILE_A + TILE_B);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes,
+            for (int kk = 0; kk < BKT / 16; ++kk) {
+                const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // one MMA's 32 bytes of K,
                                                                  // inside one swizzled row
                 const uint32_t first = ((PROMOTE ? kc : kb) > 0 || kk > 0) ? 1u : 0u;
                 if constexpr (NPL == 2) {
-                    umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
-                    umma_f16(tmem, a_im + adv, b_im + adv, id_neg, 1u);
-                    umma_f16(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
-                    umma_f16(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                    umma<ESZ>(tmem, a_re + adv, b_re + adv, id_pos, first);
+                    umma<ESZ>(tmem, a_im + adv, b_im + adv, id_neg, 1u);
+                    umma<ESZ>(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
+                    umma<ESZ>(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
                 } else if constexpr (NPL == 4) {
                     // compensated products: x = x_hi + x_lo, xy ~ x_hi y_hi + x_hi y_lo + x_lo y_hi
                     const uint64_t a_rl = sdesc(base + 2 * TILE_A), a_il = sdesc(base + 3 * TILE_A);
                     const uint64_t b_rl = sdesc(base + NPL * TILE_A + 2 * TILE_B);
                     const uint64_t b_il = sdesc(base + NPL * TILE_A + 3 * TILE_B);
-                    umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
-                    umma_f16(tmem, a_im + adv, b_im + adv, id_neg, 1u);
-                    umma_f16(tmem, a_re + adv, b_rl + adv, id_pos, 1u);
-                    umma_f16(tmem, a_im + adv, b_il + adv, id_neg, 1u);
-                    umma_f16(tmem, a_rl + adv, b_re + adv, id_pos, 1u);
-                    umma_f16(tmem, a_il + adv, b_im + adv, id_neg, 1u);
-                    umma_f16(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
-                    umma_f16(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
-                    umma_f16(tmem + BN, a_re + adv, b_il + adv, id_pos, 1u);
-                    umma_f16(tmem + BN, a_im + adv, b_rl + adv, id_pos, 1u);
-                    umma_f16(tmem + BN, a_rl + adv, b_im + adv, id_pos, 1u);
-                    umma_f16(tmem + BN, a_il + adv, b_re + adv, id_pos, 1u);
+                    umma<ESZ>(tmem, a_re + adv, b_re + adv, id_pos, first);
+                    umma<ESZ>(tmem, a_im + adv, b_im + adv, id_neg, 1u);
+                    umma<ESZ>(tmem, a_re + adv, b_rl + adv, id_pos, 1u);
+                    umma<ESZ>(tmem, a_im + adv, b_il + adv, id_neg, 1u);
+                    umma<ESZ>(tmem, a_rl + adv, b_re + adv, id_pos, 1u);
+                    umma<ESZ>(tmem, a_il + adv, b_im + adv, id_neg, 1u);
+                    umma<ESZ>(tmem + BN, a_re + adv, b_im + adv, id_pos, first);
+                    umma<ESZ>(tmem + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                    umma<ESZ>(tmem + BN, a_re + adv, b_il + adv, id_pos, 1u);
+                    umma<ESZ>(tmem + BN, a_im + adv, b_rl + adv, id_pos, 1u);
+                    umma<ESZ>(tmem + BN, a_rl + adv, b_im + adv, id_pos, 1u);
+                    umma<ESZ>(tmem + BN, a_il + adv, b_re + adv, id_pos, 1u);
                 } else {
                     const uint64_t a_sm = sdesc(base + 2 * TILE_A);
                     const uint64_t b_sm = sdesc(base + NPL * TILE_A + 2 * TILE_B);
-                    umma_f16(tmem, a_re + adv, b_re + adv, id_pos, first);
-                    umma_f16(tmem + BN, a_im + adv, b_im + adv, id_pos, first);
-                    umma_f16(tmem + 2 * BN, a_sm + adv, b_sm + adv, id_pos, first);
+                    umma<ESZ>(tmem, a_re + adv, b_re + adv, id_pos, first);
+                    umma<ESZ>(tmem + BN, a_im + adv, b_im + adv, id_pos, first);
+                    umma<ESZ>(tmem + 2 * BN, a_sm + adv, b_sm + adv, id_pos, first);
                 }
             }
             umma_commit(&empty[st]);
@@ -429,27 +446,39 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
         const int row = (warp & 3) * 32 + lane;
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const uint32_t src = PROMOTE ? 2 * BN : 0;  // accumulator columns to read
-        // sorted chunk bit 0 is C's position 0, so each thread writes an adjacent pair: bit 0
-        // is the pair, bits 1..7 come from the thread index and bits 8..12 from the iteration
-        const int sq0 = d.tb_src[0];
-        const int dpair = (sq0 & 128) ? (1 << (sq0 & 127)) * SLD : (1 << sq0);
+        // sorted chunk bits 0..2 are C's positions 0..2 (the lowest three bits of C always lie
+        // among the chunk's 7 row and 6 column bits), so each thread writes 8 consecutive
+        // elements: bits 0..2 are its own, bits 3..9 come from the thread index and bits 10..12
+        // from the iteration
+        int w8[8];
+        {
+            int dq[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int sq = d.tb_src[q];
+                dq[q] = (sq & 128) ? (1 << (sq & 127)) * SLD : (1 << sq);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w8[j] = ((j & 1) ? dq[0] : 0) + ((j & 2) ? dq[1] : 0) + ((j & 4) ? dq[2] : 0);
+        }
         int mlo = 0, nlo = 0;
         uint64_t olo = 0;
 #pragma unroll
-        for (int q = 1; q < 8; ++q)
-            if ((et >> (q - 1)) & 1) {
+        for (int q = 3; q < 10; ++q)
+            if ((et >> (q - 3)) & 1) {
                 const int sq = d.tb_src[q];
                 if (sq & 128) mlo |= 1 << (sq & 127);
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
         const int wlo = mlo * SLD + nlo;
-        if (epi && et < 32) {
+        if (epi && et < 8) {
             int mi = 0, ni = 0;
             uint64_t off = 0;
 #pragma unroll
-            for (int q = 8; q < 13; ++q)
-                if ((et >> (q - 8)) & 1) {
+            for (int q = 10; q < 13; ++q)
+                if ((et >> (q - 10)) & 1) {
                     const int sq = d.tb_src[q];
                     if (sq & 128) mi |= 1 << (sq & 127);
                     else ni |= 1 << sq;
@@ -493,25 +522,27 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
             const uint64_t cbase = mbase | deposit((uint64_t)(n0 + cb), d.ln, d.posC_n);
             if (!epi) {
                 // producer and MMA warps only join the barriers
-            } else if (d.planar_out) {
-#pragma unroll 4
-                for (int it = 0; it < (BM * CW) / 256; ++it) {
-                    const int w = wlo + hi_w[it];
-                    const float2 v0 = stage[w], v1 = stage[w + dpair];
-                    planar_out_store2(d.pout, s, cbase | olo | hi_off[it], v0, v1, eo);
-                    amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
-                                           fmaxf(fabsf(v1.x), fabsf(v1.y))));
-                }
             } else {
                 float2 *C = d.C + s * d.sC + cbase;
-#pragma unroll 4
-                for (int it = 0; it < (BM * CW) / 256; ++it) {
+#pragma unroll 2
+                for (int it = 0; it < (BM * CW) / (8 * 128); ++it) {
                     const int w = wlo + hi_w[it];
-                    const float2 v0 = stage[w], v1 = stage[w + dpair];
-                    *reinterpret_cast<float4 *>(C + (olo | hi_off[it])) =
-                        make_float4(v0.x, v0.y, v1.x, v1.y);
-                    amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
-                                           fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                    float2 v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        v[j] = stage[w + w8[j]];
+                        amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                    }
+                    const uint64_t o = olo | hi_off[it];
+                    if (d.planar_out) {
+                        planar_out_store8(d.pout, s, cbase | o, v, eo);
+                    } else {
+                        float4 *c4 = reinterpret_cast<float4 *>(C + o);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
+                                                v[2 * j + 1].y);
+                    }
                 }
             }
             __syncthreads();
@@ -554,61 +585,72 @@ bool tc_available() {
         return false;
     if (major != 10) return false;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_gemm_tc<2, 64, 128, 3, 1>) != cudaSuccess) return false;
+    if (cudaFuncGetAttributes(&fa, k_gemm_tc<2, 64, 128, 3, 1, 2>) != cudaSuccess) return false;
     return get_encode() != nullptr;
 }
 
-int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
-                         int64_t depth, int bf16, int bk, int box_rows) {
+int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t rows,
+                       int64_t depth, int dtype, int bk, int box_rows) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return -1;
+    const int esz = dtype == 2 ? 4 : 2;
+    const int row_bytes = bk * esz;
     // K must fill whole 16-byte rows; a K below the tile is zero-filled by the tensor map
-    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bk != 32 && bk != 64) || K % 8 != 0 ||
-        (K > bk && K % bk != 0))
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (row_bytes != 64 && row_bytes != 128) ||
+        (K * esz) % 16 != 0 || (K > bk && K % bk != 0) || dtype < 0 || dtype > 2)
         return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
-    cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)(K * esz), (cuuint64_t)(K * rows * esz)};
     if (box_rows != 128 && box_rows != 256) return -2;
     cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(reinterpret_cast<CUtensorMap *>(tmap_host),
-                     bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-                     const_cast<void *>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+    const CUtensorMapDataType ty = dtype == 2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUresult r = enc(reinterpret_cast<CUtensorMap *>(tmap_host), ty, 3, const_cast<void *>(base),
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -3;
 }
 
 namespace {
 
-// The kernel variants, indexed by TcGemmDesc::variant.
+// The kernel variants, indexed by TcGemmDesc::variant: (id, planes, 16-bit elements per
+// shared-memory row, N tile, stages, CTAs per SM, operand bytes).
 #define TN_TC_VARIANTS(X)          \
-    X(0, 2, 64, 128, 3, 1) /* 4M, long K (default)                  */ \
-    X(1, 2, 32, 256, 4, 1) /* 4M, N tile 256                         */ \
-    X(2, 2, 32, 128, 2, 2) /* 4M, short K: small ring, 2 CTAs per SM */ \
-    X(3, 3, 32, 128, 4, 1) /* 3M                                     */ \
-    X(4, 3, 64, 128, 2, 1) /* 3M, 128-byte swizzle                   */ \
-    X(5, 2, 32, 128, 6, 1) /* 4M, 64-byte swizzle, 6 stages          */ \
-    X(6, 4, 32, 128, 3, 1) /* split 4M (hi/lo planes), promoted      */
+    X(0, 2, 64, 128, 3, 1, 2)  /* 4M, long K (default)                  */ \
+    X(1, 2, 32, 256, 4, 1, 2)  /* 4M, N tile 256                         */ \
+    X(2, 2, 32, 128, 2, 2, 2)  /* 4M, short K: small ring, 2 CTAs per SM */ \
+    X(3, 3, 32, 128, 4, 1, 2)  /* 3M                                     */ \
+    X(4, 3, 64, 128, 2, 1, 2)  /* 3M, 128-byte swizzle                   */ \
+    X(5, 2, 32, 128, 6, 1, 2)  /* 4M, 64-byte swizzle, 6 stages          */ \
+    X(6, 4, 32, 128, 3, 1, 2)  /* split 4M (hi/lo planes), promoted      */ \
+    X(7, 2, 32, 256, 4, 1, 4)  /* TF32 4M, N tile 256, K 16 per stage    */ \
+    X(8, 2, 32, 128, 2, 2, 4)  /* TF32 4M, short K, 2 CTAs per SM        */ \
+    X(9, 2, 64, 128, 3, 1, 4)  /* TF32 4M, 128-byte swizzle, K 32        */ \
+    X(10, 3, 32, 128, 4, 1, 4) /* TF32 3M                                */ \
+    X(11, 4, 32, 128, 3, 1, 4) /* split TF32 (3xTF32), promoted          */
 
-template <int NPL, int BKT, int BNT, int STG, int MINB>
+template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 cudaError_t configure_variant() {
-    return cudaFuncSetAttribute(k_gemm_tc<NPL, BKT, BNT, STG, MINB>,
+    return cudaFuncSetAttribute(k_gemm_tc<NPL, BKT, BNT, STG, MINB, ESZ>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Cfg<NPL, BKT, BNT, STG, MINB>::SMEM_BYTES);
+                                Cfg<NPL, BKT, BNT, STG, MINB, ESZ>::SMEM_BYTES);
 }
 
-template <int NPL, int BKT, int BNT, int STG, int MINB>
+template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    if (d.ln < (BNT == 256 ? 8 : 7) || d.lk < 3 || (BKT == 64 && d.lk < 6))
+    constexpr int KEL = Cfg<NPL, BKT, BNT, STG, MINB, ESZ>::KEL;
+    if (d.ln < (BNT == 256 ? 8 : 7) || d.lk < 3 || (KEL == 64 && d.lk < 6) ||
+        (d.dtype == 2) != (ESZ == 4))
         return cudaErrorInvalidValue;
     const int64_t tiles_n = (1ll << d.ln) / BNT;
     const int64_t tiles = ((1ll << d.lm) / BM) * tiles_n;
     if (tiles > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    k_gemm_tc<NPL, BKT, BNT, STG, MINB>
+    k_gemm_tc<NPL, BKT, BNT, STG, MINB, ESZ>
         <<<dim3((unsigned)tiles, (unsigned)slices), NPL == 4 ? 192 : 128,
-           Cfg<NPL, BKT, BNT, STG, MINB>::SMEM_BYTES, st>>>(d, tiles_n);
+           Cfg<NPL, BKT, BNT, STG, MINB, ESZ>::SMEM_BYTES, st>>>(d, tiles_n);
     return cudaGetLastError();
 }
 
@@ -616,17 +658,18 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 
 cudaError_t tc_prepare() {
     cudaError_t e = cudaSuccess;
-#define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb) \
-    if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb>();
+#define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb, esz) \
+    if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb, esz>();
     TN_TC_VARIANTS(TN_TC_CONFIGURE)
 #undef TN_TC_CONFIGURE
     return e;
 }
 
+// K elements per pipeline stage of a variant (the tensor map's box width)
 int tc_variant_bk(int variant) {
     switch (variant) {
-#define TN_TC_BK(id, npl, bk, bn, stg, minb) \
-    case id: return bk;
+#define TN_TC_BK(id, npl, bk, bn, stg, minb, esz) \
+    case id: return 2 * bk / esz;
         TN_TC_VARIANTS(TN_TC_BK)
 #undef TN_TC_BK
     }
@@ -635,7 +678,7 @@ int tc_variant_bk(int variant) {
 
 int tc_variant_bn(int variant) {
     switch (variant) {
-#define TN_TC_BN(id, npl, bk, bn, stg, minb) \
+#define TN_TC_BN(id, npl, bk, bn, stg, minb, esz) \
     case id: return bn;
         TN_TC_VARIANTS(TN_TC_BN)
 #undef TN_TC_BN
@@ -643,12 +686,22 @@ int tc_variant_bn(int variant) {
     return 0;
 }
 
+bool tc_variant_tf32(int variant) {
+    switch (variant) {
+#define TN_TC_ESZ(id, npl, bk, bn, stg, minb, esz) \
+    case id: return esz == 4;
+        TN_TC_VARIANTS(TN_TC_ESZ)
+#undef TN_TC_ESZ
+    }
+    return false;
+}
+
 // Variant choice (measured on GB300): short contractions (K <= 512) are epilogue-bound and run
 // two CTAs per SM; long ones use the 128 x 256 tile (1.98 PFLOP/s on m=2^13, n=2^14, k=2^14
 // against 1.79 for 128 x 128), or 128 x 128 when N < 256.
 int tc_variant_form(int variant) {
     switch (variant) {
-#define TN_TC_FORM(id, npl, bk, bn, stg, minb) \
+#define TN_TC_FORM(id, npl, bk, bn, stg, minb, esz) \
     case id: return npl == 3 ? 2 : (npl == 4 ? 3 : 1);
         TN_TC_VARIANTS(TN_TC_FORM)
 #undef TN_TC_FORM
@@ -656,7 +709,7 @@ int tc_variant_form(int variant) {
     return 0;
 }
 
-int tc_num_variants() { return 7; }
+int tc_num_variants() { return 12; }
 
 bool tc_variant_fits(int variant, int lk, int ln) {
     const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
@@ -666,7 +719,17 @@ bool tc_variant_fits(int variant, int lk, int ln) {
     return ln >= (bn == 256 ? 8 : 7);
 }
 
-int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref) {
+// bk_pref / bn_pref: 0 or the K / N tile the caller asks for (K tile in 16-bit elements of a
+// shared-memory row: 32 = 64-byte rows, 64 = 128-byte rows, for both operand types).
+int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf32) {
+    if (tf32) {
+        if (form == 3) return 11;
+        if (form == 2) return 10;
+        if (bn_pref == 256 && ln >= 8) return 7;
+        if (bk_pref == 64) return 9;
+        if (lk <= 9) return 8;
+        return ln >= 8 && bn_pref != 128 ? 7 : 9;
+    }
     if (form == 3) return 6;
     if (form == 2) return bk_pref == 64 ? 4 : 3;
     if (bn_pref == 256 && ln >= 8) return 1;
@@ -679,8 +742,8 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref) {
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (d.lm < 7 || slices > 65535) return cudaErrorInvalidValue;
     switch (d.variant) {
-#define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb) \
-    case id: return launch_variant<npl, bk, bn, stg, minb>(d, slices, st);
+#define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb, esz) \
+    case id: return launch_variant<npl, bk, bn, stg, minb, esz>(d, slices, st);
         TN_TC_VARIANTS(TN_TC_LAUNCH)
 #undef TN_TC_LAUNCH
     }
@@ -700,8 +763,8 @@ tn_status tc_selftest_wait_timeout(int32_t limit_ms, cudaStream_t st) {
     TcGemmDesc d;
     memset(&d, 0, sizeof d);
     int32_t *exps = reinterpret_cast<int32_t *>(buf + 128 * 128);
-    if (encode_tmap_planar16(&d.tmA, buf, 64, 128, 2, 0, 64, 128) != 0 ||
-        encode_tmap_planar16(&d.tmB, buf, 64, 128, 2, 0, 64, 128) != 0) {
+    if (encode_tmap_planar(&d.tmA, buf, 64, 128, 2, 0, 64, 128) != 0 ||
+        encode_tmap_planar(&d.tmB, buf, 64, 128, 2, 0, 64, 128) != 0) {
         cudaFree(buf);
         return report(TN_ERR_CUDA, "self-test tensor maps");
     }

@@ -81,6 +81,11 @@ bool bf16_mode(tn_precision m) {
     return m == TN_PREC_BF16_SCALED || m == TN_PREC_SPLIT_BF16;
 }
 
+bool tf32_mode(tn_precision m) { return m == TN_PREC_TF32 || m == TN_PREC_SPLIT_TF32; }
+
+// Stored type of the tensor-core operands: 0 FP16, 1 BF16, 2 FP32 rounded to TF32.
+int operand_dtype(tn_precision m) { return tf32_mode(m) ? 2 : (bf16_mode(m) ? 1 : 0); }
+
 struct Tensor {
     std::vector<int> order;  // memory order of the labels, most significant first
     bool dep = false;        // depends on the slice id
@@ -157,6 +162,7 @@ struct tn_plan {
     char *arena = nullptr;
     bool own_arena = false;
     std::vector<tn::BindItem> bind_inv, bind_sl;
+    std::vector<tn::BindTiled> tiled_inv, tiled_sl;  // leaves bound by the tiled permutation
     tn::BindItem *bind_inv_dev = nullptr, *bind_sl_dev = nullptr;
     int max_rank_inv = 0, max_rank_sl = 0;
     unsigned int *meta = nullptr;  // per meta block: amax[sb] then exps[sb]
@@ -175,6 +181,10 @@ struct tn_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;           // kernels inside one replay
+    // profile mode: leaf-binding launches bracketed by events, and their running total
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_bind;
+    double bind_ms = 0;
+    int64_t bind_timed = 0;
 };
 
 namespace {
@@ -196,14 +206,16 @@ tn_status check_plan(const tn_plan_t *p) {
 // tensor cores busy) rounded up to the tcgen05 tile (M 128, N 128, K 64).
 int route(const Step &s, tn_precision mode, bool tc_ok) {
     const int lm = (int)s.M.size(), ln = (int)s.N.size(), lk = (int)s.K.size();
-    const bool tc_mode = mode == TN_PREC_FP16_SCALED || mode == TN_PREC_BF16_SCALED ||
-                         mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 ||
-                         mode == TN_PREC_MIXED;
+    const bool tc_mode = mode != TN_PREC_C64;
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 6) return K_TC;
     // large outputs of short contractions (8 <= k < 64) also go to the tensor cores: the short-K
     // variant's tensor map zero-fills the K tile past k, and its epilogue writes 2 CTAs per SM
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 3 && lm + ln >= 20)
         return K_TC;
+    // thin steps: a short contraction of a large operand with a small one (at most 16 free
+    // elements), streamed on the CUDA cores at memory speed
+    if (s.batch.empty() && lk >= 1 && lk <= 6 && std::min(lm, ln) <= 4 && std::max(lm, ln) >= 10)
+        return K_STREAM;
     // register-tiled GEMM (split along K when the output is small); a contraction of fewer than
     // 16 elements is cheaper as an element-wise pass with coalesced stores
     if (s.batch.empty() && lk >= 2 && lm >= 3 && ln >= 3 && lm + ln + lk >= 14) return K_GEMM;
@@ -444,8 +456,6 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         return fail(TN_ERR_INVALID_ARG, "bad sliced labels");
     if ((int)mode < 0 || (int)mode > (int)TN_PREC_MIXED)
         return fail(TN_ERR_INVALID_ARG, "bad precision mode");
-    if (mode == TN_PREC_TF32 || mode == TN_PREC_SPLIT_TF32)
-        return fail(TN_ERR_UNSUPPORTED, "precision mode %d is not implemented", (int)mode);
 
     auto *p = new tn_plan_t();
     p->net = net;
@@ -563,7 +573,8 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         st.kernel = route(st, mode, p->tc_ok);
         // slice-independent steps run once per call; they stay on the CUDA cores
         if (!st.dep && st.kernel == K_TC) st.kernel = K_GEMM;
-        if (mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 || mode == TN_PREC_MIXED)
+        if (mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 ||
+            mode == TN_PREC_SPLIT_TF32 || mode == TN_PREC_MIXED)
             st.form = kFormSplit;
         else
             st.form = (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
@@ -632,9 +643,11 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
             q.planes = st.form == TN_GEMM_3M ? 3 : (st.form == kFormSplit ? 4 : 2);
             if (st.tune_form) q.planes = 3;  // the tuner may pick 3M for this step
             q.cap_planes = q.planes;
-            q.bytes_per_slice = (int64_t)(2 * q.cap_planes) << p->tensors[q.tensor].rank();
+            q.bytes_per_slice = (int64_t)((tf32_mode(mode) ? 4 : 2) * q.cap_planes)
+                                << p->tensors[q.tensor].rank();
             const Tensor &X = p->tensors[q.tensor];
-            if (X.producer >= 0 && st.form != kFormSplit) {
+            // TF32 operands (FP32 storage) are always made by the conversion pass
+            if (X.producer >= 0 && st.form != kFormSplit && !tf32_mode(mode)) {
                 // A producer's direct output takes its exponent from a bound (2 K max|a| max|b|)
                 // that can exceed the true maximum by many binades, which leaves the stored
                 // values low in FP16's range; single-pass operands keep their 11 significant
@@ -743,6 +756,10 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
     p->sb = sb;
     p->arena_bytes = need;
     if (p->opts.workspace) {
+        if (reinterpret_cast<uintptr_t>(p->opts.workspace) % 256 != 0) {
+            delete p;
+            return fail(TN_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        }
         p->arena = (char *)p->opts.workspace;
     } else {
         cudaError_t e = cudaMalloc(&p->arena, (size_t)need);
@@ -790,6 +807,62 @@ tn::BindItem make_bind(const tn_plan_t *p, const Tensor &t) {
     return it;
 }
 
+// Leaves of at least this rank are bound by the tiled permutation kernel (k_bind_tiled); smaller
+// ones (gates, projectors) are gathered many per launch by k_bind.
+constexpr int kTiledBindMinRank = 12;
+
+// Tile tables of a large leaf (see tn::BindTiled) from its gather description.
+tn::BindTiled make_bind_tiled(const tn::BindItem &it) {
+    tn::BindTiled b{};
+    b.dst_off = it.dst_off;
+    b.dst_sstride = it.dst_sstride;
+    b.src_off = it.src_off;
+    b.nsl = it.nsl;
+    for (int j = 0; j < 8; ++j) {
+        b.sl_bit[j] = it.sl_bit[j];
+        b.sl_pos[j] = it.sl_pos[j];
+    }
+    const int r = it.rank;
+    // destination bits ordered by their source bit: the first five are the lowest unsliced
+    // source bits
+    std::vector<std::pair<int, int>> by_src;
+    for (int i = 0; i < r; ++i) by_src.push_back({it.pos_src[i], i});
+    std::sort(by_src.begin(), by_src.end());
+    std::vector<int> low;
+    for (int j = 0; j < 5 && j < r; ++j) low.push_back(by_src[j].second);
+    std::vector<int> tile_d;
+    for (int d = 0; d < 6; ++d) tile_d.push_back(d);
+    std::vector<int> extra;
+    for (int d : low)
+        if (d >= 6) extra.push_back(d);
+    std::sort(extra.begin(), extra.end());
+    for (int d : extra) tile_d.push_back(d);
+    b.t = (int)tile_d.size();
+    auto tile_bit = [&](int d) {
+        return (int)(std::find(tile_d.begin(), tile_d.end(), d) - tile_d.begin());
+    };
+    for (int q = 0; q < 12; ++q) b.t2d[q] = q < b.t ? (int8_t)tile_d[q] : (int8_t)-1;
+    std::vector<int> order = low;  // read order: source-contiguous bits first
+    for (int d : tile_d)
+        if (std::find(low.begin(), low.end(), d) == low.end()) order.push_back(d);
+    for (int q = 0; q < 12; ++q) {
+        b.e2t[q] = q < b.t ? (int8_t)tile_bit(order[q]) : (int8_t)-1;
+        b.e2s[q] = q < b.t ? it.pos_src[order[q]] : (int8_t)-1;
+    }
+    fill_pos(b.rest_d, TN_MAXR, -1);
+    fill_pos(b.rest_s, TN_MAXR, -1);
+    int u = 0;
+    for (int d = 0; d < r; ++d)
+        if (std::find(tile_d.begin(), tile_d.end(), d) == tile_d.end()) {
+            b.rest_d[u] = (int8_t)d;
+            b.rest_s[u] = it.pos_src[d];
+            u++;
+        }
+    b.nrest = u;
+    b.ntiles = (int64_t)1 << u;
+    return b;
+}
+
 // Direct planar output of step st (see tn::PlanarOut): the consumer's planar buffer, the
 // exponents of its meta block, and the max-abs of st's inputs for the bound.
 void fill_planar_out(const tn_plan_t *p, const Step &st, tn::PlanarOut &o) {
@@ -813,10 +886,13 @@ void fill_planar_out(const tn_plan_t *p, const Step &st, tn::PlanarOut &o) {
 tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGemmDesc &d) {
     memset(&d, 0, sizeof d);
     const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
-    const int bf = bf16_mode(p->mode);
+    const int bf = operand_dtype(p->mode);
     const int64_t Kx = (int64_t)1 << st.K.size();
     const Planar &qa = p->planars[st.pa], &qb = p->planars[st.pb];
     const int64_t sa = A.dep ? p->sb : 1, sbb = B.dep ? p->sb : 1;
+    if (tn::tc_variant_tf32(variant) != (bf == 2))
+        return fail(TN_ERR_UNSUPPORTED, "kernel variant %d does not take this operand type",
+                    variant);
     d.variant = variant;
     d.bk = tn::tc_variant_bk(variant);
     d.form = tn::tc_variant_form(variant);
@@ -825,9 +901,9 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     if (d.form == 3 && (qa.planes != 4 || qb.planes != 4))
         return fail(TN_ERR_UNSUPPORTED, "compensated products need the operands' lo planes");
     const int bn = tn::tc_variant_bn(variant);
-    if (tn::encode_tmap_planar16(&d.tmA, p->arena + qa.off, Kx, (int64_t)1 << st.M.size(),
+    if (tn::encode_tmap_planar(&d.tmA, p->arena + qa.off, Kx, (int64_t)1 << st.M.size(),
                                  qa.cap_planes * sa, bf, d.bk, 128) != 0 ||
-        tn::encode_tmap_planar16(&d.tmB, p->arena + qb.off, Kx, (int64_t)1 << st.N.size(),
+        tn::encode_tmap_planar(&d.tmB, p->arena + qb.off, Kx, (int64_t)1 << st.N.size(),
                                  qb.cap_planes * sbb, bf, d.bk, bn) != 0)
         return fail(TN_ERR_CUDA, "cuTensorMapEncodeTiled failed for step %d",
                     (int)(&st - &p->steps[0]));
@@ -842,7 +918,7 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     d.slices_b = sbb;
     d.expA = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qa.meta + p->sb);
     d.expB = reinterpret_cast<const int32_t *>(p->meta + 2 * p->sb * qb.meta + p->sb);
-    d.bf16 = bf;
+    d.dtype = bf;
     d.amax_out = st.out_meta >= 0 ? p->meta + 2 * p->sb * st.out_meta : nullptr;
     if (st.direct_planar >= 0) {
         d.planar_out = 1;
@@ -852,12 +928,12 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     fill_pos(d.posC_n, TN_MAXR, -1);
     for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(st.M[st.M.size() - 1 - i]);
     for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(st.N[st.N.size() - 1 - i]);
-    // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C; the first is
-    // always position 0 (the lowest label of C is the lowest of its side), which the
-    // epilogue's pair stores rely on
+    // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C; the first three
+    // are always positions 0-2 (C's three lowest labels are among the lowest three of M and
+    // of N), which the epilogue's 8-element stores rely on
     tn::sort_tile_bits(7, 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
-    if (d.tb_pos[0] != 0)
-        return fail(TN_ERR_UNSUPPORTED, "step %d: result bit 0 outside the epilogue chunk",
+    if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
+        return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the epilogue chunk",
                     (int)(&st - &p->steps[0]));
     return TN_OK;
 }
@@ -871,6 +947,10 @@ tn_status build_descriptors(tn_plan_t *p) {
             if (std::find(p->sliced.begin(), p->sliced.end(), l) != p->sliced.end()) nsl++;
         if (nsl > 8) return fail(TN_ERR_UNSUPPORTED, "a leaf carries more than 8 sliced labels");
         tn::BindItem it = make_bind(p, t);
+        if (t.rank() >= kTiledBindMinRank) {
+            (t.dep ? p->tiled_sl : p->tiled_inv).push_back(make_bind_tiled(it));
+            continue;
+        }
         if (t.dep) {
             p->bind_sl.push_back(it);
             p->max_rank_sl = std::max(p->max_rank_sl, t.rank());
@@ -900,7 +980,7 @@ tn_status build_descriptors(tn_plan_t *p) {
         if (st.kernel != K_TC) continue;
         st.variant = tn::tc_pick_variant(st.form == TN_GEMM_3M ? 2 : (st.form == kFormSplit ? 3 : 1),
                                          (int)st.K.size(), (int)st.N.size(), p->opts.tc_bk,
-                                         p->opts.tc_bn);
+                                         p->opts.tc_bn, tf32_mode(p->mode));
         tn_status s = make_tc_desc(p, st, st.variant, p->tc_desc[&st - &p->steps[0]]);
         if (s != TN_OK) return s;
     }
@@ -925,6 +1005,38 @@ tn_status take_events(tn_plan_t *p, EventPair &ev) {
 
 tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGemmDesc &d);
 
+// Bind the invariant leaves (sliced = false, once per call) or the sliced leaves of slices
+// [s0, s0 + ns): small leaves in one gather launch, each large leaf by the tiled permutation.
+// Profile mode brackets them with one event pair.
+tn_status bind_leaves(tn_plan_t *p, bool sliced, int64_t s0, int64_t ns, cudaStream_t stream) {
+    const auto &items = sliced ? p->bind_sl : p->bind_inv;
+    const auto &tiled = sliced ? p->tiled_sl : p->tiled_inv;
+    if (items.empty() && tiled.empty()) return TN_OK;
+    float2 *arena = reinterpret_cast<float2 *>(p->arena);
+    const double2 *src = p->net->data;
+    EventPair ev{};
+    if (p->opts.profile) {
+        tn_status s = take_events(p, ev);
+        if (s != TN_OK) return s;
+        TN_CUDA(cudaEventRecord(ev.first, stream));
+    }
+    if (!items.empty()) {
+        TN_CUDA(tn::launch_bind(sliced ? p->bind_sl_dev : p->bind_inv_dev, (int32_t)items.size(),
+                                src, arena, s0, ns, sliced ? p->max_rank_sl : p->max_rank_inv,
+                                stream));
+        p->launches++;
+    }
+    for (const auto &b : tiled) {
+        TN_CUDA(tn::launch_bind_tiled(b, src, arena, s0, ns, stream));
+        p->launches++;
+    }
+    if (p->opts.profile) {
+        TN_CUDA(cudaEventRecord(ev.second, stream));
+        p->pending_bind.push_back(ev);
+    }
+    return TN_OK;
+}
+
 // Autotune a tensor-core step (first full batch): run it once as planned, then launch every
 // applicable kernel variant (tile shape, K tile, 4M or 3M) between CUDA events and keep the
 // fastest.  All variants compute the same result; when 4M wins, the operands' sum planes are
@@ -942,6 +1054,7 @@ tn_status tune_tc_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stre
         if (!tn::tc_variant_fits(v, lk, ln)) continue;
         const int form = tn::tc_variant_form(v);
         if ((st.form == kFormSplit) != (form == 3)) continue;  // split steps stay split
+        if (tn::tc_variant_tf32(v) != tf32_mode(p->mode)) continue;
         if (form == 2 && !three_planes) continue;
         if (p->opts.gemm_form == TN_GEMM_4M && form == 2) continue;
         if (p->opts.gemm_form == TN_GEMM_3M && form == 1) continue;
@@ -1060,7 +1173,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
             cd.dst_sstride = cd.n;
             cd.amax = p->meta + 2 * p->sb * q.meta;
             cd.exps = reinterpret_cast<int32_t *>(p->meta + 2 * p->sb * q.meta + p->sb);
-            cd.bf16 = bf16_mode(p->mode);
+            cd.dtype = operand_dtype(p->mode);
             cd.planes = q.planes;
             if (X.producer < 0) {  // a leaf: no producer epilogue recorded its max-abs
                 TN_CUDA(cudaMemsetAsync(cd.amax, 0, sizeof(unsigned int) * sx, stream));
@@ -1073,6 +1186,37 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         if (prep) TN_CUDA(cudaEventRecord(prep->second, stream));
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_gemm_tc(p->tc_desc[si], slices, stream);
+        if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
+        p->launches += 1;
+    } else if (st.kernel == K_STREAM) {
+        // the operand with more free bits streams (one thread per row), the other is held in
+        // shared memory; A * B = B * A, so the roles follow the sizes
+        const bool swap = st.N.size() > st.M.size();
+        const Tensor &R = swap ? B : A, &Q = swap ? A : B;
+        const std::vector<int> &Rl = swap ? st.N : st.M, &Ql = swap ? st.M : st.N;
+        tn::GemmDesc d{};
+        d.A = arena + R.off;
+        d.B = arena + Q.off;
+        d.C = arena + C.off;
+        d.sA = swap ? sB : sA;
+        d.sB = swap ? sA : sB;
+        d.sC = sC;
+        d.lm = (int)Rl.size();
+        d.ln = (int)Ql.size();
+        d.lk = (int)st.K.size();
+        d.splits = 1;
+        d.amax_out = amax_out;
+        fill_pos(d.posC_m, TN_MAXR, -1);
+        fill_pos(d.posC_n, TN_MAXR, -1);
+        for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(Rl[Rl.size() - 1 - i]);
+        for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(Ql[Ql.size() - 1 - i]);
+        d.tile_bits = 8 + d.ln;
+        tn::sort_tile_bits(8, d.ln, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+        if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
+            return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the thin tile",
+                        (int)(&st - &p->steps[0]));
+        if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
+        e = tn::launch_gemm_thin(d, slices, stream);
         if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
         p->launches += 1;
     } else if (st.kernel == K_GEMM) {
@@ -1179,6 +1323,18 @@ tn_status tn_plan_get_info(const tn_plan_t *p, tn_plan_info *out) {
         }
     }
     out->kernel_launches = p->launches;
+    tn_plan_t *mp = const_cast<tn_plan_t *>(p);
+    for (auto &ev : mp->pending_bind) {
+        float ms_ = 0.f;
+        TN_CUDA(cudaEventSynchronize(ev.second));
+        TN_CUDA(cudaEventElapsedTime(&ms_, ev.first, ev.second));
+        mp->bind_ms += ms_;
+        mp->bind_timed += 1;
+        mp->event_pool.push_back(ev);
+    }
+    mp->pending_bind.clear();
+    out->bind_ms = p->bind_ms;
+    out->bind_launches = p->bind_timed;
     return TN_OK;
 }
 
@@ -1244,11 +1400,11 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
     TN_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) TN_CUDA(cudaSetDevice(p->device));
     float2 *arena = reinterpret_cast<float2 *>(p->arena);
-    const double2 *src = p->net->data;
     // prologue: slice-independent leaves and steps, once per call
-    TN_CUDA(tn::launch_bind(p->bind_inv_dev, (int32_t)p->bind_inv.size(), src, arena, 0, 1,
-                            p->max_rank_inv, stream));
-    if (!p->bind_inv.empty()) p->launches++;
+    {
+        tn_status s = bind_leaves(p, false, 0, 1, stream);
+        if (s != TN_OK) return s;
+    }
     for (auto &st : p->steps)
         if (!st.dep) {
             tn_status s = run_step(p, st, 1, stream);
@@ -1258,9 +1414,10 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
     const int64_t nout = (int64_t)1 << R.rank();
     for (int64_t s0 = slice_begin; s0 < slice_end; s0 += p->sb) {
         const int64_t ns = std::min(p->sb, slice_end - s0);
-        TN_CUDA(tn::launch_bind(p->bind_sl_dev, (int32_t)p->bind_sl.size(), src, arena, s0, ns,
-                                p->max_rank_sl, stream));
-        if (!p->bind_sl.empty()) p->launches++;
+        {
+            tn_status s = bind_leaves(p, true, s0, ns, stream);
+            if (s != TN_OK) return s;
+        }
         if (p->opts.autotune && !p->tuned && ns == p->sb) {
             // first full batch: tune the tensor-core steps while running it
             for (auto &st : p->steps)
@@ -1379,6 +1536,7 @@ void tn_destroy(void *handle) {
         if (p->meta) cudaFree(p->meta);
         if (p->partial) cudaFree(p->partial);
         if (p->amps_tmp) cudaFree(p->amps_tmp);
+        for (auto &ev : p->pending_bind) p->event_pool.push_back(ev);
         for (auto &st : p->steps) {
             for (auto &ev : st.pending) p->event_pool.push_back(ev);
             for (auto &ev : st.pending_prep) p->event_pool.push_back(ev);

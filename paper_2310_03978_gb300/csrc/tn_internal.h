@@ -99,6 +99,31 @@ struct BindItem {
     int8_t sl_pos[8];          // source bit of sliced label t
 };
 
+// Tiled slice binding of one large leaf (a stride-aware bit permutation, Sec. 2.4's
+// permutation done once per leaf, with slicing, Sec. 3.2): the destination is cut into tiles of
+// 2^t elements that hold destination bits 0-5 (contiguous in the destination) and the
+// destination bits of the leaf's five lowest unsliced source bits (contiguous in the source).
+// A block reads a tile in source order (a warp reads 32 consecutive complex128, 512 bytes,
+// 16 bytes per lane), stages it in shared memory and writes it in destination order (16 bytes
+// of two adjacent complex64 per lane).  The remaining destination bits number the tiles.
+struct BindTiled {
+    int64_t dst_off;            // element offset of the destination (complex64) in the arena
+    int64_t dst_sstride;        // slice stride of the destination (0 = invariant leaf)
+    int64_t src_off;            // complex128 element offset in the network buffer
+    int64_t ntiles;             // 2^(rank - t)
+    int32_t t;                  // tile bits (6..11)
+    int32_t nrest;              // rank - t
+    int32_t nsl;                // sliced labels of this leaf
+    int32_t pad_;
+    int8_t e2t[12];             // read-order bit q -> tile bit
+    int8_t e2s[12];             // read-order bit q -> source bit
+    int8_t t2d[12];             // tile bit -> destination bit (bits 0-5 map to themselves)
+    int8_t rest_d[TN_MAXR];     // tile-number bit u -> destination bit
+    int8_t rest_s[TN_MAXR];     // tile-number bit u -> source bit
+    int8_t sl_bit[8];           // which bit of the slice id fixes sliced label j
+    int8_t sl_pos[8];           // source bit of sliced label j
+};
+
 // Sort the bits of an output tile (tm row bits, tn column bits) by their position in C:
 // src[q] = row_tag | i for row bit i, or j for column bit j; pos[q] = position in C.
 void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
@@ -115,9 +140,15 @@ __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st);
 int gemm_simt_splits(int lm, int ln, int lk, int64_t slices);
+// Thin steps on the CUDA cores: A is the operand with 2^lm >= 256 rows, B has 2^ln <= 16 rows,
+// 2 <= K <= 64; tile_bits = 8 + ln with tb_src / tb_pos sorted as for the tensor-core epilogue
+// (row bits tagged 128 | bit); complex64 output only.
+cudaError_t launch_gemm_thin(const GemmDesc &d, int64_t slices, cudaStream_t st);
 cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double2 *src,
                         float2 *arena, int64_t slice_begin, int64_t slices, int32_t max_rank,
                         cudaStream_t st);
+cudaError_t launch_bind_tiled(const BindTiled &b, const double2 *src, float2 *arena,
+                              int64_t slice_begin, int64_t slices, cudaStream_t st);
 cudaError_t launch_accumulate(const float2 *root, int64_t root_sstride, int64_t n, int64_t slices,
                               double2 *amps, cudaStream_t st);
 cudaError_t launch_readout(const double2 *amps, int64_t n, double *partial, int32_t n_partial,
@@ -134,15 +165,15 @@ struct ConvertDesc {
     int64_t dst_sstride;       // elements between slices inside one plane
     unsigned int *amax;        // per slice, float bits of max(|re|, |im|)
     int32_t *exps;             // per slice exponent e: stored = value * 2^-e
-    int32_t bf16;              // 0 = fp16, 1 = bf16
+    int32_t dtype;             // 0 = fp16, 1 = bf16, 2 = FP32 rounded to TF32
     int32_t planes;            // 2: re, im; 3: re, im, re + im (3M); 4: re, im, re_lo, im_lo
 };
 cudaError_t launch_amax(const ConvertDesc &d, int64_t slices, cudaStream_t st);
 cudaError_t launch_convert16(const ConvertDesc &d, int64_t slices, cudaStream_t st);
 
 struct TcGemmDesc {
-    CUtensorMap tmA;           // planar 16-bit A: [planes * slices_a][M][K]: re, im (, re+im)
-    CUtensorMap tmB;           // planar 16-bit B: [planes * slices_b][N][K]
+    CUtensorMap tmA;           // planar A: [planes * slices_a][M][K]: re, im (, re+im | lo)
+    CUtensorMap tmB;           // planar B: [planes * slices_b][N][K]
     float2 *C;
     int64_t sC;
     int32_t lm, ln, lk;
@@ -150,9 +181,9 @@ struct TcGemmDesc {
     int64_t slices_a, slices_b;  // slices stored per plane (1 when shared)
     const int32_t *expA;       // per slice exponents of A and B (index 0 if shared)
     const int32_t *expB;
-    int32_t form;              // 1 = 4M, 2 = 3M
-    int32_t bf16;
-    int32_t bk;                // K tile: 64 (128-byte swizzle) or 32 (64-byte swizzle)
+    int32_t form;              // 1 = 4M, 2 = 3M, 3 = split 4M
+    int32_t dtype;             // operands: 0 = fp16, 1 = bf16 (kind::f16), 2 = TF32 (kind::tf32)
+    int32_t bk;                // K elements per stage (rows of 64 or 128 bytes)
     int32_t variant;           // kernel variant (tile shape, stages, CTAs per SM)
     unsigned int *amax_out;    // optional: per slice max(|re|, |im|) of C (float bits, atomicMax)
     int32_t planar_out;        // 1: write C as PlanarOut `pout` instead of complex64
@@ -172,13 +203,15 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 unsigned int tc_status_read_and_clear();
 // Self-test of the bounded waits (see tn_selftest_wait_timeout in tn.h).
 tn_status tc_selftest_wait_timeout(int32_t limit_ms, cudaStream_t st);
-// Encode a 3-D tensor map over planar 16-bit data [planes*slices][rows][K] (K contiguous),
-// box {bk, 128, 1} with the 128-byte (bk 64) or 64-byte (bk 32) swizzle.
-int encode_tmap_planar16(void *tmap_host, const void *base, int64_t K, int64_t rows,
-                         int64_t depth, int bf16, int bk, int box_rows);
-// Tensor-core kernel variants: pick one for a step (form 1 = 4M, 2 = 3M; preferences 0 = any),
-// and read its K tile and N tile.
-int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref);
+// Encode a 3-D tensor map over planar data [planes*slices][rows][K] (K contiguous; dtype 0
+// fp16, 1 bf16, 2 fp32), box {bk, box_rows, 1} with the 128-byte swizzle for rows of 128 bytes
+// (bk * element size) or the 64-byte swizzle for rows of 64 bytes.
+int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t rows,
+                       int64_t depth, int dtype, int bk, int box_rows);
+// Tensor-core kernel variants: pick one for a step (form 1 = 4M, 2 = 3M, 3 = split; preferences
+// 0 = any), and read its K tile (elements per stage), N tile and operand type.
+int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf32);
+bool tc_variant_tf32(int variant);
 int tc_variant_bk(int variant);
 int tc_variant_bn(int variant);
 int tc_variant_form(int variant);  // 1 = 4M, 2 = 3M, 3 = split 4M (hi/lo planes)

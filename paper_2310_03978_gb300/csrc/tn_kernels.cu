@@ -96,6 +96,82 @@ __global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
     }
 }
 
+// Tiled leaf binding (see BindTiled).  Shared memory holds one tile of up to 2^11 complex64; the
+// element of tile index tau sits at tau ^ (((tau >> 6) & 31) << 1).  The XOR changes bits 1-5
+// only, so the two elements of a destination pair stay adjacent and 16-byte aligned, and when
+// the source's low bits land on tile bits 6-10 the 32 lanes of a read still write 32 distinct
+// 16-byte slots of one 512-byte row.
+__device__ __forceinline__ int tile_slot(int tau) { return tau ^ (((tau >> 6) & 31) << 1); }
+
+__global__ void __launch_bounds__(256) k_bind_tiled(BindTiled b, const double2 *__restrict__ src,
+                                                    float2 *__restrict__ arena,
+                                                    int64_t slice_begin) {
+    __shared__ __align__(16) float2 tile[2048];
+    const int64_t s = blockIdx.y;
+    const uint64_t sigma = (uint64_t)(slice_begin + s);
+    uint64_t soff = 0;
+    for (int j = 0; j < b.nsl; ++j)
+        if ((sigma >> b.sl_bit[j]) & 1ull) soff |= 1ull << b.sl_pos[j];
+    const double2 *S = src + b.src_off + soff;
+    float2 *D = arena + b.dst_off + s * b.dst_sstride;
+    const int n = 1 << b.t;
+    const int tid = threadIdx.x;
+    // read-order index e = tid + 256 k: its tile index and source offset are those of tid OR'ed
+    // with those of 256 k (disjoint bits)
+    int tau0 = 0;
+    uint64_t so0 = 0;
+    for (int q = 0; q < 8 && q < b.t; ++q)
+        if ((tid >> q) & 1) {
+            tau0 |= 1 << b.e2t[q];
+            so0 |= 1ull << b.e2s[q];
+        }
+    // write-order pair j = tid + 256 k covers tile indices 2 j, 2 j + 1; destination bits of
+    // tile bits 6-8 come from tid, those of tile bits 9 and up from k
+    uint64_t dw0 = 0;
+    for (int q = 6; q < 9 && q < b.t; ++q)
+        if (((2 * tid) >> q) & 1) dw0 |= 1ull << b.t2d[q];
+    for (int64_t w = blockIdx.x; w < b.ntiles; w += gridDim.x) {
+        uint64_t dbase = 0, sbase = 0;
+        for (int u = 0; u < b.nrest; ++u)
+            if ((w >> u) & 1) {
+                dbase |= 1ull << b.rest_d[u];
+                sbase |= 1ull << b.rest_s[u];
+            }
+        // all of a thread's (up to 8) loads are issued before any is used
+        double2 v[8];
+        int slot[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if ((k << 8) + tid < n) {
+                int tau = tau0;
+                uint64_t so = so0;
+                for (int q = 8; q < b.t; ++q)
+                    if ((k >> (q - 8)) & 1) {
+                        tau |= 1 << b.e2t[q];
+                        so |= 1ull << b.e2s[q];
+                    }
+                v[k] = S[sbase | so];
+                slot[k] = tile_slot(tau);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if ((k << 8) + tid < n) tile[slot[k]] = make_float2((float)v[k].x, (float)v[k].y);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((k << 8) + tid >= (n >> 1)) break;
+            const int tau = 2 * (tid + (k << 8));
+            uint64_t doff = dbase | dw0 | (uint64_t)(tau & 63);
+            for (int q = 9; q < b.t; ++q)
+                if ((tau >> q) & 1) doff |= 1ull << b.t2d[q];
+            *reinterpret_cast<float4 *>(D + doff) =
+                *reinterpret_cast<const float4 *>(&tile[tile_slot(tau)]);
+        }
+        __syncthreads();
+    }
+}
+
 // amps[x] += sum over slices s (in increasing order) of root[s][x], in FP64.
 __global__ void k_accumulate(const float2 *root, int64_t sstride, int64_t n, int64_t slices,
                              double2 *amps) {
@@ -196,17 +272,32 @@ __device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat162>(float a, float b
     return __floats2bfloat162_rn(a, b);
 }
 
+// FP32 rounded to the nearest TF32 value (10 fraction bits, ties away from zero), kept in an
+// FP32 container: the tensor core then reads it without further rounding.
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+template <>
+__device__ __forceinline__ float2 pack2<float2>(float a, float b) {
+    return make_float2(round_tf32(a), round_tf32(b));
+}
+
 __device__ __forceinline__ float2 unpack2(__half2 h) { return __half22float2(h); }
 __device__ __forceinline__ float2 unpack2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+__device__ __forceinline__ float2 unpack2(float2 h) { return h; }
 
+// T2 is a pair of stored elements (two 16-bit numbers, or two FP32 for TF32); the planes and
+// strides of d count elements.
 template <typename T2>
 __device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, int e) {
+    using T = decltype(T2().x);
     const float2 *src = d.src + s * d.src_sstride;
-    T2 *re = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) + s * d.dst_sstride);
-    T2 *im = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) + s * d.dst_sstride +
-                                    d.plane_stride);
-    T2 *sm = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) + s * d.dst_sstride +
-                                    2 * d.plane_stride);
+    T *base = reinterpret_cast<T *>(d.dst) + s * d.dst_sstride;
+    T2 *re = reinterpret_cast<T2 *>(base);
+    T2 *im = reinterpret_cast<T2 *>(base + d.plane_stride);
+    T2 *sm = reinterpret_cast<T2 *>(base + 2 * d.plane_stride);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (d.n >> 1);
          i += (int64_t)gridDim.x * blockDim.x) {
         const float4 v = reinterpret_cast<const float4 *>(src)[i];
@@ -220,8 +311,7 @@ __device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, in
             // lo planes: the rounding residuals x - hi (exact in FP32), rounded again
             const float2 rf = unpack2(rh), jf = unpack2(ih);
             sm[i] = pack2<T2>(r0 - rf.x, r1 - rf.y);
-            T2 *iml = reinterpret_cast<T2 *>(reinterpret_cast<uint16_t *>(d.dst) +
-                                             s * d.dst_sstride + 3 * d.plane_stride);
+            T2 *iml = reinterpret_cast<T2 *>(base + 3 * d.plane_stride);
             iml[i] = pack2<T2>(i0 - jf.x, i1 - jf.y);
         }
     }
@@ -231,7 +321,8 @@ __global__ void __launch_bounds__(256) k_convert16(ConvertDesc d) {
     const int64_t s = blockIdx.y;
     const int e = scale_exponent(d.amax[s]);
     if (blockIdx.x == 0 && threadIdx.x == 0) d.exps[s] = e;
-    if (d.bf16) convert_body<__nv_bfloat162>(d, s, e);
+    if (d.dtype == 2) convert_body<float2>(d, s, e);
+    else if (d.dtype == 1) convert_body<__nv_bfloat162>(d, s, e);
     else convert_body<__half2>(d, s, e);
 }
 
@@ -263,6 +354,17 @@ cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double
     if (chunks < 1) chunks = 1;
     k_bind<<<dim3((unsigned)n_items, (unsigned)slices, (unsigned)chunks), threads, 0, st>>>(
         items_dev, src, arena, slice_begin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bind_tiled(const BindTiled &b, const double2 *src, float2 *arena,
+                              int64_t slice_begin, int64_t slices, cudaStream_t st) {
+    if (slices <= 0) return cudaSuccess;
+    if (b.t < 6 || b.t > 11 || slices > 65535 || b.ntiles < 1) return cudaErrorInvalidValue;
+    int64_t gx = (152 * 8 + slices - 1) / slices;
+    if (gx > b.ntiles) gx = b.ntiles;
+    k_bind_tiled<<<dim3((unsigned)gx, (unsigned)slices), 256, 0, st>>>(b, src, arena,
+                                                                       slice_begin);
     return cudaGetLastError();
 }
 

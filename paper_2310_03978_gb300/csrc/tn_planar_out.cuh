@@ -69,4 +69,52 @@ __device__ __forceinline__ void planar_out_store2(const PlanarOut &o, int64_t s,
     }
 }
 
+// Store eight consecutive complex values (offsets off .. off + 7, off a multiple of 8) into the
+// planar output as one 16-byte word (8 x 16 bits) per plane.
+template <typename T2>
+__device__ __forceinline__ T2 pack_pair(float a, float b);
+template <>
+__device__ __forceinline__ __half2 pack_pair<__half2>(float a, float b) {
+    return __floats2half2_rn(a, b);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat162 pack_pair<__nv_bfloat162>(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ float2 unpack_pair(__half2 h) { return __half22float2(h); }
+__device__ __forceinline__ float2 unpack_pair(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+
+template <typename T2>
+__device__ __forceinline__ void planar_out_store8_t(const PlanarOut &o, int64_t s, uint64_t off,
+                                                    const float2 (&v)[8], int e) {
+    union Row {
+        uint4 u;
+        T2 h[4];
+    } re, im, p2, p3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float r0 = ldexpf(v[2 * j].x, -e), i0 = ldexpf(v[2 * j].y, -e);
+        const float r1 = ldexpf(v[2 * j + 1].x, -e), i1 = ldexpf(v[2 * j + 1].y, -e);
+        re.h[j] = pack_pair<T2>(r0, r1);
+        im.h[j] = pack_pair<T2>(i0, i1);
+        if (o.planes == 3) p2.h[j] = pack_pair<T2>(r0 + i0, r1 + i1);
+        if (o.planes == 4) {
+            const float2 rf = unpack_pair(re.h[j]), jf = unpack_pair(im.h[j]);
+            p2.h[j] = pack_pair<T2>(r0 - rf.x, r1 - rf.y);
+            p3.h[j] = pack_pair<T2>(i0 - jf.x, i1 - jf.y);
+        }
+    }
+    uint16_t *base = static_cast<uint16_t *>(o.base) + s * o.sstride + (int64_t)off;
+    *reinterpret_cast<uint4 *>(base) = re.u;
+    *reinterpret_cast<uint4 *>(base + o.plane_stride) = im.u;
+    if (o.planes >= 3) *reinterpret_cast<uint4 *>(base + 2 * o.plane_stride) = p2.u;
+    if (o.planes == 4) *reinterpret_cast<uint4 *>(base + 3 * o.plane_stride) = p3.u;
+}
+
+__device__ __forceinline__ void planar_out_store8(const PlanarOut &o, int64_t s, uint64_t off,
+                                                  const float2 (&v)[8], int e) {
+    if (o.bf16) planar_out_store8_t<__nv_bfloat162>(o, s, off, v, e);
+    else planar_out_store8_t<__half2>(o, s, off, v, e);
+}
+
 }  // namespace tn

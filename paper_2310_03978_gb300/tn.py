@@ -46,7 +46,8 @@ class PlanInfo(C.Structure):
                 ("tmc_per_slice", C.c_double), ("num_tc_steps", C.c_int32),
                 ("num_gemm_steps", C.c_int32), ("num_stream_steps", C.c_int32),
                 ("num_generic_steps", C.c_int32), ("kernel_launches", C.c_int64),
-                ("reserved", C.c_int32 * 6)]
+                ("bind_ms", C.c_double), ("bind_launches", C.c_int64),
+                ("reserved", C.c_int32 * 2)]
 
 
 class StepInfo(C.Structure):

@@ -4,6 +4,7 @@ Tolerances (amplitude relative L2 error against FP64):
   complex64 path            <= 1e-5
   FP16 / BF16 scaled path   <= 5e-3 (FP16), 1e-2 (BF16: 8-bit significand on the dense steps)
   compensated FP16 / BF16   <= 1e-5 / 1e-4 (hi + lo operand planes, three products)
+  TF32 / 3xTF32             <= 5e-3 / 1e-5 (10-bit significand like FP16; hi + lo as above)
 and for the full-size circuit the ideal-sample XEB (2^n sum p^2 / sum p - 1) within 1e-3
 relative of the state-vector value.
 """
@@ -24,8 +25,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # held to the complex64 bar; a whole circuit adds ~7 such steps and its FP32 steps, hence 5e-5
 # there (CIRCUIT_TOL).  split_bf16: ~2^-16 per product.  mixed: bounded by its FP16 steps.
 TOL = {"c64": 1e-5, "fp16_scaled": 5e-3, "bf16_scaled": 1e-2, "split_fp16": 1e-5,
-       "split_bf16": 1e-4, "mixed": 5e-3}
-CIRCUIT_TOL = dict(TOL, split_fp16=5e-5)
+       "split_bf16": 1e-4, "mixed": 5e-3, "tf32": 5e-3, "split_tf32": 1e-5}
+CIRCUIT_TOL = dict(TOL, split_fp16=5e-5, split_tf32=5e-5)
 
 
 @pytest.fixture(scope="module")
@@ -183,13 +184,35 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
     check(got2, ref2, 1e-5)
 
 
+@pytest.mark.parametrize("shape", [(12, 4, 4), (10, 2, 6), (4, 11, 3), (13, 0, 2), (11, 3, 1),
+                                   (1, 12, 5)])
+def test_thin_steps_stream_kernel(tn, shape):
+    # a short contraction of a large operand with one of at most 16 free elements: one thread
+    # per row of the large operand (the small one may be either side); 2 slices in flight too
+    rng = np.random.default_rng(500 + 3 * shape[0] + 5 * shape[1] + shape[2])
+    tensors, labels, out = single_step(rng, *shape)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)])
+    assert kernels == ["stream"]
+    check(got, ref, 1e-5)
+    A, B = tensors
+    v = crandn(rng, 1)
+    t2 = [A[None] * v.reshape(2, *([1] * A.ndim)), B, np.ones(2, complex)]
+    l2 = [[900] + labels[0], labels[1], [900]]
+    ref2 = O.contract(t2, l2, out, [(0, 1), (0, 2)])
+    for mode in ("c64", "fp16_scaled"):
+        got2, info, k2 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode=mode)
+        assert info["slices_in_flight"] == 2 and k2[0] == "stream"
+        check(got2, ref2, 1e-5)
+
+
 # (form, K-tile preference, N-tile preference): every tensor-core kernel variant
 TC_VARIANTS = [("4m", 0, 0), ("4m", 64, 0), ("4m", 32, 0), ("4m", 0, 256), ("3m", 32, 0),
                ("3m", 64, 0)]
 
 
 @pytest.mark.parametrize("form,bk,bn", TC_VARIANTS)
-@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled"])
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled", "tf32"])
 @pytest.mark.parametrize("shape", [(7, 7, 6), (9, 8, 7), (8, 10, 8), (8, 8, 10)])
 def test_single_step_tensor_core(tn, mode, shape, form, bk, bn):
     rng = np.random.default_rng(7 + sum(shape))
@@ -201,7 +224,7 @@ def test_single_step_tensor_core(tn, mode, shape, form, bk, bn):
     check(got, ref, TOL[mode])
 
 
-@pytest.mark.parametrize("mode", ["split_fp16", "split_bf16"])
+@pytest.mark.parametrize("mode", ["split_fp16", "split_bf16", "split_tf32"])
 @pytest.mark.parametrize("bn", [0, 256])
 @pytest.mark.parametrize("shape", [(7, 7, 6), (9, 8, 7), (8, 10, 10), (10, 10, 3)])
 def test_compensated_products_on_tensor_cores(tn, mode, bn, shape):
@@ -238,7 +261,7 @@ def test_short_contraction_on_tensor_cores(tn, shape):
     rng = np.random.default_rng(70 + sum(shape))
     tensors, labels, out = single_step(rng, *shape)
     ref = O.contract(tensors, labels, out, [(0, 1)])
-    for mode in ("fp16_scaled", "bf16_scaled"):
+    for mode in ("fp16_scaled", "bf16_scaled", "tf32"):
         got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode=mode)
         assert kernels == ["gemm_tc"]
         check(got, ref, TOL[mode])
@@ -286,6 +309,21 @@ def test_tensor_core_step_with_slices_in_flight(tn):
 
 
 @pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+@pytest.mark.parametrize("lm,ln,lk,nsl", [(10, 4, 8, 3), (14, 3, 8, 0), (6, 9, 12, 2)])
+def test_large_leaves_tiled_permutation_with_slices(tn, mode, lm, ln, lk, nsl):
+    # leaves of rank >= 12 are bound by the tiled permutation kernel: random label orders, and
+    # sliced labels (contracted between A and B) at random source bit positions
+    rng = np.random.default_rng(300 + lm + 7 * ln + 13 * lk + nsl)
+    tensors, labels, out = single_step(rng, lm, ln, lk)
+    K = [l for l in labels[0] if l >= 200]
+    sliced = [int(x) for x in rng.choice(K, size=nsl, replace=False)] if nsl else []
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, info, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], sliced, mode=mode)
+    assert info["num_slices"] == 1 << nsl
+    check(got, ref, TOL[mode])
+
+
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
 def test_graph_replay_matches_direct_launches(tn, mode):
     wl = W.small_workload()
     net = wl.network
@@ -304,7 +342,8 @@ def test_graph_replay_matches_direct_launches(tn, mode):
     tnet.close()
 
 
-@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled", "split_fp16", "split_bf16"])
+@pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled", "split_fp16", "split_bf16",
+                                  "tf32", "split_tf32"])
 @pytest.mark.parametrize("lk1,first", [(7, "gemm_tc"), (5, "gemm_simt"), (1, "generic")])
 def test_chained_steps_feed_the_tensor_cores(tn, lk1, first, mode):
     # step 1 writes the operand of tensor-core step 2 directly as planar 16-bit numbers, with an
@@ -370,7 +409,8 @@ def test_host_entry_points_and_set_data(tn):
 # ------------------------------------------------------------------ the full-size circuit
 @pytest.mark.parametrize("mode,form", [("c64", "auto"), ("fp16_scaled", "4m"),
                                        ("fp16_scaled", "3m"), ("split_fp16", "auto"),
-                                       ("mixed", "auto"), ("bf16_scaled", "4m")])
+                                       ("mixed", "auto"), ("bf16_scaled", "4m"),
+                                       ("tf32", "auto"), ("split_tf32", "auto")])
 def test_bench_circuit_full_size(tn, mode, form):
     golden = os.path.join(HERE, "golden", "sycamore_5x6_c14_open10_s4.amps.txt")
     if not os.path.exists(golden):
