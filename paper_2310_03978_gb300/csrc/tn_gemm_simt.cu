@@ -206,8 +206,8 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 }
 
 // Thin steps (the low-intensity contractions of App. A.2): C[m, n] = sum_k A[m, k] B[n, k] with
-// few columns (N = NT <= 16) and a short contraction (K <= 64).  One thread owns one row m of A
-// and all NT outputs of that row.  B is held in shared memory as [K][NT] and read as broadcast
+// few columns (N = NT <= 16) and a short contraction (K <= 64, summed in one FP32 chain per
+// output: at most 64 terms).  One thread owns one row m of A and all NT outputs of that row.  B is held in shared memory as [K][NT] and read as broadcast
 // 16-byte pairs; the block's 256 rows of A are staged through shared memory in chunks of 16 of
 // K with coalesced 16-byte loads.  A step whose small operand is A runs with the roles swapped
 // (the complex product commutes).  The tile (256 x NT) is staged and written in C's order with
@@ -215,7 +215,7 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
 
 template <int NT>
-__global__ void __launch_bounds__(256) k_gemm_thin(GemmDesc d) {
+__global__ void __launch_bounds__(256, 3) k_gemm_thin(GemmDesc d) {
     __shared__ __align__(16) float2 sA[kThinRows * kThinLd];
     __shared__ __align__(16) float2 sB[64 * (NT < 2 ? 2 : NT)];
     constexpr int NB = NT < 2 ? 2 : NT;  // row stride of sB (pairs stay 16-byte aligned)
@@ -243,9 +243,6 @@ __global__ void __launch_bounds__(256) k_gemm_thin(GemmDesc d) {
             sA[r * kThinLd + 2 * q + 1] = make_float2(v.z, v.w);
         }
         __syncthreads();
-        float tr[NT], ti[NT];
-#pragma unroll
-        for (int n = 0; n < NT; ++n) tr[n] = ti[n] = 0.f;
         for (int k = 0; k < kw; ++k) {
             const float2 a = sA[tid * kThinLd + k];
             const float2 *bk = sB + (kc + k) * NB;
@@ -260,22 +257,17 @@ __global__ void __launch_bounds__(256) k_gemm_thin(GemmDesc d) {
                     b0 = bk[0];
                     b1 = b0;
                 }
-                tr[n] = fmaf(a.x, b0.x, tr[n]);
-                tr[n] = fmaf(-a.y, b0.y, tr[n]);
-                ti[n] = fmaf(a.x, b0.y, ti[n]);
-                ti[n] = fmaf(a.y, b0.x, ti[n]);
+                cr[n] = fmaf(a.x, b0.x, cr[n]);
+                cr[n] = fmaf(-a.y, b0.y, cr[n]);
+                ci[n] = fmaf(a.x, b0.y, ci[n]);
+                ci[n] = fmaf(a.y, b0.x, ci[n]);
                 if (n + 1 < NT) {
-                    tr[n + 1] = fmaf(a.x, b1.x, tr[n + 1]);
-                    tr[n + 1] = fmaf(-a.y, b1.y, tr[n + 1]);
-                    ti[n + 1] = fmaf(a.x, b1.y, ti[n + 1]);
-                    ti[n + 1] = fmaf(a.y, b1.x, ti[n + 1]);
+                    cr[n + 1] = fmaf(a.x, b1.x, cr[n + 1]);
+                    cr[n + 1] = fmaf(-a.y, b1.y, cr[n + 1]);
+                    ci[n + 1] = fmaf(a.x, b1.y, ci[n + 1]);
+                    ci[n + 1] = fmaf(a.y, b1.x, ci[n + 1]);
                 }
             }
-        }
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            cr[n] += tr[n];
-            ci[n] += ti[n];
         }
     }
     __syncthreads();

@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
         float2 *stage = reinterpret_cast<float2 *>(smem);
         uint64_t *hi_off = reinterpret_cast<uint64_t *>(smem + BM * SLD * 8);
         int *hi_w = reinterpret_cast<int *>(hi_off + 64);
-        const int e = d.expA[sa] + d.expB[sbi];
+        const Pow2 pe = pow2_of(d.expA[sa] + d.expB[sbi]);
         // epilogue threads: all four warps, or the four fold warps (the running sums) when
         // promoting; et is the epilogue thread index 0..127
         const bool epi = !PROMOTE || warp >= 2;
@@ -503,8 +503,8 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         stage[row * SLD + (c0 - cb) + j] =
-                            make_float2(ldexpf(__uint_as_float(r0[j]), e),
-                                        ldexpf(__uint_as_float(r1[j]), e));
+                            make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
+                                        scale_pow2(__uint_as_float(r1[j]), pe));
                 } else {
                     uint32_t r2[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)(2 * BN + c0), r2);
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
                         const float p1 = __uint_as_float(r0[j]), p2 = __uint_as_float(r1[j]);
                         const float p3 = __uint_as_float(r2[j]);
                         stage[row * SLD + (c0 - cb) + j] =
-                            make_float2(ldexpf(p1 - p2, e), ldexpf(p3 - p1 - p2, e));
+                            make_float2(scale_pow2(p1 - p2, pe), scale_pow2(p3 - p1 - p2, pe));
                     }
                 }
             }

@@ -811,7 +811,11 @@ tn::BindItem make_bind(const tn_plan_t *p, const Tensor &t) {
 // ones (gates, projectors) are gathered many per launch by k_bind.
 constexpr int kTiledBindMinRank = 12;
 
-// Tile tables of a large leaf (see tn::BindTiled) from its gather description.
+// Tile tables of a large leaf (see tn::BindTiled) from its gather description.  The tile holds
+// destination bits 0-5 and the destination bits of the six lowest unsliced source bits (runs
+// of 1 KiB in the source); while it has fewer than 11 bits (the two sets overlap) it grows by
+// the next destination bit and the next source bit in turn.  A block reads the tile with its
+// bits in source order, so consecutive threads read consecutive source addresses.
 tn::BindTiled make_bind_tiled(const tn::BindItem &it) {
     tn::BindTiled b{};
     b.dst_off = it.dst_off;
@@ -823,28 +827,37 @@ tn::BindTiled make_bind_tiled(const tn::BindItem &it) {
         b.sl_pos[j] = it.sl_pos[j];
     }
     const int r = it.rank;
-    // destination bits ordered by their source bit: the first five are the lowest unsliced
-    // source bits
+    // destination bits ordered by their source bit
     std::vector<std::pair<int, int>> by_src;
     for (int i = 0; i < r; ++i) by_src.push_back({it.pos_src[i], i});
     std::sort(by_src.begin(), by_src.end());
-    std::vector<int> low;
-    for (int j = 0; j < 5 && j < r; ++j) low.push_back(by_src[j].second);
+    std::vector<bool> in(r, false);
+    int nd = 0, ns = 0, t = 0;
+    auto add = [&](int d) {
+        if (!in[d]) {
+            in[d] = true;
+            t++;
+        }
+    };
+    for (; nd < 6 && nd < r; ++nd) add(nd);
+    for (; ns < 6 && ns < r; ++ns) add(by_src[ns].second);
+    for (bool dst_turn = true; t < 11 && (nd < r || ns < r); dst_turn = !dst_turn) {
+        if (dst_turn && nd < r) add(nd++);
+        else if (!dst_turn && ns < r) add(by_src[ns++].second);
+    }
+    // tile bits: destination bits 0-5 first, then the others in destination order
     std::vector<int> tile_d;
-    for (int d = 0; d < 6; ++d) tile_d.push_back(d);
-    std::vector<int> extra;
-    for (int d : low)
-        if (d >= 6) extra.push_back(d);
-    std::sort(extra.begin(), extra.end());
-    for (int d : extra) tile_d.push_back(d);
+    for (int d = 0; d < r; ++d)
+        if (in[d]) tile_d.push_back(d);
     b.t = (int)tile_d.size();
     auto tile_bit = [&](int d) {
         return (int)(std::find(tile_d.begin(), tile_d.end(), d) - tile_d.begin());
     };
     for (int q = 0; q < 12; ++q) b.t2d[q] = q < b.t ? (int8_t)tile_d[q] : (int8_t)-1;
-    std::vector<int> order = low;  // read order: source-contiguous bits first
-    for (int d : tile_d)
-        if (std::find(low.begin(), low.end(), d) == low.end()) order.push_back(d);
+    // read order: the tile's bits by increasing source bit
+    std::vector<int> order;
+    for (auto &x : by_src)
+        if (in[x.second]) order.push_back(x.second);
     for (int q = 0; q < 12; ++q) {
         b.e2t[q] = q < b.t ? (int8_t)tile_bit(order[q]) : (int8_t)-1;
         b.e2s[q] = q < b.t ? it.pos_src[order[q]] : (int8_t)-1;
@@ -853,7 +866,7 @@ tn::BindTiled make_bind_tiled(const tn::BindItem &it) {
     fill_pos(b.rest_s, TN_MAXR, -1);
     int u = 0;
     for (int d = 0; d < r; ++d)
-        if (std::find(tile_d.begin(), tile_d.end(), d) == tile_d.end()) {
+        if (!in[d]) {
             b.rest_d[u] = (int8_t)d;
             b.rest_s[u] = it.pos_src[d];
             u++;

@@ -102,7 +102,7 @@ struct BindItem {
 // Tiled slice binding of one large leaf (a stride-aware bit permutation, Sec. 2.4's
 // permutation done once per leaf, with slicing, Sec. 3.2): the destination is cut into tiles of
 // 2^t elements that hold destination bits 0-5 (contiguous in the destination) and the
-// destination bits of the leaf's five lowest unsliced source bits (contiguous in the source).
+// destination bits of the leaf's six lowest unsliced source bits (contiguous in the source).
 // A block reads a tile in source order (a warp reads 32 consecutive complex128, 512 bytes,
 // 16 bytes per lane), stages it in shared memory and writes it in destination order (16 bytes
 // of two adjacent complex64 per lane).  The remaining destination bits number the tiles.
@@ -111,7 +111,7 @@ struct BindTiled {
     int64_t dst_sstride;        // slice stride of the destination (0 = invariant leaf)
     int64_t src_off;            // complex128 element offset in the network buffer
     int64_t ntiles;             // 2^(rank - t)
-    int32_t t;                  // tile bits (6..11)
+    int32_t t;                  // tile bits (11..12, fewer only for ranks below 11)
     int32_t nrest;              // rank - t
     int32_t nsl;                // sliced labels of this leaf
     int32_t pad_;
@@ -129,6 +129,26 @@ struct BindTiled {
 void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
                     int8_t *src, int8_t *pos);
 
+
+// Exact power-of-two scaling: x * 2^e rounded once, like ldexpf(x, e), as one multiplication by
+// the float 2^e whenever 2^e is representable (-149 <= e <= 127; subnormal below -126), which
+// is the case for every exponent the scaling produces in practice; ldexpf otherwise.
+struct Pow2 {
+    float f;
+    int e;
+    bool exact;
+};
+__device__ __forceinline__ Pow2 pow2_of(int e) {
+    Pow2 p;
+    p.e = e;
+    p.exact = e >= -149 && e <= 127;
+    p.f = e >= -126 ? __int_as_float((min(e, 127) + 127) << 23)
+                    : __int_as_float(1 << (max(e, -149) + 149));
+    return p;
+}
+__device__ __forceinline__ float scale_pow2(float x, const Pow2 &p) {
+    return p.exact ? x * p.f : ldexpf(x, p.e);
+}
 
 // Warp-reduced atomicMax of a non-negative float into *slot (float bits order like unsigned).
 __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {

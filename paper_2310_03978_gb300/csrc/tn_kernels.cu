@@ -96,17 +96,19 @@ __global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
     }
 }
 
-// Tiled leaf binding (see BindTiled).  Shared memory holds one tile of up to 2^11 complex64; the
-// element of tile index tau sits at tau ^ (((tau >> 6) & 31) << 1).  The XOR changes bits 1-5
-// only, so the two elements of a destination pair stay adjacent and 16-byte aligned, and when
-// the source's low bits land on tile bits 6-10 the 32 lanes of a read still write 32 distinct
+// Tiled leaf binding (see BindTiled).  Shared memory holds one tile of up to MAXN complex64
+// (2^11, or 2^12 when the six lowest source bits all lie above destination bit 5); the element
+// of tile index tau sits at tau ^ (((tau >> 6) & 31) << 1).  The XOR changes bits 1-5 only, so
+// the two elements of a destination pair stay adjacent and 16-byte aligned, and when the
+// source's low bits land on tile bits 6-10 the 32 lanes of a read still write 32 distinct
 // 16-byte slots of one 512-byte row.
 __device__ __forceinline__ int tile_slot(int tau) { return tau ^ (((tau >> 6) & 31) << 1); }
 
+template <int MAXN>
 __global__ void __launch_bounds__(256) k_bind_tiled(BindTiled b, const double2 *__restrict__ src,
                                                     float2 *__restrict__ arena,
                                                     int64_t slice_begin) {
-    __shared__ __align__(16) float2 tile[2048];
+    __shared__ __align__(16) float2 tile[MAXN];
     const int64_t s = blockIdx.y;
     const uint64_t sigma = (uint64_t)(slice_begin + s);
     uint64_t soff = 0;
@@ -137,30 +139,19 @@ __global__ void __launch_bounds__(256) k_bind_tiled(BindTiled b, const double2 *
                 dbase |= 1ull << b.rest_d[u];
                 sbase |= 1ull << b.rest_s[u];
             }
-        // all of a thread's (up to 8) loads are issued before any is used
-        double2 v[8];
-        int slot[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if ((k << 8) + tid < n) {
-                int tau = tau0;
-                uint64_t so = so0;
-                for (int q = 8; q < b.t; ++q)
-                    if ((k >> (q - 8)) & 1) {
-                        tau |= 1 << b.e2t[q];
-                        so |= 1ull << b.e2s[q];
-                    }
-                v[k] = S[sbase | so];
-                slot[k] = tile_slot(tau);
-            }
+        for (int k = 0; (k << 8) + tid < n; ++k) {
+            int tau = tau0;
+            uint64_t so = so0;
+            for (int q = 8; q < b.t; ++q)
+                if ((k >> (q - 8)) & 1) {
+                    tau |= 1 << b.e2t[q];
+                    so |= 1ull << b.e2s[q];
+                }
+            const double2 v = S[sbase | so];
+            tile[tile_slot(tau)] = make_float2((float)v.x, (float)v.y);
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if ((k << 8) + tid < n) tile[slot[k]] = make_float2((float)v[k].x, (float)v[k].y);
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if ((k << 8) + tid >= (n >> 1)) break;
+        for (int k = 0; (k << 8) + tid < (n >> 1); ++k) {
             const int tau = 2 * (tid + (k << 8));
             uint64_t doff = dbase | dw0 | (uint64_t)(tau & 63);
             for (int q = 9; q < b.t; ++q)
@@ -293,6 +284,7 @@ __device__ __forceinline__ float2 unpack2(float2 h) { return h; }
 template <typename T2>
 __device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, int e) {
     using T = decltype(T2().x);
+    const Pow2 pe = pow2_of(-e);
     const float2 *src = d.src + s * d.src_sstride;
     T *base = reinterpret_cast<T *>(d.dst) + s * d.dst_sstride;
     T2 *re = reinterpret_cast<T2 *>(base);
@@ -301,8 +293,8 @@ __device__ __forceinline__ void convert_body(const ConvertDesc &d, int64_t s, in
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (d.n >> 1);
          i += (int64_t)gridDim.x * blockDim.x) {
         const float4 v = reinterpret_cast<const float4 *>(src)[i];
-        const float r0 = ldexpf(v.x, -e), i0 = ldexpf(v.y, -e);
-        const float r1 = ldexpf(v.z, -e), i1 = ldexpf(v.w, -e);
+        const float r0 = scale_pow2(v.x, pe), i0 = scale_pow2(v.y, pe);
+        const float r1 = scale_pow2(v.z, pe), i1 = scale_pow2(v.w, pe);
         const T2 rh = pack2<T2>(r0, r1), ih = pack2<T2>(i0, i1);
         re[i] = rh;
         im[i] = ih;
@@ -360,11 +352,16 @@ cudaError_t launch_bind(const BindItem *items_dev, int32_t n_items, const double
 cudaError_t launch_bind_tiled(const BindTiled &b, const double2 *src, float2 *arena,
                               int64_t slice_begin, int64_t slices, cudaStream_t st) {
     if (slices <= 0) return cudaSuccess;
-    if (b.t < 6 || b.t > 11 || slices > 65535 || b.ntiles < 1) return cudaErrorInvalidValue;
-    int64_t gx = (152 * 8 + slices - 1) / slices;
+    if (b.t < 6 || b.t > 12 || slices > 65535 || b.ntiles < 1) return cudaErrorInvalidValue;
+    const int per_sm = b.t <= 11 ? 8 : 6;  // resident blocks (16 or 32 KiB of shared memory)
+    int64_t gx = (152 * per_sm + slices - 1) / slices;
     if (gx > b.ntiles) gx = b.ntiles;
-    k_bind_tiled<<<dim3((unsigned)gx, (unsigned)slices), 256, 0, st>>>(b, src, arena,
-                                                                       slice_begin);
+    if (b.t <= 11)
+        k_bind_tiled<2048><<<dim3((unsigned)gx, (unsigned)slices), 256, 0, st>>>(b, src, arena,
+                                                                                 slice_begin);
+    else
+        k_bind_tiled<4096><<<dim3((unsigned)gx, (unsigned)slices), 256, 0, st>>>(b, src, arena,
+                                                                                 slice_begin);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,8 @@ namespace tn {
 
 __device__ __forceinline__ void planar_out_store(const PlanarOut &o, int64_t s, uint64_t off,
                                                  float re, float im, int e) {
-    const float r = ldexpf(re, -e), i = ldexpf(im, -e);
+    const Pow2 pe = pow2_of(-e);
+    const float r = scale_pow2(re, pe), i = scale_pow2(im, pe);
     const int64_t base = s * o.sstride + (int64_t)off;
     if (o.bf16) {
         __nv_bfloat16 *p = static_cast<__nv_bfloat16 *>(o.base) + base;
@@ -39,8 +40,9 @@ __device__ __forceinline__ void planar_out_store(const PlanarOut &o, int64_t s, 
 // as one 2 x 16-bit word per plane.
 __device__ __forceinline__ void planar_out_store2(const PlanarOut &o, int64_t s, uint64_t off,
                                                   float2 v0, float2 v1, int e) {
-    const float r0 = ldexpf(v0.x, -e), i0 = ldexpf(v0.y, -e);
-    const float r1 = ldexpf(v1.x, -e), i1 = ldexpf(v1.y, -e);
+    const Pow2 pe = pow2_of(-e);
+    const float r0 = scale_pow2(v0.x, pe), i0 = scale_pow2(v0.y, pe);
+    const float r1 = scale_pow2(v1.x, pe), i1 = scale_pow2(v1.y, pe);
     const int64_t base = s * o.sstride + (int64_t)off;
     const int64_t ps = o.plane_stride / 2;
     if (o.bf16) {
@@ -91,10 +93,11 @@ __device__ __forceinline__ void planar_out_store8_t(const PlanarOut &o, int64_t 
         uint4 u;
         T2 h[4];
     } re, im, p2, p3;
+    const Pow2 pe = pow2_of(-e);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float r0 = ldexpf(v[2 * j].x, -e), i0 = ldexpf(v[2 * j].y, -e);
-        const float r1 = ldexpf(v[2 * j + 1].x, -e), i1 = ldexpf(v[2 * j + 1].y, -e);
+        const float r0 = scale_pow2(v[2 * j].x, pe), i0 = scale_pow2(v[2 * j].y, pe);
+        const float r1 = scale_pow2(v[2 * j + 1].x, pe), i1 = scale_pow2(v[2 * j + 1].y, pe);
         re.h[j] = pack_pair<T2>(r0, r1);
         im.h[j] = pack_pair<T2>(i0, i1);
         if (o.planes == 3) p2.h[j] = pack_pair<T2>(r0 + i0, r1 + i1);
