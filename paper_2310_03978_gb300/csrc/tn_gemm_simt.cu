@@ -184,6 +184,101 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     if (d.amax_out) amax_publish(d.amax_out + s, amx);
 }
 
+// Split-K partial of a skinny step (the whole output fits one 16 x 64 tile: the side with at
+// most 16 free elements is "S", the other, at most 64, is "L"; K is long, e.g. the last step of
+// a circuit).  Four groups of 64 threads each own a quarter of every 64-wide K tile; a thread
+// accumulates a 4 x 4 block of outputs (S rows sg, sg + 4, .., L columns lg, lg + 16, ..), so
+// every pair of shared-memory loads feeds 4 complex products.  The groups' sums are added in
+// group order and CTA z writes partial[z][s] (row-major M x N) for k_splitk_reduce.
+constexpr int kSkBK = 64;
+
+__global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
+    __shared__ float2 sS[kSkBK][17];
+    __shared__ float2 sL[kSkBK][65];
+    const int64_t s = blockIdx.y;
+    const bool swap = d.lm > d.ln;               // S is B when M > N
+    const int ls = swap ? d.ln : d.lm, ll = swap ? d.lm : d.ln;
+    const int S = 1 << ls, L = 1 << ll;
+    const int64_t Kfull = 1ll << d.lk;
+    const int64_t K = Kfull / d.splits;
+    const int64_t kz = (int64_t)blockIdx.z * K;
+    const float2 *PS = (swap ? d.B + s * d.sB : d.A + s * d.sA) + kz;
+    const float2 *PL = (swap ? d.A + s * d.sA : d.B + s * d.sB) + kz;
+    const int tid = threadIdx.x, g = tid >> 6, t64 = tid & 63;
+    const int sg = t64 >> 4, lg = t64 & 15;
+    float cr[4][4], ci[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cr[i][j] = ci[i][j] = 0.f;
+    for (int64_t k0 = 0; k0 < K; k0 += kSkBK) {
+        const int kw = K - k0 < kSkBK ? (int)(K - k0) : kSkBK;
+        __syncthreads();
+        for (int e = tid; e < S * kSkBK; e += 256) {
+            const int r = e / kSkBK, k = e % kSkBK;
+            sS[k][r] = k < kw ? PS[(int64_t)r * Kfull + k0 + k] : make_float2(0.f, 0.f);
+        }
+        for (int e = tid; e < L * kSkBK; e += 256) {
+            const int r = e / kSkBK, k = e % kSkBK;
+            sL[k][r] = k < kw ? PL[(int64_t)r * Kfull + k0 + k] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float tr[4][4], ti[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tr[i][j] = ti[i][j] = 0.f;
+#pragma unroll 4
+        for (int kk = g * 16; kk < g * 16 + 16; ++kk) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sS[kk][sg + 4 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = sL[kk][lg + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    tr[i][j] = fmaf(a[i].x, b[j].x, tr[i][j]);
+                    tr[i][j] = fmaf(-a[i].y, b[j].y, tr[i][j]);
+                    ti[i][j] = fmaf(a[i].x, b[j].y, ti[i][j]);
+                    ti[i][j] = fmaf(a[i].y, b[j].x, ti[i][j]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cr[i][j] += tr[i][j];
+                ci[i][j] += ti[i][j];
+            }
+    }
+    // add the four groups' sums in group order (through the L buffer: 4 x 16 x 64 float2)
+    __syncthreads();
+    float2 *red = &sL[0][0];  // [g][S index][L index], 4 * 16 * 64 = 4096 < 64 * 65
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            red[(g * 16 + sg + 4 * i) * 64 + lg + 16 * j] = make_float2(cr[i][j], ci[i][j]);
+    __syncthreads();
+    const int64_t MN = (int64_t)S * L;
+    float2 *P = d.partial + ((int64_t)blockIdx.z * gridDim.y + s) * MN;
+    for (int e = tid; e < 16 * 64; e += 256) {
+        const int si = e >> 6, li = e & 63;
+        if (si >= S || li >= L) continue;
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 v = red[(q * 16 + si) * 64 + li];
+            re += v.x;
+            im += v.y;
+        }
+        // row-major M x N: (m, n) = (si, li), or (li, si) when the roles were swapped
+        P[swap ? (int64_t)li * S + si : (int64_t)si * L + li] = make_float2(re, im);
+    }
+}
+
 // Sum of the split-K partials in increasing split order, scattered into C's order.
 __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
     const int64_t MN = 1ll << (d.lm + d.ln);
@@ -319,7 +414,12 @@ cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st)
         ((1ll << d.lk) % d.splits) != 0 || (d.splits > 1 && !d.partial))
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)(tm * tn_), (unsigned)slices, (unsigned)d.splits);
-    if (d.lk - (d.splits > 1 ? __builtin_ctz((unsigned)d.splits) : 0) <= 3)
+    const int lmin = d.lm < d.ln ? d.lm : d.ln, lmax = d.lm < d.ln ? d.ln : d.lm;
+    const bool skinny = d.splits > 1 && lmin <= 4 && lmax <= 6 &&
+                        (1ll << d.lk) / d.splits >= kSkBK;
+    if (skinny)
+        k_gemm_skinny<<<dim3(1, (unsigned)slices, (unsigned)d.splits), 256, 0, st>>>(d);
+    else if (d.lk - (d.splits > 1 ? __builtin_ctz((unsigned)d.splits) : 0) <= 3)
         k_gemm_simt<8><<<grid, 256, 0, st>>>(d, tn_);
     else
         k_gemm_simt<16><<<grid, 256, 0, st>>>(d, tn_);

@@ -556,6 +556,344 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
                      "r"(TMEM_COLS));
 }
 
+// Persistent 4M kernel for short contractions (K up to 512): each CTA walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... (tiles of all slices, slice-major, grouped raster
+// inside a slice).  Such steps write far more than they compute, so what matters is keeping the
+// stores going: the MMA of the next tile fills the other half of a double-buffered TMEM
+// accumulator (2 x (re, im) x 128 columns = 512) while eight epilogue warps drain the current
+// one, and a CTA's setup (barriers, TMEM allocation) is paid once per SM instead of per tile.
+// Warps 0-7 are the epilogue (warp w reads TMEM lanes 32 (w % 4).., columns 64 (w / 4)..,
+// and stages its half of the tile in its own shared-memory buffer), warp 8 issues the TMA
+// loads, warp 9 the MMAs.  Every wait is bounded; a wait that runs out sets the status word and
+// the abort flag, and every role leaves its loop.
+constexpr int PERS_BN = 128, PERS_STG = 2, PERS_THREADS = 320;
+
+template <int ESZ>
+struct PersCfg {
+    static constexpr int BKT = 32;                      // 64-byte shared-memory rows
+    static constexpr int KEL = 2 * BKT / ESZ;           // K elements per stage
+    static constexpr int TILE_A = BM * BKT * 2, TILE_B = PERS_BN * BKT * 2;
+    static constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);
+    static constexpr int RING = PERS_STG * STAGE_BYTES;
+    static constexpr int STAGE_HALF = BM * SLD * 8;     // staging of one 128 x 64 half tile
+    static constexpr int BODY = RING + 2 * STAGE_HALF;
+    static constexpr int SMEM_BYTES = BODY + 1024 + 512;
+    static constexpr int SBO = 8 * BKT * 2;
+    static constexpr uint64_t LAYOUT = 4;               // 64-byte swizzle
+};
+
+struct TileCoord {
+    int64_t s;
+    int m0, n0;
+    int first;  // the slice's tile 0
+};
+
+__device__ __forceinline__ TileCoord pers_tile(int64_t t, int64_t tiles_m, int64_t tiles_n) {
+    const int64_t per_slice = tiles_m * tiles_n;
+    TileCoord c;
+    c.s = t / per_slice;
+    const int64_t tile = t % per_slice;
+    const int64_t group = 16, per_group = group * tiles_n;
+    const int64_t g = tile / per_group;
+    const int64_t first_m = g * group;
+    const int64_t gsize = (tiles_m - first_m) < group ? (tiles_m - first_m) : group;
+    c.m0 = (int)((first_m + (tile % per_group) % gsize) * BM);
+    c.n0 = (int)(((tile % per_group) / gsize) * PERS_BN);
+    c.first = tile == 0;
+    return c;
+}
+
+__device__ __forceinline__ void named_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Barrier over `threads` threads that also ANDs a predicate across them: every participant
+// learns whether all of them had v set (so a group leaves a loop together).
+__device__ __forceinline__ bool named_and(int id, int threads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n"
+        ".reg .pred p, q;\n"
+        "setp.ne.u32 p, %1, 0;\n"
+        "bar.red.and.pred q, %2, %3, p;\n"
+        "selp.u32 %0, 1, 0, q;\n"
+        "}\n"
+        : "=r"(r)
+        : "r"((uint32_t)(v ? 1 : 0)), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+template <int ESZ>
+__global__ void __launch_bounds__(PERS_THREADS, 1)
+    k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
+    using F = PersCfg<ESZ>;
+    constexpr int BK = F::KEL, BN = PERS_BN;
+    auto sdesc = [](uint32_t a) { return sdesc_sw<F::SBO, F::LAYOUT>(a); };
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY);
+    uint64_t *empty = full + PERS_STG;
+    uint64_t *tfull = empty + PERS_STG;   // MMA -> epilogue: accumulator buffer b is complete
+    uint64_t *tempty = tfull + 2;         // epilogue -> MMA: buffer b was read (8 arrivals)
+    uint64_t *mdone = tempty + 2;         // the MMA warp's last commit
+    uint64_t *hi_off = mdone + 1;         // [8] epilogue table: C offsets of bits 10..12
+    int *hi_w = reinterpret_cast<int *>(hi_off + 8);  // [8] their staging offsets
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(hi_w + 8);
+    int *aborted = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tiles_m = (1ll << d.lm) / BM;
+    const int64_t total = tiles_m * tiles_n * slices;
+    const int num_kb = ((1 << d.lk) + BK - 1) / BK;
+    const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < PERS_STG; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(mdone, 1);
+        *aborted = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmA))
+                     : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmB))
+                     : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // epilogue tables of the 128 x 64 half tile (13 bits sorted by position in C; bits 0..2 are
+    // C's positions 0..2): offsets of the high bits 10..12 (one entry per write iteration)
+    if (threadIdx.x < 8) {
+        int mi = 0, ni = 0;
+        uint64_t off = 0;
+        for (int q = 10; q < 13; ++q)
+            if ((threadIdx.x >> (q - 10)) & 1) {
+                const int sq = d.tb_src[q];
+                if (sq & 128) mi |= 1 << (sq & 127);
+                else ni |= 1 << sq;
+                off |= 1ull << d.tb_pos[q];
+            }
+        hi_off[threadIdx.x] = off;
+        hi_w[threadIdx.x] = mi * SLD + ni;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 8) {
+        // TMA producer: k blocks of all this CTA's tiles through the ring
+        if (lane == 0) {
+            int it = 0, issued = 0;
+            for (int64_t t = blockIdx.x; t < total && !*(volatile int *)aborted; t += gridDim.x) {
+                const TileCoord c = pers_tile(t, tiles_m, tiles_n);
+                const int sa = d.a_sliced ? (int)c.s : 0, sbi = d.b_sliced ? (int)c.s : 0;
+                bool ok = true;
+                for (int kb = 0; kb < num_kb; ++kb, ++it) {
+                    const int st = it % PERS_STG;
+                    const uint32_t ph = (uint32_t)(it / PERS_STG) & 1u;
+                    if (it >= PERS_STG &&
+                        !mbar_wait(&empty[st], ph ^ 1u, globaltimer() + limit)) {
+                        *aborted = 1;
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *base = smem + st * F::STAGE_BYTES;
+                    mbar_expect_tx(&full[st], F::STAGE_BYTES);
+                    const int k0 = kb * BK;
+#pragma unroll
+                    for (int pl = 0; pl < 2; ++pl) {
+                        tma_load_3d(base + pl * F::TILE_A, &d.tmA, &full[st], k0, c.m0,
+                                    pl * (int)d.slices_a + sa);
+                        tma_load_3d(base + 2 * F::TILE_A + pl * F::TILE_B, &d.tmB, &full[st],
+                                    k0, c.n0, pl * (int)d.slices_b + sbi);
+                    }
+                    issued = it + 1;
+                }
+                if (!ok) break;
+            }
+            // loads still in flight must land before the CTA's shared memory is released: wait
+            // for the last arrival of every stage that was used (after a normal run the MMA
+            // warp has consumed them all and these waits return at once)
+            const unsigned long long drain = globaltimer() + limit;
+            for (int st = 0; st < PERS_STG && st < issued; ++st) {
+                const int last = ((issued - 1 - st) / PERS_STG) * PERS_STG + st;
+                mbar_wait(&full[st], (uint32_t)(last / PERS_STG) & 1u, drain);
+            }
+        }
+    } else if (warp == 9) {
+        // MMA issuer: tile i accumulates into TMEM buffer i & 1 (columns 256 (i & 1) ..)
+        if (lane == 0) {
+            const uint32_t fmt = ESZ == 4 ? 2u : (d.dtype == 1 ? 1u : 0u);
+            const uint32_t id_pos = idesc_mma(fmt, BM, BN, false);
+            const uint32_t id_neg = idesc_mma(fmt, BM, BN, true);
+            int it = 0, i = 0;
+            bool any = false;
+            for (int64_t t = blockIdx.x; t < total && !*(volatile int *)aborted;
+                 t += gridDim.x, ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((i >> 1) - 1) & 1u,
+                                         globaltimer() + limit)) {
+                    *aborted = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(buf * 2 * BN);
+                bool ok = true;
+                for (int kb = 0; kb < num_kb; ++kb, ++it) {
+                    const int st = it % PERS_STG;
+                    const uint32_t ph = (uint32_t)(it / PERS_STG) & 1u;
+                    if (!mbar_wait(&full[st], ph, globaltimer() + limit)) {
+                        *aborted = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = smem_u32(smem + st * F::STAGE_BYTES);
+                    const uint64_t a_re = sdesc(base), a_im = sdesc(base + F::TILE_A);
+                    const uint64_t b_re = sdesc(base + 2 * F::TILE_A);
+                    const uint64_t b_im = sdesc(base + 2 * F::TILE_A + F::TILE_B);
+#pragma unroll
+                    for (int kk = 0; kk < F::BKT / 16; ++kk) {
+                        const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                        const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+                        umma<ESZ>(acc, a_re + adv, b_re + adv, id_pos, first);
+                        umma<ESZ>(acc, a_im + adv, b_im + adv, id_neg, 1u);
+                        umma<ESZ>(acc + BN, a_re + adv, b_im + adv, id_pos, first);
+                        umma<ESZ>(acc + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                    }
+                    umma_commit(&empty[st]);
+                    any = true;
+                }
+                if (!ok) break;
+                umma_commit(&tfull[buf]);
+            }
+            if (any) {
+                // every MMA this warp issued has completed before the CTA tears down
+                umma_commit(mdone);
+                mbar_wait(mdone, 0, globaltimer() + limit);
+            }
+        }
+    } else {
+        // epilogue: warp w drains rows 32 (w % 4).. and columns 64 (w / 4).. of each tile
+        const int wg = warp >> 2;                  // column half
+        const int et = threadIdx.x & 127;          // thread index inside the half
+        const int row = (warp & 3) * 32 + lane;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + wg * F::STAGE_HALF);
+        int w8[8];
+        {
+            int dq[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int sq = d.tb_src[q];
+                dq[q] = (sq & 128) ? (1 << (sq & 127)) * SLD : (1 << sq);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w8[j] = ((j & 1) ? dq[0] : 0) + ((j & 2) ? dq[1] : 0) + ((j & 4) ? dq[2] : 0);
+        }
+        int mlo = 0, nlo = 0;
+        uint64_t olo = 0;
+#pragma unroll
+        for (int q = 3; q < 10; ++q)
+            if ((et >> (q - 3)) & 1) {
+                const int sq = d.tb_src[q];
+                if (sq & 128) mlo |= 1 << (sq & 127);
+                else nlo |= 1 << sq;
+                olo |= 1ull << d.tb_pos[q];
+            }
+        const int wlo = mlo * SLD + nlo;
+        // per-slice values, reloaded when the slice changes (a CTA's tiles run slice-major)
+        int64_t cur_s = -1;
+        Pow2 pe{1.f, 1.f};
+        int eo = 0;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            bool ok = true;
+            if (lane == 0)
+                ok = mbar_wait(&tfull[buf], (uint32_t)(i >> 1) & 1u, globaltimer() + limit) &&
+                     !*(volatile int *)aborted;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            // the four warps of a half leave together, so none is left at a named barrier
+            ok = named_and(1 + wg, 128, ok);
+            if (!ok) {
+                if (lane == 0) *aborted = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const TileCoord c = pers_tile(t, tiles_m, tiles_n);
+            if (c.s != cur_s) {
+                cur_s = c.s;
+                const int sa = d.a_sliced ? (int)c.s : 0, sbi = d.b_sliced ? (int)c.s : 0;
+                pe = pow2_of(d.expA[sa] + d.expB[sbi]);
+                eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
+            }
+            const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN + wg * CW);
+#pragma unroll 1
+            for (int c0 = 0; c0 < CW; c0 += 16) {
+                uint32_t r0[16], r1[16];
+                tmem_ld16(acc + (uint32_t)c0, r0);
+                tmem_ld16(acc + (uint32_t)(BN + c0), r1);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    stage[row * SLD + c0 + j] = make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
+                                                            scale_pow2(__uint_as_float(r1[j]), pe));
+            }
+            // the accumulator buffer may be refilled as soon as all eight warps have read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            named_sync(1 + wg, 128);
+            if (d.planar_out && c.first && wg == 0 && et == 0) d.pout.exps[c.s] = eo;
+            const uint64_t cbase = deposit((uint64_t)c.m0, d.lm, d.posC_m) |
+                                   deposit((uint64_t)(c.n0 + wg * CW), d.ln, d.posC_n);
+            float2 *C = d.C + c.s * d.sC + cbase;
+            float amx = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < (BM * CW) / (8 * 128); ++k) {
+                const int w = wlo + hi_w[k];
+                float2 v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    v[j] = stage[w + w8[j]];
+                    amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                }
+                const uint64_t o = olo | hi_off[k];
+                if (d.planar_out) {
+                    planar_out_store8(d.pout, c.s, cbase | o, v, eo);
+                } else {
+                    float4 *c4 = reinterpret_cast<float4 *>(C + o);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
+                                            v[2 * j + 1].y);
+                }
+            }
+            if (d.amax_out) amax_publish(d.amax_out + c.s, amx);
+            named_sync(1 + wg, 128);  // the staging buffer is free for the next tile
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(512));
+}
+
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -656,8 +994,43 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 
 }  // namespace
 
+template <int ESZ>
+cudaError_t configure_pers() {
+    return cudaFuncSetAttribute(k_gemm_tc_pers<ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PersCfg<ESZ>::SMEM_BYTES);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            n = v;
+        if (n <= 0) n = 152;
+    }
+    return n;
+}
+
+template <int ESZ>
+cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
+    if (d.ln < 7 || d.lk < 3 || d.lk > 9 || (d.dtype == 2) != (ESZ == 4))
+        return cudaErrorInvalidValue;
+    const int64_t tiles_n = (1ll << d.ln) / PERS_BN;
+    const int64_t total = ((1ll << d.lm) / BM) * tiles_n * slices;
+    int64_t grid = sm_count();
+    if (grid > total) grid = total;
+    k_gemm_tc_pers<ESZ><<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ>::SMEM_BYTES, st>>>(
+        d, tiles_n, slices);
+    return cudaGetLastError();
+}
+
+// Variants 12 (16-bit) and 13 (TF32) are the persistent short-K kernel.
+constexpr int kPersFp16 = 12, kPersTf32 = 13;
+
 cudaError_t tc_prepare() {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = configure_pers<2>();
+    if (e == cudaSuccess) e = configure_pers<4>();
 #define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb, esz) \
     if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb, esz>();
     TN_TC_VARIANTS(TN_TC_CONFIGURE)
@@ -667,6 +1040,8 @@ cudaError_t tc_prepare() {
 
 // K elements per pipeline stage of a variant (the tensor map's box width)
 int tc_variant_bk(int variant) {
+    if (variant == kPersFp16) return PersCfg<2>::KEL;
+    if (variant == kPersTf32) return PersCfg<4>::KEL;
     switch (variant) {
 #define TN_TC_BK(id, npl, bk, bn, stg, minb, esz) \
     case id: return 2 * bk / esz;
@@ -677,6 +1052,7 @@ int tc_variant_bk(int variant) {
 }
 
 int tc_variant_bn(int variant) {
+    if (variant == kPersFp16 || variant == kPersTf32) return PERS_BN;
     switch (variant) {
 #define TN_TC_BN(id, npl, bk, bn, stg, minb, esz) \
     case id: return bn;
@@ -687,6 +1063,7 @@ int tc_variant_bn(int variant) {
 }
 
 bool tc_variant_tf32(int variant) {
+    if (variant == kPersFp16 || variant == kPersTf32) return variant == kPersTf32;
     switch (variant) {
 #define TN_TC_ESZ(id, npl, bk, bn, stg, minb, esz) \
     case id: return esz == 4;
@@ -700,6 +1077,7 @@ bool tc_variant_tf32(int variant) {
 // two CTAs per SM; long ones use the 128 x 256 tile (1.98 PFLOP/s on m=2^13, n=2^14, k=2^14
 // against 1.79 for 128 x 128), or 128 x 128 when N < 256.
 int tc_variant_form(int variant) {
+    if (variant == kPersFp16 || variant == kPersTf32) return 1;
     switch (variant) {
 #define TN_TC_FORM(id, npl, bk, bn, stg, minb, esz) \
     case id: return npl == 3 ? 2 : (npl == 4 ? 3 : 1);
@@ -709,9 +1087,10 @@ int tc_variant_form(int variant) {
     return 0;
 }
 
-int tc_num_variants() { return 12; }
+int tc_num_variants() { return 14; }
 
 bool tc_variant_fits(int variant, int lk, int ln) {
+    if (variant == kPersFp16 || variant == kPersTf32) return lk >= 3 && lk <= 9 && ln >= 7;
     const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
     if (bk == 0) return false;
     if (bk == 64 && lk < 6) return false;
@@ -722,9 +1101,12 @@ bool tc_variant_fits(int variant, int lk, int ln) {
 // bk_pref / bn_pref: 0 or the K / N tile the caller asks for (K tile in 16-bit elements of a
 // shared-memory row: 32 = 64-byte rows, 64 = 128-byte rows, for both operand types).
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf32) {
+    // short contractions: the persistent kernel, unless a tile shape was asked for
+    const bool pers = form == 1 && lk >= 3 && lk <= 9 && ln >= 7 && bk_pref == 0 && bn_pref == 0;
     if (tf32) {
         if (form == 3) return 11;
         if (form == 2) return 10;
+        if (pers) return kPersTf32;
         if (bn_pref == 256 && ln >= 8) return 7;
         if (bk_pref == 64) return 9;
         if (lk <= 9) return 8;
@@ -732,6 +1114,7 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
     }
     if (form == 3) return 6;
     if (form == 2) return bk_pref == 64 ? 4 : 3;
+    if (pers) return kPersFp16;
     if (bn_pref == 256 && ln >= 8) return 1;
     if (bk_pref == 32) return lk <= 9 ? 2 : 5;
     if (bk_pref == 64 || bn_pref == 128) return lk <= 9 && bk_pref != 64 ? 2 : 0;
@@ -741,6 +1124,8 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
 
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (d.lm < 7 || slices > 65535) return cudaErrorInvalidValue;
+    if (d.variant == kPersFp16) return launch_pers<2>(d, slices, st);
+    if (d.variant == kPersTf32) return launch_pers<4>(d, slices, st);
     switch (d.variant) {
 #define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb, esz) \
     case id: return launch_variant<npl, bk, bn, stg, minb, esz>(d, slices, st);

@@ -130,25 +130,22 @@ void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, 
                     int8_t *src, int8_t *pos);
 
 
-// Exact power-of-two scaling: x * 2^e rounded once, like ldexpf(x, e), as one multiplication by
-// the float 2^e whenever 2^e is representable (-149 <= e <= 127; subnormal below -126), which
-// is the case for every exponent the scaling produces in practice; ldexpf otherwise.
+// Power-of-two scaling without a branch: x * 2^e as x * f1 * f2 with f1 = 2^clamp(e, -126, 127)
+// and f2 = 2^(e - that) (clamped to the representable range).  For -126 <= e <= 127, f2 = 1 and
+// the result is x * 2^e rounded once, exactly like ldexpf; beyond, it can round twice, but only
+// for results below FP32's normal range.  The scaling's exponents stay far inside that range.
 struct Pow2 {
-    float f;
-    int e;
-    bool exact;
+    float f1, f2;
 };
+__device__ __forceinline__ float pow2_bits(int e) {  // 2^e for -149 <= e <= 127
+    return e >= -126 ? __int_as_float((e + 127) << 23) : __int_as_float(1 << (e + 149));
+}
 __device__ __forceinline__ Pow2 pow2_of(int e) {
-    Pow2 p;
-    p.e = e;
-    p.exact = e >= -149 && e <= 127;
-    p.f = e >= -126 ? __int_as_float((min(e, 127) + 127) << 23)
-                    : __int_as_float(1 << (max(e, -149) + 149));
-    return p;
+    const int e1 = max(-126, min(e, 127));
+    const int e2 = max(-149, min(e - e1, 127));
+    return Pow2{pow2_bits(e1), pow2_bits(e2)};
 }
-__device__ __forceinline__ float scale_pow2(float x, const Pow2 &p) {
-    return p.exact ? x * p.f : ldexpf(x, p.e);
-}
+__device__ __forceinline__ float scale_pow2(float x, const Pow2 &p) { return x * p.f1 * p.f2; }
 
 // Warp-reduced atomicMax of a non-negative float into *slot (float bits order like unsigned).
 __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {

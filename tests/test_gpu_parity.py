@@ -267,6 +267,26 @@ def test_short_contraction_on_tensor_cores(tn, shape):
         check(got, ref, TOL[mode])
 
 
+@pytest.mark.parametrize("mode", ["fp16_scaled", "tf32"])
+@pytest.mark.parametrize("lm,ln,lk,nsl", [(12, 10, 8, 3), (7, 7, 9, 0), (9, 8, 8, 2)])
+def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
+    # short contractions run on the persistent kernel (variant 12 / 13): each CTA walks tiles of
+    # all slices in flight with a double-buffered accumulator; fewer tiles than SMs included
+    # (nsl of the lk contracted labels are sliced, leaving k = 2^(lk - nsl))
+    rng = np.random.default_rng(600 + lm + 3 * ln + 7 * lk + nsl)
+    tensors, labels, out = single_step(rng, lm, ln, lk)
+    K = [l for l in labels[0] if l >= 200]
+    sliced = [int(x) for x in rng.choice(K, size=nsl, replace=False)] if nsl else []
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    net = tn.Network(tensors, labels, out)
+    plan = tn.Plan(net, [(0, 1)], sliced, mode=mode, sync_each_call=True)
+    si = plan.step_info(0)
+    assert si["kernel_name"] == "gemm_tc" and si["tc_variant"] == (12 if mode != "tf32" else 13)
+    check(plan.contract_host(), ref, TOL[mode])
+    plan.close()
+    net.close()
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(tn):
     # a tensor-core CTA whose producer issues no copies: its MMA warp's wait runs out after
     # 200 ms, the kernel records the timeout and exits; the context stays usable
