@@ -128,7 +128,9 @@ typedef struct {
     double prep_ms;                /* profile mode: time of its operand conversions (tensor-
                                       core steps: amax + planar 16-bit copies)               */
     int32_t tc_variant;            /* tensor-core kernel variant in use (-1 otherwise)       */
-    int32_t reserved2;
+    int32_t store_run_log2;        /* GEMM kernels: log2 of the longest run of consecutive
+                                      result elements one staged chunk writes (its bits that
+                                      are also the result's lowest positions)                */
 } tn_step_info;
 
 /*

@@ -576,29 +576,33 @@ struct PersCfg {
     static constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);
     static constexpr int RING = PERS_STG * STAGE_BYTES;
     static constexpr int STAGE_HALF = BM * SLD * 8;     // staging of one 128 x 64 half tile
+    static constexpr int DEP = 6 * 256 * 8;              // byte-wise deposit tables of m0, n0
     static constexpr int BODY = RING + 2 * STAGE_HALF;
-    static constexpr int SMEM_BYTES = BODY + 1024 + 512;
+    static constexpr int SMEM_BYTES = BODY + DEP + 1024 + 512;
     static constexpr int SBO = 8 * BKT * 2;
     static constexpr uint64_t LAYOUT = 4;               // 64-byte swizzle
 };
 
 struct TileCoord {
-    int64_t s;
-    int m0, n0;
-    int first;  // the slice's tile 0
+    int s;
+    uint32_t mt, nt;  // tile row and column
+    int first;        // the slice's tile 0
 };
 
-__device__ __forceinline__ TileCoord pers_tile(int64_t t, int64_t tiles_m, int64_t tiles_n) {
-    const int64_t per_slice = tiles_m * tiles_n;
+// Tile t of the walk (all counts below 2^31, so 32-bit divisions suffice): slice-major, then
+// groups of 16 m-tiles that sweep the n-tiles together (they share B in L2).
+__device__ __forceinline__ TileCoord pers_tile(uint32_t t, uint32_t tiles_m, uint32_t tiles_n) {
+    const uint32_t per_slice = tiles_m * tiles_n;
     TileCoord c;
-    c.s = t / per_slice;
-    const int64_t tile = t % per_slice;
-    const int64_t group = 16, per_group = group * tiles_n;
-    const int64_t g = tile / per_group;
-    const int64_t first_m = g * group;
-    const int64_t gsize = (tiles_m - first_m) < group ? (tiles_m - first_m) : group;
-    c.m0 = (int)((first_m + (tile % per_group) % gsize) * BM);
-    c.n0 = (int)(((tile % per_group) / gsize) * PERS_BN);
+    c.s = (int)(t / per_slice);
+    const uint32_t tile = t - (uint32_t)c.s * per_slice;
+    const uint32_t per_group = 16u * tiles_n;
+    const uint32_t g = tile / per_group, r = tile - g * per_group;
+    const uint32_t first_m = g * 16u;
+    const uint32_t gsize = (tiles_m - first_m) < 16u ? (tiles_m - first_m) : 16u;
+    const uint32_t q = r / gsize;
+    c.mt = first_m + (r - q * gsize);
+    c.nt = q;
     c.first = tile == 0;
     return c;
 }
@@ -633,7 +637,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY + F::DEP);
     uint64_t *empty = full + PERS_STG;
     uint64_t *tfull = empty + PERS_STG;   // MMA -> epilogue: accumulator buffer b is complete
     uint64_t *tempty = tfull + 2;         // epilogue -> MMA: buffer b was read (8 arrivals)
@@ -643,11 +647,25 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(hi_w + 8);
     int *aborted = reinterpret_cast<int *>(tmem_slot + 1);
 
+    // deposit tables: dep[j][b] = C offset of byte b of the tile row index (j = 0..2) or of
+    // the tile column index (j = 3..5), i.e. of m bits 7 + 8 j .. and n bits 7 + 8 (j - 3) ..
+    uint64_t (*dep)[256] = reinterpret_cast<uint64_t (*)[256]>(smem + F::BODY);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tiles_m = (1ll << d.lm) / BM;
-    const int64_t total = tiles_m * tiles_n * slices;
+    const uint32_t tiles_m = (uint32_t)((1ll << d.lm) / BM);
+    const uint32_t tn32 = (uint32_t)tiles_n;
+    const uint32_t total = tiles_m * tn32 * (uint32_t)slices;
     const int num_kb = ((1 << d.lk) + BK - 1) / BK;
     const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
+    for (int e = threadIdx.x; e < 6 * 256; e += PERS_THREADS) {
+        const int j = e >> 8, b = e & 255;
+        const bool nside = j >= 3;
+        const int first = 7 + 8 * (nside ? j - 3 : j), nb = nside ? d.ln : d.lm;
+        const int8_t *pos = nside ? d.posC_n : d.posC_m;
+        uint64_t v = 0;
+        for (int i = 0; i < 8; ++i)
+            if (((b >> i) & 1) && first + i < nb) v |= 1ull << pos[first + i];
+        dep[j][b] = v;
+    }
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < PERS_STG; ++i) {
@@ -696,9 +714,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
         // TMA producer: k blocks of all this CTA's tiles through the ring
         if (lane == 0) {
             int it = 0, issued = 0;
-            for (int64_t t = blockIdx.x; t < total && !*(volatile int *)aborted; t += gridDim.x) {
-                const TileCoord c = pers_tile(t, tiles_m, tiles_n);
-                const int sa = d.a_sliced ? (int)c.s : 0, sbi = d.b_sliced ? (int)c.s : 0;
+            for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted; t += gridDim.x) {
+                const TileCoord c = pers_tile(t, tiles_m, tn32);
+                const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
+                const int m0 = (int)(c.mt * BM), n0 = (int)(c.nt * PERS_BN);
                 bool ok = true;
                 for (int kb = 0; kb < num_kb; ++kb, ++it) {
                     const int st = it % PERS_STG;
@@ -714,10 +733,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     const int k0 = kb * BK;
 #pragma unroll
                     for (int pl = 0; pl < 2; ++pl) {
-                        tma_load_3d(base + pl * F::TILE_A, &d.tmA, &full[st], k0, c.m0,
+                        tma_load_3d(base + pl * F::TILE_A, &d.tmA, &full[st], k0, m0,
                                     pl * (int)d.slices_a + sa);
                         tma_load_3d(base + 2 * F::TILE_A + pl * F::TILE_B, &d.tmB, &full[st],
-                                    k0, c.n0, pl * (int)d.slices_b + sbi);
+                                    k0, n0, pl * (int)d.slices_b + sbi);
                     }
                     issued = it + 1;
                 }
@@ -740,7 +759,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             const uint32_t id_neg = idesc_mma(fmt, BM, BN, true);
             int it = 0, i = 0;
             bool any = false;
-            for (int64_t t = blockIdx.x; t < total && !*(volatile int *)aborted;
+            for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted;
                  t += gridDim.x, ++i) {
                 const int buf = i & 1;
                 if (i >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((i >> 1) - 1) & 1u,
@@ -816,11 +835,13 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             }
         const int wlo = mlo * SLD + nlo;
         // per-slice values, reloaded when the slice changes (a CTA's tiles run slice-major)
-        int64_t cur_s = -1;
+        int cur_s = -1;
         Pow2 pe{1.f, 1.f};
         int eo = 0;
+        // C offset of this warp's column half: n bit 6
+        const uint64_t half_off = wg ? (1ull << d.posC_n[6]) : 0ull;
         int i = 0;
-        for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
             const int buf = i & 1;
             bool ok = true;
             if (lane == 0)
@@ -834,10 +855,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const TileCoord c = pers_tile(t, tiles_m, tiles_n);
+            const TileCoord c = pers_tile(t, tiles_m, tn32);
             if (c.s != cur_s) {
                 cur_s = c.s;
-                const int sa = d.a_sliced ? (int)c.s : 0, sbi = d.b_sliced ? (int)c.s : 0;
+                const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
                 pe = pow2_of(d.expA[sa] + d.expB[sbi]);
                 eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
             }
@@ -859,9 +880,11 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             if (lane == 0) mbar_arrive(&tempty[buf]);
             named_sync(1 + wg, 128);
             if (d.planar_out && c.first && wg == 0 && et == 0) d.pout.exps[c.s] = eo;
-            const uint64_t cbase = deposit((uint64_t)c.m0, d.lm, d.posC_m) |
-                                   deposit((uint64_t)(c.n0 + wg * CW), d.ln, d.posC_n);
-            float2 *C = d.C + c.s * d.sC + cbase;
+            const uint64_t cbase = dep[0][c.mt & 255] | dep[1][(c.mt >> 8) & 255] |
+                                   dep[2][(c.mt >> 16) & 255] | dep[3][c.nt & 255] |
+                                   dep[4][(c.nt >> 8) & 255] | dep[5][(c.nt >> 16) & 255] |
+                                   half_off;
+            float2 *C = d.C + (int64_t)c.s * d.sC + cbase;
             float amx = 0.f;
 #pragma unroll 2
             for (int k = 0; k < (BM * CW) / (8 * 128); ++k) {
@@ -1014,10 +1037,13 @@ int sm_count() {
 
 template <int ESZ>
 cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    if (d.ln < 7 || d.lk < 3 || d.lk > 9 || (d.dtype == 2) != (ESZ == 4))
+    // tile rows and columns index the deposit tables with 24 bits each; tiles count in 32 bits
+    if (d.ln < 7 || d.lk < 3 || d.lk > 9 || d.lm > 31 || d.ln > 31 ||
+        (d.dtype == 2) != (ESZ == 4))
         return cudaErrorInvalidValue;
     const int64_t tiles_n = (1ll << d.ln) / PERS_BN;
     const int64_t total = ((1ll << d.lm) / BM) * tiles_n * slices;
+    if (total > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     int64_t grid = sm_count();
     if (grid > total) grid = total;
     k_gemm_tc_pers<ESZ><<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ>::SMEM_BYTES, st>>>(

@@ -1368,6 +1368,34 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
     out->log2_c = (int)st.lc.size();
     out->gemm_form = st.kernel == K_TC ? st.form : 0;
     out->tc_variant = st.kernel == K_TC ? st.variant : -1;
+    {
+        // sorted chunk bits that are C's lowest positions: 0, 1, 2, ...
+        const Tensor &C = p->tensors[st.c];
+        int8_t pm[TN_MAXR], pn[TN_MAXR], src[32], pos[32];
+        const std::vector<int> *Ms = &st.M, *Ns = &st.N;
+        int tm = 0, tn_ = 0;
+        if (st.kernel == K_TC) {
+            tm = 7;
+            tn_ = 6;
+        } else if (st.kernel == K_GEMM) {
+            tm = std::min((int)st.M.size(), 6);
+            tn_ = std::min((int)st.N.size(), 6);
+        } else if (st.kernel == K_STREAM) {
+            if (st.N.size() > st.M.size()) std::swap(Ms, Ns);
+            tm = 8;
+            tn_ = (int)Ns->size();
+        }
+        int run = 0;
+        if (tm + tn_ > 0) {
+            for (int i = 0; i < (int)Ms->size(); ++i) pm[i] = (int8_t)C.pos((*Ms)[Ms->size() - 1 - i]);
+            for (int i = 0; i < (int)Ns->size(); ++i) pn[i] = (int8_t)C.pos((*Ns)[Ns->size() - 1 - i]);
+            tn::sort_tile_bits(tm, tn_, pm, pn, 64, src, pos);
+            while (run < tm + tn_ && pos[run] == run) run++;
+        } else {
+            run = std::min(C.rank(), 10);  // element-wise kernel: consecutive threads, C order
+        }
+        out->store_run_log2 = run;
+    }
     out->tcc = st.tcc;
     Step &ms = const_cast<Step &>(st);
     tn_plan_t *mp = const_cast<tn_plan_t *>(p);
