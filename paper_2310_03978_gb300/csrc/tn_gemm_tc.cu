@@ -562,11 +562,13 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
 // stores going: the MMA of the next tile fills the other half of a double-buffered TMEM
 // accumulator (2 x (re, im) x 128 columns = 512) while eight epilogue warps drain the current
 // one, and a CTA's setup (barriers, TMEM allocation) is paid once per SM instead of per tile.
-// Warps 0-7 are the epilogue (warp w reads TMEM lanes 32 (w % 4).., columns 64 (w / 4)..,
-// and stages its half of the tile in its own shared-memory buffer), warp 8 issues the TMA
-// loads, warp 9 the MMAs.  Every wait is bounded; a wait that runs out sets the status word and
+// Warps 0-7 are the epilogue (warp w reads TMEM lanes 32 (w % 4).., columns 64 (w / 4).., and
+// stages its half of the tile, 32 columns at a time, in its own shared-memory buffer), warp 8
+// issues the TMA loads, warp 9 the MMAs.  Every wait is bounded; a wait that runs out sets the status word and
 // the abort flag, and every role leaves its loop.
-constexpr int PERS_BN = 128, PERS_STG = 2, PERS_THREADS = 320;
+// 4 ring stages keep the TMA loads of the next tiles in flight; the epilogue stages 32 columns
+// at a time (a 128 x 32 chunk: 7 row and 5 column bits)
+constexpr int PERS_BN = 128, PERS_STG = 4, PERS_THREADS = 320, PCW = 32, PSLD = PCW + 1;
 
 template <int ESZ>
 struct PersCfg {
@@ -575,7 +577,7 @@ struct PersCfg {
     static constexpr int TILE_A = BM * BKT * 2, TILE_B = PERS_BN * BKT * 2;
     static constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);
     static constexpr int RING = PERS_STG * STAGE_BYTES;
-    static constexpr int STAGE_HALF = BM * SLD * 8;     // staging of one 128 x 64 half tile
+    static constexpr int STAGE_HALF = BM * PSLD * 8;    // staging of one 128 x 32 chunk
     static constexpr int DEP = 6 * 256 * 8;              // byte-wise deposit tables of m0, n0
     static constexpr int BODY = RING + 2 * STAGE_HALF;
     static constexpr int SMEM_BYTES = BODY + DEP + 1024 + 512;
@@ -690,12 +692,12 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // epilogue tables of the 128 x 64 half tile (13 bits sorted by position in C; bits 0..2 are
-    // C's positions 0..2): offsets of the high bits 10..12 (one entry per write iteration)
-    if (threadIdx.x < 8) {
+    // epilogue tables of the 128 x 32 chunk (12 bits sorted by position in C; bits 0..2 are
+    // C's positions 0..2): offsets of the high bits 10..11 (one entry per write iteration)
+    if (threadIdx.x < 4) {
         int mi = 0, ni = 0;
         uint64_t off = 0;
-        for (int q = 10; q < 13; ++q)
+        for (int q = 10; q < 12; ++q)
             if ((threadIdx.x >> (q - 10)) & 1) {
                 const int sq = d.tb_src[q];
                 if (sq & 128) mi |= 1 << (sq & 127);
@@ -703,7 +705,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 off |= 1ull << d.tb_pos[q];
             }
         hi_off[threadIdx.x] = off;
-        hi_w[threadIdx.x] = mi * SLD + ni;
+        hi_w[threadIdx.x] = mi * PSLD + ni;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -817,7 +819,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int sq = d.tb_src[q];
-                dq[q] = (sq & 128) ? (1 << (sq & 127)) * SLD : (1 << sq);
+                dq[q] = (sq & 128) ? (1 << (sq & 127)) * PSLD : (1 << sq);
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -833,13 +835,14 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
-        const int wlo = mlo * SLD + nlo;
+        const int wlo = mlo * PSLD + nlo;
         // per-slice values, reloaded when the slice changes (a CTA's tiles run slice-major)
         int cur_s = -1;
         Pow2 pe{1.f, 1.f};
         int eo = 0;
-        // C offset of this warp's column half: n bit 6
+        // C offsets of this warp's column half (n bit 6) and of the second chunk (n bit 5)
         const uint64_t half_off = wg ? (1ull << d.posC_n[6]) : 0ull;
+        const uint64_t pass_off = 1ull << d.posC_n[5];
         int i = 0;
         for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
             const int buf = i & 1;
@@ -862,48 +865,56 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 pe = pow2_of(d.expA[sa] + d.expB[sbi]);
                 eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
             }
-            const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN + wg * CW);
-#pragma unroll 1
-            for (int c0 = 0; c0 < CW; c0 += 16) {
-                uint32_t r0[16], r1[16];
-                tmem_ld16(acc + (uint32_t)c0, r0);
-                tmem_ld16(acc + (uint32_t)(BN + c0), r1);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    stage[row * SLD + c0 + j] = make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
-                                                            scale_pow2(__uint_as_float(r1[j]), pe));
-            }
-            // the accumulator buffer may be refilled as soon as all eight warps have read it
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-            named_sync(1 + wg, 128);
+            const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN + wg * 2 * PCW);
             if (d.planar_out && c.first && wg == 0 && et == 0) d.pout.exps[c.s] = eo;
-            const uint64_t cbase = dep[0][c.mt & 255] | dep[1][(c.mt >> 8) & 255] |
-                                   dep[2][(c.mt >> 16) & 255] | dep[3][c.nt & 255] |
-                                   dep[4][(c.nt >> 8) & 255] | dep[5][(c.nt >> 16) & 255] |
-                                   half_off;
-            float2 *C = d.C + (int64_t)c.s * d.sC + cbase;
+            const uint64_t cbase0 = dep[0][c.mt & 255] | dep[1][(c.mt >> 8) & 255] |
+                                    dep[2][(c.mt >> 16) & 255] | dep[3][c.nt & 255] |
+                                    dep[4][(c.nt >> 8) & 255] | dep[5][(c.nt >> 16) & 255] |
+                                    half_off;
             float amx = 0.f;
-#pragma unroll 2
-            for (int k = 0; k < (BM * CW) / (8 * 128); ++k) {
-                const int w = wlo + hi_w[k];
-                float2 v[8];
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass) named_sync(1 + wg, 128);  // the staging buffer is free again
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    v[j] = stage[w + w8[j]];
-                    amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                for (int c0 = 0; c0 < PCW; c0 += 16) {
+                    uint32_t r0[16], r1[16];
+                    tmem_ld16(acc + (uint32_t)(pass * PCW + c0), r0);
+                    tmem_ld16(acc + (uint32_t)(BN + pass * PCW + c0), r1);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        stage[row * PSLD + c0 + j] =
+                            make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
+                                        scale_pow2(__uint_as_float(r1[j]), pe));
                 }
-                const uint64_t o = olo | hi_off[k];
-                if (d.planar_out) {
-                    planar_out_store8(d.pout, c.s, cbase | o, v, eo);
-                } else {
-                    float4 *c4 = reinterpret_cast<float4 *>(C + o);
+                if (pass) {
+                    // the accumulator buffer may be refilled once all eight warps have read it
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
+                }
+                named_sync(1 + wg, 128);
+                const uint64_t cbase = cbase0 | (pass ? pass_off : 0ull);
+                float2 *C = d.C + (int64_t)c.s * d.sC + cbase;
+#pragma unroll 2
+                for (int k = 0; k < (BM * PCW) / (8 * 128); ++k) {
+                    const int w = wlo + hi_w[k];
+                    float2 v[8];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
-                                            v[2 * j + 1].y);
+                    for (int j = 0; j < 8; ++j) {
+                        v[j] = stage[w + w8[j]];
+                        amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                    }
+                    const uint64_t o = olo | hi_off[k];
+                    if (d.planar_out) {
+                        planar_out_store8(d.pout, c.s, cbase | o, v, eo);
+                    } else {
+                        float4 *c4 = reinterpret_cast<float4 *>(C + o);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
+                                                v[2 * j + 1].y);
+                    }
                 }
             }
             if (d.amax_out) amax_publish(d.amax_out + c.s, amx);

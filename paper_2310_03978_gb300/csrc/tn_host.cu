@@ -944,7 +944,9 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     // epilogue chunk: 7 row bits and 6 column bits, sorted by position in C; the first three
     // are always positions 0-2 (C's three lowest labels are among the lowest three of M and
     // of N), which the epilogue's 8-element stores rely on
-    tn::sort_tile_bits(7, 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+    // (the persistent short-K variants stage 32-column chunks: 7 row and 5 column bits)
+    const bool pers = variant == 12 || variant == 13;
+    tn::sort_tile_bits(7, pers ? 5 : 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
     if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
         return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the epilogue chunk",
                     (int)(&st - &p->steps[0]));
