@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--step-profile", type=int, default=0,
+                    help="per-step roofline of the circuit workload: print the N slowest steps")
     ap.add_argument("--step", default=None,
                     help="single-step microbench 'lm,ln,lk' (log2 of m, n, k) instead of the "
                          "circuit: one random dense contraction with shuffled label orders")
@@ -498,6 +500,71 @@ def run_step_bench(args):
     net.close()
 
 
+def run_step_profile(args):
+    """Per-step roofline of the bench workload: every step's CUDA-event time in profile mode
+    (after the warm-up calls, averaged over --steps calls), its T_cc and algorithmic bytes (the
+    storage formats the plan uses), the bound of its kernel class (tensor cores: the measured
+    BF16 peak, halved for TF32; CUDA cores: the FP32 ALU peak; both against the measured HBM copy
+    bandwidth) and the fraction of that roofline reached.  One JSON line per step, slowest
+    first, then a summary line."""
+    import torch
+    from paper_2310_03978_gb300 import tn, workload as W
+    wl = W.bench_workload()
+    net = tn.Network.from_workload(wl.network)
+    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, profile=True,
+                   autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
+    info = plan.info()
+    nsteps = info["num_steps"]
+    amps = torch.zeros(1 << len(wl.network.open_labels), dtype=torch.complex128, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        plan.contract(amps)
+    torch.cuda.synchronize()
+    before = [plan.step_info(i) for i in range(nsteps)]
+    for _ in range(args.steps):
+        plan.contract(amps)
+    torch.cuda.synchronize()
+    pk = peaks()
+    hbm = pk["hbm_gbs"] * 1e9
+    tensor = pk["bf16_tflops_sustained"] * 1e12 * (0.5 if args.mode in ("tf32", "split_tf32")
+                                                  else 1.0)
+    alu = 80.54784e12
+    rows = []
+    for i in range(nsteps):
+        a = plan.step_info(i)
+        b = before[i]
+        n = a["launches"] - b["launches"]
+        if n <= 0:
+            continue
+        ms = (a["time_ms"] - b["time_ms"] + a["prep_ms"] - b["prep_ms"]) / args.steps
+        sl = info["slices_in_flight"] if a["slice_dependent"] else 1
+        tcc, tmc = a["tcc"] * sl, a["tmc_bytes"] * sl
+        form = a["gemm_form"]
+        # executed tensor work: 4M = T_cc, 3M = 3/4 T_cc, compensated = 3 T_cc
+        executed = tcc * {2: 0.75, 3: 3.0}.get(form, 1.0)
+        compute = executed / tensor if a["kernel_name"] == "gemm_tc" else tcc / alu
+        roof = max(compute, tmc / hbm)
+        rows.append({"step": i, "kernel": a["kernel_name"], "variant": a["tc_variant"],
+                     "log2_mnk": [a["log2_m"], a["log2_n"], a["log2_k"]],
+                     "slices": sl, "ms": ms, "tflops": tcc / (ms / 1e3) / 1e12,
+                     "gbs": tmc / (ms / 1e3) / 1e9,
+                     "bound": "tensor" if compute >= tmc / hbm and a["kernel_name"] == "gemm_tc"
+                     else ("alu" if compute >= tmc / hbm else "hbm"),
+                     "roofline_ms": roof * 1e3, "frac": roof * 1e3 / ms,
+                     "store_run_log2": a["store_run_log2"]})
+    rows.sort(key=lambda r: -r["ms"])
+    for r in rows[:args.step_profile]:
+        print(json.dumps(r))
+    total = sum(r["ms"] for r in rows)
+    roof = sum(r["roofline_ms"] for r in rows)
+    print(json.dumps({"summary": True, "workload": WORKLOAD, "mode": args.mode,
+                      "steps_timed": len(rows), "sum_ms": total, "roofline_ms": roof,
+                      "frac": roof / total, "peaks": {"hbm_gbs": pk["hbm_gbs"],
+                                                      "tensor_tflops": tensor / 1e12,
+                                                      "alu_tflops": alu / 1e12}}))
+    plan.close()
+    net.close()
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
     if rank != 0:
@@ -551,6 +618,9 @@ def main():
     O.build()
     if args.step:
         run_step_bench(args)
+        return
+    if args.step_profile:
+        run_step_profile(args)
         return
     if world > 1:
         import torch

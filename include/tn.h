@@ -131,6 +131,10 @@ typedef struct {
     int32_t store_run_log2;        /* GEMM kernels: log2 of the longest run of consecutive
                                       result elements one staged chunk writes (its bits that
                                       are also the result's lowest positions)                */
+    double tmc_bytes;              /* algorithmic bytes of one slice of the step in its storage
+                                      formats: operands read once (complex64, or the planar
+                                      copies a tensor-core step reads), the result written once
+                                      (complex64, or planar when written directly)           */
 } tn_step_info;
 
 /*

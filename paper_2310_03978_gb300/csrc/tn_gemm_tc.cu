@@ -570,20 +570,41 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
 // at a time (a 128 x 32 chunk: 7 row and 5 column bits)
 constexpr int PERS_BN = 128, PERS_STG = 4, PERS_THREADS = 320, PCW = 32, PSLD = PCW + 1;
 
-template <int ESZ>
+// Shared-memory rows of RB bytes: 64 (64-byte swizzle, K elements 32 / 16 per stage for 16-bit /
+// TF32), 32 (32-byte swizzle) or 16 (no swizzle, 16-bit K = 8).  Each stage's TMA box is exactly
+// K wide for the short contractions, so no zero fill is fetched; with 16-byte rows the MMA's
+// second K half (elements 8..15) reads a zero page that sits one tile further (the descriptor's
+// leading-dimension offset).
+template <int ESZ, int RB>
 struct PersCfg {
-    static constexpr int BKT = 32;                      // 64-byte shared-memory rows
-    static constexpr int KEL = 2 * BKT / ESZ;           // K elements per stage
-    static constexpr int TILE_A = BM * BKT * 2, TILE_B = PERS_BN * BKT * 2;
-    static constexpr int STAGE_BYTES = 2 * (TILE_A + TILE_B);
+    static constexpr int KEL = RB / ESZ;                  // K elements per stage
+    static constexpr int TILE = BM * RB;                  // one plane of A or B (128 rows)
+    static constexpr int TSTRIDE = RB == 16 ? 2 * TILE : TILE;  // tile + zero page
+    static constexpr int STAGE_BYTES = 4 * TSTRIDE;       // A re, A im, B re, B im
+    static constexpr int TX_BYTES = 4 * TILE;             // bytes the TMA writes per stage
     static constexpr int RING = PERS_STG * STAGE_BYTES;
-    static constexpr int STAGE_HALF = BM * PSLD * 8;    // staging of one 128 x 32 chunk
-    static constexpr int DEP = 6 * 256 * 8;              // byte-wise deposit tables of m0, n0
+    static constexpr int STAGE_HALF = BM * PSLD * 8;      // staging of one 128 x 32 chunk
+    static constexpr int DEP = 6 * 256 * 8;               // byte-wise deposit tables of m0, n0
     static constexpr int BODY = RING + 2 * STAGE_HALF;
     static constexpr int SMEM_BYTES = BODY + DEP + 1024 + 512;
-    static constexpr int SBO = 8 * BKT * 2;
-    static constexpr uint64_t LAYOUT = 4;               // 64-byte swizzle
+    static constexpr int SBO = 8 * RB;                    // next 8-row group
+    static constexpr int LBO = RB == 16 ? TILE : 16;      // next 16 bytes of K (no swizzle)
+    static constexpr uint64_t LAYOUT = RB == 64 ? 4 : (RB == 32 ? 6 : 0);
+    static constexpr int KSTEPS = RB == 16 ? 1 : RB / 32; // MMAs (32 bytes of K) per stage
+    static_assert(RB == 16 ? ESZ == 2 : (RB == 32 || RB == 64), "row width");
 };
+
+// Shared-memory matrix descriptor with an explicit leading-dimension offset (K-major tiles).
+template <int SBO, int LBO, uint64_t LAYOUT>
+__device__ __forceinline__ uint64_t sdesc_lbo(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)(SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= LAYOUT << 61;
+    return d;
+}
 
 struct TileCoord {
     int s;
@@ -613,6 +634,10 @@ __device__ __forceinline__ void named_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+__device__ __forceinline__ void named_arrive(int id, int threads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 // Barrier over `threads` threads that also ANDs a predicate across them: every participant
 // learns whether all of them had v set (so a group leaves a loop together).
 __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
@@ -630,24 +655,25 @@ __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
     return r != 0;
 }
 
-template <int ESZ>
+template <int ESZ, int RB>
 __global__ void __launch_bounds__(PERS_THREADS, 1)
     k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
-    using F = PersCfg<ESZ>;
+    using F = PersCfg<ESZ, RB>;
     constexpr int BK = F::KEL, BN = PERS_BN;
-    auto sdesc = [](uint32_t a) { return sdesc_sw<F::SBO, F::LAYOUT>(a); };
+    auto sdesc = [](uint32_t a) { return sdesc_lbo<F::SBO, F::LBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY + F::DEP);
     uint64_t *empty = full + PERS_STG;
     uint64_t *tfull = empty + PERS_STG;   // MMA -> epilogue: accumulator buffer b is complete
-    uint64_t *tempty = tfull + 2;         // epilogue -> MMA: buffer b was read (8 arrivals)
+    uint64_t *tempty = tfull + 2;         // epilogue -> MMA: buffer b was read (4 arrivals)
     uint64_t *mdone = tempty + 2;         // the MMA warp's last commit
     uint64_t *hi_off = mdone + 1;         // [8] epilogue table: C offsets of bits 10..12
     int *hi_w = reinterpret_cast<int *>(hi_off + 8);  // [8] their staging offsets
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(hi_w + 8);
     int *aborted = reinterpret_cast<int *>(tmem_slot + 1);
+    int *drain_stop = aborted + 1;        // the drain warps ended the staging hand-off
 
     // deposit tables: dep[j][b] = C offset of byte b of the tile row index (j = 0..2) or of
     // the tile column index (j = 3..5), i.e. of m bits 7 + 8 j .. and n bits 7 + 8 (j - 3) ..
@@ -658,6 +684,15 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     const uint32_t total = tiles_m * tn32 * (uint32_t)slices;
     const int num_kb = ((1 << d.lk) + BK - 1) / BK;
     const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
+    if (RB == 16) {
+        // zero pages: the second 16 bytes of K of every tile of every stage (never loaded)
+        for (int e = threadIdx.x; e < PERS_STG * 4 * (F::TILE / 16); e += PERS_THREADS) {
+            const int tile = e / (F::TILE / 16), q = e % (F::TILE / 16);
+            *reinterpret_cast<uint4 *>(smem + tile * F::TSTRIDE + F::TILE + q * 16) =
+                make_uint4(0u, 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     for (int e = threadIdx.x; e < 6 * 256; e += PERS_THREADS) {
         const int j = e >> 8, b = e & 255;
         const bool nside = j >= 3;
@@ -676,10 +711,11 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 8);
+            mbar_init(&tempty[b], 4);
         }
         mbar_init(mdone, 1);
         *aborted = 0;
+        *drain_stop = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmA))
                      : "memory");
@@ -731,14 +767,14 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                         break;
                     }
                     uint8_t *base = smem + st * F::STAGE_BYTES;
-                    mbar_expect_tx(&full[st], F::STAGE_BYTES);
+                    mbar_expect_tx(&full[st], F::TX_BYTES);
                     const int k0 = kb * BK;
 #pragma unroll
                     for (int pl = 0; pl < 2; ++pl) {
-                        tma_load_3d(base + pl * F::TILE_A, &d.tmA, &full[st], k0, m0,
+                        tma_load_3d(base + pl * F::TSTRIDE, &d.tmA, &full[st], k0, m0,
                                     pl * (int)d.slices_a + sa);
-                        tma_load_3d(base + 2 * F::TILE_A + pl * F::TILE_B, &d.tmB, &full[st],
-                                    k0, n0, pl * (int)d.slices_b + sbi);
+                        tma_load_3d(base + (2 + pl) * F::TSTRIDE, &d.tmB, &full[st], k0, n0,
+                                    pl * (int)d.slices_b + sbi);
                     }
                     issued = it + 1;
                 }
@@ -782,11 +818,11 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t base = smem_u32(smem + st * F::STAGE_BYTES);
-                    const uint64_t a_re = sdesc(base), a_im = sdesc(base + F::TILE_A);
-                    const uint64_t b_re = sdesc(base + 2 * F::TILE_A);
-                    const uint64_t b_im = sdesc(base + 2 * F::TILE_A + F::TILE_B);
+                    const uint64_t a_re = sdesc(base), a_im = sdesc(base + F::TSTRIDE);
+                    const uint64_t b_re = sdesc(base + 2 * F::TSTRIDE);
+                    const uint64_t b_im = sdesc(base + 3 * F::TSTRIDE);
 #pragma unroll
-                    for (int kk = 0; kk < F::BKT / 16; ++kk) {
+                    for (int kk = 0; kk < F::KSTEPS; ++kk) {
                         const uint64_t adv = (uint64_t)(kk * 32) >> 4;
                         const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
                         umma<ESZ>(acc, a_re + adv, b_re + adv, id_pos, first);
@@ -806,13 +842,75 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 mbar_wait(mdone, 0, globaltimer() + limit);
             }
         }
+    } else if (warp < 4) {
+        // drain warps: warp w reads TMEM lanes 32 w.. (rows) of each tile, 32 columns at a time,
+        // scales them and stages the 128 x 32 chunk in staging buffer n & 1 (n counts chunks)
+        const int row = warp * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        int cur_s = -1;
+        Pow2 pe{1.f, 1.f};
+        int n = 0, i = 0;
+        bool left = false;
+        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            bool ok = true;
+            if (lane == 0)
+                ok = mbar_wait(&tfull[buf], (uint32_t)(i >> 1) & 1u, globaltimer() + limit) &&
+                     !*(volatile int *)aborted;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            ok = named_and(5, 128, ok);  // the four drain warps decide together
+            if (!ok) {
+                if (lane == 0) {
+                    *aborted = 1;
+                    *drain_stop = 1;
+                }
+                // wake the store warps (they see the stop flag and leave); buffer n & 1 is
+                // theirs to wait on next
+                if (n >= 2) named_sync(3 + (n & 1), 256);
+                named_arrive(1 + (n & 1), 256);
+                left = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const TileCoord c = pers_tile(t, tiles_m, tn32);
+            if (c.s != cur_s) {
+                cur_s = c.s;
+                const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
+                pe = pow2_of(d.expA[sa] + d.expB[sbi]);
+            }
+            const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN);
+#pragma unroll 1
+            for (int q = 0; q < BN / PCW; ++q, ++n) {
+                float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
+                if (n >= 2) named_sync(3 + (n & 1), 256);  // the store warps freed this buffer
+#pragma unroll
+                for (int c0 = 0; c0 < PCW; c0 += 16) {
+                    uint32_t r0[16], r1[16];
+                    tmem_ld16(acc + (uint32_t)(q * PCW + c0), r0);
+                    tmem_ld16(acc + (uint32_t)(BN + q * PCW + c0), r1);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        stage[row * PSLD + c0 + j] =
+                            make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
+                                        scale_pow2(__uint_as_float(r1[j]), pe));
+                }
+                if (q == BN / PCW - 1) {
+                    // the accumulator buffer may be refilled once all four warps have read it
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
+                }
+                named_arrive(1 + (n & 1), 256);  // chunk n is staged
+            }
+        }
+        // take the store warps' releases of the last two chunks, so every arrival is matched
+        if (!left)
+            for (int k = n - 2; k < n; ++k)
+                if (k >= 0) named_sync(3 + (k & 1), 256);
     } else {
-        // epilogue: warp w drains rows 32 (w % 4).. and columns 64 (w / 4).. of each tile
-        const int wg = warp >> 2;                  // column half
-        const int et = threadIdx.x & 127;          // thread index inside the half
-        const int row = (warp & 3) * 32 + lane;
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + wg * F::STAGE_HALF);
+        // store warps: write staged chunk n of each tile in the order of C's memory index
+        const int et = threadIdx.x - 128;
         int w8[8];
         {
             int dq[3];
@@ -836,65 +934,34 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 olo |= 1ull << d.tb_pos[q];
             }
         const int wlo = mlo * PSLD + nlo;
-        // per-slice values, reloaded when the slice changes (a CTA's tiles run slice-major)
-        int cur_s = -1;
-        Pow2 pe{1.f, 1.f};
-        int eo = 0;
-        // C offsets of this warp's column half (n bit 6) and of the second chunk (n bit 5)
-        const uint64_t half_off = wg ? (1ull << d.posC_n[6]) : 0ull;
-        const uint64_t pass_off = 1ull << d.posC_n[5];
-        int i = 0;
-        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const int buf = i & 1;
-            bool ok = true;
-            if (lane == 0)
-                ok = mbar_wait(&tfull[buf], (uint32_t)(i >> 1) & 1u, globaltimer() + limit) &&
-                     !*(volatile int *)aborted;
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            // the four warps of a half leave together, so none is left at a named barrier
-            ok = named_and(1 + wg, 128, ok);
-            if (!ok) {
-                if (lane == 0) *aborted = 1;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // C offsets of the column chunk inside the tile: n bits 5 and 6
+        const uint64_t off5 = 1ull << d.posC_n[5], off6 = 1ull << d.posC_n[6];
+        int cur_s = -1, eo = 0;
+        int n = 0;
+        bool stop = false;
+        for (uint32_t t = blockIdx.x; t < total && !stop; t += gridDim.x) {
             const TileCoord c = pers_tile(t, tiles_m, tn32);
             if (c.s != cur_s) {
                 cur_s = c.s;
-                const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
-                pe = pow2_of(d.expA[sa] + d.expB[sbi]);
                 eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
             }
-            const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN + wg * 2 * PCW);
-            if (d.planar_out && c.first && wg == 0 && et == 0) d.pout.exps[c.s] = eo;
+            if (d.planar_out && c.first && et == 0) d.pout.exps[c.s] = eo;
             const uint64_t cbase0 = dep[0][c.mt & 255] | dep[1][(c.mt >> 8) & 255] |
                                     dep[2][(c.mt >> 16) & 255] | dep[3][c.nt & 255] |
-                                    dep[4][(c.nt >> 8) & 255] | dep[5][(c.nt >> 16) & 255] |
-                                    half_off;
+                                    dep[4][(c.nt >> 8) & 255] | dep[5][(c.nt >> 16) & 255];
             float amx = 0.f;
 #pragma unroll 1
-            for (int pass = 0; pass < 2; ++pass) {
-                if (pass) named_sync(1 + wg, 128);  // the staging buffer is free again
-#pragma unroll
-                for (int c0 = 0; c0 < PCW; c0 += 16) {
-                    uint32_t r0[16], r1[16];
-                    tmem_ld16(acc + (uint32_t)(pass * PCW + c0), r0);
-                    tmem_ld16(acc + (uint32_t)(BN + pass * PCW + c0), r1);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        stage[row * PSLD + c0 + j] =
-                            make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
-                                        scale_pow2(__uint_as_float(r1[j]), pe));
+            for (int q = 0; q < BN / PCW; ++q, ++n) {
+                named_sync(1 + (n & 1), 256);  // chunk n is staged
+                // only the drain warps end the hand-off early (after a wait of theirs ran out),
+                // so every barrier the other side waits on is still arrived at
+                if (*(volatile int *)drain_stop) {
+                    stop = true;
+                    break;
                 }
-                if (pass) {
-                    // the accumulator buffer may be refilled once all eight warps have read it
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[buf]);
-                }
-                named_sync(1 + wg, 128);
-                const uint64_t cbase = cbase0 | (pass ? pass_off : 0ull);
+                const float2 *stage =
+                    reinterpret_cast<const float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
+                const uint64_t cbase = cbase0 | ((q & 1) ? off5 : 0ull) | ((q & 2) ? off6 : 0ull);
                 float2 *C = d.C + (int64_t)c.s * d.sC + cbase;
 #pragma unroll 2
                 for (int k = 0; k < (BM * PCW) / (8 * 128); ++k) {
@@ -916,9 +983,9 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                                                 v[2 * j + 1].y);
                     }
                 }
+                named_arrive(3 + (n & 1), 256);  // buffer n & 1 is free again
             }
-            if (d.amax_out) amax_publish(d.amax_out + c.s, amx);
-            named_sync(1 + wg, 128);  // the staging buffer is free for the next tile
+            if (!stop && d.amax_out) amax_publish(d.amax_out + c.s, amx);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -968,7 +1035,8 @@ int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t row
     const int esz = dtype == 2 ? 4 : 2;
     const int row_bytes = bk * esz;
     // K must fill whole 16-byte rows; a K below the tile is zero-filled by the tensor map
-    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (row_bytes != 64 && row_bytes != 128) ||
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 ||
+        (row_bytes != 16 && row_bytes != 32 && row_bytes != 64 && row_bytes != 128) ||
         (K * esz) % 16 != 0 || (K > bk && K % bk != 0) || dtype < 0 || dtype > 2)
         return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
@@ -981,7 +1049,10 @@ int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t row
                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     CUresult r = enc(reinterpret_cast<CUtensorMap *>(tmap_host), ty, 3, const_cast<void *>(base),
                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     row_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                     : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                     : row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                       : CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -3;
 }
@@ -1028,10 +1099,11 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 
 }  // namespace
 
-template <int ESZ>
+template <int ESZ, int RB>
 cudaError_t configure_pers() {
-    return cudaFuncSetAttribute(k_gemm_tc_pers<ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                PersCfg<ESZ>::SMEM_BYTES);
+    return cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PersCfg<ESZ, RB>::SMEM_BYTES);
 }
 
 int sm_count() {
@@ -1046,7 +1118,7 @@ int sm_count() {
     return n;
 }
 
-template <int ESZ>
+template <int ESZ, int RB>
 cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     // tile rows and columns index the deposit tables with 24 bits each; tiles count in 32 bits
     if (d.ln < 7 || d.lk < 3 || d.lk > 9 || d.lm > 31 || d.ln > 31 ||
@@ -1057,17 +1129,35 @@ cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (total > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     int64_t grid = sm_count();
     if (grid > total) grid = total;
-    k_gemm_tc_pers<ESZ><<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ>::SMEM_BYTES, st>>>(
+    k_gemm_tc_pers<ESZ, RB><<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ, RB>::SMEM_BYTES, st>>>(
         d, tiles_n, slices);
     return cudaGetLastError();
 }
 
-// Variants 12 (16-bit) and 13 (TF32) are the persistent short-K kernel.
-constexpr int kPersFp16 = 12, kPersTf32 = 13;
+// Variants 12-16 are the persistent short-K kernel: 16-bit with rows of 64, 16 and 32 bytes
+// (12, 14, 15), TF32 with rows of 64 and 32 bytes (13, 16).
+constexpr int kPersFp16 = 12, kPersTf32 = 13, kPersFp16R16 = 14, kPersFp16R32 = 15,
+              kPersTf32R32 = 16;
+
+bool is_pers(int v) { return v >= kPersFp16 && v <= kPersTf32R32; }
+
+int pers_kel(int v) {
+    switch (v) {
+        case kPersFp16: return PersCfg<2, 64>::KEL;
+        case kPersTf32: return PersCfg<4, 64>::KEL;
+        case kPersFp16R16: return PersCfg<2, 16>::KEL;
+        case kPersFp16R32: return PersCfg<2, 32>::KEL;
+        case kPersTf32R32: return PersCfg<4, 32>::KEL;
+    }
+    return 0;
+}
 
 cudaError_t tc_prepare() {
-    cudaError_t e = configure_pers<2>();
-    if (e == cudaSuccess) e = configure_pers<4>();
+    cudaError_t e = configure_pers<2, 64>();
+    if (e == cudaSuccess) e = configure_pers<4, 64>();
+    if (e == cudaSuccess) e = configure_pers<2, 16>();
+    if (e == cudaSuccess) e = configure_pers<2, 32>();
+    if (e == cudaSuccess) e = configure_pers<4, 32>();
 #define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb, esz) \
     if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb, esz>();
     TN_TC_VARIANTS(TN_TC_CONFIGURE)
@@ -1077,8 +1167,7 @@ cudaError_t tc_prepare() {
 
 // K elements per pipeline stage of a variant (the tensor map's box width)
 int tc_variant_bk(int variant) {
-    if (variant == kPersFp16) return PersCfg<2>::KEL;
-    if (variant == kPersTf32) return PersCfg<4>::KEL;
+    if (is_pers(variant)) return pers_kel(variant);
     switch (variant) {
 #define TN_TC_BK(id, npl, bk, bn, stg, minb, esz) \
     case id: return 2 * bk / esz;
@@ -1089,7 +1178,7 @@ int tc_variant_bk(int variant) {
 }
 
 int tc_variant_bn(int variant) {
-    if (variant == kPersFp16 || variant == kPersTf32) return PERS_BN;
+    if (is_pers(variant)) return PERS_BN;
     switch (variant) {
 #define TN_TC_BN(id, npl, bk, bn, stg, minb, esz) \
     case id: return bn;
@@ -1100,7 +1189,7 @@ int tc_variant_bn(int variant) {
 }
 
 bool tc_variant_tf32(int variant) {
-    if (variant == kPersFp16 || variant == kPersTf32) return variant == kPersTf32;
+    if (is_pers(variant)) return variant == kPersTf32 || variant == kPersTf32R32;
     switch (variant) {
 #define TN_TC_ESZ(id, npl, bk, bn, stg, minb, esz) \
     case id: return esz == 4;
@@ -1114,7 +1203,7 @@ bool tc_variant_tf32(int variant) {
 // two CTAs per SM; long ones use the 128 x 256 tile (1.98 PFLOP/s on m=2^13, n=2^14, k=2^14
 // against 1.79 for 128 x 128), or 128 x 128 when N < 256.
 int tc_variant_form(int variant) {
-    if (variant == kPersFp16 || variant == kPersTf32) return 1;
+    if (is_pers(variant)) return 1;
     switch (variant) {
 #define TN_TC_FORM(id, npl, bk, bn, stg, minb, esz) \
     case id: return npl == 3 ? 2 : (npl == 4 ? 3 : 1);
@@ -1124,10 +1213,10 @@ int tc_variant_form(int variant) {
     return 0;
 }
 
-int tc_num_variants() { return 14; }
+int tc_num_variants() { return 17; }
 
 bool tc_variant_fits(int variant, int lk, int ln) {
-    if (variant == kPersFp16 || variant == kPersTf32) return lk >= 3 && lk <= 9 && ln >= 7;
+    if (is_pers(variant)) return lk >= 3 && lk <= 9 && ln >= 7;
     const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
     if (bk == 0) return false;
     if (bk == 64 && lk < 6) return false;
@@ -1143,7 +1232,7 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
     if (tf32) {
         if (form == 3) return 11;
         if (form == 2) return 10;
-        if (pers) return kPersTf32;
+        if (pers) return lk == 3 ? kPersTf32R32 : kPersTf32;
         if (bn_pref == 256 && ln >= 8) return 7;
         if (bk_pref == 64) return 9;
         if (lk <= 9) return 8;
@@ -1151,7 +1240,7 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
     }
     if (form == 3) return 6;
     if (form == 2) return bk_pref == 64 ? 4 : 3;
-    if (pers) return kPersFp16;
+    if (pers) return lk == 3 ? kPersFp16R16 : (lk == 4 ? kPersFp16R32 : kPersFp16);
     if (bn_pref == 256 && ln >= 8) return 1;
     if (bk_pref == 32) return lk <= 9 ? 2 : 5;
     if (bk_pref == 64 || bn_pref == 128) return lk <= 9 && bk_pref != 64 ? 2 : 0;
@@ -1161,8 +1250,14 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
 
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (d.lm < 7 || slices > 65535) return cudaErrorInvalidValue;
-    if (d.variant == kPersFp16) return launch_pers<2>(d, slices, st);
-    if (d.variant == kPersTf32) return launch_pers<4>(d, slices, st);
+    switch (d.variant) {
+        case kPersFp16: return launch_pers<2, 64>(d, slices, st);
+        case kPersTf32: return launch_pers<4, 64>(d, slices, st);
+        case kPersFp16R16: return launch_pers<2, 16>(d, slices, st);
+        case kPersFp16R32: return launch_pers<2, 32>(d, slices, st);
+        case kPersTf32R32: return launch_pers<4, 32>(d, slices, st);
+        default: break;
+    }
     switch (d.variant) {
 #define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb, esz) \
     case id: return launch_variant<npl, bk, bn, stg, minb, esz>(d, slices, st);

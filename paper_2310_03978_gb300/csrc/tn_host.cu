@@ -945,7 +945,7 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     // are always positions 0-2 (C's three lowest labels are among the lowest three of M and
     // of N), which the epilogue's 8-element stores rely on
     // (the persistent short-K variants stage 32-column chunks: 7 row and 5 column bits)
-    const bool pers = variant == 12 || variant == 13;
+    const bool pers = variant >= 12 && variant <= 16;
     tn::sort_tile_bits(7, pers ? 5 : 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
     if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
         return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the epilogue chunk",
@@ -1397,6 +1397,20 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
             run = std::min(C.rank(), 10);  // element-wise kernel: consecutive threads, C order
         }
         out->store_run_log2 = run;
+    }
+    {
+        const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
+        const double esz = tf32_mode(p->mode) ? 4.0 : 2.0;
+        auto operand = [&](const Tensor &X, int planar) {
+            const double n = std::ldexp(1.0, X.rank());
+            if (st.kernel == K_TC && planar >= 0) return n * esz * p->planars[planar].planes;
+            return n * 8.0;
+        };
+        double bytes = operand(A, st.kernel == K_TC ? st.pa : -1) +
+                       operand(B, st.kernel == K_TC ? st.pb : -1);
+        const double nc = std::ldexp(1.0, C.rank());
+        bytes += st.direct_planar >= 0 ? nc * esz * p->planars[st.direct_planar].planes : nc * 8.0;
+        out->tmc_bytes = bytes;
     }
     out->tcc = st.tcc;
     Step &ms = const_cast<Step &>(st);

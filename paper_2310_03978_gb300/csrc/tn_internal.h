@@ -221,8 +221,8 @@ unsigned int tc_status_read_and_clear();
 // Self-test of the bounded waits (see tn_selftest_wait_timeout in tn.h).
 tn_status tc_selftest_wait_timeout(int32_t limit_ms, cudaStream_t st);
 // Encode a 3-D tensor map over planar data [planes*slices][rows][K] (K contiguous; dtype 0
-// fp16, 1 bf16, 2 fp32), box {bk, box_rows, 1} with the 128-byte swizzle for rows of 128 bytes
-// (bk * element size) or the 64-byte swizzle for rows of 64 bytes.
+// fp16, 1 bf16, 2 fp32), box {bk, box_rows, 1}; the swizzle follows the row width bk * element
+// size: 128-, 64- or 32-byte swizzle for rows of 128, 64 or 32 bytes, none for 16 bytes.
 int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t rows,
                        int64_t depth, int dtype, int bk, int box_rows);
 // Tensor-core kernel variants: pick one for a step (form 1 = 4M, 2 = 3M, 3 = split; preferences

@@ -56,7 +56,7 @@ class StepInfo(C.Structure):
                 ("log2_a", C.c_int32), ("log2_b", C.c_int32), ("log2_c", C.c_int32),
                 ("gemm_form", C.c_int32), ("tcc", C.c_double), ("time_ms", C.c_double),
                 ("launches", C.c_int64), ("prep_ms", C.c_double), ("tc_variant", C.c_int32),
-                ("store_run_log2", C.c_int32)]
+                ("store_run_log2", C.c_int32), ("tmc_bytes", C.c_double)]
 
 
 class TnError(RuntimeError):

@@ -268,7 +268,8 @@ def test_short_contraction_on_tensor_cores(tn, shape):
 
 
 @pytest.mark.parametrize("mode", ["fp16_scaled", "tf32"])
-@pytest.mark.parametrize("lm,ln,lk,nsl", [(12, 10, 8, 3), (7, 7, 9, 0), (9, 8, 8, 2)])
+@pytest.mark.parametrize("lm,ln,lk,nsl", [(12, 10, 8, 3), (7, 7, 9, 0), (9, 8, 8, 2),
+                                         (12, 10, 6, 3), (10, 10, 4, 0), (11, 9, 3, 0)])
 def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
     # short contractions run on the persistent kernel (variant 12 / 13): each CTA walks tiles of
     # all slices in flight with a double-buffered accumulator; fewer tiles than SMs included
@@ -281,7 +282,10 @@ def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
     net = tn.Network(tensors, labels, out)
     plan = tn.Plan(net, [(0, 1)], sliced, mode=mode, sync_each_call=True)
     si = plan.step_info(0)
-    assert si["kernel_name"] == "gemm_tc" and si["tc_variant"] == (12 if mode != "tf32" else 13)
+    # rows of 16 / 32 / 64 bytes hold exactly k for k = 8 / 16 (16-bit) and k = 8 (TF32)
+    k = lk - nsl
+    want = {3: 16}.get(k, 13) if mode == "tf32" else {3: 14, 4: 15}.get(k, 12)
+    assert si["kernel_name"] == "gemm_tc" and si["tc_variant"] == want
     check(plan.contract_host(), ref, TOL[mode])
     plan.close()
     net.close()
