@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <vector>
 
 #include "tn_internal.h"
 #include "tn_planar_out.cuh"
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
 // the abort flag, and every role leaves its loop.
 // 4 ring stages keep the TMA loads of the next tiles in flight; the epilogue stages 32 columns
 // at a time (a 128 x 32 chunk: 7 row and 5 column bits)
-constexpr int PERS_BN = 128, PERS_STG = 4, PERS_THREADS = 320, PCW = 32, PSLD = PCW + 1;
+constexpr int PERS_BN = 128, PERS_STG = 4, PERS_THREADS = 320, PCW = 32;
 
 // Shared-memory rows of RB bytes: 64 (64-byte swizzle, K elements 32 / 16 per stage for 16-bit /
 // TF32), 32 (32-byte swizzle) or 16 (no swizzle, 16-bit K = 8).  Each stage's TMA box is exactly
@@ -583,7 +584,7 @@ struct PersCfg {
     static constexpr int STAGE_BYTES = 4 * TSTRIDE;       // A re, A im, B re, B im
     static constexpr int TX_BYTES = 4 * TILE;             // bytes the TMA writes per stage
     static constexpr int RING = PERS_STG * STAGE_BYTES;
-    static constexpr int STAGE_HALF = BM * PSLD * 8;      // staging of one 128 x 32 chunk
+    static constexpr int STAGE_HALF = BM * PCW * 8;       // staging of one 128 x 32 chunk
     static constexpr int DEP = 6 * 256 * 8;               // byte-wise deposit tables of m0, n0
     static constexpr int BODY = RING + 2 * STAGE_HALF;
     static constexpr int SMEM_BYTES = BODY + DEP + 1024 + 512;
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 off |= 1ull << d.tb_pos[q];
             }
         hi_off[threadIdx.x] = off;
-        hi_w[threadIdx.x] = mi * PSLD + ni;
+        hi_w[threadIdx.x] = (mi << 8) | ni;  // row and column parts of the chunk element
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -847,6 +848,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
         // scales them and stages the 128 x 32 chunk in staging buffer n & 1 (n counts chunks)
         const int row = warp * 32 + lane;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        int phr = 0;  // column swizzle of this row (see tc_choose_swizzle)
+#pragma unroll
+        for (int b = 0; b < 7; ++b)
+            if ((row >> b) & 1) phr ^= d.phi[b];
         int cur_s = -1;
         Pow2 pe{1.f, 1.f};
         int n = 0, i = 0;
@@ -891,7 +896,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        stage[row * PSLD + c0 + j] =
+                        stage[row * PCW + ((c0 + j) ^ phr)] =
                             make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
                                         scale_pow2(__uint_as_float(r1[j]), pe));
                 }
@@ -909,19 +914,32 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             for (int k = n - 2; k < n; ++k)
                 if (k >= 0) named_sync(3 + (k & 1), 256);
     } else {
-        // store warps: write staged chunk n of each tile in the order of C's memory index
+        // store warps: write staged chunk n of each tile in the order of C's memory index; a
+        // chunk element is (row r, column c) = the OR of the row / column parts of its sorted bits
+        // 0..2 (j), 3..9 (the thread) and 10..11 (the iteration), stored at r * 32 + (c ^ phi(r))
         const int et = threadIdx.x - 128;
-        int w8[8];
+        auto phi_of = [&](int r) {
+            int p = 0;
+#pragma unroll
+            for (int b = 0; b < 7; ++b)
+                if ((r >> b) & 1) p ^= d.phi[b];
+            return p;
+        };
+        int rj[8], cj[8];
         {
-            int dq[3];
+            int rq[3], cq[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int sq = d.tb_src[q];
-                dq[q] = (sq & 128) ? (1 << (sq & 127)) * PSLD : (1 << sq);
+                rq[q] = (sq & 128) ? 1 << (sq & 127) : 0;
+                cq[q] = (sq & 128) ? 0 : 1 << sq;
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                w8[j] = ((j & 1) ? dq[0] : 0) + ((j & 2) ? dq[1] : 0) + ((j & 4) ? dq[2] : 0);
+            for (int j = 0; j < 8; ++j) {
+                rj[j] = ((j & 1) ? rq[0] : 0) | ((j & 2) ? rq[1] : 0) | ((j & 4) ? rq[2] : 0);
+                cj[j] = ((j & 1) ? cq[0] : 0) | ((j & 2) ? cq[1] : 0) | ((j & 4) ? cq[2] : 0);
+                cj[j] |= phi_of(rj[j]) << 8;  // the swizzle of row part j rides in bits 8..
+            }
         }
         int mlo = 0, nlo = 0;
         uint64_t olo = 0;
@@ -933,7 +951,6 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
-        const int wlo = mlo * PSLD + nlo;
         // C offsets of the column chunk inside the tile: n bits 5 and 6
         const uint64_t off5 = 1ull << d.posC_n[5], off6 = 1ull << d.posC_n[6];
         int cur_s = -1, eo = 0;
@@ -965,11 +982,15 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 float2 *C = d.C + (int64_t)c.s * d.sC + cbase;
 #pragma unroll 2
                 for (int k = 0; k < (BM * PCW) / (8 * 128); ++k) {
-                    const int w = wlo + hi_w[k];
+                    const int hk = hi_w[k];
+                    const int rb = mlo | (hk >> 8), cb = nlo | (hk & 255);
+                    const int pb = phi_of(rb);
                     float2 v[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        v[j] = stage[w + w8[j]];
+                        const int r = rb | rj[j];
+                        const int cc = (cb | (cj[j] & 255)) ^ pb ^ (cj[j] >> 8);
+                        v[j] = stage[r * PCW + cc];
                         amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
                     }
                     const uint64_t o = olo | hi_off[k];
@@ -1214,6 +1235,63 @@ int tc_variant_form(int variant) {
 }
 
 int tc_num_variants() { return 17; }
+
+namespace {
+int gf2_rank(std::vector<int> v) {
+    int r = 0;
+    for (int bit = 3; bit >= 0; --bit) {
+        int piv = -1;
+        for (size_t i = r; i < v.size(); ++i)
+            if ((v[i] >> bit) & 1) {
+                piv = (int)i;
+                break;
+            }
+        if (piv < 0) continue;
+        std::swap(v[r], v[piv]);
+        for (size_t i = 0; i < v.size(); ++i)
+            if ((int)i != r && ((v[i] >> bit) & 1)) v[i] ^= v[r];
+        ++r;
+    }
+    return r;
+}
+}  // namespace
+
+void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi) {
+    // contribution of a chunk bit to the bank pair (column bits below 4: the bit itself;
+    // column bit 4: none; row bit i: phi[i])
+    auto contrib = [&](int sq, const int *ph) {
+        return (sq & 128) ? ph[sq & 127] : ((sq & 127) < 4 ? 1 << (sq & 127) : 0);
+    };
+    int best[7] = {1, 2, 4, 8, 0, 0, 0};
+    int best_score = -1;
+    int ph[7];
+    // phi of row bits 0..4 is a permutation of the four unit masks plus 0 (full rank for the
+    // drain writes); rows 5, 6 take any unit mask or 0
+    const int units[5] = {0, 1, 2, 4, 8};
+    for (int a = 0; a < 5 && best_score < 8; ++a)
+        for (int b = 0; b < 5; ++b)
+            for (int c = 0; c < 5; ++c)
+                for (int d = 0; d < 5; ++d)
+                    for (int e = 0; e < 5; ++e) {
+                        ph[0] = units[a]; ph[1] = units[b]; ph[2] = units[c];
+                        ph[3] = units[d]; ph[4] = units[e];
+                        if (gf2_rank({ph[0], ph[1], ph[2], ph[3], ph[4]}) < 4) continue;
+                        for (int f = 0; f < 5; ++f)
+                            for (int g = 0; g < 5; ++g) {
+                                ph[5] = units[f];
+                                ph[6] = units[g];
+                                std::vector<int> lanes;
+                                for (int q = 3; q < 8; ++q) lanes.push_back(contrib(tb_src[q], ph));
+                                const int score = 2 * gf2_rank(lanes);
+                                if (score > best_score) {
+                                    best_score = score;
+                                    for (int i = 0; i < 7; ++i) best[i] = ph[i];
+                                }
+                            }
+                    }
+    for (int i = 0; i < 7; ++i) phi[i] = (int8_t)best[i];
+    phi[7] = 0;
+}
 
 bool tc_variant_fits(int variant, int lk, int ln) {
     if (is_pers(variant)) return lk >= 3 && lk <= 9 && ln >= 7;

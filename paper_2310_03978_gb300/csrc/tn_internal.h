@@ -211,6 +211,8 @@ struct TcGemmDesc {
     int8_t tb_pos[16];         //   C: (is_row << 7) | bit index, and its position in C
     int8_t posC_m[TN_MAXR];
     int8_t posC_n[TN_MAXR];
+    int8_t phi[8];             // persistent short-K epilogue: XOR swizzle of the staging column
+                               //   by row bit i (a bit mask below 16; see tc_choose_swizzle)
 };
 bool tc_available();
 // Set the kernels' shared-memory limits (once per device, outside any stream capture).
@@ -234,5 +236,10 @@ int tc_variant_bn(int variant);
 int tc_variant_form(int variant);  // 1 = 4M, 2 = 3M, 3 = split 4M (hi/lo planes)
 int tc_num_variants();
 bool tc_variant_fits(int variant, int lk, int ln);
+// Staging swizzle of the persistent kernel's 128 x 32 chunk: element (row r, column c) sits at
+// r * 32 + (c ^ phi(r)), phi linear in the row bits (phi[i] for row bit i).  Chosen so that the
+// drain warps' writes (lanes = row bits 0..4) and the store warps' reads (lanes = the chunk's
+// sorted bits 3..7) each spread over all 16 eight-byte bank pairs.
+void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi);
 
 }  // namespace tn
