@@ -184,6 +184,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -657,7 +671,7 @@ __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
 }
 
 template <int ESZ, int RB>
-__global__ void __launch_bounds__(PERS_THREADS, 1)
+__global__ void __maxnreg__(200)
     k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
     using F = PersCfg<ESZ, RB>;
     constexpr int BK = F::KEL, BN = PERS_BN;
@@ -879,35 +893,47 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const TileCoord c = pers_tile(t, tiles_m, tn32);
             if (c.s != cur_s) {
+                // staged values are the result times 2^-eo when it is written as scaled planar
+                // numbers (one power-of-two factor here, none in the store warps)
                 cur_s = c.s;
                 const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
-                pe = pow2_of(d.expA[sa] + d.expB[sbi]);
+                const int eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
+                pe = pow2_of(d.expA[sa] + d.expB[sbi] - eo);
             }
             const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN);
-#pragma unroll 1
-            for (int q = 0; q < BN / PCW; ++q, ++n) {
+            // chunk q's 32 columns (re, im) are loaded while chunk q - 1 is staged: one TMEM
+            // round trip per chunk is hidden behind the previous chunk's shared-memory stores
+            uint32_t re0[32], im0[32], re1[32], im1[32];
+            tmem_ld32(acc, re0);
+            tmem_ld32(acc + (uint32_t)BN, im0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            auto stage_chunk = [&](const uint32_t (&re)[32], const uint32_t (&im)[32]) {
                 float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
                 if (n >= 2) named_sync(3 + (n & 1), 256);  // the store warps freed this buffer
 #pragma unroll
-                for (int c0 = 0; c0 < PCW; c0 += 16) {
-                    uint32_t r0[16], r1[16];
-                    tmem_ld16(acc + (uint32_t)(q * PCW + c0), r0);
-                    tmem_ld16(acc + (uint32_t)(BN + q * PCW + c0), r1);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        stage[row * PCW + ((c0 + j) ^ phr)] =
-                            make_float2(scale_pow2(__uint_as_float(r0[j]), pe),
-                                        scale_pow2(__uint_as_float(r1[j]), pe));
-                }
-                if (q == BN / PCW - 1) {
-                    // the accumulator buffer may be refilled once all four warps have read it
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[buf]);
-                }
+                for (int j = 0; j < 32; ++j)
+                    stage[row * PCW + (j ^ phr)] = make_float2(
+                        scale_pow2(__uint_as_float(re[j]), pe), scale_pow2(__uint_as_float(im[j]), pe));
                 named_arrive(1 + (n & 1), 256);  // chunk n is staged
-            }
+                ++n;
+            };
+            tmem_ld32(acc + (uint32_t)PCW, re1);
+            tmem_ld32(acc + (uint32_t)(BN + PCW), im1);
+            stage_chunk(re0, im0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_ld32(acc + (uint32_t)(2 * PCW), re0);
+            tmem_ld32(acc + (uint32_t)(BN + 2 * PCW), im0);
+            stage_chunk(re1, im1);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_ld32(acc + (uint32_t)(3 * PCW), re1);
+            tmem_ld32(acc + (uint32_t)(BN + 3 * PCW), im1);
+            stage_chunk(re0, im0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // every column of the accumulator buffer has been read: it may be refilled
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            stage_chunk(re1, im1);
         }
         // take the store warps' releases of the last two chunks, so every arrival is matched
         if (!left)
@@ -925,7 +951,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 if ((r >> b) & 1) p ^= d.phi[b];
             return p;
         };
-        int rj[8], cj[8];
+        // element j of an 8-run sits at row part rj, column part cj (disjoint from the other
+        // parts), so its address is (rb + rj) * 32 + ((cb ^ phi(rb)) ^ (cj ^ phi(rj))):
+        // rj32[j] = 32 rj and yj[j] = cj ^ phi(rj) are constants of the thread
+        int rj32[8], yj[8];
         {
             int rq[3], cq[3];
 #pragma unroll
@@ -936,9 +965,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                rj[j] = ((j & 1) ? rq[0] : 0) | ((j & 2) ? rq[1] : 0) | ((j & 4) ? rq[2] : 0);
-                cj[j] = ((j & 1) ? cq[0] : 0) | ((j & 2) ? cq[1] : 0) | ((j & 4) ? cq[2] : 0);
-                cj[j] |= phi_of(rj[j]) << 8;  // the swizzle of row part j rides in bits 8..
+                const int r = ((j & 1) ? rq[0] : 0) | ((j & 2) ? rq[1] : 0) | ((j & 4) ? rq[2] : 0);
+                const int c = ((j & 1) ? cq[0] : 0) | ((j & 2) ? cq[1] : 0) | ((j & 4) ? cq[2] : 0);
+                rj32[j] = r * PCW;
+                yj[j] = c ^ phi_of(r);
             }
         }
         int mlo = 0, nlo = 0;
@@ -951,6 +981,15 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 else nlo |= 1 << sq;
                 olo |= 1ull << d.tb_pos[q];
             }
+        // row base (times 32) and swizzled column base of the thread's 8-run in iteration k
+        int rbk32[4], xk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int hk = hi_w[k];
+            const int rb = mlo | (hk >> 8), cb = nlo | (hk & 255);
+            rbk32[k] = rb * PCW;
+            xk[k] = cb ^ phi_of(rb);
+        }
         // C offsets of the column chunk inside the tile: n bits 5 and 6
         const uint64_t off5 = 1ull << d.posC_n[5], off6 = 1ull << d.posC_n[6];
         int cur_s = -1, eo = 0;
@@ -966,7 +1005,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             const uint64_t cbase0 = dep[0][c.mt & 255] | dep[1][(c.mt >> 8) & 255] |
                                     dep[2][(c.mt >> 16) & 255] | dep[3][c.nt & 255] |
                                     dep[4][(c.nt >> 8) & 255] | dep[5][(c.nt >> 16) & 255];
-            float amx = 0.f;
+            float amj[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // independent chains
 #pragma unroll 1
             for (int q = 0; q < BN / PCW; ++q, ++n) {
                 named_sync(1 + (n & 1), 256);  // chunk n is staged
@@ -980,22 +1019,18 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     reinterpret_cast<const float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
                 const uint64_t cbase = cbase0 | ((q & 1) ? off5 : 0ull) | ((q & 2) ? off6 : 0ull);
                 float2 *C = d.C + (int64_t)c.s * d.sC + cbase;
-#pragma unroll 2
+#pragma unroll
                 for (int k = 0; k < (BM * PCW) / (8 * 128); ++k) {
-                    const int hk = hi_w[k];
-                    const int rb = mlo | (hk >> 8), cb = nlo | (hk & 255);
-                    const int pb = phi_of(rb);
+                    const int rb32 = rbk32[k], xb = xk[k];
                     float2 v[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const int r = rb | rj[j];
-                        const int cc = (cb | (cj[j] & 255)) ^ pb ^ (cj[j] >> 8);
-                        v[j] = stage[r * PCW + cc];
-                        amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                        v[j] = stage[rb32 + rj32[j] + (xb ^ yj[j])];
+                        amj[j] = fmaxf(amj[j], fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
                     }
                     const uint64_t o = olo | hi_off[k];
                     if (d.planar_out) {
-                        planar_out_store8(d.pout, c.s, cbase | o, v, eo);
+                        planar_out_store8_prescaled(d.pout, c.s, cbase | o, v);
                     } else {
                         float4 *c4 = reinterpret_cast<float4 *>(C + o);
 #pragma unroll
@@ -1006,7 +1041,13 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 }
                 named_arrive(3 + (n & 1), 256);  // buffer n & 1 is free again
             }
-            if (!stop && d.amax_out) amax_publish(d.amax_out + c.s, amx);
+            if (!stop && d.amax_out) {
+                float amx = amj[0];
+#pragma unroll
+                for (int j = 1; j < 8; ++j) amx = fmaxf(amx, amj[j]);
+                // the true scale of planar values is 2^eo times the staged one
+                amax_publish(d.amax_out + c.s, d.planar_out ? scale_pow2(amx, pow2_of(eo)) : amx);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -86,7 +86,7 @@ __device__ __forceinline__ __nv_bfloat162 pack_pair<__nv_bfloat162>(float a, flo
 __device__ __forceinline__ float2 unpack_pair(__half2 h) { return __half22float2(h); }
 __device__ __forceinline__ float2 unpack_pair(__nv_bfloat162 h) { return __bfloat1622float2(h); }
 
-template <typename T2>
+template <typename T2, bool SCALE>
 __device__ __forceinline__ void planar_out_store8_t(const PlanarOut &o, int64_t s, uint64_t off,
                                                     const float2 (&v)[8], int e) {
     union Row {
@@ -96,8 +96,10 @@ __device__ __forceinline__ void planar_out_store8_t(const PlanarOut &o, int64_t 
     const Pow2 pe = pow2_of(-e);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float r0 = scale_pow2(v[2 * j].x, pe), i0 = scale_pow2(v[2 * j].y, pe);
-        const float r1 = scale_pow2(v[2 * j + 1].x, pe), i1 = scale_pow2(v[2 * j + 1].y, pe);
+        const float r0 = SCALE ? scale_pow2(v[2 * j].x, pe) : v[2 * j].x;
+        const float i0 = SCALE ? scale_pow2(v[2 * j].y, pe) : v[2 * j].y;
+        const float r1 = SCALE ? scale_pow2(v[2 * j + 1].x, pe) : v[2 * j + 1].x;
+        const float i1 = SCALE ? scale_pow2(v[2 * j + 1].y, pe) : v[2 * j + 1].y;
         re.h[j] = pack_pair<T2>(r0, r1);
         im.h[j] = pack_pair<T2>(i0, i1);
         if (o.planes == 3) p2.h[j] = pack_pair<T2>(r0 + i0, r1 + i1);
@@ -116,8 +118,15 @@ __device__ __forceinline__ void planar_out_store8_t(const PlanarOut &o, int64_t 
 
 __device__ __forceinline__ void planar_out_store8(const PlanarOut &o, int64_t s, uint64_t off,
                                                   const float2 (&v)[8], int e) {
-    if (o.bf16) planar_out_store8_t<__nv_bfloat162>(o, s, off, v, e);
-    else planar_out_store8_t<__half2>(o, s, off, v, e);
+    if (o.bf16) planar_out_store8_t<__nv_bfloat162, true>(o, s, off, v, e);
+    else planar_out_store8_t<__half2, true>(o, s, off, v, e);
+}
+
+// The same for values already multiplied by 2^-e.
+__device__ __forceinline__ void planar_out_store8_prescaled(const PlanarOut &o, int64_t s,
+                                                            uint64_t off, const float2 (&v)[8]) {
+    if (o.bf16) planar_out_store8_t<__nv_bfloat162, false>(o, s, off, v, 0);
+    else planar_out_store8_t<__half2, false>(o, s, off, v, 0);
 }
 
 }  // namespace tn
