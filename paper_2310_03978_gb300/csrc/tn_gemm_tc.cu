@@ -184,19 +184,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-}
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
     asm volatile(
@@ -671,7 +658,7 @@ __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
 }
 
 template <int ESZ, int RB>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(PERS_THREADS, 1)
     k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
     using F = PersCfg<ESZ, RB>;
     constexpr int BK = F::KEL, BN = PERS_BN;
@@ -901,39 +888,45 @@ __global__ void __maxnreg__(200)
                 pe = pow2_of(d.expA[sa] + d.expB[sbi] - eo);
             }
             const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN);
-            // chunk q's 32 columns (re, im) are loaded while chunk q - 1 is staged: one TMEM
-            // round trip per chunk is hidden behind the previous chunk's shared-memory stores
-            uint32_t re0[32], im0[32], re1[32], im1[32];
-            tmem_ld32(acc, re0);
-            tmem_ld32(acc + (uint32_t)BN, im0);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            auto stage_chunk = [&](const uint32_t (&re)[32], const uint32_t (&im)[32]) {
+            // the accumulator is read 16 columns (re, im) at a time, the next 16 being loaded
+            // while the current ones are staged, so most of each TMEM round trip is hidden; a
+            // 128 x 32 chunk is two such units
+            uint32_t re0[16], im0[16], re1[16], im1[16];
+            auto stage_unit = [&](const uint32_t (&re)[16], const uint32_t (&im)[16], int h) {
                 float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
-                if (n >= 2) named_sync(3 + (n & 1), 256);  // the store warps freed this buffer
+                if (h == 0 && n >= 2) named_sync(3 + (n & 1), 256);  // buffer freed
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    stage[row * PCW + (j ^ phr)] = make_float2(
+                for (int j = 0; j < 16; ++j)
+                    stage[row * PCW + ((16 * h + j) ^ phr)] = make_float2(
                         scale_pow2(__uint_as_float(re[j]), pe), scale_pow2(__uint_as_float(im[j]), pe));
-                named_arrive(1 + (n & 1), 256);  // chunk n is staged
-                ++n;
+                if (h == 1) {
+                    named_arrive(1 + (n & 1), 256);  // chunk n is staged
+                    ++n;
+                }
             };
-            tmem_ld32(acc + (uint32_t)PCW, re1);
-            tmem_ld32(acc + (uint32_t)(BN + PCW), im1);
-            stage_chunk(re0, im0);
+            auto load_unit = [&](int u, uint32_t (&re)[16], uint32_t (&im)[16]) {
+                tmem_ld16(acc + (uint32_t)(16 * u), re);
+                tmem_ld16(acc + (uint32_t)(BN + 16 * u), im);
+            };
+            load_unit(0, re0, im0);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            tmem_ld32(acc + (uint32_t)(2 * PCW), re0);
-            tmem_ld32(acc + (uint32_t)(BN + 2 * PCW), im0);
-            stage_chunk(re1, im1);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            tmem_ld32(acc + (uint32_t)(3 * PCW), re1);
-            tmem_ld32(acc + (uint32_t)(BN + 3 * PCW), im1);
-            stage_chunk(re0, im0);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            // every column of the accumulator buffer has been read: it may be refilled
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-            stage_chunk(re1, im1);
+#pragma unroll
+            for (int u = 0; u < BN / 16; u += 2) {
+                load_unit(u + 1, re1, im1);
+                stage_unit(re0, im0, 0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (u + 2 < BN / 16) {
+                    load_unit(u + 2, re0, im0);
+                    stage_unit(re1, im1, 1);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                } else {
+                    // every column of the accumulator buffer has been read: it may be refilled
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
+                    stage_unit(re1, im1, 1);
+                }
+            }
         }
         // take the store warps' releases of the last two chunks, so every arrival is matched
         if (!left)
