@@ -66,6 +66,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--feed-tc", action="store_true",
+                    help="single-step microbench: the step's result feeds a second tensor-core "
+                         "step, so it is written as scaled planar 16-bit numbers")
     ap.add_argument("--step-profile", type=int, default=0,
                     help="per-step roofline of the circuit workload: print the N slowest steps")
     ap.add_argument("--step", default=None,
@@ -454,15 +457,28 @@ def run_step_bench(args):
     scale = 2.0 ** (-(ra + rb) / 4)  # amplitude-like magnitudes
     A = (rng.standard_normal((2,) * ra) + 1j * rng.standard_normal((2,) * ra)) * scale
     B = (rng.standard_normal((2,) * rb) + 1j * rng.standard_normal((2,) * rb)) * scale
-    net = tn.Network([A, B], [la, lb], out)
-    ref = O.contract([A, B], [la, lb], out, [(0, 1)]) if lm + ln + lk <= 22 else None
+    tensors, labels, path = [A, B], [la, lb], [(0, 1)]
+    if args.feed_tc:
+        # the measured step's result feeds a second tensor-core step (over all but two of its M
+        # labels, with 7 new labels), so it is written directly as scaled planar 16-bit numbers
+        if lm < 9:
+            raise SystemExit("--feed-tc needs lm >= 9")
+        P = list(range(300, 307))
+        T = (rng.standard_normal((2,) * (lm - 2 + 7)) +
+             1j * rng.standard_normal((2,) * (lm - 2 + 7))) * 2.0 ** -6
+        tensors, labels = [A, B, T], [la, lb, M[2:] + P]
+        out = M[:2] + N + P
+        path = [(0, 1), (0, 2)]
+    net = tn.Network(tensors, labels, out)
+    ref = (O.contract(tensors, labels, out, path)
+           if lm + ln + lk <= 22 and not args.feed_tc else None)
     pk = peaks()
     bind_bytes = 24.0 * ((1 << ra) + (1 << rb))  # complex128 read + complex64 written
-    amps = torch.zeros(1 << (lm + ln), dtype=torch.complex128, device="cuda")
+    amps = torch.zeros(1 << len(out), dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
     for mode in args.mode.split(","):
         for form in args.gemm_form.split(","):
-            plan = tn.Plan(net, [(0, 1)], (), mode=mode, profile=True, gemm_form=form,
+            plan = tn.Plan(net, path, (), mode=mode, profile=True, gemm_form=form,
                            tc_bk=args.tc_bk, tc_bn=args.tc_bn, autotune=bool(args.autotune))
             for _ in range(args.warmup):
                 plan.contract(amps, stream=stream)
@@ -494,7 +510,8 @@ def run_step_bench(args):
                 "bind_frac_hbm": bind_bytes / (bind_ms / 1e3) / 1e9 / pk["hbm_gbs"],
                 "config": {"lm": lm, "ln": ln, "lk": lk, "rank_a": ra, "rank_b": rb,
                            "mode": mode, "gemm_form": form, "tc_bk": args.tc_bk,
-                           "tc_bn": args.tc_bn, "autotune": args.autotune},
+                           "tc_bn": args.tc_bn, "autotune": args.autotune,
+                           "feeds_tensor_cores": bool(args.feed_tc)},
                 "rel_l2_vs_oracle": check}))
             plan.close()
     net.close()
