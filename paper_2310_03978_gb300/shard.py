@@ -58,3 +58,44 @@ def max_over_ranks(value: float, device=None, group=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def contract_resumable(plan, slice_begin: int, slice_end: int, checkpoint: str,
+                       chunk: int = 0, on_chunk=None):
+    """Contract slices [slice_begin, slice_end) in chunks, keeping a checkpoint of the partial FP64
+    amplitudes and of the next slice to contract, so that a job interrupted between chunks
+    resumes where it stopped (slices are independent sub-tasks whose results are summed,
+    Sec. 3.2 and Sec. 5).
+
+    ``plan`` needs ``contract_host(b, e)`` (the sum over slices [b, e) as a host complex128
+    array) and ``info()["slices_in_flight"]``; ``chunk`` is the number of slices per chunk (0: the
+    plan's slices in flight).  Chunk results are added in FP64 in chunk order.  The checkpoint
+    (numpy .npz: amplitudes, next slice, range) is written to a temporary name and renamed, so
+    the file on disk is always complete; a checkpoint for another slice range is rejected.
+    ``on_chunk(next_slice)`` runs after each saved chunk.  Returns the amplitudes of the range."""
+    import os
+    import numpy as np
+    if slice_end <= slice_begin:
+        raise ValueError("empty slice range")
+    if chunk <= 0:
+        chunk = max(1, int(plan.info()["slices_in_flight"]))
+    nxt, amps = slice_begin, None
+    if os.path.exists(checkpoint):
+        with np.load(checkpoint) as z:
+            if int(z["slice_begin"]) != slice_begin or int(z["slice_end"]) != slice_end:
+                raise ValueError("checkpoint %s is for slices [%d, %d), not [%d, %d)" % (
+                    checkpoint, int(z["slice_begin"]), int(z["slice_end"]), slice_begin,
+                    slice_end))
+            nxt = int(z["next_slice"])
+            amps = np.array(z["amps"], dtype=np.complex128)
+    while nxt < slice_end:
+        e = min(slice_end, nxt + chunk)
+        part = np.asarray(plan.contract_host(nxt, e), dtype=np.complex128)
+        amps = part.copy() if amps is None else amps + part
+        nxt = e
+        tmp = checkpoint + ".tmp.npz"
+        np.savez(tmp, amps=amps, next_slice=nxt, slice_begin=slice_begin, slice_end=slice_end)
+        os.replace(tmp, checkpoint)
+        if on_chunk is not None:
+            on_chunk(nxt)
+    return amps

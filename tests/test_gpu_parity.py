@@ -291,6 +291,31 @@ def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
     net.close()
 
 
+def test_checkpointed_contraction_on_the_gpu(tn, tmp_path):
+    # slice chunks through the C ABI, interrupted after the first chunk and resumed
+    from paper_2310_03978_gb300 import shard
+    wl = W.small_workload()
+    net = wl.network
+    sliced = W.greedy_slices(net.labels, net.open_labels, wl.path, 3)
+    ref = O.contract_network(net, wl.path)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.Plan(tnet, wl.path, sliced, mode="c64", max_slices_in_flight=2)
+    ck = str(tmp_path / "ck.npz")
+
+    class Stop(Exception):
+        pass
+
+    def stop(nxt):
+        if nxt == 2:
+            raise Stop()
+
+    with pytest.raises(Stop):
+        shard.contract_resumable(plan, 0, 8, ck, on_chunk=stop)
+    check(shard.contract_resumable(plan, 0, 8, ck), ref, TOL["c64"])
+    plan.close()
+    tnet.close()
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(tn):
     # a tensor-core CTA whose producer issues no copies: its MMA warp's wait runs out after
     # 200 ms, the kernel records the timeout and exits; the context stays usable

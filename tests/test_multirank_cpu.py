@@ -92,3 +92,51 @@ def test_slice_ranges_partition(num, world):
         assert e0 == b1
     lens = [e - b for b, e in ranges]
     assert max(lens) - min(lens) <= 1
+
+
+class _OraclePlan:
+    """Stand-in for a plan on the CPU: contract_host sums the oracle's slices [b, e)."""
+
+    def __init__(self, wl, sliced, in_flight=2):
+        from oracle import oracle as O
+        self.O, self.wl, self.sliced, self.in_flight = O, wl, sliced, in_flight
+        self.calls = []
+
+    def info(self):
+        return {"slices_in_flight": self.in_flight, "num_slices": 1 << len(self.sliced)}
+
+    def contract_host(self, b, e):
+        self.calls.append((b, e))
+        return self.O.contract_network(self.wl.network, self.wl.path, self.sliced, b, e)
+
+
+def test_checkpointed_slice_range_resumes_after_interruption(tmp_path):
+    from oracle import oracle as O
+    wl = W.small_workload()
+    net = wl.network
+    sliced = W.greedy_slices(net.labels, net.open_labels, wl.path, 3)
+    full = O.contract_network(net, wl.path)
+    ck = str(tmp_path / "ck.npz")
+
+    class Stop(Exception):
+        pass
+
+    def stop_after_two(nxt):
+        if nxt >= 4:
+            raise Stop()
+
+    plan = _OraclePlan(wl, sliced)
+    with pytest.raises(Stop):
+        shard.contract_resumable(plan, 0, 8, ck, on_chunk=stop_after_two)
+    assert plan.calls == [(0, 2), (2, 4)]
+    # a new process resumes at slice 4 and finishes the range
+    plan2 = _OraclePlan(wl, sliced)
+    amps = shard.contract_resumable(plan2, 0, 8, ck)
+    assert plan2.calls == [(4, 6), (6, 8)]
+    np.testing.assert_allclose(amps, full, rtol=0, atol=1e-13)
+    # finished: nothing left to do; another range is refused
+    plan3 = _OraclePlan(wl, sliced)
+    np.testing.assert_allclose(shard.contract_resumable(plan3, 0, 8, ck), full, atol=1e-13)
+    assert plan3.calls == []
+    with pytest.raises(ValueError):
+        shard.contract_resumable(plan3, 0, 4, ck)
