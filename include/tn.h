@@ -81,7 +81,10 @@ typedef struct {
     int32_t profile;               /* 1 = time every step with CUDA events on the contraction
                                       stream (read by tn_plan_get_step_info after the stream is
                                       synchronised)                                           */
-    int32_t tc_bk;                 /* tensor-core K tile preference: 0 = automatic, 32 or 64  */
+    int32_t tc_bk;                 /* tensor-core shared-memory row preference, in 16-bit
+                                      elements: 0 = automatic, 32 (64-byte rows) or 64
+                                      (128-byte rows); a preference selects the one-tile-per-CTA
+                                      kernels instead of the persistent short-K kernel        */
     int32_t tc_bn;                 /* tensor-core N tile preference: 0 = automatic, 128, 256  */
     int32_t autotune;              /* 1 = during the first full batch, time every applicable
                                       tensor-core kernel variant (tile shape, 4M / 3M) per step
@@ -127,7 +130,12 @@ typedef struct {
     int64_t launches;              /* profile mode: launches timed                           */
     double prep_ms;                /* profile mode: time of its operand conversions (tensor-
                                       core steps: amax + planar 16-bit copies)               */
-    int32_t tc_variant;            /* tensor-core kernel variant in use (-1 otherwise)       */
+    int32_t tc_variant;            /* tensor-core kernel variant in use (-1 otherwise):
+                                      0-5 4M / 3M 16-bit one tile per CTA (128 x 128 or
+                                      128 x 256), 6 compensated 16-bit, 7-10 the TF32
+                                      counterparts of 0-3, 11 3xTF32, 12-16 the persistent
+                                      short-K kernel (16-bit rows of 64 / 16 / 32 bytes: 12,
+                                      14, 15; TF32 rows of 64 / 32 bytes: 13, 16)            */
     int32_t store_run_log2;        /* GEMM kernels: log2 of the longest run of consecutive
                                       result elements one staged chunk writes (its bits that
                                       are also the result's lowest positions)                */

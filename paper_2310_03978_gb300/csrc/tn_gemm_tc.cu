@@ -1,23 +1,25 @@
 // Complex GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
 // C[m, n] = 2^(eA + eB) * sum_k A[m, k] * B[n, k] for one slice per grid row, where A and B are
-// stored as planar 16-bit numbers (a real plane and an imaginary plane, FP16 or BF16) scaled by
-// per-slice powers of two (the dynamic scaling that Sec. 4.2 proposes, made exact by using
-// powers of two), and the sum runs in FP32 in tensor memory.  The complex product is formed from
-// four real products (4M):
+// stored as planar numbers (a real plane and an imaginary plane: FP16 or BF16 with kind::f16, or
+// FP32 rounded to TF32 with kind::tf32) scaled by per-slice powers of two (the dynamic scaling that
+// Sec. 4.2 proposes, made exact by using powers of two), and the sum runs in FP32 in tensor memory.
+// The complex product is formed from four real products (4M):
 //     Cre = Are*Bre - Aim*Bim,   Cim = Are*Bim + Aim*Bre,
-// with the minus sign taken by the instruction descriptor's negate-A bit, or from three (3M,
+// with the minus sign taken by the instruction descriptor's negate-A bit, from three (3M,
 // Gauss's product):
 //     P1 = Are*Bre, P2 = Aim*Bim, P3 = (Are+Aim)*(Bre+Bim);  Cre = P1 - P2, Cim = P3 - P1 - P2,
-// where the sum planes Are+Aim and Bre+Bim are rounded once from FP32 by the conversion kernel.
+// where the sum planes Are+Aim and Bre+Bim are rounded once from FP32 by the conversion kernel, or
+// from compensated hi / lo planes (x = hi + lo, xy ~ hi hi + hi lo + lo hi, Sec. 4.2's 3xTF32
+// scheme) with the accumulator promoted to an FP32 running sum every 512 of K.
 //
-// One CTA computes a 128 x 128 output tile: warp 0 lane 0 issues TMA loads (128-byte swizzle)
-// into a shared-memory ring (3 stages for 4M, 2 for 3M), warp 1 lane 0 issues tcgen05.mma into
-// the TMEM accumulators (2 or 3 of 128 columns), and all four warps drain TMEM through
-// tcgen05.ld, apply the exponent and scatter the complex64 result into the consumer's memory
-// order (Sec. 4.1 index reordering, done at the producer's store).  Every mbarrier wait gives up
-// after a device-time limit, records a timeout in a status word and lets the CTA release its
-// TMEM and exit.
+// k_gemm_tc: one CTA per output tile (128 x 128 or 128 x 256): warp 0 lane 0 issues TMA loads
+// into a shared-memory ring, warp 1 lane 0 issues tcgen05.mma into the TMEM accumulators, and the
+// epilogue warps drain TMEM through tcgen05.ld, apply the exponent and scatter the result into the
+// consumer's memory order (Sec. 4.1 index reordering, done at the producer's store).
+// k_gemm_tc_pers: the persistent 4M kernel for short contractions (see its comment below).
+// Every mbarrier wait gives up after a device-time limit, records a timeout in a status word and
+// lets the CTA release its TMEM and exit.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
