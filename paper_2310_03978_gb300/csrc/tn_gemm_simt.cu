@@ -191,10 +191,18 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
 // every pair of shared-memory loads feeds 4 complex products.  The groups' sums are added in
 // group order and CTA z writes partial[z][s] (row-major M x N) for k_splitk_reduce.
 constexpr int kSkBK = 64;
+constexpr int kSkS = kSkBK * 17, kSkL = kSkBK * 65;   // one buffer: S [k][16 + 1], L [k][64 + 1]
+constexpr int kSkSmem = 2 * (kSkS + kSkL) * 8;        // double-buffered, bytes
+
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
 
 __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
-    __shared__ float2 sS[kSkBK][17];
-    __shared__ float2 sL[kSkBK][65];
+    extern __shared__ __align__(16) float2 skmem[];
     const int64_t s = blockIdx.y;
     const bool swap = d.lm > d.ln;               // S is B when M > N
     const int ls = swap ? d.ln : d.lm, ll = swap ? d.lm : d.ln;
@@ -206,23 +214,44 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
     const float2 *PL = (swap ? d.A + s * d.sA : d.B + s * d.sB) + kz;
     const int tid = threadIdx.x, g = tid >> 6, t64 = tid & 63;
     const int sg = t64 >> 4, lg = t64 & 15;
+    auto bufS = [&](int b) { return reinterpret_cast<float2(*)[17]>(skmem + b * (kSkS + kSkL)); };
+    auto bufL = [&](int b) {
+        return reinterpret_cast<float2(*)[65]>(skmem + b * (kSkS + kSkL) + kSkS);
+    };
+    // asynchronous copy of the K tile starting at k0 into buffer b (zero past this CTA's range)
+    auto prefetch = [&](int b, int64_t k0) {
+        float2(*sS)[17] = bufS(b);
+        float2(*sL)[65] = bufL(b);
+        for (int e = tid; e < S * kSkBK; e += 256) {
+            const int r = e / kSkBK, k = e % kSkBK;
+            const bool ok = k0 + k < K;
+            cp_async8(&sS[k][r], PS + (ok ? (int64_t)r * Kfull + k0 + k : 0), ok);
+        }
+        for (int e = tid; e < L * kSkBK; e += 256) {
+            const int r = e / kSkBK, k = e % kSkBK;
+            const bool ok = k0 + k < K;
+            cp_async8(&sL[k][r], PL + (ok ? (int64_t)r * Kfull + k0 + k : 0), ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     float cr[4][4], ci[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) cr[i][j] = ci[i][j] = 0.f;
-    for (int64_t k0 = 0; k0 < K; k0 += kSkBK) {
-        const int kw = K - k0 < kSkBK ? (int)(K - k0) : kSkBK;
-        __syncthreads();
-        for (int e = tid; e < S * kSkBK; e += 256) {
-            const int r = e / kSkBK, k = e % kSkBK;
-            sS[k][r] = k < kw ? PS[(int64_t)r * Kfull + k0 + k] : make_float2(0.f, 0.f);
+    const int64_t ntiles = (K + kSkBK - 1) / kSkBK;
+    prefetch(0, 0);
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int b = (int)(t & 1);
+        if (t + 1 < ntiles) {
+            prefetch(b ^ 1, (t + 1) * kSkBK);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");  // tile t has landed
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        for (int e = tid; e < L * kSkBK; e += 256) {
-            const int r = e / kSkBK, k = e % kSkBK;
-            sL[k][r] = k < kw ? PL[(int64_t)r * Kfull + k0 + k] : make_float2(0.f, 0.f);
-        }
         __syncthreads();
+        const float2(*sS)[17] = bufS(b);
+        const float2(*sL)[65] = bufL(b);
         float tr[4][4], ti[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -230,19 +259,19 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
             for (int j = 0; j < 4; ++j) tr[i][j] = ti[i][j] = 0.f;
 #pragma unroll 4
         for (int kk = g * 16; kk < g * 16 + 16; ++kk) {
-            float2 a[4], b[4];
+            float2 a[4], bb[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = sS[kk][sg + 4 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = sL[kk][lg + 16 * j];
+            for (int j = 0; j < 4; ++j) bb[j] = sL[kk][lg + 16 * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    tr[i][j] = fmaf(a[i].x, b[j].x, tr[i][j]);
-                    tr[i][j] = fmaf(-a[i].y, b[j].y, tr[i][j]);
-                    ti[i][j] = fmaf(a[i].x, b[j].y, ti[i][j]);
-                    ti[i][j] = fmaf(a[i].y, b[j].x, ti[i][j]);
+                    tr[i][j] = fmaf(a[i].x, bb[j].x, tr[i][j]);
+                    tr[i][j] = fmaf(-a[i].y, bb[j].y, tr[i][j]);
+                    ti[i][j] = fmaf(a[i].x, bb[j].y, ti[i][j]);
+                    ti[i][j] = fmaf(a[i].y, bb[j].x, ti[i][j]);
                 }
         }
 #pragma unroll
@@ -252,10 +281,10 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
                 cr[i][j] += tr[i][j];
                 ci[i][j] += ti[i][j];
             }
+        __syncthreads();  // buffer b is refilled by the prefetch of tile t + 2
     }
-    // add the four groups' sums in group order (through the L buffer: 4 x 16 x 64 float2)
-    __syncthreads();
-    float2 *red = &sL[0][0];  // [g][S index][L index], 4 * 16 * 64 = 4096 < 64 * 65
+    // add the four groups' sums in group order (through buffer 0's L part: 4 x 16 x 64 float2)
+    float2 *red = &bufL(0)[0][0];  // 4 * 16 * 64 = 4096 < 64 * 65
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -407,6 +436,11 @@ __global__ void __launch_bounds__(256, 3) k_gemm_thin(GemmDesc d) {
 
 }  // namespace
 
+cudaError_t simt_prepare() {
+    return cudaFuncSetAttribute(k_gemm_skinny, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSkSmem);
+}
+
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st) {
     const int64_t M = 1ll << d.lm, N = 1ll << d.ln;
     const int64_t tm = (M + BM - 1) / BM, tn_ = (N + BN - 1) / BN;
@@ -418,7 +452,7 @@ cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st)
     const bool skinny = d.splits > 1 && lmin <= 4 && lmax <= 6 &&
                         (1ll << d.lk) / d.splits >= kSkBK;
     if (skinny)
-        k_gemm_skinny<<<dim3(1, (unsigned)slices, (unsigned)d.splits), 256, 0, st>>>(d);
+        k_gemm_skinny<<<dim3(1, (unsigned)slices, (unsigned)d.splits), 256, kSkSmem, st>>>(d);
     else if (d.lk - (d.splits > 1 ? __builtin_ctz((unsigned)d.splits) : 0) <= 3)
         k_gemm_simt<8><<<grid, 256, 0, st>>>(d, tn_);
     else
@@ -451,6 +485,15 @@ void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, 
 // Number of K splits for a CUDA-core GEMM step: enough CTAs to fill the GPU a few times when
 // the output tiles alone cannot, with at least 256 contracted elements per split.
 int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {
+    const int lmin = lm < ln ? lm : ln, lmax = lm < ln ? ln : lm;
+    if (lmin <= 4 && lmax <= 6 && lk >= 11) {
+        // skinny (the whole output is one CTA's tile): about 16 CTAs per SM in total, each with
+        // at least 1024 contracted elements
+        const int64_t want = (16 * 152 + slices - 1) / slices;
+        int sp = 1;
+        while (sp < want && (1ll << lk) / (sp * 2) >= 1024 && sp < 4096) sp *= 2;
+        return sp;
+    }
     const int64_t tiles = ((1ll << lm) + BM - 1) / BM * (((1ll << ln) + BN - 1) / BN) * slices;
     int splits = 1;
     while (tiles * splits < 4 * 152 && (lk - 8) > 0 && (1ll << lk) / (splits * 2) >= 256 &&

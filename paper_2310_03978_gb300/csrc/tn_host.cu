@@ -463,6 +463,10 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
     p->device = net->device;
     if (opts) p->opts = *opts;
     p->tc_ok = tn::tc_available() && tn::tc_prepare() == cudaSuccess;
+    if (tn::simt_prepare() != cudaSuccess) {
+        delete p;
+        return fail(TN_ERR_CUDA, "setting the CUDA-core kernels' shared-memory limit failed");
+    }
 
     std::map<int, int> cnt;  // holders of each label (tensors + output)
     for (auto &ls : net->labels)

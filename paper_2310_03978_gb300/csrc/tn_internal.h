@@ -155,6 +155,8 @@ __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {
 
 // Kernel launchers (stream-ordered; return the launch error).
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
+// Set the CUDA-core kernels' shared-memory limits (once per device, outside any stream capture).
+cudaError_t simt_prepare();
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st);
 int gemm_simt_splits(int lm, int ln, int lk, int64_t slices);
 // Thin steps on the CUDA cores: A is the operand with 2^lm >= 256 rows, B has 2^ln <= 16 rows,
