@@ -455,6 +455,21 @@ def test_host_entry_points_and_set_data(tn):
     tnet.close()
 
 
+def test_caller_workspace_is_used_and_misalignment_rejected(tn):
+    wl = W.small_workload()
+    net = wl.network
+    tnet = tn.Network.from_workload(net)
+    ws = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    plan = tn.Plan(tnet, wl.path, (), mode="c64", workspace=ws)
+    assert plan.info()["workspace_bytes"] <= ws.numel()
+    check(plan.contract_host(), O.contract_network(net, wl.path), 1e-5)
+    plan.close()
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(tnet, wl.path, (), mode="c64", workspace=ws[8:])  # 8 bytes past 256 alignment
+    assert e.value.status == 1  # TN_ERR_INVALID_ARG
+    tnet.close()
+
+
 # ------------------------------------------------------------------ the full-size circuit
 @pytest.mark.parametrize("mode,form", [("c64", "auto"), ("fp16_scaled", "4m"),
                                        ("fp16_scaled", "3m"), ("split_fp16", "auto"),
