@@ -121,6 +121,41 @@ def test_slices_sum_to_unsliced_and_ranges_split(tn):
     check(one, full, 1e-6)
 
 
+def test_degenerate_networks_and_ragged_batches(tn):
+    rng = np.random.default_rng(77)
+    # a single tensor (no pairwise step): the amplitudes are the tensor in the open order
+    T = crandn(rng, 6)
+    lab = [5, 3, 1, 0, 4, 2]
+    out = [0, 1, 2, 3, 4, 5]
+    got, info, _ = gpu_amps(tn, [T], [lab], out, [])
+    assert info["num_steps"] == 0
+    check(got, np.transpose(T, [lab.index(l) for l in out]).reshape(-1), 1e-6)
+    # no open label: the contraction is a scalar
+    A, B = crandn(rng, 5), crandn(rng, 5)
+    la = [10, 11, 12, 13, 14]
+    lb = [14, 12, 10, 13, 11]
+    got, _, _ = gpu_amps(tn, [A, B], [la, lb], [], [(0, 1)])
+    check(got, O.contract([A, B], [la, lb], [], [(0, 1)]), 1e-5)
+    # an empty slice range adds nothing; 8 slices in batches of 3, 3, 2
+    wl = W.small_workload()
+    net = wl.network
+    sl = W.greedy_slices(net.labels, net.open_labels, wl.path, 3)
+    ref = O.contract_network(net, wl.path)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.Plan(tnet, wl.path, sl, mode="c64", max_slices_in_flight=3, sync_each_call=True)
+    amps = torch.zeros(1 << len(net.open_labels), dtype=torch.complex128, device="cuda")
+    plan.contract(amps, 2, 2)
+    assert torch.count_nonzero(amps).item() == 0
+    assert plan.info()["slices_in_flight"] == 3
+    plan.contract(amps)
+    torch.cuda.synchronize()
+    check(amps.cpu().numpy(), ref, 1e-5)
+    with pytest.raises(tn.TnError):
+        plan.contract(amps, 0, 9)  # past the last slice
+    plan.close()
+    tnet.close()
+
+
 def test_all_open_norm_and_readout(tn):
     circ = W.random_circuit(3, 4, 10, seed=8)
     net = W.build_network(circ, list(range(12)), {})
