@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -642,6 +643,16 @@ __device__ __forceinline__ void named_arrive(int id, int threads) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+// One 32-bit word holding re (low half) and im (high half) as FP16 (dtype 0) or BF16 (1).
+__device__ __forceinline__ uint32_t pack_re_im(float re, float im, int dtype) {
+    if (dtype == 1) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    const __half2 h = __floats2half2_rn(re, im);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 // Barrier over `threads` threads that also ANDs a predicate across them: every participant
 // learns whether all of them had v set (so a group leaves a loop together).
 __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
@@ -659,7 +670,7 @@ __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
     return r != 0;
 }
 
-template <int ESZ, int RB>
+template <int ESZ, int RB, bool PACKED>
 __global__ void __launch_bounds__(PERS_THREADS, 1)
     k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
     using F = PersCfg<ESZ, RB>;
@@ -851,11 +862,14 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
         // scales them and stages the 128 x 32 chunk in staging buffer n & 1 (n counts chunks)
         const int row = warp * 32 + lane;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // a planar two-plane result is staged as one 32-bit word per element (16-bit re | im),
+        // which halves the shared-memory traffic; other results as complex64
+        constexpr bool packed = PACKED;
         int phr = 0;  // column swizzle of this row (see tc_choose_swizzle)
 #pragma unroll
         for (int b = 0; b < 7; ++b)
-            if ((row >> b) & 1) phr ^= d.phi[b];
-        int cur_s = -1;
+            if ((row >> b) & 1) phr ^= packed ? d.phi5[b] : d.phi[b];
+        int cur_s = -1, eo = 0;
         Pow2 pe{1.f, 1.f};
         int n = 0, i = 0;
         bool left = false;
@@ -886,7 +900,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 // numbers (one power-of-two factor here, none in the store warps)
                 cur_s = c.s;
                 const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
-                const int eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
+                eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
                 pe = pow2_of(d.expA[sa] + d.expB[sbi] - eo);
             }
             const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN);
@@ -894,13 +908,26 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             // while the current ones are staged, so most of each TMEM round trip is hidden; a
             // 128 x 32 chunk is two such units
             uint32_t re0[16], im0[16], re1[16], im1[16];
+            float amx = 0.f;  // packed mode: max-abs of the staged (scaled) values
             auto stage_unit = [&](const uint32_t (&re)[16], const uint32_t (&im)[16], int h) {
                 float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
                 if (h == 0 && n >= 2) named_sync(3 + (n & 1), 256);  // buffer freed
+                if constexpr (packed) {
+                    uint32_t *stage32 = reinterpret_cast<uint32_t *>(stage);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    stage[row * PCW + ((16 * h + j) ^ phr)] = make_float2(
-                        scale_pow2(__uint_as_float(re[j]), pe), scale_pow2(__uint_as_float(im[j]), pe));
+                    for (int j = 0; j < 16; ++j) {
+                        const float r = scale_pow2(__uint_as_float(re[j]), pe);
+                        const float m = scale_pow2(__uint_as_float(im[j]), pe);
+                        amx = fmaxf(amx, fmaxf(fabsf(r), fabsf(m)));
+                        stage32[row * PCW + ((16 * h + j) ^ phr)] = pack_re_im(r, m, d.dtype);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        stage[row * PCW + ((16 * h + j) ^ phr)] =
+                            make_float2(scale_pow2(__uint_as_float(re[j]), pe),
+                                        scale_pow2(__uint_as_float(im[j]), pe));
+                }
                 if (h == 1) {
                     named_arrive(1 + (n & 1), 256);  // chunk n is staged
                     ++n;
@@ -929,6 +956,8 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     stage_unit(re1, im1, 1);
                 }
             }
+            // packed mode publishes the tile's max-abs here, at the true scale (2^eo times)
+            if (packed && d.amax_out) amax_publish(d.amax_out + c.s, scale_pow2(amx, pow2_of(eo)));
         }
         // take the store warps' releases of the last two chunks, so every arrival is matched
         if (!left)
@@ -939,11 +968,12 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
         // chunk element is (row r, column c) = the OR of the row / column parts of its sorted bits
         // 0..2 (j), 3..9 (the thread) and 10..11 (the iteration), stored at r * 32 + (c ^ phi(r))
         const int et = threadIdx.x - 128;
+        constexpr bool packed = PACKED;
         auto phi_of = [&](int r) {
             int p = 0;
 #pragma unroll
             for (int b = 0; b < 7; ++b)
-                if ((r >> b) & 1) p ^= d.phi[b];
+                if ((r >> b) & 1) p ^= packed ? d.phi5[b] : d.phi[b];
             return p;
         };
         // element j of an 8-run sits at row part rj, column part cj (disjoint from the other
@@ -1017,26 +1047,45 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
 #pragma unroll
                 for (int k = 0; k < (BM * PCW) / (8 * 128); ++k) {
                     const int rb32 = rbk32[k], xb = xk[k];
-                    float2 v[8];
+                    if constexpr (packed) {
+                        // 8 words (re | im) -> one 16-byte word of 8 16-bit numbers per plane
+                        const uint32_t *stage32 = reinterpret_cast<const uint32_t *>(stage);
+                        uint32_t w[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        v[j] = stage[rb32 + rj32[j] + (xb ^ yj[j])];
-                        amj[j] = fmaxf(amj[j], fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
-                    }
-                    const uint64_t o = olo | hi_off[k];
-                    if (d.planar_out) {
-                        planar_out_store8_prescaled(d.pout, c.s, cbase | o, v);
+                        for (int j = 0; j < 8; ++j) w[j] = stage32[rb32 + rj32[j] + (xb ^ yj[j])];
+                        const uint4 re = make_uint4(
+                            __byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
+                            __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
+                        const uint4 im = make_uint4(
+                            __byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
+                            __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
+                        uint16_t *pb = static_cast<uint16_t *>(d.pout.base) +
+                                       (int64_t)c.s * d.pout.sstride +
+                                       (int64_t)(cbase | olo | hi_off[k]);
+                        *reinterpret_cast<uint4 *>(pb) = re;
+                        *reinterpret_cast<uint4 *>(pb + d.pout.plane_stride) = im;
                     } else {
-                        float4 *c4 = reinterpret_cast<float4 *>(C + o);
+                        float2 v[8];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
-                                                v[2 * j + 1].y);
+                        for (int j = 0; j < 8; ++j) {
+                            v[j] = stage[rb32 + rj32[j] + (xb ^ yj[j])];
+                            amj[j] = fmaxf(amj[j], fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                        }
+                        const uint64_t o = olo | hi_off[k];
+                        if (d.planar_out) {
+                            planar_out_store8_prescaled(d.pout, c.s, cbase | o, v);
+                        } else {
+                            float4 *c4 = reinterpret_cast<float4 *>(C + o);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x,
+                                                    v[2 * j + 1].y);
+                        }
                     }
                 }
                 named_arrive(3 + (n & 1), 256);  // buffer n & 1 is free again
             }
-            if (!stop && d.amax_out) {
+            if (!stop && d.amax_out && !packed) {
                 float amx = amj[0];
 #pragma unroll
                 for (int j = 1; j < 8; ++j) amx = fmaxf(amx, amj[j]);
@@ -1158,9 +1207,14 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 
 template <int ESZ, int RB>
 cudaError_t configure_pers() {
-    return cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                PersCfg<ESZ, RB>::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         PersCfg<ESZ, RB>::SMEM_BYTES);
+    if (e == cudaSuccess && ESZ == 2)
+        e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, ESZ == 2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 PersCfg<ESZ, RB>::SMEM_BYTES);
+    return e;
 }
 
 int sm_count() {
@@ -1186,8 +1240,13 @@ cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (total > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     int64_t grid = sm_count();
     if (grid > total) grid = total;
-    k_gemm_tc_pers<ESZ, RB><<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ, RB>::SMEM_BYTES, st>>>(
-        d, tiles_n, slices);
+    // planar two-plane results (16-bit only) use the packed staging
+    if (ESZ == 2 && d.planar_out && d.pout.planes == 2)
+        k_gemm_tc_pers<ESZ, RB, ESZ == 2>
+            <<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ, RB>::SMEM_BYTES, st>>>(d, tiles_n, slices);
+    else
+        k_gemm_tc_pers<ESZ, RB, false>
+            <<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ, RB>::SMEM_BYTES, st>>>(d, tiles_n, slices);
     return cudaGetLastError();
 }
 
@@ -1275,7 +1334,7 @@ int tc_num_variants() { return 17; }
 namespace {
 int gf2_rank(std::vector<int> v) {
     int r = 0;
-    for (int bit = 3; bit >= 0; --bit) {
+    for (int bit = 4; bit >= 0; --bit) {
         int piv = -1;
         for (size_t i = r; i < v.size(); ++i)
             if ((v[i] >> bit) & 1) {
@@ -1292,39 +1351,36 @@ int gf2_rank(std::vector<int> v) {
 }
 }  // namespace
 
-void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi) {
-    // contribution of a chunk bit to the bank pair (column bits below 4: the bit itself;
-    // column bit 4: none; row bit i: phi[i])
+void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits) {
+    // bank index of a chunk element: its column's low `bits` bits XOR phi(row); a chunk bit
+    // contributes its own bit when it is a column bit below `bits`, phi[i] for row bit i
     auto contrib = [&](int sq, const int *ph) {
-        return (sq & 128) ? ph[sq & 127] : ((sq & 127) < 4 ? 1 << (sq & 127) : 0);
+        return (sq & 128) ? ph[sq & 127] : ((sq & 127) < bits ? 1 << (sq & 127) : 0);
     };
-    int best[7] = {1, 2, 4, 8, 0, 0, 0};
-    int best_score = -1;
-    int ph[7];
-    // phi of row bits 0..4 is a permutation of the four unit masks plus 0 (full rank for the
-    // drain writes); rows 5, 6 take any unit mask or 0
-    const int units[5] = {0, 1, 2, 4, 8};
-    for (int a = 0; a < 5 && best_score < 8; ++a)
-        for (int b = 0; b < 5; ++b)
-            for (int c = 0; c < 5; ++c)
-                for (int d = 0; d < 5; ++d)
-                    for (int e = 0; e < 5; ++e) {
-                        ph[0] = units[a]; ph[1] = units[b]; ph[2] = units[c];
-                        ph[3] = units[d]; ph[4] = units[e];
-                        if (gf2_rank({ph[0], ph[1], ph[2], ph[3], ph[4]}) < 4) continue;
-                        for (int f = 0; f < 5; ++f)
-                            for (int g = 0; g < 5; ++g) {
-                                ph[5] = units[f];
-                                ph[6] = units[g];
-                                std::vector<int> lanes;
-                                for (int q = 3; q < 8; ++q) lanes.push_back(contrib(tb_src[q], ph));
-                                const int score = 2 * gf2_rank(lanes);
-                                if (score > best_score) {
-                                    best_score = score;
-                                    for (int i = 0; i < 7; ++i) best[i] = ph[i];
-                                }
-                            }
-                    }
+    // rows 0..4 (the lanes of a drain write) take a permutation of the unit masks (with 0 when
+    // bits = 4), so a drain write spreads over all banks; rows 5, 6 take any unit mask or 0
+    std::vector<int> units = {0};
+    for (int b = 0; b < bits; ++b) units.push_back(1 << b);
+    std::vector<int> perm = bits == 5 ? std::vector<int>{1, 2, 4, 8, 16}
+                                      : std::vector<int>{0, 1, 2, 4, 8};
+    std::sort(perm.begin(), perm.end());
+    int best[7] = {perm[0], perm[1], perm[2], perm[3], perm[4], 0, 0};
+    int best_rank = -1;
+    do {
+        int ph[7] = {perm[0], perm[1], perm[2], perm[3], perm[4], 0, 0};
+        for (int f : units)
+            for (int g : units) {
+                ph[5] = f;
+                ph[6] = g;
+                std::vector<int> lanes;
+                for (int q = 3; q < 8; ++q) lanes.push_back(contrib(tb_src[q], ph));
+                const int r = gf2_rank(lanes);
+                if (r > best_rank) {
+                    best_rank = r;
+                    for (int i = 0; i < 7; ++i) best[i] = ph[i];
+                }
+            }
+    } while (best_rank < bits && std::next_permutation(perm.begin(), perm.end()));
     for (int i = 0; i < 7; ++i) phi[i] = (int8_t)best[i];
     phi[7] = 0;
 }

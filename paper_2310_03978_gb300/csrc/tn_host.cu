@@ -951,7 +951,10 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     // (the persistent short-K variants stage 32-column chunks: 7 row and 5 column bits)
     const bool pers = variant >= 12 && variant <= 16;
     tn::sort_tile_bits(7, pers ? 5 : 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
-    if (pers) tn::tc_choose_swizzle(d.tb_src, d.phi);
+    if (pers) {
+        tn::tc_choose_swizzle(d.tb_src, d.phi, 4);
+        tn::tc_choose_swizzle(d.tb_src, d.phi5, 5);
+    }
     if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
         return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the epilogue chunk",
                     (int)(&st - &p->steps[0]));

@@ -215,6 +215,7 @@ struct TcGemmDesc {
     int8_t posC_n[TN_MAXR];
     int8_t phi[8];             // persistent short-K epilogue: XOR swizzle of the staging column
                                //   by row bit i (a bit mask below 16; see tc_choose_swizzle)
+    int8_t phi5[8];            //   the same for 4-byte staged elements (masks below 32)
 };
 bool tc_available();
 // Set the kernels' shared-memory limits (once per device, outside any stream capture).
@@ -241,7 +242,8 @@ bool tc_variant_fits(int variant, int lk, int ln);
 // Staging swizzle of the persistent kernel's 128 x 32 chunk: element (row r, column c) sits at
 // r * 32 + (c ^ phi(r)), phi linear in the row bits (phi[i] for row bit i).  Chosen so that the
 // drain warps' writes (lanes = row bits 0..4) and the store warps' reads (lanes = the chunk's
-// sorted bits 3..7) each spread over all 16 eight-byte bank pairs.
-void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi);
+// sorted bits 3..7) each spread over all banks: 16 eight-byte bank pairs (bits = 4, complex64
+// staging) or 32 four-byte banks (bits = 5, packed 16-bit re / im).
+void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits);
 
 }  // namespace tn
