@@ -253,6 +253,71 @@ tn_status tn_readout_noalloc(const void *amps_dev, int64_t num_amps, int32_t n_q
  */
 tn_status tn_selftest_wait_timeout(int32_t limit_ms, void *stream);
 
+/*
+ * Contraction-path optimisation (host only; no device is used).
+ *
+ * Simulated annealing over the contraction tree (Sec. 3.2): the score
+ *     log2(T_cc + alpha * T_mc) + beta * log2(T_sc)
+ * (T_cc: multiply-adds of all pairwise steps, T_mc: elements read and written by them, T_sc: the
+ * largest intermediate, all per slice, plus log2 of the slice count) is lowered by local updates
+ * that exchange the three nearest descendants of a vertex (X = (A, (B, C)) becomes ((A, C), B)
+ * or ((A, B), C)), one per internal vertex in each sweep from the root to the leaves, accepted
+ * by the Metropolis rule; the temperature falls geometrically from t_start to t_end over the
+ * sweeps.  Dynamic slicing (Sec. 3.2): with max_log2_size > 0, while the largest intermediate
+ * exceeds 2^max_log2_size, the bond whose slicing gives the lowest score is sliced and the tree
+ * is re-tuned by sweeps_per_slice further sweeps.  `chains` independent chains (one host thread
+ * each, seeds derived from `seed`) run; the lowest final score wins.  Results are deterministic
+ * for given inputs and options.
+ */
+typedef struct {
+    uint64_t seed;
+    int32_t sweeps;            /* sweeps before slicing (< 0: default 200)                   */
+    int32_t sweeps_per_slice;  /* re-tuning sweeps after each sliced bond (< 0: default 40)  */
+    int32_t sweeps_final;      /* sweeps after slicing (< 0: default 200)                    */
+    int32_t max_log2_size;     /* dynamic slicing target in log2 elements; 0 = no slicing    */
+    int32_t max_sliced;        /* most bonds to slice (<= 0: 64; capped by sliced_capacity)  */
+    int32_t chains;            /* independent chains (<= 0: 1; at most 256)                  */
+    double t_start, t_end;     /* temperatures in score units (<= 0: defaults 1.0 and 0.01)  */
+    double alpha;              /* weight of T_mc (>= 0)                                       */
+    double beta;               /* weight of log2(T_sc) (>= 0)                                 */
+    int32_t reserved[8];
+} tn_path_options;
+
+typedef struct {
+    double log2_tcc;               /* log2 of T_cc per slice (real flops, 8 per multiply-add) */
+    double log2_tcc_total;         /* log2 of T_cc over all slices                            */
+    double log2_tmc;               /* log2 of T_mc per slice (elements)                       */
+    double score;                  /* final score of the returned tree                        */
+    double initial_log2_tcc;       /* the same for the input path, unsliced                   */
+    int32_t initial_max_log2_size;
+    int32_t max_log2_size;         /* largest intermediate per slice, log2 elements           */
+    int32_t num_sliced;            /* bonds written to sliced_out                             */
+    int32_t reserved0;
+    int64_t moves_tried, moves_accepted;
+    int64_t reserved[4];
+} tn_path_info;
+
+/*
+ * Improve a contraction path (and choose sliced bonds).
+ *   num_tensors, ranks, labels, num_open, open_labels   the network's structure, as in
+ *                     tn_network_load (host memory); every dimension is taken as 2
+ *   path_in           the starting path: num_tensors - 1 pairs (a, b), result in a (Sec. 3.1)
+ *   opts              may be NULL (defaults)
+ *   path_out          num_tensors - 1 pairs, the optimised path in the same format (may alias
+ *                     path_in only if the caller no longer needs the input)
+ *   sliced_out        up to sliced_capacity labels: the sliced bonds, in label order
+ *   info              costs before and after (host memory out)
+ * Every label must lie on exactly two tensors, or on one tensor and in open_labels; labels on
+ * three or more tensors (hyperedges) give TN_ERR_UNSUPPORTED.  Open labels are never sliced.
+ * Errors: TN_ERR_INVALID_ARG, TN_ERR_SHAPE (dangling or repeated label), TN_ERR_PATH (invalid
+ * path_in), TN_ERR_UNSUPPORTED.
+ */
+tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
+                           const int32_t *const *labels, int32_t num_open,
+                           const int32_t *open_labels, const int32_t *path_in,
+                           const tn_path_options *opts, int32_t *path_out, int32_t *sliced_out,
+                           int32_t sliced_capacity, tn_path_info *info);
+
 /* Free a network or a plan (NULL is a no-op).  Destroy plans before their network. */
 void tn_destroy(void *handle);
 

@@ -20,6 +20,7 @@
 // k_gemm_tc_pers: the persistent 4M kernel for short contractions (see its comment below).
 // Every mbarrier wait gives up after a device-time limit, records a timeout in a status word and
 // lets the CTA release its TMEM and exit.
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -643,15 +644,45 @@ __device__ __forceinline__ void named_arrive(int id, int threads) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// One 32-bit word holding re (low half) and im (high half) as FP16 (dtype 0) or BF16 (1).
-__device__ __forceinline__ uint32_t pack_re_im(float re, float im, int dtype) {
-    if (dtype == 1) {
+// One 32-bit word holding re (low half) and im (high half) as FP16 (DT 0) or BF16 (DT 1).
+template <int DT>
+__device__ __forceinline__ uint32_t pack_re_im(float re, float im) {
+    if constexpr (DT == 1) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
         return *reinterpret_cast<const uint32_t *>(&h);
+    } else {
+        const __half2 h = __floats2half2_rn(re, im);
+        return *reinterpret_cast<const uint32_t *>(&h);
     }
-    const __half2 h = __floats2half2_rn(re, im);
-    return *reinterpret_cast<const uint32_t *>(&h);
 }
+
+// (a, b) times the power of two p.f1 * p.f2.  ONE (p.f2 == 1, the usual case: the exponents of a
+// step's inputs and output differ by a few dozen) takes one paired FP32 multiply for both; each
+// lane is rounded like a scalar multiply, so the result equals scale_pow2 of each.
+template <bool ONE>
+__device__ __forceinline__ void scale_pair(float a, float b, const Pow2 &p, float &x, float &y) {
+    if constexpr (ONE) {
+        asm("{\n\t.reg .b64 t, u;\n\tmov.b64 t, {%2, %3};\n\tmov.b64 u, {%4, %4};\n\t"
+            "mul.rn.f32x2 t, t, u;\n\tmov.b64 {%0, %1}, t;\n\t}"
+            : "=f"(x), "=f"(y)
+            : "f"(a), "f"(b), "f"(p.f1));
+    } else {
+        x = scale_pow2(a, p);
+        y = scale_pow2(b, p);
+    }
+}
+
+// max(a, b, c) in one instruction (NaN operands are ignored, as by fmaxf)
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+template <bool V>
+using BoolC = std::integral_constant<bool, V>;
+template <int V>
+using IntC = std::integral_constant<int, V>;
 
 // Barrier over `threads` threads that also ANDs a predicate across them: every participant
 // learns whether all of them had v set (so a group leaves a loop together).
@@ -871,6 +902,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             if ((row >> b) & 1) phr ^= packed ? d.phi5[b] : d.phi[b];
         int cur_s = -1, eo = 0;
         Pow2 pe{1.f, 1.f};
+        bool one = true;  // pe.f2 == 1: a single multiply scales a value
         int n = 0, i = 0;
         bool left = false;
         for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
@@ -902,6 +934,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
                 eo = d.planar_out ? planar_out_exponent(d.pout, c.s) : 0;
                 pe = pow2_of(d.expA[sa] + d.expB[sbi] - eo);
+                one = pe.f2 == 1.f;
             }
             const uint32_t acc = tmem + lane_base + (uint32_t)(buf * 2 * BN);
             // the accumulator is read 16 columns (re, im) at a time, the next 16 being loaded
@@ -912,21 +945,41 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             auto stage_unit = [&](const uint32_t (&re)[16], const uint32_t (&im)[16], int h) {
                 float2 *stage = reinterpret_cast<float2 *>(smem + F::RING + (n & 1) * F::STAGE_HALF);
                 if (h == 0 && n >= 2) named_sync(3 + (n & 1), 256);  // buffer freed
+                // column c of this row sits at word row * PCW + (c ^ phr) = rowp ^ c (PCW = 32)
+                const int rowp = row * PCW | phr;
+                // the unrolled loops are specialised on the output type and on whether one
+                // multiply scales a value (both uniform over the tile)
                 if constexpr (packed) {
                     uint32_t *stage32 = reinterpret_cast<uint32_t *>(stage);
+                    auto put = [&](auto dt, auto one_c) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float r = scale_pow2(__uint_as_float(re[j]), pe);
-                        const float m = scale_pow2(__uint_as_float(im[j]), pe);
-                        amx = fmaxf(amx, fmaxf(fabsf(r), fabsf(m)));
-                        stage32[row * PCW + ((16 * h + j) ^ phr)] = pack_re_im(r, m, d.dtype);
+                        for (int j = 0; j < 16; ++j) {
+                            float r, m;
+                            scale_pair<decltype(one_c)::value>(__uint_as_float(re[j]),
+                                                               __uint_as_float(im[j]), pe, r, m);
+                            amx = max3f(amx, fabsf(r), fabsf(m));
+                            stage32[rowp ^ (16 * h + j)] = pack_re_im<decltype(dt)::value>(r, m);
+                        }
+                    };
+                    if (d.dtype == 1) {
+                        if (one) put(IntC<1>{}, BoolC<true>{});
+                        else put(IntC<1>{}, BoolC<false>{});
+                    } else {
+                        if (one) put(IntC<0>{}, BoolC<true>{});
+                        else put(IntC<0>{}, BoolC<false>{});
                     }
                 } else {
+                    auto put = [&](auto one_c) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        stage[row * PCW + ((16 * h + j) ^ phr)] =
-                            make_float2(scale_pow2(__uint_as_float(re[j]), pe),
-                                        scale_pow2(__uint_as_float(im[j]), pe));
+                        for (int j = 0; j < 16; ++j) {
+                            float r, m;
+                            scale_pair<decltype(one_c)::value>(__uint_as_float(re[j]),
+                                                               __uint_as_float(im[j]), pe, r, m);
+                            stage[rowp ^ (16 * h + j)] = make_float2(r, m);
+                        }
+                    };
+                    if (one) put(BoolC<true>{});
+                    else put(BoolC<false>{});
                 }
                 if (h == 1) {
                     named_arrive(1 + (n & 1), 256);  // chunk n is staged

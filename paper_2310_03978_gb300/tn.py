@@ -26,8 +26,8 @@ KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc"}
 # Every symbol declared in include/tn.h.
 EXPORTS = ("tn_network_load", "tn_network_set_data", "tn_plan", "tn_plan_get_info",
            "tn_plan_get_step_info", "tn_contract", "tn_contract_host", "tn_readout",
-           "tn_readout_noalloc", "tn_selftest_wait_timeout", "tn_destroy", "tn_status_string",
-           "tn_last_error_detail")
+           "tn_readout_noalloc", "tn_selftest_wait_timeout", "tn_path_optimize", "tn_destroy",
+           "tn_status_string", "tn_last_error_detail")
 
 
 class PlanOptions(C.Structure):
@@ -59,6 +59,23 @@ class StepInfo(C.Structure):
                 ("store_run_log2", C.c_int32), ("tmc_bytes", C.c_double)]
 
 
+class PathOptions(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("sweeps", C.c_int32), ("sweeps_per_slice", C.c_int32),
+                ("sweeps_final", C.c_int32), ("max_log2_size", C.c_int32),
+                ("max_sliced", C.c_int32), ("chains", C.c_int32), ("t_start", C.c_double),
+                ("t_end", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+                ("reserved", C.c_int32 * 8)]
+
+
+class PathInfo(C.Structure):
+    _fields_ = [("log2_tcc", C.c_double), ("log2_tcc_total", C.c_double),
+                ("log2_tmc", C.c_double), ("score", C.c_double),
+                ("initial_log2_tcc", C.c_double), ("initial_max_log2_size", C.c_int32),
+                ("max_log2_size", C.c_int32), ("num_sliced", C.c_int32),
+                ("reserved0", C.c_int32), ("moves_tried", C.c_int64),
+                ("moves_accepted", C.c_int64), ("reserved", C.c_int64 * 4)]
+
+
 class TnError(RuntimeError):
     def __init__(self, status, detail):
         super().__init__("%s: %s" % (STATUS.get(status, status), detail))
@@ -88,6 +105,8 @@ def lib():
         L.tn_readout.argtypes = [vp, vp, i32, vp, vp]
         L.tn_readout_noalloc.argtypes = [vp, i64, i32, vp, vp]
         L.tn_selftest_wait_timeout.argtypes = [i32, vp]
+        L.tn_path_optimize.argtypes = [i32, vp, vp, i32, vp, vp, C.POINTER(PathOptions), vp, vp,
+                                       i32, C.POINTER(PathInfo)]
         L.tn_destroy.argtypes = [vp]
         L.tn_destroy.restype = None
         L.tn_status_string.argtypes = [C.c_int]
@@ -122,6 +141,37 @@ def readout_noalloc(amps, n_qubits, stream=None):
                                     int(n_qubits), C.c_void_p(out.ctypes.data),
                                     _stream_ptr(stream)))
     return out
+
+
+def path_optimize(labels, open_labels, path, seed=0, sweeps=-1, sweeps_per_slice=-1,
+                  sweeps_final=-1, max_log2_size=0, max_sliced=0, chains=1, t_start=0.0,
+                  t_end=0.0, alpha=0.0, beta=0.0):
+    """Simulated-annealing path optimisation with dynamic slicing (tn_path_optimize, host
+    only).  ``labels`` per tensor, ``open_labels`` the output labels, ``path`` the starting
+    pairs.  Returns (path, sliced_labels, info dict)."""
+    n = len(labels)
+    ranks = np.array([len(l) for l in labels], dtype=np.int32)
+    labs = [np.ascontiguousarray(np.asarray(l, dtype=np.int32)) for l in labels]
+    lab_p = (C.c_void_p * n)(*[l.ctypes.data if len(l) else None for l in labs])
+    op = np.ascontiguousarray(np.asarray(open_labels, dtype=np.int32))
+    pin = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
+    if pin.size != 2 * (n - 1):
+        raise ValueError("path must have num_tensors - 1 pairs")
+    pout = np.zeros(max(1, 2 * (n - 1)), dtype=np.int32)
+    cap = 64
+    sl = np.zeros(cap, dtype=np.int32)
+    o = PathOptions(seed=seed, sweeps=sweeps, sweeps_per_slice=sweeps_per_slice,
+                    sweeps_final=sweeps_final, max_log2_size=max_log2_size,
+                    max_sliced=max_sliced, chains=chains, t_start=t_start, t_end=t_end,
+                    alpha=alpha, beta=beta)
+    info = PathInfo()
+    _check(lib().tn_path_optimize(n, ranks.ctypes.data, lab_p, len(op),
+                                  op.ctypes.data if len(op) else None,
+                                  pin.ctypes.data if pin.size else None, C.byref(o),
+                                  pout.ctypes.data, sl.ctypes.data, cap, C.byref(info)))
+    pairs = [(int(pout[2 * i]), int(pout[2 * i + 1])) for i in range(n - 1)]
+    d = {f: getattr(info, f) for f, _ in PathInfo._fields_ if not f.startswith("reserved")}
+    return pairs, [int(x) for x in sl[:info.num_sliced]], d
 
 
 class Network:

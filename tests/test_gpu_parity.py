@@ -326,6 +326,18 @@ def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
     net.close()
 
 
+def test_persistent_kernel_far_input_scales(tn):
+    # inputs near 2^-70: the exponents of the operand planes sum to far below -126, so the
+    # epilogue scales with two power-of-two factors instead of one (results near 2^-137, FP32
+    # subnormals, still within the tolerance)
+    rng = np.random.default_rng(77)
+    tensors, labels, out = single_step(rng, 12, 9, 5, scale=2.0 ** -70)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)], mode="fp16_scaled")
+    assert kernels == ["gemm_tc"]
+    check(got, ref, TOL["fp16_scaled"])
+
+
 def test_checkpointed_contraction_on_the_gpu(tn, tmp_path):
     # slice chunks through the C ABI, interrupted after the first chunk and resumed
     from paper_2310_03978_gb300 import shard
