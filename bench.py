@@ -39,6 +39,8 @@ FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 
 
+SA_SEED = 7  # annealing seed of the optimised-path measurement
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -64,6 +66,12 @@ def parse_args():
                     help="1: time the headline steps as CUDA-graph replays and measure the "
                          "dominant kernel in a separate profiled pass of the same steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--sa-alpha", type=float, default=1024.0,
+                    help="weight of the memory term T_mc in the annealing score (multiply-adds "
+                         "per element moved)")
+    ap.add_argument("--sa-steps", type=int, default=3,
+                    help="also time the bench circuit along an annealed path with dynamic "
+                         "slicing (same amplitudes, less work); 0 = skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--feed-tc", action="store_true",
@@ -347,6 +355,34 @@ def run_ours(args, rank, world, local_rank):
     c64 = measure("c64", args.c64_steps, 1) if args.c64_steps > 0 else None
     split = measure("split_fp16", args.split_steps, 1) if args.split_steps > 0 else None
 
+    # the same circuit along a path from the annealing optimiser (Sec. 3.2) with dynamic slicing
+    # to the same 2^28 cap: the same amplitudes with a fraction of the work
+    sa = None
+    if world == 1 and args.sa_steps > 0:
+        t0 = time.perf_counter()
+        sa_path, sa_sliced, sa_info = tn.path_optimize(
+            wl.network.labels, wl.network.open_labels, wl.path, seed=SA_SEED, sweeps=300,
+            sweeps_per_slice=40, sweeps_final=200, t_start=0.03, t_end=0.001,
+            max_log2_size=28, chains=8, alpha=args.sa_alpha)
+        sa_opt_s = time.perf_counter() - t0
+        splan = tn.Plan(net, sa_path, sa_sliced, mode=args.mode, use_graph=True,
+                        autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
+        amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
+        splan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        sa_result = amps.cpu().numpy().copy()
+        for _ in range(max(3, args.warmup)):
+            splan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        sms = time_steps(torch, lambda: splan.contract(amps, stream=stream), args.sa_steps,
+                         stream) / args.sa_steps
+        si = splan.info()
+        splan.close()
+        del amps
+        sa = {"ms": sms, "flops": si["tcc_per_slice"] * si["num_slices"] + si["tcc_invariant"],
+              "slices": si["num_slices"], "max_log2": si["max_log2_size"], "opt_s": sa_opt_s,
+              "info": sa_info, "result": sa_result}
+
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
     # contract into a host array (D2H), every step
     plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, mixed_topk=args.mixed_topk)
@@ -371,7 +407,8 @@ def run_ours(args, rank, world, local_rank):
     golden = read_golden() if rank == 0 else None
     acc = {}
     if golden is not None:
-        for name, r in (("head", head), ("c64", c64), ("split_fp16", split)):
+        for name, r in (("head", head), ("c64", c64), ("split_fp16", split),
+                        ("annealed_path", sa)):
             if r is None:
                 continue
             x_ref = O.readout(golden, wl.circuit.n_qubits)[3]
@@ -425,6 +462,15 @@ def run_ours(args, rank, world, local_rank):
         line["split_fp16"] = {"value": batches * split["flops"] / (split["ms"] / 1e3) / 1e12,
                               "unit": "TFLOPS", "ms_per_step": split["ms"],
                               "steps": split["steps"], "roofline": split["roofline"]}
+    if sa is not None:
+        line["annealed_path"] = {
+            "s_per_batch": sa["ms"] / 1e3, "speedup_s_per_batch": head["ms"] / sa["ms"],
+            "effective_tflops": sa["flops"] / (sa["ms"] / 1e3) / 1e12,
+            "flops_per_batch": sa["flops"], "slices": sa["slices"],
+            "max_intermediate_log2": sa["max_log2"], "steps": args.sa_steps,
+            "optimiser_s": sa["opt_s"], "optimiser": "tn_path_optimize seed %d, 8 chains, "
+            "300 + 40 per slice + 200 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
+            % (SA_SEED, args.sa_alpha)}
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {

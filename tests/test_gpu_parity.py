@@ -541,3 +541,39 @@ def test_bench_circuit_full_size(tn, mode, form):
     assert abs(x_got - x_ref) / abs(x_ref) <= (1e-2 if mode == "bf16_scaled" else 1e-3)
     if mode == "fp16_scaled":
         assert "gemm_tc" in kernels
+
+
+# ------------------------------------------------------------------ optimised paths (Sec. 3.2)
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+def test_annealed_path_with_dynamic_slices(tn, mode):
+    # the small circuit along a path and slices from the annealing optimiser
+    wl = W.small_workload()
+    net = wl.network
+    ref = read_golden("sycamore_3x4_c8_open6")
+    path, sliced, info = tn.path_optimize(net.labels, net.open_labels, wl.path, seed=11,
+                                          sweeps=100, sweeps_per_slice=20, sweeps_final=50,
+                                          t_start=0.1, t_end=0.001, max_log2_size=7)
+    assert info["num_sliced"] >= 1
+    got, pinfo, _ = gpu_amps(tn, net.tensors, net.labels, net.open_labels, path, sliced,
+                             mode=mode)
+    assert pinfo["max_log2_size"] <= 7
+    check(got, ref, TOL[mode])
+
+
+def test_bench_circuit_on_an_annealed_path(tn):
+    golden = os.path.join(HERE, "golden", "sycamore_5x6_c14_open10_s4.amps.txt")
+    if not os.path.exists(golden):
+        pytest.skip("golden amplitudes not generated")
+    wl = W.bench_workload()
+    net = wl.network
+    ref = read_golden("sycamore_5x6_c14_open10_s4")
+    path, sliced, info = tn.path_optimize(net.labels, net.open_labels, wl.path, seed=7,
+                                          sweeps=300, sweeps_per_slice=40, sweeps_final=200,
+                                          t_start=0.03, t_end=0.001, max_log2_size=28, chains=8)
+    assert info["max_log2_size"] <= 28
+    got, pinfo, kernels = gpu_amps(tn, net.tensors, net.labels, net.open_labels, path, sliced,
+                                   mode="fp16_scaled")
+    check(got, ref, CIRCUIT_TOL["fp16_scaled"])
+    n = wl.circuit.n_qubits
+    x_ref, x_got = O.readout(ref, n)[3], O.readout(got, n)[3]
+    assert abs(x_got - x_ref) / abs(x_ref) <= 1e-3
