@@ -131,6 +131,8 @@ struct Step {
     int out_meta = -1;           // meta block whose per-slice max-abs this step's epilogue records
     int direct_planar = -1;      // planar copy this step writes directly instead of complex64
     int64_t part_off = -1;       // K_GEMM split-K partials (byte offset in the arena)
+    int chain = -1;              // run of small element-wise steps launched together (k_generic_chain)
+    bool chain_head = false;     // first step of its run: launches the whole run
     // profile mode: recorded (start, stop) event pairs not yet read, and the running totals
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending, pending_prep;
     double time_ms = 0, prep_ms = 0;
@@ -164,6 +166,9 @@ struct tn_plan {
     std::vector<tn::BindItem> bind_inv, bind_sl;
     std::vector<tn::BindTiled> tiled_inv, tiled_sl;  // leaves bound by the tiled permutation
     tn::BindItem *bind_inv_dev = nullptr, *bind_sl_dev = nullptr;
+    std::vector<std::vector<int>> chains;  // step indices of each run of chained steps
+    std::vector<int64_t> chain_first;      // first descriptor of each run in chain_dev
+    tn::GenericDesc *chain_dev = nullptr;
     int max_rank_inv = 0, max_rank_sl = 0;
     unsigned int *meta = nullptr;  // per meta block: amax[sb] then exps[sb]
     int nmeta = 0;
@@ -692,16 +697,46 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
         for (auto &x : p->tensors)
             if (x.meta >= 0 && x.producer >= 0) p->steps[x.producer].out_meta = x.meta;
     }
+    // runs of consecutive small element-wise steps are launched together, one block per slice
+    // (k_generic_chain): runs of the slice-independent prologue and runs of the slice loop,
+    // each in its own execution order; not in profile mode, which times every step on its own
+    if (!p->opts.profile) {
+        std::vector<int> run[2];  // [0] prologue, [1] slice loop
+        auto close_run = [&](std::vector<int> &r) {
+            if (r.size() >= 2) {
+                const int id = (int)p->chains.size();
+                for (int k : r) p->steps[k].chain = id;
+                p->steps[r[0]].chain_head = true;
+                p->chains.push_back(r);
+            }
+            r.clear();
+        };
+        for (int s = 0; s < path_len; ++s) {
+            const Step &st = p->steps[s];
+            const int rc = p->tensors[st.c].rank(), nk = (int)st.K.size();
+            const bool small = st.kernel == K_GENERIC && st.out_meta < 0 &&
+                               rc <= tn::kChainMaxRankC && nk <= tn::kChainMaxNk &&
+                               rc + nk <= tn::kChainMaxWork;
+            std::vector<int> &r = run[st.dep ? 1 : 0];
+            if (small) r.push_back(s);
+            else close_run(r);
+        }
+        close_run(run[0]);
+        close_run(run[1]);
+    }
     // op timeline: invariant leaves, invariant steps, sliced leaves, dependent steps (each
-    // tensor-core step preceded by its conversions), accumulate
+    // tensor-core step preceded by its conversions; a run of chained steps is one op, so every
+    // tensor it touches is live at that op and no two of them share memory), accumulate
     std::vector<Op> ops;
     ops.push_back({0, -1});
     for (int s = 0; s < path_len; ++s)
-        if (!p->steps[s].dep) ops.push_back({1, s});
+        if (!p->steps[s].dep && (p->steps[s].chain < 0 || p->steps[s].chain_head))
+            ops.push_back({1, s});
     ops.push_back({2, -1});
     for (int s = 0; s < path_len; ++s)
         if (p->steps[s].dep) {
             Step &st = p->steps[s];
+            if (st.chain >= 0 && !st.chain_head) continue;  // part of its run's op
             if (st.kernel == K_TC) {
                 ops.push_back({3, st.pa});
                 ops.push_back({3, st.pb});
@@ -716,11 +751,15 @@ extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const in
             for (auto &x : p->tensors)
                 if (x.producer < 0 && x.dep == (op.kind == 2)) x.t0 = x.t1 = t;
         } else if (op.kind == 1) {
-            Step &st = p->steps[op.index];
-            st.t = t;
-            p->tensors[st.c].t0 = p->tensors[st.c].t1 = t;
-            p->tensors[st.a].t1 = t;
-            p->tensors[st.b].t1 = t;
+            const Step &head = p->steps[op.index];
+            const std::vector<int> one{op.index};
+            for (int k : head.chain_head ? p->chains[head.chain] : one) {
+                Step &st = p->steps[k];
+                st.t = t;
+                p->tensors[st.c].t0 = p->tensors[st.c].t1 = t;
+                p->tensors[st.a].t1 = t;
+                p->tensors[st.b].t1 = t;
+            }
         }
     }
     for (auto &st : p->steps) {
@@ -961,6 +1000,37 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     return TN_OK;
 }
 
+tn::GenericDesc make_generic_desc(const tn_plan_t *p, const Step &st, unsigned int *amax_out) {
+    const Tensor &A = p->tensors[st.a], &B = p->tensors[st.b], &C = p->tensors[st.c];
+    float2 *arena = reinterpret_cast<float2 *>(p->arena);
+    tn::GenericDesc d{};
+    d.A = arena + A.off;
+    d.B = arena + B.off;
+    d.C = arena + C.off;
+    d.sA = A.dep ? ((int64_t)1 << A.rank()) : 0;
+    d.sB = B.dep ? ((int64_t)1 << B.rank()) : 0;
+    d.sC = C.dep ? ((int64_t)1 << C.rank()) : 0;
+    d.rank_c = C.rank();
+    d.nk = (int)st.K.size();
+    d.amax_out = amax_out;
+    fill_pos(d.posA_c, TN_MAXR, -1);
+    fill_pos(d.posB_c, TN_MAXR, -1);
+    fill_pos(d.posA_k, TN_MAXR, -1);
+    fill_pos(d.posB_k, TN_MAXR, -1);
+    for (int i = 0; i < C.rank(); ++i) {
+        const int l = C.order[C.rank() - 1 - i];
+        d.posA_c[i] = (int8_t)A.pos(l);
+        d.posB_c[i] = (int8_t)B.pos(l);
+    }
+    const int nk = (int)st.K.size();
+    for (int j = 0; j < nk; ++j) {
+        const int l = st.K[nk - 1 - j];
+        d.posA_k[j] = (int8_t)A.pos(l);
+        d.posB_k[j] = (int8_t)B.pos(l);
+    }
+    return d;
+}
+
 tn_status build_descriptors(tn_plan_t *p) {
     for (auto &t : p->tensors) {
         if (t.leaf < 0) continue;
@@ -998,6 +1068,16 @@ tn_status build_descriptors(tn_plan_t *p) {
     TN_CUDA(cudaMalloc(&p->partial, sizeof(double) * 2 * p->n_partial));
     TN_CUDA(cudaMalloc(&p->amps_tmp, sizeof(double2) << p->net->open.size()));
 
+    if (!p->chains.empty()) {
+        std::vector<tn::GenericDesc> all;
+        for (const auto &run : p->chains) {
+            p->chain_first.push_back((int64_t)all.size());
+            for (int k : run) all.push_back(make_generic_desc(p, p->steps[k], nullptr));
+        }
+        TN_CUDA(cudaMalloc(&p->chain_dev, sizeof(tn::GenericDesc) * all.size()));
+        TN_CUDA(cudaMemcpy(p->chain_dev, all.data(), sizeof(tn::GenericDesc) * all.size(),
+                           cudaMemcpyHostToDevice));
+    }
     p->tc_desc.resize(p->steps.size());
     for (auto &st : p->steps) {
         if (st.kernel != K_TC) continue;
@@ -1134,6 +1214,18 @@ tn_status tune_tc_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stre
 // Launch one step; in profile mode its main kernel (and, for a tensor-core step, its operand
 // conversions) are bracketed by CUDA events on the contraction stream.
 tn_status run_step(tn_plan_t *p, Step &st, int64_t slices, cudaStream_t stream) {
+    if (st.chain >= 0) {
+        // the run's first step launches the whole run; the others are part of that launch
+        if (!st.chain_head) return TN_OK;
+        const cudaError_t e = tn::launch_generic_chain(
+            p->chain_dev + p->chain_first[st.chain], (int32_t)p->chains[st.chain].size(), slices,
+            stream);
+        if (e != cudaSuccess)
+            return fail(TN_ERR_CUDA, "step %d chain launch: %s", (int)(&st - &p->steps[0]),
+                        cudaGetErrorString(e));
+        p->launches += 1;
+        return TN_OK;
+    }
     if (!p->opts.profile) return run_step_inner(p, st, slices, stream, nullptr, nullptr);
     EventPair ev{nullptr, nullptr}, prep{nullptr, nullptr};
     tn_status s = take_events(p, ev);
@@ -1281,31 +1373,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
         p->launches += 1;
     } else {
-        tn::GenericDesc d{};
-        d.A = arena + A.off;
-        d.B = arena + B.off;
-        d.C = arena + C.off;
-        d.sA = sA;
-        d.sB = sB;
-        d.sC = sC;
-        d.rank_c = C.rank();
-        d.nk = (int)st.K.size();
-        d.amax_out = amax_out;
-        fill_pos(d.posA_c, TN_MAXR, -1);
-        fill_pos(d.posB_c, TN_MAXR, -1);
-        fill_pos(d.posA_k, TN_MAXR, -1);
-        fill_pos(d.posB_k, TN_MAXR, -1);
-        for (int i = 0; i < C.rank(); ++i) {
-            const int l = C.order[C.rank() - 1 - i];
-            d.posA_c[i] = (int8_t)A.pos(l);
-            d.posB_c[i] = (int8_t)B.pos(l);
-        }
-        const int nk = (int)st.K.size();
-        for (int j = 0; j < nk; ++j) {
-            const int l = st.K[nk - 1 - j];
-            d.posA_k[j] = (int8_t)A.pos(l);
-            d.posB_k[j] = (int8_t)B.pos(l);
-        }
+        const tn::GenericDesc d = make_generic_desc(p, st, amax_out);
         if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
         e = tn::launch_generic(d, slices, stream);
         if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
@@ -1598,6 +1666,7 @@ void tn_destroy(void *handle) {
         if (p->own_arena && p->arena) cudaFree(p->arena);
         if (p->bind_inv_dev) cudaFree(p->bind_inv_dev);
         if (p->bind_sl_dev) cudaFree(p->bind_sl_dev);
+        if (p->chain_dev) cudaFree(p->chain_dev);
         if (p->meta) cudaFree(p->meta);
         if (p->partial) cudaFree(p->partial);
         if (p->amps_tmp) cudaFree(p->amps_tmp);

@@ -66,6 +66,11 @@ struct GenericDesc {
     int8_t posB_k[TN_MAXR];
 };
 
+// Limits of a step run by k_generic_chain: output bits, contracted bits, and their sum.
+constexpr int kChainMaxRankC = 12;
+constexpr int kChainMaxNk = 10;
+constexpr int kChainMaxWork = 14;
+
 // Complex GEMM C[m, n] = sum_k A[m, k] * B[n, k] with A = [M][K] and B = [N][K] row-major per
 // slice and C written at pdep(m -> posC_m) | pdep(n -> posC_n), i.e. in the consumer's order.
 struct GemmDesc {
@@ -155,6 +160,9 @@ __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {
 
 // Kernel launchers (stream-ordered; return the launch error).
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
+// nsteps descriptors in device memory, one block per slice (see k_generic_chain)
+cudaError_t launch_generic_chain(const GenericDesc *steps_dev, int32_t nsteps, int64_t slices,
+                                 cudaStream_t st);
 // Set the CUDA-core kernels' shared-memory limits (once per device, outside any stream capture).
 cudaError_t simt_prepare();
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st);

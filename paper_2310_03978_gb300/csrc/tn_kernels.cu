@@ -77,6 +77,53 @@ __global__ void __launch_bounds__(256) k_generic(GenericDesc d, int64_t total) {
     }
 }
 
+// A run of consecutive small element-wise steps in one launch: block s executes every step of
+// the run for slice s in order, one thread per output element as in k_generic, with a block
+// barrier between steps (a step's outputs are read by later steps of the same block only).  The
+// plan gives all tensors a run touches pairwise disjoint memory, so blocks never race.
+__global__ void __launch_bounds__(256) k_generic_chain(const GenericDesc *steps, int32_t nsteps) {
+    __shared__ uint64_t koffA[1024], koffB[1024];
+    __shared__ uint64_t loA[1024], loB[1024];
+    const int64_t s = blockIdx.x;
+    for (int i = 0; i < nsteps; ++i) {
+        const GenericDesc &d = steps[i];
+        const int nk = d.nk, rc = d.rank_c;
+        const int lb = rc < 10 ? rc : 10;
+        for (int j = threadIdx.x; j < (1 << lb); j += blockDim.x) {
+            loA[j] = deposit((uint64_t)j, lb, d.posA_c);
+            loB[j] = deposit((uint64_t)j, lb, d.posB_c);
+        }
+        for (int k = threadIdx.x; k < (1 << nk); k += blockDim.x) {
+            koffA[k] = deposit((uint64_t)k, nk, d.posA_k);
+            koffB[k] = deposit((uint64_t)k, nk, d.posB_k);
+        }
+        __syncthreads();
+        const int K = 1 << nk;
+        for (int64_t ch = 0; ch < (1ll << (rc - lb)); ++ch) {
+            const uint64_t c0 = (uint64_t)ch << lb;
+            const uint64_t hA = deposit(c0 >> lb, rc - lb, d.posA_c + lb);
+            const uint64_t hB = deposit(c0 >> lb, rc - lb, d.posB_c + lb);
+            const float2 *Ab = d.A + s * d.sA + hA;
+            const float2 *Bb = d.B + s * d.sB + hB;
+            float2 *Cb = d.C + s * d.sC + (int64_t)c0;
+            for (int j = threadIdx.x; j < (1 << lb); j += blockDim.x) {
+                const float2 *A = Ab + loA[j];
+                const float2 *B = Bb + loB[j];
+                float re = 0.f, im = 0.f;
+                for (int k = 0; k < K; ++k) {
+                    const float2 a = A[koffA[k]], b = B[koffB[k]];
+                    re = fmaf(a.x, b.x, re);
+                    re = fmaf(-a.y, b.y, re);
+                    im = fmaf(a.x, b.y, im);
+                    im = fmaf(a.y, b.x, im);
+                }
+                Cb[j] = make_float2(re, im);
+            }
+        }
+        __syncthreads();  // outputs visible to the next step; tables free
+    }
+}
+
 // Leaf binding: grid (item, slice, chunk); the blocks of one (item, slice) share its elements.
 __global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
                        int64_t slice_begin) {
@@ -333,6 +380,14 @@ cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st
     int64_t blocks = total >> lb;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_generic<<<(unsigned)blocks, 256, 0, st>>>(d, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generic_chain(const GenericDesc *steps_dev, int32_t nsteps, int64_t slices,
+                                 cudaStream_t st) {
+    if (nsteps <= 0 || slices <= 0) return cudaSuccess;
+    if (slices > 0x7fffffff) return cudaErrorInvalidValue;
+    k_generic_chain<<<(unsigned)slices, 256, 0, st>>>(steps_dev, nsteps);
     return cudaGetLastError();
 }
 

@@ -577,3 +577,28 @@ def test_bench_circuit_on_an_annealed_path(tn):
     n = wl.circuit.n_qubits
     x_ref, x_got = O.readout(ref, n)[3], O.readout(got, n)[3]
     assert abs(x_got - x_ref) / abs(x_ref) <= 1e-3
+
+
+# ------------------------------------------------------------------ batched small steps (a10)
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+def test_chained_small_steps_match_single_launches(tn, mode):
+    # runs of small element-wise steps go out as one launch (one block per slice); profile mode
+    # launches every step on its own: both must give the oracle's amplitudes
+    wl = W.small_workload()
+    net = wl.network
+    sl = W.greedy_slices(net.labels, net.open_labels, wl.path, 3)
+    ref = O.contract_network(net, wl.path)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    res, launches = {}, {}
+    for prof in (False, True):
+        plan = tn.Plan(tnet, wl.path, sl, mode=mode, profile=prof, sync_each_call=True)
+        amps = torch.zeros(1 << len(net.open_labels), dtype=torch.complex128, device="cuda")
+        l0 = plan.info()["kernel_launches"]
+        plan.contract(amps)
+        launches[prof] = plan.info()["kernel_launches"] - l0
+        res[prof] = amps.cpu().numpy()
+        plan.close()
+    tnet.close()
+    assert launches[False] < launches[True] // 4
+    check(res[False], ref, TOL[mode])
+    check(res[True], ref, TOL[mode])
