@@ -66,7 +66,7 @@ def parse_args():
                     help="1: time the headline steps as CUDA-graph replays and measure the "
                          "dominant kernel in a separate profiled pass of the same steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--sa-alpha", type=float, default=1024.0,
+    ap.add_argument("--sa-alpha", type=float, default=512.0,
                     help="weight of the memory term T_mc in the annealing score (multiply-adds "
                          "per element moved)")
     ap.add_argument("--sa-steps", type=int, default=3,
@@ -361,9 +361,9 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and args.sa_steps > 0:
         t0 = time.perf_counter()
         sa_path, sa_sliced, sa_info = tn.path_optimize(
-            wl.network.labels, wl.network.open_labels, wl.path, seed=SA_SEED, sweeps=300,
-            sweeps_per_slice=40, sweeps_final=200, t_start=0.03, t_end=0.001,
-            max_log2_size=28, chains=8, alpha=args.sa_alpha)
+            wl.network.labels, wl.network.open_labels, wl.path, seed=SA_SEED, sweeps=1000,
+            sweeps_per_slice=40, sweeps_final=500, t_start=0.03, t_end=0.001,
+            max_log2_size=28, chains=16, alpha=args.sa_alpha)
         sa_opt_s = time.perf_counter() - t0
         splan = tn.Plan(net, sa_path, sa_sliced, mode=args.mode, use_graph=True,
                         autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
@@ -468,8 +468,8 @@ def run_ours(args, rank, world, local_rank):
             "effective_tflops": sa["flops"] / (sa["ms"] / 1e3) / 1e12,
             "flops_per_batch": sa["flops"], "slices": sa["slices"],
             "max_intermediate_log2": sa["max_log2"], "steps": args.sa_steps,
-            "optimiser_s": sa["opt_s"], "optimiser": "tn_path_optimize seed %d, 8 chains, "
-            "300 + 40 per slice + 200 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
+            "optimiser_s": sa["opt_s"], "optimiser": "tn_path_optimize seed %d, 16 chains, "
+            "1000 + 40 per slice + 500 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
             % (SA_SEED, args.sa_alpha)}
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)

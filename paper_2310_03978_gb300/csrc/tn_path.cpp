@@ -230,7 +230,8 @@ struct Chain {
     Tree T;
     Rng rng;
     int64_t tried = 0, accepted = 0;
-    Chain(const Tree &t, uint64_t seed) : T(t), rng(seed) {}
+    std::vector<uint64_t> scratch;  // the candidate label set of a local update
+    Chain(const Tree &t, uint64_t seed) : T(t), rng(seed), scratch(t.W) {}
 
     // one local update at internal vertex x (Metropolis at temperature temp)
     void update(int x, double temp, const Params &p, double &cur) {
@@ -249,13 +250,7 @@ struct Chain {
         uint64_t *lq = t.set(q);
         const uint64_t *la = t.set(a), *lk = t.set(k), *lm = t.set(m);
         const int W = t.W;
-        uint64_t nq[64];
-        std::vector<uint64_t> big;
-        uint64_t *nqp = nq;
-        if (W > 64) {
-            big.resize(W);
-            nqp = big.data();
-        }
+        uint64_t *nqp = scratch.data();
         for (int w = 0; w < W; ++w) nqp[w] = la[w] ^ lk[w];
         const int sz_q_old = t.sz[q], cc_q_old = t.cc[q], cc_x_old = t.cc[x];
         const int sz_q_new = t.pc_masked(nqp);
