@@ -139,6 +139,63 @@ def contract_network(net, path, sliced=(), slice_begin=0, slice_end=None):
                     slice_end)
 
 
+def contract_sparse(tensors, labels, open_labels, path, samples):
+    """Sparse-state contraction (Sec. 3.3): the amplitudes of the sampled bitstrings.
+
+    ``samples`` is an (S, len(open_labels)) array of 0/1; column j is the value of
+    open_labels[j].  Every tensor keeps, for the open labels it carries, only the configurations
+    of those labels that occur among the samples (its merged sparse bond), each with a dense
+    array over its other labels.  A pairwise step (path format of Sec. 3.1) takes the
+    configurations of the union of its operands' open labels that occur among the samples; for
+    each it picks the operand entries with the matching projections and contracts their dense
+    parts with the plain einsum of Eq. chap2_einsum.  The root carries every open label and no
+    dense label; entry i of the result is its value at sample i.  Every dense label must lie on
+    exactly two tensors (no hyperedges)."""
+    samples = np.asarray(samples, dtype=np.int64).reshape(-1, len(open_labels))
+    col = {l: j for j, l in enumerate(open_labels)}
+
+    def configs(open_ls):
+        # distinct projections of the samples onto these open labels, sorted
+        if not open_ls:
+            return [()]
+        cols = [col[l] for l in open_ls]
+        return sorted(set(tuple(int(v) for v in row[cols]) for row in samples))
+
+    items = []
+    for t, ls in zip(tensors, labels):
+        ls = [int(x) for x in ls]
+        t = np.asarray(t, dtype=np.complex128)
+        ol = sorted([l for l in ls if l in col], key=lambda l: col[l])
+        dl = [l for l in ls if l not in col]
+        vals = {}
+        for cfg in configs(ol):
+            at = dict(zip(ol, cfg))
+            idx = tuple(at[l] if l in at else slice(None) for l in ls)
+            vals[cfg] = np.ascontiguousarray(t[idx])  # dense labels in the tensor's order
+        items.append((ol, dl, vals))
+    last = 0
+    for a, b in path:
+        oa, da, va = items[a]
+        ob, db, vb = items[b]
+        oc = sorted(oa + ob, key=lambda l: col[l])
+        shared = set(da) & set(db)
+        dc = [l for l in da if l not in shared] + [l for l in db if l not in shared]
+        vc = {}
+        for cfg in configs(oc):
+            at = dict(zip(oc, cfg))
+            ca = tuple(at[l] for l in oa)
+            cb = tuple(at[l] for l in ob)
+            vc[cfg] = einsum_pair(va[ca], da, vb[cb], db, dc)
+        items[a] = (oc, dc, vc)
+        items[b] = None
+        last = a
+    oc, dc, vc = items[last]
+    if dc or oc != list(open_labels):
+        raise ValueError("the path does not reduce to the open labels")
+    return np.array([complex(vc[tuple(int(v) for v in row)]) for row in samples],
+                    dtype=np.complex128)
+
+
 def statevector(n_qubits, gates):
     """Full 2^n state after ``gates`` (objects with .qubits and .matrix), qubit 0 = MSB."""
     g = len(gates)

@@ -253,3 +253,68 @@ def test_pins_catch_wrong_qubit_order():
     e0[0] = 1
     sv = O.statevector(2, [W.Gate((1,), G)])
     assert np.abs(sv - np.kron(G, np.eye(2)) @ e0).max() > 1e-3
+
+
+# ---------------------------------------------------------------- sparse-state contraction
+def _samples(rng, n_rows, n_bits, dup=True):
+    s = rng.integers(0, 2, size=(n_rows, n_bits))
+    if dup:  # repeated bitstrings must give repeated amplitudes
+        s[1] = s[0]
+        s[-1] = s[2]
+    return s
+
+
+def _sv_index(bits):
+    # qubit 0 = most significant bit of the state-vector index
+    return int("".join(str(int(b)) for b in bits), 2)
+
+
+def test_sparse_state_matches_the_state_vector_at_the_samples():
+    circ = W.random_circuit(3, 4, 8, seed=31)
+    net = _network_all_open(circ)
+    path = W.greedy_path(net.labels, net.open_labels)
+    rng = np.random.default_rng(5)
+    smp = _samples(rng, 48, circ.n_qubits)
+    got = O.contract_sparse(net.tensors, net.labels, net.open_labels, path, smp)
+    sv = O.statevector(circ.n_qubits, circ.gates)
+    np.testing.assert_allclose(got, sv[[_sv_index(r) for r in smp]], rtol=0, atol=1e-13)
+
+
+def test_sparse_state_closed_forms():
+    n = 6
+    net = _network_all_open(W.ghz_circuit(n))
+    path = W.greedy_path(net.labels, net.open_labels)
+    smp = np.array([[0] * n, [1] * n, [1] + [0] * (n - 1), [0, 1] * (n // 2)])
+    got = O.contract_sparse(net.tensors, net.labels, net.open_labels, path, smp)
+    np.testing.assert_allclose(got, [2 ** -0.5, 2 ** -0.5, 0, 0], atol=1e-14)
+    net = _network_all_open(W.hadamard_circuit(n))
+    smp = np.random.default_rng(2).integers(0, 2, size=(10, n))
+    got = O.contract_sparse(net.tensors, net.labels, net.open_labels,
+                            W.greedy_path(net.labels, net.open_labels), smp)
+    np.testing.assert_allclose(got, np.full(10, 2 ** (-n / 2)), atol=1e-14)
+
+
+def test_sparse_state_with_closed_qubits_and_any_path():
+    # a batch of open qubits among closed ones; the dense contraction over all open bitstrings,
+    # read at the samples, and two different paths agree
+    wl = W.small_workload()
+    net = wl.network
+    rng = np.random.default_rng(13)
+    smp = _samples(rng, 20, len(net.open_labels))
+    dense = O.contract_network(net, wl.path)
+    idx = [_sv_index(r) for r in smp]
+    got = O.contract_sparse(net.tensors, net.labels, net.open_labels, wl.path, smp)
+    np.testing.assert_allclose(got, dense[idx], rtol=0, atol=1e-13)
+    other = W.greedy_path(net.labels, net.open_labels, rng=W.Xoshiro256ss(4), temperature=1.0)
+    got2 = O.contract_sparse(net.tensors, net.labels, net.open_labels, other, smp)
+    np.testing.assert_allclose(got2, dense[idx], rtol=0, atol=1e-13)
+
+
+def test_pins_catch_a_swapped_sample_column():
+    circ = W.random_circuit(2, 3, 6, seed=7)
+    net = _network_all_open(circ)
+    path = W.greedy_path(net.labels, net.open_labels)
+    smp = np.random.default_rng(3).integers(0, 2, size=(16, circ.n_qubits))
+    sv = O.statevector(circ.n_qubits, circ.gates)
+    wrong = O.contract_sparse(net.tensors, net.labels, net.open_labels, path, smp[:, ::-1])
+    assert np.abs(wrong - sv[[_sv_index(r) for r in smp]]).max() > 1e-3
