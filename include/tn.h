@@ -318,7 +318,54 @@ tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
                            const tn_path_options *opts, int32_t *path_out, int32_t *sliced_out,
                            int32_t sliced_capacity, tn_path_info *info);
 
-/* Free a network or a plan (NULL is a no-op).  Destroy plans before their network. */
+/*
+ * Sparse-state contraction (Sec. 3.3): the amplitudes of a list of sampled bitstrings.
+ *
+ * Every tensor keeps, for the open labels it carries, only the configurations of those labels
+ * that occur among the samples (its merged sparse bond), each with a complex64 array over its
+ * other labels.  A pairwise step (path format of Sec. 3.1) forms the configurations of the union
+ * of its operands' open labels that occur among the samples, pairs each with its projections
+ * onto the operands (gather tables built at plan time) and contracts the other labels per
+ * configuration on the CUDA cores (FP32 arithmetic); the root holds one value per distinct
+ * sample.  No slicing; every non-open label must lie on exactly two tensors.
+ */
+typedef struct tn_sparse_plan tn_sparse_plan_t;
+
+typedef struct {
+    int64_t num_steps;
+    int64_t num_samples;
+    int64_t distinct_samples;     /* distinct bitstrings among the samples                    */
+    int64_t total_configs;        /* sum over all tensors of their sampled configurations     */
+    int64_t arena_bytes;          /* device storage of all tensors (no reuse)                 */
+    double tcc;                   /* real flops of all steps (8 per complex multiply-add)     */
+    int64_t kernel_launches;      /* kernels launched by this plan so far                     */
+    int32_t max_log2_dense;       /* largest dense part of a tensor, log2 elements            */
+    int32_t reserved0;
+    int64_t reserved[4];
+} tn_sparse_info;
+
+/*
+ * Plan a sparse-state contraction of `net` along `path` (num_tensors - 1 pairs).
+ *   samples           num_samples x num_open bytes, row i = sample i, byte j = value (0 or 1) of
+ *                     the network's open label j (host memory, copied)
+ * Errors: TN_ERR_INVALID_ARG (sizes, a byte other than 0/1), TN_ERR_PATH, TN_ERR_UNSUPPORTED
+ * (more than 64 open labels, a hyperedge, a tensor too large), TN_ERR_OOM, TN_ERR_CUDA.
+ */
+tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
+                         int64_t num_samples, const uint8_t *samples, tn_sparse_plan_t **out);
+
+/*
+ * ADD the amplitudes of the samples into amps_dev (device complex128[num_samples], caller-owned
+ * and caller-zeroed, entry i = sample i, repeated samples get the same value); all work on
+ * `stream`.  Errors: TN_ERR_INVALID_ARG, TN_ERR_CUDA.
+ */
+tn_status tn_sparse_contract(tn_sparse_plan_t *plan, void *amps_dev, void *stream);
+
+/* Statistics of a sparse-state plan (host memory out). */
+tn_status tn_sparse_get_info(const tn_sparse_plan_t *plan, tn_sparse_info *out);
+
+/* Free a network, a plan or a sparse-state plan (NULL is a no-op).  Destroy plans before their
+ * network. */
 void tn_destroy(void *handle);
 
 /* Static description of a status code. */

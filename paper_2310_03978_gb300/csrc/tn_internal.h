@@ -160,6 +160,27 @@ __device__ __forceinline__ void amax_publish(unsigned int *slot, float m) {
 
 // Kernel launchers (stream-ordered; return the launch error).
 cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st);
+// Sparse-state contraction (Sec. 3.3).  A leaf's sparse form: for each sampled configuration c
+// of its open labels, the complex64 array over its other (dense) labels, dst[c * 2^rank_d + j] =
+// src[cfg_off[c] | deposit(j -> pos_d)].
+struct SparseLeafDesc {
+    const double2 *src;        // the leaf's complex128 data (row-major over all its labels)
+    float2 *dst;
+    const int64_t *cfg_off;    // per configuration: the element offset its open-label values select
+    int64_t nconf;
+    int32_t rank_d;            // dense labels
+    int8_t pos_d[TN_MAXR];     // dense bit i (0 = least significant) -> bit of the leaf's index
+};
+// all leaves in one launch (descriptors in device memory)
+cudaError_t launch_sparse_leaves(const SparseLeafDesc *leaves_dev, int32_t n, int32_t max_rank,
+                                 cudaStream_t st);
+// one step: for each configuration c of the result, C[c] = einsum(A[gA[c]], B[gB[c]]) over the
+// dense labels described by d (d.sA, d.sB, d.sC = per-configuration strides)
+cudaError_t launch_sparse_step(const GenericDesc &d, const int32_t *gA, const int32_t *gB,
+                               int64_t nconf, cudaStream_t st);
+// amps[i] += root[idx[i]] for the n samples (complex128 accumulation)
+cudaError_t launch_sparse_amps(const float2 *root, const int32_t *idx, int64_t n, double2 *amps,
+                               cudaStream_t st);
 // nsteps descriptors in device memory, one block per slice (see k_generic_chain)
 cudaError_t launch_generic_chain(const GenericDesc *steps_dev, int32_t nsteps, int64_t slices,
                                  cudaStream_t st);

@@ -124,6 +124,68 @@ __global__ void __launch_bounds__(256) k_generic_chain(const GenericDesc *steps,
     }
 }
 
+// Sparse-state leaves (Sec. 3.3): grid (leaf, chunk); block (leaf, chunk) writes a strided part
+// of that leaf's configurations x dense elements.
+__global__ void k_sparse_leaves(const SparseLeafDesc *leaves) {
+    const SparseLeafDesc &d = leaves[blockIdx.x];
+    const int64_t nd = 1ll << d.rank_d;
+    const int64_t total = d.nconf * nd;
+    for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.y * blockDim.x) {
+        const int64_t c = i >> d.rank_d;
+        const uint64_t j = (uint64_t)(i & (nd - 1));
+        const double2 v = d.src[d.cfg_off[c] | (int64_t)deposit(j, d.rank_d, d.pos_d)];
+        d.dst[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// One sparse-state step: thread per (configuration c, dense output j), summing over the
+// contracted dense bits in increasing order; the operand entries are the configurations gA[c],
+// gB[c] (the projections of c onto each operand's open labels).
+__global__ void __launch_bounds__(256) k_sparse_step(GenericDesc d, const int32_t *gA,
+                                                     const int32_t *gB, int64_t nconf) {
+    __shared__ uint64_t koffA[1024], koffB[1024];
+    const int nk = d.nk;
+    const bool table = nk <= 10;
+    if (table) {
+        for (int k = threadIdx.x; k < (1 << nk); k += blockDim.x) {
+            koffA[k] = deposit((uint64_t)k, nk, d.posA_k);
+            koffB[k] = deposit((uint64_t)k, nk, d.posB_k);
+        }
+    }
+    __syncthreads();
+    const int64_t total = nconf << d.rank_c;
+    const int64_t K = 1ll << nk;
+    const uint64_t jmask = (1ull << d.rank_c) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i >> d.rank_c;
+        const uint64_t j = (uint64_t)i & jmask;
+        const float2 *A = d.A + (int64_t)gA[c] * d.sA + deposit(j, d.rank_c, d.posA_c);
+        const float2 *B = d.B + (int64_t)gB[c] * d.sB + deposit(j, d.rank_c, d.posB_c);
+        float re = 0.f, im = 0.f;
+        for (int64_t k = 0; k < K; ++k) {
+            const uint64_t oa = table ? koffA[k] : deposit((uint64_t)k, nk, d.posA_k);
+            const uint64_t ob = table ? koffB[k] : deposit((uint64_t)k, nk, d.posB_k);
+            const float2 a = A[oa], b = B[ob];
+            re = fmaf(a.x, b.x, re);
+            re = fmaf(-a.y, b.y, re);
+            im = fmaf(a.x, b.y, im);
+            im = fmaf(a.y, b.x, im);
+        }
+        d.C[c * d.sC + (int64_t)j] = make_float2(re, im);
+    }
+}
+
+__global__ void k_sparse_amps(const float2 *root, const int32_t *idx, int64_t n, double2 *amps) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = root[idx[i]];
+        amps[i].x += (double)v.x;
+        amps[i].y += (double)v.y;
+    }
+}
+
 // Leaf binding: grid (item, slice, chunk); the blocks of one (item, slice) share its elements.
 __global__ void k_bind(const BindItem *items, const double2 *src, float2 *arena,
                        int64_t slice_begin) {
@@ -388,6 +450,30 @@ cudaError_t launch_generic_chain(const GenericDesc *steps_dev, int32_t nsteps, i
     if (nsteps <= 0 || slices <= 0) return cudaSuccess;
     if (slices > 0x7fffffff) return cudaErrorInvalidValue;
     k_generic_chain<<<(unsigned)slices, 256, 0, st>>>(steps_dev, nsteps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_leaves(const SparseLeafDesc *leaves_dev, int32_t n, int32_t max_rank,
+                                 cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t chunks = ((1ll << (max_rank < 24 ? max_rank : 24)) + 255) / 256;
+    if (chunks > 1024) chunks = 1024;
+    if (chunks < 1) chunks = 1;
+    k_sparse_leaves<<<dim3((unsigned)n, (unsigned)chunks), 256, 0, st>>>(leaves_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_step(const GenericDesc &d, const int32_t *gA, const int32_t *gB,
+                               int64_t nconf, cudaStream_t st) {
+    if (nconf <= 0) return cudaSuccess;
+    k_sparse_step<<<grid_for(nconf << d.rank_c, 256), 256, 0, st>>>(d, gA, gB, nconf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_amps(const float2 *root, const int32_t *idx, int64_t n, double2 *amps,
+                               cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_sparse_amps<<<grid_for(n, 256), 256, 0, st>>>(root, idx, n, amps);
     return cudaGetLastError();
 }
 

@@ -26,7 +26,8 @@ KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc"}
 # Every symbol declared in include/tn.h.
 EXPORTS = ("tn_network_load", "tn_network_set_data", "tn_plan", "tn_plan_get_info",
            "tn_plan_get_step_info", "tn_contract", "tn_contract_host", "tn_readout",
-           "tn_readout_noalloc", "tn_selftest_wait_timeout", "tn_path_optimize", "tn_destroy",
+           "tn_readout_noalloc", "tn_selftest_wait_timeout", "tn_path_optimize",
+           "tn_sparse_plan", "tn_sparse_contract", "tn_sparse_get_info", "tn_destroy",
            "tn_status_string", "tn_last_error_detail")
 
 
@@ -76,6 +77,14 @@ class PathInfo(C.Structure):
                 ("moves_accepted", C.c_int64), ("reserved", C.c_int64 * 4)]
 
 
+class SparseInfo(C.Structure):
+    _fields_ = [("num_steps", C.c_int64), ("num_samples", C.c_int64),
+                ("distinct_samples", C.c_int64), ("total_configs", C.c_int64),
+                ("arena_bytes", C.c_int64), ("tcc", C.c_double), ("kernel_launches", C.c_int64),
+                ("max_log2_dense", C.c_int32), ("reserved0", C.c_int32),
+                ("reserved", C.c_int64 * 4)]
+
+
 class TnError(RuntimeError):
     def __init__(self, status, detail):
         super().__init__("%s: %s" % (STATUS.get(status, status), detail))
@@ -107,6 +116,9 @@ def lib():
         L.tn_selftest_wait_timeout.argtypes = [i32, vp]
         L.tn_path_optimize.argtypes = [i32, vp, vp, i32, vp, vp, C.POINTER(PathOptions), vp, vp,
                                        i32, C.POINTER(PathInfo)]
+        L.tn_sparse_plan.argtypes = [vp, i32, vp, i64, vp, C.POINTER(vp)]
+        L.tn_sparse_contract.argtypes = [vp, vp, vp]
+        L.tn_sparse_get_info.argtypes = [vp, C.POINTER(SparseInfo)]
         L.tn_destroy.argtypes = [vp]
         L.tn_destroy.restype = None
         L.tn_status_string.argtypes = [C.c_int]
@@ -284,6 +296,45 @@ class Plan:
         _check(lib().tn_readout(self.handle, C.c_void_p(amps.data_ptr()), int(n_qubits),
                                 C.c_void_p(out.ctypes.data), _stream_ptr(stream)))
         return out
+
+    def close(self):
+        if self.handle:
+            lib().tn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SparsePlan:
+    """Sparse-state contraction of a network for a list of sampled bitstrings (tn_sparse_plan;
+    Sec. 3.3).  ``samples``: (S, num_open) array of 0/1, column j = open label j."""
+
+    def __init__(self, network, path, samples):
+        self.network = network
+        smp = np.ascontiguousarray(np.asarray(samples, dtype=np.uint8))
+        if smp.ndim != 2 or smp.shape[1] != network.num_open:
+            raise ValueError("samples must be (S, num_open)")
+        self.num_samples = smp.shape[0]
+        pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
+        h = C.c_void_p()
+        _check(lib().tn_sparse_plan(network.handle, len(pp) // 2,
+                                    pp.ctypes.data if pp.size else None, smp.shape[0],
+                                    smp.ctypes.data, C.byref(h)))
+        self.handle = h
+
+    def contract(self, amps, stream=None):
+        """ADD the samples' amplitudes into a complex128 CUDA tensor of num_samples entries."""
+        _check(lib().tn_sparse_contract(self.handle, C.c_void_p(amps.data_ptr()),
+                                        _stream_ptr(stream)))
+
+    def info(self):
+        i = SparseInfo()
+        _check(lib().tn_sparse_get_info(self.handle, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in SparseInfo._fields_ if not f.startswith("reserved")}
 
     def close(self):
         if self.handle:

@@ -602,3 +602,72 @@ def test_chained_small_steps_match_single_launches(tn, mode):
     assert launches[False] < launches[True] // 4
     check(res[False], ref, TOL[mode])
     check(res[True], ref, TOL[mode])
+
+
+# ------------------------------------------------------------------ sparse-state (Sec. 3.3)
+def sparse_amps(tn, tensors, labels, open_labels, path, samples):
+    net = tn.Network(tensors, labels, open_labels)
+    plan = tn.SparsePlan(net, path, samples)
+    amps = torch.zeros(len(samples), dtype=torch.complex128, device="cuda")
+    plan.contract(amps)
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    net.close()
+    return amps.cpu().numpy(), info
+
+
+def sv_index(bits):
+    return int("".join(str(int(b)) for b in bits), 2)
+
+
+def test_sparse_state_matches_oracle_and_state_vector(tn):
+    circ = W.random_circuit(3, 4, 8, seed=31)
+    net = W.build_network(circ, list(range(12)), {})
+    path = W.greedy_path(net.labels, net.open_labels)
+    rng = np.random.default_rng(5)
+    smp = rng.integers(0, 2, size=(200, 12))
+    smp[1] = smp[0]
+    smp[-1] = smp[7]
+    got, info = sparse_amps(tn, net.tensors, net.labels, net.open_labels, path, smp)
+    ref = O.contract_sparse(net.tensors, net.labels, net.open_labels, path, smp)
+    check(got, ref, TOL["c64"])
+    sv = O.statevector(12, circ.gates)
+    check(got, sv[[sv_index(r) for r in smp]], TOL["c64"])
+    assert got[0] == got[1] and got[7] == got[-1]
+    assert info["distinct_samples"] == len({tuple(r) for r in smp})
+    assert info["num_steps"] == net.num_tensors - 1
+    assert info["kernel_launches"] == info["num_steps"] + 2
+
+
+def test_sparse_state_with_closed_qubits_and_closed_forms(tn):
+    wl = W.small_workload()
+    net = wl.network
+    rng = np.random.default_rng(13)
+    smp = rng.integers(0, 2, size=(40, len(net.open_labels)))
+    got, _ = sparse_amps(tn, net.tensors, net.labels, net.open_labels, wl.path, smp)
+    dense = O.contract_network(net, wl.path)
+    check(got, dense[[sv_index(r) for r in smp]], TOL["c64"])
+    n = 8
+    g = W.build_network(W.ghz_circuit(n), list(range(n)), {})
+    smp = np.array([[0] * n, [1] * n, [1] + [0] * (n - 1), [1] * n])
+    got, info = sparse_amps(tn, g.tensors, g.labels, g.open_labels,
+                            W.greedy_path(g.labels, g.open_labels), smp)
+    np.testing.assert_allclose(got, [2 ** -0.5, 2 ** -0.5, 0, 2 ** -0.5], atol=1e-6)
+    assert info["distinct_samples"] == 3
+
+
+def test_sparse_state_rejects_bad_input(tn):
+    circ = W.random_circuit(2, 2, 4, seed=3)
+    net = W.build_network(circ, list(range(4)), {})
+    path = W.greedy_path(net.labels, net.open_labels)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    with pytest.raises(tn.TnError) as e:
+        tn.SparsePlan(tnet, path, np.array([[0, 1, 2, 0]]))
+    assert e.value.status == 1  # TN_ERR_INVALID_ARG
+    bad = list(path)
+    bad[-1] = (bad[-1][0], bad[0][1])  # a retired id
+    with pytest.raises(tn.TnError) as e:
+        tn.SparsePlan(tnet, bad, np.zeros((3, 4)))
+    assert e.value.status == 3  # TN_ERR_PATH
+    tnet.close()
