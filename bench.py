@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--sa-alpha", type=float, default=512.0,
                     help="weight of the memory term T_mc in the annealing score (multiply-adds "
                          "per element moved)")
+    ap.add_argument("--sparse-steps", type=int, default=3,
+                    help="also time a sparse-state contraction (24-qubit circuit, all qubits "
+                         "open, 4096 sampled bitstrings); 0 = skip")
     ap.add_argument("--sa-steps", type=int, default=3,
                     help="also time the bench circuit along an annealed path with dynamic "
                          "slicing (same amplitudes, less work); 0 = skip")
@@ -383,6 +386,35 @@ def run_ours(args, rank, world, local_rank):
               "slices": si["num_slices"], "max_log2": si["max_log2_size"], "opt_s": sa_opt_s,
               "info": sa_info, "result": sa_result}
 
+    # sparse-state contraction (Sec. 3.3): the amplitudes of 4096 sampled bitstrings of a
+    # 24-qubit circuit with every qubit open, along an annealed path
+    sparse = None
+    if world == 1 and args.sparse_steps > 0:
+        circ_s, net_s, smp = W.sparse_state_workload()
+        g = W.greedy_path(net_s.labels, net_s.open_labels)
+        sp_path, _, _ = tn.path_optimize(net_s.labels, net_s.open_labels, g, seed=SA_SEED,
+                                         sweeps=500, sweeps_final=0, t_start=0.03,
+                                         t_end=0.001, chains=8)
+        tnet_s = tn.Network(net_s.tensors, net_s.labels, net_s.open_labels)
+        splan = tn.SparsePlan(tnet_s, sp_path, smp)
+        amps = torch.zeros(len(smp), dtype=torch.complex128, device=dev)
+        splan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        sp_result = amps.cpu().numpy().copy()
+        for _ in range(2):
+            splan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        sp_ms = time_steps(torch, lambda: splan.contract(amps, stream=stream),
+                           args.sparse_steps, stream) / args.sparse_steps
+        sp_info = splan.info()
+        splan.close()
+        tnet_s.close()
+        del amps
+        sv = O.statevector(circ_s.n_qubits, circ_s.gates)
+        ref = sv[[int("".join(str(int(b)) for b in r), 2) for r in smp]]
+        sparse = {"ms": sp_ms, "info": sp_info, "rel_l2": O.rel_l2(sp_result, ref),
+                  "qubits": circ_s.n_qubits, "samples": len(smp)}
+
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
     # contract into a host array (D2H), every step
     plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, mixed_topk=args.mixed_topk)
@@ -471,6 +503,15 @@ def run_ours(args, rank, world, local_rank):
             "optimiser_s": sa["opt_s"], "optimiser": "tn_path_optimize seed %d, 16 chains, "
             "1000 + 40 per slice + 500 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
             % (SA_SEED, args.sa_alpha)}
+    if sparse is not None:
+        si = sparse["info"]
+        line["sparse_state"] = {
+            "workload": "sycamore_4x6_c12_all_open, %d seeded uniform bitstrings" % sparse["samples"],
+            "ms_per_batch": sparse["ms"], "samples": sparse["samples"],
+            "distinct_samples": si["distinct_samples"], "flops_per_batch": si["tcc"],
+            "effective_tflops": si["tcc"] / (sparse["ms"] / 1e3) / 1e12,
+            "arena_bytes": si["arena_bytes"], "kernel": "CUDA cores, FP32",
+            "amp_rel_l2_vs_statevector": sparse["rel_l2"]}
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {

@@ -538,6 +538,23 @@ def sycamore_workload(name, rows, cols, cycles, k_open, num_sliced, config_id, r
     return Workload(name, circ, net, path, sliced)
 
 
+def sparse_state_workload(rows=4, cols=6, cycles=12, num_samples=4096, config_id=9):
+    """Sparse-state input (Sec. 3.3): a seeded Sycamore-shaped circuit with every qubit open and
+    ``num_samples`` seeded uniform bitstrings standing in for sampled ones (column j = qubit j,
+    the network's open label j).  Returns (circuit, network, samples as an (S, n) uint8 array)."""
+    seed = BASE_SEED + config_id
+    circ = random_circuit(rows, cols, cycles, seed)
+    n = circ.n_qubits
+    net = build_network(circ, list(range(n)), {})
+    rng = Xoshiro256ss(seed ^ 0x5A4D)
+    smp = np.zeros((num_samples, n), dtype=np.uint8)
+    for i in range(num_samples):
+        x = rng.next()
+        for j in range(n):
+            smp[i, j] = (x >> j) & 1
+    return circ, net, smp
+
+
 def small_workload() -> Workload:
     """12-qubit 3x4 grid, 8 cycles, 6 open qubits (64 amplitudes), greedy path, no slicing."""
     return sycamore_workload("sycamore_3x4_c8_open6", 3, 4, 8, 6, 0, 0)
