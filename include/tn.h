@@ -326,8 +326,9 @@ tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
  * other labels.  A pairwise step (path format of Sec. 3.1) forms the configurations of the union
  * of its operands' open labels that occur among the samples, pairs each with its projections
  * onto the operands (gather tables built at plan time) and contracts the other labels per
- * configuration on the CUDA cores (FP32 arithmetic); the root holds one value per distinct
- * sample.  No slicing; every non-open label must lie on exactly two tensors.
+ * configuration on the CUDA cores (FP32 arithmetic: a 64 x 64-tiled GEMM per configuration
+ * when the step has at least 8 rows, columns and contracted elements, else one thread per
+ * output); the root holds one value per distinct sample.  No slicing; every non-open label must lie on exactly two tensors.
  */
 typedef struct tn_sparse_plan tn_sparse_plan_t;
 
@@ -340,7 +341,7 @@ typedef struct {
     double tcc;                   /* real flops of all steps (8 per complex multiply-add)     */
     int64_t kernel_launches;      /* kernels launched by this plan so far                     */
     int32_t max_log2_dense;       /* largest dense part of a tensor, log2 elements            */
-    int32_t reserved0;
+    int32_t gemm_steps;           /* steps run as a tiled GEMM per configuration              */
     int64_t reserved[4];
 } tn_sparse_info;
 

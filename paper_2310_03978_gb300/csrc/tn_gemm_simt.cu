@@ -434,11 +434,121 @@ __global__ void __launch_bounds__(256, 3) k_gemm_thin(GemmDesc d) {
     if (d.amax_out) amax_publish(d.amax_out + s, amx);
 }
 
+
+// Sparse-state step with a dense GEMM inside each configuration (Sec. 3.3): for configuration c
+// of the result, C[c][m][n] = sum_k A[gA[c]][m, k] B[gB[c]][n, k], where the operands' labels sit
+// at arbitrary bit positions (offsets by deposit) and C is row-major over (A-only labels,
+// B-only labels).  Same 64 x 64 tile and double-buffered shared-memory K loop as k_gemm_simt;
+// grid x = tiles x configurations.
+template <int BK>
+__global__ void __launch_bounds__(256) k_sparse_gemm(GenericDesc d, int32_t ln, const int32_t *gA,
+                                                     const int32_t *gB, int64_t tiles_m,
+                                                     int64_t tiles_n) {
+    __shared__ __align__(16) float2 As[2][BK][BM + 1];
+    __shared__ __align__(16) float2 Bs[2][BK][BN + 1];
+    __shared__ uint64_t offm[BM], offn[BN];
+    const int lm = d.rank_c - ln, nk = d.nk;
+    const int64_t tiles = tiles_m * tiles_n;
+    const int64_t c = (int64_t)blockIdx.x / tiles;
+    const int64_t tile = (int64_t)blockIdx.x % tiles;
+    const int64_t m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+    const int64_t M = 1ll << lm, N = 1ll << ln, K = 1ll << nk;
+    const float2 *A = d.A + (int64_t)gA[c] * d.sA;
+    const float2 *B = d.B + (int64_t)gB[c] * d.sB;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (tid < BM) offm[tid] = m0 + tid < M ? deposit((uint64_t)(m0 + tid), lm, d.posA_c + ln) : 0;
+    else if (tid < BM + BN) {
+        const int j = tid - BM;
+        offn[j] = n0 + j < N ? deposit((uint64_t)(n0 + j), ln, d.posB_c) : 0;
+    }
+    __syncthreads();
+    constexpr int KQ = BK / 4;
+    const int lr = tid >> 2, lk = (tid & 3) * KQ;
+    float2 ra[KQ], rb[KQ];
+    auto load = [&](int64_t k0) {
+        const int64_t gm = m0 + lr, gn = n0 + lr;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int64_t gk = k0 + lk + q;
+            const bool kin = gk < K;
+            const uint64_t oka = kin ? deposit((uint64_t)gk, nk, d.posA_k) : 0;
+            const uint64_t okb = kin ? deposit((uint64_t)gk, nk, d.posB_k) : 0;
+            ra[q] = (gm < M && kin) ? A[offm[lr] | oka] : make_float2(0.f, 0.f);
+            rb[q] = (gn < N && kin) ? B[offn[lr] | okb] : make_float2(0.f, 0.f);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            As[buf][lk + q][lr] = ra[q];
+            Bs[buf][lk + q][lr] = rb[q];
+        }
+    };
+    float cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0.f;
+    load(0);
+    store(0);
+    __syncthreads();
+    const int64_t ktiles = (K + BK - 1) / BK;
+    for (int64_t kt = 0; kt < ktiles; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < ktiles) load((kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
+                    cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
+                    ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
+                    ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
+                }
+        }
+        if (kt + 1 < ktiles) store(buf ^ 1);
+        __syncthreads();
+    }
+    float2 *Cc = d.C + c * d.sC;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t gn = n0 + tx + 16 * j;
+            if (gn < N) Cc[gm * N + gn] = make_float2(cr[i][j], ci[i][j]);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t simt_prepare() {
     return cudaFuncSetAttribute(k_gemm_skinny, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSkSmem);
+}
+
+cudaError_t launch_sparse_gemm(const GenericDesc &d, int32_t ln, const int32_t *gA,
+                               const int32_t *gB, int64_t nconf, cudaStream_t st) {
+    if (nconf <= 0) return cudaSuccess;
+    const int lm = d.rank_c - ln;
+    if (lm < 0 || ln < 0 || d.nk < 1) return cudaErrorInvalidValue;
+    const int64_t tiles_m = ((1ll << lm) + BM - 1) / BM, tiles_n = ((1ll << ln) + BN - 1) / BN;
+    const int64_t blocks = tiles_m * tiles_n * nconf;
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (d.nk >= 4)
+        k_sparse_gemm<16><<<(unsigned)blocks, 256, 0, st>>>(d, ln, gA, gB, tiles_m, tiles_n);
+    else
+        k_sparse_gemm<8><<<(unsigned)blocks, 256, 0, st>>>(d, ln, gA, gB, tiles_m, tiles_n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st) {

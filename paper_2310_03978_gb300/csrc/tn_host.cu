@@ -1694,6 +1694,8 @@ struct tn_sparse_plan {
     struct St {
         int a = -1, b = -1, c = -1;
         int64_t ga = 0, gb = 0;      // offsets of the gather tables in `gather`
+        int ln = 0;                  // B-only dense labels (the low bits of C's dense index)
+        bool gemm = false;           // tiled GEMM per configuration (else element-wise)
         tn::GenericDesc d{};
     };
     std::vector<St> steps;
@@ -1895,6 +1897,13 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
             d.posA_k[j] = (int8_t)dense_bit(A.dense, l);
             d.posB_k[j] = (int8_t)dense_bit(B.dense, l);
         }
+        {
+            int nb = 0;
+            for (int l : B.dense)
+                if (std::find(shared.begin(), shared.end(), l) == shared.end()) ++nb;
+            st.ln = nb;
+            st.gemm = d.rank_c - nb >= 3 && nb >= 3 && d.nk >= 3;
+        }
         p->tcc += 8.0 * (double)C.cfg.size() * std::ldexp(1.0, d.rank_c + d.nk);
         p->steps.push_back(st);
         node[a] = c;
@@ -1991,8 +2000,13 @@ tn_status tn_sparse_contract(tn_sparse_plan_t *p, void *amps_dev, void *stream_)
                                      stream));
     p->launches += 1;
     for (const auto &st : p->steps) {
-        TN_CUDA(tn::launch_sparse_step(st.d, p->gather + st.ga, p->gather + st.gb,
-                                       (int64_t)p->ten[st.c].cfg.size(), stream));
+        const int64_t nconf = (int64_t)p->ten[st.c].cfg.size();
+        if (st.gemm)
+            TN_CUDA(tn::launch_sparse_gemm(st.d, st.ln, p->gather + st.ga, p->gather + st.gb,
+                                           nconf, stream));
+        else
+            TN_CUDA(tn::launch_sparse_step(st.d, p->gather + st.ga, p->gather + st.gb, nconf,
+                                           stream));
         p->launches += 1;
     }
     TN_CUDA(tn::launch_sparse_amps(p->arena + p->ten[p->root].off, p->sample_idx,
@@ -2016,6 +2030,7 @@ tn_status tn_sparse_get_info(const tn_sparse_plan_t *p, tn_sparse_info *out) {
     int mx = 0;
     for (const auto &T : p->ten) mx = std::max(mx, (int)T.dense.size());
     out->max_log2_dense = mx;
+    for (const auto &st : p->steps) out->gemm_steps += st.gemm ? 1 : 0;
     return TN_OK;
 }
 

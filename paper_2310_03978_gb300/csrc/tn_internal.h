@@ -178,6 +178,10 @@ cudaError_t launch_sparse_leaves(const SparseLeafDesc *leaves_dev, int32_t n, in
 // dense labels described by d (d.sA, d.sB, d.sC = per-configuration strides)
 cudaError_t launch_sparse_step(const GenericDesc &d, const int32_t *gA, const int32_t *gB,
                                int64_t nconf, cudaStream_t st);
+// the same step as a 64 x 64-tiled GEMM per configuration: C's dense index is (A-only labels,
+// then the ln B-only labels), row-major; for steps with enough m, n and k
+cudaError_t launch_sparse_gemm(const GenericDesc &d, int32_t ln, const int32_t *gA,
+                               const int32_t *gB, int64_t nconf, cudaStream_t st);
 // amps[i] += root[idx[i]] for the n samples (complex128 accumulation)
 cudaError_t launch_sparse_amps(const float2 *root, const int32_t *idx, int64_t n, double2 *amps,
                                cudaStream_t st);

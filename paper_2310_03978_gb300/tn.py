@@ -81,7 +81,7 @@ class SparseInfo(C.Structure):
     _fields_ = [("num_steps", C.c_int64), ("num_samples", C.c_int64),
                 ("distinct_samples", C.c_int64), ("total_configs", C.c_int64),
                 ("arena_bytes", C.c_int64), ("tcc", C.c_double), ("kernel_launches", C.c_int64),
-                ("max_log2_dense", C.c_int32), ("reserved0", C.c_int32),
+                ("max_log2_dense", C.c_int32), ("gemm_steps", C.c_int32),
                 ("reserved", C.c_int64 * 4)]
 
 

@@ -671,3 +671,13 @@ def test_sparse_state_rejects_bad_input(tn):
         tn.SparsePlan(tnet, bad, np.zeros((3, 4)))
     assert e.value.status == 3  # TN_ERR_PATH
     tnet.close()
+
+
+def test_sparse_state_tiled_steps_over_many_configurations(tn):
+    # an 18-qubit all-open circuit: its larger steps run as tiled GEMMs per configuration
+    circ, net, smp = W.sparse_state_workload(3, 6, 10, 512, config_id=11)
+    path = W.greedy_path(net.labels, net.open_labels)
+    got, info = sparse_amps(tn, net.tensors, net.labels, net.open_labels, path, smp)
+    assert info["gemm_steps"] > 0
+    sv = O.statevector(circ.n_qubits, circ.gates)
+    check(got, sv[[sv_index(r) for r in smp]], TOL["c64"])
