@@ -396,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
                                          sweeps=500, sweeps_final=0, t_start=0.03,
                                          t_end=0.001, chains=8)
         tnet_s = tn.Network(net_s.tensors, net_s.labels, net_s.open_labels)
-        splan = tn.SparsePlan(tnet_s, sp_path, smp)
+        splan = tn.SparsePlan(tnet_s, sp_path, smp, mode=args.mode)
         amps = torch.zeros(len(smp), dtype=torch.complex128, device=dev)
         splan.contract(amps, stream=stream)
         torch.cuda.synchronize()
@@ -510,7 +510,8 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_batch": sparse["ms"], "samples": sparse["samples"],
             "distinct_samples": si["distinct_samples"], "flops_per_batch": si["tcc"],
             "effective_tflops": si["tcc"] / (sparse["ms"] / 1e3) / 1e12,
-            "arena_bytes": si["arena_bytes"], "kernel": "CUDA cores, FP32",
+            "arena_bytes": si["arena_bytes"], "dense_subtrees": si["dense_subtrees"],
+            "dense_subtree_steps": si["dense_subtree_steps"], "mode": args.mode,
             "amp_rel_l2_vs_statevector": sparse["rel_l2"]}
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)

@@ -342,18 +342,25 @@ typedef struct {
     int64_t kernel_launches;      /* kernels launched by this plan so far                     */
     int32_t max_log2_dense;       /* largest dense part of a tensor, log2 elements            */
     int32_t gemm_steps;           /* steps run as a tiled GEMM per configuration              */
-    int64_t reserved[4];
+    int64_t dense_subtrees;       /* subtrees without open labels run by ordinary plans       */
+    int64_t dense_subtree_steps;  /* steps inside them                                        */
+    int64_t reserved[2];
 } tn_sparse_info;
 
 /*
  * Plan a sparse-state contraction of `net` along `path` (num_tensors - 1 pairs).
  *   samples           num_samples x num_open bytes, row i = sample i, byte j = value (0 or 1) of
  *                     the network's open label j (host memory, copied)
+ *   mode              precision of the dense subtrees: every maximal subtree of the path with no
+ *                     open label below it (and at least 2^28 flops) is contracted by an ordinary
+ *                     plan in this mode (layout pass, tensor cores in the low-precision modes)
+ *                     and its result joins the sparse steps, which always run in FP32
  * Errors: TN_ERR_INVALID_ARG (sizes, a byte other than 0/1), TN_ERR_PATH, TN_ERR_UNSUPPORTED
  * (more than 64 open labels, a hyperedge, a tensor too large), TN_ERR_OOM, TN_ERR_CUDA.
  */
 tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
-                         int64_t num_samples, const uint8_t *samples, tn_sparse_plan_t **out);
+                         int64_t num_samples, const uint8_t *samples, tn_precision mode,
+                         tn_sparse_plan_t **out);
 
 /*
  * ADD the amplitudes of the samples into amps_dev (device complex128[num_samples], caller-owned

@@ -1665,6 +1665,8 @@ tn_status tn_readout(const tn_plan_t *p, const void *amps_dev, int32_t n_qubits,
 namespace {
 
 constexpr uint32_t kSparseMagic = 0x544e5350u;  // "TNSP"
+// a dense subtree gets an ordinary plan when its steps hold at least this many flops
+constexpr double kSparseDenseMinFlops = 268435456.0;
 
 uint64_t pext64(uint64_t x, uint64_t mask) {  // bits of x at the set bits of mask, packed
     uint64_t r = 0;
@@ -1699,6 +1701,21 @@ struct tn_sparse_plan {
         tn::GenericDesc d{};
     };
     std::vector<St> steps;
+    // maximal subtrees without open labels, contracted by ordinary dense plans (layout pass,
+    // tensor cores in the low-precision modes); their results are converted into the arena
+    struct Sub {
+        tn_network *net = nullptr;
+        tn_plan_t *plan = nullptr;
+        int node = -1;               // the sparse tensor the subtree produces
+        double2 *out = nullptr;      // its complex128 result
+        int64_t n = 0;
+    };
+    std::vector<Sub> subs;
+    std::vector<char> skip;          // per step: computed inside a dense subtree
+    std::vector<tn::SparseLeafDesc> convs;
+    tn::SparseLeafDesc *conv_dev = nullptr;
+    int64_t *zero_off = nullptr;
+    tn_precision mode = TN_PREC_C64;
     std::vector<tn::SparseLeafDesc> leaves;
     int max_leaf_rank = 0;
     int root = -1;
@@ -1714,6 +1731,13 @@ struct tn_sparse_plan {
 namespace {
 
 void sparse_free(tn_sparse_plan_t *p) {
+    for (auto &sb : p->subs) {
+        if (sb.plan) tn_destroy(sb.plan);
+        if (sb.net) tn_destroy(sb.net);
+        if (sb.out) cudaFree(sb.out);
+    }
+    if (p->conv_dev) cudaFree(p->conv_dev);
+    if (p->zero_off) cudaFree(p->zero_off);
     if (p->arena) cudaFree(p->arena);
     if (p->gather) cudaFree(p->gather);
     if (p->cfg_off) cudaFree(p->cfg_off);
@@ -1750,7 +1774,8 @@ int dense_bit(const std::vector<int> &dense, int label) {  // bit position, or -
 extern "C" {
 
 tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
-                         int64_t num_samples, const uint8_t *samples, tn_sparse_plan_t **out) {
+                         int64_t num_samples, const uint8_t *samples, tn_precision mode,
+                         tn_sparse_plan_t **out) {
     tn_status cs = check_net(net);
     if (cs != TN_OK) return cs;
     if (!out || num_samples < 1 || !samples || path_len < 0 || (path_len > 0 && !path))
@@ -1771,7 +1796,10 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
         if (!open_index.count(kv.first) && kv.second != 2)
             return fail(TN_ERR_UNSUPPORTED, "sparse-state: label %d lies on %d tensors",
                         kv.first, kv.second);
+    if ((int)mode < (int)TN_PREC_C64 || (int)mode > (int)TN_PREC_MIXED)
+        return fail(TN_ERR_INVALID_ARG, "tn_sparse_plan: unknown precision mode");
     auto *p = new tn_sparse_plan_t;
+    p->mode = mode;
     p->net = net;
     p->device = net->device;
     p->num_samples = num_samples;
@@ -1920,6 +1948,83 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
         }
         p->distinct = (int64_t)R.cfg.size();
     }
+    // maximal dense subtrees (no open label below them) worth an ordinary plan
+    p->skip.assign(p->steps.size(), 0);
+    std::vector<int> step_of((size_t)(2 * n - 1), -1), parent((size_t)(2 * n - 1), -1);
+    for (size_t k = 0; k < p->steps.size(); ++k) {
+        step_of[(size_t)p->steps[k].c] = (int)k;
+        parent[(size_t)p->steps[k].a] = p->steps[k].c;
+        parent[(size_t)p->steps[k].b] = p->steps[k].c;
+    }
+    std::vector<std::pair<int, std::vector<int>>> dense_roots;  // root node, its steps
+    for (size_t k = 0; k < p->steps.size(); ++k) {
+        const int c = p->steps[k].c;
+        const int par = parent[(size_t)c];
+        if (!p->ten[c].open.empty() || (par >= 0 && p->ten[par].open.empty())) continue;
+        // c is the root of a maximal dense subtree: gather its steps (path order) and work
+        std::vector<int> sub_steps, stack{c};
+        double work = 0;
+        while (!stack.empty()) {
+            const int v = stack.back();
+            stack.pop_back();
+            const int sk = step_of[(size_t)v];
+            if (sk < 0) continue;
+            sub_steps.push_back(sk);
+            work += 8.0 * std::ldexp(1.0, p->steps[sk].d.rank_c + p->steps[sk].d.nk);
+            stack.push_back(p->steps[sk].a);
+            stack.push_back(p->steps[sk].b);
+        }
+        if (work < kSparseDenseMinFlops || p->ten[c].dense.size() > 30) continue;
+        std::sort(sub_steps.begin(), sub_steps.end());
+        dense_roots.emplace_back(c, sub_steps);
+    }
+    for (auto &dr : dense_roots) {
+        const int c = dr.first;
+        const std::vector<int> &sub_steps = dr.second;
+        // local ids of the subtree's leaves (original tensor ids), in increasing order
+        std::vector<int> lv;
+        for (int sk : sub_steps)
+            for (int side = 0; side < 2; ++side) {
+                const int id = path[2 * sk + side];
+                if (std::find(lv.begin(), lv.end(), id) == lv.end()) lv.push_back(id);
+            }
+        std::sort(lv.begin(), lv.end());
+        std::vector<int32_t> lpath;
+        for (int sk : sub_steps)
+            for (int side = 0; side < 2; ++side)
+                lpath.push_back((int32_t)(std::lower_bound(lv.begin(), lv.end(),
+                                                           path[2 * sk + side]) - lv.begin()));
+        tn_sparse_plan_t::Sub sb;
+        sb.node = c;
+        sb.net = new tn_network();
+        sb.net->device = net->device;
+        for (int id : lv) {
+            sb.net->labels.push_back(net->labels[id]);
+            sb.net->offset.push_back(sb.net->total);
+            sb.net->total += (int64_t)1 << net->labels[id].size();
+        }
+        sb.net->open = p->ten[c].dense;
+        cudaError_t e = cudaMalloc(&sb.net->data, sizeof(double2) * (size_t)sb.net->total);
+        for (size_t q = 0; e == cudaSuccess && q < lv.size(); ++q)
+            e = cudaMemcpy(sb.net->data + sb.net->offset[q], net->data + net->offset[lv[q]],
+                           sizeof(double2) * ((size_t)1 << net->labels[lv[q]].size()),
+                           cudaMemcpyDeviceToDevice);
+        sb.n = (int64_t)1 << p->ten[c].dense.size();
+        if (e == cudaSuccess) e = cudaMalloc(&sb.out, sizeof(double2) * (size_t)sb.n);
+        p->subs.push_back(sb);  // owned by the plan from here on
+        if (e != cudaSuccess) {
+            sparse_free(p);
+            return fail(e == cudaErrorMemoryAllocation ? TN_ERR_OOM : TN_ERR_CUDA,
+                        "sparse-state dense subtree: %s", cudaGetErrorString(e));
+        }
+        tn_status ps = tn_plan(sb.net, (int32_t)sub_steps.size(), lpath.data(), 0, nullptr, mode,
+                               nullptr, &p->subs.back().plan);
+        if (ps != TN_OK) {
+            sparse_free(p);
+            return ps;
+        }
+        for (int sk : sub_steps) p->skip[(size_t)sk] = 1;
+    }
     // arena: every tensor its own range (configurations x dense elements)
     int64_t off = 0;
     for (auto &T : p->ten) {
@@ -1961,6 +2066,24 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
     if (e == cudaSuccess)
         e = upload(reinterpret_cast<void **>(&p->sample_idx), idx.data(),
                    idx.size() * sizeof(int32_t));
+    if (e == cudaSuccess && !p->subs.empty()) {
+        const int64_t zero = 0;
+        e = upload(reinterpret_cast<void **>(&p->zero_off), &zero, sizeof(int64_t));
+        for (auto &sb : p->subs) {
+            tn::SparseLeafDesc cd{};
+            cd.src = sb.out;
+            cd.dst = p->arena + p->ten[sb.node].off;
+            cd.cfg_off = p->zero_off;
+            cd.nconf = 1;
+            cd.rank_d = (int)p->ten[sb.node].dense.size();
+            fill_pos(cd.pos_d, TN_MAXR, -1);
+            for (int i = 0; i < cd.rank_d; ++i) cd.pos_d[i] = (int8_t)i;
+            p->convs.push_back(cd);
+        }
+        if (e == cudaSuccess)
+            e = upload(reinterpret_cast<void **>(&p->conv_dev), p->convs.data(),
+                       p->convs.size() * sizeof(tn::SparseLeafDesc));
+    }
     if (e == cudaSuccess) {
         for (int t = 0; t < n; ++t) {
             auto &d = p->leaves[t];
@@ -1996,10 +2119,26 @@ tn_status tn_sparse_contract(tn_sparse_plan_t *p, void *amps_dev, void *stream_)
     int dev = 0;
     TN_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) TN_CUDA(cudaSetDevice(p->device));
+    // dense subtrees first: ordinary plans into their complex128 buffers, then into the arena
+    int max_conv = 0;
+    for (auto &sb : p->subs) {
+        TN_CUDA(cudaMemsetAsync(sb.out, 0, sizeof(double2) * (size_t)sb.n, stream));
+        tn_plan_info pi{};
+        tn_status ps = tn_plan_get_info(sb.plan, &pi);
+        if (ps == TN_OK) ps = tn_contract(sb.plan, 0, pi.num_slices, sb.out, stream);
+        if (ps != TN_OK) return ps;
+        max_conv = std::max(max_conv, (int)(63 - __builtin_clzll((uint64_t)sb.n)));
+    }
+    if (!p->subs.empty()) {
+        TN_CUDA(tn::launch_sparse_leaves(p->conv_dev, (int32_t)p->convs.size(), max_conv, stream));
+        p->launches += 1;
+    }
     TN_CUDA(tn::launch_sparse_leaves(p->leaves_dev, (int32_t)p->leaves.size(), p->max_leaf_rank,
                                      stream));
     p->launches += 1;
-    for (const auto &st : p->steps) {
+    for (size_t k = 0; k < p->steps.size(); ++k) {
+        const auto &st = p->steps[k];
+        if (p->skip[k]) continue;
         const int64_t nconf = (int64_t)p->ten[st.c].cfg.size();
         if (st.gemm)
             TN_CUDA(tn::launch_sparse_gemm(st.d, st.ln, p->gather + st.ga, p->gather + st.gb,
@@ -2030,6 +2169,8 @@ tn_status tn_sparse_get_info(const tn_sparse_plan_t *p, tn_sparse_info *out) {
     int mx = 0;
     for (const auto &T : p->ten) mx = std::max(mx, (int)T.dense.size());
     out->max_log2_dense = mx;
+    out->dense_subtrees = (int64_t)p->subs.size();
+    for (size_t k = 0; k < p->skip.size(); ++k) out->dense_subtree_steps += p->skip[k] ? 1 : 0;
     for (const auto &st : p->steps) out->gemm_steps += st.gemm ? 1 : 0;
     return TN_OK;
 }

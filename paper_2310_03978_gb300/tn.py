@@ -82,7 +82,8 @@ class SparseInfo(C.Structure):
                 ("distinct_samples", C.c_int64), ("total_configs", C.c_int64),
                 ("arena_bytes", C.c_int64), ("tcc", C.c_double), ("kernel_launches", C.c_int64),
                 ("max_log2_dense", C.c_int32), ("gemm_steps", C.c_int32),
-                ("reserved", C.c_int64 * 4)]
+                ("dense_subtrees", C.c_int64), ("dense_subtree_steps", C.c_int64),
+                ("reserved", C.c_int64 * 2)]
 
 
 class TnError(RuntimeError):
@@ -116,7 +117,7 @@ def lib():
         L.tn_selftest_wait_timeout.argtypes = [i32, vp]
         L.tn_path_optimize.argtypes = [i32, vp, vp, i32, vp, vp, C.POINTER(PathOptions), vp, vp,
                                        i32, C.POINTER(PathInfo)]
-        L.tn_sparse_plan.argtypes = [vp, i32, vp, i64, vp, C.POINTER(vp)]
+        L.tn_sparse_plan.argtypes = [vp, i32, vp, i64, vp, C.c_int, C.POINTER(vp)]
         L.tn_sparse_contract.argtypes = [vp, vp, vp]
         L.tn_sparse_get_info.argtypes = [vp, C.POINTER(SparseInfo)]
         L.tn_destroy.argtypes = [vp]
@@ -313,7 +314,7 @@ class SparsePlan:
     """Sparse-state contraction of a network for a list of sampled bitstrings (tn_sparse_plan;
     Sec. 3.3).  ``samples``: (S, num_open) array of 0/1, column j = open label j."""
 
-    def __init__(self, network, path, samples):
+    def __init__(self, network, path, samples, mode="c64"):
         self.network = network
         smp = np.ascontiguousarray(np.asarray(samples, dtype=np.uint8))
         if smp.ndim != 2 or smp.shape[1] != network.num_open:
@@ -323,7 +324,7 @@ class SparsePlan:
         h = C.c_void_p()
         _check(lib().tn_sparse_plan(network.handle, len(pp) // 2,
                                     pp.ctypes.data if pp.size else None, smp.shape[0],
-                                    smp.ctypes.data, C.byref(h)))
+                                    smp.ctypes.data, PRECISION[mode], C.byref(h)))
         self.handle = h
 
     def contract(self, amps, stream=None):

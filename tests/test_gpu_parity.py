@@ -681,3 +681,24 @@ def test_sparse_state_tiled_steps_over_many_configurations(tn):
     assert info["gemm_steps"] > 0
     sv = O.statevector(circ.n_qubits, circ.gates)
     check(got, sv[[sv_index(r) for r in smp]], TOL["c64"])
+
+
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+def test_sparse_state_dense_subtrees_on_ordinary_plans(tn, mode):
+    # the 24-qubit all-open circuit: the subtrees below the open bonds run as ordinary plans
+    # (tensor cores in FP16-scaled mode), the rest as sparse steps
+    circ, net, smp = W.sparse_state_workload(num_samples=512)
+    path, _, _ = tn.path_optimize(net.labels, net.open_labels,
+                                  W.greedy_path(net.labels, net.open_labels), seed=7,
+                                  sweeps=500, sweeps_final=0, t_start=0.03, t_end=0.001, chains=8)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.SparsePlan(tnet, path, smp, mode=mode)
+    amps = torch.zeros(len(smp), dtype=torch.complex128, device="cuda")
+    plan.contract(amps)
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    tnet.close()
+    assert info["dense_subtrees"] > 0 and info["dense_subtree_steps"] > 0
+    sv = O.statevector(circ.n_qubits, circ.gates)
+    check(amps.cpu().numpy(), sv[[sv_index(r) for r in smp]], TOL[mode])
