@@ -327,8 +327,8 @@ tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
  * of its operands' open labels that occur among the samples, pairs each with its projections
  * onto the operands (gather tables built at plan time) and contracts the other labels per
  * configuration on the CUDA cores (FP32 arithmetic: a 64 x 64-tiled GEMM per configuration
- * when the step has at least 8 rows, columns and contracted elements, else one thread per
- * output); the root holds one value per distinct sample.  No slicing; every non-open label must lie on exactly two tensors.
+ * when the step has at least 8 rows, columns and contracted elements, a thread per row for at
+ * most 16 columns, else one thread per output); the root holds one value per distinct sample.  No slicing; every non-open label must lie on exactly two tensors.
  */
 typedef struct tn_sparse_plan tn_sparse_plan_t;
 
@@ -344,7 +344,8 @@ typedef struct {
     int32_t gemm_steps;           /* steps run as a tiled GEMM per configuration              */
     int64_t dense_subtrees;       /* subtrees without open labels run by ordinary plans       */
     int64_t dense_subtree_steps;  /* steps inside them                                        */
-    int64_t reserved[2];
+    int64_t thin_steps;           /* steps run as thread-per-row thin kernels (<= 16 columns) */
+    int64_t reserved[1];
 } tn_sparse_info;
 
 /*

@@ -435,6 +435,60 @@ __global__ void __launch_bounds__(256, 3) k_gemm_thin(GemmDesc d) {
 }
 
 
+// Thin sparse-state step (at most 16 columns): thread per (configuration c, row m) holding all
+// NN outputs of its row; B[gB[c]] is staged in shared memory 64 values of k at a time, so each
+// element of A is read once.  Block = 256 rows of one configuration.
+template <int NN>
+__global__ void __launch_bounds__(256) k_sparse_thin(GenericDesc d, const int32_t *gA,
+                                                     const int32_t *gB, int64_t mblocks) {
+    constexpr int KC = 64;
+    __shared__ float2 Bs[KC][NN];
+    __shared__ uint64_t offak[KC], offbk[KC];
+    constexpr int ln = NN == 1 ? 0 : NN == 2 ? 1 : NN == 4 ? 2 : NN == 8 ? 3 : 4;  // NN = 2^ln
+    const int lm = d.rank_c - ln, nk = d.nk;
+    const int64_t c = (int64_t)blockIdx.x / mblocks;
+    const int64_t m = ((int64_t)blockIdx.x % mblocks) * 256 + threadIdx.x;
+    const int64_t M = 1ll << lm, K = 1ll << nk;
+    const float2 *A = d.A + (int64_t)gA[c] * d.sA;
+    const float2 *B = d.B + (int64_t)gB[c] * d.sB;
+    const bool row_ok = m < M;
+    const uint64_t offm = row_ok ? deposit((uint64_t)m, lm, d.posA_c + ln) : 0;
+    float cr[NN], ci[NN];
+#pragma unroll
+    for (int n = 0; n < NN; ++n) cr[n] = ci[n] = 0.f;
+    for (int64_t k0 = 0; k0 < K; k0 += KC) {
+        const int kc = (int)(K - k0 < KC ? K - k0 : KC);
+        __syncthreads();  // the previous chunk is consumed
+        if (threadIdx.x < kc) {
+            offak[threadIdx.x] = deposit((uint64_t)(k0 + threadIdx.x), nk, d.posA_k);
+            offbk[threadIdx.x] = deposit((uint64_t)(k0 + threadIdx.x), nk, d.posB_k);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kc * NN; e += blockDim.x) {
+            const int kk = e / NN, n = e % NN;
+            Bs[kk][n] = B[deposit((uint64_t)n, ln, d.posB_c) | offbk[kk]];
+        }
+        __syncthreads();
+        if (row_ok)
+            for (int kk = 0; kk < kc; ++kk) {
+                const float2 a = A[offm | offak[kk]];
+#pragma unroll
+                for (int n = 0; n < NN; ++n) {
+                    const float2 b = Bs[kk][n];
+                    cr[n] = fmaf(a.x, b.x, cr[n]);
+                    cr[n] = fmaf(-a.y, b.y, cr[n]);
+                    ci[n] = fmaf(a.x, b.y, ci[n]);
+                    ci[n] = fmaf(a.y, b.x, ci[n]);
+                }
+            }
+    }
+    if (row_ok) {
+        float2 *Cc = d.C + c * d.sC + m * NN;
+#pragma unroll
+        for (int n = 0; n < NN; ++n) Cc[n] = make_float2(cr[n], ci[n]);
+    }
+}
+
 // Sparse-state step with a dense GEMM inside each configuration (Sec. 3.3): for configuration c
 // of the result, C[c][m][n] = sum_k A[gA[c]][m, k] B[gB[c]][n, k], where the operands' labels sit
 // at arbitrary bit positions (offsets by deposit) and C is row-major over (A-only labels,
@@ -534,6 +588,24 @@ __global__ void __launch_bounds__(256) k_sparse_gemm(GenericDesc d, int32_t ln, 
 cudaError_t simt_prepare() {
     return cudaFuncSetAttribute(k_gemm_skinny, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSkSmem);
+}
+
+cudaError_t launch_sparse_thin(const GenericDesc &d, int32_t ln, const int32_t *gA,
+                               const int32_t *gB, int64_t nconf, cudaStream_t st) {
+    if (nconf <= 0) return cudaSuccess;
+    const int lm = d.rank_c - ln;
+    if (lm < 0 || ln < 0 || ln > 4) return cudaErrorInvalidValue;
+    const int64_t mblocks = ((1ll << lm) + 255) / 256;
+    const int64_t blocks = mblocks * nconf;
+    if (blocks > 0x7fffffffll) return cudaErrorInvalidValue;
+    switch (ln) {
+    case 0: k_sparse_thin<1><<<(unsigned)blocks, 256, 0, st>>>(d, gA, gB, mblocks); break;
+    case 1: k_sparse_thin<2><<<(unsigned)blocks, 256, 0, st>>>(d, gA, gB, mblocks); break;
+    case 2: k_sparse_thin<4><<<(unsigned)blocks, 256, 0, st>>>(d, gA, gB, mblocks); break;
+    case 3: k_sparse_thin<8><<<(unsigned)blocks, 256, 0, st>>>(d, gA, gB, mblocks); break;
+    default: k_sparse_thin<16><<<(unsigned)blocks, 256, 0, st>>>(d, gA, gB, mblocks); break;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_gemm(const GenericDesc &d, int32_t ln, const int32_t *gA,

@@ -1697,7 +1697,8 @@ struct tn_sparse_plan {
         int a = -1, b = -1, c = -1;
         int64_t ga = 0, gb = 0;      // offsets of the gather tables in `gather`
         int ln = 0;                  // B-only dense labels (the low bits of C's dense index)
-        bool gemm = false;           // tiled GEMM per configuration (else element-wise)
+        bool gemm = false;           // tiled GEMM per configuration
+        bool thin = false;           // at most 16 columns: thread per row (else element-wise)
         tn::GenericDesc d{};
     };
     std::vector<St> steps;
@@ -1931,6 +1932,7 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
                 if (std::find(shared.begin(), shared.end(), l) == shared.end()) ++nb;
             st.ln = nb;
             st.gemm = d.rank_c - nb >= 3 && nb >= 3 && d.nk >= 3;
+            st.thin = !st.gemm && nb <= 4 && d.rank_c - nb >= 5 && d.nk >= 2;
         }
         p->tcc += 8.0 * (double)C.cfg.size() * std::ldexp(1.0, d.rank_c + d.nk);
         p->steps.push_back(st);
@@ -2143,6 +2145,9 @@ tn_status tn_sparse_contract(tn_sparse_plan_t *p, void *amps_dev, void *stream_)
         if (st.gemm)
             TN_CUDA(tn::launch_sparse_gemm(st.d, st.ln, p->gather + st.ga, p->gather + st.gb,
                                            nconf, stream));
+        else if (st.thin)
+            TN_CUDA(tn::launch_sparse_thin(st.d, st.ln, p->gather + st.ga, p->gather + st.gb,
+                                           nconf, stream));
         else
             TN_CUDA(tn::launch_sparse_step(st.d, p->gather + st.ga, p->gather + st.gb, nconf,
                                            stream));
@@ -2171,7 +2176,10 @@ tn_status tn_sparse_get_info(const tn_sparse_plan_t *p, tn_sparse_info *out) {
     out->max_log2_dense = mx;
     out->dense_subtrees = (int64_t)p->subs.size();
     for (size_t k = 0; k < p->skip.size(); ++k) out->dense_subtree_steps += p->skip[k] ? 1 : 0;
-    for (const auto &st : p->steps) out->gemm_steps += st.gemm ? 1 : 0;
+    for (const auto &st : p->steps) {
+        out->gemm_steps += st.gemm ? 1 : 0;
+        out->thin_steps += st.thin ? 1 : 0;
+    }
     return TN_OK;
 }
 

@@ -182,6 +182,9 @@ cudaError_t launch_sparse_step(const GenericDesc &d, const int32_t *gA, const in
 // then the ln B-only labels), row-major; for steps with enough m, n and k
 cudaError_t launch_sparse_gemm(const GenericDesc &d, int32_t ln, const int32_t *gA,
                                const int32_t *gB, int64_t nconf, cudaStream_t st);
+// the same step for at most 16 columns (ln <= 4): thread per (configuration, row)
+cudaError_t launch_sparse_thin(const GenericDesc &d, int32_t ln, const int32_t *gA,
+                               const int32_t *gB, int64_t nconf, cudaStream_t st);
 // amps[i] += root[idx[i]] for the n samples (complex128 accumulation)
 cudaError_t launch_sparse_amps(const float2 *root, const int32_t *idx, int64_t n, double2 *amps,
                                cudaStream_t st);

@@ -700,5 +700,6 @@ def test_sparse_state_dense_subtrees_on_ordinary_plans(tn, mode):
     plan.close()
     tnet.close()
     assert info["dense_subtrees"] > 0 and info["dense_subtree_steps"] > 0
+    assert info["thin_steps"] > 0 and info["gemm_steps"] > 0
     sv = O.statevector(circ.n_qubits, circ.gates)
     check(amps.cpu().numpy(), sv[[sv_index(r) for r in smp]], TOL[mode])
