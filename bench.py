@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--sa-alpha", type=float, default=512.0,
                     help="weight of the memory term T_mc in the annealing score (multiply-adds "
                          "per element moved)")
+    ap.add_argument("--sparse-only", action="store_true",
+                    help="run only the sparse-state measurement and print its JSON line")
     ap.add_argument("--sparse-steps", type=int, default=3,
                     help="also time a sparse-state contraction (24-qubit circuit, all qubits "
                          "open, 4096 sampled bitstrings); 0 = skip")
@@ -396,32 +398,7 @@ def run_ours(args, rank, world, local_rank):
 
     # sparse-state contraction (Sec. 3.3): the amplitudes of 4096 sampled bitstrings of a
     # 24-qubit circuit with every qubit open, along an annealed path
-    sparse = None
-    if world == 1 and args.sparse_steps > 0:
-        circ_s, net_s, smp = W.sparse_state_workload()
-        g = W.greedy_path(net_s.labels, net_s.open_labels)
-        sp_path, _, _ = tn.path_optimize(net_s.labels, net_s.open_labels, g, seed=SA_SEED,
-                                         sweeps=500, sweeps_final=0, t_start=0.03,
-                                         t_end=0.001, chains=8)
-        tnet_s = tn.Network(net_s.tensors, net_s.labels, net_s.open_labels)
-        splan = tn.SparsePlan(tnet_s, sp_path, smp, mode=args.mode)
-        amps = torch.zeros(len(smp), dtype=torch.complex128, device=dev)
-        splan.contract(amps, stream=stream)
-        torch.cuda.synchronize()
-        sp_result = amps.cpu().numpy().copy()
-        for _ in range(2):
-            splan.contract(amps, stream=stream)
-        torch.cuda.synchronize()
-        sp_ms = time_steps(torch, lambda: splan.contract(amps, stream=stream),
-                           args.sparse_steps, stream) / args.sparse_steps
-        sp_info = splan.info()
-        splan.close()
-        tnet_s.close()
-        del amps
-        sv = O.statevector(circ_s.n_qubits, circ_s.gates)
-        ref = sv[[int("".join(str(int(b)) for b in r), 2) for r in smp]]
-        sparse = {"ms": sp_ms, "info": sp_info, "rel_l2": O.rel_l2(sp_result, ref),
-                  "qubits": circ_s.n_qubits, "samples": len(smp)}
+    sparse = measure_sparse(args, dev, stream) if world == 1 and args.sparse_steps > 0 else None
 
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
     # contract into a host array (D2H), every step
@@ -513,15 +490,7 @@ def run_ours(args, rank, world, local_rank):
             "1000 + 40 per slice + 500 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
             % (SA_SEED, args.sa_alpha)}
     if sparse is not None:
-        si = sparse["info"]
-        line["sparse_state"] = {
-            "workload": "sycamore_4x6_c12_all_open, %d seeded uniform bitstrings" % sparse["samples"],
-            "ms_per_batch": sparse["ms"], "samples": sparse["samples"],
-            "distinct_samples": si["distinct_samples"], "flops_per_batch": si["tcc"],
-            "effective_tflops": si["tcc"] / (sparse["ms"] / 1e3) / 1e12,
-            "arena_bytes": si["arena_bytes"], "dense_subtrees": si["dense_subtrees"],
-            "dense_subtree_steps": si["dense_subtree_steps"], "mode": args.mode,
-            "amp_rel_l2_vs_statevector": sparse["rel_l2"]}
+        line["sparse_state"] = sparse_line(args, sparse)
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)
         line["cpu_baseline"] = {
@@ -532,6 +501,51 @@ def run_ours(args, rank, world, local_rank):
                       % (smp["shape"], smp["outputs"], smp["fixed_labels"], smp["seconds"],
                          head["flops"] / smp["rate"])}
     print(json.dumps(line))
+
+
+def measure_sparse(args, dev, stream):
+    """Sparse-state contraction of 4096 seeded bitstrings of the 24-qubit all-open circuit along
+    an annealed path; time per batch and the error against the host state vector."""
+    import torch
+    from oracle import oracle as O
+    from paper_2310_03978_gb300 import tn, workload as W
+    circ_s, net_s, smp = W.sparse_state_workload()
+    g = W.greedy_path(net_s.labels, net_s.open_labels)
+    sp_path, _, _ = tn.path_optimize(net_s.labels, net_s.open_labels, g, seed=SA_SEED,
+                                     sweeps=500, sweeps_final=0, t_start=0.03, t_end=0.001,
+                                     chains=8)
+    tnet_s = tn.Network(net_s.tensors, net_s.labels, net_s.open_labels)
+    splan = tn.SparsePlan(tnet_s, sp_path, smp, mode=args.mode)
+    amps = torch.zeros(len(smp), dtype=torch.complex128, device=dev)
+    splan.contract(amps, stream=stream)
+    torch.cuda.synchronize()
+    sp_result = amps.cpu().numpy().copy()
+    for _ in range(2):
+        splan.contract(amps, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(1, args.sparse_steps)
+    sp_ms = time_steps(torch, lambda: splan.contract(amps, stream=stream), steps, stream) / steps
+    sp_info = splan.info()
+    splan.close()
+    tnet_s.close()
+    del amps
+    sv = O.statevector(circ_s.n_qubits, circ_s.gates)
+    ref = sv[[int("".join(str(int(b)) for b in r), 2) for r in smp]]
+    return {"ms": sp_ms, "info": sp_info, "rel_l2": O.rel_l2(sp_result, ref),
+            "qubits": circ_s.n_qubits, "samples": len(smp)}
+
+
+def sparse_line(args, sparse):
+    si = sparse["info"]
+    return {"workload": "sycamore_4x6_c12_all_open, %d seeded uniform bitstrings"
+                        % sparse["samples"],
+            "ms_per_batch": sparse["ms"], "samples": sparse["samples"],
+            "distinct_samples": si["distinct_samples"], "flops_per_batch": si["tcc"],
+            "effective_tflops": si["tcc"] / (sparse["ms"] / 1e3) / 1e12,
+            "arena_bytes": si["arena_bytes"], "dense_subtrees": si["dense_subtrees"],
+            "dense_subtree_steps": si["dense_subtree_steps"], "gemm_steps": si["gemm_steps"],
+            "thin_steps": si["thin_steps"], "mode": args.mode,
+            "amp_rel_l2_vs_statevector": sparse["rel_l2"]}
 
 
 def run_step_bench(args):
@@ -735,6 +749,13 @@ def main():
         return
     if args.step_profile:
         run_step_profile(args)
+        return
+    if args.sparse_only:
+        import torch
+        torch.cuda.set_device(local_rank)
+        r = measure_sparse(args, torch.device("cuda", local_rank), torch.cuda.current_stream())
+        print(json.dumps({"metric": "sparse-state ms per batch", "value": r["ms"], "unit": "ms",
+                          "higher_is_better": False, **sparse_line(args, r)}))
         return
     if world > 1:
         import torch
