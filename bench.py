@@ -544,7 +544,8 @@ def sparse_line(args, sparse):
             "effective_tflops": si["tcc"] / (sparse["ms"] / 1e3) / 1e12,
             "arena_bytes": si["arena_bytes"], "dense_subtrees": si["dense_subtrees"],
             "dense_subtree_steps": si["dense_subtree_steps"], "gemm_steps": si["gemm_steps"],
-            "thin_steps": si["thin_steps"], "mode": args.mode,
+            "thin_steps": si["thin_steps"], "grouped_steps": si["grouped_steps"],
+            "mode": args.mode,
             "amp_rel_l2_vs_statevector": sparse["rel_l2"]}
 
 

@@ -326,9 +326,11 @@ tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
  * other labels.  A pairwise step (path format of Sec. 3.1) forms the configurations of the union
  * of its operands' open labels that occur among the samples, pairs each with its projections
  * onto the operands (gather tables built at plan time) and contracts the other labels per
- * configuration on the CUDA cores (FP32 arithmetic: a 64 x 64-tiled GEMM per configuration
- * when the step has at least 8 rows, columns and contracted elements, a thread per row for at
- * most 16 columns, else one thread per output); the root holds one value per distinct sample.  No slicing; every non-open label must lie on exactly two tensors.
+ * configuration on the CUDA cores (FP32 arithmetic: result configurations that share an entry of
+ * one operand form one 64 x 64-tiled GEMM over the stacked entries of the other (grouped GEMM)
+ * when at least 8 elements are contracted and the tiles are at least a quarter full; else a
+ * tiled GEMM per configuration, a thread per row for at most 16 columns, or one thread per
+ * output); the root holds one value per distinct sample.  No slicing; every non-open label must lie on exactly two tensors.
  */
 typedef struct tn_sparse_plan tn_sparse_plan_t;
 
@@ -345,7 +347,7 @@ typedef struct {
     int64_t dense_subtrees;       /* subtrees without open labels run by ordinary plans       */
     int64_t dense_subtree_steps;  /* steps inside them                                        */
     int64_t thin_steps;           /* steps run as thread-per-row thin kernels (<= 16 columns) */
-    int64_t reserved[1];
+    int64_t grouped_steps;        /* steps run as grouped GEMMs over shared operand entries   */
 } tn_sparse_info;
 
 /*

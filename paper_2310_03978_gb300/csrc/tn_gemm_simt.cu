@@ -489,6 +489,114 @@ __global__ void __launch_bounds__(256) k_sparse_thin(GenericDesc d, const int32_
     }
 }
 
+// Grouped sparse-state step (see SparseGroupDesc): one 64 x 64 tile of one group's GEMM per CTA.
+// Row r / column q of the tile resolve to an operand element offset (without k) and a part of
+// the result offset, so C[(row part) + (column part)] = sum_k A[rowA + offA(k)] B[colB + offB(k)].
+template <int BK>
+__global__ void __launch_bounds__(256) k_sparse_group(GenericDesc d, int32_t ln,
+                                                      SparseGroupDesc g) {
+    __shared__ __align__(16) float2 As[2][BK][BM + 1];
+    __shared__ __align__(16) float2 Bs[2][BK][BN + 1];
+    __shared__ int64_t rowA[BM], colB[BN], outR[BM], outC[BN];
+    const int lm = d.rank_c - ln, nk = d.nk;
+    const int64_t M = 1ll << lm, N = 1ll << ln, K = 1ll << nk;
+    const int32_t *t = g.tiles + 3 * (int64_t)blockIdx.x;
+    const int grp = t[0];
+    const int64_t r0 = (int64_t)t[1] * BM, q0 = (int64_t)t[2] * BN;
+    const int64_t off = g.grp_off[grp], len = g.grp_len[grp];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // rows: m of A (grouped by A) or (member, m) (grouped by B); columns likewise for n of B
+    const int64_t rows = g.by_a ? M : len * M, cols = g.by_a ? len * N : N;
+    if (tid < BM) {
+        const int64_t r = r0 + tid;
+        int64_t ra = -1, orow = 0;
+        if (r < rows) {
+            const int64_t m = g.by_a ? r : (r & (M - 1));
+            const int64_t c = g.by_a ? g.members[off] : g.members[off + (r >> lm)];
+            ra = (int64_t)g.gA[c] * d.sA + (int64_t)deposit((uint64_t)m, lm, d.posA_c + ln);
+            orow = (g.by_a ? 0 : c * d.sC) + m * N;
+        }
+        rowA[tid] = ra;
+        outR[tid] = orow;
+    } else if (tid < BM + BN) {
+        const int j = tid - BM;
+        const int64_t q = q0 + j;
+        int64_t cb = -1, ocol = 0;
+        if (q < cols) {
+            const int64_t n = g.by_a ? (q & (N - 1)) : q;
+            const int64_t c = g.by_a ? g.members[off + (q >> ln)] : g.members[off];
+            cb = (int64_t)g.gB[c] * d.sB + (int64_t)deposit((uint64_t)n, ln, d.posB_c);
+            ocol = (g.by_a ? c * d.sC : 0) + n;
+        }
+        colB[j] = cb;
+        outC[j] = ocol;
+    }
+    __syncthreads();
+    constexpr int KQ = BK / 4;
+    const int lr = tid >> 2, lk = (tid & 3) * KQ;
+    float2 ra[KQ], rb[KQ];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int64_t gk = k0 + lk + q;
+            const bool kin = gk < K;
+            const uint64_t oka = kin ? deposit((uint64_t)gk, nk, d.posA_k) : 0;
+            const uint64_t okb = kin ? deposit((uint64_t)gk, nk, d.posB_k) : 0;
+            ra[q] = (rowA[lr] >= 0 && kin) ? d.A[rowA[lr] + (int64_t)oka] : make_float2(0.f, 0.f);
+            rb[q] = (colB[lr] >= 0 && kin) ? d.B[colB[lr] + (int64_t)okb] : make_float2(0.f, 0.f);
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            As[buf][lk + q][lr] = ra[q];
+            Bs[buf][lk + q][lr] = rb[q];
+        }
+    };
+    float cr[TM][TN], ci[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0.f;
+    load(0);
+    store(0);
+    __syncthreads();
+    const int64_t ktiles = (K + BK - 1) / BK;
+    for (int64_t kt = 0; kt < ktiles; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < ktiles) load((kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    cr[i][j] = fmaf(a[i].x, b[j].x, cr[i][j]);
+                    cr[i][j] = fmaf(-a[i].y, b[j].y, cr[i][j]);
+                    ci[i][j] = fmaf(a[i].x, b[j].y, ci[i][j]);
+                    ci[i][j] = fmaf(a[i].y, b[j].x, ci[i][j]);
+                }
+        }
+        if (kt + 1 < ktiles) store(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int r = ty + 16 * i;
+        if (rowA[r] < 0) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int q = tx + 16 * j;
+            if (colB[q] >= 0) d.C[outR[r] + outC[q]] = make_float2(cr[i][j], ci[i][j]);
+        }
+    }
+}
+
 // Sparse-state step with a dense GEMM inside each configuration (Sec. 3.3): for configuration c
 // of the result, C[c][m][n] = sum_k A[gA[c]][m, k] B[gB[c]][n, k], where the operands' labels sit
 // at arbitrary bit positions (offsets by deposit) and C is row-major over (A-only labels,
@@ -588,6 +696,17 @@ __global__ void __launch_bounds__(256) k_sparse_gemm(GenericDesc d, int32_t ln, 
 cudaError_t simt_prepare() {
     return cudaFuncSetAttribute(k_gemm_skinny, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kSkSmem);
+}
+
+cudaError_t launch_sparse_group(const GenericDesc &d, int32_t ln, const SparseGroupDesc &g,
+                                cudaStream_t st) {
+    if (g.ntiles <= 0) return cudaSuccess;
+    if (g.ntiles > 0x7fffffffll || d.rank_c - ln < 0 || ln < 0) return cudaErrorInvalidValue;
+    if (d.nk >= 4)
+        k_sparse_group<16><<<(unsigned)g.ntiles, 256, 0, st>>>(d, ln, g);
+    else
+        k_sparse_group<8><<<(unsigned)g.ntiles, 256, 0, st>>>(d, ln, g);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_thin(const GenericDesc &d, int32_t ln, const int32_t *gA,

@@ -1699,6 +1699,9 @@ struct tn_sparse_plan {
         int ln = 0;                  // B-only dense labels (the low bits of C's dense index)
         bool gemm = false;           // tiled GEMM per configuration
         bool thin = false;           // at most 16 columns: thread per row (else element-wise)
+        bool grouped = false;        // grouped GEMM over configurations sharing an operand entry
+        int64_t g_members = 0, g_off = 0, g_len = 0, g_tiles = 0;  // offsets in `gather`
+        tn::SparseGroupDesc g{};
         tn::GenericDesc d{};
     };
     std::vector<St> steps;
@@ -1934,6 +1937,59 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
             st.gemm = d.rank_c - nb >= 3 && nb >= 3 && d.nk >= 3;
             st.thin = !st.gemm && nb <= 4 && d.rank_c - nb >= 5 && d.nk >= 2;
         }
+        if (d.nk >= 3) {
+            // group the result configurations by the operand entry they share (the operand with
+            // fewer distinct entries): one GEMM per group over the stacked other operand
+            const int64_t nc = (int64_t)C.cfg.size();
+            const int32_t *ga = gather_host.data() + st.ga, *gb = gather_host.data() + st.gb;
+            std::vector<int32_t> ka(ga, ga + nc), kb(gb, gb + nc);
+            std::sort(ka.begin(), ka.end());
+            std::sort(kb.begin(), kb.end());
+            const int64_t na = std::unique(ka.begin(), ka.end()) - ka.begin();
+            const int64_t nbk = std::unique(kb.begin(), kb.end()) - kb.begin();
+            const bool by_a = na <= nbk;
+            const int32_t *key = by_a ? ga : gb;
+            std::vector<int32_t> order((size_t)nc);
+            for (int64_t i = 0; i < nc; ++i) order[(size_t)i] = (int32_t)i;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+            const int lmv = d.rank_c - st.ln;
+            const int64_t M = 1ll << lmv, N = 1ll << st.ln;
+            std::vector<int32_t> goff, glen, tiles;
+            double useful = 0, padded = 0;
+            for (int64_t i = 0; i < nc;) {
+                int64_t j = i;
+                while (j < nc && key[order[(size_t)j]] == key[order[(size_t)i]]) ++j;
+                const int64_t len = j - i;
+                const int64_t rows = by_a ? M : len * M, cols = by_a ? len * N : N;
+                const int64_t tr = (rows + 63) / 64, tc = (cols + 63) / 64;
+                const int gi = (int)goff.size();
+                goff.push_back((int32_t)i);
+                glen.push_back((int32_t)len);
+                for (int64_t a2 = 0; a2 < tr; ++a2)
+                    for (int64_t b2 = 0; b2 < tc; ++b2) {
+                        tiles.push_back(gi);
+                        tiles.push_back((int32_t)a2);
+                        tiles.push_back((int32_t)b2);
+                    }
+                useful += (double)rows * (double)cols;
+                padded += (double)(tr * tc) * 4096.0;
+                i = j;
+            }
+            if (useful >= 0.25 * padded && (int64_t)tiles.size() / 3 < 0x7fffffffll) {
+                st.grouped = true;
+                st.g.by_a = by_a ? 1 : 0;
+                st.g.ntiles = (int64_t)tiles.size() / 3;
+                st.g_members = (int64_t)gather_host.size();
+                gather_host.insert(gather_host.end(), order.begin(), order.end());
+                st.g_off = (int64_t)gather_host.size();
+                gather_host.insert(gather_host.end(), goff.begin(), goff.end());
+                st.g_len = (int64_t)gather_host.size();
+                gather_host.insert(gather_host.end(), glen.begin(), glen.end());
+                st.g_tiles = (int64_t)gather_host.size();
+                gather_host.insert(gather_host.end(), tiles.begin(), tiles.end());
+            }
+        }
         p->tcc += 8.0 * (double)C.cfg.size() * std::ldexp(1.0, d.rank_c + d.nk);
         p->steps.push_back(st);
         node[a] = c;
@@ -2102,6 +2158,14 @@ tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_
                     "sparse-state plan: %s", cudaGetErrorString(e));
     }
     for (auto &st : p->steps) {
+        if (st.grouped) {
+            st.g.gA = p->gather + st.ga;
+            st.g.gB = p->gather + st.gb;
+            st.g.members = p->gather + st.g_members;
+            st.g.grp_off = p->gather + st.g_off;
+            st.g.grp_len = p->gather + st.g_len;
+            st.g.tiles = p->gather + st.g_tiles;
+        }
         st.d.A = p->arena + p->ten[st.a].off;
         st.d.B = p->arena + p->ten[st.b].off;
         st.d.C = p->arena + p->ten[st.c].off;
@@ -2142,7 +2206,9 @@ tn_status tn_sparse_contract(tn_sparse_plan_t *p, void *amps_dev, void *stream_)
         const auto &st = p->steps[k];
         if (p->skip[k]) continue;
         const int64_t nconf = (int64_t)p->ten[st.c].cfg.size();
-        if (st.gemm)
+        if (st.grouped)
+            TN_CUDA(tn::launch_sparse_group(st.d, st.ln, st.g, stream));
+        else if (st.gemm)
             TN_CUDA(tn::launch_sparse_gemm(st.d, st.ln, p->gather + st.ga, p->gather + st.gb,
                                            nconf, stream));
         else if (st.thin)
@@ -2177,8 +2243,9 @@ tn_status tn_sparse_get_info(const tn_sparse_plan_t *p, tn_sparse_info *out) {
     out->dense_subtrees = (int64_t)p->subs.size();
     for (size_t k = 0; k < p->skip.size(); ++k) out->dense_subtree_steps += p->skip[k] ? 1 : 0;
     for (const auto &st : p->steps) {
-        out->gemm_steps += st.gemm ? 1 : 0;
-        out->thin_steps += st.thin ? 1 : 0;
+        out->gemm_steps += !st.grouped && st.gemm ? 1 : 0;
+        out->thin_steps += !st.grouped && !st.gemm && st.thin ? 1 : 0;
+        out->grouped_steps += st.grouped ? 1 : 0;
     }
     return TN_OK;
 }

@@ -182,6 +182,21 @@ cudaError_t launch_sparse_step(const GenericDesc &d, const int32_t *gA, const in
 // then the ln B-only labels), row-major; for steps with enough m, n and k
 cudaError_t launch_sparse_gemm(const GenericDesc &d, int32_t ln, const int32_t *gA,
                                const int32_t *gB, int64_t nconf, cudaStream_t st);
+// Grouped form of a sparse-state step (the gather-indexed grouped GEMM): the result
+// configurations are grouped by the configuration of one operand (by_a: A's), so each group is
+// one GEMM whose other operand is the stack of its members' entries (columns (member, n) when
+// grouped by A, rows (member, m) when grouped by B).  Tiles of 64 x 64 are listed on the host.
+struct SparseGroupDesc {
+    const int32_t *gA, *gB;    // per result configuration: operand configurations
+    const int32_t *members;    // result configurations, group by group
+    const int32_t *grp_off;    // per group: first member
+    const int32_t *grp_len;    // per group: members
+    const int32_t *tiles;      // per tile: group, row tile, column tile
+    int64_t ntiles;
+    int32_t by_a;
+};
+cudaError_t launch_sparse_group(const GenericDesc &d, int32_t ln, const SparseGroupDesc &g,
+                                cudaStream_t st);
 // the same step for at most 16 columns (ln <= 4): thread per (configuration, row)
 cudaError_t launch_sparse_thin(const GenericDesc &d, int32_t ln, const int32_t *gA,
                                const int32_t *gB, int64_t nconf, cudaStream_t st);

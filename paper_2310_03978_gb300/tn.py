@@ -83,7 +83,7 @@ class SparseInfo(C.Structure):
                 ("arena_bytes", C.c_int64), ("tcc", C.c_double), ("kernel_launches", C.c_int64),
                 ("max_log2_dense", C.c_int32), ("gemm_steps", C.c_int32),
                 ("dense_subtrees", C.c_int64), ("dense_subtree_steps", C.c_int64),
-                ("thin_steps", C.c_int64), ("reserved", C.c_int64 * 1)]
+                ("thin_steps", C.c_int64), ("grouped_steps", C.c_int64)]
 
 
 class TnError(RuntimeError):
