@@ -6,7 +6,9 @@
  * in pairwise steps along a given path (Sec. 3.1), each step being the einsum of Sec. 2.4,
  * Eq. (chap2_einsum), run as a (permuted) complex GEMM on the GPU (Sec. 4.1).  The network may
  * be cut on a set of bonds (slicing, Sec. 3.2); every slice is an independent sub-task and the
- * amplitudes are the sum of the slice results.
+ * amplitudes are the sum of the slice results.  Two further entry points: path annealing with
+ * dynamic slicing on the host (tn_path_optimize, Sec. 3.2) and the sparse-state contraction for
+ * a list of sampled bitstrings (tn_sparse_plan / tn_sparse_contract, Sec. 3.3).
  *
  * Conventions for every entry point:
  *   - Every call returns a tn_status; nothing is thrown across the ABI.  On failure a message is
@@ -38,7 +40,7 @@ typedef enum {
     TN_ERR_CUDA = 5,         /* a CUDA runtime/driver call failed; see the detail message   */
     TN_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                          */
     TN_ERR_UNSUPPORTED = 7,  /* valid input this build does not handle (e.g. dim != 2)     */
-    TN_ERR_NUMERIC = 8       /* scaled low-precision storage overflowed                     */
+    TN_ERR_NUMERIC = 8       /* reserved: scaled storage overflow (bounded exponents rule it out) */
 } tn_status;
 
 /* Arithmetic of the contraction steps (Sec. 4.2-4.3).  Storage between steps is complex64
@@ -204,7 +206,10 @@ tn_status tn_plan_get_step_info(const tn_plan_t *plan, int64_t step, tn_step_inf
  *                     up to FP64 rounding.
  * Device work is asynchronous on `stream`; an asynchronous failure is reported by this call
  * when opts.sync_each_call was set, otherwise by the next call on the plan.
- * Errors: TN_ERR_INVALID_ARG (range), TN_ERR_CUDA, TN_ERR_TIMEOUT, TN_ERR_NUMERIC.
+ * Errors: TN_ERR_INVALID_ARG (range), TN_ERR_CUDA, TN_ERR_TIMEOUT.  (TN_ERR_NUMERIC is not
+ * returned: every power-of-two exponent of the scaled 16-bit storage comes from a bound on
+ * measured max-abs values, so that storage cannot overflow for finite inputs; non-finite inputs
+ * propagate into the amplitudes.)
  */
 tn_status tn_contract(tn_plan_t *plan, int64_t slice_begin, int64_t slice_end, void *amps_dev,
                       void *stream);
