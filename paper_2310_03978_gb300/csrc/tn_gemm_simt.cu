@@ -498,6 +498,7 @@ __global__ void __launch_bounds__(256) k_sparse_group(GenericDesc d, int32_t ln,
     __shared__ __align__(16) float2 As[2][BK][BM + 1];
     __shared__ __align__(16) float2 Bs[2][BK][BN + 1];
     __shared__ int64_t rowA[BM], colB[BN], outR[BM], outC[BN];
+    __shared__ uint64_t kofA[2][BK], kofB[2][BK];  // operand offsets of the K chunk's elements
     const int lm = d.rank_c - ln, nk = d.nk;
     const int64_t M = 1ll << lm, N = 1ll << ln, K = 1ll << nk;
     const int32_t *t = g.tiles + 3 * (int64_t)blockIdx.x;
@@ -531,19 +532,30 @@ __global__ void __launch_bounds__(256) k_sparse_group(GenericDesc d, int32_t ln,
         colB[j] = cb;
         outC[j] = ocol;
     }
+    // K-chunk offset tables (deposits of k into A's and B's contracted bits): chunk kt uses
+    // buffer kt & 1; threads 128.. fill a chunk's table before the barrier that precedes its
+    // loads, two chunks ahead of its use
+    auto koffs = [&](int64_t k0, int buf) {
+        const int e = tid - 128;
+        if (e >= 0 && e < BK) {
+            const int64_t gk = k0 + e;
+            kofA[buf][e] = gk < K ? deposit((uint64_t)gk, nk, d.posA_k) : 0;
+            kofB[buf][e] = gk < K ? deposit((uint64_t)gk, nk, d.posB_k) : 0;
+        }
+    };
+    koffs(0, 0);
     __syncthreads();
     constexpr int KQ = BK / 4;
     const int lr = tid >> 2, lk = (tid & 3) * KQ;
     float2 ra[KQ], rb[KQ];
-    auto load = [&](int64_t k0) {
+    auto load = [&](int64_t k0, int buf) {
 #pragma unroll
         for (int q = 0; q < KQ; ++q) {
-            const int64_t gk = k0 + lk + q;
-            const bool kin = gk < K;
-            const uint64_t oka = kin ? deposit((uint64_t)gk, nk, d.posA_k) : 0;
-            const uint64_t okb = kin ? deposit((uint64_t)gk, nk, d.posB_k) : 0;
-            ra[q] = (rowA[lr] >= 0 && kin) ? d.A[rowA[lr] + (int64_t)oka] : make_float2(0.f, 0.f);
-            rb[q] = (colB[lr] >= 0 && kin) ? d.B[colB[lr] + (int64_t)okb] : make_float2(0.f, 0.f);
+            const bool kin = k0 + lk + q < K;
+            ra[q] = (rowA[lr] >= 0 && kin) ? d.A[rowA[lr] + (int64_t)kofA[buf][lk + q]]
+                                           : make_float2(0.f, 0.f);
+            rb[q] = (colB[lr] >= 0 && kin) ? d.B[colB[lr] + (int64_t)kofB[buf][lk + q]]
+                                           : make_float2(0.f, 0.f);
         }
     };
     auto store = [&](int buf) {
@@ -558,13 +570,17 @@ __global__ void __launch_bounds__(256) k_sparse_group(GenericDesc d, int32_t ln,
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) cr[i][j] = ci[i][j] = 0.f;
-    load(0);
+    load(0, 0);
     store(0);
-    __syncthreads();
     const int64_t ktiles = (K + BK - 1) / BK;
+    if (ktiles > 1) koffs(BK, 1);
+    __syncthreads();
     for (int64_t kt = 0; kt < ktiles; ++kt) {
         const int buf = kt & 1;
-        if (kt + 1 < ktiles) load((kt + 1) * BK);
+        if (kt + 1 < ktiles) load((kt + 1) * BK, buf ^ 1);
+        // the table of chunk kt + 2 reuses buffer buf (its last reads were chunk kt's loads, in
+        // the previous iteration); the barrier below publishes it before chunk kt + 2 loads
+        if (kt + 2 < ktiles) koffs((kt + 2) * BK, buf);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             float2 a[TM], b[TN];
