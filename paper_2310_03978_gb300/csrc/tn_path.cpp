@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <new>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -366,12 +367,35 @@ struct Chain {
 
 }  // namespace
 
+static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
+                                    const int32_t *const *labels, int32_t num_open,
+                                    const int32_t *open_labels, const int32_t *path_in,
+                                    const tn_path_options *opts, int32_t *path_out,
+                                    int32_t *sliced_out, int32_t sliced_capacity,
+                                    tn_path_info *info);
+
 extern "C" tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
                                       const int32_t *const *labels, int32_t num_open,
                                       const int32_t *open_labels, const int32_t *path_in,
                                       const tn_path_options *opts, int32_t *path_out,
                                       int32_t *sliced_out, int32_t sliced_capacity,
                                       tn_path_info *info) {
+    try {
+        return path_optimize_impl(num_tensors, ranks, labels, num_open, open_labels, path_in,
+                                  opts, path_out, sliced_out, sliced_capacity, info);
+    } catch (const std::bad_alloc &) {
+        return tn::report(TN_ERR_OOM, "tn_path_optimize: host memory exhausted");
+    } catch (...) {
+        return tn::report(TN_ERR_INVALID_ARG, "tn_path_optimize: internal error");
+    }
+}
+
+static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
+                                    const int32_t *const *labels, int32_t num_open,
+                                    const int32_t *open_labels, const int32_t *path_in,
+                                    const tn_path_options *opts, int32_t *path_out,
+                                    int32_t *sliced_out, int32_t sliced_capacity,
+                                    tn_path_info *info) {
     if (num_tensors < 1 || !ranks || !labels || num_open < 0 || (num_open > 0 && !open_labels) ||
         (num_tensors > 1 && (!path_in || !path_out)) || sliced_capacity < 0 ||
         (sliced_capacity > 0 && !sliced_out) || !info)
@@ -471,9 +495,20 @@ extern "C" tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
     chains.reserve(o.chains);
     for (int c = 0; c < o.chains; ++c)
         chains.emplace_back(T0, o.seed * 0x9e3779b97f4a7c15ull + (uint64_t)c + 1);
+    // chains that get no thread (thread creation refused) run on the calling thread; nothing
+    // is thrown across the C ABI
     std::vector<std::thread> th;
-    for (int c = 1; c < o.chains; ++c) th.emplace_back([&, c] { chains[c].run(P, prm); });
-    chains[0].run(P, prm);
+    std::vector<char> started((size_t)o.chains, 0);
+    for (int c = 1; c < o.chains; ++c) {
+        try {
+            th.emplace_back([&, c] { chains[c].run(P, prm); });
+            started[(size_t)c] = 1;
+        } catch (...) {
+            break;
+        }
+    }
+    for (int c = 0; c < o.chains; ++c)
+        if (!started[(size_t)c]) chains[c].run(P, prm);
     for (auto &t : th) t.join();
     int best = 0;
     double best_score = chains[0].T.score(o.alpha, o.beta);
