@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <new>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -448,9 +449,26 @@ tn_status build_descriptors(tn_plan_t *p);
 
 }  // namespace
 
+static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int32_t *path,
+                           int32_t num_sliced, const int32_t *sliced_labels, tn_precision mode,
+                           const tn_plan_options *opts, tn_plan_t **out);
+
+// host allocations of the planners may throw; nothing crosses the C ABI
 extern "C" tn_status tn_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
                              int32_t num_sliced, const int32_t *sliced_labels, tn_precision mode,
                              const tn_plan_options *opts, tn_plan_t **out) {
+    try {
+        return plan_impl(net, path_len, path, num_sliced, sliced_labels, mode, opts, out);
+    } catch (const std::bad_alloc &) {
+        return fail(TN_ERR_OOM, "tn_plan: host memory exhausted");
+    } catch (...) {
+        return fail(TN_ERR_INVALID_ARG, "tn_plan: internal error");
+    }
+}
+
+static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int32_t *path,
+                           int32_t num_sliced, const int32_t *sliced_labels, tn_precision mode,
+                           const tn_plan_options *opts, tn_plan_t **out) {
     g_err.clear();
     if (!out) return fail(TN_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -1777,9 +1795,27 @@ int dense_bit(const std::vector<int> &dense, int label) {  // bit position, or -
 
 extern "C" {
 
+static tn_status sparse_plan_impl(const tn_network_t *net, int32_t path_len,
+                                  const int32_t *path, int64_t num_samples,
+                                  const uint8_t *samples, tn_precision mode,
+                                  tn_sparse_plan_t **out);
+
 tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
                          int64_t num_samples, const uint8_t *samples, tn_precision mode,
                          tn_sparse_plan_t **out) {
+    try {
+        return sparse_plan_impl(net, path_len, path, num_samples, samples, mode, out);
+    } catch (const std::bad_alloc &) {
+        return fail(TN_ERR_OOM, "tn_sparse_plan: host memory exhausted");
+    } catch (...) {
+        return fail(TN_ERR_INVALID_ARG, "tn_sparse_plan: internal error");
+    }
+}
+
+static tn_status sparse_plan_impl(const tn_network_t *net, int32_t path_len,
+                                  const int32_t *path, int64_t num_samples,
+                                  const uint8_t *samples, tn_precision mode,
+                                  tn_sparse_plan_t **out) {
     tn_status cs = check_net(net);
     if (cs != TN_OK) return cs;
     if (!out || num_samples < 1 || !samples || path_len < 0 || (path_len > 0 && !path))
