@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtn.so")
-SOURCES = ["tn_host.cu", "tn_kernels.cu", "tn_gemm_simt.cu", "tn_gemm_tc.cu", "tn_noalloc.cu",
-           "tn_path.cpp"]
+SOURCES = ["tn_host.cu", "tn_sparse.cu", "tn_kernels.cu", "tn_gemm_simt.cu", "tn_gemm_tc.cu",
+           "tn_noalloc.cu", "tn_path.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #define TN_MAXR 48  // largest rank handled by a kernel descriptor
 
 #include "../../include/tn.h"
@@ -18,6 +20,13 @@ namespace tn {
 
 // Record `msg` as this thread's error detail (tn_last_error_detail) and return `s`.
 tn_status report(tn_status s, const char *msg);
+// The same with a printf format.
+tn_status reportf(tn_status s, const char *fmt, ...);
+
+constexpr uint32_t kNetMagic = 0x544e4e54u;     // "TNNT": a tn_network
+constexpr uint32_t kSparseMagic = 0x544e5350u;  // "TNSP": a sparse-state plan
+// Free a sparse-state plan (tn_destroy of a handle with kSparseMagic).
+void sparse_destroy(void *handle);
 
 // Direct planar 16-bit output of a GEMM whose result feeds a tensor-core step: the producer
 // writes stored = value * 2^-e into the consumer's planar buffer (re, im, and for the 3M form
@@ -298,3 +307,15 @@ bool tc_variant_fits(int variant, int lk, int ln);
 void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits);
 
 }  // namespace tn
+
+// A loaded network (tn_network_load): labels and offsets on the host, the complex128 data on the
+// device.  Shared by the dense planner and the sparse-state planner.
+struct tn_network {
+    uint32_t magic = tn::kNetMagic;
+    int device = 0;
+    std::vector<std::vector<int>> labels;  // per tensor, row-major order
+    std::vector<int64_t> offset;           // complex128 element offset of each tensor
+    std::vector<int> open;
+    int64_t total = 0;                     // complex128 elements
+    double2 *data = nullptr;               // device copy
+};
