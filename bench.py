@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--sa-alpha", type=float, default=512.0,
                     help="weight of the memory term T_mc in the annealing score (multiply-adds "
                          "per element moved)")
+    ap.add_argument("--small-steps", type=int, default=50,
+                    help="also time the 12-qubit circuit (64 amplitudes, complex64); 0 = skip")
     ap.add_argument("--sparse-only", action="store_true",
                     help="run only the sparse-state measurement and print its JSON line")
     ap.add_argument("--sparse-steps", type=int, default=3,
@@ -397,6 +399,34 @@ def run_ours(args, rank, world, local_rank):
               "slices": si["num_slices"], "max_log2": si["max_log2_size"], "opt_s": sa_opt_s,
               "info": sa_info, "result": sa_result}
 
+    # the 12-qubit circuit (3x4 grid, 8 cycles, 64 amplitudes) on the complex64 path: latency of
+    # one small batch, checked against the state vector
+    small = None
+    if world == 1 and args.small_steps > 0:
+        wl_s = W.small_workload()
+        tnet_sm = tn.Network.from_workload(wl_s.network)
+        splan = tn.Plan(tnet_sm, wl_s.path, wl_s.sliced, mode="c64", use_graph=True)
+        amps = torch.zeros(1 << len(wl_s.network.open_labels), dtype=torch.complex128, device=dev)
+        splan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        sm_result = amps.cpu().numpy().copy()
+        for _ in range(3):
+            splan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        sm_ms = time_steps(torch, lambda: splan.contract(amps, stream=stream), args.small_steps,
+                           stream) / args.small_steps
+        sm_launch = splan.info()["kernel_launches"]
+        splan.close()
+        tnet_sm.close()
+        del amps
+        nq = wl_s.network
+        sv = O.statevector(wl_s.circuit.n_qubits, wl_s.circuit.gates)
+        idx = [W.full_index(nq.n_qubits, nq.open_qubits, nq.closed_bits, x)
+               for x in range(1 << len(nq.open_qubits))]
+        small = {"workload": "sycamore_3x4_c8_open6", "mode": "c64", "us_per_batch": sm_ms * 1e3,
+                 "steps": args.small_steps,
+                 "amp_rel_l2_vs_statevector": O.rel_l2(sm_result, sv[idx])}
+
     # sparse-state contraction (Sec. 3.3): the amplitudes of 4096 sampled bitstrings of a
     # 24-qubit circuit with every qubit open, along an annealed path
     sparse = measure_sparse(args, dev, stream) if world == 1 and args.sparse_steps > 0 else None
@@ -490,6 +520,8 @@ def run_ours(args, rank, world, local_rank):
             "optimiser_s": sa["opt_s"], "optimiser": "tn_path_optimize seed %d, 16 chains, "
             "1000 + 40 per slice + 500 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
             % (SA_SEED, args.sa_alpha)}
+    if small is not None:
+        line["small_circuit"] = small
     if sparse is not None:
         line["sparse_state"] = sparse_line(args, sparse)
     if world == 1 and not args.no_cpu_baseline:
