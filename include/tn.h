@@ -285,7 +285,11 @@ typedef struct {
     double t_start, t_end;     /* temperatures in score units (<= 0: defaults 1.0 and 0.01)  */
     double alpha;              /* weight of T_mc (>= 0)                                       */
     double beta;               /* weight of log2(T_sc) (>= 0)                                 */
-    int32_t reserved[8];
+    int32_t greedy_trials;     /* > 0: each chain first builds this many random greedy trees
+                                  (cost log2 size(out) - g log2(size(a) + size(b)), g and the
+                                  noise temperature drawn per tree) and anneals from the best
+                                  of them and path_in                                         */
+    int32_t reserved[7];
 } tn_path_options;
 
 typedef struct {

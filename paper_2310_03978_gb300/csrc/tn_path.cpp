@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <queue>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -224,8 +225,137 @@ void path_from_tree(const Tree &T, int32_t *out) {
 
 struct Params {
     double alpha, beta, t_start, t_end;
-    int sweeps, sweeps_per_slice, sweeps_final, max_log2_size, max_sliced;
+    int sweeps, sweeps_per_slice, sweeps_final, max_log2_size, max_sliced, greedy_trials;
 };
+
+// Random greedy tree: repeatedly contract the connected pair with the lowest perturbed cost
+// log2 size(result) - g * log2(size(a) + size(b)) (sizes in elements, every dim 2); the
+// perturbation subtracts 8 * temp * G with G a Gumbel(0, 1) draw, so temp = 0 is a plain greedy
+// rule.  (In log units a large result is charged by its width, not its element count, which
+// keeps the rule from contracting every small pair before the first large one.)  Tensors left
+// without a shared label at the end are paired smallest first.
+void random_greedy(const Problem &P, Rng &rng, double g, double temp, Tree &T) {
+    const int n = P.n, W = P.W;
+    T.n = n;
+    T.W = W;
+    T.lc.assign(2 * n - 1, -1);
+    T.rc.assign(2 * n - 1, -1);
+    T.par.assign(2 * n - 1, -1);
+    T.L.assign((size_t)(2 * n - 1) * W, 0);
+    T.sz.assign(2 * n - 1, 0);
+    T.cc.assign(2 * n - 1, 0);
+    if (T.S.size() != (size_t)W) T.S.assign(W, 0);
+    T.emax = (int)P.value.size() + 1;
+    std::copy(P.leaf.begin(), P.leaf.end(), T.L.begin());
+    const int nl = (int)P.value.size();
+    std::vector<int> holder((size_t)nl * 2, -1);   // the (at most two) active holders of a label
+    std::vector<int> version((size_t)(2 * n - 1), 0);
+    std::vector<char> alive((size_t)(2 * n - 1), 0);
+    std::vector<int> pc((size_t)(2 * n - 1), 0);   // label counts
+    auto add_holder = [&](int l, int v) {
+        if (holder[2 * l] < 0) holder[2 * l] = v;
+        else holder[2 * l + 1] = v;
+    };
+    auto drop_holder = [&](int l, int v) {
+        if (holder[2 * l] == v) holder[2 * l] = -1;
+        else if (holder[2 * l + 1] == v) holder[2 * l + 1] = -1;
+    };
+    for (int v = 0; v < n; ++v) {
+        alive[v] = 1;
+        const uint64_t *lv = T.set(v);
+        for (int w = 0; w < W; ++w) {
+            uint64_t b = lv[w];
+            pc[v] += __builtin_popcountll(b);
+            while (b) {
+                add_holder(w * 64 + __builtin_ctzll(b), v);
+                b &= b - 1;
+            }
+        }
+    }
+    struct Cand {
+        double key;
+        int a, b, va, vb;
+        bool operator<(const Cand &o) const { return key > o.key; }  // min-heap
+    };
+    std::priority_queue<Cand> q;
+    auto push_pair = [&](int a, int b) {
+        const uint64_t *la = T.set(a), *lb = T.set(b);
+        int x = 0;
+        for (int w = 0; w < W; ++w) x += __builtin_popcountll(la[w] ^ lb[w]);
+        const double cost = (double)x - g * std::log2(std::ldexp(1.0, pc[a]) + std::ldexp(1.0, pc[b]));
+        double key = cost;
+        if (temp > 0) {
+            double u = rng.uniform();
+            if (u < 1e-300) u = 1e-300;
+            key -= 8.0 * temp * (-std::log(-std::log(u)));
+        }
+        q.push(Cand{key, a, b, version[a], version[b]});
+    };
+    auto push_neighbours = [&](int v) {
+        const uint64_t *lv = T.set(v);
+        for (int w = 0; w < W; ++w) {
+            uint64_t b = lv[w];
+            while (b) {
+                const int l = w * 64 + __builtin_ctzll(b);
+                b &= b - 1;
+                for (int h = 0; h < 2; ++h) {
+                    const int u = holder[2 * l + h];
+                    if (u >= 0 && u != v && u < v) push_pair(u, v);
+                    else if (u >= 0 && u != v) push_pair(v, u);
+                }
+            }
+        }
+    };
+    for (int v = 0; v < n; ++v) push_neighbours(v);
+    int next = n, remaining = n;
+    auto merge = [&](int a, int b) {
+        const int c = next++;
+        T.lc[c] = a;
+        T.rc[c] = b;
+        T.par[a] = c;
+        T.par[b] = c;
+        const uint64_t *la = T.set(a), *lb = T.set(b);
+        uint64_t *lc = T.set(c);
+        for (int w = 0; w < W; ++w) {
+            lc[w] = la[w] ^ lb[w];
+            for (uint64_t x = la[w]; x; x &= x - 1) drop_holder(w * 64 + __builtin_ctzll(x), a);
+            for (uint64_t x = lb[w]; x; x &= x - 1) drop_holder(w * 64 + __builtin_ctzll(x), b);
+        }
+        for (int w = 0; w < W; ++w)
+            for (uint64_t x = lc[w]; x; x &= x - 1) {
+                add_holder(w * 64 + __builtin_ctzll(x), c);
+                pc[c] += 1;
+            }
+        alive[a] = alive[b] = 0;
+        version[a]++;
+        version[b]++;
+        alive[c] = 1;
+        --remaining;
+        return c;
+    };
+    while (!q.empty()) {
+        const Cand t = q.top();
+        q.pop();
+        if (!alive[t.a] || !alive[t.b] || version[t.a] != t.va || version[t.b] != t.vb) continue;
+        const int c = merge(t.a, t.b);
+        push_neighbours(c);
+    }
+    // no shared label left: pair the remaining tensors, smallest first
+    while (remaining > 1) {
+        int a = -1, b = -1;
+        for (int v = 0; v < next; ++v) {
+            if (!alive[v]) continue;
+            if (a < 0 || pc[v] < pc[a]) {
+                b = a;
+                a = v;
+            } else if (b < 0 || pc[v] < pc[b]) {
+                b = v;
+            }
+        }
+        merge(a, b);
+    }
+    T.root = n == 1 ? 0 : next - 1;
+}
 
 struct Chain {
     Tree T;
@@ -351,7 +481,26 @@ struct Chain {
         return true;
     }
 
+    // random greedy trees with sampled cost weight and temperature; keep the best by score
+    void greedy_start(const Problem &P, const Params &p) {
+        T.rebuild();
+        double best = T.score(p.alpha, p.beta);
+        Tree cand = T;
+        for (int k = 0; k < p.greedy_trials; ++k) {
+            const double g = 0.5 + rng.uniform();                      // size weight in [0.5, 1.5)
+            const double temp = std::exp2(-8.0 + 8.0 * rng.uniform());  // in [2^-8, 1)
+            random_greedy(P, rng, g, temp, cand);
+            cand.rebuild();
+            const double sc = cand.score(p.alpha, p.beta);
+            if (sc < best) {
+                best = sc;
+                T = cand;
+            }
+        }
+    }
+
     void run(const Problem &P, const Params &p) {
+        if (p.greedy_trials > 0) greedy_start(P, p);
         T.rebuild();
         anneal(p.sweeps, p.t_start, p.t_end, p);
         if (p.max_log2_size > 0) {
@@ -420,6 +569,7 @@ static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
         o.max_log2_size = opts->max_log2_size;
         if (opts->max_sliced > 0) o.max_sliced = opts->max_sliced;
         if (opts->chains > 0) o.chains = opts->chains;
+        if (opts->greedy_trials > 0) o.greedy_trials = opts->greedy_trials;
     }
     if (o.alpha < 0 || o.beta < 0 || o.max_log2_size < 0 || o.chains > 256 || o.t_end > o.t_start)
         return tn::report(TN_ERR_INVALID_ARG, "tn_path_optimize: invalid option");
@@ -485,7 +635,7 @@ static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
     }
     T0.rebuild();
     const Params prm{o.alpha, o.beta, o.t_start, o.t_end, o.sweeps, o.sweeps_per_slice,
-                     o.sweeps_final, o.max_log2_size, o.max_sliced};
+                     o.sweeps_final, o.max_log2_size, o.max_sliced, o.greedy_trials};
     tn_path_info out{};
     out.initial_log2_tcc = 3.0 + Tree::log2_sum(T0.hcc);
     out.initial_max_log2_size = T0.max_size();

@@ -164,3 +164,24 @@ def test_argument_checks():
     with pytest.raises(T.TnError) as e:
         T.path_optimize(labels, open_labels, path, t_start=0.01, t_end=0.1)
     assert e.value.status == code["TN_ERR_INVALID_ARG"]
+
+
+def test_random_greedy_start_beats_the_plain_greedy_tree():
+    # 30-qubit bench circuit: random greedy trees (no annealing) against the greedy input path
+    wl = W.bench_workload()
+    net = wl.network
+    _, tcc0, _ = W.path_cost(net.labels, net.open_labels, wl.path)
+    path, _, info = T.path_optimize(net.labels, net.open_labels, wl.path, seed=2, sweeps=0,
+                                    sweeps_final=0, greedy_trials=20)
+    max_log, tcc, _ = W.path_cost(net.labels, net.open_labels, path)
+    assert tcc <= tcc0 and abs(info["log2_tcc"] - math.log2(tcc)) < 1e-9
+    again, _, _ = T.path_optimize(net.labels, net.open_labels, wl.path, seed=2, sweeps=0,
+                                  sweeps_final=0, greedy_trials=20)
+    assert again == path
+    # the amplitudes along a random greedy tree of the small circuit equal the oracle's
+    sw = W.small_workload()
+    p2, _, _ = T.path_optimize(sw.network.labels, sw.network.open_labels, sw.path, seed=3,
+                               sweeps=0, sweeps_final=0, greedy_trials=10)
+    ref = O.contract(sw.network.tensors, sw.network.labels, sw.network.open_labels, sw.path)
+    got = O.contract(sw.network.tensors, sw.network.labels, sw.network.open_labels, p2)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
