@@ -72,6 +72,10 @@ def parse_args():
                          "per element moved)")
     ap.add_argument("--small-steps", type=int, default=50,
                     help="also time the 12-qubit circuit (64 amplitudes, complex64); 0 = skip")
+    ap.add_argument("--sycamore53", type=int, default=0,
+                    help="time this many batches of slices of the 53-qubit 16-cycle circuit "
+                         "(annealed path, slices capped at 2^30 elements) and extrapolate to "
+                         "all slices; prints its own JSON line")
     ap.add_argument("--sparse-only", action="store_true",
                     help="run only the sparse-state measurement and print its JSON line")
     ap.add_argument("--sparse-steps", type=int, default=3,
@@ -536,6 +540,161 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
+def supported_slices(net, sliced, seed, count):
+    """Up to ``count`` distinct slice ids (bit j = value of sliced[j]) on which no tensor, alone
+    or with its neighbouring vectors absorbed, is zero once restricted to its sliced bonds (entries
+    below 1e-12 of its largest count as zero): a seeded depth-first search over the bits with the
+    values tried in random order."""
+    import itertools
+    pos = {l: j for j, l in enumerate(sliced)}
+    # every gate also with its neighbouring vectors (|0> inputs, <b| projectors) absorbed: a
+    # projector after a swap-like fSim fixes the partner's input bond
+    vec = {ls[0]: t for t, ls in zip(net.tensors, net.labels) if len(ls) == 1}
+    pieces = list(zip(net.tensors, net.labels))
+    for t, ls in zip(net.tensors, net.labels):
+        if len(ls) < 2 or not any(l in vec for l in ls):
+            continue
+        ls = list(ls)
+        for l in list(ls):
+            if l in vec:
+                t = np.moveaxis(np.tensordot(t, vec[l], axes=([ls.index(l)], [0])), -1, -1)
+                ls.remove(l)
+        pieces.append((t, ls))
+    cons = []
+    for t, ls in pieces:
+        if not len(ls):
+            continue
+        axes = [i for i, l in enumerate(ls) if l in pos]
+        if not axes:
+            continue
+        big = np.abs(t) > 1e-12 * np.abs(t).max()
+        ok = set()
+        for vals in itertools.product((0, 1), repeat=len(axes)):
+            idx = [slice(None)] * t.ndim
+            for a, v in zip(axes, vals):
+                idx[a] = v
+            if big[tuple(idx)].any():
+                ok.add(vals)
+        if len(ok) < 1 << len(axes):
+            cons.append(([pos[ls[a]] for a in axes], ok))
+    by_bit = [[] for _ in sliced]
+    for c in cons:
+        for b in c[0]:
+            by_bit[b].append(c)
+    rng = np.random.default_rng(seed)
+    found = []
+    for _ in range(64 * count):
+        if len(found) == count:
+            break
+        val = [-1] * len(sliced)
+
+        def fits(b):
+            for bits, ok in by_bit[b]:
+                if not any(all(val[x] < 0 or val[x] == v for x, v in zip(bits, vs)) for vs in ok):
+                    return False
+            return True
+
+        def dfs(b):
+            if b == len(sliced):
+                return True
+            for v in rng.permutation(2):
+                val[b] = int(v)
+                if fits(b) and dfs(b + 1):
+                    return True
+            val[b] = -1
+            return False
+
+        if dfs(0):
+            s = sum(v << j for j, v in enumerate(val))
+            if s not in found:
+                found.append(s)
+    return found
+
+
+def run_sycamore53(args):
+    """53-qubit, 16-cycle Sycamore-shaped circuit, 2^12 amplitudes (12 open qubits): a path
+    annealed from random greedy trees with the largest intermediate bounded by slicing to 2^30
+    elements; `args.sycamore53` batches of slices timed, the time per slice extrapolated to all
+    slices; the first two slices also contracted on the complex64 path for the error."""
+    import torch
+    from oracle import oracle as O
+    from paper_2310_03978_gb300 import tn, workload as W
+    circ, net = W.sycamore53_network()
+    t0 = time.perf_counter()
+    g = W.greedy_path(net.labels, net.open_labels)
+    path, _, _ = tn.path_optimize(net.labels, net.open_labels, g, seed=SA_SEED, sweeps=2000,
+                                  sweeps_final=0, t_start=0.01, t_end=0.0005, chains=16,
+                                  greedy_trials=100, beta=1.0)
+    path, sliced, info = tn.path_optimize(net.labels, net.open_labels, path, seed=SA_SEED + 1,
+                                          sweeps=0, sweeps_per_slice=60, sweeps_final=300,
+                                          t_start=0.005, t_end=0.0005, chains=16,
+                                          max_log2_size=30)
+    opt_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.Plan(tnet, path, sliced, mode=args.mode, use_graph=True, autotune=True,
+                   mixed_topk=args.mixed_topk)
+    pi = plan.info()
+    sb = pi["slices_in_flight"]
+    amps = torch.zeros(1 << len(net.open_labels), dtype=torch.complex128, device="cuda")
+    for w in range(2):  # the first batch autotunes
+        plan.contract(amps, w * sb, (w + 1) * sb, stream=stream)
+    torch.cuda.synchronize()
+    nb = max(1, args.sycamore53)
+    state = {"i": 2}
+
+    def batch():
+        i = state["i"]
+        plan.contract(amps, i * sb, (i + 1) * sb, stream=stream)
+        state["i"] = i + 1
+
+    ms = time_steps(torch, batch, nb, stream)
+    per_slice_ms = ms / (nb * sb)
+    flops_slice = pi["tcc_per_slice"]
+    # the error of the chosen precision against complex64 on the same slices.  With fSim at
+    # theta = pi/2 and no final single-qubit layer most slices vanish (a closed qubit's projector
+    # after its last swap-like fSim fixes the partner's input bond); candidates that no tensor
+    # forces to zero come from a seeded search, the first two that contribute are compared.
+    cplan = tn.Plan(tnet, path, sliced, mode="c64", max_slices_in_flight=2)
+    part = torch.zeros_like(amps)
+    ref = np.zeros(amps.numel(), dtype=np.complex128)
+    got = np.zeros_like(ref)
+    picks = []
+    for s in supported_slices(net, sliced, SA_SEED, 8):
+        part.zero_()
+        cplan.contract(part, s, s + 1, stream=stream)
+        torch.cuda.synchronize()
+        r = part.cpu().numpy()
+        if np.linalg.norm(r) == 0:
+            continue
+        part.zero_()
+        plan.contract(part, s, s + 1, stream=stream)
+        torch.cuda.synchronize()
+        ref += r
+        got += part.cpu().numpy()
+        picks.append(s)
+        if len(picks) == 2:
+            break
+    plan.close()
+    cplan.close()
+    tnet.close()
+    err = O.rel_l2(got, ref) if np.linalg.norm(ref) > 0 else None
+    return {"metric": "53-qubit sliced contraction: s per 2^12-amplitude batch (extrapolated)",
+            "value": per_slice_ms / 1e3 * pi["num_slices"], "unit": "s",
+            "higher_is_better": False, "mode": args.mode,
+            "config": {"workload": "sycamore53_6x9_c16_open12", "qubits": 53, "cycles": 16,
+                       "open_qubits": 12, "sliced_bonds": len(sliced),
+                       "slices": pi["num_slices"], "slices_in_flight": sb,
+                       "max_intermediate_log2": pi["max_log2_size"],
+                       "flops_per_slice": flops_slice,
+                       "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
+                       "path": "annealed from 100 random greedy trees x 16 chains, "
+                               "dynamic slicing to 2^30", "optimiser_s": opt_s},
+            "timed_slices": nb * sb, "ms_per_slice": per_slice_ms,
+            "effective_tflops": flops_slice / (per_slice_ms / 1e3) / 1e12,
+            "rel_l2_vs_c64_on_2_slices": err, "compared_slices": [int(s) for s in picks]}
+
+
 def measure_sparse(args, dev, stream):
     """Sparse-state contraction of 4096 seeded bitstrings of the 24-qubit all-open circuit along
     an annealed path; time per batch and the error against the host state vector."""
@@ -783,6 +942,11 @@ def main():
         return
     if args.step_profile:
         run_step_profile(args)
+        return
+    if args.sycamore53:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(run_sycamore53(args)))
         return
     if args.sparse_only:
         import torch

@@ -332,71 +332,92 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // Thin steps (the low-intensity contractions of App. A.2): C[m, n] = sum_k A[m, k] B[n, k] with
 // few columns (N = NT <= 16) and a short contraction (K <= 64, summed in one FP32 chain per
 // output: at most 64 terms).  One thread owns one row m of A and all NT outputs of that row.  B is held in shared memory as [K][NT] and read as broadcast
-// 16-byte pairs; the block's 256 rows of A are staged through shared memory in chunks of 16 of
-// K with coalesced 16-byte loads.  A step whose small operand is A runs with the roles swapped
-// (the complex product commutes).  The tile (256 x NT) is staged and written in C's order with
-// 8 consecutive elements per thread, as in the other epilogues.
+// 16-byte pairs.  For K <= 8 (KS = K) each thread loads its own row of A straight into registers
+// (K * 8 contiguous bytes; a warp reads one contiguous span) and the block holds only the output
+// stage, so more blocks fit on an SM and more loads are in flight; for longer K (KS = 0) the
+// block's 256 rows of A are staged through shared memory in chunks of 16 of K with coalesced
+// 16-byte loads.  A step whose small operand is A runs with the roles swapped (the complex
+// product commutes).  The tile (256 x NT) is staged and written in C's order with 8 consecutive
+// elements per thread, as in the other epilogues.
 constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
 
-template <int NT>
-__global__ void __launch_bounds__(256, 3) k_gemm_thin(GemmDesc d) {
-    __shared__ __align__(16) float2 sA[kThinRows * kThinLd];
-    __shared__ __align__(16) float2 sB[64 * (NT < 2 ? 2 : NT)];
+template <int NT, int KS>
+__global__ void __launch_bounds__(256, (KS && NT < 16) ? 4 : 3) k_gemm_thin(GemmDesc d) {
     constexpr int NB = NT < 2 ? 2 : NT;  // row stride of sB (pairs stay 16-byte aligned)
+    constexpr int LD = NT + 1;           // row stride of the output stage
+    __shared__ __align__(16) float2 sA[KS ? kThinRows * LD : kThinRows * kThinLd];
+    __shared__ __align__(16) float2 sB[(KS ? KS : 64) * NB];
     const int64_t s = blockIdx.y;
     const int64_t m0 = (int64_t)blockIdx.x * kThinRows;
-    const int K = 1 << d.lk;
+    const int K = KS ? KS : 1 << d.lk;
     const float2 *A = d.A + s * d.sA + m0 * K;
     const float2 *B = d.B + s * d.sB;
     const int tid = threadIdx.x;
-    for (int e = tid; e < NT * K; e += 256) {
-        const int n = e / K, k = e % K;
-        sB[k * NB + n] = B[e];
-    }
     float cr[NT], ci[NT];
 #pragma unroll
     for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
-    for (int kc = 0; kc < K; kc += kThinKC) {
-        const int kw = K - kc < kThinKC ? K - kc : kThinKC;  // a power of two >= 2
-        const int hp = kw >> 1;                               // 16-byte pairs per row
-        __syncthreads();
-        for (int e = tid; e < kThinRows * hp; e += 256) {
-            const int r = e / hp, q = e % hp;
-            const float4 v = *reinterpret_cast<const float4 *>(A + (int64_t)r * K + kc + 2 * q);
-            sA[r * kThinLd + 2 * q] = make_float2(v.x, v.y);
-            sA[r * kThinLd + 2 * q + 1] = make_float2(v.z, v.w);
-        }
-        __syncthreads();
-        for (int k = 0; k < kw; ++k) {
-            const float2 a = sA[tid * kThinLd + k];
-            const float2 *bk = sB + (kc + k) * NB;
+    auto mac = [&](const float2 a, const float2 *bk) {
 #pragma unroll
-            for (int n = 0; n < NT; n += 2) {
-                float2 b0, b1;
-                if (NT >= 2) {
-                    const float4 bb = *reinterpret_cast<const float4 *>(bk + n);
-                    b0 = make_float2(bb.x, bb.y);
-                    b1 = make_float2(bb.z, bb.w);
-                } else {
-                    b0 = bk[0];
-                    b1 = b0;
-                }
-                cr[n] = fmaf(a.x, b0.x, cr[n]);
-                cr[n] = fmaf(-a.y, b0.y, cr[n]);
-                ci[n] = fmaf(a.x, b0.y, ci[n]);
-                ci[n] = fmaf(a.y, b0.x, ci[n]);
-                if (n + 1 < NT) {
-                    cr[n + 1] = fmaf(a.x, b1.x, cr[n + 1]);
-                    cr[n + 1] = fmaf(-a.y, b1.y, cr[n + 1]);
-                    ci[n + 1] = fmaf(a.x, b1.y, ci[n + 1]);
-                    ci[n + 1] = fmaf(a.y, b1.x, ci[n + 1]);
-                }
+        for (int n = 0; n < NT; n += 2) {
+            float2 b0, b1;
+            if (NT >= 2) {
+                const float4 bb = *reinterpret_cast<const float4 *>(bk + n);
+                b0 = make_float2(bb.x, bb.y);
+                b1 = make_float2(bb.z, bb.w);
+            } else {
+                b0 = bk[0];
+                b1 = b0;
+            }
+            cr[n] = fmaf(a.x, b0.x, cr[n]);
+            cr[n] = fmaf(-a.y, b0.y, cr[n]);
+            ci[n] = fmaf(a.x, b0.y, ci[n]);
+            ci[n] = fmaf(a.y, b0.x, ci[n]);
+            if (n + 1 < NT) {
+                cr[n + 1] = fmaf(a.x, b1.x, cr[n + 1]);
+                cr[n + 1] = fmaf(-a.y, b1.y, cr[n + 1]);
+                ci[n + 1] = fmaf(a.x, b1.y, ci[n + 1]);
+                ci[n + 1] = fmaf(a.y, b1.x, ci[n + 1]);
             }
         }
+    };
+    if constexpr (KS != 0) {
+        float2 a[KS];
+        const float4 *Ar = reinterpret_cast<const float4 *>(A + (int64_t)tid * KS);
+#pragma unroll
+        for (int q = 0; q < KS / 2; ++q) {
+            const float4 v = Ar[q];
+            a[2 * q] = make_float2(v.x, v.y);
+            a[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        for (int e = tid; e < NT * KS; e += 256) {
+            const int n = e / KS, k = e % KS;
+            sB[k * NB + n] = B[e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KS; ++k) mac(a[k], sB + k * NB);
+    } else {
+        for (int e = tid; e < NT * K; e += 256) {
+            const int n = e / K, k = e % K;
+            sB[k * NB + n] = B[e];
+        }
+        for (int kc = 0; kc < K; kc += kThinKC) {
+            const int kw = K - kc < kThinKC ? K - kc : kThinKC;  // a power of two >= 2
+            const int hp = kw >> 1;                               // 16-byte pairs per row
+            __syncthreads();
+            for (int e = tid; e < kThinRows * hp; e += 256) {
+                const int r = e / hp, q = e % hp;
+                const float4 v =
+                    *reinterpret_cast<const float4 *>(A + (int64_t)r * K + kc + 2 * q);
+                sA[r * kThinLd + 2 * q] = make_float2(v.x, v.y);
+                sA[r * kThinLd + 2 * q + 1] = make_float2(v.z, v.w);
+            }
+            __syncthreads();
+            for (int k = 0; k < kw; ++k) mac(sA[tid * kThinLd + k], sB + (kc + k) * NB);
+        }
+        __syncthreads();  // the stage below reuses sA
     }
-    __syncthreads();
     // stage rows with stride NT + 1 and write 8 consecutive elements of C per task
-    constexpr int LD = NT + 1;
     float2 *stage = sA;
 #pragma unroll
     for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
@@ -819,17 +840,27 @@ int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {
     return splits;
 }
 
+template <int NT>
+void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
+    switch (d.lk) {
+        case 1: k_gemm_thin<NT, 2><<<grid, 256, 0, st>>>(d); break;
+        case 2: k_gemm_thin<NT, 4><<<grid, 256, 0, st>>>(d); break;
+        case 3: k_gemm_thin<NT, 8><<<grid, 256, 0, st>>>(d); break;
+        default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
+    }
+}
+
 cudaError_t launch_gemm_thin(const GemmDesc &d, int64_t slices, cudaStream_t st) {
     if (d.lm < 8 || d.ln < 0 || d.ln > 4 || d.lk < 1 || d.lk > 6 || slices > 65535 ||
         d.tile_bits != 8 + d.ln || d.tile_bits < 3 || d.planar_out)
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)((1ll << d.lm) / kThinRows), (unsigned)slices);
     switch (d.ln) {
-        case 0: k_gemm_thin<1><<<grid, 256, 0, st>>>(d); break;
-        case 1: k_gemm_thin<2><<<grid, 256, 0, st>>>(d); break;
-        case 2: k_gemm_thin<4><<<grid, 256, 0, st>>>(d); break;
-        case 3: k_gemm_thin<8><<<grid, 256, 0, st>>>(d); break;
-        default: k_gemm_thin<16><<<grid, 256, 0, st>>>(d); break;
+        case 0: launch_thin_n<1>(d, grid, st); break;
+        case 1: launch_thin_n<2>(d, grid, st); break;
+        case 2: launch_thin_n<4>(d, grid, st); break;
+        case 3: launch_thin_n<8>(d, grid, st); break;
+        default: launch_thin_n<16>(d, grid, st); break;
     }
     return cudaGetLastError();
 }

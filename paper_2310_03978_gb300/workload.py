@@ -538,6 +538,19 @@ def sycamore_workload(name, rows, cols, cycles, k_open, num_sliced, config_id, r
     return Workload(name, circ, net, path, sliced)
 
 
+def sycamore53_network(cycles=16, k_open=12, config_id=4):
+    """The 53-qubit Sycamore-shaped circuit (6x9 grid without site (5, 8)), ``cycles`` cycles,
+    the last ``k_open`` qubits open and the others closed on seeded bits.  No path: the greedy
+    path is far too costly here; the caller anneals one.  Returns (circuit, network)."""
+    seed = BASE_SEED + config_id
+    circ = random_circuit(6, 9, cycles, seed, removed=((5, 8),))
+    n = circ.n_qubits
+    rng = Xoshiro256ss(seed ^ 0x5EED)
+    open_q = list(range(n - k_open, n))
+    closed = {q: rng.below(2) for q in range(n - k_open)}
+    return circ, build_network(circ, open_q, closed)
+
+
 def sparse_state_workload(rows=4, cols=6, cycles=12, num_samples=4096, config_id=9):
     """Sparse-state input (Sec. 3.3): a seeded Sycamore-shaped circuit with every qubit open and
     ``num_samples`` seeded uniform bitstrings standing in for sampled ones (column j = qubit j,

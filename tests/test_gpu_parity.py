@@ -220,10 +220,11 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
 
 
 @pytest.mark.parametrize("shape", [(12, 4, 4), (10, 2, 6), (4, 11, 3), (13, 0, 2), (11, 3, 1),
-                                   (1, 12, 5)])
+                                   (1, 12, 5), (14, 2, 2), (12, 1, 3), (10, 4, 1)])
 def test_thin_steps_stream_kernel(tn, shape):
     # a short contraction of a large operand with one of at most 16 free elements: one thread
-    # per row of the large operand (the small one may be either side); 2 slices in flight too
+    # per row of the large operand (the small one may be either side); k <= 8 loads rows into
+    # registers, longer k stages them in shared memory; 2 slices in flight too
     rng = np.random.default_rng(500 + 3 * shape[0] + 5 * shape[1] + shape[2])
     tensors, labels, out = single_step(rng, *shape)
     ref = O.contract(tensors, labels, out, [(0, 1)])
