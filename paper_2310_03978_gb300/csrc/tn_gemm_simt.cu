@@ -331,31 +331,31 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 
 // Thin steps (the low-intensity contractions of App. A.2): C[m, n] = sum_k A[m, k] B[n, k] with
 // few columns (N = NT <= 16) and a short contraction (K <= 64, summed in one FP32 chain per
-// output: at most 64 terms).  One thread owns one row m of A and all NT outputs of that row.  B is held in shared memory as [K][NT] and read as broadcast
-// 16-byte pairs.  For K <= 8 (KS = K) each thread loads its own row of A straight into registers
-// (K * 8 contiguous bytes; a warp reads one contiguous span) and the block holds only the output
-// stage, so more blocks fit on an SM and more loads are in flight; for longer K (KS = 0) the
-// block's 256 rows of A are staged through shared memory in chunks of 16 of K with coalesced
+// output: at most 64 terms).  One thread owns one row m of A and all NT outputs of that row; a
+// tile is 256 rows.  B is held in shared memory as [K][NT] and read as broadcast 16-byte pairs.
+// For K <= 8 (KS = K) the grid holds as many blocks as fit on the GPU, each walking its slice's
+// tiles with a stride: a thread loads its own row of A straight into registers (K * 8 contiguous
+// bytes; a warp reads one contiguous span) and fetches its row of the next tile before it stores
+// the current one, so loads stay in flight during the store phase.  For longer K (KS = 0) a block
+// takes one tile and stages its rows through shared memory in chunks of 16 of K with coalesced
 // 16-byte loads.  A step whose small operand is A runs with the roles swapped (the complex
-// product commutes).  The tile (256 x NT) is staged and written in C's order with 8 consecutive
+// product commutes).  Each tile (256 x NT) is staged and written in C's order with 8 consecutive
 // elements per thread, as in the other epilogues.
 constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
+constexpr int thin_min_blocks(int nt, int ks) { return (ks && nt < 16) ? 4 : 3; }
 
 template <int NT, int KS>
-__global__ void __launch_bounds__(256, (KS && NT < 16) ? 4 : 3) k_gemm_thin(GemmDesc d) {
+__global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(GemmDesc d) {
     constexpr int NB = NT < 2 ? 2 : NT;  // row stride of sB (pairs stay 16-byte aligned)
     constexpr int LD = NT + 1;           // row stride of the output stage
     __shared__ __align__(16) float2 sA[KS ? kThinRows * LD : kThinRows * kThinLd];
     __shared__ __align__(16) float2 sB[(KS ? KS : 64) * NB];
     const int64_t s = blockIdx.y;
-    const int64_t m0 = (int64_t)blockIdx.x * kThinRows;
     const int K = KS ? KS : 1 << d.lk;
-    const float2 *A = d.A + s * d.sA + m0 * K;
+    const float2 *As = d.A + s * d.sA;
     const float2 *B = d.B + s * d.sB;
     const int tid = threadIdx.x;
     float cr[NT], ci[NT];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
     auto mac = [&](const float2 a, const float2 *bk) {
 #pragma unroll
         for (int n = 0; n < NT; n += 2) {
@@ -380,23 +380,79 @@ __global__ void __launch_bounds__(256, (KS && NT < 16) ? 4 : 3) k_gemm_thin(Gemm
             }
         }
     };
-    if constexpr (KS != 0) {
-        float2 a[KS];
-        const float4 *Ar = reinterpret_cast<const float4 *>(A + (int64_t)tid * KS);
+    // output: stage rows with stride NT + 1, then write 8 consecutive elements of C per task
+    float2 *stage = sA;
+    auto soff = [&](int sq) { return (sq & 128) ? (LD << (sq & 127)) : (1 << sq); };
+    int w8[8];
+    {
+        const int d0 = soff(d.tb_src[0]), d1 = soff(d.tb_src[1]), d2 = soff(d.tb_src[2]);
 #pragma unroll
-        for (int q = 0; q < KS / 2; ++q) {
-            const float4 v = Ar[q];
-            a[2 * q] = make_float2(v.x, v.y);
-            a[2 * q + 1] = make_float2(v.z, v.w);
+        for (int j = 0; j < 8; ++j)
+            w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
+    }
+    const int nb = d.tile_bits;
+    float amx = 0.f;
+    auto emit = [&](int64_t m0) {  // callers synchronise before the stage is written
+#pragma unroll
+        for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
+        __syncthreads();
+        float2 *C = d.C + s * d.sC + deposit((uint64_t)m0, d.lm, d.posC_m);
+        for (int task = tid; task < (1 << (nb - 3)); task += 256) {
+            int w = 0;
+            uint64_t off = 0;
+            for (int q = 3; q < nb; ++q)
+                if ((task >> (q - 3)) & 1) {
+                    w += soff(d.tb_src[q]);
+                    off |= 1ull << d.tb_pos[q];
+                }
+            float2 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = stage[w + w8[j]];
+                amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+            }
+            float4 *c4 = reinterpret_cast<float4 *>(C + off);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
         }
+    };
+    if constexpr (KS != 0) {
+        const int64_t tiles = (1ll << d.lm) / kThinRows;
+        float2 a[KS], an[KS];
+        auto fetch = [&](float2 *dst, int64_t t) {
+            const float4 *Ar =
+                reinterpret_cast<const float4 *>(As + (t * kThinRows + tid) * KS);
+#pragma unroll
+            for (int q = 0; q < KS / 2; ++q) {
+                const float4 v = Ar[q];
+                dst[2 * q] = make_float2(v.x, v.y);
+                dst[2 * q + 1] = make_float2(v.z, v.w);
+            }
+        };
+        int64_t t = blockIdx.x;  // < tiles: the launch makes at most one block per tile
+        fetch(a, t);
         for (int e = tid; e < NT * KS; e += 256) {
             const int n = e / KS, k = e % KS;
             sB[k * NB + n] = B[e];
         }
         __syncthreads();
+        for (; t < tiles; t += gridDim.x) {
+            if (t + gridDim.x < tiles) fetch(an, t + gridDim.x);
 #pragma unroll
-        for (int k = 0; k < KS; ++k) mac(a[k], sB + k * NB);
+            for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
+#pragma unroll
+            for (int k = 0; k < KS; ++k) mac(a[k], sB + k * NB);
+            emit(t * kThinRows);
+            __syncthreads();  // the stage is read before the next tile writes it
+#pragma unroll
+            for (int k = 0; k < KS; ++k) a[k] = an[k];
+        }
     } else {
+        const int64_t m0 = (int64_t)blockIdx.x * kThinRows;
+        const float2 *A = As + m0 * K;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
         for (int e = tid; e < NT * K; e += 256) {
             const int n = e / K, k = e % K;
             sB[k * NB + n] = B[e];
@@ -415,46 +471,11 @@ __global__ void __launch_bounds__(256, (KS && NT < 16) ? 4 : 3) k_gemm_thin(Gemm
             __syncthreads();
             for (int k = 0; k < kw; ++k) mac(sA[tid * kThinLd + k], sB + (kc + k) * NB);
         }
-        __syncthreads();  // the stage below reuses sA
-    }
-    // stage rows with stride NT + 1 and write 8 consecutive elements of C per task
-    float2 *stage = sA;
-#pragma unroll
-    for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
-    __syncthreads();
-    auto soff = [&](int sq) { return (sq & 128) ? (LD << (sq & 127)) : (1 << sq); };
-    int w8[8];
-    {
-        const int d0 = soff(d.tb_src[0]), d1 = soff(d.tb_src[1]), d2 = soff(d.tb_src[2]);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
-    }
-    const int nb = d.tile_bits;
-    float2 *C = d.C + s * d.sC + deposit((uint64_t)m0, d.lm, d.posC_m);
-    float amx = 0.f;
-    for (int task = tid; task < (1 << (nb - 3)); task += 256) {
-        int w = 0;
-        uint64_t off = 0;
-        for (int q = 3; q < nb; ++q)
-            if ((task >> (q - 3)) & 1) {
-                w += soff(d.tb_src[q]);
-                off |= 1ull << d.tb_pos[q];
-            }
-        float2 v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            v[j] = stage[w + w8[j]];
-            amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
-        }
-        float4 *c4 = reinterpret_cast<float4 *>(C + off);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+        __syncthreads();  // the stage reuses sA
+        emit(m0);
     }
     if (d.amax_out) amax_publish(d.amax_out + s, amx);
 }
-
 
 // Thin sparse-state step (at most 16 columns): thread per (configuration c, row m) holding all
 // NN outputs of its row; B[gB[c]] is staged in shared memory 64 values of k at a time, so each
@@ -840,12 +861,31 @@ int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {
     return splits;
 }
 
+// Blocks per slice for the tile-walking variant: the blocks its launch bounds guarantee on every
+// SM, spread over the slices, at most one per tile.  (Only attribute queries here: the launch may
+// be under stream capture.)
+template <int NT, int KS>
+void launch_thin_walk(const GemmDesc &d, dim3 grid, cudaStream_t st) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            sms = v;
+        if (sms <= 0) sms = 152;
+    }
+    const int64_t resident = (int64_t)sms * thin_min_blocks(NT, KS);
+    const int64_t per_slice = (resident + grid.y - 1) / grid.y;
+    if (per_slice < (int64_t)grid.x) grid.x = (unsigned)per_slice;
+    k_gemm_thin<NT, KS><<<grid, 256, 0, st>>>(d);
+}
+
 template <int NT>
 void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
     switch (d.lk) {
-        case 1: k_gemm_thin<NT, 2><<<grid, 256, 0, st>>>(d); break;
-        case 2: k_gemm_thin<NT, 4><<<grid, 256, 0, st>>>(d); break;
-        case 3: k_gemm_thin<NT, 8><<<grid, 256, 0, st>>>(d); break;
+        case 1: launch_thin_walk<NT, 2>(d, grid, st); break;
+        case 2: launch_thin_walk<NT, 4>(d, grid, st); break;
+        case 3: launch_thin_walk<NT, 8>(d, grid, st); break;
         default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
     }
 }

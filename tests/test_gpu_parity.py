@@ -220,7 +220,8 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
 
 
 @pytest.mark.parametrize("shape", [(12, 4, 4), (10, 2, 6), (4, 11, 3), (13, 0, 2), (11, 3, 1),
-                                   (1, 12, 5), (14, 2, 2), (12, 1, 3), (10, 4, 1)])
+                                   (1, 12, 5), (14, 2, 2), (12, 1, 3), (10, 4, 1), (18, 2, 2),
+                                   (3, 17, 1)])
 def test_thin_steps_stream_kernel(tn, shape):
     # a short contraction of a large operand with one of at most 16 free elements: one thread
     # per row of the large operand (the small one may be either side); k <= 8 loads rows into
