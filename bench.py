@@ -76,6 +76,10 @@ def parse_args():
                     help="time this many batches of slices of the 53-qubit 16-cycle circuit "
                          "(annealed path, slices capped at 2^30 elements) and extrapolate to "
                          "all slices; prints its own JSON line")
+    ap.add_argument("--sycamore53-modes", default="",
+                    help="comma-separated precision modes for --sycamore53 (default: --mode)")
+    ap.add_argument("--sycamore53-compare", type=int, default=8,
+                    help="contributing slices compared with complex64 under --sycamore53")
     ap.add_argument("--sparse-only", action="store_true",
                     help="run only the sparse-state measurement and print its JSON line")
     ap.add_argument("--sparse-steps", type=int, default=3,
@@ -614,8 +618,9 @@ def supported_slices(net, sliced, seed, count):
 def run_sycamore53(args):
     """53-qubit, 16-cycle Sycamore-shaped circuit, 2^12 amplitudes (12 open qubits): a path
     annealed from random greedy trees with the largest intermediate bounded by slicing to 2^30
-    elements; `args.sycamore53` batches of slices timed, the time per slice extrapolated to all
-    slices; the first two slices also contracted on the complex64 path for the error."""
+    elements; per precision mode, `args.sycamore53` batches of slices timed and the time per
+    slice extrapolated to all slices, and the amplitudes of up to `args.sycamore53_compare`
+    contributing slices compared with the complex64 path.  Yields one JSON record per mode."""
     import torch
     from oracle import oracle as O
     from paper_2310_03978_gb300 import tn, workload as W
@@ -632,67 +637,73 @@ def run_sycamore53(args):
     opt_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     tnet = tn.Network(net.tensors, net.labels, net.open_labels)
-    plan = tn.Plan(tnet, path, sliced, mode=args.mode, use_graph=True, autotune=True,
-                   mixed_topk=args.mixed_topk)
-    pi = plan.info()
-    sb = pi["slices_in_flight"]
-    amps = torch.zeros(1 << len(net.open_labels), dtype=torch.complex128, device="cuda")
-    for w in range(2):  # the first batch autotunes
-        plan.contract(amps, w * sb, (w + 1) * sb, stream=stream)
-    torch.cuda.synchronize()
-    nb = max(1, args.sycamore53)
-    state = {"i": 2}
+    nout = 1 << len(net.open_labels)
+    part = torch.zeros(nout, dtype=torch.complex128, device="cuda")
 
-    def batch():
-        i = state["i"]
-        plan.contract(amps, i * sb, (i + 1) * sb, stream=stream)
-        state["i"] = i + 1
-
-    ms = time_steps(torch, batch, nb, stream)
-    per_slice_ms = ms / (nb * sb)
-    flops_slice = pi["tcc_per_slice"]
-    # the error of the chosen precision against complex64 on the same slices.  With fSim at
-    # theta = pi/2 and no final single-qubit layer most slices vanish (a closed qubit's projector
-    # after its last swap-like fSim fixes the partner's input bond); candidates that no tensor
-    # forces to zero come from a seeded search, the first two that contribute are compared.
-    cplan = tn.Plan(tnet, path, sliced, mode="c64", max_slices_in_flight=2)
-    part = torch.zeros_like(amps)
-    ref = np.zeros(amps.numel(), dtype=np.complex128)
-    got = np.zeros_like(ref)
-    picks = []
-    for s in supported_slices(net, sliced, SA_SEED, 8):
-        part.zero_()
-        cplan.contract(part, s, s + 1, stream=stream)
-        torch.cuda.synchronize()
-        r = part.cpu().numpy()
-        if np.linalg.norm(r) == 0:
-            continue
+    def one_slice(plan, s):
         part.zero_()
         plan.contract(part, s, s + 1, stream=stream)
         torch.cuda.synchronize()
-        ref += r
-        got += part.cpu().numpy()
-        picks.append(s)
-        if len(picks) == 2:
+        return part.cpu().numpy()
+
+    # complex64 amplitudes of contributing slices.  With fSim at theta = pi/2 and no final
+    # single-qubit layer most slices vanish (a closed qubit's projector after its last swap-like
+    # fSim fixes the partner's input bond); candidates that no tensor forces to zero come from a
+    # seeded search, and the first ones whose complex64 result is nonzero are kept.
+    ncmp = max(0, args.sycamore53_compare)
+    cplan = tn.Plan(tnet, path, sliced, mode="c64", max_slices_in_flight=1)
+    picks, refs = [], []
+    for s in supported_slices(net, sliced, SA_SEED, 3 * ncmp):
+        if len(picks) == ncmp:
             break
-    plan.close()
+        r = one_slice(cplan, s)
+        if np.linalg.norm(r) > 0:
+            picks.append(s)
+            refs.append(r)
     cplan.close()
+    ref = np.sum(refs, axis=0) if refs else np.zeros(nout, dtype=np.complex128)
+    modes = [m for m in (args.sycamore53_modes or args.mode).split(",") if m]
+    for mode in modes:
+        plan = tn.Plan(tnet, path, sliced, mode=mode, use_graph=True, autotune=True,
+                       mixed_topk=args.mixed_topk)
+        pi = plan.info()
+        sb = pi["slices_in_flight"]
+        amps = torch.zeros(nout, dtype=torch.complex128, device="cuda")
+        for w in range(2):  # the first batch autotunes
+            plan.contract(amps, w * sb, (w + 1) * sb, stream=stream)
+        torch.cuda.synchronize()
+        nb = max(1, args.sycamore53)
+        state = {"i": 2}
+
+        def batch():
+            i = state["i"]
+            plan.contract(amps, i * sb, (i + 1) * sb, stream=stream)
+            state["i"] = i + 1
+
+        ms = time_steps(torch, batch, nb, stream)
+        per_slice_ms = ms / (nb * sb)
+        flops_slice = pi["tcc_per_slice"]
+        got = np.sum([one_slice(plan, s) for s in picks], axis=0) if picks else ref
+        per = [O.rel_l2(one_slice(plan, s), r) for s, r in zip(picks[:2], refs[:2])]
+        plan.close()
+        err = O.rel_l2(got, ref) if np.linalg.norm(ref) > 0 else None
+        yield {"metric": "53-qubit sliced contraction: s per 2^12-amplitude batch (extrapolated)",
+               "value": per_slice_ms / 1e3 * pi["num_slices"], "unit": "s",
+               "higher_is_better": False, "mode": mode,
+               "config": {"workload": "sycamore53_6x9_c16_open12", "qubits": 53, "cycles": 16,
+                          "open_qubits": 12, "sliced_bonds": len(sliced),
+                          "slices": pi["num_slices"], "slices_in_flight": sb,
+                          "max_intermediate_log2": pi["max_log2_size"],
+                          "workspace_bytes": pi["workspace_bytes"],
+                          "flops_per_slice": flops_slice,
+                          "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
+                          "path": "annealed from 100 random greedy trees x 16 chains, "
+                                  "dynamic slicing to 2^30", "optimiser_s": opt_s},
+               "timed_slices": nb * sb, "ms_per_slice": per_slice_ms,
+               "effective_tflops": flops_slice / (per_slice_ms / 1e3) / 1e12,
+               "rel_l2_vs_c64": err, "rel_l2_vs_c64_first_slices": per,
+               "compared_slices": [int(s) for s in picks]}
     tnet.close()
-    err = O.rel_l2(got, ref) if np.linalg.norm(ref) > 0 else None
-    return {"metric": "53-qubit sliced contraction: s per 2^12-amplitude batch (extrapolated)",
-            "value": per_slice_ms / 1e3 * pi["num_slices"], "unit": "s",
-            "higher_is_better": False, "mode": args.mode,
-            "config": {"workload": "sycamore53_6x9_c16_open12", "qubits": 53, "cycles": 16,
-                       "open_qubits": 12, "sliced_bonds": len(sliced),
-                       "slices": pi["num_slices"], "slices_in_flight": sb,
-                       "max_intermediate_log2": pi["max_log2_size"],
-                       "flops_per_slice": flops_slice,
-                       "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
-                       "path": "annealed from 100 random greedy trees x 16 chains, "
-                               "dynamic slicing to 2^30", "optimiser_s": opt_s},
-            "timed_slices": nb * sb, "ms_per_slice": per_slice_ms,
-            "effective_tflops": flops_slice / (per_slice_ms / 1e3) / 1e12,
-            "rel_l2_vs_c64_on_2_slices": err, "compared_slices": [int(s) for s in picks]}
 
 
 def measure_sparse(args, dev, stream):
@@ -946,7 +957,8 @@ def main():
     if args.sycamore53:
         import torch
         torch.cuda.set_device(local_rank)
-        print(json.dumps(run_sycamore53(args)))
+        for rec in run_sycamore53(args):
+            print(json.dumps(rec), flush=True)
         return
     if args.sparse_only:
         import torch
