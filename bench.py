@@ -544,15 +544,14 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
-def supported_slices(net, sliced, seed, count):
-    """Up to ``count`` distinct slice ids (bit j = value of sliced[j]) on which no tensor, alone
-    or with its neighbouring vectors absorbed, is zero once restricted to its sliced bonds (entries
-    below 1e-12 of its largest count as zero): a seeded depth-first search over the bits with the
-    values tried in random order."""
+def slice_constraints(net, sliced):
+    """Necessary conditions for a slice to contribute: for every tensor, alone and (for a gate)
+    with its neighbouring vectors (|0> inputs, <b| projectors) absorbed, the value tuples of its
+    sliced bonds on which it is not identically zero (entries below 1e-12 of its largest count as
+    zero).  Returns [(bit positions in the slice id, allowed value tuples)] for the tensors that
+    exclude some tuple.  A projector after a swap-like fSim fixes the partner's input bond."""
     import itertools
     pos = {l: j for j, l in enumerate(sliced)}
-    # every gate also with its neighbouring vectors (|0> inputs, <b| projectors) absorbed: a
-    # projector after a swap-like fSim fixes the partner's input bond
     vec = {ls[0]: t for t, ls in zip(net.tensors, net.labels) if len(ls) == 1}
     pieces = list(zip(net.tensors, net.labels))
     for t, ls in zip(net.tensors, net.labels):
@@ -561,13 +560,11 @@ def supported_slices(net, sliced, seed, count):
         ls = list(ls)
         for l in list(ls):
             if l in vec:
-                t = np.moveaxis(np.tensordot(t, vec[l], axes=([ls.index(l)], [0])), -1, -1)
+                t = np.tensordot(t, vec[l], axes=([ls.index(l)], [0]))
                 ls.remove(l)
         pieces.append((t, ls))
     cons = []
     for t, ls in pieces:
-        if not len(ls):
-            continue
         axes = [i for i, l in enumerate(ls) if l in pos]
         if not axes:
             continue
@@ -581,6 +578,19 @@ def supported_slices(net, sliced, seed, count):
                 ok.add(vals)
         if len(ok) < 1 << len(axes):
             cons.append(([pos[ls[a]] for a in axes], ok))
+    return cons
+
+
+def slice_supported(cons, s):
+    """Whether slice id ``s`` meets every condition of ``slice_constraints``."""
+    return all(tuple((s >> b) & 1 for b in bits) in ok for bits, ok in cons)
+
+
+def supported_slices(net, sliced, seed, count):
+    """Up to ``count`` distinct slice ids (bit j = value of sliced[j]) that meet
+    ``slice_constraints``: a seeded depth-first search over the bits with the values tried in
+    random order."""
+    cons = slice_constraints(net, sliced)
     by_bit = [[] for _ in sliced]
     for c in cons:
         for b in c[0]:
