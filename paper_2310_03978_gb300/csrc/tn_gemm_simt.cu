@@ -333,7 +333,7 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // few columns (N = NT <= 16) and a short contraction (K <= 64, summed in one FP32 chain per
 // output: at most 64 terms).  One thread owns one row m of A and all NT outputs of that row; a
 // tile is 256 rows.  B is held in shared memory as [K][NT] and read as broadcast 16-byte pairs.
-// For K <= 8 (KS = K) the grid holds as many blocks as fit on the GPU, each walking its slice's
+// For K <= 8 and NT <= 8 (KS = K) the grid holds as many blocks as fit on the GPU, each walking its slice's
 // tiles with a stride: a thread loads its own row of A straight into registers (K * 8 contiguous
 // bytes; a warp reads one contiguous span) and fetches its row of the next tile before it stores
 // the current one, so loads stay in flight during the store phase.  For longer K (KS = 0) a block
@@ -342,7 +342,7 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // product commutes).  Each tile (256 x NT) is staged and written in C's order with 8 consecutive
 // elements per thread, as in the other epilogues.
 constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
-constexpr int thin_min_blocks(int nt, int ks) { return (ks && nt < 16) ? 4 : 3; }
+constexpr int thin_min_blocks(int nt, int ks) { return (ks && nt < 8) ? 4 : 3; }  // nt <= 8 when ks > 0
 
 template <int NT, int KS>
 __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(GemmDesc d) {
@@ -390,28 +390,38 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         for (int j = 0; j < 8; ++j)
             w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
     }
-    const int nb = d.tile_bits;
+    // a tile has 256 * NT elements (tile_bits = 8 + log2 NT): 32 * NT tasks of 8, at most two
+    // per thread; their stage and C offsets are the same for every tile, so they are set once
+    constexpr int TASKS = kThinRows * NT / 8, TPT = (TASKS + 255) / 256;
+    int wt[TPT];
+    uint64_t ot[TPT];
+#pragma unroll
+    for (int i = 0; i < TPT; ++i) {
+        const int task = tid + 256 * i;
+        wt[i] = 0;
+        ot[i] = 0;
+        for (int q = 3; q < d.tile_bits; ++q)
+            if ((task >> (q - 3)) & 1) {
+                wt[i] += soff(d.tb_src[q]);
+                ot[i] |= 1ull << d.tb_pos[q];
+            }
+    }
     float amx = 0.f;
     auto emit = [&](int64_t m0) {  // callers synchronise before the stage is written
 #pragma unroll
         for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
         __syncthreads();
         float2 *C = d.C + s * d.sC + deposit((uint64_t)m0, d.lm, d.posC_m);
-        for (int task = tid; task < (1 << (nb - 3)); task += 256) {
-            int w = 0;
-            uint64_t off = 0;
-            for (int q = 3; q < nb; ++q)
-                if ((task >> (q - 3)) & 1) {
-                    w += soff(d.tb_src[q]);
-                    off |= 1ull << d.tb_pos[q];
-                }
+#pragma unroll
+        for (int i = 0; i < TPT; ++i) {
+            if (TASKS % 256 != 0 && tid + 256 * i >= TASKS) break;
             float2 v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                v[j] = stage[w + w8[j]];
+                v[j] = stage[wt[i] + w8[j]];
                 amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
             }
-            float4 *c4 = reinterpret_cast<float4 *>(C + off);
+            float4 *c4 = reinterpret_cast<float4 *>(C + ot[i]);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
@@ -882,11 +892,15 @@ void launch_thin_walk(const GemmDesc &d, dim3 grid, cudaStream_t st) {
 
 template <int NT>
 void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
-    switch (d.lk) {
-        case 1: launch_thin_walk<NT, 2>(d, grid, st); break;
-        case 2: launch_thin_walk<NT, 4>(d, grid, st); break;
-        case 3: launch_thin_walk<NT, 8>(d, grid, st); break;
-        default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
+    if constexpr (NT == 16) {  // 16 columns: the streaming form would spill; one tile per block
+        k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d);
+    } else {
+        switch (d.lk) {
+            case 1: launch_thin_walk<NT, 2>(d, grid, st); break;
+            case 2: launch_thin_walk<NT, 4>(d, grid, st); break;
+            case 3: launch_thin_walk<NT, 8>(d, grid, st); break;
+            default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
+        }
     }
 }
 
