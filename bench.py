@@ -625,6 +625,23 @@ def supported_slices(net, sliced, seed, count):
     return found
 
 
+def sycamore53_path():
+    """The 53-qubit 16-cycle network and its path: 100 random greedy trees per chain and 2000
+    annealing sweeps (16 chains), then dynamic slicing to 2^30 elements with re-tuning.  Returns
+    (network, path, sliced labels, optimiser seconds)."""
+    from paper_2310_03978_gb300 import tn, workload as W
+    _, net = W.sycamore53_network()
+    t0 = time.perf_counter()
+    g = W.greedy_path(net.labels, net.open_labels)
+    path, _, _ = tn.path_optimize(net.labels, net.open_labels, g, seed=SA_SEED, sweeps=2000,
+                                  sweeps_final=0, t_start=0.01, t_end=0.0005, chains=16,
+                                  greedy_trials=100, beta=1.0)
+    path, sliced, _ = tn.path_optimize(net.labels, net.open_labels, path, seed=SA_SEED + 1,
+                                       sweeps=0, sweeps_per_slice=60, sweeps_final=300,
+                                       t_start=0.005, t_end=0.0005, chains=16, max_log2_size=30)
+    return net, path, sliced, time.perf_counter() - t0
+
+
 def run_sycamore53(args):
     """53-qubit, 16-cycle Sycamore-shaped circuit, 2^12 amplitudes (12 open qubits): a path
     annealed from random greedy trees with the largest intermediate bounded by slicing to 2^30
@@ -633,18 +650,8 @@ def run_sycamore53(args):
     contributing slices compared with the complex64 path.  Yields one JSON record per mode."""
     import torch
     from oracle import oracle as O
-    from paper_2310_03978_gb300 import tn, workload as W
-    circ, net = W.sycamore53_network()
-    t0 = time.perf_counter()
-    g = W.greedy_path(net.labels, net.open_labels)
-    path, _, _ = tn.path_optimize(net.labels, net.open_labels, g, seed=SA_SEED, sweeps=2000,
-                                  sweeps_final=0, t_start=0.01, t_end=0.0005, chains=16,
-                                  greedy_trials=100, beta=1.0)
-    path, sliced, info = tn.path_optimize(net.labels, net.open_labels, path, seed=SA_SEED + 1,
-                                          sweeps=0, sweeps_per_slice=60, sweeps_final=300,
-                                          t_start=0.005, t_end=0.0005, chains=16,
-                                          max_log2_size=30)
-    opt_s = time.perf_counter() - t0
+    from paper_2310_03978_gb300 import tn
+    net, path, sliced, opt_s = sycamore53_path()
     stream = torch.cuda.current_stream()
     tnet = tn.Network(net.tensors, net.labels, net.open_labels)
     nout = 1 << len(net.open_labels)
@@ -843,7 +850,8 @@ def run_step_bench(args):
 
 
 def run_step_profile(args):
-    """Per-step roofline of the bench workload: every step's CUDA-event time in profile mode
+    """Per-step roofline of the bench workload (or, with --sycamore53, of one batch of slices of
+    the 53-qubit 16-cycle path): every step's CUDA-event time in profile mode
     (after the warm-up calls, averaged over --steps calls), its T_cc and algorithmic bytes (the
     storage formats the plan uses), the bound of its kernel class (tensor cores: the measured
     BF16 peak, halved for TF32; CUDA cores: the FP32 ALU peak; both against the measured HBM copy
@@ -851,19 +859,34 @@ def run_step_profile(args):
     first, then a summary line."""
     import torch
     from paper_2310_03978_gb300 import tn, workload as W
-    wl = W.bench_workload()
-    net = tn.Network.from_workload(wl.network)
-    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, profile=True,
+    if args.sycamore53:  # one batch of slices per call, consecutive batches
+        wnet, path, sliced, _ = sycamore53_path()
+        workload = "sycamore53_6x9_c16_open12"
+    else:  # every slice per call
+        wl = W.bench_workload()
+        wnet, path, sliced, workload = wl.network, wl.path, wl.sliced, WORKLOAD
+    net = tn.Network(wnet.tensors, wnet.labels, wnet.open_labels)
+    plan = tn.Plan(net, path, sliced, mode=args.mode, profile=True,
                    autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
     info = plan.info()
     nsteps = info["num_steps"]
-    amps = torch.zeros(1 << len(wl.network.open_labels), dtype=torch.complex128, device="cuda")
+    sb = info["slices_in_flight"]
+    amps = torch.zeros(1 << len(wnet.open_labels), dtype=torch.complex128, device="cuda")
+    calls = {"n": 0}
+
+    def call():
+        if args.sycamore53:
+            plan.contract(amps, calls["n"] * sb, (calls["n"] + 1) * sb)
+        else:
+            plan.contract(amps)
+        calls["n"] += 1
+
     for _ in range(max(1, args.warmup)):
-        plan.contract(amps)
+        call()
     torch.cuda.synchronize()
     before = [plan.step_info(i) for i in range(nsteps)]
     for _ in range(args.steps):
-        plan.contract(amps)
+        call()
     torch.cuda.synchronize()
     pk = peaks()
     hbm = pk["hbm_gbs"] * 1e9
@@ -898,7 +921,8 @@ def run_step_profile(args):
         print(json.dumps(r))
     total = sum(r["ms"] for r in rows)
     roof = sum(r["roofline_ms"] for r in rows)
-    print(json.dumps({"summary": True, "workload": WORKLOAD, "mode": args.mode,
+    print(json.dumps({"summary": True, "workload": workload, "mode": args.mode,
+                      "slices_per_call": sb if args.sycamore53 else info["num_slices"],
                       "steps_timed": len(rows), "sum_ms": total, "roofline_ms": roof,
                       "frac": roof / total, "peaks": {"hbm_gbs": pk["hbm_gbs"],
                                                       "tensor_tflops": tensor / 1e12,
