@@ -336,7 +336,8 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // For K <= 8 and NT <= 8 (KS = K) the grid holds as many blocks as fit on the GPU, each walking its slice's
 // tiles with a stride: a thread loads its own row of A straight into registers (K * 8 contiguous
 // bytes; a warp reads one contiguous span) and fetches its row of the next tile before it stores
-// the current one, so loads stay in flight during the store phase.  For longer K (KS = 0) a block
+// the current one, so loads stay in flight during the store phase; two output stages taken in
+// turn leave one block barrier per tile.  For longer K (KS = 0) a block
 // takes one tile and stages its rows through shared memory in chunks of 16 of K with coalesced
 // 16-byte loads.  A step whose small operand is A runs with the roles swapped (the complex
 // product commutes).  Each tile (256 x NT) is staged and written in C's order with 8 consecutive
@@ -348,7 +349,9 @@ template <int NT, int KS>
 __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(GemmDesc d) {
     constexpr int NB = NT < 2 ? 2 : NT;  // row stride of sB (pairs stay 16-byte aligned)
     constexpr int LD = NT + 1;           // row stride of the output stage
-    __shared__ __align__(16) float2 sA[KS ? kThinRows * LD : kThinRows * kThinLd];
+    // KS > 0: two output stages used in turn (one barrier per tile); KS = 0: rows of A, then
+    // the stage
+    __shared__ __align__(16) float2 sA[KS ? 2 * kThinRows * LD : kThinRows * kThinLd];
     __shared__ __align__(16) float2 sB[(KS ? KS : 64) * NB];
     const int64_t s = blockIdx.y;
     const int K = KS ? KS : 1 << d.lk;
@@ -381,7 +384,6 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         }
     };
     // output: stage rows with stride NT + 1, then write 8 consecutive elements of C per task
-    float2 *stage = sA;
     auto soff = [&](int sq) { return (sq & 128) ? (LD << (sq & 127)) : (1 << sq); };
     int w8[8];
     {
@@ -407,11 +409,13 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
             }
     }
     float amx = 0.f;
-    auto emit = [&](int64_t m0) {  // callers synchronise before the stage is written
+    // write the tile whose C offset (its rows' deposit) is cbase through `stage`; callers make
+    // sure no thread still reads `stage` from an earlier tile
+    auto emit = [&](float2 *stage, uint64_t cbase) {
 #pragma unroll
         for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
         __syncthreads();
-        float2 *C = d.C + s * d.sC + deposit((uint64_t)m0, d.lm, d.posC_m);
+        float2 *C = d.C + s * d.sC + cbase;
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
             if (TASKS % 256 != 0 && tid + 256 * i >= TASKS) break;
@@ -440,6 +444,16 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
                 dst[2 * q + 1] = make_float2(v.z, v.w);
             }
         };
+        // C offset of tile t: deposit(t * 256), its 8 low bits zero; the warp's lanes take one
+        // bit each and OR their contributions
+        auto tile_base = [&](int64_t t) {
+            uint64_t r = 0;
+            for (int i = 8 + (tid & 31); i < d.lm; i += 32)
+                if (((uint64_t)t >> (i - 8)) & 1ull) r |= 1ull << d.posC_m[i];
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)r);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(r >> 32));
+            return ((uint64_t)hi << 32) | lo;
+        };
         int64_t t = blockIdx.x;  // < tiles: the launch makes at most one block per tile
         fetch(a, t);
         for (int e = tid; e < NT * KS; e += 256) {
@@ -447,14 +461,17 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
             sB[k * NB + n] = B[e];
         }
         __syncthreads();
+        int buf = 0;
         for (; t < tiles; t += gridDim.x) {
             if (t + gridDim.x < tiles) fetch(an, t + gridDim.x);
 #pragma unroll
             for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
 #pragma unroll
             for (int k = 0; k < KS; ++k) mac(a[k], sB + k * NB);
-            emit(t * kThinRows);
-            __syncthreads();  // the stage is read before the next tile writes it
+            // stage `buf` was last read two tiles ago, before every thread passed the barrier
+            // inside the previous tile's emit
+            emit(sA + buf * kThinRows * LD, tile_base(t));
+            buf ^= 1;
 #pragma unroll
             for (int k = 0; k < KS; ++k) a[k] = an[k];
         }
@@ -482,7 +499,7 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
             for (int k = 0; k < kw; ++k) mac(sA[tid * kThinLd + k], sB + (kc + k) * NB);
         }
         __syncthreads();  // the stage reuses sA
-        emit(m0);
+        emit(sA, deposit((uint64_t)m0, d.lm, d.posC_m));
     }
     if (d.amax_out) amax_publish(d.amax_out + s, amx);
 }
