@@ -2,9 +2,10 @@
 
 Every value here comes from the CPU oracle's state-vector simulator (oracle.statevector, a
 brute-force application of every gate matrix to the full 2^n state), read at the workload's open
-subspace.  Nothing here touches the GPU path.
+subspace (or, for the sparse-state workload, at its sampled bitstrings).  Nothing here touches
+the GPU path.  bench.py reads these files for the errors it reports.
 
-    python tests/golden/make_golden.py [small|bench ...]
+    python tests/golden/make_golden.py [small|bench|sparse ...]
 """
 import os
 import sys
@@ -42,9 +43,32 @@ def write(name, wl):
     print("wrote", path, "in %.1f s" % (time.time() - t0))
 
 
+def write_sparse(name):
+    """The 24-qubit all-open circuit of the sparse-state workload: the state-vector amplitude of
+    each of its 4096 seeded bitstrings (row i = sample i, qubit 0 = MSB of the index)."""
+    t0 = time.time()
+    circ, _, smp = W.sparse_state_workload()
+    sv = O.statevector(circ.n_qubits, circ.gates)
+    amps = sv[[int("".join(str(int(b)) for b in r), 2) for r in smp]]
+    norm = float(np.sum(np.abs(sv) ** 2))
+    del sv
+    path = os.path.join(HERE, name + ".amps.txt")
+    with open(path, "w") as f:
+        f.write("# %s: %d qubits, all open; amplitude of each of the %d seeded samples from the\n"
+                % (name, circ.n_qubits, len(smp)))
+        f.write("# oracle state vector (qubit 0 = MSB), one row per sample\n")
+        f.write("# full-state norm %.17g, oracle threads %d, %.1f s\n"
+                % (norm, O.num_threads(), time.time() - t0))
+        for a in amps:
+            f.write("%.17e %.17e\n" % (a.real, a.imag))
+    print("wrote", path, "in %.1f s" % (time.time() - t0))
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["small", "bench"]
+    which = sys.argv[1:] or ["small", "bench", "sparse"]
     if "small" in which:
         write("sycamore_3x4_c8_open6", W.small_workload())
     if "bench" in which:
         write("sycamore_5x6_c14_open10_s4", W.bench_workload())
+    if "sparse" in which:
+        write_sparse("sparse_state_sycamore_4x6_c12_all_open")
