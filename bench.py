@@ -77,6 +77,8 @@ def parse_args():
                          "all slices; prints its own JSON line")
     ap.add_argument("--sycamore53-modes", default="",
                     help="comma-separated precision modes for --sycamore53 (default: --mode)")
+    ap.add_argument("--sycamore53-sweeps", type=int, default=2000,
+                    help="annealing sweeps of the 53-qubit path before slicing")
     ap.add_argument("--sycamore53-compare", type=int, default=8,
                     help="contributing slices compared with complex64 under --sycamore53")
     ap.add_argument("--sparse-only", action="store_true",
@@ -649,15 +651,15 @@ def supported_slices(net, sliced, seed, count):
     return found
 
 
-def sycamore53_path():
-    """The 53-qubit 16-cycle network and its path: 100 random greedy trees per chain and 2000
-    annealing sweeps (16 chains), then dynamic slicing to 2^30 elements with re-tuning.  Returns
-    (network, path, sliced labels, optimiser seconds)."""
+def sycamore53_path(sweeps=2000):
+    """The 53-qubit 16-cycle network and its path: 100 random greedy trees per chain and
+    ``sweeps`` annealing sweeps (16 chains), then dynamic slicing to 2^30 elements with re-tuning.
+    Returns (network, path, sliced labels, optimiser seconds)."""
     from paper_2310_03978_gb300 import tn, workload as W
     _, net = W.sycamore53_network()
     t0 = time.perf_counter()
     g = W.greedy_path(net.labels, net.open_labels)
-    path, _, _ = tn.path_optimize(net.labels, net.open_labels, g, seed=SA_SEED, sweeps=2000,
+    path, _, _ = tn.path_optimize(net.labels, net.open_labels, g, seed=SA_SEED, sweeps=sweeps,
                                   sweeps_final=0, t_start=0.01, t_end=0.0005, chains=16,
                                   greedy_trials=100, beta=1.0)
     path, sliced, _ = tn.path_optimize(net.labels, net.open_labels, path, seed=SA_SEED + 1,
@@ -674,7 +676,7 @@ def run_sycamore53(args):
     contributing slices compared with the complex64 path.  Yields one JSON record per mode."""
     import torch
     from paper_2310_03978_gb300 import tn
-    net, path, sliced, opt_s = sycamore53_path()
+    net, path, sliced, opt_s = sycamore53_path(args.sycamore53_sweeps)
     stream = torch.cuda.current_stream()
     tnet = tn.Network(net.tensors, net.labels, net.open_labels)
     nout = 1 << len(net.open_labels)
@@ -738,7 +740,8 @@ def run_sycamore53(args):
                           "flops_per_slice": flops_slice,
                           "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
                           "path": "annealed from 100 random greedy trees x 16 chains, "
-                                  "dynamic slicing to 2^30", "optimiser_s": opt_s},
+                                  "%d sweeps, dynamic slicing to 2^30" % args.sycamore53_sweeps,
+                          "optimiser_s": opt_s},
                "timed_slices": nb * sb, "ms_per_slice": per_slice_ms,
                "effective_tflops": flops_slice / (per_slice_ms / 1e3) / 1e12,
                "rel_l2_vs_c64": err, "rel_l2_vs_c64_first_slices": per,
@@ -884,7 +887,7 @@ def run_step_profile(args):
     import torch
     from paper_2310_03978_gb300 import tn, workload as W
     if args.sycamore53:  # one batch of slices per call, consecutive batches
-        wnet, path, sliced, _ = sycamore53_path()
+        wnet, path, sliced, _ = sycamore53_path(args.sycamore53_sweeps)
         workload = "sycamore53_6x9_c16_open12"
     else:  # every slice per call
         wl = W.bench_workload()
