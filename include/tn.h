@@ -289,7 +289,11 @@ typedef struct {
                                   (cost log2 size(out) - g log2(size(a) + size(b)), g and the
                                   noise temperature drawn per tree) and anneals from the best
                                   of them and path_in                                         */
-    int32_t reserved[7];
+    int32_t balance_log2;      /* balanced indices (App. A.2): > 0 counts the multiply-adds of
+                                  every unbalanced step 2^balance_log2 times in T_cc (a step is
+                                  unbalanced when, as a GEMM, k < 64 or min(m, n) < 32); the
+                                  reported T_cc stays the plain count.  0 = off              */
+    int32_t reserved[6];
 } tn_path_options;
 
 typedef struct {

@@ -80,7 +80,19 @@ struct Tree {
     int nsl = 0;
     // histograms over internal nodes: cc exponents, T_mc terms, sizes (index = log2)
     std::vector<int64_t> hcc, hmc, hsz;
+    // balanced indices (App. A.2): cc exponents of the unbalanced internal nodes, whose
+    // multiply-adds count 2^gb times in the score (gb = 0: off)
+    std::vector<int64_t> hub;
+    int gb = 0;
     int emax = 0;  // histogram length: number of labels + 1
+
+    // a step with children of su and sw labels and cc labels in their union, as a GEMM:
+    // k = su + sw - cc contracted labels, m = su - k and n = sw - k free ones; unbalanced when
+    // k < 2^6 or min(m, n) < 2^5 elements
+    static bool unbalanced(int su, int sw, int c) {
+        const int k = su + sw - c;
+        return k < 6 || std::min(su - k, sw - k) < 5;
+    }
 
     const uint64_t *set(int v) const { return &L[(size_t)v * W]; }
     uint64_t *set(int v) { return &L[(size_t)v * W]; }
@@ -100,6 +112,7 @@ struct Tree {
         hcc.assign(emax, 0);
         hmc.assign(emax, 0);
         hsz.assign(emax, 0);
+        hub.assign(emax, 0);
         std::vector<int> order;
         order.reserve(2 * n);
         std::vector<int> st{root};
@@ -124,6 +137,7 @@ struct Tree {
             sz[v] = pc_masked(o);
             cc[v] = pc_union(a, b);
             hcc[cc[v]] += 1;
+            if (gb > 0 && unbalanced(sz[lc[v]], sz[rc[v]], cc[v])) hub[cc[v]] += 1;
             hmc[sz[lc[v]]] += 1;
             hmc[sz[rc[v]]] += 1;
             hmc[sz[v]] += 1;
@@ -150,6 +164,12 @@ struct Tree {
     // multiply-adds (the factor 8 of real flops is a constant offset)
     double score(double alpha, double beta) const {
         double l = log2_sum(hcc);
+        if (gb > 0 && std::any_of(hub.begin(), hub.end(), [](int64_t x) { return x != 0; })) {
+            // T_cc + (2^gb - 1) T_unbalanced
+            const double y = std::log2(std::exp2((double)gb) - 1.0) + log2_sum(hub);
+            const double m = std::max(l, y);
+            l = m + std::log2(std::exp2(l - m) + std::exp2(y - m));
+        }
         if (alpha > 0) {
             const double y = std::log2(alpha) + log2_sum(hmc);
             const double m = std::max(l, y);
@@ -387,17 +407,33 @@ struct Chain {
         const int sz_q_new = t.pc_masked(nqp);
         const int cc_q_new = t.pc_union(la, lk);
         const int cc_x_new = t.pc_union(nqp, lm);
-        auto apply = [&](int sq_rm, int cq_rm, int cx_rm, int sq_add, int cq_add, int cx_add) {
+        // balance of q and x before (q = (k, m), x = (q, a)) and after (q = (a, k), x = (q, m))
+        bool ub_old_q = false, ub_old_x = false, ub_new_q = false, ub_new_x = false;
+        if (t.gb > 0) {
+            ub_old_q = Tree::unbalanced(t.sz[k], t.sz[m], cc_q_old);
+            ub_old_x = Tree::unbalanced(sz_q_old, t.sz[a], cc_x_old);
+            ub_new_q = Tree::unbalanced(t.sz[a], t.sz[k], cc_q_new);
+            ub_new_x = Tree::unbalanced(sz_q_new, t.sz[m], cc_x_new);
+        }
+        auto apply = [&](int sq_rm, int cq_rm, int cx_rm, int sq_add, int cq_add, int cx_add,
+                         bool uq_rm, bool ux_rm, bool uq_add, bool ux_add) {
             t.hcc[cq_rm] -= 1;
             t.hcc[cx_rm] -= 1;
             t.hcc[cq_add] += 1;
             t.hcc[cx_add] += 1;
+            if (t.gb > 0) {
+                t.hub[cq_rm] -= uq_rm;
+                t.hub[cx_rm] -= ux_rm;
+                t.hub[cq_add] += uq_add;
+                t.hub[cx_add] += ux_add;
+            }
             t.hmc[sq_rm] -= 2;
             t.hmc[sq_add] += 2;
             t.hsz[sq_rm] -= 1;
             t.hsz[sq_add] += 1;
         };
-        apply(sz_q_old, cc_q_old, cc_x_old, sz_q_new, cc_q_new, cc_x_new);
+        apply(sz_q_old, cc_q_old, cc_x_old, sz_q_new, cc_q_new, cc_x_new, ub_old_q, ub_old_x,
+              ub_new_q, ub_new_x);
         const double nxt = t.score(p.alpha, p.beta);
         const double d = nxt - cur;
         if (d <= 0.0 || (temp > 0.0 && rng.uniform() < std::exp(-d / temp))) {
@@ -416,7 +452,8 @@ struct Chain {
             cur = nxt;
             ++accepted;
         } else {
-            apply(sz_q_new, cc_q_new, cc_x_new, sz_q_old, cc_q_old, cc_x_old);
+            apply(sz_q_new, cc_q_new, cc_x_new, sz_q_old, cc_q_old, cc_x_old, ub_new_q, ub_new_x,
+                  ub_old_q, ub_old_x);
         }
     }
 
@@ -570,8 +607,10 @@ static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
         if (opts->max_sliced > 0) o.max_sliced = opts->max_sliced;
         if (opts->chains > 0) o.chains = opts->chains;
         if (opts->greedy_trials > 0) o.greedy_trials = opts->greedy_trials;
+        o.balance_log2 = opts->balance_log2;
     }
-    if (o.alpha < 0 || o.beta < 0 || o.max_log2_size < 0 || o.chains > 256 || o.t_end > o.t_start)
+    if (o.alpha < 0 || o.beta < 0 || o.max_log2_size < 0 || o.chains > 256 || o.t_end > o.t_start ||
+        o.balance_log2 < 0 || o.balance_log2 > 16)
         return tn::report(TN_ERR_INVALID_ARG, "tn_path_optimize: invalid option");
     o.max_sliced = std::min(o.max_sliced, sliced_capacity);
 
@@ -633,6 +672,7 @@ static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
         *info = tn_path_info{};
         return TN_OK;
     }
+    T0.gb = o.balance_log2;
     T0.rebuild();
     const Params prm{o.alpha, o.beta, o.t_start, o.t_end, o.sweeps, o.sweeps_per_slice,
                      o.sweeps_final, o.max_log2_size, o.max_sliced, o.greedy_trials};

@@ -65,7 +65,8 @@ class PathOptions(C.Structure):
                 ("sweeps_final", C.c_int32), ("max_log2_size", C.c_int32),
                 ("max_sliced", C.c_int32), ("chains", C.c_int32), ("t_start", C.c_double),
                 ("t_end", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
-                ("greedy_trials", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("greedy_trials", C.c_int32), ("balance_log2", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class PathInfo(C.Structure):
@@ -158,10 +159,12 @@ def readout_noalloc(amps, n_qubits, stream=None):
 
 def path_optimize(labels, open_labels, path, seed=0, sweeps=-1, sweeps_per_slice=-1,
                   sweeps_final=-1, max_log2_size=0, max_sliced=0, chains=1, t_start=0.0,
-                  t_end=0.0, alpha=0.0, beta=0.0, greedy_trials=0):
+                  t_end=0.0, alpha=0.0, beta=0.0, greedy_trials=0, balance_log2=0):
     """Simulated-annealing path optimisation with dynamic slicing (tn_path_optimize, host
     only).  ``labels`` per tensor, ``open_labels`` the output labels, ``path`` the starting
-    pairs.  Returns (path, sliced_labels, info dict)."""
+    pairs; ``balance_log2`` > 0 weighs the multiply-adds of unbalanced steps (k < 64 or
+    min(m, n) < 32 as a GEMM) 2^balance_log2 times in the score.  Returns (path, sliced_labels,
+    info dict)."""
     n = len(labels)
     ranks = np.array([len(l) for l in labels], dtype=np.int32)
     labs = [np.ascontiguousarray(np.asarray(l, dtype=np.int32)) for l in labels]
@@ -176,7 +179,8 @@ def path_optimize(labels, open_labels, path, seed=0, sweeps=-1, sweeps_per_slice
     o = PathOptions(seed=seed, sweeps=sweeps, sweeps_per_slice=sweeps_per_slice,
                     sweeps_final=sweeps_final, max_log2_size=max_log2_size,
                     max_sliced=max_sliced, chains=chains, t_start=t_start, t_end=t_end,
-                    alpha=alpha, beta=beta, greedy_trials=greedy_trials)
+                    alpha=alpha, beta=beta, greedy_trials=greedy_trials,
+                    balance_log2=balance_log2)
     info = PathInfo()
     _check(lib().tn_path_optimize(n, ranks.ctypes.data, lab_p, len(op),
                                   op.ctypes.data if len(op) else None,

@@ -185,3 +185,33 @@ def test_random_greedy_start_beats_the_plain_greedy_tree():
     ref = O.contract(sw.network.tensors, sw.network.labels, sw.network.open_labels, sw.path)
     got = O.contract(sw.network.tensors, sw.network.labels, sw.network.open_labels, p2)
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_balanced_indices_term():
+    # App. A.2: with balance_log2 > 0 the multiply-adds of steps that are unbalanced as GEMMs
+    # (k < 64 or min(m, n) < 32) weigh 2^balance_log2 times in the score; the reported T_cc is
+    # still the plain count, and the unbalanced share of the work falls
+    wl = W.bench_workload()
+    net = wl.network
+
+    def unbalanced_share(path):
+        steps = W.replay_path(net.labels, net.open_labels, path)
+        total = sum(s.tcc for s in steps)
+        ub = sum(s.tcc for s in steps
+                 if len(s.k_labels) < 6 or min(len(s.m_labels), len(s.n_labels)) < 5)
+        return ub / total, total
+
+    kw = dict(seed=5, sweeps=200, sweeps_final=0, t_start=0.03, t_end=0.001, chains=4)
+    p0, _, i0 = T.path_optimize(net.labels, net.open_labels, wl.path, **kw)
+    p3, _, i3 = T.path_optimize(net.labels, net.open_labels, wl.path, balance_log2=3, **kw)
+    f0, t0 = unbalanced_share(p0)
+    f3, t3 = unbalanced_share(p3)
+    assert abs(i3["log2_tcc"] - math.log2(t3)) < 1e-9 and abs(i0["log2_tcc"] - math.log2(t0)) < 1e-9
+    assert f3 < f0 / 4
+    again = T.path_optimize(net.labels, net.open_labels, wl.path, balance_log2=0, **kw)
+    assert again[0] == p0  # 0 is the default: off
+    code = {v: k for k, v in T.STATUS.items()}
+    for bad in (-1, 17):
+        with pytest.raises(T.TnError) as e:
+            T.path_optimize(net.labels, net.open_labels, wl.path, balance_log2=bad, sweeps=1)
+        assert e.value.status == code["TN_ERR_INVALID_ARG"]
