@@ -282,7 +282,7 @@ typedef struct {
     int32_t max_log2_size;     /* dynamic slicing target in log2 elements; 0 = no slicing    */
     int32_t max_sliced;        /* most bonds to slice (<= 0: 64; capped by sliced_capacity)  */
     int32_t chains;            /* independent chains (<= 0: 1; at most 256)                  */
-    double t_start, t_end;     /* temperatures in score units (<= 0: defaults 1.0 and 0.01)  */
+    double t_start, t_end;     /* temperatures in score units (<= 0: defaults 0.05, 0.001)   */
     double alpha;              /* weight of T_mc (>= 0)                                       */
     double beta;               /* weight of log2(T_sc) (>= 0)                                 */
     int32_t greedy_trials;     /* > 0: each chain first builds this many random greedy trees

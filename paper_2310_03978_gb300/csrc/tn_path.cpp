@@ -590,8 +590,8 @@ static tn_status path_optimize_impl(int32_t num_tensors, const int32_t *ranks,
     o.sweeps = 200;
     o.sweeps_per_slice = 40;
     o.sweeps_final = 200;
-    o.t_start = 1.0;
-    o.t_end = 0.01;
+    o.t_start = 0.05;
+    o.t_end = 0.001;
     o.max_sliced = 64;
     o.chains = 1;
     if (opts) {
