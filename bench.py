@@ -79,6 +79,8 @@ def parse_args():
                     help="comma-separated precision modes for --sycamore53 (default: --mode)")
     ap.add_argument("--sycamore53-sweeps", type=int, default=2000,
                     help="annealing sweeps of the 53-qubit path before slicing")
+    ap.add_argument("--sycamore53-retune", type=int, default=60,
+                    help="re-tuning sweeps after each sliced bond of the 53-qubit path")
     ap.add_argument("--sycamore53-compare", type=int, default=8,
                     help="contributing slices compared with complex64 under --sycamore53")
     ap.add_argument("--sparse-only", action="store_true",
@@ -651,10 +653,10 @@ def supported_slices(net, sliced, seed, count):
     return found
 
 
-def sycamore53_path(sweeps=2000):
+def sycamore53_path(sweeps=2000, retune=60):
     """The 53-qubit 16-cycle network and its path: 100 random greedy trees per chain and
-    ``sweeps`` annealing sweeps (16 chains), then dynamic slicing to 2^30 elements with re-tuning.
-    Returns (network, path, sliced labels, optimiser seconds)."""
+    ``sweeps`` annealing sweeps (16 chains), then dynamic slicing to 2^30 elements with ``retune``
+    re-tuning sweeps per sliced bond.  Returns (network, path, sliced labels, optimiser seconds)."""
     from paper_2310_03978_gb300 import tn, workload as W
     _, net = W.sycamore53_network()
     t0 = time.perf_counter()
@@ -663,7 +665,7 @@ def sycamore53_path(sweeps=2000):
                                   sweeps_final=0, t_start=0.01, t_end=0.0005, chains=16,
                                   greedy_trials=100, beta=1.0)
     path, sliced, _ = tn.path_optimize(net.labels, net.open_labels, path, seed=SA_SEED + 1,
-                                       sweeps=0, sweeps_per_slice=60, sweeps_final=300,
+                                       sweeps=0, sweeps_per_slice=retune, sweeps_final=300,
                                        t_start=0.005, t_end=0.0005, chains=16, max_log2_size=30)
     return net, path, sliced, time.perf_counter() - t0
 
@@ -676,7 +678,7 @@ def run_sycamore53(args):
     contributing slices compared with the complex64 path.  Yields one JSON record per mode."""
     import torch
     from paper_2310_03978_gb300 import tn
-    net, path, sliced, opt_s = sycamore53_path(args.sycamore53_sweeps)
+    net, path, sliced, opt_s = sycamore53_path(args.sycamore53_sweeps, args.sycamore53_retune)
     stream = torch.cuda.current_stream()
     tnet = tn.Network(net.tensors, net.labels, net.open_labels)
     nout = 1 << len(net.open_labels)
@@ -740,7 +742,8 @@ def run_sycamore53(args):
                           "flops_per_slice": flops_slice,
                           "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
                           "path": "annealed from 100 random greedy trees x 16 chains, "
-                                  "%d sweeps, dynamic slicing to 2^30" % args.sycamore53_sweeps,
+                                  "%d sweeps, dynamic slicing to 2^30 with %d re-tuning sweeps "
+                                  "per bond" % (args.sycamore53_sweeps, args.sycamore53_retune),
                           "optimiser_s": opt_s},
                "timed_slices": nb * sb, "ms_per_slice": per_slice_ms,
                "effective_tflops": flops_slice / (per_slice_ms / 1e3) / 1e12,
@@ -887,7 +890,7 @@ def run_step_profile(args):
     import torch
     from paper_2310_03978_gb300 import tn, workload as W
     if args.sycamore53:  # one batch of slices per call, consecutive batches
-        wnet, path, sliced, _ = sycamore53_path(args.sycamore53_sweeps)
+        wnet, path, sliced, _ = sycamore53_path(args.sycamore53_sweeps, args.sycamore53_retune)
         workload = "sycamore53_6x9_c16_open12"
     else:  # every slice per call
         wl = W.bench_workload()
