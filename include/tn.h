@@ -54,13 +54,33 @@ typedef enum {
     TN_PREC_SPLIT_TF32 = 2,   /* dense steps: 3xTF32 compensated products (Sec. 4.2):
                                  hi = TF32(x), lo = TF32(x - hi), three products            */
     TN_PREC_FP16_SCALED = 3,  /* dense steps: FP16 tensor cores, per-tensor 2^e scaling     */
-    TN_PREC_BF16_SCALED = 4,  /* dense steps: BF16 tensor cores, per-tensor 2^e scaling     */
+    TN_PREC_BF16_SCALED = 4,  /* dense steps: BF16 tensor cores, per-tensor 2^e scaling; the
+                                 largest-T_cc dense steps run single-pass BF16, as many as the
+                                 error model allows within eps_budget (5e-3 when 0), the
+                                 others compensated 3xBF16 (Sec. 4.3's top-k policy)         */
     TN_PREC_SPLIT_BF16 = 5,   /* dense steps: compensated BF16 products (3xBF16, Sec. 4.2)   */
     TN_PREC_SPLIT_FP16 = 6,   /* dense steps: compensated FP16 products (3xFP16, Sec. 4.2):
                                  x = hi + lo, xy ~ hi hi + hi lo + lo hi, near-FP32 accuracy  */
     TN_PREC_MIXED = 7         /* Sec. 4.3: the mixed_topk largest-T_cc dense steps single-pass
                                  FP16, the other dense steps compensated FP16                */
 } tn_precision;
+
+/* Precision policy of the dense (tensor-core) steps, Sec. 4.3 / Table 3.  The dense steps are
+ * ranked by T_cc; the first k run single-pass in the mode's type, the rest as compensated hi/lo
+ * products of the same type (3 products, near-FP32 accuracy).  k is
+ *   - every dense step for TN_PREC_FP16_SCALED and TN_PREC_TF32, mixed_topk for
+ *     TN_PREC_MIXED (1 when 0), at most mixed_topk (when > 0) for the other single-pass modes;
+ *   - then lowered until the predicted amplitude error fits the budget, when there is one
+ *     (eps_budget > 0, or TN_PREC_BF16_SCALED's default of 5e-3).
+ * Error model (predicted relative L2 error of the amplitudes against exact arithmetic):
+ *   eps^2 = k (c u)^2 + (dense steps compensated) d_split^2 + d_floor^2,
+ * with u the unit roundoff of the single-pass type (2^-11 FP16 and TF32, 2^-8 BF16),
+ * c = 1.5 sqrt(2/7) (two operands rounded to nearest; sqrt(1/7) is the relative Frobenius
+ * error of round-to-nearest for significands uniform in [1, 2); 1.5 is a safety factor over the
+ * ~1.15 measured on the 30-qubit 14-cycle circuit), d_split = 4e-6 (a compensated step with
+ * accumulator promotion, measured) and d_floor = 1e-5 (the complex64 storage of the leaves and
+ * the FP32 steps).  Errors of independent steps add in quadrature.  A budget on the amplitude
+ * error r also bounds the paper's eps_L2^2 (Eq. l2_squared_error): eps_L2^2 <= 2r + r^2. */
 
 /* Complex GEMM form for the tensor-core steps: 4M = four real products, 3M = three. */
 typedef enum { TN_GEMM_AUTO = 0, TN_GEMM_4M = 1, TN_GEMM_3M = 2 } tn_gemm_form;
@@ -91,10 +111,15 @@ typedef struct {
     int32_t autotune;              /* 1 = during the first full batch, time every applicable
                                       tensor-core kernel variant (tile shape, 4M / 3M) per step
                                       and keep the fastest                                    */
-    int32_t mixed_topk;            /* TN_PREC_MIXED: how many tensor-core steps, largest T_cc
-                                      first, run single-pass FP16 (0 = 1); the others use
-                                      compensated hi/lo products                             */
-    int32_t reserved[4];
+    int32_t mixed_topk;            /* how many tensor-core steps, largest T_cc first, run
+                                      single-pass (TN_PREC_MIXED: exactly that many, 0 = 1;
+                                      FP16/BF16-scaled and TF32: at most that many, 0 = all);
+                                      the others use compensated hi/lo products              */
+    int32_t reserved0;
+    double eps_budget;             /* > 0: largest predicted amplitude relative L2 error the
+                                      precision policy may reach (error model above); 0 = none,
+                                      except TN_PREC_BF16_SCALED (5e-3)                      */
+    int32_t reserved[2];
 } tn_plan_options;
 
 typedef struct {
@@ -118,7 +143,10 @@ typedef struct {
                                       (slice fixing + permutation into plan order + complex64
                                       conversion, Sec. 3.2 / 4.1)                            */
     int64_t bind_launches;         /* profile mode: binding passes timed                     */
-    int32_t reserved[2];
+    int32_t num_single_pass;       /* tensor-core steps run single-pass (the policy's k)      */
+    int32_t num_compensated;       /* tensor-core steps run with compensated hi/lo products   */
+    double eps_predicted;          /* the error model's amplitude relative L2 error of the
+                                      plan (precision policy above)                          */
 } tn_plan_info;
 
 typedef struct {
@@ -137,7 +165,9 @@ typedef struct {
                                       128 x 256), 6 compensated 16-bit, 7-10 the TF32
                                       counterparts of 0-3, 11 3xTF32, 12-16 the persistent
                                       short-K kernel (16-bit rows of 64 / 16 / 32 bytes: 12,
-                                      14, 15; TF32 rows of 64 / 32 bytes: 13, 16)            */
+                                      14, 15; TF32 rows of 64 / 32 bytes: 13, 16), 17-22 the
+                                      128 x 64 tile for results 64 wide (4M 16-bit / TF32,
+                                      compensated 16-bit / TF32, 3M 16-bit / TF32)           */
     int32_t store_run_log2;        /* GEMM kernels: log2 of the longest run of consecutive
                                       result elements one staged chunk writes (its bits that
                                       are also the result's lowest positions)                */

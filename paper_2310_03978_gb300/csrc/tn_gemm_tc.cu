@@ -1200,7 +1200,7 @@ int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t row
         return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
     cuuint64_t strides[2] = {(cuuint64_t)(K * esz), (cuuint64_t)(K * rows * esz)};
-    if (box_rows != 128 && box_rows != 256) return -2;
+    if (box_rows != 64 && box_rows != 128 && box_rows != 256) return -2;
     cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType ty = dtype == 2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -1232,7 +1232,13 @@ namespace {
     X(8, 2, 32, 128, 2, 2, 4)  /* TF32 4M, short K, 2 CTAs per SM        */ \
     X(9, 2, 64, 128, 3, 1, 4)  /* TF32 4M, 128-byte swizzle, K 32        */ \
     X(10, 3, 32, 128, 4, 1, 4) /* TF32 3M                                */ \
-    X(11, 4, 32, 128, 3, 1, 4) /* split TF32 (3xTF32), promoted          */
+    X(11, 4, 32, 128, 3, 1, 4) /* split TF32 (3xTF32), promoted          */ \
+    X(17, 2, 32, 64, 4, 2, 2)  /* 4M, N tile 64, 2 CTAs per SM           */ \
+    X(18, 2, 32, 64, 4, 2, 4)  /* TF32 4M, N tile 64                     */ \
+    X(19, 4, 32, 64, 2, 2, 2)  /* split 4M, N tile 64                    */ \
+    X(20, 4, 32, 64, 2, 2, 4)  /* split TF32, N tile 64                  */ \
+    X(21, 3, 32, 64, 2, 2, 2)  /* 3M, N tile 64                          */ \
+    X(22, 3, 32, 64, 2, 2, 4)  /* TF32 3M, N tile 64                     */
 
 template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 cudaError_t configure_variant() {
@@ -1244,7 +1250,7 @@ cudaError_t configure_variant() {
 template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     constexpr int KEL = Cfg<NPL, BKT, BNT, STG, MINB, ESZ>::KEL;
-    if (d.ln < (BNT == 256 ? 8 : 7) || d.lk < 3 || (KEL == 64 && d.lk < 6) ||
+    if (d.ln < (BNT == 256 ? 8 : (BNT == 64 ? 6 : 7)) || d.lk < 3 || (KEL == 64 && d.lk < 6) ||
         (d.dtype == 2) != (ESZ == 4))
         return cudaErrorInvalidValue;
     const int64_t tiles_n = (1ll << d.ln) / BNT;
@@ -1382,7 +1388,7 @@ int tc_variant_form(int variant) {
     return 0;
 }
 
-int tc_num_variants() { return 17; }
+int tc_num_variants() { return 23; }
 
 namespace {
 int gf2_rank(std::vector<int> v) {
@@ -1444,12 +1450,20 @@ bool tc_variant_fits(int variant, int lk, int ln) {
     if (bk == 0) return false;
     if (bk == 64 && lk < 6) return false;
     if (lk < 3) return false;
+    // the 64-column tile is for narrow results (n = 64 .. 512); wider ones fill 128 or 256
+    if (bn == 64) return ln >= 6 && ln <= 9;
     return ln >= (bn == 256 ? 8 : 7);
 }
 
 // bk_pref / bn_pref: 0 or the K / N tile the caller asks for (K tile in 16-bit elements of a
 // shared-memory row: 32 = 64-byte rows, 64 = 128-byte rows, for both operand types).
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf32) {
+    // n = 64: the 64-column tile (2 CTAs per SM), in every form
+    if (ln < 7) {
+        if (form == 3) return tf32 ? 20 : 19;
+        if (form == 2) return tf32 ? 22 : 21;
+        return tf32 ? 18 : 17;
+    }
     // short contractions: the persistent kernel, unless a tile shape was asked for
     const bool pers = form == 1 && lk >= 3 && lk <= 9 && ln >= 7 && bk_pref == 0 && bn_pref == 0;
     if (tf32) {

@@ -61,6 +61,8 @@ tn_status fail(tn_status s, const char *fmt, ...) {
 
 tn_status tn::report(tn_status s, const char *msg) { return fail(s, "%s", msg); }
 
+void tn::clear_error() { g_err.clear(); }
+
 tn_status tn::reportf(tn_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -87,6 +89,33 @@ bool tf32_mode(tn_precision m) { return m == TN_PREC_TF32 || m == TN_PREC_SPLIT_
 
 // Stored type of the tensor-core operands: 0 FP16, 1 BF16, 2 FP32 rounded to TF32.
 int operand_dtype(tn_precision m) { return tf32_mode(m) ? 2 : (bf16_mode(m) ? 1 : 0); }
+
+// Modes whose dense steps run single-pass unless the precision policy demotes some of them.
+bool single_pass_mode(tn_precision m) {
+    return m == TN_PREC_FP16_SCALED || m == TN_PREC_BF16_SCALED || m == TN_PREC_TF32;
+}
+
+// Error model of the precision policy (Sec. 4.3; stated in full in tn.h).  A single-pass step
+// rounds both operands to nearest in a type of unit roundoff u; for significands uniform in
+// [1, 2) the relative Frobenius error of that rounding is u / sqrt(7) per operand, so a step
+// adds about sqrt(2/7) u to the relative error of its result, which carries to the amplitudes
+// with a gain near 1 (the rest of the network is a product of unitaries and projections).
+// Steps round independently, so their errors add in quadrature.
+constexpr double kErrSafety = 1.5;       // over the ~1.15 measured on circuits
+constexpr double kErrSplitStep = 4e-6;   // compensated step with accumulator promotion
+constexpr double kErrFloor = 1e-5;       // complex64 leaves and FP32 steps
+constexpr double kBf16DefaultBudget = 5e-3;
+
+double unit_roundoff(tn_precision m) {
+    return bf16_mode(m) ? std::ldexp(1.0, -8) : std::ldexp(1.0, -11);  // FP16, TF32: 2^-11
+}
+
+double predicted_eps(tn_precision m, int single, int split) {
+    if (m == TN_PREC_C64) return kErrFloor;
+    const double cu = kErrSafety * std::sqrt(2.0 / 7.0) * unit_roundoff(m);
+    return std::sqrt(single * cu * cu + split * kErrSplitStep * kErrSplitStep +
+                     kErrFloor * kErrFloor);
+}
 
 struct Tensor {
     std::vector<int> order;  // memory order of the labels, most significant first
@@ -179,6 +208,8 @@ struct tn_plan {
     int n_partial = 64;
     int max_log = 0;
     bool tc_ok = false;
+    int single_pass = 0, compensated = 0;  // precision policy: dense steps of each kind
+    double eps_pred = 0;                   // the error model's amplitude error of the plan
     std::vector<tn::TcGemmDesc> tc_desc;  // per step (only K_TC entries used)
     int64_t launches = 0;                 // kernels launched by this plan
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> event_pool;
@@ -218,6 +249,11 @@ int route(const Step &s, tn_precision mode, bool tc_ok) {
     // large outputs of short contractions (8 <= k < 64) also go to the tensor cores: the short-K
     // variant's tensor map zero-fills the K tile past k, and its epilogue writes 2 CTAs per SM
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 3 && lm + ln >= 20)
+        return K_TC;
+    // a narrow side of 64 (App. A.2's m, n >= 32 threshold): the 64-column tile, the wide side
+    // as M, when that side has at least 2^12 rows to spread over the SMs
+    if (s.batch.empty() && tc_mode && tc_ok && std::min(lm, ln) == 6 && std::max(lm, ln) >= 12 &&
+        lk >= 3)
         return K_TC;
     // thin steps: a short contraction of a large operand with a small one (at most 16 free
     // elements), streamed on the CUDA cores at memory speed
@@ -348,6 +384,7 @@ tn_status tn_network_load(int32_t num_tensors, const int32_t *ranks,
 }
 
 tn_status tn_network_set_data(tn_network_t *net, const double *const *data) {
+    g_err.clear();
     if (check_net(net) != TN_OK) return TN_ERR_INVALID_ARG;
     if (!data) return fail(TN_ERR_INVALID_ARG, "data is NULL");
     std::vector<double2> host((size_t)net->total);
@@ -606,22 +643,47 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
             st.form = kFormSplit;
         else
             st.form = (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
-        st.tune_form = p->opts.autotune && p->opts.gemm_form == TN_GEMM_AUTO &&
-                       st.kernel == K_TC && st.form != kFormSplit;
     }
 
-    if (mode == TN_PREC_MIXED) {
-        // Sec. 4.3: the steps with the largest T_cc run single-pass (FP16), the others with
-        // compensated hi/lo products
+    if (mode == TN_PREC_MIXED || single_pass_mode(mode)) {
+        // Sec. 4.3 / Table 3: the dense steps with the largest T_cc run single-pass, the others
+        // with compensated hi/lo products of the same type; k from the mode, mixed_topk and
+        // the error budget (precision policy in tn.h)
         std::vector<int> tc;
         for (int s = 0; s < path_len; ++s)
             if (p->steps[s].kernel == K_TC && p->steps[s].dep) tc.push_back(s);
         std::stable_sort(tc.begin(), tc.end(), [&](int x, int y) {
             return p->steps[x].tcc > p->steps[y].tcc;
         });
-        const int topk = p->opts.mixed_topk > 0 ? p->opts.mixed_topk : 1;
-        for (int i = 0; i < (int)tc.size() && i < topk; ++i) p->steps[tc[i]].form = TN_GEMM_4M;
+        const int ntc = (int)tc.size(), topk = p->opts.mixed_topk;
+        const double budget = p->opts.eps_budget > 0 ? p->opts.eps_budget
+                              : (mode == TN_PREC_BF16_SCALED ? kBf16DefaultBudget : 0.0);
+        int k = ntc;
+        if (mode == TN_PREC_MIXED) k = topk > 0 ? std::min(topk, ntc) : (budget > 0 ? ntc : 1);
+        else if (topk > 0) k = std::min(topk, ntc);
+        k = std::min(k, ntc);
+        if (budget > 0)
+            while (k > 0 && predicted_eps(mode, k, ntc - k) > budget) --k;
+        const int split_form_default =
+            (p->opts.gemm_form == TN_GEMM_3M) ? TN_GEMM_3M : TN_GEMM_4M;
+        for (int i = 0; i < ntc; ++i) {
+            Step &st = p->steps[tc[i]];
+            st.form = i < k ? (mode == TN_PREC_MIXED ? TN_GEMM_4M : split_form_default)
+                            : kFormSplit;
+        }
+        p->single_pass = k;
+        p->compensated = ntc - k;
+        p->eps_pred = predicted_eps(mode, k, ntc - k);
+    } else {
+        int ntc = 0;
+        for (auto &st : p->steps) ntc += st.kernel == K_TC && st.dep;
+        p->single_pass = 0;  // c64 (no dense steps) or a compensated mode
+        p->compensated = mode == TN_PREC_C64 ? 0 : ntc;
+        p->eps_pred = predicted_eps(mode, 0, p->compensated);
     }
+    for (auto &st : p->steps)
+        st.tune_form = p->opts.autotune && p->opts.gemm_form == TN_GEMM_AUTO &&
+                       st.kernel == K_TC && st.form != kFormSplit;
 
     // 3. layout: root first, then every step's operands from its result's order
     p->tensors[p->root].order = net->open;
@@ -634,7 +696,14 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
         // Operand roles of a GEMM step: the tensor-core epilogue maps consecutive lanes to
         // consecutive rows (m), the CUDA-core one maps them to consecutive columns (n); give the
         // label at bit 0 of the result to the side whose stores are then contiguous.
-        if ((st.kernel == K_TC || st.kernel == K_GEMM) && !co.empty()) {
+        if (st.kernel == K_TC && std::min(st.M.size(), st.N.size()) < 7) {
+            // the 64-column tile: the wide side must be M (tiles of 128 rows)
+            if (st.M.size() < st.N.size()) {
+                std::swap(st.a, st.b);
+                std::swap(st.la, st.lb);
+                std::swap(st.M, st.N);
+            }
+        } else if ((st.kernel == K_TC || st.kernel == K_GEMM) && !co.empty()) {
             const int low = co.back();
             const bool low_in_m = std::find(st.M.begin(), st.M.end(), low) != st.M.end();
             const bool want_m = st.kernel == K_TC;
@@ -1409,6 +1478,7 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
 extern "C" {
 
 tn_status tn_plan_get_info(const tn_plan_t *p, tn_plan_info *out) {
+    g_err.clear();
     if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
     if (!out) return fail(TN_ERR_INVALID_ARG, "out is NULL");
     memset(out, 0, sizeof *out);
@@ -1445,10 +1515,14 @@ tn_status tn_plan_get_info(const tn_plan_t *p, tn_plan_info *out) {
     mp->pending_bind.clear();
     out->bind_ms = p->bind_ms;
     out->bind_launches = p->bind_timed;
+    out->num_single_pass = p->single_pass;
+    out->num_compensated = p->compensated;
+    out->eps_predicted = p->eps_pred;
     return TN_OK;
 }
 
 tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *out) {
+    g_err.clear();
     if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
     if (!out || step < 0 || step >= (int64_t)p->steps.size())
         return fail(TN_ERR_INVALID_ARG, "bad step index");
@@ -1631,6 +1705,7 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
 
 tn_status tn_contract_host(tn_plan_t *p, int64_t slice_begin, int64_t slice_end,
                            double *amps_host, void *stream_) {
+    g_err.clear();
     if (check_plan(p) != TN_OK) return TN_ERR_INVALID_ARG;
     if (!amps_host) return fail(TN_ERR_INVALID_ARG, "amps_host is NULL");
     cudaStream_t stream = (cudaStream_t)stream_;

@@ -22,6 +22,8 @@ namespace tn {
 tn_status report(tn_status s, const char *msg);
 // The same with a printf format.
 tn_status reportf(tn_status s, const char *fmt, ...);
+// Clear this thread's error detail (every entry point does so on entry).
+void clear_error();
 
 constexpr uint32_t kNetMagic = 0x544e4e54u;     // "TNNT": a tn_network
 constexpr uint32_t kSparseMagic = 0x544e5350u;  // "TNSP": a sparse-state plan

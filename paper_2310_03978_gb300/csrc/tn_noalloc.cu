@@ -99,6 +99,7 @@ tn_status scratch_address(int dev, double **out) {
 
 extern "C" tn_status tn_readout_noalloc(const void *amps_dev, int64_t num_amps, int32_t n_qubits,
                                         double out[4], void *stream_) {
+    tn::clear_error();
     if (!amps_dev || !out || num_amps <= 0 || n_qubits < 0 || n_qubits > 1000)
         return tn::report(TN_ERR_INVALID_ARG, "tn_readout_noalloc: bad arguments");
     if (num_amps > kMaxAmps)

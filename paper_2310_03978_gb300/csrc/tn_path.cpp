@@ -32,6 +32,7 @@
 
 namespace tn {
 tn_status report(tn_status s, const char *msg);  // records the thread's error message
+void clear_error();                               // clears it (every entry point)
 }
 
 namespace {
@@ -566,6 +567,7 @@ extern "C" tn_status tn_path_optimize(int32_t num_tensors, const int32_t *ranks,
                                       const tn_path_options *opts, int32_t *path_out,
                                       int32_t *sliced_out, int32_t sliced_capacity,
                                       tn_path_info *info) {
+    tn::clear_error();
     try {
         return path_optimize_impl(num_tensors, ranks, labels, num_open, open_labels, path_in,
                                   opts, path_out, sliced_out, sliced_capacity, info);

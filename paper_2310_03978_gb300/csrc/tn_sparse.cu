@@ -170,6 +170,7 @@ static tn_status sparse_plan_impl(const tn_network_t *net, int32_t path_len,
 tn_status tn_sparse_plan(const tn_network_t *net, int32_t path_len, const int32_t *path,
                          int64_t num_samples, const uint8_t *samples, tn_precision mode,
                          tn_sparse_plan_t **out) {
+    tn::clear_error();
     try {
         return sparse_plan_impl(net, path_len, path, num_samples, samples, mode, out);
     } catch (const std::bad_alloc &) {
@@ -581,6 +582,7 @@ static tn_status sparse_plan_impl(const tn_network_t *net, int32_t path_len,
 }
 
 tn_status tn_sparse_contract(tn_sparse_plan_t *p, void *amps_dev, void *stream_) {
+    tn::clear_error();
     if (!p || p->magic != kSparseMagic)
         return fail(TN_ERR_INVALID_ARG, "not a sparse-state plan handle");
     if (!amps_dev) return fail(TN_ERR_INVALID_ARG, "amps_dev is NULL");
@@ -630,6 +632,7 @@ tn_status tn_sparse_contract(tn_sparse_plan_t *p, void *amps_dev, void *stream_)
 }
 
 tn_status tn_sparse_get_info(const tn_sparse_plan_t *p, tn_sparse_info *out) {
+    tn::clear_error();
     if (!p || p->magic != kSparseMagic || !out)
         return fail(TN_ERR_INVALID_ARG, "not a sparse-state plan handle");
     *out = tn_sparse_info{};

@@ -36,7 +36,8 @@ class PlanOptions(C.Structure):
                 ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
                 ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
                 ("profile", C.c_int32), ("tc_bk", C.c_int32), ("tc_bn", C.c_int32),
-                ("autotune", C.c_int32), ("mixed_topk", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("autotune", C.c_int32), ("mixed_topk", C.c_int32), ("reserved0", C.c_int32),
+                ("eps_budget", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
 class PlanInfo(C.Structure):
@@ -48,7 +49,8 @@ class PlanInfo(C.Structure):
                 ("num_gemm_steps", C.c_int32), ("num_stream_steps", C.c_int32),
                 ("num_generic_steps", C.c_int32), ("kernel_launches", C.c_int64),
                 ("bind_ms", C.c_double), ("bind_launches", C.c_int64),
-                ("reserved", C.c_int32 * 2)]
+                ("num_single_pass", C.c_int32), ("num_compensated", C.c_int32),
+                ("eps_predicted", C.c_double)]
 
 
 class StepInfo(C.Structure):
@@ -147,11 +149,33 @@ def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def _device_amps(amps, numel=None, what="amps"):
+    """Check that ``amps`` is a contiguous complex128 CUDA tensor (of ``numel`` entries when
+    given) before its address goes to a kernel: the kernels read or write numel complex128
+    values at that address, so another dtype, a host tensor or a strided view would send them
+    past the buffer."""
+    import torch
+    if not isinstance(amps, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % what)
+    if amps.dtype != torch.complex128:
+        raise TypeError("%s must be complex128, got %s" % (what, amps.dtype))
+    if not amps.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if numel is not None and amps.numel() != numel:
+        raise ValueError("%s must have %d entries, got %d" % (what, numel, amps.numel()))
+    if numel is None and amps.numel() == 0:
+        raise ValueError("%s is empty" % what)
+    if not amps.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    return C.c_void_p(amps.data_ptr())
+
+
 def readout_noalloc(amps, n_qubits, stream=None):
     """FP64 readout of a complex128 CUDA tensor without a plan and without device allocation
     (tn_readout_noalloc): [sum p, sum p^2, F_l, ideal-sample XEB]."""
     out = np.zeros(4, dtype=np.float64)
-    _check(lib().tn_readout_noalloc(C.c_void_p(amps.data_ptr()), int(amps.numel()),
+    ptr = _device_amps(amps)
+    _check(lib().tn_readout_noalloc(ptr, int(amps.numel()),
                                     int(n_qubits), C.c_void_p(out.ctypes.data),
                                     _stream_ptr(stream)))
     return out
@@ -240,7 +264,7 @@ class Plan:
     def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
                  workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
                  profile=False, use_graph=False, tc_bk=0, tc_bn=0, autotune=False,
-                 mixed_topk=0):
+                 mixed_topk=0, eps_budget=0.0):
         self.network = network
         opts = PlanOptions()
         opts.max_slices_in_flight = int(max_slices_in_flight)
@@ -257,6 +281,7 @@ class Plan:
         opts.tc_bn = int(tc_bn)
         opts.autotune = 1 if autotune else 0
         opts.mixed_topk = int(mixed_topk)
+        opts.eps_budget = float(eps_budget)
         pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
         sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
         h = C.c_void_p()
@@ -269,7 +294,7 @@ class Plan:
     def info(self) -> dict:
         i = PlanInfo()
         _check(lib().tn_plan_get_info(self.handle, C.byref(i)))
-        return {f: getattr(i, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
+        return {f: getattr(i, f) for f, _ in PlanInfo._fields_ if not f.startswith("reserved")}
 
     def step_info(self, step: int) -> dict:
         s = StepInfo()
@@ -282,8 +307,9 @@ class Plan:
         """amps: torch complex128 CUDA tensor of 2^num_open entries; results are added."""
         if slice_end is None:
             slice_end = self.info()["num_slices"]
-        _check(lib().tn_contract(self.handle, int(slice_begin), int(slice_end),
-                                 C.c_void_p(amps.data_ptr()), _stream_ptr(stream)))
+        ptr = _device_amps(amps, 1 << self.network.num_open)
+        _check(lib().tn_contract(self.handle, int(slice_begin), int(slice_end), ptr,
+                                 _stream_ptr(stream)))
 
     def contract_host(self, slice_begin=0, slice_end=None, stream=None, out=None):
         """Contract into a host complex128 numpy array (synchronises)."""
@@ -292,13 +318,17 @@ class Plan:
         n = 1 << self.network.num_open
         if out is None:
             out = np.zeros(n, dtype=np.complex128)
+        if (not isinstance(out, np.ndarray) or out.dtype != np.complex128 or out.size != n
+                or not out.flags.c_contiguous):
+            raise ValueError("out must be a contiguous complex128 array of %d entries" % n)
         _check(lib().tn_contract_host(self.handle, int(slice_begin), int(slice_end),
                                       C.c_void_p(out.ctypes.data), _stream_ptr(stream)))
         return out
 
     def readout(self, amps, n_qubits, stream=None):
         out = np.zeros(4, dtype=np.float64)
-        _check(lib().tn_readout(self.handle, C.c_void_p(amps.data_ptr()), int(n_qubits),
+        ptr = _device_amps(amps, 1 << self.network.num_open)
+        _check(lib().tn_readout(self.handle, ptr, int(n_qubits),
                                 C.c_void_p(out.ctypes.data), _stream_ptr(stream)))
         return out
 
@@ -333,8 +363,8 @@ class SparsePlan:
 
     def contract(self, amps, stream=None):
         """ADD the samples' amplitudes into a complex128 CUDA tensor of num_samples entries."""
-        _check(lib().tn_sparse_contract(self.handle, C.c_void_p(amps.data_ptr()),
-                                        _stream_ptr(stream)))
+        ptr = _device_amps(amps, self.num_samples)
+        _check(lib().tn_sparse_contract(self.handle, ptr, _stream_ptr(stream)))
 
     def info(self):
         i = SparseInfo()
