@@ -54,7 +54,12 @@ def parse_args():
     ap.add_argument("--tc-bn", type=int, default=0, choices=[0, 128, 256])
     ap.add_argument("--mixed-topk", type=int, default=0,
                     help="mode mixed: tensor-core steps (largest T_cc first) kept single-pass FP16")
+    ap.add_argument("--eps-budget", type=float, default=0.0,
+                    help="predicted amplitude error budget of the precision policy (0 = the "
+                         "mode's default)")
     ap.add_argument("--c64-steps", type=int, default=2)
+    ap.add_argument("--bf16-steps", type=int, default=2,
+                    help="steps of the BF16-scaled arm (error-budgeted policy); 0 = skip")
     ap.add_argument("--split-steps", type=int, default=2,
                     help="steps of the compensated FP16 (3xFP16) tensor-core arm; 0 = skip")
     ap.add_argument("--autotune", type=int, default=1,
@@ -77,10 +82,16 @@ def parse_args():
                          "all slices; prints its own JSON line")
     ap.add_argument("--sycamore53-modes", default="",
                     help="comma-separated precision modes for --sycamore53 (default: --mode)")
-    ap.add_argument("--sycamore53-sweeps", type=int, default=2000,
-                    help="annealing sweeps of the 53-qubit path before slicing")
-    ap.add_argument("--sycamore53-retune", type=int, default=60,
-                    help="re-tuning sweeps after each sliced bond of the 53-qubit path")
+    ap.add_argument("--c53-cycles", type=int, default=16, choices=[16, 20],
+                    help="cycles of the 53-qubit circuit for --sycamore53 / --step-profile")
+    ap.add_argument("--config4-batches", type=int, default=2,
+                    help="53-qubit 16-cycle circuit: batches of slices timed per mode in the "
+                         "default run (0 = skip)")
+    ap.add_argument("--config4-modes", default="fp16_scaled,split_bf16,c64")
+    ap.add_argument("--config5-slices", type=int, default=256,
+                    help="53-qubit 20-cycle circuit: contiguous slices timed in the default run "
+                         "(0 = skip)")
+    ap.add_argument("--config5-modes", default="fp16_scaled,c64")
     ap.add_argument("--sycamore53-compare", type=int, default=8,
                     help="contributing slices compared with complex64 under --sycamore53")
     ap.add_argument("--sparse-only", action="store_true",
@@ -253,6 +264,14 @@ def rel_l2(a, ref):
     return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
 
 
+def max_entry_err(a, ref):
+    """max |a - ref| / max |ref|: the largest error of one amplitude, relative to the largest
+    amplitude."""
+    a = np.asarray(a, dtype=np.complex128).reshape(-1)
+    ref = np.asarray(ref, dtype=np.complex128).reshape(-1)
+    return float(np.max(np.abs(a - ref)) / np.max(np.abs(ref)))
+
+
 def eps_l2sq(a, ref):
     """Relative error of the squared L2 norm (Eq. l2_squared_error)."""
     l2 = float(np.sum(np.abs(np.asarray(ref).reshape(-1)) ** 2))
@@ -263,6 +282,12 @@ def xeb_ideal(amps, n_qubits):
     """XEB of ideal samples from the amplitudes: 2^n sum p^2 / sum p - 1, p = |amplitude|^2."""
     p = np.abs(np.asarray(amps).reshape(-1)) ** 2
     return float(2.0 ** n_qubits * np.sum(p * p) / np.sum(p) - 1.0)
+
+
+def p2_over_p(amps):
+    """sum p^2 / sum p over the amplitudes (p = |a|^2): (ideal-sample XEB + 1) / 2^n."""
+    p = np.abs(np.asarray(amps).reshape(-1)) ** 2
+    return float(np.sum(p * p) / np.sum(p))
 
 
 def time_steps(torch, step, steps, stream):
@@ -326,12 +351,14 @@ def run_ours(args, rank, world, local_rank):
 
     net = tn.Network.from_workload(net_w)
 
-    def measure(mode, steps, warmup, clocks=False, graph=False):
+    def measure(mode, steps, warmup, clocks=False, graph=False, topk=None, budget=None):
+        topk = args.mixed_topk if topk is None else topk
+        budget = args.eps_budget if budget is None else budget
         if graph:
             # headline: graph replays, no per-kernel events; the roofline comes from a profiled
             # pass of the same number of steps right after
             gplan = tn.Plan(net, wl.path, wl.sliced, mode=mode, use_graph=True,
-                            autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
+                            autotune=bool(args.autotune), mixed_topk=topk, eps_budget=budget)
             amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
             for _ in range(warmup):
                 contract(gplan, amps)
@@ -350,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
             glaunch = (gplan.info()["kernel_launches"] - launches0) // steps
             gplan.close()
             del amps
-            res = measure(mode, steps, 1, clocks=False, graph=False)
+            res = measure(mode, steps, 1, clocks=False, graph=False, topk=topk, budget=budget)
             res["ms_profiled"] = res["ms"]
             res["ms"] = max_over_ranks(gms) / steps
             res["clocks"] = gclk
@@ -358,7 +385,7 @@ def run_ours(args, rank, world, local_rank):
             res["graph"] = True
             return res
         plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True,
-                       autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
+                       autotune=bool(args.autotune), mixed_topk=topk, eps_budget=budget)
         info = plan.info()
         amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
         # correctness pass (not timed)
@@ -403,6 +430,8 @@ def run_ours(args, rank, world, local_rank):
     head = measure(args.mode, args.steps, args.warmup, clocks=True, graph=bool(args.graph))
     c64 = measure("c64", args.c64_steps, 1) if args.c64_steps > 0 else None
     split = measure("split_fp16", args.split_steps, 1) if args.split_steps > 0 else None
+    bf16 = (measure("bf16_scaled", args.bf16_steps, 1, topk=0, budget=0.0)
+            if args.bf16_steps > 0 and args.mode != "bf16_scaled" else None)
 
     # the same circuit along a path from the annealing optimiser (Sec. 3.2) with dynamic slicing
     # to the same 2^28 cap: the same amplitudes with a fraction of the work
@@ -467,9 +496,24 @@ def run_ours(args, rank, world, local_rank):
     # 24-qubit circuit with every qubit open, along an annealed path
     sparse = measure_sparse(args, dev, stream) if world == 1 and args.sparse_steps > 0 else None
 
+    # the 53-qubit configurations (Sec. 5 / Table 5 shapes): 16 cycles, a few batches of slices
+    # per mode; 20 cycles, a contiguous range of slices extrapolated to all of them
+    c53 = {}
+    if world == 1 and args.config4_batches > 0:
+        c53["config4"] = measure_c53(args, 16, [m for m in args.config4_modes.split(",") if m],
+                                     batches=args.config4_batches, compare=8,
+                                     profile_mode="fp16_scaled")
+    if world == 1 and args.config5_slices > 0:
+        modes5 = [m for m in args.config5_modes.split(",") if m]
+        c53["config5"] = measure_c53(args, 20, modes5,
+                                     slices={m: (args.config5_slices if m != "c64" else 0)
+                                             for m in modes5},
+                                     batches=1, compare=8)
+
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
     # contract into a host array (D2H), every step
-    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, mixed_topk=args.mixed_topk)
+    plan = tn.Plan(net, wl.path, wl.sliced, mode=args.mode, mixed_topk=args.mixed_topk,
+                   eps_budget=args.eps_budget)
     host_out = np.zeros(1 << n_open, dtype=np.complex128)
     plan.contract_host(s_begin, s_end, out=host_out)
     barrier()
@@ -492,14 +536,19 @@ def run_ours(args, rank, world, local_rank):
     acc = {}
     if golden is not None:
         for name, r in (("head", head), ("c64", c64), ("split_fp16", split),
-                        ("annealed_path", sa)):
+                        ("bf16_scaled", bf16), ("annealed_path", sa)):
             if r is None:
                 continue
             x_ref = xeb_ideal(golden, wl.circuit.n_qubits)
             x_got = xeb_ideal(r["result"], wl.circuit.n_qubits)
             acc[name] = {"amp_rel_l2": rel_l2(r["result"], golden),
+                         "amp_max_rel": max_entry_err(r["result"], golden),
                          "eps_l2sq": eps_l2sq(r["result"], golden),
                          "xeb_ideal_rel_err": abs(x_got - x_ref) / abs(x_ref)}
+            if "eps_predicted" in r.get("info", {}):
+                acc[name]["eps_predicted"] = r["info"]["eps_predicted"]
+                acc[name]["single_pass_steps"] = r["info"]["num_single_pass"]
+                acc[name]["compensated_steps"] = r["info"]["num_compensated"]
     if rank != 0:
         return
     batches = 1 if strong else world
@@ -542,6 +591,12 @@ def run_ours(args, rank, world, local_rank):
                        "unit": "TFLOPS", "ms_per_step": c64["ms"], "steps": c64["steps"],
                        "roofline": c64["roofline"]}
         line["mixed_over_c64"] = c64["ms"] / head["ms"]
+    if bf16 is not None:
+        line["bf16_scaled"] = {"value": batches * bf16["flops"] / (bf16["ms"] / 1e3) / 1e12,
+                               "unit": "TFLOPS", "ms_per_step": bf16["ms"],
+                               "steps": bf16["steps"], "roofline": bf16["roofline"],
+                               "single_pass_steps": bf16["info"]["num_single_pass"],
+                               "compensated_steps": bf16["info"]["num_compensated"]}
     if split is not None:
         line["split_fp16"] = {"value": batches * split["flops"] / (split["ms"] / 1e3) / 1e12,
                               "unit": "TFLOPS", "ms_per_step": split["ms"],
@@ -558,6 +613,10 @@ def run_ours(args, rank, world, local_rank):
             % (SA_SEED, args.sa_alpha)}
     if small is not None:
         line["small_circuit"] = small
+    for key, cycles in (("config4", 16), ("config5", 20)):
+        if key in c53:
+            line[key] = {"workload": "sycamore53_6x9_c%d_open12" % cycles, "qubits": 53,
+                         "cycles": cycles, "open_qubits": 12, **c53[key]}
     if sparse is not None:
         line["sparse_state"] = sparse_line(args, sparse)
     if world == 1 and not args.no_cpu_baseline:
@@ -572,93 +631,32 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
-def slice_constraints(net, sliced):
-    """Necessary conditions for a slice to contribute: for every tensor, alone and (for a gate)
-    with its neighbouring vectors (|0> inputs, <b| projectors) absorbed, the value tuples of its
-    sliced bonds on which it is not identically zero (entries below 1e-12 of its largest count as
-    zero).  Returns [(bit positions in the slice id, allowed value tuples)] for the tensors that
-    exclude some tuple.  A projector after a swap-like fSim fixes the partner's input bond."""
-    import itertools
-    pos = {l: j for j, l in enumerate(sliced)}
-    vec = {ls[0]: t for t, ls in zip(net.tensors, net.labels) if len(ls) == 1}
-    pieces = list(zip(net.tensors, net.labels))
-    for t, ls in zip(net.tensors, net.labels):
-        if len(ls) < 2 or not any(l in vec for l in ls):
-            continue
-        ls = list(ls)
-        for l in list(ls):
-            if l in vec:
-                t = np.tensordot(t, vec[l], axes=([ls.index(l)], [0]))
-                ls.remove(l)
-        pieces.append((t, ls))
-    cons = []
-    for t, ls in pieces:
-        axes = [i for i, l in enumerate(ls) if l in pos]
-        if not axes:
-            continue
-        big = np.abs(t) > 1e-12 * np.abs(t).max()
-        ok = set()
-        for vals in itertools.product((0, 1), repeat=len(axes)):
-            idx = [slice(None)] * t.ndim
-            for a, v in zip(axes, vals):
-                idx[a] = v
-            if big[tuple(idx)].any():
-                ok.add(vals)
-        if len(ok) < 1 << len(axes):
-            cons.append(([pos[ls[a]] for a in axes], ok))
-    return cons
+from paper_2310_03978_gb300.slice_support import (slice_constraints, slice_supported,  # noqa: E402,F401
+                                                    supported_slices)
 
 
-def slice_supported(cons, s):
-    """Whether slice id ``s`` meets every condition of ``slice_constraints``."""
-    return all(tuple((s >> b) & 1 for b in bits) in ok for bits, ok in cons)
+def sycamore53_path(cycles=16, sweeps=None, retune=None):
+    """The 53-qubit network (6x9 grid without site (5, 8), 12 open qubits) of ``cycles`` cycles
+    and its path (``stored_path``)."""
+    return stored_path("sycamore53_6x9_c%d_open12" % cycles, sweeps, retune)
 
 
-def supported_slices(net, sliced, seed, count):
-    """Up to ``count`` distinct slice ids (bit j = value of sliced[j]) that meet
-    ``slice_constraints``: a seeded depth-first search over the bits with the values tried in
-    random order."""
-    cons = slice_constraints(net, sliced)
-    by_bit = [[] for _ in sliced]
-    for c in cons:
-        for b in c[0]:
-            by_bit[b].append(c)
-    rng = np.random.default_rng(seed)
-    found = []
-    for _ in range(64 * count):
-        if len(found) == count:
-            break
-        val = [-1] * len(sliced)
-
-        def fits(b):
-            for bits, ok in by_bit[b]:
-                if not any(all(val[x] < 0 or val[x] == v for x, v in zip(bits, vs)) for vs in ok):
-                    return False
-            return True
-
-        def dfs(b):
-            if b == len(sliced):
-                return True
-            for v in rng.permutation(2):
-                val[b] = int(v)
-                if fits(b) and dfs(b + 1):
-                    return True
-            val[b] = -1
-            return False
-
-        if dfs(0):
-            s = sum(v << j for j, v in enumerate(val))
-            if s not in found:
-                found.append(s)
-    return found
-
-
-def sycamore53_path(sweeps=2000, retune=60):
-    """The 53-qubit 16-cycle network and its path: 100 random greedy trees per chain and
-    ``sweeps`` annealing sweeps (16 chains), then dynamic slicing to 2^30 elements with ``retune``
-    re-tuning sweeps per sliced bond.  Returns (network, path, sliced labels, optimiser seconds)."""
+def stored_path(name, sweeps=None, retune=None):
+    """A named large workload's network and its path: the stored one (``paths/make_paths.py``)
+    unless an annealing effort is given, else 100 random greedy trees per chain and ``sweeps``
+    annealing sweeps (16 chains), then dynamic slicing to the size cap with ``retune``
+    re-tuning sweeps per sliced bond.  Returns (network, path, sliced labels, description)."""
     from paper_2310_03978_gb300 import tn, workload as W
-    _, net = W.sycamore53_network()
+    from paper_2310_03978_gb300.paths import make_paths as MP
+    _, cap, d_sweeps, d_retune = MP.SETTINGS[name]
+    _, net = MP.network(name)
+    rec = MP.load(name) if sweeps is None and retune is None else None
+    if rec is not None:
+        return net, [tuple(p) for p in rec["path"]], rec["sliced"], {
+            "path": "stored (%s): %s" % (os.path.basename(MP.path_file(name)), rec["optimiser"]),
+            "optimiser_s": rec["optimiser_s"]}
+    sweeps = d_sweeps if sweeps is None else sweeps
+    retune = d_retune if retune is None else retune
     t0 = time.perf_counter()
     g = W.greedy_path(net.labels, net.open_labels)
     path, _, _ = tn.path_optimize(net.labels, net.open_labels, g, seed=SA_SEED, sweeps=sweeps,
@@ -666,19 +664,66 @@ def sycamore53_path(sweeps=2000, retune=60):
                                   greedy_trials=100, beta=1.0)
     path, sliced, _ = tn.path_optimize(net.labels, net.open_labels, path, seed=SA_SEED + 1,
                                        sweeps=0, sweeps_per_slice=retune, sweeps_final=300,
-                                       t_start=0.005, t_end=0.0005, chains=16, max_log2_size=30)
-    return net, path, sliced, time.perf_counter() - t0
+                                       t_start=0.005, t_end=0.0005, chains=16,
+                                       max_log2_size=cap)
+    return net, path, sliced, {
+        "path": "annealed here: 100 random greedy trees x 16 chains, %d sweeps, dynamic slicing "
+                "to 2^%d with %d re-tuning sweeps per bond" % (sweeps, cap, retune),
+        "optimiser_s": time.perf_counter() - t0}
 
 
-def run_sycamore53(args):
-    """53-qubit, 16-cycle Sycamore-shaped circuit, 2^12 amplitudes (12 open qubits): a path
-    annealed from random greedy trees with the largest intermediate bounded by slicing to 2^30
-    elements; per precision mode, `args.sycamore53` batches of slices timed and the time per
-    slice extrapolated to all slices, and the amplitudes of up to `args.sycamore53_compare`
-    contributing slices compared with the complex64 path.  Yields one JSON record per mode."""
+def step_rows(plan, info, before, calls, mode):
+    """Per-step roofline rows of a profile-mode plan after ``calls`` timed calls, slowest first:
+    each step's CUDA-event time, its T_cc and algorithmic bytes (the storage formats the plan
+    uses), the bound of its kernel class (tensor cores: the measured sustained BF16 peak, halved
+    for TF32, on the executed products; CUDA cores: the FP32 ALU peak; both against the measured
+    HBM copy bandwidth) and the fraction of that roofline reached."""
+    pk = peaks()
+    hbm = pk["hbm_gbs"] * 1e9
+    tensor = pk["bf16_tflops_sustained"] * 1e12 * (0.5 if mode in ("tf32", "split_tf32")
+                                                  else 1.0)
+    alu = NUM_SMS * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6
+    rows = []
+    for i in range(info["num_steps"]):
+        a = plan.step_info(i)
+        b = before[i]
+        n = a["launches"] - b["launches"]
+        if n <= 0:
+            continue
+        ms = (a["time_ms"] - b["time_ms"] + a["prep_ms"] - b["prep_ms"]) / calls
+        sl = info["slices_in_flight"] if a["slice_dependent"] else 1
+        tcc, tmc = a["tcc"] * sl, a["tmc_bytes"] * sl
+        form = a["gemm_form"]
+        # executed tensor work: 4M = T_cc, 3M = 3/4 T_cc, compensated = 3 T_cc
+        executed = tcc * {2: 0.75, 3: 3.0}.get(form, 1.0)
+        compute = executed / tensor if a["kernel_name"] == "gemm_tc" else tcc / alu
+        roof = max(compute, tmc / hbm)
+        rows.append({"step": i, "kernel": a["kernel_name"], "variant": a["tc_variant"],
+                     "log2_mnk": [a["log2_m"], a["log2_n"], a["log2_k"]],
+                     "slices": sl, "ms": ms, "tflops": tcc / (ms / 1e3) / 1e12,
+                     "gbs": tmc / (ms / 1e3) / 1e9,
+                     "bound": "tensor" if compute >= tmc / hbm and a["kernel_name"] == "gemm_tc"
+                     else ("alu" if compute >= tmc / hbm else "hbm"),
+                     "roofline_ms": roof * 1e3, "frac": roof * 1e3 / ms,
+                     "store_run_log2": a["store_run_log2"]})
+    rows.sort(key=lambda r: -r["ms"])
+    return rows, {"hbm_gbs": pk["hbm_gbs"], "tensor_tflops": tensor / 1e12,
+                  "alu_tflops": alu / 1e12}
+
+
+def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mode=None,
+                ref_mode="c64"):
+    """The 53-qubit Sycamore-shaped circuit of ``cycles`` cycles (2^12 amplitudes on 12 open
+    qubits) along its stored path.  Per precision mode: a plan (CUDA-graph replay, autotuned on
+    its first batch), a contiguous range of slices timed after two warm-up batches (``batches``
+    batches of the slices in flight, or ``slices`` slices; a dict gives a count per mode), the
+    time per slice extrapolated to all slices (the method of Sec. 5), and the amplitudes of up to
+    ``compare`` contributing slices compared with ``ref_mode`` (complex64: within 1e-5 of FP64 on
+    the circuits the oracle can check).  With ``profile_mode`` one more batch of that mode runs
+    in profile mode for the per-step roofline."""
     import torch
     from paper_2310_03978_gb300 import tn
-    net, path, sliced, opt_s = sycamore53_path(args.sycamore53_sweeps, args.sycamore53_retune)
+    net, path, sliced, pdesc = sycamore53_path(cycles)
     stream = torch.cuda.current_stream()
     tnet = tn.Network(net.tensors, net.labels, net.open_labels)
     nout = 1 << len(net.open_labels)
@@ -690,66 +735,104 @@ def run_sycamore53(args):
         torch.cuda.synchronize()
         return part.cpu().numpy()
 
-    # complex64 amplitudes of contributing slices.  With fSim at theta = pi/2 and no final
+    # reference amplitudes of contributing slices.  With fSim at theta = pi/2 and no final
     # single-qubit layer most slices vanish (a closed qubit's projector after its last swap-like
     # fSim fixes the partner's input bond); candidates that no tensor forces to zero come from a
-    # seeded search, and the first ones whose complex64 result is nonzero are kept.
-    ncmp = max(0, args.sycamore53_compare)
-    cplan = tn.Plan(tnet, path, sliced, mode="c64", max_slices_in_flight=1)
+    # seeded search, and the first ones whose reference result is nonzero are kept.
     picks, refs = [], []
-    for s in supported_slices(net, sliced, SA_SEED, 3 * ncmp):
-        if len(picks) == ncmp:
-            break
-        r = one_slice(cplan, s)
-        if np.linalg.norm(r) > 0:
-            picks.append(s)
-            refs.append(r)
-    cplan.close()
-    ref = np.sum(refs, axis=0) if refs else np.zeros(nout, dtype=np.complex128)
-    modes = [m for m in (args.sycamore53_modes or args.mode).split(",") if m]
+    t0 = time.perf_counter()
+    if compare > 0:
+        cplan = tn.Plan(tnet, path, sliced, mode=ref_mode, max_slices_in_flight=1)
+        for s in supported_slices(net, sliced, SA_SEED, 3 * compare):
+            if len(picks) == compare:
+                break
+            r = one_slice(cplan, s)
+            if np.linalg.norm(r) > 0:
+                picks.append(s)
+                refs.append(r)
+        cplan.close()
+    ref = np.sum(refs, axis=0) if refs else None
+    out = {**pdesc, "sliced_bonds": len(sliced), "compared_slices": [int(s) for s in picks],
+           "reference_mode": ref_mode, "reference_s": time.perf_counter() - t0, "modes": {}}
     for mode in modes:
         plan = tn.Plan(tnet, path, sliced, mode=mode, use_graph=True, autotune=True,
-                       mixed_topk=args.mixed_topk)
+                       eps_budget=args.eps_budget)
         pi = plan.info()
         sb = pi["slices_in_flight"]
         amps = torch.zeros(nout, dtype=torch.complex128, device="cuda")
         for w in range(2):  # the first batch autotunes
             plan.contract(amps, w * sb, (w + 1) * sb, stream=stream)
         torch.cuda.synchronize()
-        nb = max(1, args.sycamore53)
-        state = {"i": 2}
-
-        def batch():
-            i = state["i"]
-            plan.contract(amps, i * sb, (i + 1) * sb, stream=stream)
-            state["i"] = i + 1
-
-        ms = time_steps(torch, batch, nb, stream)
-        per_slice_ms = ms / (nb * sb)
+        s0 = 2 * sb
+        want = slices.get(mode, 0) if isinstance(slices, dict) else slices
+        nsl = min(want if want > 0 else max(1, batches) * sb, pi["num_slices"] - s0)
+        ms = time_steps(torch, lambda: plan.contract(amps, s0, s0 + nsl, stream=stream), 1,
+                        stream)
+        per_slice_ms = ms / nsl
         flops_slice = pi["tcc_per_slice"]
-        got = np.sum([one_slice(plan, s) for s in picks], axis=0) if picks else ref
-        per = [rel_l2(one_slice(plan, s), r) for s, r in zip(picks[:2], refs[:2])]
-        plan.close()
-        err = rel_l2(got, ref) if np.linalg.norm(ref) > 0 else None
-        yield {"metric": "53-qubit sliced contraction: s per 2^12-amplitude batch (extrapolated)",
-               "value": per_slice_ms / 1e3 * pi["num_slices"], "unit": "s",
-               "higher_is_better": False, "mode": mode,
-               "config": {"workload": "sycamore53_6x9_c16_open12", "qubits": 53, "cycles": 16,
-                          "open_qubits": 12, "sliced_bonds": len(sliced),
-                          "slices": pi["num_slices"], "slices_in_flight": sb,
-                          "max_intermediate_log2": pi["max_log2_size"],
-                          "workspace_bytes": pi["workspace_bytes"],
-                          "flops_per_slice": flops_slice,
-                          "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
-                          "path": "annealed from 100 random greedy trees x 16 chains, "
-                                  "%d sweeps, dynamic slicing to 2^30 with %d re-tuning sweeps "
-                                  "per bond" % (args.sycamore53_sweeps, args.sycamore53_retune),
-                          "optimiser_s": opt_s},
-               "timed_slices": nb * sb, "ms_per_slice": per_slice_ms,
+        rec = {"slices_timed": nsl, "slice_range": [s0, s0 + nsl], "slices_in_flight": sb,
+               "ms_per_slice": per_slice_ms,
+               "s_per_batch_extrapolated": per_slice_ms / 1e3 * pi["num_slices"],
                "effective_tflops": flops_slice / (per_slice_ms / 1e3) / 1e12,
-               "rel_l2_vs_c64": err, "rel_l2_vs_c64_first_slices": per,
-               "compared_slices": [int(s) for s in picks]}
+               "workspace_bytes": pi["workspace_bytes"],
+               "single_pass_steps": pi["num_single_pass"],
+               "compensated_steps": pi["num_compensated"],
+               "eps_predicted": pi["eps_predicted"]}
+        if picks:
+            tot = np.sum([one_slice(plan, s) for s in picks], axis=0)
+            rec["amp_rel_l2_vs_ref"] = rel_l2(tot, ref)
+            rec["amp_max_rel_vs_ref"] = max_entry_err(tot, ref)
+            rec["eps_l2sq_vs_ref"] = eps_l2sq(tot, ref)
+            # the ideal-sample XEB of the summed slices, 2^n sum p^2 / sum p - 1, is dominated
+            # by the -1 while the slices hold a small part of each amplitude; its well-conditioned
+            # part is sum p^2 / sum p (= (XEB + 1) / 2^n), compared relatively
+            rec["xeb_ratio_rel_err_vs_ref"] = abs(p2_over_p(tot) / p2_over_p(ref) - 1.0)
+        plan.close()
+        if mode == profile_mode:
+            pplan = tn.Plan(tnet, path, sliced, mode=mode, profile=True, autotune=True,
+                            eps_budget=args.eps_budget)
+            pinfo = pplan.info()
+            psb = pinfo["slices_in_flight"]
+            for w in range(2):
+                pplan.contract(amps, w * psb, (w + 1) * psb, stream=stream)
+            torch.cuda.synchronize()
+            before = [pplan.step_info(i) for i in range(pinfo["num_steps"])]
+            pplan.contract(amps, 2 * psb, 3 * psb, stream=stream)
+            torch.cuda.synchronize()
+            rows, pk_used = step_rows(pplan, pinfo, before, 1, mode)
+            tot_ms = sum(r["ms"] for r in rows)
+            roof_ms = sum(r["roofline_ms"] for r in rows)
+            rec["step_roofline"] = {"frac": roof_ms / tot_ms, "sum_ms": tot_ms,
+                                    "roofline_ms": roof_ms, "slices": psb,
+                                    "top": [{k: r[k] for k in ("step", "kernel", "variant",
+                                                               "log2_mnk", "ms", "bound",
+                                                               "frac")} for r in rows[:6]],
+                                    "peaks": pk_used}
+            pplan.close()
+        del amps
+        out["modes"][mode] = rec
+        out.update({"slices": pi["num_slices"], "max_intermediate_log2": pi["max_log2_size"],
+                    "flops_per_slice": flops_slice,
+                    "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],
+                    "steps": pi["num_steps"]})
     tnet.close()
+    return out
+
+
+def run_sycamore53(args):
+    """--sycamore53 N: the 53-qubit circuit (--c53-cycles) on its stored path, N batches of
+    slices per mode; one JSON record per mode."""
+    modes = [m for m in (args.sycamore53_modes or args.mode).split(",") if m]
+    res = measure_c53(args, args.c53_cycles, modes, batches=args.sycamore53,
+                      compare=args.sycamore53_compare)
+    for mode, rec in res["modes"].items():
+        yield {"metric": "53-qubit sliced contraction: s per 2^12-amplitude batch (extrapolated)",
+               "value": rec["s_per_batch_extrapolated"], "unit": "s", "higher_is_better": False,
+               "mode": mode,
+               "config": {"workload": "sycamore53_6x9_c%d_open12" % args.c53_cycles,
+                          "qubits": 53, "cycles": args.c53_cycles, "open_qubits": 12,
+                          **{k: v for k, v in res.items() if k != "modes"}},
+               **rec}
 
 
 def measure_sparse(args, dev, stream):
@@ -881,7 +964,7 @@ def run_step_bench(args):
 
 def run_step_profile(args):
     """Per-step roofline of the bench workload (or, with --sycamore53, of one batch of slices of
-    the 53-qubit 16-cycle path): every step's CUDA-event time in profile mode
+    the 53-qubit path of --c53-cycles cycles): every step's CUDA-event time in profile mode
     (after the warm-up calls, averaged over --steps calls), its T_cc and algorithmic bytes (the
     storage formats the plan uses), the bound of its kernel class (tensor cores: the measured
     BF16 peak, halved for TF32; CUDA cores: the FP32 ALU peak; both against the measured HBM copy
@@ -890,8 +973,8 @@ def run_step_profile(args):
     import torch
     from paper_2310_03978_gb300 import tn, workload as W
     if args.sycamore53:  # one batch of slices per call, consecutive batches
-        wnet, path, sliced, _ = sycamore53_path(args.sycamore53_sweeps, args.sycamore53_retune)
-        workload = "sycamore53_6x9_c16_open12"
+        wnet, path, sliced, _ = sycamore53_path(args.c53_cycles)
+        workload = "sycamore53_6x9_c%d_open12" % args.c53_cycles
     else:  # every slice per call
         wl = W.bench_workload()
         wnet, path, sliced, workload = wl.network, wl.path, wl.sliced, WORKLOAD
@@ -918,35 +1001,7 @@ def run_step_profile(args):
     for _ in range(args.steps):
         call()
     torch.cuda.synchronize()
-    pk = peaks()
-    hbm = pk["hbm_gbs"] * 1e9
-    tensor = pk["bf16_tflops_sustained"] * 1e12 * (0.5 if args.mode in ("tf32", "split_tf32")
-                                                  else 1.0)
-    alu = 80.54784e12
-    rows = []
-    for i in range(nsteps):
-        a = plan.step_info(i)
-        b = before[i]
-        n = a["launches"] - b["launches"]
-        if n <= 0:
-            continue
-        ms = (a["time_ms"] - b["time_ms"] + a["prep_ms"] - b["prep_ms"]) / args.steps
-        sl = info["slices_in_flight"] if a["slice_dependent"] else 1
-        tcc, tmc = a["tcc"] * sl, a["tmc_bytes"] * sl
-        form = a["gemm_form"]
-        # executed tensor work: 4M = T_cc, 3M = 3/4 T_cc, compensated = 3 T_cc
-        executed = tcc * {2: 0.75, 3: 3.0}.get(form, 1.0)
-        compute = executed / tensor if a["kernel_name"] == "gemm_tc" else tcc / alu
-        roof = max(compute, tmc / hbm)
-        rows.append({"step": i, "kernel": a["kernel_name"], "variant": a["tc_variant"],
-                     "log2_mnk": [a["log2_m"], a["log2_n"], a["log2_k"]],
-                     "slices": sl, "ms": ms, "tflops": tcc / (ms / 1e3) / 1e12,
-                     "gbs": tmc / (ms / 1e3) / 1e9,
-                     "bound": "tensor" if compute >= tmc / hbm and a["kernel_name"] == "gemm_tc"
-                     else ("alu" if compute >= tmc / hbm else "hbm"),
-                     "roofline_ms": roof * 1e3, "frac": roof * 1e3 / ms,
-                     "store_run_log2": a["store_run_log2"]})
-    rows.sort(key=lambda r: -r["ms"])
+    rows, pk_used = step_rows(plan, info, before, args.steps, args.mode)
     for r in rows[:args.step_profile]:
         print(json.dumps(r))
     total = sum(r["ms"] for r in rows)
@@ -954,9 +1009,7 @@ def run_step_profile(args):
     print(json.dumps({"summary": True, "workload": workload, "mode": args.mode,
                       "slices_per_call": sb if args.sycamore53 else info["num_slices"],
                       "steps_timed": len(rows), "sum_ms": total, "roofline_ms": roof,
-                      "frac": roof / total, "peaks": {"hbm_gbs": pk["hbm_gbs"],
-                                                      "tensor_tflops": tensor / 1e12,
-                                                      "alu_tflops": alu / 1e12}}))
+                      "frac": roof / total, "peaks": pk_used}))
     plan.close()
     net.close()
 

@@ -551,6 +551,20 @@ def sycamore53_network(cycles=16, k_open=12, config_id=4):
     return circ, build_network(circ, open_q, closed)
 
 
+def sycamore45_network(cycles=14, k_open=12, config_id=6):
+    """A 45-qubit Sycamore-shaped circuit (5x9 grid), ``cycles`` cycles, the last ``k_open``
+    qubits open and the others closed on seeded bits: the shape of the paper's 45-qubit 14-cycle
+    precision study (Sec. 4.3, Tables 2-3).  No path: the caller anneals one.  Returns (circuit,
+    network)."""
+    seed = BASE_SEED + config_id
+    circ = random_circuit(5, 9, cycles, seed)
+    n = circ.n_qubits
+    rng = Xoshiro256ss(seed ^ 0x5EED)
+    open_q = list(range(n - k_open, n))
+    closed = {q: rng.below(2) for q in range(n - k_open)}
+    return circ, build_network(circ, open_q, closed)
+
+
 def sparse_state_workload(rows=4, cols=6, cycles=12, num_samples=4096, config_id=9):
     """Sparse-state input (Sec. 3.3): a seeded Sycamore-shaped circuit with every qubit open and
     ``num_samples`` seeded uniform bitstrings standing in for sampled ones (column j = qubit j,

@@ -1,11 +1,11 @@
-"""Host-side choice of contributing slices for the 53-qubit parity check (bench.py): the
+"""Host-side choice of contributing slices for the 53-qubit parity check (slice_support.py): the
 conditions of ``slice_constraints`` are necessary, so every slice whose oracle contraction is
 nonzero must meet them, and the seeded search returns only slices that do.  Small Sycamore-shaped
 circuits (fSim at theta = pi/2, no final single-qubit layer), sliced to a few bonds; no GPU."""
 import numpy as np
 import pytest
 
-import bench
+from paper_2310_03978_gb300 import slice_support as S
 from oracle import oracle as O
 from paper_2310_03978_gb300 import workload as W
 
@@ -35,20 +35,20 @@ def sliced_circuit(seed, rows, cols, cycles, n_sliced):
                                                  (31, (2, 4, 8), 4)])
 def test_contributing_slices_meet_the_conditions(seed, shape, n_sliced):
     net, path, sliced = sliced_circuit(seed, *shape, n_sliced)
-    cons = bench.slice_constraints(net, sliced)
+    cons = S.slice_constraints(net, sliced)
     total = 0.0
     for s in range(1 << len(sliced)):
         a = O.contract(net.tensors, net.labels, net.open_labels, path, sliced, s, s + 1)
         total += np.linalg.norm(a)
         if np.linalg.norm(a) > 1e-12:
-            assert bench.slice_supported(cons, s), s
+            assert S.slice_supported(cons, s), s
     assert total > 0
     # the wires sliced here make most slices vanish, and the conditions see it
-    assert sum(bench.slice_supported(cons, s) for s in range(1 << len(sliced))) < 1 << len(sliced)
-    found = bench.supported_slices(net, sliced, 7, 1 << len(sliced))
+    assert sum(S.slice_supported(cons, s) for s in range(1 << len(sliced))) < 1 << len(sliced)
+    found = S.supported_slices(net, sliced, 7, 1 << len(sliced))
     assert len(found) == len(set(found))
-    assert all(bench.slice_supported(cons, s) for s in found)
-    assert sorted(found) == [s for s in range(1 << len(sliced)) if bench.slice_supported(cons, s)]
+    assert all(S.slice_supported(cons, s) for s in found)
+    assert sorted(found) == [s for s in range(1 << len(sliced)) if S.slice_supported(cons, s)]
 
 
 def test_a_projector_after_a_swap_like_fsim_fixes_the_partner_wire():
@@ -61,8 +61,8 @@ def test_a_projector_after_a_swap_like_fsim_fixes_the_partner_wire():
     net = W.build_network(circ, [1], {0: 1})
     fs = net.labels[4]  # (out0, out1, in0, in1)
     in1 = fs[3]
-    cons = bench.slice_constraints(net, [in1])
-    assert not bench.slice_supported(cons, 0) and bench.slice_supported(cons, 1)
+    cons = S.slice_constraints(net, [in1])
+    assert not S.slice_supported(cons, 0) and S.slice_supported(cons, 1)
     path = W.greedy_path(net.labels, net.open_labels)
     a0 = O.contract(net.tensors, net.labels, net.open_labels, path, [in1], 0, 1)
     a1 = O.contract(net.tensors, net.labels, net.open_labels, path, [in1], 1, 2)
