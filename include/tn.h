@@ -167,7 +167,8 @@ typedef struct {
                                       short-K kernel (16-bit rows of 64 / 16 / 32 bytes: 12,
                                       14, 15; TF32 rows of 64 / 32 bytes: 13, 16), 17-22 the
                                       128 x 64 tile for results 64 wide (4M 16-bit / TF32,
-                                      compensated 16-bit / TF32, 3M 16-bit / TF32)           */
+                                      compensated 16-bit / TF32, 3M 16-bit / TF32), 23-28 the
+                                      128 x 32 tile for results 32 wide (same order)          */
     int32_t store_run_log2;        /* GEMM kernels: log2 of the longest run of consecutive
                                       result elements one staged chunk writes (its bits that
                                       are also the result's lowest positions)                */

@@ -184,15 +184,18 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmDesc d, int64_t tiles_n) 
     if (d.amax_out) amax_publish(d.amax_out + s, amx);
 }
 
-// Split-K partial of a skinny step (the whole output fits one 16 x 64 tile: the side with at
-// most 16 free elements is "S", the other, at most 64, is "L"; K is long, e.g. the last step of
-// a circuit).  Four groups of 64 threads each own a quarter of every 64-wide K tile; a thread
-// accumulates a 4 x 4 block of outputs (S rows sg, sg + 4, .., L columns lg, lg + 16, ..), so
-// every pair of shared-memory loads feeds 4 complex products.  The groups' sums are added in
-// group order and CTA z writes partial[z][s] (row-major M x N) for k_splitk_reduce.
+// Split-K partial of a skinny step (the whole output fits one SW x LW tile of 1024 elements,
+// 16 x 64 or 32 x 32: the side with at most SW free elements is "S", the other, at most LW, is
+// "L"; K is long, e.g. the last step of a circuit).  Four groups of 64 threads each own a quarter
+// of every 64-wide K tile; a thread accumulates a 4 x 4 block of outputs (S rows sg, sg + SW/4,
+// .., L columns lg, lg + LW/4, ..), so every pair of shared-memory loads feeds 4 complex
+// products.  The groups' sums are added in group order and CTA z writes partial[z][s] (row-major
+// M x N) for k_splitk_reduce.
 constexpr int kSkBK = 64;
-constexpr int kSkS = kSkBK * 17, kSkL = kSkBK * 65;   // one buffer: S [k][16 + 1], L [k][64 + 1]
-constexpr int kSkSmem = 2 * (kSkS + kSkL) * 8;        // double-buffered, bytes
+// one buffer: S [k][SW + 1], L [k][LW + 1]; double-buffered (the 16 x 64 form is the larger)
+constexpr int sk_buf(int sw) { return kSkBK * (sw + 1) + kSkBK * (1024 / sw + 1); }
+constexpr int kSkSmem = 2 * sk_buf(16) * 8;            // bytes
+static_assert(sk_buf(32) <= sk_buf(16), "shared-memory size of the skinny forms");
 
 __device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, bool valid) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -201,7 +204,10 @@ __device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, bool v
                  : "memory");
 }
 
+template <int SW>
 __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
+    constexpr int LW = 1024 / SW, CS = LW / 4, RS = SW / 4;
+    constexpr int kSkS = kSkBK * (SW + 1), kSkL = kSkBK * (LW + 1);
     extern __shared__ __align__(16) float2 skmem[];
     const int64_t s = blockIdx.y;
     const bool swap = d.lm > d.ln;               // S is B when M > N
@@ -213,15 +219,17 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
     const float2 *PS = (swap ? d.B + s * d.sB : d.A + s * d.sA) + kz;
     const float2 *PL = (swap ? d.A + s * d.sA : d.B + s * d.sB) + kz;
     const int tid = threadIdx.x, g = tid >> 6, t64 = tid & 63;
-    const int sg = t64 >> 4, lg = t64 & 15;
-    auto bufS = [&](int b) { return reinterpret_cast<float2(*)[17]>(skmem + b * (kSkS + kSkL)); };
+    const int sg = t64 / CS, lg = t64 % CS;
+    auto bufS = [&](int b) {
+        return reinterpret_cast<float2(*)[SW + 1]>(skmem + b * (kSkS + kSkL));
+    };
     auto bufL = [&](int b) {
-        return reinterpret_cast<float2(*)[65]>(skmem + b * (kSkS + kSkL) + kSkS);
+        return reinterpret_cast<float2(*)[LW + 1]>(skmem + b * (kSkS + kSkL) + kSkS);
     };
     // asynchronous copy of the K tile starting at k0 into buffer b (zero past this CTA's range)
     auto prefetch = [&](int b, int64_t k0) {
-        float2(*sS)[17] = bufS(b);
-        float2(*sL)[65] = bufL(b);
+        float2(*sS)[SW + 1] = bufS(b);
+        float2(*sL)[LW + 1] = bufL(b);
         for (int e = tid; e < S * kSkBK; e += 256) {
             const int r = e / kSkBK, k = e % kSkBK;
             const bool ok = k0 + k < K;
@@ -250,8 +258,8 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        const float2(*sS)[17] = bufS(b);
-        const float2(*sL)[65] = bufL(b);
+        const float2(*sS)[SW + 1] = bufS(b);
+        const float2(*sL)[LW + 1] = bufL(b);
         float tr[4][4], ti[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -261,9 +269,9 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
         for (int kk = g * 16; kk < g * 16 + 16; ++kk) {
             float2 a[4], bb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sS[kk][sg + 4 * i];
+            for (int i = 0; i < 4; ++i) a[i] = sS[kk][sg + RS * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = sL[kk][lg + 16 * j];
+            for (int j = 0; j < 4; ++j) bb[j] = sL[kk][lg + CS * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -283,23 +291,25 @@ __global__ void __launch_bounds__(256) k_gemm_skinny(GemmDesc d) {
             }
         __syncthreads();  // buffer b is refilled by the prefetch of tile t + 2
     }
-    // add the four groups' sums in group order (through buffer 0's L part: 4 x 16 x 64 float2)
-    float2 *red = &bufL(0)[0][0];  // 4 * 16 * 64 = 4096 < 64 * 65
+    // add the four groups' sums in group order (through the buffers, idle after the last
+    // barrier: 4 x 1024 float2 <= 2 buffers)
+    float2 *red = skmem;
+    static_assert(4 * 1024 <= 2 * (kSkS + kSkL), "reduction space");
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            red[(g * 16 + sg + 4 * i) * 64 + lg + 16 * j] = make_float2(cr[i][j], ci[i][j]);
+            red[(g * SW + sg + RS * i) * LW + lg + CS * j] = make_float2(cr[i][j], ci[i][j]);
     __syncthreads();
     const int64_t MN = (int64_t)S * L;
     float2 *P = d.partial + ((int64_t)blockIdx.z * gridDim.y + s) * MN;
-    for (int e = tid; e < 16 * 64; e += 256) {
-        const int si = e >> 6, li = e & 63;
+    for (int e = tid; e < SW * LW; e += 256) {
+        const int si = e / LW, li = e % LW;
         if (si >= S || li >= L) continue;
         float re = 0.f, im = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float2 v = red[(q * 16 + si) * 64 + li];
+            const float2 v = red[(q * SW + si) * LW + li];
             re += v.x;
             im += v.y;
         }
@@ -330,8 +340,8 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 }
 
 // Thin steps (the low-intensity contractions of App. A.2): C[m, n] = sum_k A[m, k] B[n, k] with
-// few columns (N = NT <= 16) and a short contraction (K <= 64, summed in one FP32 chain per
-// output: at most 64 terms).  One thread owns one row m of A and all NT outputs of that row; a
+// few columns (N = NT <= 16) and a contraction of K <= 1024 (summed in one FP32 chain per
+// output).  One thread owns one row m of A and all NT outputs of that row; a
 // tile is 256 rows.  B is held in shared memory as [K][NT] and read as broadcast 16-byte pairs.
 // For K <= 8 and NT <= 8 (KS = K) the grid holds as many blocks as fit on the GPU, each walking its slice's
 // tiles with a stride: a thread loads its own row of A straight into registers (K * 8 contiguous
@@ -480,23 +490,29 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         const float2 *A = As + m0 * K;
 #pragma unroll
         for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
-        for (int e = tid; e < NT * K; e += 256) {
-            const int n = e / K, k = e % K;
-            sB[k * NB + n] = B[e];
-        }
-        for (int kc = 0; kc < K; kc += kThinKC) {
-            const int kw = K - kc < kThinKC ? K - kc : kThinKC;  // a power of two >= 2
-            const int hp = kw >> 1;                               // 16-byte pairs per row
-            __syncthreads();
-            for (int e = tid; e < kThinRows * hp; e += 256) {
-                const int r = e / hp, q = e % hp;
-                const float4 v =
-                    *reinterpret_cast<const float4 *>(A + (int64_t)r * K + kc + 2 * q);
-                sA[r * kThinLd + 2 * q] = make_float2(v.x, v.y);
-                sA[r * kThinLd + 2 * q + 1] = make_float2(v.z, v.w);
+        // the small operand 64 of K at a time (K up to 1024), the rows of A 16 of K at a time
+        for (int kb = 0; kb < K; kb += 64) {
+            const int kbw = K - kb < 64 ? K - kb : 64;
+            __syncthreads();  // every thread is done with the previous part of sB
+            for (int e = tid; e < NT * kbw; e += 256) {
+                const int n = e / kbw, k = e % kbw;
+                sB[k * NB + n] = B[(int64_t)n * K + kb + k];
             }
-            __syncthreads();
-            for (int k = 0; k < kw; ++k) mac(sA[tid * kThinLd + k], sB + (kc + k) * NB);
+            for (int kc = kb; kc < kb + kbw; kc += kThinKC) {
+                const int kw = kb + kbw - kc < kThinKC ? kb + kbw - kc : kThinKC;  // 2^j >= 2
+                const int hp = kw >> 1;  // 16-byte pairs per row
+                __syncthreads();
+                for (int e = tid; e < kThinRows * hp; e += 256) {
+                    const int r = e / hp, q = e % hp;
+                    const float4 v =
+                        *reinterpret_cast<const float4 *>(A + (int64_t)r * K + kc + 2 * q);
+                    sA[r * kThinLd + 2 * q] = make_float2(v.x, v.y);
+                    sA[r * kThinLd + 2 * q + 1] = make_float2(v.z, v.w);
+                }
+                __syncthreads();
+                for (int k = 0; k < kw; ++k)
+                    mac(sA[tid * kThinLd + k], sB + (kc - kb + k) * NB);
+            }
         }
         __syncthreads();  // the stage reuses sA
         emit(sA, deposit((uint64_t)m0, d.lm, d.posC_m));
@@ -779,8 +795,12 @@ __global__ void __launch_bounds__(256) k_sparse_gemm(GenericDesc d, int32_t ln, 
 }  // namespace
 
 cudaError_t simt_prepare() {
-    return cudaFuncSetAttribute(k_gemm_skinny, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSkSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_skinny<16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSkSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gemm_skinny<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSkSmem);
+    return e;
 }
 
 cudaError_t launch_sparse_group(const GenericDesc &d, int32_t ln, const SparseGroupDesc &g,
@@ -835,10 +855,12 @@ cudaError_t launch_gemm_simt(const GemmDesc &d, int64_t slices, cudaStream_t st)
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)(tm * tn_), (unsigned)slices, (unsigned)d.splits);
     const int lmin = d.lm < d.ln ? d.lm : d.ln, lmax = d.lm < d.ln ? d.ln : d.lm;
-    const bool skinny = d.splits > 1 && lmin <= 4 && lmax <= 6 &&
-                        (1ll << d.lk) / d.splits >= kSkBK;
-    if (skinny)
-        k_gemm_skinny<<<dim3(1, (unsigned)slices, (unsigned)d.splits), 256, kSkSmem, st>>>(d);
+    const bool sk16 = lmin <= 4 && lmax <= 6, sk32 = lmin == 5 && lmax == 5;
+    const bool skinny = d.splits > 1 && (sk16 || sk32) && (1ll << d.lk) / d.splits >= kSkBK;
+    if (skinny && sk16)
+        k_gemm_skinny<16><<<dim3(1, (unsigned)slices, (unsigned)d.splits), 256, kSkSmem, st>>>(d);
+    else if (skinny)
+        k_gemm_skinny<32><<<dim3(1, (unsigned)slices, (unsigned)d.splits), 256, kSkSmem, st>>>(d);
     else if (d.lk - (d.splits > 1 ? __builtin_ctz((unsigned)d.splits) : 0) <= 3)
         k_gemm_simt<8><<<grid, 256, 0, st>>>(d, tn_);
     else
@@ -872,7 +894,7 @@ void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, 
 // the output tiles alone cannot, with at least 256 contracted elements per split.
 int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {
     const int lmin = lm < ln ? lm : ln, lmax = lm < ln ? ln : lm;
-    if (lmin <= 4 && lmax <= 6 && lk >= 11) {
+    if (((lmin <= 4 && lmax <= 6) || (lmin == 5 && lmax == 5)) && lk >= 11) {
         // skinny (the whole output is one CTA's tile): about 16 CTAs per SM in total, each with
         // at least 1024 contracted elements
         const int64_t want = (16 * 152 + slices - 1) / slices;
@@ -922,7 +944,7 @@ void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
 }
 
 cudaError_t launch_gemm_thin(const GemmDesc &d, int64_t slices, cudaStream_t st) {
-    if (d.lm < 8 || d.ln < 0 || d.ln > 4 || d.lk < 1 || d.lk > 6 || slices > 65535 ||
+    if (d.lm < 8 || d.ln < 0 || d.ln > 4 || d.lk < 1 || d.lk > 10 || slices > 65535 ||
         d.tile_bits != 8 + d.ln || d.tile_bits < 3 || d.planar_out)
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)((1ll << d.lm) / kThinRows), (unsigned)slices);

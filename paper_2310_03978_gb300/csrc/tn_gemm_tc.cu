@@ -228,6 +228,11 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
     constexpr int TMEM_COLS = F::TMEM_COLS;
     constexpr int TILE_A = F::TILE_A, TILE_B = F::TILE_B;
     constexpr int BK = F::KEL, BN = BNT;  // K elements per stage, N tile
+    // epilogue chunk: 64 columns (13 bits with the 7 row bits), or the whole 32-column tile
+    constexpr int CWK = BN < CW ? BN : CW;
+    constexpr int CHB = CWK == 64 ? 13 : 12;       // bits of a chunk
+    constexpr int ITERS = (BM * CWK) / (8 * 128);  // 8-element stores per thread and chunk
+    static_assert(CWK == 64 || CWK == 32, "epilogue chunk of 64 or 32 columns");
     auto sdesc = [](uint32_t a) { return sdesc_sw<F::SBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -435,12 +440,12 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
     }
     have = __syncthreads_and(have && *(volatile int *)aborted == 0 ? 1 : 0) != 0;
     if (have) {
-        // The tile is written in chunks of CW = 64 columns: each chunk is staged in shared
-        // memory and written out in the order of C's memory index.  A chunk has 13 bits (7 row,
-        // 6 column), sorted on the host by their position in C; element t of the chunk in that
-        // order takes its low 7 bits from the thread index and its high 6 from the iteration.
-        // C's positions 0..5 always belong to a chunk, so each warp store covers >= 64
-        // consecutive elements.
+        // The tile is written in chunks of CWK columns (64, or the whole tile when it is 32
+        // wide): each chunk is staged in shared memory and written out in the order of C's
+        // memory index.  A chunk has CHB bits (7 row bits and 6 or 5 column bits), sorted on the
+        // host by their position in C; element t of the chunk in that order takes bits 0..2 from
+        // the thread's own 8 elements, bits 3..9 from the thread index and the rest from the
+        // iteration.
         float2 *stage = reinterpret_cast<float2 *>(smem);
         uint64_t *hi_off = reinterpret_cast<uint64_t *>(smem + BM * SLD * 8);
         int *hi_w = reinterpret_cast<int *>(hi_off + 64);
@@ -479,11 +484,11 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
                 olo |= 1ull << d.tb_pos[q];
             }
         const int wlo = mlo * SLD + nlo;
-        if (epi && et < 8) {
+        if (epi && et < ITERS) {
             int mi = 0, ni = 0;
             uint64_t off = 0;
 #pragma unroll
-            for (int q = 10; q < 13; ++q)
+            for (int q = 10; q < CHB; ++q)
                 if ((et >> (q - 10)) & 1) {
                     const int sq = d.tb_src[q];
                     if (sq & 128) mi |= 1 << (sq & 127);
@@ -498,9 +503,9 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
         if (d.planar_out && blockIdx.x == 0 && threadIdx.x == 0) d.pout.exps[s] = eo;
         float amx = 0.f;
 #pragma unroll 1
-        for (int cb = 0; cb < BN; cb += CW) {
+        for (int cb = 0; cb < BN; cb += CWK) {
 #pragma unroll 1
-            for (int c0 = cb; c0 < cb + CW && epi; c0 += 16) {
+            for (int c0 = cb; c0 < cb + CWK && epi; c0 += 16) {
                 uint32_t r0[16], r1[16];
                 tmem_ld16(tmem + lane_base + src + (uint32_t)c0, r0);
                 tmem_ld16(tmem + lane_base + src + (uint32_t)(BN + c0), r1);
@@ -531,7 +536,7 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
             } else {
                 float2 *C = d.C + s * d.sC + cbase;
 #pragma unroll 2
-                for (int it = 0; it < (BM * CW) / (8 * 128); ++it) {
+                for (int it = 0; it < ITERS; ++it) {
                     const int w = wlo + hi_w[it];
                     float2 v[8];
 #pragma unroll
@@ -581,13 +586,17 @@ constexpr int PERS_BN = 128, PERS_STG = 4, PERS_THREADS = 320, PCW = 32;
 // K wide for the short contractions, so no zero fill is fetched; with 16-byte rows the MMA's
 // second K half (elements 8..15) reads a zero page that sits one tile further (the descriptor's
 // leading-dimension offset).
-template <int ESZ, int RB>
+// BNP is the N tile (128, or 64 / 32 for results that narrow); B's planes then fill only the
+// first BNP rows of their 128-row slots.
+template <int ESZ, int RB, int BNP = PERS_BN>
 struct PersCfg {
     static constexpr int KEL = RB / ESZ;                  // K elements per stage
-    static constexpr int TILE = BM * RB;                  // one plane of A or B (128 rows)
+    static constexpr int TILE = BM * RB;                  // one plane of A (128 rows)
+    static constexpr int TILE_B = BNP * RB;               // one plane of B (BNP rows)
     static constexpr int TSTRIDE = RB == 16 ? 2 * TILE : TILE;  // tile + zero page
     static constexpr int STAGE_BYTES = 4 * TSTRIDE;       // A re, A im, B re, B im
-    static constexpr int TX_BYTES = 4 * TILE;             // bytes the TMA writes per stage
+    static constexpr int TX_BYTES = 2 * TILE + 2 * TILE_B;  // bytes the TMA writes per stage
+    static constexpr int LBN = BNP == 128 ? 7 : (BNP == 64 ? 6 : 5);  // log2 of the N tile
     static constexpr int RING = PERS_STG * STAGE_BYTES;
     static constexpr int STAGE_HALF = BM * PCW * 8;       // staging of one 128 x 32 chunk
     static constexpr int DEP = 6 * 256 * 8;               // byte-wise deposit tables of m0, n0
@@ -598,6 +607,7 @@ struct PersCfg {
     static constexpr uint64_t LAYOUT = RB == 64 ? 4 : (RB == 32 ? 6 : 0);
     static constexpr int KSTEPS = RB == 16 ? 1 : RB / 32; // MMAs (32 bytes of K) per stage
     static_assert(RB == 16 ? ESZ == 2 : (RB == 32 || RB == 64), "row width");
+    static_assert(BNP == 128 || BNP == 64 || BNP == 32, "N tile");
 };
 
 // Shared-memory matrix descriptor with an explicit leading-dimension offset (K-major tiles).
@@ -701,11 +711,11 @@ __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
     return r != 0;
 }
 
-template <int ESZ, int RB, bool PACKED>
+template <int ESZ, int RB, bool PACKED, int BNP>
 __global__ void __launch_bounds__(PERS_THREADS, 1)
     k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
-    using F = PersCfg<ESZ, RB>;
-    constexpr int BK = F::KEL, BN = PERS_BN;
+    using F = PersCfg<ESZ, RB, BNP>;
+    constexpr int BK = F::KEL, BN = BNP;
     auto sdesc = [](uint32_t a) { return sdesc_lbo<F::SBO, F::LBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -722,7 +732,8 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     int *drain_stop = aborted + 1;        // the drain warps ended the staging hand-off
 
     // deposit tables: dep[j][b] = C offset of byte b of the tile row index (j = 0..2) or of
-    // the tile column index (j = 3..5), i.e. of m bits 7 + 8 j .. and n bits 7 + 8 (j - 3) ..
+    // the tile column index (j = 3..5), i.e. of m bits 7 + 8 j .. and n bits LBN + 8 (j - 3) ..
+    // (LBN = log2 of the N tile)
     uint64_t (*dep)[256] = reinterpret_cast<uint64_t (*)[256]>(smem + F::BODY);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tiles_m = (uint32_t)((1ll << d.lm) / BM);
@@ -742,7 +753,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     for (int e = threadIdx.x; e < 6 * 256; e += PERS_THREADS) {
         const int j = e >> 8, b = e & 255;
         const bool nside = j >= 3;
-        const int first = 7 + 8 * (nside ? j - 3 : j), nb = nside ? d.ln : d.lm;
+        const int first = (nside ? F::LBN + 8 * (j - 3) : 7 + 8 * j), nb = nside ? d.ln : d.lm;
         const int8_t *pos = nside ? d.posC_n : d.posC_m;
         uint64_t v = 0;
         for (int i = 0; i < 8; ++i)
@@ -801,7 +812,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted; t += gridDim.x) {
                 const TileCoord c = pers_tile(t, tiles_m, tn32);
                 const int sa = d.a_sliced ? c.s : 0, sbi = d.b_sliced ? c.s : 0;
-                const int m0 = (int)(c.mt * BM), n0 = (int)(c.nt * PERS_BN);
+                const int m0 = (int)(c.mt * BM), n0 = (int)(c.nt * BN);
                 bool ok = true;
                 for (int kb = 0; kb < num_kb; ++kb, ++it) {
                     const int st = it % PERS_STG;
@@ -1068,8 +1079,9 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             rbk32[k] = rb * PCW;
             xk[k] = cb ^ phi_of(rb);
         }
-        // C offsets of the column chunk inside the tile: n bits 5 and 6
-        const uint64_t off5 = 1ull << d.posC_n[5], off6 = 1ull << d.posC_n[6];
+        // C offsets of the column chunk inside the tile: n bits 5 and 6 (those the tile has)
+        const uint64_t off5 = BN > 32 ? 1ull << d.posC_n[5] : 0ull;
+        const uint64_t off6 = BN > 64 ? 1ull << d.posC_n[6] : 0ull;
         int cur_s = -1, eo = 0;
         int n = 0;
         bool stop = false;
@@ -1200,7 +1212,7 @@ int encode_tmap_planar(void *tmap_host, const void *base, int64_t K, int64_t row
         return -2;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)depth};
     cuuint64_t strides[2] = {(cuuint64_t)(K * esz), (cuuint64_t)(K * rows * esz)};
-    if (box_rows != 64 && box_rows != 128 && box_rows != 256) return -2;
+    if (box_rows != 32 && box_rows != 64 && box_rows != 128 && box_rows != 256) return -2;
     cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType ty = dtype == 2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -1238,7 +1250,13 @@ namespace {
     X(19, 4, 32, 64, 2, 2, 2)  /* split 4M, N tile 64                    */ \
     X(20, 4, 32, 64, 2, 2, 4)  /* split TF32, N tile 64                  */ \
     X(21, 3, 32, 64, 2, 2, 2)  /* 3M, N tile 64                          */ \
-    X(22, 3, 32, 64, 2, 2, 4)  /* TF32 3M, N tile 64                     */
+    X(22, 3, 32, 64, 2, 2, 4)  /* TF32 3M, N tile 64                     */ \
+    X(23, 2, 32, 32, 4, 2, 2)  /* 4M, N tile 32, 2 CTAs per SM           */ \
+    X(24, 2, 32, 32, 4, 2, 4)  /* TF32 4M, N tile 32                     */ \
+    X(25, 4, 32, 32, 2, 2, 2)  /* split 4M, N tile 32                    */ \
+    X(26, 4, 32, 32, 2, 2, 4)  /* split TF32, N tile 32                  */ \
+    X(27, 3, 32, 32, 2, 2, 2)  /* 3M, N tile 32                          */ \
+    X(28, 3, 32, 32, 2, 2, 4)  /* TF32 3M, N tile 32                     */
 
 template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 cudaError_t configure_variant() {
@@ -1250,7 +1268,8 @@ cudaError_t configure_variant() {
 template <int NPL, int BKT, int BNT, int STG, int MINB, int ESZ>
 cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     constexpr int KEL = Cfg<NPL, BKT, BNT, STG, MINB, ESZ>::KEL;
-    if (d.ln < (BNT == 256 ? 8 : (BNT == 64 ? 6 : 7)) || d.lk < 3 || (KEL == 64 && d.lk < 6) ||
+    if (d.ln < (BNT == 256 ? 8 : (BNT == 64 ? 6 : (BNT == 32 ? 5 : 7))) || d.lk < 3 ||
+        (KEL == 64 && d.lk < 6) ||
         (d.dtype == 2) != (ESZ == 4))
         return cudaErrorInvalidValue;
     const int64_t tiles_n = (1ll << d.ln) / BNT;
@@ -1264,15 +1283,15 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 
 }  // namespace
 
-template <int ESZ, int RB>
+template <int ESZ, int RB, int BNP>
 cudaError_t configure_pers() {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, false>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, false, BNP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         PersCfg<ESZ, RB>::SMEM_BYTES);
+                                         PersCfg<ESZ, RB, BNP>::SMEM_BYTES);
     if (e == cudaSuccess && ESZ == 2)
-        e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, ESZ == 2>,
+        e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, ESZ == 2, BNP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 PersCfg<ESZ, RB>::SMEM_BYTES);
+                                 PersCfg<ESZ, RB, BNP>::SMEM_BYTES);
     return e;
 }
 
@@ -1288,36 +1307,44 @@ int sm_count() {
     return n;
 }
 
-template <int ESZ, int RB>
+template <int ESZ, int RB, int BNP>
 cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
+    using F = PersCfg<ESZ, RB, BNP>;
     // tile rows and columns index the deposit tables with 24 bits each; tiles count in 32 bits
-    if (d.ln < 7 || d.lk < 3 || d.lk > 9 || d.lm > 31 || d.ln > 31 ||
+    if (d.ln < F::LBN || d.lk < 3 || d.lk > 9 || d.lm > 31 || d.ln > 31 ||
         (d.dtype == 2) != (ESZ == 4))
         return cudaErrorInvalidValue;
-    const int64_t tiles_n = (1ll << d.ln) / PERS_BN;
+    const int64_t tiles_n = (1ll << d.ln) / BNP;
     const int64_t total = ((1ll << d.lm) / BM) * tiles_n * slices;
     if (total > 0x7fffffffll) return cudaErrorInvalidConfiguration;
     int64_t grid = sm_count();
     if (grid > total) grid = total;
     // planar two-plane results (16-bit only) use the packed staging
     if (ESZ == 2 && d.planar_out && d.pout.planes == 2)
-        k_gemm_tc_pers<ESZ, RB, ESZ == 2>
-            <<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ, RB>::SMEM_BYTES, st>>>(d, tiles_n, slices);
+        k_gemm_tc_pers<ESZ, RB, ESZ == 2, BNP>
+            <<<(unsigned)grid, PERS_THREADS, F::SMEM_BYTES, st>>>(d, tiles_n, slices);
     else
-        k_gemm_tc_pers<ESZ, RB, false>
-            <<<(unsigned)grid, PERS_THREADS, PersCfg<ESZ, RB>::SMEM_BYTES, st>>>(d, tiles_n, slices);
+        k_gemm_tc_pers<ESZ, RB, false, BNP>
+            <<<(unsigned)grid, PERS_THREADS, F::SMEM_BYTES, st>>>(d, tiles_n, slices);
     return cudaGetLastError();
 }
 
-// Variants 12-16 are the persistent short-K kernel: 16-bit with rows of 64, 16 and 32 bytes
-// (12, 14, 15), TF32 with rows of 64 and 32 bytes (13, 16).
+// Variants 12-16 are the persistent short-K kernel with 128-column tiles: 16-bit with rows of
+// 64, 16 and 32 bytes (12, 14, 15), TF32 with rows of 64 and 32 bytes (13, 16); 29-33 the same
+// five with 64-column tiles, 34-38 with 32-column tiles.
 constexpr int kPersFp16 = 12, kPersTf32 = 13, kPersFp16R16 = 14, kPersFp16R32 = 15,
-              kPersTf32R32 = 16;
+              kPersTf32R32 = 16, kPers64 = 29, kPers32 = 34;
 
-bool is_pers(int v) { return v >= kPersFp16 && v <= kPersTf32R32; }
+bool is_pers(int v) {
+    return (v >= kPersFp16 && v <= kPersTf32R32) || (v >= kPers64 && v < kPers32 + 5);
+}
+
+// the 128-column variant (12-16) of the same row width and operand type, and the N tile
+int pers_base(int v) { return v >= kPers32 ? v - kPers32 + 12 : (v >= kPers64 ? v - kPers64 + 12 : v); }
+int pers_bn(int v) { return v >= kPers32 ? 32 : (v >= kPers64 ? 64 : PERS_BN); }
 
 int pers_kel(int v) {
-    switch (v) {
+    switch (pers_base(v)) {
         case kPersFp16: return PersCfg<2, 64>::KEL;
         case kPersTf32: return PersCfg<4, 64>::KEL;
         case kPersFp16R16: return PersCfg<2, 16>::KEL;
@@ -1327,12 +1354,32 @@ int pers_kel(int v) {
     return 0;
 }
 
+template <int BNP>
+cudaError_t launch_pers_bn(int base, const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
+    switch (base) {
+        case kPersFp16: return launch_pers<2, 64, BNP>(d, slices, st);
+        case kPersTf32: return launch_pers<4, 64, BNP>(d, slices, st);
+        case kPersFp16R16: return launch_pers<2, 16, BNP>(d, slices, st);
+        case kPersFp16R32: return launch_pers<2, 32, BNP>(d, slices, st);
+        case kPersTf32R32: return launch_pers<4, 32, BNP>(d, slices, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int BNP>
+cudaError_t configure_pers_bn() {
+    cudaError_t e = configure_pers<2, 64, BNP>();
+    if (e == cudaSuccess) e = configure_pers<4, 64, BNP>();
+    if (e == cudaSuccess) e = configure_pers<2, 16, BNP>();
+    if (e == cudaSuccess) e = configure_pers<2, 32, BNP>();
+    if (e == cudaSuccess) e = configure_pers<4, 32, BNP>();
+    return e;
+}
+
 cudaError_t tc_prepare() {
-    cudaError_t e = configure_pers<2, 64>();
-    if (e == cudaSuccess) e = configure_pers<4, 64>();
-    if (e == cudaSuccess) e = configure_pers<2, 16>();
-    if (e == cudaSuccess) e = configure_pers<2, 32>();
-    if (e == cudaSuccess) e = configure_pers<4, 32>();
+    cudaError_t e = configure_pers_bn<128>();
+    if (e == cudaSuccess) e = configure_pers_bn<64>();
+    if (e == cudaSuccess) e = configure_pers_bn<32>();
 #define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb, esz) \
     if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb, esz>();
     TN_TC_VARIANTS(TN_TC_CONFIGURE)
@@ -1353,7 +1400,7 @@ int tc_variant_bk(int variant) {
 }
 
 int tc_variant_bn(int variant) {
-    if (is_pers(variant)) return PERS_BN;
+    if (is_pers(variant)) return pers_bn(variant);
     switch (variant) {
 #define TN_TC_BN(id, npl, bk, bn, stg, minb, esz) \
     case id: return bn;
@@ -1363,8 +1410,10 @@ int tc_variant_bn(int variant) {
     return 0;
 }
 
+bool tc_variant_is_pers(int variant) { return is_pers(variant); }
+
 bool tc_variant_tf32(int variant) {
-    if (is_pers(variant)) return variant == kPersTf32 || variant == kPersTf32R32;
+    if (is_pers(variant)) return pers_base(variant) == kPersTf32 || pers_base(variant) == kPersTf32R32;
     switch (variant) {
 #define TN_TC_ESZ(id, npl, bk, bn, stg, minb, esz) \
     case id: return esz == 4;
@@ -1388,7 +1437,7 @@ int tc_variant_form(int variant) {
     return 0;
 }
 
-int tc_num_variants() { return 23; }
+int tc_num_variants() { return 39; }
 
 namespace {
 int gf2_rank(std::vector<int> v) {
@@ -1445,20 +1494,38 @@ void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits) {
 }
 
 bool tc_variant_fits(int variant, int lk, int ln) {
-    if (is_pers(variant)) return lk >= 3 && lk <= 9 && ln >= 7;
+    if (is_pers(variant)) {
+        const int bn = pers_bn(variant);
+        return lk >= 3 && lk <= 9 && (bn == 128 ? ln >= 7 : (bn == 64 ? ln == 6 : ln == 5));
+    }
     const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
     if (bk == 0) return false;
     if (bk == 64 && lk < 6) return false;
     if (lk < 3) return false;
-    // the 64-column tile is for narrow results (n = 64 .. 512); wider ones fill 128 or 256
+    // the 64-column tile is for narrow results (n = 64 .. 512); wider ones fill 128 or 256;
+    // the 32-column tile for n = 32 only
     if (bn == 64) return ln >= 6 && ln <= 9;
+    if (bn == 32) return ln == 5;
     return ln >= (bn == 256 ? 8 : 7);
 }
 
 // bk_pref / bn_pref: 0 or the K / N tile the caller asks for (K tile in 16-bit elements of a
 // shared-memory row: 32 = 64-byte rows, 64 = 128-byte rows, for both operand types).
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf32) {
-    // n = 64: the 64-column tile (2 CTAs per SM), in every form
+    // n = 32 or 64: the 32- or 64-column tile, persistent for short 4M contractions, else one
+    // tile per CTA (2 CTAs per SM) in every form
+    const bool pers_narrow = form == 1 && lk >= 3 && lk <= 9 && bk_pref == 0 && bn_pref == 0 &&
+                             (ln == 5 || ln == 6);
+    if (pers_narrow) {
+        const int off = ln == 5 ? kPers32 - 12 : kPers64 - 12;
+        if (tf32) return off + (lk == 3 ? kPersTf32R32 : kPersTf32);
+        return off + (lk == 3 ? kPersFp16R16 : (lk == 4 ? kPersFp16R32 : kPersFp16));
+    }
+    if (ln == 5) {
+        if (form == 3) return tf32 ? 26 : 25;
+        if (form == 2) return tf32 ? 28 : 27;
+        return tf32 ? 24 : 23;
+    }
     if (ln < 7) {
         if (form == 3) return tf32 ? 20 : 19;
         if (form == 2) return tf32 ? 22 : 21;
@@ -1487,13 +1554,11 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
 
 cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (d.lm < 7 || slices > 65535) return cudaErrorInvalidValue;
-    switch (d.variant) {
-        case kPersFp16: return launch_pers<2, 64>(d, slices, st);
-        case kPersTf32: return launch_pers<4, 64>(d, slices, st);
-        case kPersFp16R16: return launch_pers<2, 16>(d, slices, st);
-        case kPersFp16R32: return launch_pers<2, 32>(d, slices, st);
-        case kPersTf32R32: return launch_pers<4, 32>(d, slices, st);
-        default: break;
+    if (is_pers(d.variant)) {
+        const int bn = pers_bn(d.variant), base = pers_base(d.variant);
+        if (bn == 64) return launch_pers_bn<64>(base, d, slices, st);
+        if (bn == 32) return launch_pers_bn<32>(base, d, slices, st);
+        return launch_pers_bn<128>(base, d, slices, st);
     }
     switch (d.variant) {
 #define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb, esz) \

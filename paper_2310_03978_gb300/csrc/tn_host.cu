@@ -250,14 +250,14 @@ int route(const Step &s, tn_precision mode, bool tc_ok) {
     // variant's tensor map zero-fills the K tile past k, and its epilogue writes 2 CTAs per SM
     if (s.batch.empty() && tc_mode && tc_ok && lm >= 7 && ln >= 7 && lk >= 3 && lm + ln >= 20)
         return K_TC;
-    // a narrow side of 64 (App. A.2's m, n >= 32 threshold): the 64-column tile, the wide side
-    // as M, when that side has at least 2^12 rows to spread over the SMs
-    if (s.batch.empty() && tc_mode && tc_ok && std::min(lm, ln) == 6 && std::max(lm, ln) >= 12 &&
-        lk >= 3)
+    // a narrow side of 32 or 64 (App. A.2's m, n >= 32 threshold): the 32- or 64-column tile,
+    // the wide side as M, when that side has at least 2^12 rows to spread over the SMs
+    if (s.batch.empty() && tc_mode && tc_ok && (std::min(lm, ln) == 5 || std::min(lm, ln) == 6) &&
+        std::max(lm, ln) >= 12 && lk >= 3)
         return K_TC;
-    // thin steps: a short contraction of a large operand with a small one (at most 16 free
-    // elements), streamed on the CUDA cores at memory speed
-    if (s.batch.empty() && lk >= 1 && lk <= 6 && std::min(lm, ln) <= 4 && std::max(lm, ln) >= 10)
+    // thin steps: a contraction (k <= 1024) of a large operand with a small one (at most 16
+    // free elements), streamed on the CUDA cores at memory speed
+    if (s.batch.empty() && lk >= 1 && lk <= 10 && std::min(lm, ln) <= 4 && std::max(lm, ln) >= 10)
         return K_STREAM;
     // register-tiled GEMM (split along K when the output is small); a contraction of fewer than
     // 16 elements is cheaper as an element-wise pass with coalesced stores
@@ -697,7 +697,7 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
         // consecutive rows (m), the CUDA-core one maps them to consecutive columns (n); give the
         // label at bit 0 of the result to the side whose stores are then contiguous.
         if (st.kernel == K_TC && std::min(st.M.size(), st.N.size()) < 7) {
-            // the 64-column tile: the wide side must be M (tiles of 128 rows)
+            // the 32- or 64-column tile: the wide side must be M (tiles of 128 rows)
             if (st.M.size() < st.N.size()) {
                 std::swap(st.a, st.b);
                 std::swap(st.la, st.lb);
@@ -1076,8 +1076,8 @@ tn_status make_tc_desc(const tn_plan_t *p, const Step &st, int variant, tn::TcGe
     // are always positions 0-2 (C's three lowest labels are among the lowest three of M and
     // of N), which the epilogue's 8-element stores rely on
     // (the persistent short-K variants stage 32-column chunks: 7 row and 5 column bits)
-    const bool pers = variant >= 12 && variant <= 16;
-    tn::sort_tile_bits(7, pers ? 5 : 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+    const bool pers = tn::tc_variant_is_pers(variant);
+    tn::sort_tile_bits(7, pers || bn == 32 ? 5 : 6, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
     if (pers) {
         tn::tc_choose_swizzle(d.tb_src, d.phi, 4);
         tn::tc_choose_swizzle(d.tb_src, d.phi5, 5);

@@ -301,6 +301,7 @@ int tc_variant_bn(int variant);
 int tc_variant_form(int variant);  // 1 = 4M, 2 = 3M, 3 = split 4M (hi/lo planes)
 int tc_num_variants();
 bool tc_variant_fits(int variant, int lk, int ln);
+bool tc_variant_is_pers(int variant);  // the persistent short-K kernel (one CTA per SM)
 // Staging swizzle of the persistent kernel's 128 x 32 chunk: element (row r, column c) sits at
 // r * 32 + (c ^ phi(r)), phi linear in the row bits (phi[i] for row bit i).  Chosen so that the
 // drain warps' writes (lanes = row bits 0..4) and the store warps' reads (lanes = the chunk's

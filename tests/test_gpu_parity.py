@@ -208,6 +208,8 @@ def single_step(rng, lm, ln, lk, scale=1.0, scramble=True):
     ((5, 9, 4), "gemm_simt"),
     ((6, 4, 14), "gemm_simt"),   # few outputs, long contraction: split along K
     ((3, 3, 13), "gemm_simt"),
+    ((5, 5, 13), "gemm_simt"),   # 32 x 32 result, long contraction: the skinny split-K form
+    ((5, 5, 16), "gemm_simt"),
 ])
 def test_single_step_cuda_core_kernels(tn, shape, kernel):
     rng = np.random.default_rng(sum(shape))
@@ -229,11 +231,12 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
 
 @pytest.mark.parametrize("shape", [(12, 4, 4), (10, 2, 6), (4, 11, 3), (13, 0, 2), (11, 3, 1),
                                    (1, 12, 5), (14, 2, 2), (12, 1, 3), (10, 4, 1), (18, 2, 2),
-                                   (3, 17, 1)])
+                                   (3, 17, 1), (12, 3, 8), (10, 4, 10), (3, 13, 9), (11, 0, 7)])
 def test_thin_steps_stream_kernel(tn, shape):
-    # a short contraction of a large operand with one of at most 16 free elements: one thread
-    # per row of the large operand (the small one may be either side); k <= 8 loads rows into
-    # registers, longer k stages them in shared memory; 2 slices in flight too
+    # a contraction (k <= 1024) of a large operand with one of at most 16 free elements: one
+    # thread per row of the large operand (the small one may be either side); k <= 8 loads rows
+    # into registers, longer k stages them in shared memory (the small operand 64 of k at a
+    # time); 2 slices in flight too
     rng = np.random.default_rng(500 + 3 * shape[0] + 5 * shape[1] + shape[2])
     tensors, labels, out = single_step(rng, *shape)
     ref = O.contract(tensors, labels, out, [(0, 1)])
@@ -269,22 +272,32 @@ def test_single_step_tensor_core(tn, mode, shape, form, bk, bn):
     check(got, ref, TOL[mode])
 
 
-@pytest.mark.parametrize("mode,form", [("fp16_scaled", "4m"), ("bf16_scaled", "4m"),
-                                       ("tf32", "4m"), ("fp16_scaled", "3m"), ("tf32", "3m"),
-                                       ("split_fp16", "auto"), ("split_bf16", "auto"),
-                                       ("split_tf32", "auto")])
-@pytest.mark.parametrize("shape", [(13, 6, 6), (12, 6, 9), (6, 13, 7), (14, 6, 3)])
-def test_narrow_results_on_the_64_column_tile(tn, mode, form, shape):
-    # a result 64 wide on one side (App. A.2: n >= 32 keeps the tensor cores busy): the
-    # 128 x 64 tile, the wide side taken as M whichever operand holds it; 2 slices in flight
+@pytest.mark.parametrize("mode,form,bk", [("fp16_scaled", "4m", 0), ("bf16_scaled", "4m", 0),
+                                          ("tf32", "4m", 0), ("fp16_scaled", "4m", 32),
+                                          ("tf32", "4m", 32), ("fp16_scaled", "3m", 0),
+                                          ("tf32", "3m", 0), ("split_fp16", "auto", 0),
+                                          ("split_bf16", "auto", 0), ("split_tf32", "auto", 0)])
+@pytest.mark.parametrize("shape", [(13, 6, 6), (12, 6, 9), (6, 13, 7), (14, 6, 3), (13, 5, 5),
+                                   (5, 14, 5), (12, 5, 8), (13, 5, 3)])
+def test_narrow_results_on_the_64_and_32_column_tiles(tn, mode, form, bk, shape):
+    # a result 64 or 32 wide on one side (App. A.2: n >= 32 keeps the tensor cores busy): the
+    # 128 x 64 or 128 x 32 tile, the wide side taken as M whichever operand holds it; short 4M
+    # contractions on the persistent kernel unless a K tile is asked for (then one tile per
+    # CTA); 2 slices in flight
     rng = np.random.default_rng(900 + 3 * shape[0] + 5 * shape[1] + shape[2])
     tensors, labels, out = single_step(rng, *shape, scale=2.0 ** -8)
     ref = O.contract(tensors, labels, out, [(0, 1)])
     net = tn.Network(tensors, labels, out)
-    plan = tn.Plan(net, [(0, 1)], (), mode=mode, gemm_form=form, sync_each_call=True)
+    plan = tn.Plan(net, [(0, 1)], (), mode=mode, gemm_form=form, tc_bk=bk,
+                   sync_each_call=True)
     si = plan.step_info(0)
-    assert si["kernel_name"] == "gemm_tc" and 17 <= si["tc_variant"] <= 22
-    assert si["log2_m"] == max(shape[0], shape[1]) and si["log2_n"] == 6
+    narrow = min(shape[0], shape[1])
+    if form == "4m" and bk == 0:   # persistent: 29-33 (64 columns), 34-38 (32 columns)
+        lo, hi = (29, 33) if narrow == 6 else (34, 38)
+    else:                          # one tile per CTA: 17-22 (64 columns), 23-28 (32 columns)
+        lo, hi = (17, 22) if narrow == 6 else (23, 28)
+    assert si["kernel_name"] == "gemm_tc" and lo <= si["tc_variant"] <= hi
+    assert si["log2_m"] == max(shape[0], shape[1]) and si["log2_n"] == narrow
     check(plan.contract_host(), ref, TOL[mode])
     plan.close()
     net.close()
@@ -295,7 +308,7 @@ def test_narrow_results_on_the_64_column_tile(tn, mode, form, shape):
     l2 = [[900] + labels[0], labels[1], [900]]
     ref2 = O.contract(t2, l2, out, [(0, 1), (0, 2)])
     got2, info, k2 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode=mode,
-                              gemm_form=form)
+                              gemm_form=form, tc_bk=bk)
     assert info["slices_in_flight"] == 2 and k2[0] == "gemm_tc"
     check(got2, ref2, TOL[mode])
 
@@ -422,7 +435,9 @@ def test_short_contraction_on_tensor_cores(tn, shape):
 
 @pytest.mark.parametrize("mode", ["fp16_scaled", "tf32"])
 @pytest.mark.parametrize("lm,ln,lk,nsl", [(12, 10, 8, 3), (7, 7, 9, 0), (9, 8, 8, 2),
-                                         (12, 10, 6, 3), (10, 10, 4, 0), (11, 9, 3, 0)])
+                                         (12, 10, 6, 3), (10, 10, 4, 0), (11, 9, 3, 0),
+                                         (14, 6, 8, 2), (13, 5, 4, 0), (6, 14, 4, 1),
+                                         (15, 5, 6, 1), (13, 6, 3, 0)])
 def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
     # short contractions run on the persistent kernel (variant 12 / 13): each CTA walks tiles of
     # all slices in flight with a double-buffered accumulator; fewer tiles than SMs included
@@ -438,6 +453,8 @@ def test_persistent_short_k_kernel_over_slices(tn, mode, lm, ln, lk, nsl):
     # rows of 16 / 32 / 64 bytes hold exactly k for k = 8 / 16 (16-bit) and k = 8 (TF32)
     k = lk - nsl
     want = {3: 16}.get(k, 13) if mode == "tf32" else {3: 14, 4: 15}.get(k, 12)
+    # results 64 or 32 wide: the same kernel with 64- or 32-column tiles (variants + 17 / + 22)
+    want += {6: 17, 5: 22}.get(min(lm, ln), 0)
     assert si["kernel_name"] == "gemm_tc" and si["tc_variant"] == want
     check(plan.contract_host(), ref, TOL[mode])
     plan.close()
