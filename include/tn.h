@@ -147,6 +147,9 @@ typedef struct {
     int32_t num_compensated;       /* tensor-core steps run with compensated hi/lo products   */
     double eps_predicted;          /* the error model's amplitude relative L2 error of the
                                       plan (precision policy above)                          */
+    int32_t num_open_sliced;       /* sliced labels that are open: amplitude batches of
+                                      2^(num_open - num_open_sliced) amplitudes              */
+    int32_t reserved[3];
 } tn_plan_info;
 
 typedef struct {
@@ -209,7 +212,11 @@ tn_status tn_network_set_data(tn_network_t *net, const double *const *data);
  *   path              path_len = num_tensors - 1 pairs (a, b): tensor a becomes the
  *                     contraction of a and b and id b is retired (Sec. 3.1)
  *   sliced_labels     bonds cut by slicing (Sec. 3.2); bit j of a slice id fixes
- *                     sliced_labels[j]; open labels cannot be sliced
+ *                     sliced_labels[j].  An open label may be sliced too: it then splits the
+ *                     amplitudes into batches instead of a sum (open-qubit amplitude batches run
+ *                     in the same launches as the slices): a slice's result is added to the
+ *                     block of amps whose index bits for those labels equal the slice id's
+ *                     bits for them, and the intermediates no longer carry those labels
  *   mode              tn_precision
  *   opts              may be NULL (defaults)
  * The plan decides the memory order of every intermediate so that each dense step reads its

@@ -184,6 +184,8 @@ struct tn_plan {
     tn_precision mode = TN_PREC_C64;
     tn_plan_options opts{};
     std::vector<int> sliced;
+    std::vector<int> root_open;  // the open labels the root keeps (open minus sliced), in order
+    tn::AccMap acc;              // where root elements and slices go in amps
     std::vector<Tensor> tensors;
     std::vector<Step> steps;
     std::vector<Planar> planars;
@@ -539,10 +541,6 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
             delete p;
             return fail(TN_ERR_INVALID_ARG, "sliced label %d is not in the network", l);
         }
-        if (std::find(net->open.begin(), net->open.end(), l) != net->open.end()) {
-            delete p;
-            return fail(TN_ERR_INVALID_ARG, "open label %d cannot be sliced", l);
-        }
         if (std::find(p->sliced.begin(), p->sliced.end(), l) != p->sliced.end()) {
             delete p;
             return fail(TN_ERR_INVALID_ARG, "sliced label %d repeated", l);
@@ -622,8 +620,28 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
     for (int i = 0; i < nt; ++i)
         if (alive[i]) { root_id = i; break; }
     p->root = cur[root_id];
+    // the root keeps the open labels that are not sliced; sliced open labels select the block
+    // of the amplitudes a slice is added to
+    for (int l : net->open)
+        if (!is_sliced(l)) p->root_open.push_back(l);
     {
-        std::vector<int> rl = lab[root_id], ol = net->open;
+        const int no = (int)net->open.size();
+        auto open_bit = [&](int l) {
+            return no - 1 - (int)(std::find(net->open.begin(), net->open.end(), l) -
+                                  net->open.begin());
+        };
+        const int nr = (int)p->root_open.size();
+        p->acc.nroot = nr;
+        for (int r = 0; r < nr; ++r) p->acc.root_pos[r] = (int8_t)open_bit(p->root_open[nr - 1 - r]);
+        for (int j = 0; j < (int)p->sliced.size(); ++j)
+            if (std::find(net->open.begin(), net->open.end(), p->sliced[j]) != net->open.end()) {
+                p->acc.bj[p->acc.nb] = (int8_t)j;
+                p->acc.bpos[p->acc.nb] = (int8_t)open_bit(p->sliced[j]);
+                p->acc.nb++;
+            }
+    }
+    {
+        std::vector<int> rl = lab[root_id], ol = p->root_open;
         std::sort(rl.begin(), rl.end());
         std::sort(ol.begin(), ol.end());
         if (rl != ol) {
@@ -686,7 +704,7 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
                        st.kernel == K_TC && st.form != kFormSplit;
 
     // 3. layout: root first, then every step's operands from its result's order
-    p->tensors[p->root].order = net->open;
+    p->tensors[p->root].order = p->root_open;
     for (int s = path_len - 1; s >= 0; --s) {
         Step &st = p->steps[s];
         const std::vector<int> &co = p->tensors[st.c].order;
@@ -725,7 +743,7 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
         p->tensors[st.a].order = oa;
         p->tensors[st.b].order = ob;
     }
-    if (path_len == 0) p->tensors[p->root].order = net->open;
+    if (path_len == 0) p->tensors[p->root].order = p->root_open;
 
     // 4. tensor-core operands get planar 16-bit copies.  When the operand's producer is a GEMM
     //    step of the slice loop (with whole 64 x 64 tiles to spare), that producer writes the
@@ -752,10 +770,15 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
                 // subnormals, so those are split from complex64 with their measured max-abs.
                 // A CUDA-core producer writes directly only with whole 64 x 64 tiles, and then
                 // never splits K (its epilogue must hold final sums).
+                // A CUDA-core producer that would split K (judged at one slice in flight, its
+                // fewest tiles) writes complex64 instead: a long contraction over few tiles
+                // needs the split more than the saved conversion pass.
                 const Step &pr = p->steps[X.producer];
                 q.direct = pr.dep && (pr.kernel == K_TC ||
                                       (pr.kernel == K_GEMM && pr.M.size() >= 6 &&
-                                       pr.N.size() >= 6));
+                                       pr.N.size() >= 6 &&
+                                       tn::gemm_simt_splits((int)pr.M.size(), (int)pr.N.size(),
+                                                            (int)pr.K.size(), 1) == 1));
             }
             (side ? st.pb : st.pa) = (int)p->planars.size();
             p->planars.push_back(q);
@@ -1515,6 +1538,7 @@ tn_status tn_plan_get_info(const tn_plan_t *p, tn_plan_info *out) {
     mp->pending_bind.clear();
     out->bind_ms = p->bind_ms;
     out->bind_launches = p->bind_timed;
+    out->num_open_sliced = p->acc.nb;
     out->num_single_pass = p->single_pass;
     out->num_compensated = p->compensated;
     out->eps_predicted = p->eps_pred;
@@ -1607,6 +1631,21 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
     return TN_OK;
 }
 
+// FP64 sum of the ns slices in flight (ids s0..) into the amplitudes (Sec. 5: the answer is the
+// sum of the sub-task results); with sliced open labels each slice goes to its own block.
+static cudaError_t accumulate(tn_plan_t *p, const Tensor &R, int64_t nout, int64_t ns, int64_t s0,
+                              void *amps_dev, cudaStream_t stream) {
+    float2 *arena = reinterpret_cast<float2 *>(p->arena);
+    double2 *amps = reinterpret_cast<double2 *>(amps_dev);
+    if (p->acc.nb == 0)
+        return tn::launch_accumulate(arena + R.off, R.dep ? nout : 0, nout, R.dep ? ns : 1, amps,
+                                     stream);
+    // a root that does not depend on the slice (possible only when nothing below it is sliced)
+    // is still added once per slice: each slice id names its own block
+    return tn::launch_accumulate_batched(arena + R.off, R.dep ? nout : 0, nout, ns, s0, p->acc,
+                                         amps, stream);
+}
+
 tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void *amps_dev,
                       void *stream_) {
     g_err.clear();
@@ -1653,8 +1692,7 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
                     if (s != TN_OK) return s;
                 }
             p->tuned = true;
-            TN_CUDA(tn::launch_accumulate(arena + R.off, R.dep ? nout : 0, nout, R.dep ? ns : 1,
-                                          reinterpret_cast<double2 *>(amps_dev), stream));
+            TN_CUDA(accumulate(p, R, nout, ns, s0, amps_dev, stream));
             p->launches++;
             continue;
         }
@@ -1690,8 +1728,7 @@ tn_status tn_contract(tn_plan_t *p, int64_t slice_begin, int64_t slice_end, void
                     if (s != TN_OK) return s;
                 }
         }
-        TN_CUDA(tn::launch_accumulate(arena + R.off, R.dep ? nout : 0, nout, R.dep ? ns : 1,
-                                      reinterpret_cast<double2 *>(amps_dev), stream));
+        TN_CUDA(accumulate(p, R, nout, ns, s0, amps_dev, stream));
         p->launches++;
     }
     if (p->opts.sync_each_call) {

@@ -232,6 +232,18 @@ cudaError_t launch_bind_tiled(const BindTiled &b, const double2 *src, float2 *ar
                               int64_t slice_begin, int64_t slices, cudaStream_t st);
 cudaError_t launch_accumulate(const float2 *root, int64_t root_sstride, int64_t n, int64_t slices,
                               double2 *amps, cudaStream_t st);
+// Where the root's elements go when open labels are sliced (amplitude batches): root bit r is
+// amplitude-index bit root_pos[r]; bit bj[i] of the slice id is amplitude-index bit bpos[i].
+struct AccMap {
+    int32_t nroot = 0, nb = 0;
+    int8_t root_pos[TN_MAXR];
+    int8_t bj[TN_MAXR];
+    int8_t bpos[TN_MAXR];
+};
+// amps[root element mapped by m, slice s0 + s] += root[s][x], slices in increasing order
+cudaError_t launch_accumulate_batched(const float2 *root, int64_t root_sstride, int64_t n,
+                                      int64_t slices, int64_t s0, const AccMap &m,
+                                      double2 *amps, cudaStream_t st);
 cudaError_t launch_readout(const double2 *amps, int64_t n, double *partial, int32_t n_partial,
                            cudaStream_t st);
 cudaError_t launch_zero_f64(double2 *p, int64_t n, cudaStream_t st);

@@ -287,6 +287,30 @@ __global__ void k_accumulate(const float2 *root, int64_t sstride, int64_t n, int
     }
 }
 
+// The same with sliced open labels (amplitude batches, Sec. 3.2 slicing applied to open
+// bonds): slice s0 + s adds its root into the block of amps that its bits for those labels
+// select.  A thread owns one root element and walks the slices in increasing order; different
+// threads write different amplitudes, and slices of one block are summed in slice order.
+__global__ void k_accumulate_batched(const float2 *root, int64_t sstride, int64_t n,
+                                     int64_t slices, int64_t s0, const AccMap m,
+                                     double2 *amps) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t xo = deposit((uint64_t)x, m.nroot, m.root_pos);
+        for (int64_t s = 0; s < slices; ++s) {
+            const uint64_t sig = (uint64_t)(s0 + s);
+            uint64_t o = xo;
+            for (int i = 0; i < m.nb; ++i)
+                if ((sig >> m.bj[i]) & 1ull) o |= 1ull << m.bpos[i];
+            const float2 v = root[s * sstride + x];
+            double2 a = amps[o];
+            a.x += (double)v.x;
+            a.y += (double)v.y;
+            amps[o] = a;
+        }
+    }
+}
+
 // FP64 readout, pass 1: block partial sums of p = |a|^2 and p^2 (fixed order per block).
 __global__ void __launch_bounds__(256) k_readout_partial(const double2 *amps, int64_t n,
                                                          double *partial) {
@@ -509,6 +533,14 @@ cudaError_t launch_bind_tiled(const BindTiled &b, const double2 *src, float2 *ar
 cudaError_t launch_accumulate(const float2 *root, int64_t root_sstride, int64_t n, int64_t slices,
                               double2 *amps, cudaStream_t st) {
     k_accumulate<<<grid_for(n, 256), 256, 0, st>>>(root, root_sstride, n, slices, amps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_batched(const float2 *root, int64_t root_sstride, int64_t n,
+                                      int64_t slices, int64_t s0, const AccMap &m,
+                                      double2 *amps, cudaStream_t st) {
+    k_accumulate_batched<<<grid_for(n, 256), 256, 0, st>>>(root, root_sstride, n, slices, s0, m,
+                                                          amps);
     return cudaGetLastError();
 }
 

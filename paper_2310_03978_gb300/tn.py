@@ -50,7 +50,8 @@ class PlanInfo(C.Structure):
                 ("num_generic_steps", C.c_int32), ("kernel_launches", C.c_int64),
                 ("bind_ms", C.c_double), ("bind_launches", C.c_int64),
                 ("num_single_pass", C.c_int32), ("num_compensated", C.c_int32),
-                ("eps_predicted", C.c_double)]
+                ("eps_predicted", C.c_double), ("num_open_sliced", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class StepInfo(C.Structure):

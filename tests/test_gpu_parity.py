@@ -717,6 +717,56 @@ def test_bench_circuit_on_an_annealed_path(tn):
     assert abs(x_got - x_ref) / abs(x_ref) <= 1e-3
 
 
+# ------------------------------------------------------------------ amplitude batches (a10)
+@pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
+def test_sliced_open_labels_give_amplitude_batches(tn, mode):
+    # two of the six open labels sliced along with three bonds: 32 slices, each added into the
+    # amplitude block its open bits select; whole range, split ranges and graph replay all give
+    # the oracle's (unsliced) amplitudes
+    wl = W.small_workload()
+    net = wl.network
+    ref = O.contract_network(net, wl.path)
+    bonds = W.greedy_slices(net.labels, net.open_labels, wl.path, 3)
+    sliced = bonds + [net.open_labels[4], net.open_labels[1]]  # slice bits 3, 4: open bits
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.Plan(tnet, wl.path, sliced, mode=mode, sync_each_call=True,
+                   max_slices_in_flight=6)
+    info = plan.info()
+    assert info["num_open_sliced"] == 2 and info["num_slices"] == 32
+    check(plan.contract_host(), ref, TOL[mode])
+    split = plan.contract_host(0, 13) + plan.contract_host(13, 32)
+    check(split, ref, TOL[mode])
+    # slices 0..7 have 0 for both sliced open labels (amplitude bits 1 and 4): only that block
+    # of the amplitudes is set
+    part = plan.contract_host(0, 8)
+    idx = np.arange(64)
+    in_block = ((idx >> (5 - 4)) & 1) == 0
+    in_block &= ((idx >> (5 - 1)) & 1) == 0
+    assert np.all(part[~in_block] == 0)
+    plan.close()
+    graph = tn.Plan(tnet, wl.path, sliced, mode=mode, use_graph=True, max_slices_in_flight=8)
+    for _ in range(2):
+        check(graph.contract_host(), ref, TOL[mode])
+    graph.close()
+    tnet.close()
+
+
+def test_all_open_circuit_in_64_amplitude_batches(tn):
+    # every qubit of a 12-qubit circuit open, six of them sliced: 64 batches of 64 amplitudes in
+    # one call, against the state vector
+    circ = W.random_circuit(3, 4, 8, seed=21)
+    net = W.build_network(circ, list(range(12)), {})
+    path = W.greedy_path(net.labels, net.open_labels)
+    sv = O.statevector(12, circ.gates)
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    plan = tn.Plan(tnet, path, net.open_labels[:6], mode="c64", use_graph=True)
+    assert plan.info()["num_slices"] == 64 and plan.info()["slices_in_flight"] == 64
+    for _ in range(2):
+        check(plan.contract_host(), sv, TOL["c64"])
+    plan.close()
+    tnet.close()
+
+
 # ------------------------------------------------------------------ batched small steps (a10)
 @pytest.mark.parametrize("mode", ["c64", "fp16_scaled"])
 def test_chained_small_steps_match_single_launches(tn, mode):
