@@ -71,7 +71,7 @@ def parse_args():
                     help="1: time the headline steps as CUDA-graph replays and measure the "
                          "dominant kernel in a separate profiled pass of the same steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--sa-alpha", type=float, default=512.0,
+    ap.add_argument("--sa-alpha", type=float, default=0.0,
                     help="weight of the memory term T_mc in the annealing score (multiply-adds "
                          "per element moved)")
     ap.add_argument("--small-steps", type=int, default=50,
@@ -82,6 +82,11 @@ def parse_args():
                          "all slices; prints its own JSON line")
     ap.add_argument("--sycamore53-modes", default="",
                     help="comma-separated precision modes for --sycamore53 (default: --mode)")
+    ap.add_argument("--table3", action="store_true",
+                    help="the Table 3 shape on the 45-qubit 14-cycle circuit (time and eps_L2^2 "
+                         "against the number of single-pass dense steps; error budgets)")
+    ap.add_argument("--table3-slices", type=int, default=1024,
+                    help="contiguous slices timed per row of --table3")
     ap.add_argument("--c53-cycles", type=int, default=16, choices=[16, 20],
                     help="cycles of the 53-qubit circuit for --sycamore53 / --step-profile")
     ap.add_argument("--config4-batches", type=int, default=2,
@@ -99,13 +104,15 @@ def parse_args():
     ap.add_argument("--sparse-steps", type=int, default=3,
                     help="also time a sparse-state contraction (24-qubit circuit, all qubits "
                          "open, 4096 sampled bitstrings); 0 = skip")
-    ap.add_argument("--sa-topk", type=int, default=4,
-                    help="the annealed path runs in the mixed policy with this many single-pass "
-                         "FP16 dense steps (the rest compensated) when --mode is fp16_scaled")
+    ap.add_argument("--sa-greedy-trials", type=int, default=20,
+                    help="random greedy initial trees per annealing chain of the annealed path")
+    ap.add_argument("--sa-budget", type=float, default=1e-3,
+                    help="predicted amplitude error budget of the annealed path's plan")
     ap.add_argument("--sa-steps", type=int, default=3,
                     help="also time the bench circuit along an annealed path with dynamic "
                          "slicing (same amplitudes, less work); 0 = skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--feed-tc", action="store_true",
                     help="single-step microbench: the step's result feeds a second tensor-core "
@@ -171,6 +178,50 @@ def oracle_sample(wl, seconds):
     return {"seconds": dt, "flops": fl, "rate": rate, "outputs": outs,
             "fixed_labels": len(order) - keep, "step": di, "threads": O.num_threads(),
             "shape": "m=2^%d n=2^%d k=2^%d" % (len(st.m_labels), len(st.n_labels), lk)}
+
+
+def oracle_small_circuit(repeats):
+    """The whole oracle contraction of the 12-qubit 3x4 8-cycle circuit (its 64 amplitudes, the
+    plain complex64 configuration): seconds of each of ``repeats`` runs."""
+    from oracle import oracle as O
+    from paper_2310_03978_gb300 import workload as W
+    wl = W.small_workload()
+    O.contract_network(wl.network, wl.path)  # warm
+    out = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        O.contract_network(wl.network, wl.path)
+        out.append(time.perf_counter() - t0)
+    return out
+
+
+def oracle_child(task, threads):
+    """Run an oracle timing (``task``: {"kind": "sample", "seconds": s} or {"kind": "small",
+    "repeats": r}) in a child process with OMP_NUM_THREADS = ``threads`` (None: all cores), so
+    the oracle's thread pool is sized at load; returns the child's JSON result."""
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child",
+                        json.dumps(task)], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_child(spec):
+    from oracle import oracle as O
+    from paper_2310_03978_gb300 import workload as W
+    task = json.loads(spec)
+    if task["kind"] == "sample":
+        smp = oracle_sample(W.bench_workload(), task["seconds"])
+        print(json.dumps({"rate": smp["rate"], "seconds": smp["seconds"],
+                          "outputs": smp["outputs"], "threads": smp["threads"],
+                          "shape": smp["shape"]}))
+    else:
+        secs = oracle_small_circuit(task["repeats"])
+        print(json.dumps({"seconds": secs, "median_s": statistics.median(secs),
+                          "threads": O.num_threads()}))
 
 
 # ---------------------------------------------------------------------------------- clocks
@@ -301,6 +352,17 @@ def time_steps(torch, step, steps, stream):
     return start.elapsed_time(end)
 
 
+def time_each(torch, step, steps, stream):
+    """CUDA-event time of each of ``steps`` calls (ms), recorded on ``stream`` around each."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        step()
+        ev[i + 1].record(stream)
+    ev[-1].synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+
+
 def time_contract(torch, plan, amps, steps, stream):
     return time_steps(torch, lambda: plan.contract(amps, stream=stream), steps, stream)
 
@@ -370,7 +432,8 @@ def run_ours(args, rank, world, local_rank):
                 time.sleep(0.5)
             barrier()
             torch.cuda.synchronize()
-            gms = time_steps(torch, lambda: contract(gplan, amps), steps, stream)
+            each = time_each(torch, lambda: contract(gplan, amps), steps, stream)
+            gms = sum(each)
             torch.cuda.synchronize()
             barrier()
             gclk = sampler.stop() if sampler else None
@@ -383,6 +446,7 @@ def run_ours(args, rank, world, local_rank):
             res["clocks"] = gclk
             res["launches"] = glaunch
             res["graph"] = True
+            res["each_ms"] = each
             return res
         plan = tn.Plan(net, wl.path, wl.sliced, mode=mode, profile=True,
                        autotune=bool(args.autotune), mixed_topk=topk, eps_budget=budget)
@@ -441,14 +505,17 @@ def run_ours(args, rank, world, local_rank):
         sa_path, sa_sliced, sa_info = tn.path_optimize(
             wl.network.labels, wl.network.open_labels, wl.path, seed=SA_SEED, sweeps=1000,
             sweeps_per_slice=40, sweeps_final=500, t_start=0.03, t_end=0.001,
-            max_log2_size=28, chains=16, alpha=args.sa_alpha)
+            max_log2_size=28, chains=16, alpha=args.sa_alpha,
+            greedy_trials=args.sa_greedy_trials)
         sa_opt_s = time.perf_counter() - t0
-        # along this path single-pass FP16 on every dense step misses the 1e-3 ideal-XEB bar
-        # (1.6e-3): the mixed policy keeps the sa_topk largest steps single-pass
-        sa_mode = "mixed" if args.mode == "fp16_scaled" else args.mode
-        sa_topk = args.sa_topk if sa_mode == "mixed" else args.mixed_topk
+        # single-pass FP16 on every dense step of an annealed path can miss the 1e-3 ideal-XEB
+        # bar (1.6e-3 on the greedy-started one): the error budget keeps the predicted amplitude
+        # error at sa_budget, single-pass on the largest steps, the rest compensated
+        sa_mode = args.mode
+        sa_topk = args.mixed_topk
         splan = tn.Plan(net, sa_path, sa_sliced, mode=sa_mode, use_graph=True,
-                        autotune=bool(args.autotune), mixed_topk=sa_topk)
+                        autotune=bool(args.autotune), mixed_topk=sa_topk,
+                        eps_budget=args.sa_budget)
         amps = torch.zeros(1 << n_open, dtype=torch.complex128, device=dev)
         splan.contract(amps, stream=stream)
         torch.cuda.synchronize()
@@ -461,7 +528,8 @@ def run_ours(args, rank, world, local_rank):
         si = splan.info()
         splan.close()
         del amps
-        sa = {"mode": sa_mode, "topk": sa_topk,
+        sa = {"mode": sa_mode, "topk": sa_topk, "single_pass": si["num_single_pass"],
+              "compensated": si["num_compensated"], "eps_predicted": si["eps_predicted"],
               "ms": sms, "flops": si["tcc_per_slice"] * si["num_slices"] + si["tcc_invariant"],
               "slices": si["num_slices"], "max_log2": si["max_log2_size"], "opt_s": sa_opt_s,
               "info": sa_info, "result": sa_result}
@@ -491,6 +559,36 @@ def run_ours(args, rank, world, local_rank):
                  "steps": args.small_steps,
                  "amp_rel_l2_vs_statevector": (rel_l2(sm_result, sm_ref)
                                                if sm_ref is not None else None)}
+
+    # open-qubit amplitude batches in one launch: the same 12-qubit circuit with every qubit open
+    # and six of them sliced, 64 batches of 64 amplitudes per call (graph replay)
+    amp_batches = None
+    if world == 1 and args.small_steps > 0:
+        wl_s = W.small_workload()
+        net_b = W.build_network(wl_s.circuit, list(range(wl_s.circuit.n_qubits)), {})
+        path_b = W.greedy_path(net_b.labels, net_b.open_labels)
+        tnet_b = tn.Network(net_b.tensors, net_b.labels, net_b.open_labels)
+        bplan = tn.Plan(tnet_b, path_b, net_b.open_labels[:6], mode="c64", use_graph=True)
+        amps = torch.zeros(1 << len(net_b.open_labels), dtype=torch.complex128, device=dev)
+        bplan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        b_result = amps.cpu().numpy().copy()
+        for _ in range(3):
+            bplan.contract(amps, stream=stream)
+        torch.cuda.synchronize()
+        b_ms = time_steps(torch, lambda: bplan.contract(amps, stream=stream), args.small_steps,
+                          stream) / args.small_steps
+        b_info = bplan.info()
+        bplan.close()
+        tnet_b.close()
+        del amps
+        b_ref = golden_amps("sycamore_3x4_c8_all_open")
+        amp_batches = {"workload": "sycamore_3x4_c8_all_open: 12 qubits open, 6 sliced",
+                   "mode": "c64", "batches": b_info["num_slices"], "amplitudes_per_batch": 64,
+                   "slices_in_flight": b_info["slices_in_flight"], "us_per_call": b_ms * 1e3,
+                   "us_per_64_amplitudes": b_ms * 1e3 / b_info["num_slices"],
+                   "amp_rel_l2_vs_statevector": (rel_l2(b_result, b_ref)
+                                                 if b_ref is not None else None)}
 
     # sparse-state contraction (Sec. 3.3): the amplitudes of 4096 sampled bitstrings of a
     # 24-qubit circuit with every qubit open, along an annealed path
@@ -561,6 +659,9 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": head["ms"],
+        "ms_per_step_median": statistics.median(head["each_ms"]) if head.get("each_ms") else None,
+        "ms_per_step_min_max": ([min(head["each_ms"]), max(head["each_ms"])]
+                                if head.get("each_ms") else None),
         "s_per_batch": head["ms"] / 1e3,
         "higher_is_better": True,
         "scaling": args.scaling,
@@ -607,12 +708,20 @@ def run_ours(args, rank, world, local_rank):
             "effective_tflops": sa["flops"] / (sa["ms"] / 1e3) / 1e12,
             "flops_per_batch": sa["flops"], "slices": sa["slices"],
             "max_intermediate_log2": sa["max_log2"], "steps": args.sa_steps,
-            "mode": sa["mode"], **({"mixed_topk": sa["topk"]} if sa["mode"] == "mixed" else {}),
+            "mode": sa["mode"], "eps_budget": args.sa_budget,
+            "single_pass_steps": sa["single_pass"], "compensated_steps": sa["compensated"],
+            "eps_predicted": sa["eps_predicted"],
             "optimiser_s": sa["opt_s"], "optimiser": "tn_path_optimize seed %d, 16 chains, "
-            "1000 + 40 per slice + 500 sweeps, T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
-            % (SA_SEED, args.sa_alpha)}
+            "%d random greedy trees per chain, 1000 + 40 per slice + 500 sweeps, "
+            "T 0.03 -> 0.001, alpha %g, beta 0, cap 2^28"
+            % (SA_SEED, args.sa_greedy_trials, args.sa_alpha)}
     if small is not None:
         line["small_circuit"] = small
+    if amp_batches is not None:
+        if small is not None:
+            amp_batches["speedup_over_one_batch_per_call"] = (
+                small["us_per_batch"] / amp_batches["us_per_64_amplitudes"])
+        line["amplitude_batches"] = amp_batches
     for key, cycles in (("config4", 16), ("config5", 20)):
         if key in c53:
             line[key] = {"workload": "sycamore53_6x9_c%d_open12" % cycles, "qubits": 53,
@@ -621,13 +730,26 @@ def run_ours(args, rank, world, local_rank):
         line["sparse_state"] = sparse_line(args, sparse)
     if world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(wl, args.cpu_seconds)
+        one = oracle_child({"kind": "sample", "seconds": args.cpu_seconds / 2}, 1)
+        sm_all = oracle_child({"kind": "small", "repeats": 5}, None)
+        sm_one = oracle_child({"kind": "small", "repeats": 5}, 1)
         line["cpu_baseline"] = {
             "value": smp["rate"] / 1e12, "unit": "TFLOPS", "cores": smp["threads"],
             "kind": "oracle",
             "sample": "oracle einsum of the dominant step (%s) on %d output elements "
                       "(%d free labels fixed), %.1f s; s per batch extrapolated %.1f"
                       % (smp["shape"], smp["outputs"], smp["fixed_labels"], smp["seconds"],
-                         head["flops"] / smp["rate"])}
+                         head["flops"] / smp["rate"]),
+            "one_core": ({"value": one["rate"] / 1e12, "unit": "TFLOPS", "cores": one["threads"],
+                          "sample": "the same step on %d output elements, %.1f s"
+                                    % (one["outputs"], one["seconds"]),
+                          "s_per_batch_extrapolated": head["flops"] / one["rate"]}
+                         if "rate" in one else one),
+            "small_circuit": {
+                "workload": "sycamore_3x4_c8_open6 (64 amplitudes), whole oracle contraction",
+                "s_per_batch_median": sm_all.get("median_s"), "cores": sm_all.get("threads"),
+                "s_per_batch_median_one_core": sm_one.get("median_s"), "repeats": 5,
+                "gpu_us_per_batch": small["us_per_batch"] if small else None}}
     print(json.dumps(line))
 
 
@@ -833,6 +955,99 @@ def run_sycamore53(args):
                           "qubits": 53, "cycles": args.c53_cycles, "open_qubits": 12,
                           **{k: v for k, v in res.items() if k != "modes"}},
                **rec}
+
+
+def read_slice_golden(name):
+    """Stored FP64 oracle amplitudes of a few slices of a stored-path workload
+    (tests/golden/make_golden.py): (slice ids, amplitudes summed in increasing slice order)."""
+    path = os.path.join(ROOT, "tests", "golden", name + ".slices.amps.txt")
+    if not os.path.exists(path):
+        return None, None
+    slices = None
+    for line in open(path):
+        if line.startswith("# slices:"):
+            slices = [int(x) for x in line.split(":", 1)[1].split()]
+            break
+    rows = np.loadtxt(path, comments="#")
+    return slices, rows[:, 0] + 1j * rows[:, 1]
+
+
+def run_table3(args):
+    """The shape of the paper's Table 3 (Sec. 4.3) on the 45-qubit 14-cycle Sycamore-shaped
+    circuit (5x9 grid, 12 open qubits, stored annealed path with 2^13 slices at the 2^26 cap):
+    the k dense steps with the largest T_cc single-pass, the others compensated, for the paper's
+    pair (TF32 / 3xTF32) and for FP16 / 3xFP16; per k the time of a contiguous range of slices
+    (relative to all single-pass), the share of T_cc made single-pass, and the amplitude error
+    of the stored slices against the FP64 oracle (eps_L2^2, Eq. l2_squared_error; rel. L2; per
+    entry).  Then the error budget: the k the precision policy picks for a few budgets, with its
+    prediction and the measured error.  One JSON line per row."""
+    import torch
+    from paper_2310_03978_gb300 import tn
+    name = "sycamore45_5x9_c14_open12"
+    net, path, sliced, pdesc = stored_path(name)
+    gold_slices, gold = read_slice_golden(name)
+    stream = torch.cuda.current_stream()
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    nout = 1 << len(net.open_labels)
+    amps = torch.zeros(nout, dtype=torch.complex128, device="cuda")
+    part = torch.zeros(nout, dtype=torch.complex128, device="cuda")
+
+    def run(mode, topk=0, budget=0.0):
+        plan = tn.Plan(tnet, path, sliced, mode=mode, use_graph=True, autotune=True,
+                       mixed_topk=topk, eps_budget=budget)
+        info = plan.info()
+        sb = info["slices_in_flight"]
+        for w in range(2):  # the first batch autotunes
+            plan.contract(amps, w * sb, (w + 1) * sb, stream=stream)
+        torch.cuda.synchronize()
+        n = min(args.table3_slices, info["num_slices"] - 2 * sb)
+        ms = time_steps(torch, lambda: plan.contract(amps, 2 * sb, 2 * sb + n, stream=stream),
+                        1, stream)
+        got = None
+        if gold_slices:
+            got = np.zeros(nout, dtype=np.complex128)
+            for s in sorted(gold_slices):  # summed in increasing slice order, like the oracle
+                part.zero_()
+                plan.contract(part, s, s + 1, stream=stream)
+                torch.cuda.synchronize()
+                got += part.cpu().numpy()
+        # T_cc of the single-pass dense steps over all T_cc (per slice)
+        steps = [plan.step_info(i) for i in range(info["num_steps"])]
+        single = sum(st["tcc"] for st in steps if st["kernel"] == 3 and st["gemm_form"] in (1, 2)
+                     and st["slice_dependent"])
+        plan.close()
+        rec = {"mode": mode, "single_pass_steps": info["num_single_pass"],
+               "compensated_steps": info["num_compensated"],
+               "tcc_ratio_single_pass": single / info["tcc_per_slice"],
+               "ms_per_slice": ms / n, "slices_timed": n, "eps_predicted": info["eps_predicted"]}
+        if got is not None:
+            rec.update({"eps_l2sq": eps_l2sq(got, gold), "amp_rel_l2": rel_l2(got, gold),
+                        "amp_max_rel": max_entry_err(got, gold)})
+        return rec, info
+
+    base = {"metric": "Table 3 shape: time and eps_L2^2 against k single-pass dense steps",
+            "workload": name, "qubits": 45, "cycles": 14, "open_qubits": 12,
+            "slices": 1 << len(sliced), "reference": "FP64 oracle, slices %s" % gold_slices,
+            **pdesc}
+    for fast, slow in (("tf32", "split_tf32"), ("fp16_scaled", "split_fp16")):
+        rows = []
+        r0, info = run(slow)
+        rows.append(dict(r0, k=0))
+        ndense = r0["compensated_steps"]
+        for k in [k for k in (1, 2, 4, 8, 16, 32, 64) if k < ndense] + [ndense]:
+            r, _ = run(fast, topk=k, budget=1.0)  # a loose budget: k exactly
+            rows.append(dict(r, k=k))
+        t_all = rows[-1]["ms_per_slice"]
+        for r in rows:
+            r["relative_time"] = r["ms_per_slice"] / t_all
+            print(json.dumps({**base, "pair": "%s / %s" % (fast, slow), "dense_steps": ndense,
+                              "steps": info["num_steps"],
+                              "flops_per_slice": info["tcc_per_slice"], **r}), flush=True)
+    for mode in ("fp16_scaled", "bf16_scaled", "tf32"):
+        for budget in (1e-4, 1e-3, 5e-3):
+            r, _ = run(mode, budget=budget)
+            print(json.dumps({**base, "budget": budget, **r}), flush=True)
+    tnet.close()
 
 
 def measure_sparse(args, dev, stream):
@@ -1054,6 +1269,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.oracle_child:
+        run_oracle_child(args.oracle_child)
+        return
     if args.impl == "reference":
         from oracle import oracle as O
         O.build()
@@ -1070,6 +1288,11 @@ def main():
         return
     if args.step_profile:
         run_step_profile(args)
+        return
+    if args.table3:
+        import torch
+        torch.cuda.set_device(local_rank)
+        run_table3(args)
         return
     if args.sycamore53:
         import torch

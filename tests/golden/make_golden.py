@@ -109,6 +109,12 @@ if __name__ == "__main__":
         write_slices("sycamore45_5x9_c14_open12", 4)
     if "small" in which:
         write("sycamore_3x4_c8_open6", W.small_workload())
+        # the same circuit with every qubit open (the amplitude-batch measurement)
+        wl = W.small_workload()
+        n = wl.circuit.n_qubits
+        net = W.build_network(wl.circuit, list(range(n)), {})
+        write("sycamore_3x4_c8_all_open", W.Workload("sycamore_3x4_c8_all_open", wl.circuit, net,
+                                                     [], []))
     if "bench" in which:
         write("sycamore_5x6_c14_open10_s4", W.bench_workload())
     if "sparse" in which:
