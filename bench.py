@@ -71,7 +71,7 @@ def parse_args():
                     help="1: time the headline steps as CUDA-graph replays and measure the "
                          "dominant kernel in a separate profiled pass of the same steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--sa-alpha", type=float, default=0.0,
+    ap.add_argument("--sa-alpha", type=float, default=512.0,
                     help="weight of the memory term T_mc in the annealing score (multiply-adds "
                          "per element moved)")
     ap.add_argument("--small-steps", type=int, default=50,
@@ -92,11 +92,13 @@ def parse_args():
     ap.add_argument("--config4-batches", type=int, default=2,
                     help="53-qubit 16-cycle circuit: batches of slices timed per mode in the "
                          "default run (0 = skip)")
-    ap.add_argument("--config4-modes", default="fp16_scaled,split_bf16,c64")
+    ap.add_argument("--config4-modes", default="fp16_scaled:0.001,fp16_scaled,split_bf16,c64",
+                    help="precision modes of the 53-qubit 16-cycle arms; mode:budget gives the "
+                         "precision policy an error budget")
     ap.add_argument("--config5-slices", type=int, default=256,
-                    help="53-qubit 20-cycle circuit: contiguous slices timed in the default run "
-                         "(0 = skip)")
-    ap.add_argument("--config5-modes", default="fp16_scaled,c64")
+                    help="53-qubit 20-cycle circuit: contiguous slices timed for the first mode "
+                         "(a quarter of them for the others, one batch for complex64; 0 = skip)")
+    ap.add_argument("--config5-modes", default="fp16_scaled:0.001,fp16_scaled,c64")
     ap.add_argument("--sycamore53-compare", type=int, default=8,
                     help="contributing slices compared with complex64 under --sycamore53")
     ap.add_argument("--sparse-only", action="store_true",
@@ -600,12 +602,14 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and args.config4_batches > 0:
         c53["config4"] = measure_c53(args, 16, [m for m in args.config4_modes.split(",") if m],
                                      batches=args.config4_batches, compare=8,
-                                     profile_mode="fp16_scaled")
+                                     profile_mode=("fp16_scaled:0.001", "fp16_scaled"))
     if world == 1 and args.config5_slices > 0:
         modes5 = [m for m in args.config5_modes.split(",") if m]
         c53["config5"] = measure_c53(args, 20, modes5,
-                                     slices={m: (args.config5_slices if m != "c64" else 0)
-                                             for m in modes5},
+                                     slices={m: (0 if m.startswith("c64") else
+                                                 args.config5_slices if i == 0 else
+                                                 max(1, args.config5_slices // 4))
+                                             for i, m in enumerate(modes5)},
                                      batches=1, compare=8)
 
     # end to end through the host-buffer entry points: set the network's numbers (H2D) and
@@ -841,7 +845,7 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
     batches of the slices in flight, or ``slices`` slices; a dict gives a count per mode), the
     time per slice extrapolated to all slices (the method of Sec. 5), and the amplitudes of up to
     ``compare`` contributing slices compared with ``ref_mode`` (complex64: within 1e-5 of FP64 on
-    the circuits the oracle can check).  With ``profile_mode`` one more batch of that mode runs
+    the circuits the oracle can check).  For the modes in ``profile_mode`` one more batch runs
     in profile mode for the per-step roofline."""
     import torch
     from paper_2310_03978_gb300 import tn
@@ -876,9 +880,12 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
     ref = np.sum(refs, axis=0) if refs else None
     out = {**pdesc, "sliced_bonds": len(sliced), "compared_slices": [int(s) for s in picks],
            "reference_mode": ref_mode, "reference_s": time.perf_counter() - t0, "modes": {}}
-    for mode in modes:
+    for mode_spec in modes:
+        # "mode" or "mode:budget" (the precision policy's error budget for that arm)
+        mode, _, bud = mode_spec.partition(":")
+        budget = float(bud) if bud else args.eps_budget
         plan = tn.Plan(tnet, path, sliced, mode=mode, use_graph=True, autotune=True,
-                       eps_budget=args.eps_budget)
+                       eps_budget=budget)
         pi = plan.info()
         sb = pi["slices_in_flight"]
         amps = torch.zeros(nout, dtype=torch.complex128, device="cuda")
@@ -886,7 +893,7 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
             plan.contract(amps, w * sb, (w + 1) * sb, stream=stream)
         torch.cuda.synchronize()
         s0 = 2 * sb
-        want = slices.get(mode, 0) if isinstance(slices, dict) else slices
+        want = slices.get(mode_spec, 0) if isinstance(slices, dict) else slices
         nsl = min(want if want > 0 else max(1, batches) * sb, pi["num_slices"] - s0)
         ms = time_steps(torch, lambda: plan.contract(amps, s0, s0 + nsl, stream=stream), 1,
                         stream)
@@ -899,7 +906,7 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
                "workspace_bytes": pi["workspace_bytes"],
                "single_pass_steps": pi["num_single_pass"],
                "compensated_steps": pi["num_compensated"],
-               "eps_predicted": pi["eps_predicted"]}
+               "eps_predicted": pi["eps_predicted"], "eps_budget": budget}
         if picks:
             tot = np.sum([one_slice(plan, s) for s in picks], axis=0)
             rec["amp_rel_l2_vs_ref"] = rel_l2(tot, ref)
@@ -910,9 +917,9 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
             # part is sum p^2 / sum p (= (XEB + 1) / 2^n), compared relatively
             rec["xeb_ratio_rel_err_vs_ref"] = abs(p2_over_p(tot) / p2_over_p(ref) - 1.0)
         plan.close()
-        if mode == profile_mode:
+        if profile_mode and mode_spec in profile_mode:
             pplan = tn.Plan(tnet, path, sliced, mode=mode, profile=True, autotune=True,
-                            eps_budget=args.eps_budget)
+                            eps_budget=budget)
             pinfo = pplan.info()
             psb = pinfo["slices_in_flight"]
             for w in range(2):
@@ -932,7 +939,7 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
                                     "peaks": pk_used}
             pplan.close()
         del amps
-        out["modes"][mode] = rec
+        out["modes"][mode_spec] = rec
         out.update({"slices": pi["num_slices"], "max_intermediate_log2": pi["max_log2_size"],
                     "flops_per_slice": flops_slice,
                     "flops_per_batch": flops_slice * pi["num_slices"] + pi["tcc_invariant"],

@@ -343,7 +343,8 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // few columns (N = NT <= 16) and a contraction of K <= 1024 (summed in one FP32 chain per
 // output).  One thread owns one row m of A and all NT outputs of that row; a
 // tile is 256 rows.  B is held in shared memory as [K][NT] and read as broadcast 16-byte pairs.
-// For K <= 8 and NT <= 8 (KS = K) the grid holds as many blocks as fit on the GPU, each walking its slice's
+// For K <= 8 and NT <= 8, or K <= 16 and NT = 16 (KS = K; 2 blocks per SM, the two output
+// stages in dynamic shared memory), the grid holds as many blocks as fit on the GPU, each walking its slice's
 // tiles with a stride: a thread loads its own row of A straight into registers (K * 8 contiguous
 // bytes; a warp reads one contiguous span) and fetches its row of the next tile before it stores
 // the current one, so loads stay in flight during the store phase; two output stages taken in
@@ -353,7 +354,14 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // product commutes).  Each tile (256 x NT) is staged and written in C's order with 8 consecutive
 // elements per thread, as in the other epilogues.
 constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
-constexpr int thin_min_blocks(int nt, int ks) { return (ks && nt < 8) ? 4 : 3; }  // nt <= 8 when ks > 0
+// blocks per SM the launch bounds guarantee: the walking form keeps its rows of A in registers
+// (two tiles' worth), so 16 columns with it fit 2 blocks
+constexpr int thin_min_blocks(int nt, int ks) {
+    return ks && nt == 16 ? 2 : ((ks && nt < 8) ? 4 : 3);
+}
+// the walking form with 16 columns stages its two output tiles in dynamic shared memory
+constexpr bool thin_dyn_smem(int nt, int ks) { return ks != 0 && nt == 16; }
+constexpr int thin_dyn_bytes(int nt) { return 2 * kThinRows * (nt + 1) * 8; }
 
 template <int NT, int KS>
 __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(GemmDesc d) {
@@ -361,7 +369,10 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
     constexpr int LD = NT + 1;           // row stride of the output stage
     // KS > 0: two output stages used in turn (one barrier per tile); KS = 0: rows of A, then
     // the stage
-    __shared__ __align__(16) float2 sA[KS ? 2 * kThinRows * LD : kThinRows * kThinLd];
+    constexpr bool DYN = thin_dyn_smem(NT, KS);
+    __shared__ __align__(16) float2 sA_st[DYN ? 2 : (KS ? 2 * kThinRows * LD : kThinRows * kThinLd)];
+    extern __shared__ __align__(16) float2 sA_dyn[];
+    float2 *sA = DYN ? sA_dyn : sA_st;
     __shared__ __align__(16) float2 sB[(KS ? KS : 64) * NB];
     const int64_t s = blockIdx.y;
     const int K = KS ? KS : 1 << d.lk;
@@ -795,7 +806,12 @@ __global__ void __launch_bounds__(256) k_sparse_gemm(GenericDesc d, int32_t ln, 
 }  // namespace
 
 cudaError_t simt_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_skinny<16>,
+    cudaError_t e = cudaSuccess;
+    for (auto f : {k_gemm_thin<16, 2>, k_gemm_thin<16, 4>, k_gemm_thin<16, 8>, k_gemm_thin<16, 16>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     thin_dyn_bytes(16));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_skinny<16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSkSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gemm_skinny<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -926,13 +942,19 @@ void launch_thin_walk(const GemmDesc &d, dim3 grid, cudaStream_t st) {
     const int64_t resident = (int64_t)sms * thin_min_blocks(NT, KS);
     const int64_t per_slice = (resident + grid.y - 1) / grid.y;
     if (per_slice < (int64_t)grid.x) grid.x = (unsigned)per_slice;
-    k_gemm_thin<NT, KS><<<grid, 256, 0, st>>>(d);
+    k_gemm_thin<NT, KS><<<grid, 256, thin_dyn_smem(NT, KS) ? thin_dyn_bytes(NT) : 0, st>>>(d);
 }
 
 template <int NT>
 void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
-    if constexpr (NT == 16) {  // 16 columns: the streaming form would spill; one tile per block
-        k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d);
+    if constexpr (NT == 16) {  // 16 columns: the walking form up to K = 16, 2 blocks per SM
+        switch (d.lk) {
+            case 1: launch_thin_walk<NT, 2>(d, grid, st); break;
+            case 2: launch_thin_walk<NT, 4>(d, grid, st); break;
+            case 3: launch_thin_walk<NT, 8>(d, grid, st); break;
+            case 4: launch_thin_walk<NT, 16>(d, grid, st); break;
+            default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
+        }
     } else {
         switch (d.lk) {
             case 1: launch_thin_walk<NT, 2>(d, grid, st); break;
