@@ -1202,7 +1202,8 @@ def run_step_profile(args):
         wnet, path, sliced, workload = wl.network, wl.path, wl.sliced, WORKLOAD
     net = tn.Network(wnet.tensors, wnet.labels, wnet.open_labels)
     plan = tn.Plan(net, path, sliced, mode=args.mode, profile=True,
-                   autotune=bool(args.autotune), mixed_topk=args.mixed_topk)
+                   autotune=bool(args.autotune), mixed_topk=args.mixed_topk,
+                   eps_budget=args.eps_budget)
     info = plan.info()
     nsteps = info["num_steps"]
     sb = info["slices_in_flight"]
@@ -1229,6 +1230,8 @@ def run_step_profile(args):
     total = sum(r["ms"] for r in rows)
     roof = sum(r["roofline_ms"] for r in rows)
     print(json.dumps({"summary": True, "workload": workload, "mode": args.mode,
+                      "eps_budget": args.eps_budget, "single_pass_steps": info["num_single_pass"],
+                      "compensated_steps": info["num_compensated"],
                       "slices_per_call": sb if args.sycamore53 else info["num_slices"],
                       "steps_timed": len(rows), "sum_ms": total, "roofline_ms": roof,
                       "frac": roof / total, "peaks": pk_used}))

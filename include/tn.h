@@ -171,7 +171,10 @@ typedef struct {
                                       14, 15; TF32 rows of 64 / 32 bytes: 13, 16), 17-22 the
                                       128 x 64 tile for results 64 wide (4M 16-bit / TF32,
                                       compensated 16-bit / TF32, 3M 16-bit / TF32), 23-28 the
-                                      128 x 32 tile for results 32 wide (same order)          */
+                                      128 x 32 tile for results 32 wide (same order), 29-33 /
+                                      34-38 the persistent kernel's variants of 12-16 with 64- /
+                                      32-column tiles, 39-53 the compensated (hi / lo) forms of
+                                      12-16, 29-33 and 34-38                                 */
     int32_t store_run_log2;        /* GEMM kernels: log2 of the longest run of consecutive
                                       result elements one staged chunk writes (its bits that
                                       are also the result's lowest positions)                */

@@ -587,17 +587,20 @@ constexpr int PERS_BN = 128, PERS_STG = 4, PERS_THREADS = 320, PCW = 32;
 // second K half (elements 8..15) reads a zero page that sits one tile further (the descriptor's
 // leading-dimension offset).
 // BNP is the N tile (128, or 64 / 32 for results that narrow); B's planes then fill only the
-// first BNP rows of their 128-row slots.
-template <int ESZ, int RB, int BNP = PERS_BN>
+// first BNP rows of their 128-row slots.  NPL planes per operand: 2 (re, im: 4M) or 4 (hi and lo
+// planes of re and im: compensated products, K <= 512 needs no accumulator promotion); the
+// compensated form with 128-byte rows keeps 2 ring stages to fit shared memory.
+template <int ESZ, int RB, int BNP = PERS_BN, int NPL = 2>
 struct PersCfg {
     static constexpr int KEL = RB / ESZ;                  // K elements per stage
     static constexpr int TILE = BM * RB;                  // one plane of A (128 rows)
     static constexpr int TILE_B = BNP * RB;               // one plane of B (BNP rows)
     static constexpr int TSTRIDE = RB == 16 ? 2 * TILE : TILE;  // tile + zero page
-    static constexpr int STAGE_BYTES = 4 * TSTRIDE;       // A re, A im, B re, B im
-    static constexpr int TX_BYTES = 2 * TILE + 2 * TILE_B;  // bytes the TMA writes per stage
+    static constexpr int STAGE_BYTES = 2 * NPL * TSTRIDE;  // A planes, then B planes
+    static constexpr int TX_BYTES = NPL * (TILE + TILE_B);  // bytes the TMA writes per stage
     static constexpr int LBN = BNP == 128 ? 7 : (BNP == 64 ? 6 : 5);  // log2 of the N tile
-    static constexpr int RING = PERS_STG * STAGE_BYTES;
+    static constexpr int STG = NPL == 4 && RB == 64 ? 2 : PERS_STG;   // ring stages
+    static constexpr int RING = STG * STAGE_BYTES;
     static constexpr int STAGE_HALF = BM * PCW * 8;       // staging of one 128 x 32 chunk
     static constexpr int DEP = 6 * 256 * 8;               // byte-wise deposit tables of m0, n0
     static constexpr int BODY = RING + 2 * STAGE_HALF;
@@ -608,6 +611,7 @@ struct PersCfg {
     static constexpr int KSTEPS = RB == 16 ? 1 : RB / 32; // MMAs (32 bytes of K) per stage
     static_assert(RB == 16 ? ESZ == 2 : (RB == 32 || RB == 64), "row width");
     static_assert(BNP == 128 || BNP == 64 || BNP == 32, "N tile");
+    static_assert(NPL == 2 || NPL == 4, "4M or compensated planes");
 };
 
 // Shared-memory matrix descriptor with an explicit leading-dimension offset (K-major tiles).
@@ -711,18 +715,18 @@ __device__ __forceinline__ bool named_and(int id, int threads, bool v) {
     return r != 0;
 }
 
-template <int ESZ, int RB, bool PACKED, int BNP>
+template <int ESZ, int RB, bool PACKED, int BNP, int NPL>
 __global__ void __launch_bounds__(PERS_THREADS, 1)
     k_gemm_tc_pers(const __grid_constant__ TcGemmDesc d, int64_t tiles_n, int64_t slices) {
-    using F = PersCfg<ESZ, RB, BNP>;
-    constexpr int BK = F::KEL, BN = BNP;
+    using F = PersCfg<ESZ, RB, BNP, NPL>;
+    constexpr int BK = F::KEL, BN = BNP, STG = F::STG;
     auto sdesc = [](uint32_t a) { return sdesc_lbo<F::SBO, F::LBO, F::LAYOUT>(a); };
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + F::BODY + F::DEP);
-    uint64_t *empty = full + PERS_STG;
-    uint64_t *tfull = empty + PERS_STG;   // MMA -> epilogue: accumulator buffer b is complete
+    uint64_t *empty = full + STG;
+    uint64_t *tfull = empty + STG;        // MMA -> epilogue: accumulator buffer b is complete
     uint64_t *tempty = tfull + 2;         // epilogue -> MMA: buffer b was read (4 arrivals)
     uint64_t *mdone = tempty + 2;         // the MMA warp's last commit
     uint64_t *hi_off = mdone + 1;         // [8] epilogue table: C offsets of bits 10..12
@@ -743,7 +747,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
     if (RB == 16) {
         // zero pages: the second 16 bytes of K of every tile of every stage (never loaded)
-        for (int e = threadIdx.x; e < PERS_STG * 4 * (F::TILE / 16); e += PERS_THREADS) {
+        for (int e = threadIdx.x; e < STG * 2 * NPL * (F::TILE / 16); e += PERS_THREADS) {
             const int tile = e / (F::TILE / 16), q = e % (F::TILE / 16);
             *reinterpret_cast<uint4 *>(smem + tile * F::TSTRIDE + F::TILE + q * 16) =
                 make_uint4(0u, 0u, 0u, 0u);
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     }
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < PERS_STG; ++i) {
+        for (int i = 0; i < STG; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
@@ -815,9 +819,9 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 const int m0 = (int)(c.mt * BM), n0 = (int)(c.nt * BN);
                 bool ok = true;
                 for (int kb = 0; kb < num_kb; ++kb, ++it) {
-                    const int st = it % PERS_STG;
-                    const uint32_t ph = (uint32_t)(it / PERS_STG) & 1u;
-                    if (it >= PERS_STG &&
+                    const int st = it % STG;
+                    const uint32_t ph = (uint32_t)(it / STG) & 1u;
+                    if (it >= STG &&
                         !mbar_wait(&empty[st], ph ^ 1u, globaltimer() + limit)) {
                         *aborted = 1;
                         ok = false;
@@ -827,10 +831,10 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     mbar_expect_tx(&full[st], F::TX_BYTES);
                     const int k0 = kb * BK;
 #pragma unroll
-                    for (int pl = 0; pl < 2; ++pl) {
+                    for (int pl = 0; pl < NPL; ++pl) {
                         tma_load_3d(base + pl * F::TSTRIDE, &d.tmA, &full[st], k0, m0,
                                     pl * (int)d.slices_a + sa);
-                        tma_load_3d(base + (2 + pl) * F::TSTRIDE, &d.tmB, &full[st], k0, n0,
+                        tma_load_3d(base + (NPL + pl) * F::TSTRIDE, &d.tmB, &full[st], k0, n0,
                                     pl * (int)d.slices_b + sbi);
                     }
                     issued = it + 1;
@@ -841,9 +845,9 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
             // for the last arrival of every stage that was used (after a normal run the MMA
             // warp has consumed them all and these waits return at once)
             const unsigned long long drain = globaltimer() + limit;
-            for (int st = 0; st < PERS_STG && st < issued; ++st) {
-                const int last = ((issued - 1 - st) / PERS_STG) * PERS_STG + st;
-                mbar_wait(&full[st], (uint32_t)(last / PERS_STG) & 1u, drain);
+            for (int st = 0; st < STG && st < issued; ++st) {
+                const int last = ((issued - 1 - st) / STG) * STG + st;
+                mbar_wait(&full[st], (uint32_t)(last / STG) & 1u, drain);
             }
         }
     } else if (warp == 9) {
@@ -866,8 +870,8 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                 const uint32_t acc = tmem + (uint32_t)(buf * 2 * BN);
                 bool ok = true;
                 for (int kb = 0; kb < num_kb; ++kb, ++it) {
-                    const int st = it % PERS_STG;
-                    const uint32_t ph = (uint32_t)(it / PERS_STG) & 1u;
+                    const int st = it % STG;
+                    const uint32_t ph = (uint32_t)(it / STG) & 1u;
                     if (!mbar_wait(&full[st], ph, globaltimer() + limit)) {
                         *aborted = 1;
                         ok = false;
@@ -876,8 +880,8 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t base = smem_u32(smem + st * F::STAGE_BYTES);
                     const uint64_t a_re = sdesc(base), a_im = sdesc(base + F::TSTRIDE);
-                    const uint64_t b_re = sdesc(base + 2 * F::TSTRIDE);
-                    const uint64_t b_im = sdesc(base + 3 * F::TSTRIDE);
+                    const uint64_t b_re = sdesc(base + NPL * F::TSTRIDE);
+                    const uint64_t b_im = sdesc(base + (NPL + 1) * F::TSTRIDE);
 #pragma unroll
                     for (int kk = 0; kk < F::KSTEPS; ++kk) {
                         const uint64_t adv = (uint64_t)(kk * 32) >> 4;
@@ -886,6 +890,21 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                         umma<ESZ>(acc, a_im + adv, b_im + adv, id_neg, 1u);
                         umma<ESZ>(acc + BN, a_re + adv, b_im + adv, id_pos, first);
                         umma<ESZ>(acc + BN, a_im + adv, b_re + adv, id_pos, 1u);
+                        if constexpr (NPL == 4) {
+                            // compensated: x = hi + lo, xy ~ hi hi + hi lo + lo hi (Sec. 4.2)
+                            const uint64_t a_rl = sdesc(base + 2 * F::TSTRIDE);
+                            const uint64_t a_il = sdesc(base + 3 * F::TSTRIDE);
+                            const uint64_t b_rl = sdesc(base + (NPL + 2) * F::TSTRIDE);
+                            const uint64_t b_il = sdesc(base + (NPL + 3) * F::TSTRIDE);
+                            umma<ESZ>(acc, a_re + adv, b_rl + adv, id_pos, 1u);
+                            umma<ESZ>(acc, a_im + adv, b_il + adv, id_neg, 1u);
+                            umma<ESZ>(acc, a_rl + adv, b_re + adv, id_pos, 1u);
+                            umma<ESZ>(acc, a_il + adv, b_im + adv, id_neg, 1u);
+                            umma<ESZ>(acc + BN, a_re + adv, b_il + adv, id_pos, 1u);
+                            umma<ESZ>(acc + BN, a_im + adv, b_rl + adv, id_pos, 1u);
+                            umma<ESZ>(acc + BN, a_rl + adv, b_im + adv, id_pos, 1u);
+                            umma<ESZ>(acc + BN, a_il + adv, b_re + adv, id_pos, 1u);
+                        }
                     }
                     umma_commit(&empty[st]);
                     any = true;
@@ -1283,15 +1302,15 @@ cudaError_t launch_variant(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
 
 }  // namespace
 
-template <int ESZ, int RB, int BNP>
+template <int ESZ, int RB, int BNP, int NPL>
 cudaError_t configure_pers() {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, false, BNP>,
+    using F = PersCfg<ESZ, RB, BNP, NPL>;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, false, BNP, NPL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         PersCfg<ESZ, RB, BNP>::SMEM_BYTES);
+                                         F::SMEM_BYTES);
     if (e == cudaSuccess && ESZ == 2)
-        e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, ESZ == 2, BNP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 PersCfg<ESZ, RB, BNP>::SMEM_BYTES);
+        e = cudaFuncSetAttribute(k_gemm_tc_pers<ESZ, RB, ESZ == 2, BNP, NPL>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM_BYTES);
     return e;
 }
 
@@ -1307,9 +1326,9 @@ int sm_count() {
     return n;
 }
 
-template <int ESZ, int RB, int BNP>
+template <int ESZ, int RB, int BNP, int NPL>
 cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
-    using F = PersCfg<ESZ, RB, BNP>;
+    using F = PersCfg<ESZ, RB, BNP, NPL>;
     // tile rows and columns index the deposit tables with 24 bits each; tiles count in 32 bits
     if (d.ln < F::LBN || d.lk < 3 || d.lk > 9 || d.lm > 31 || d.ln > 31 ||
         (d.dtype == 2) != (ESZ == 4))
@@ -1321,27 +1340,40 @@ cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     if (grid > total) grid = total;
     // planar two-plane results (16-bit only) use the packed staging
     if (ESZ == 2 && d.planar_out && d.pout.planes == 2)
-        k_gemm_tc_pers<ESZ, RB, ESZ == 2, BNP>
+        k_gemm_tc_pers<ESZ, RB, ESZ == 2, BNP, NPL>
             <<<(unsigned)grid, PERS_THREADS, F::SMEM_BYTES, st>>>(d, tiles_n, slices);
     else
-        k_gemm_tc_pers<ESZ, RB, false, BNP>
+        k_gemm_tc_pers<ESZ, RB, false, BNP, NPL>
             <<<(unsigned)grid, PERS_THREADS, F::SMEM_BYTES, st>>>(d, tiles_n, slices);
     return cudaGetLastError();
 }
 
 // Variants 12-16 are the persistent short-K kernel with 128-column tiles: 16-bit with rows of
 // 64, 16 and 32 bytes (12, 14, 15), TF32 with rows of 64 and 32 bytes (13, 16); 29-33 the same
-// five with 64-column tiles, 34-38 with 32-column tiles.
+// five with 64-column tiles, 34-38 with 32-column tiles; 39-53 the compensated (hi / lo planes)
+// counterparts of 12-16, 29-33 and 34-38 in that order.
 constexpr int kPersFp16 = 12, kPersTf32 = 13, kPersFp16R16 = 14, kPersFp16R32 = 15,
-              kPersTf32R32 = 16, kPers64 = 29, kPers32 = 34;
+              kPersTf32R32 = 16, kPers64 = 29, kPers32 = 34, kPersSplit = 39, kPersEnd = 54;
 
 bool is_pers(int v) {
-    return (v >= kPersFp16 && v <= kPersTf32R32) || (v >= kPers64 && v < kPers32 + 5);
+    return (v >= kPersFp16 && v <= kPersTf32R32) || (v >= kPers64 && v < kPersEnd);
 }
 
-// the 128-column variant (12-16) of the same row width and operand type, and the N tile
-int pers_base(int v) { return v >= kPers32 ? v - kPers32 + 12 : (v >= kPers64 ? v - kPers64 + 12 : v); }
-int pers_bn(int v) { return v >= kPers32 ? 32 : (v >= kPers64 ? 64 : PERS_BN); }
+bool pers_split(int v) { return v >= kPersSplit && v < kPersEnd; }
+
+// the 4M 128-column variant (12-16) of the same row width and operand type, and the N tile
+int pers_base(int v) { return v < kPers64 ? v : 12 + (v - kPers64) % 5; }
+int pers_bn(int v) {
+    if (v < kPers64) return PERS_BN;
+    const int g = ((v - kPers64) / 5) % 3;  // 29-33 / 44-48: 64; 34-38 / 49-53: 32; 39-43: 128
+    return g == 0 ? 64 : (g == 1 ? 32 : PERS_BN);
+}
+
+// the persistent variant for an N tile, compensated or not, on the row width of base (12-16)
+int pers_variant(int base, int bn, bool split) {
+    if (!split) return bn == 128 ? base : (bn == 64 ? kPers64 : kPers32) + base - 12;
+    return kPersSplit + (bn == 128 ? 0 : (bn == 64 ? 5 : 10)) + base - 12;
+}
 
 int pers_kel(int v) {
     switch (pers_base(v)) {
@@ -1354,32 +1386,35 @@ int pers_kel(int v) {
     return 0;
 }
 
-template <int BNP>
+template <int BNP, int NPL>
 cudaError_t launch_pers_bn(int base, const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     switch (base) {
-        case kPersFp16: return launch_pers<2, 64, BNP>(d, slices, st);
-        case kPersTf32: return launch_pers<4, 64, BNP>(d, slices, st);
-        case kPersFp16R16: return launch_pers<2, 16, BNP>(d, slices, st);
-        case kPersFp16R32: return launch_pers<2, 32, BNP>(d, slices, st);
-        case kPersTf32R32: return launch_pers<4, 32, BNP>(d, slices, st);
+        case kPersFp16: return launch_pers<2, 64, BNP, NPL>(d, slices, st);
+        case kPersTf32: return launch_pers<4, 64, BNP, NPL>(d, slices, st);
+        case kPersFp16R16: return launch_pers<2, 16, BNP, NPL>(d, slices, st);
+        case kPersFp16R32: return launch_pers<2, 32, BNP, NPL>(d, slices, st);
+        case kPersTf32R32: return launch_pers<4, 32, BNP, NPL>(d, slices, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int BNP>
+template <int BNP, int NPL>
 cudaError_t configure_pers_bn() {
-    cudaError_t e = configure_pers<2, 64, BNP>();
-    if (e == cudaSuccess) e = configure_pers<4, 64, BNP>();
-    if (e == cudaSuccess) e = configure_pers<2, 16, BNP>();
-    if (e == cudaSuccess) e = configure_pers<2, 32, BNP>();
-    if (e == cudaSuccess) e = configure_pers<4, 32, BNP>();
+    cudaError_t e = configure_pers<2, 64, BNP, NPL>();
+    if (e == cudaSuccess) e = configure_pers<4, 64, BNP, NPL>();
+    if (e == cudaSuccess) e = configure_pers<2, 16, BNP, NPL>();
+    if (e == cudaSuccess) e = configure_pers<2, 32, BNP, NPL>();
+    if (e == cudaSuccess) e = configure_pers<4, 32, BNP, NPL>();
     return e;
 }
 
 cudaError_t tc_prepare() {
-    cudaError_t e = configure_pers_bn<128>();
-    if (e == cudaSuccess) e = configure_pers_bn<64>();
-    if (e == cudaSuccess) e = configure_pers_bn<32>();
+    cudaError_t e = configure_pers_bn<128, 2>();
+    if (e == cudaSuccess) e = configure_pers_bn<64, 2>();
+    if (e == cudaSuccess) e = configure_pers_bn<32, 2>();
+    if (e == cudaSuccess) e = configure_pers_bn<128, 4>();
+    if (e == cudaSuccess) e = configure_pers_bn<64, 4>();
+    if (e == cudaSuccess) e = configure_pers_bn<32, 4>();
 #define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb, esz) \
     if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb, esz>();
     TN_TC_VARIANTS(TN_TC_CONFIGURE)
@@ -1427,7 +1462,7 @@ bool tc_variant_tf32(int variant) {
 // two CTAs per SM; long ones use the 128 x 256 tile (1.98 PFLOP/s on m=2^13, n=2^14, k=2^14
 // against 1.79 for 128 x 128), or 128 x 128 when N < 256.
 int tc_variant_form(int variant) {
-    if (is_pers(variant)) return 1;
+    if (is_pers(variant)) return pers_split(variant) ? 3 : 1;
     switch (variant) {
 #define TN_TC_FORM(id, npl, bk, bn, stg, minb, esz) \
     case id: return npl == 3 ? 2 : (npl == 4 ? 3 : 1);
@@ -1437,7 +1472,7 @@ int tc_variant_form(int variant) {
     return 0;
 }
 
-int tc_num_variants() { return 39; }
+int tc_num_variants() { return kPersEnd; }
 
 namespace {
 int gf2_rank(std::vector<int> v) {
@@ -1512,15 +1547,15 @@ bool tc_variant_fits(int variant, int lk, int ln) {
 // bk_pref / bn_pref: 0 or the K / N tile the caller asks for (K tile in 16-bit elements of a
 // shared-memory row: 32 = 64-byte rows, 64 = 128-byte rows, for both operand types).
 int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf32) {
-    // n = 32 or 64: the 32- or 64-column tile, persistent for short 4M contractions, else one
-    // tile per CTA (2 CTAs per SM) in every form
-    const bool pers_narrow = form == 1 && lk >= 3 && lk <= 9 && bk_pref == 0 && bn_pref == 0 &&
-                             (ln == 5 || ln == 6);
-    if (pers_narrow) {
-        const int off = ln == 5 ? kPers32 - 12 : kPers64 - 12;
-        if (tf32) return off + (lk == 3 ? kPersTf32R32 : kPersTf32);
-        return off + (lk == 3 ? kPersFp16R16 : (lk == 4 ? kPersFp16R32 : kPersFp16));
+    // short 4M or compensated contractions: the persistent kernel with a 128-, 64- or 32-column
+    // tile, unless a tile shape was asked for
+    if ((form == 1 || form == 3) && lk >= 3 && lk <= 9 && bk_pref == 0 && bn_pref == 0 &&
+        ln >= 5) {
+        const int base = tf32 ? (lk == 3 ? kPersTf32R32 : kPersTf32)
+                              : (lk == 3 ? kPersFp16R16 : (lk == 4 ? kPersFp16R32 : kPersFp16));
+        return pers_variant(base, ln >= 7 ? 128 : (ln == 6 ? 64 : 32), form == 3);
     }
+    // n = 32 or 64: otherwise the 32- or 64-column one-tile kernel (2 CTAs per SM), every form
     if (ln == 5) {
         if (form == 3) return tf32 ? 26 : 25;
         if (form == 2) return tf32 ? 28 : 27;
@@ -1531,12 +1566,9 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
         if (form == 2) return tf32 ? 22 : 21;
         return tf32 ? 18 : 17;
     }
-    // short contractions: the persistent kernel, unless a tile shape was asked for
-    const bool pers = form == 1 && lk >= 3 && lk <= 9 && ln >= 7 && bk_pref == 0 && bn_pref == 0;
     if (tf32) {
         if (form == 3) return 11;
         if (form == 2) return 10;
-        if (pers) return lk == 3 ? kPersTf32R32 : kPersTf32;
         if (bn_pref == 256 && ln >= 8) return 7;
         if (bk_pref == 64) return 9;
         if (lk <= 9) return 8;
@@ -1544,7 +1576,6 @@ int tc_pick_variant(int form, int lk, int ln, int bk_pref, int bn_pref, bool tf3
     }
     if (form == 3) return 6;
     if (form == 2) return bk_pref == 64 ? 4 : 3;
-    if (pers) return lk == 3 ? kPersFp16R16 : (lk == 4 ? kPersFp16R32 : kPersFp16);
     if (bn_pref == 256 && ln >= 8) return 1;
     if (bk_pref == 32) return lk <= 9 ? 2 : 5;
     if (bk_pref == 64 || bn_pref == 128) return lk <= 9 && bk_pref != 64 ? 2 : 0;
@@ -1556,9 +1587,14 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
     if (d.lm < 7 || slices > 65535) return cudaErrorInvalidValue;
     if (is_pers(d.variant)) {
         const int bn = pers_bn(d.variant), base = pers_base(d.variant);
-        if (bn == 64) return launch_pers_bn<64>(base, d, slices, st);
-        if (bn == 32) return launch_pers_bn<32>(base, d, slices, st);
-        return launch_pers_bn<128>(base, d, slices, st);
+        if (pers_split(d.variant)) {
+            if (bn == 64) return launch_pers_bn<64, 4>(base, d, slices, st);
+            if (bn == 32) return launch_pers_bn<32, 4>(base, d, slices, st);
+            return launch_pers_bn<128, 4>(base, d, slices, st);
+        }
+        if (bn == 64) return launch_pers_bn<64, 2>(base, d, slices, st);
+        if (bn == 32) return launch_pers_bn<32, 2>(base, d, slices, st);
+        return launch_pers_bn<128, 2>(base, d, slices, st);
     }
     switch (d.variant) {
 #define TN_TC_LAUNCH(id, npl, bk, bn, stg, minb, esz) \

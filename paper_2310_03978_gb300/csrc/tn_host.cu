@@ -264,6 +264,9 @@ int route(const Step &s, tn_precision mode, bool tc_ok) {
     // register-tiled GEMM (split along K when the output is small); a contraction of fewer than
     // 16 elements is cheaper as an element-wise pass with coalesced stores
     if (s.batch.empty() && lk >= 2 && lm >= 3 && ln >= 3 && lm + ln + lk >= 14) return K_GEMM;
+    // a long contraction (k >= 1024) into a small result: the CUDA-core GEMM splits K over many
+    // CTAs where the element-wise kernel would give each output one serial sum
+    if (s.batch.empty() && lk >= 10 && lm + ln >= 1) return K_GEMM;
     return K_GENERIC;
 }
 

@@ -202,7 +202,9 @@ def single_step(rng, lm, ln, lk, scale=1.0, scramble=True):
     ((3, 2, 2), "generic"),      # tiny
     ((9, 9, 1), "generic"),      # outer-product-like: 2^18 outputs, k = 2
     ((9, 9, 2), "gemm_simt"),    # k = 4: register-tiled, zero-padded K tile
-    ((2, 2, 11), "generic"),     # k > 2^10: offsets computed without the shared table
+    ((2, 2, 9), "generic"),      # 16 outputs of 512 terms each
+    ((2, 2, 11), "gemm_simt"),   # k >= 2^10 into a small result: split along K
+    ((10, 1, 13), "gemm_simt"),  # a 2-wide result of a long contraction
     ((6, 5, 4), "gemm_simt"),
     ((7, 6, 9), "gemm_simt"),
     ((5, 9, 4), "gemm_simt"),
@@ -227,6 +229,21 @@ def test_single_step_cuda_core_kernels(tn, shape, kernel):
     got2, info, _ = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900])
     assert info["slices_in_flight"] == 2
     check(got2, ref2, 1e-5)
+
+
+def test_long_contraction_with_a_batch_label_on_the_elementwise_kernel(tn):
+    # a hyperedge b on three tensors is a batch index of the step that meets two of them; such
+    # steps run element-wise, here with k = 2^11 (offsets computed without the shared table)
+    rng = np.random.default_rng(66)
+    K = list(range(200, 211))
+    tensors = [crandn(rng, 14, 2.0 ** -6), crandn(rng, 13, 2.0 ** -6), crandn(rng, 1)]
+    labels = [[500] + K + [0, 1], [500] + K + [100], [500]]
+    out = [100, 0, 1]
+    path = [(0, 1), (0, 2)]
+    ref = O.contract(tensors, labels, out, path)
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, path)
+    assert kernels[0] == "generic"
+    check(got, ref, 1e-5)
 
 
 @pytest.mark.parametrize("shape", [(12, 4, 4), (10, 2, 6), (4, 11, 3), (13, 0, 2), (11, 3, 1),
@@ -294,6 +311,8 @@ def test_narrow_results_on_the_64_and_32_column_tiles(tn, mode, form, bk, shape)
     narrow = min(shape[0], shape[1])
     if form == "4m" and bk == 0:   # persistent: 29-33 (64 columns), 34-38 (32 columns)
         lo, hi = (29, 33) if narrow == 6 else (34, 38)
+    elif "split" in mode:          # persistent compensated: 44-48 (64), 49-53 (32 columns)
+        lo, hi = (44, 48) if narrow == 6 else (49, 53)
     else:                          # one tile per CTA: 17-22 (64 columns), 23-28 (32 columns)
         lo, hi = (17, 22) if narrow == 6 else (23, 28)
     assert si["kernel_name"] == "gemm_tc" and lo <= si["tc_variant"] <= hi
