@@ -430,6 +430,10 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
             }
     }
     float amx = 0.f;
+    // a result that feeds a tensor-core step is written as its scaled planar 16-bit copy, with
+    // the exponent bounded from the inputs' max-abs (as in the other epilogues)
+    const int eo = d.planar_out ? planar_out_exponent(d.pout, s) : 0;
+    if (d.planar_out && blockIdx.x == 0 && tid == 0) d.pout.exps[s] = eo;
     // write the tile whose C offset (its rows' deposit) is cbase through `stage`; callers make
     // sure no thread still reads `stage` from an earlier tile
     auto emit = [&](float2 *stage, uint64_t cbase) {
@@ -446,10 +450,14 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
                 v[j] = stage[wt[i] + w8[j]];
                 amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
             }
-            float4 *c4 = reinterpret_cast<float4 *>(C + ot[i]);
+            if (d.planar_out) {
+                planar_out_store8(d.pout, s, cbase | ot[i], v, eo);
+            } else {
+                float4 *c4 = reinterpret_cast<float4 *>(C + ot[i]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+                for (int j = 0; j < 4; ++j)
+                    c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+            }
         }
     };
     if constexpr (KS != 0) {
@@ -967,7 +975,7 @@ void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
 
 cudaError_t launch_gemm_thin(const GemmDesc &d, int64_t slices, cudaStream_t st) {
     if (d.lm < 8 || d.ln < 0 || d.ln > 4 || d.lk < 1 || d.lk > 10 || slices > 65535 ||
-        d.tile_bits != 8 + d.ln || d.tile_bits < 3 || d.planar_out)
+        d.tile_bits != 8 + d.ln || d.tile_bits < 3)
         return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)((1ll << d.lm) / kThinRows), (unsigned)slices);
     switch (d.ln) {

@@ -777,7 +777,7 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
                 // fewest tiles) writes complex64 instead: a long contraction over few tiles
                 // needs the split more than the saved conversion pass.
                 const Step &pr = p->steps[X.producer];
-                q.direct = pr.dep && (pr.kernel == K_TC ||
+                q.direct = pr.dep && (pr.kernel == K_TC || pr.kernel == K_STREAM ||
                                       (pr.kernel == K_GEMM && pr.M.size() >= 6 &&
                                        pr.N.size() >= 6 &&
                                        tn::gemm_simt_splits((int)pr.M.size(), (int)pr.N.size(),
@@ -795,7 +795,7 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
         for (auto &q : p->planars)
             if (q.direct) {
                 const Step &pr = p->steps[p->tensors[q.tensor].producer];
-                if (pr.kernel == K_GEMM) {
+                if (pr.kernel == K_GEMM || pr.kernel == K_STREAM) {
                     need_meta(pr.a);
                     need_meta(pr.b);
                 }
@@ -1435,6 +1435,10 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         d.lk = (int)st.K.size();
         d.splits = 1;
         d.amax_out = amax_out;
+        if (st.direct_planar >= 0) {
+            d.planar_out = 1;
+            fill_planar_out(p, st, d.pout);
+        }
         fill_pos(d.posC_m, TN_MAXR, -1);
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(Rl[Rl.size() - 1 - i]);

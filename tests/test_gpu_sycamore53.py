@@ -1,0 +1,81 @@
+"""The 53-qubit 16- and 20-cycle configurations at full size on the GPU, through the C ABI.
+
+The CPU oracle cannot contract a slice of these paths (2.2e13 - 3.1e13 flops each), so the checks
+are properties that hold at any size, run in the launch configuration the bench times (stored
+annealed path, 2^30 / 2^31 size cap, as many slices in flight as the workspace allows, CUDA-graph
+replay):
+  * the FP16-scaled path against the complex64 path (itself within 1e-5 of the oracle on every
+    circuit the oracle can contract) on contributing slices: amplitude relative L2 within the
+    5e-3 bar, per entry too;
+  * a slice that the host's slice conditions rule out (a projector after a swap-like fSim fixes a
+    sliced bond) contracts to zero up to the 6e-17 of cos(pi/2) in the gate (below 1e-9 of a
+    contributing slice);
+  * slice ranges split anywhere add up to the whole range (within FP64 rounding).
+"""
+import numpy as np
+import pytest
+
+from paper_2310_03978_gb300 import slice_support as S
+from paper_2310_03978_gb300.paths import make_paths as MP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_03978_gb300 import tn as T
+    T.lib()
+    return T
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("cycles", [16, 20])
+def test_full_size_53_qubit_paths(tn, cycles):
+    rec = MP.load(cycles)
+    if rec is None:
+        pytest.skip("stored path not written")
+    _, net = MP.network(MP.name_of(cycles))
+    path = [tuple(p) for p in rec["path"]]
+    sliced = rec["sliced"]
+    tnet = tn.Network(net.tensors, net.labels, net.open_labels)
+    nout = 1 << len(net.open_labels)
+    part = torch.zeros(nout, dtype=torch.complex128, device="cuda")
+
+    def one(plan, s0, s1):
+        part.zero_()
+        plan.contract(part, s0, s1)
+        torch.cuda.synchronize()
+        return part.cpu().numpy()
+
+    cons = S.slice_constraints(net, sliced)
+    picks = S.supported_slices(net, sliced, 7, 6)
+    ruled_out = next(s for s in range(1 << 12) if not S.slice_supported(cons, s))
+    ref = tn.Plan(tnet, path, sliced, mode="c64", max_slices_in_flight=1)
+    refs = {s: one(ref, s, s + 1) for s in picks}
+    zero_ref = one(ref, ruled_out, ruled_out + 1)
+    ref.close()
+    scale = max(np.linalg.norm(r) for r in refs.values())
+    contributing = [s for s in picks if np.linalg.norm(refs[s]) > 1e-6 * scale][:2]
+    assert contributing, "no contributing slice among the candidates"
+    assert np.linalg.norm(zero_ref) <= 1e-9 * scale
+    plan = tn.Plan(tnet, path, sliced, mode="fp16_scaled", use_graph=True, autotune=True)
+    sb = plan.info()["slices_in_flight"]
+    assert sb >= 2 and plan.info()["max_log2_size"] <= (30 if cycles == 16 else 31)
+    for s in contributing:
+        got = one(plan, s, s + 1)
+        assert rel(got, refs[s]) <= 5e-3
+        assert np.max(np.abs(got - refs[s])) <= 5e-3 * np.max(np.abs(refs[s]))
+    assert np.linalg.norm(one(plan, ruled_out, ruled_out + 1)) <= 1e-9 * scale
+    # a full batch under graph replay, and the same range split in two
+    s0 = ((min(contributing) // sb) * sb)
+    whole = one(plan, s0, s0 + sb)
+    split = one(plan, s0, s0 + 1) + one(plan, s0 + 1, s0 + sb)
+    assert np.linalg.norm(split - whole) <= 1e-12 * max(np.linalg.norm(whole), 1e-30)
+    plan.close()
+    tnet.close()
