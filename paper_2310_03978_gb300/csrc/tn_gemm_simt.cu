@@ -413,20 +413,25 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         for (int j = 0; j < 8; ++j)
             w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
     }
-    // a tile has 256 * NT elements (tile_bits = 8 + log2 NT): 32 * NT tasks of 8, at most two
-    // per thread; their stage and C offsets are the same for every tile, so they are set once
-    constexpr int TASKS = kThinRows * NT / 8, TPT = (TASKS + 255) / 256;
-    int wt[TPT];
-    uint64_t ot[TPT];
+    // a tile has 256 * NT elements (tile_bits = 8 + log2 NT): 32 * NT runs of 8 consecutive
+    // elements of C; their stage and C offsets are the same for every tile, so they are set once
+    constexpr int TASKS = kThinRows * NT / 8;
+    // two lanes share each run of 8: for complex64 results lane half h writes elements 4j + 2h
+    // and 4j + 2h + 1 in its store j, so each store instruction fills whole 32-byte sectors; a
+    // planar 16-bit result (16 bytes per plane and run) is written by the even lane alone
+    constexpr int SUBS = TASKS * 2, SPT = (SUBS + 255) / 256;
+    int ws[SPT];
+    uint64_t os[SPT];
+    const int d0 = w8[1], d1 = w8[2], d2 = w8[4];
 #pragma unroll
-    for (int i = 0; i < TPT; ++i) {
-        const int task = tid + 256 * i;
-        wt[i] = 0;
-        ot[i] = 0;
+    for (int i = 0; i < SPT; ++i) {
+        const int u = tid + 256 * i, r = u >> 1, h = u & 1;
+        ws[i] = h ? d1 : 0;
+        os[i] = h ? 2 : 0;
         for (int q = 3; q < d.tile_bits; ++q)
-            if ((task >> (q - 3)) & 1) {
-                wt[i] += soff(d.tb_src[q]);
-                ot[i] |= 1ull << d.tb_pos[q];
+            if ((r >> (q - 3)) & 1) {
+                ws[i] += soff(d.tb_src[q]);
+                os[i] |= 1ull << d.tb_pos[q];
             }
     }
     float amx = 0.f;
@@ -441,22 +446,33 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
         __syncthreads();
         float2 *C = d.C + s * d.sC + cbase;
+        if (d.planar_out) {
+            if ((tid & 1) == 0) {
 #pragma unroll
-        for (int i = 0; i < TPT; ++i) {
-            if (TASKS % 256 != 0 && tid + 256 * i >= TASKS) break;
-            float2 v[8];
+                for (int i = 0; i < SPT; ++i) {
+                    if (SUBS % 256 != 0 && tid + 256 * i >= SUBS) break;
+                    float2 v[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                v[j] = stage[wt[i] + w8[j]];
-                amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                    for (int j = 0; j < 8; ++j) {
+                        v[j] = stage[ws[i] + w8[j]];
+                        amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                    }
+                    planar_out_store8(d.pout, s, cbase | os[i], v, eo);
+                }
             }
-            if (d.planar_out) {
-                planar_out_store8(d.pout, s, cbase | ot[i], v, eo);
-            } else {
-                float4 *c4 = reinterpret_cast<float4 *>(C + ot[i]);
+        } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    c4[j] = make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+            for (int i = 0; i < SPT; ++i) {
+                if (SUBS % 256 != 0 && tid + 256 * i >= SUBS) break;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int w = ws[i] + (j ? d2 : 0);
+                    const float2 v0 = stage[w], v1 = stage[w + d0];
+                    amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
+                                           fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                    *reinterpret_cast<float4 *>(C + (os[i] + 4 * j)) =
+                        make_float4(v0.x, v0.y, v1.x, v1.y);
+                }
             }
         }
     };

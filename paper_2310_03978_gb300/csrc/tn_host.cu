@@ -1368,9 +1368,9 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         TN_CUDA(cudaMemsetAsync(amax_out, 0, sizeof(unsigned int) * (C.dep ? slices : 1),
                                 stream));
     }
-    // a direct CUDA-core producer bounds its output from its inputs' max-abs; inputs that are
-    // leaves (no producer epilogue records it) get an amax pass here
-    if (st.kernel == K_GEMM && st.direct_planar >= 0) {
+    // a direct CUDA-core or streaming producer bounds its output from its inputs' max-abs;
+    // inputs that are leaves (no producer epilogue records it) get an amax pass here
+    if ((st.kernel == K_GEMM || st.kernel == K_STREAM) && st.direct_planar >= 0) {
         for (int side = 0; side < 2; ++side) {
             const Tensor &X = side ? B : A;
             if (X.producer >= 0) continue;

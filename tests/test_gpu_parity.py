@@ -618,13 +618,16 @@ def test_chained_steps_feed_the_tensor_cores(tn, lk1, first, mode):
 def test_thin_step_feeds_the_tensor_cores(tn, mode, nsl):
     # step 1 is thin (2^11 x 8, k = 4: the streaming kernel) and its result is an operand of
     # the tensor-core step 2 (m = 2^7, n = 2^8, k = 2^7): for single-pass consumers it writes
-    # the planar 16-bit copy itself, with an exponent bounded from its inputs' max-abs
+    # the planar 16-bit copy itself, with an exponent bounded from its inputs' max-abs (its
+    # inputs are leaves, measured by an amax pass; at these magnitudes, ~2^-60 after step 1, an
+    # unscaled FP16 copy would flush to zero)
     rng = np.random.default_rng(45 + nsl)
     a = list(range(0, 11))
     k1 = [100, 101]
     b = [200, 201, 202]
     c = list(range(300, 308))
-    tensors = [crandn(rng, 13, 2.0 ** -5), crandn(rng, 5, 2.0 ** -2), crandn(rng, 15, 2.0 ** -6)]
+    tensors = [crandn(rng, 13, 2.0 ** -30), crandn(rng, 5, 2.0 ** -30),
+               crandn(rng, 15, 2.0 ** -6)]
     labels = [a + k1, k1 + b, a[7:] + b + c]
     out = [int(x) for x in rng.permutation(a[:7] + c)]
     path = [(0, 1), (0, 2)]
