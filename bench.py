@@ -121,6 +121,9 @@ def parse_args():
                          "step, so it is written as scaled planar 16-bit numbers")
     ap.add_argument("--step-profile", type=int, default=0,
                     help="per-step roofline of the circuit workload: print the N slowest steps")
+    ap.add_argument("--thin-tc", type=int, default=0, choices=[-1, 0, 1],
+                    help="streaming steps on the tensor cores: 0 automatic, 1 all that fit, "
+                         "-1 none")
     ap.add_argument("--step", default=None,
                     help="single-step microbench 'lm,ln,lk' (log2 of m, n, k) instead of the "
                          "circuit: one random dense contraction with shuffled label orders")
@@ -885,7 +888,7 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
         mode, _, bud = mode_spec.partition(":")
         budget = float(bud) if bud else args.eps_budget
         plan = tn.Plan(tnet, path, sliced, mode=mode, use_graph=True, autotune=True,
-                       eps_budget=budget)
+                       eps_budget=budget, thin_tc=args.thin_tc)
         pi = plan.info()
         sb = pi["slices_in_flight"]
         amps = torch.zeros(nout, dtype=torch.complex128, device="cuda")
@@ -919,7 +922,7 @@ def measure_c53(args, cycles, modes, batches=0, slices=0, compare=8, profile_mod
         plan.close()
         if profile_mode and mode_spec in profile_mode:
             pplan = tn.Plan(tnet, path, sliced, mode=mode, profile=True, autotune=True,
-                            eps_budget=budget)
+                            eps_budget=budget, thin_tc=args.thin_tc)
             pinfo = pplan.info()
             psb = pinfo["slices_in_flight"]
             for w in range(2):
@@ -1146,7 +1149,8 @@ def run_step_bench(args):
     for mode in args.mode.split(","):
         for form in args.gemm_form.split(","):
             plan = tn.Plan(net, path, (), mode=mode, profile=True, gemm_form=form,
-                           tc_bk=args.tc_bk, tc_bn=args.tc_bn, autotune=bool(args.autotune))
+                           tc_bk=args.tc_bk, tc_bn=args.tc_bn, autotune=bool(args.autotune),
+                           thin_tc=args.thin_tc)
             for _ in range(args.warmup):
                 plan.contract(amps, stream=stream)
             torch.cuda.synchronize()
@@ -1203,7 +1207,7 @@ def run_step_profile(args):
     net = tn.Network(wnet.tensors, wnet.labels, wnet.open_labels)
     plan = tn.Plan(net, path, sliced, mode=args.mode, profile=True,
                    autotune=bool(args.autotune), mixed_topk=args.mixed_topk,
-                   eps_budget=args.eps_budget)
+                   eps_budget=args.eps_budget, thin_tc=args.thin_tc)
     info = plan.info()
     nsteps = info["num_steps"]
     sb = info["slices_in_flight"]

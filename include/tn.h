@@ -115,7 +115,11 @@ typedef struct {
                                       single-pass (TN_PREC_MIXED: exactly that many, 0 = 1;
                                       FP16/BF16-scaled and TF32: at most that many, 0 = all);
                                       the others use compensated hi/lo products              */
-    int32_t reserved0;
+    int32_t thin_tc;               /* streaming (thin-operand) steps with 4-16 columns and
+                                      4-16 terms on the tensor cores (compensated TF32,
+                                      FP32-level accuracy) in the tensor-core modes: 0 =
+                                      those with 16 terms, 1 = all of them, -1 = none (CUDA
+                                      cores)                                                  */
     double eps_budget;             /* > 0: largest predicted amplitude relative L2 error the
                                       precision policy may reach (error model above); 0 = none,
                                       except TN_PREC_BF16_SCALED (5e-3)                      */
@@ -153,7 +157,8 @@ typedef struct {
 } tn_plan_info;
 
 typedef struct {
-    int32_t kernel;                /* 0 generic, 1 stream, 2 CUDA-core GEMM, 3 tcgen05 GEMM  */
+    int32_t kernel;                /* 0 generic, 1 stream, 2 CUDA-core GEMM, 3 tcgen05 GEMM,
+                                      4 stream on the tensor cores (opts.thin_tc)           */
     int32_t slice_dependent;       /* 0 = computed once per call and shared by all slices    */
     int32_t log2_m, log2_n, log2_k, log2_batch;  /* GEMM extents of the step (Sec. A.2)    */
     int32_t log2_a, log2_b, log2_c;              /* operand and result sizes               */

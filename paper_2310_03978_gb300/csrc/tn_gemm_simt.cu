@@ -342,7 +342,9 @@ __global__ void k_splitk_reduce(GemmDesc d, int64_t slices) {
 // Thin steps (the low-intensity contractions of App. A.2): C[m, n] = sum_k A[m, k] B[n, k] with
 // few columns (N = NT <= 16) and a contraction of K <= 1024 (summed in one FP32 chain per
 // output).  One thread owns one row m of A and all NT outputs of that row; a
-// tile is 256 rows.  B is held in shared memory as [K][NT] and read as broadcast 16-byte pairs.
+// tile is 256 rows.  B is held in shared memory as [K][NT] and read as broadcast 16-byte pairs,
+// or, in the walking form with NT * K <= 16, in every thread's registers (those steps would
+// otherwise spend most of the L1 / shared-memory pipe on the broadcasts).
 // For K <= 8 and NT <= 8, or K <= 16 and NT = 16 (KS = K; 2 blocks per SM, the two output
 // stages in dynamic shared memory), the grid holds as many blocks as fit on the GPU, each walking its slice's
 // tiles with a stride: a thread loads its own row of A straight into registers (K * 8 contiguous
@@ -359,6 +361,10 @@ constexpr int kThinRows = 256, kThinKC = 16, kThinLd = kThinKC + 1;
 constexpr int thin_min_blocks(int nt, int ks) {
     return ks && nt == 16 ? 2 : ((ks && nt < 8) ? 4 : 3);
 }
+// the walking form holds a small operand of at most 16 complex values in registers (every
+// thread the same values), so the inner loop reads no shared memory at all; larger ones stay
+// in shared memory, read as broadcast 16-byte pairs
+constexpr bool thin_b_in_regs(int nt, int ks) { return ks != 0 && nt * ks <= 16; }
 // the walking form with 16 columns stages its two output tiles in dynamic shared memory
 constexpr bool thin_dyn_smem(int nt, int ks) { return ks != 0 && nt == 16; }
 constexpr int thin_dyn_bytes(int nt) { return 2 * kThinRows * (nt + 1) * 8; }
@@ -373,7 +379,8 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
     __shared__ __align__(16) float2 sA_st[DYN ? 2 : (KS ? 2 * kThinRows * LD : kThinRows * kThinLd)];
     extern __shared__ __align__(16) float2 sA_dyn[];
     float2 *sA = DYN ? sA_dyn : sA_st;
-    __shared__ __align__(16) float2 sB[(KS ? KS : 64) * NB];
+    constexpr bool BREG = thin_b_in_regs(NT, KS);
+    __shared__ __align__(16) float2 sB[BREG ? 2 : (KS ? KS : 64) * NB];
     const int64_t s = blockIdx.y;
     const int K = KS ? KS : 1 << d.lk;
     const float2 *As = d.A + s * d.sA;
@@ -501,18 +508,37 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         };
         int64_t t = blockIdx.x;  // < tiles: the launch makes at most one block per tile
         fetch(a, t);
-        for (int e = tid; e < NT * KS; e += 256) {
-            const int n = e / KS, k = e % KS;
-            sB[k * NB + n] = B[e];
+        float2 breg[BREG ? KS * NT : 1];
+        if constexpr (BREG) {
+#pragma unroll
+            for (int e = 0; e < NT * KS; ++e) breg[(e % KS) * NT + e / KS] = B[e];
+        } else {
+            for (int e = tid; e < NT * KS; e += 256) {
+                const int n = e / KS, k = e % KS;
+                sB[k * NB + n] = B[e];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         int buf = 0;
         for (; t < tiles; t += gridDim.x) {
             if (t + gridDim.x < tiles) fetch(an, t + gridDim.x);
 #pragma unroll
             for (int n = 0; n < NT; ++n) cr[n] = ci[n] = 0.f;
+            if constexpr (BREG) {
 #pragma unroll
-            for (int k = 0; k < KS; ++k) mac(a[k], sB + k * NB);
+                for (int k = 0; k < KS; ++k)
+#pragma unroll
+                    for (int n = 0; n < NT; ++n) {
+                        const float2 b = breg[k * NT + n];
+                        cr[n] = fmaf(a[k].x, b.x, cr[n]);
+                        cr[n] = fmaf(-a[k].y, b.y, cr[n]);
+                        ci[n] = fmaf(a[k].x, b.y, ci[n]);
+                        ci[n] = fmaf(a[k].y, b.x, ci[n]);
+                    }
+            } else {
+#pragma unroll
+                for (int k = 0; k < KS; ++k) mac(a[k], sB + k * NB);
+            }
             // stage `buf` was last read two tiles ago, before every thread passed the barrier
             // inside the previous tile's emit
             emit(sA + buf * kThinRows * LD, tile_base(t));

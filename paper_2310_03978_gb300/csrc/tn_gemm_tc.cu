@@ -567,7 +567,8 @@ __global__ void __launch_bounds__(NPL == 4 ? 192 : 128, MINB)
                      "r"(TMEM_COLS));
 }
 
-// Persistent 4M kernel for short contractions (K up to 512): each CTA walks the tiles
+// Persistent 4M kernel for short contractions (K up to 512; with 64-byte rows also up to 4096,
+// where the autotuner finds it faster than one tile per CTA): each CTA walks the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ... (tiles of all slices, slice-major, grouped raster
 // inside a slice).  Such steps write far more than they compute, so what matters is keeping the
 // stores going: the MMA of the next tile fills the other half of a double-buffered TMEM
@@ -1185,6 +1186,416 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
                      "r"(512));
 }
 
+// Thin steps on the tensor cores (the low-intensity contractions of App. A.2):
+// C[m, n] = sum_k A[m, k] B[n, k] for a complex64 A of 2^lm rows, NT = 2^ln in {4, 8, 16}
+// columns and KC = 2^lk in {4, 8, 16} terms.  The complex product is one real product: A read
+// as 2^lm x 2 KC real numbers (re, im interleaved along k) times the 2 KC x 2 NT real matrix B'
+// with B'[2k, 2n] = B'[2k+1, 2n+1] = Re B[n, k], B'[2k+1, 2n] = -Im B[n, k] and
+// B'[2k, 2n+1] = Im B[n, k] gives C as 2^lm x 2 NT real numbers (re, im interleaved along n).
+// The products run in TF32 with compensated operands (x = hi + lo, hi = x rounded to TF32,
+// A B' ~ Ahi B'lo + Alo B'hi + Ahi B'hi: Sec. 4.2's 3xTF32 scheme), which keeps the result at
+// FP32-level accuracy while the tensor cores take the 4 NT KC multiply-adds per row that bound
+// the CUDA-core form once NT and KC reach 8-16.
+// A 256-row tile is loaded by TMA as two 128-row halves into a ring of raw stages (rows of
+// 8 KC bytes with the matching swizzle; as many stages as shared memory holds, so enough reads
+// stay in flight), split into hi / lo parts in one of two slots the MMAs read (which frees the
+// raw stage at once), and accumulated in TMEM as two 128 x 32 blocks (B' has zero rows beyond
+// 2 NT).  Warps 0-7 drain the accumulator (warp w reads TMEM lanes 32 (w % 4).. of half w / 4,
+// so thread t holds row t of the tile) and write the tile in C's order through a shared-memory
+// stage, 8 consecutive elements of C per task as the CUDA-core thin kernel does; warps 8-11
+// split the halves and build B' hi / lo when the slice changes; warp 12 issues the TMA loads,
+// warp 13 the MMAs.  Every wait is bounded; a wait that runs out sets the status word and the
+// abort flag, and every role leaves its loop.
+template <int NT, int KC>
+struct ThinTcCfg {
+    static constexpr int RB = 8 * KC;             // bytes of one row of A (2 KC floats)
+    static constexpr int NR = 2 * NT;             // real result columns
+    static constexpr int NP = 32;                 // MMA N (the 32-column shape of the
+                                                  // narrow tiles; B' rows past NR are zero)
+    static constexpr int HALF = BM * RB;          // one 128-row half of a tile
+    static constexpr int CS = 2;                  // hi / lo slots the MMAs read
+    static constexpr int SLOT = 2 * HALF;         // hi, then lo
+    static constexpr int BPL = ((NP * RB + 1023) / 1024) * 1024;  // one plane of B'
+    static constexpr int LD = NT + 1;             // row stride of the output stage (float2)
+    static constexpr int ESTAGE = 256 * LD * 8;   // one output stage
+    static constexpr int FIXED = CS * SLOT + 2 * BPL + 2 * ESTAGE;
+    // raw TMA stages: what is left of shared memory, at most 32 and 128 KB
+    static constexpr int RS_FIT = (232448 - 2048 - FIXED) / HALF;
+    static constexpr int RS_CAP = (131072 / HALF) < 32 ? (131072 / HALF) : 32;
+    static constexpr int RS = RS_FIT < RS_CAP ? RS_FIT : RS_CAP;
+    static constexpr int RAW = RS * HALF;
+    static constexpr int BODY = RAW + FIXED;
+    static constexpr int SMEM_BYTES = BODY + 1024 + 1024;
+    static constexpr int SBO = 8 * RB;            // next 8-row group
+    static constexpr uint64_t LAYOUT = RB == 128 ? 2 : (RB == 64 ? 4 : 6);
+    static constexpr int KSTEPS = RB / 32;        // MMAs (8 TF32 of K) per half
+    static constexpr int TMEM_COLS = 4 * NP;      // 2 buffers x 2 halves
+    static constexpr int THREADS = 448;
+    static_assert(NT == 4 || NT == 8 || NT == 16, "columns");
+    static_assert(KC == 4 || KC == 8 || KC == 16, "terms");
+    static_assert(RS >= 4, "raw stages");
+    static_assert((2 * RS + 2 * CS + 5) * 8 + 8 <= 1024, "barriers");
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+// Byte offset, inside a tile written with the TMA swizzle of rows of RB bytes (128: 16-byte
+// chunk index XOR bits 7-9 of the offset; 64: XOR bits 7-8; 32: XOR bit 7), of the logical
+// byte offset `o` = row * RB + byte; the tile starts on a 1024-byte boundary.
+template <int RB>
+__device__ __forceinline__ uint32_t swizzled(uint32_t o) {
+    constexpr uint32_t mask = RB == 128 ? 7u : (RB == 64 ? 3u : 1u);
+    return o ^ (((o >> 7) & mask) << 4);
+}
+
+// x rounded to the nearest TF32 number (the low 13 bits of the result are zero)
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[N]) {
+    static_assert(N == 8 || N == 16 || N == 32, "columns per load");
+    if constexpr (N == 8) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7])
+            : "r"(taddr));
+    } else {
+#pragma unroll
+        for (int q = 0; q < N / 16; ++q) {
+            uint32_t (&part)[16] = *reinterpret_cast<uint32_t (*)[16]>(&r[16 * q]);
+            tmem_ld16(taddr + (uint32_t)(16 * q), part);
+        }
+    }
+}
+
+template <int NT, int KC>
+__global__ void __launch_bounds__(448, 1)
+    k_gemm_thin_tc(const __grid_constant__ ThinTcDesc d, int64_t slices) {
+    using F = ThinTcCfg<NT, KC>;
+    constexpr int RS = F::RS, CS = F::CS, LD = F::LD;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *raw = smem;                   // RS raw stages (TMA)
+    uint8_t *slots = smem + F::RAW;        // CS slots: hi, lo (MMA operands)
+    uint8_t *bhi = slots + CS * F::SLOT, *blo = bhi + F::BPL;
+    float2 *estage = reinterpret_cast<float2 *>(blo + F::BPL);
+    uint64_t *rfull = reinterpret_cast<uint64_t *>(smem + F::BODY);  // TMA -> split
+    uint64_t *rempty = rfull + RS;  // split -> TMA: the raw stage was read (128 arrivals)
+    uint64_t *cfull = rempty + RS;  // split -> MMA: hi / lo (and B') are in place (128)
+    uint64_t *cempty = cfull + CS;  // MMA -> split: the slot was consumed
+    uint64_t *tfull = cempty + CS;  // MMA -> drain: accumulator buffer b is complete
+    uint64_t *tempty = tfull + 2;   // drain -> MMA: buffer b was read (8 arrivals)
+    uint64_t *mdone = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
+    int *aborted = reinterpret_cast<int *>(tmem_slot + 1);
+    const GemmDesc &g = d.g;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tps = (uint32_t)((1ll << g.lm) / 256);  // tiles per slice
+    const uint32_t total = tps * (uint32_t)slices;
+    const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < RS; ++i) {
+            mbar_init(&rfull[i], 1);
+            mbar_init(&rempty[i], 128);
+        }
+        for (int i = 0; i < CS; ++i) {
+            mbar_init(&cfull[i], 128);
+            mbar_init(&cempty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(mdone, 1);
+        *aborted = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&d.tmA))
+                     : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(F::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 12) {
+        // TMA producer: the two halves of every tile of this CTA through the raw ring
+        if (lane == 0) {
+            int it = 0, issued = 0;
+            for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted; t += gridDim.x) {
+                const uint32_t s = t / tps, tile = t - s * tps;
+                const int z = g.sA ? (int)s : 0;
+                bool ok = true;
+                for (int h = 0; h < 2; ++h, ++it) {
+                    const int rs = it % RS;
+                    if (it >= RS && !mbar_wait(&rempty[rs], ((uint32_t)(it / RS) & 1u) ^ 1u,
+                                               globaltimer() + limit)) {
+                        *aborted = 1;
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&rfull[rs], F::HALF);
+                    tma_load_3d(raw + rs * F::HALF, &d.tmA, &rfull[rs], 0,
+                                (int)(tile * 256u + 128u * (uint32_t)h), z);
+                    issued = it + 1;
+                }
+                if (!ok) break;
+            }
+            // loads in flight land before the CTA's shared memory is released
+            const unsigned long long drain = globaltimer() + limit;
+            for (int rs = 0; rs < RS && rs < issued; ++rs) {
+                const int last = ((issued - 1 - rs) / RS) * RS + rs;
+                mbar_wait(&rfull[rs], (uint32_t)(last / RS) & 1u, drain);
+            }
+        }
+    } else if (warp == 13) {
+        // MMA issuer: tile i accumulates into TMEM buffer i & 1, half h into its 32 columns
+        if (lane == 0) {
+            const uint32_t idesc = idesc_mma(2u, BM, F::NP, false);
+            auto sd = [](uint32_t a) { return sdesc_lbo<F::SBO, 16, F::LAYOUT>(a); };
+            const uint64_t bh = sd(smem_u32(bhi)), bl = sd(smem_u32(blo));
+            int it = 0, i = 0;
+            bool any = false;
+            for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted;
+                 t += gridDim.x, ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((i >> 1) - 1) & 1u,
+                                         globaltimer() + limit)) {
+                    *aborted = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool ok = true;
+                for (int h = 0; h < 2; ++h, ++it) {
+                    const int cs = it % CS;
+                    if (!mbar_wait(&cfull[cs], (uint32_t)(it / CS) & 1u, globaltimer() + limit)) {
+                        *aborted = 1;
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t acc = tmem + (uint32_t)((2 * buf + h) * F::NP);
+                    const uint32_t base = smem_u32(slots + cs * F::SLOT);
+                    const uint64_t ah = sd(base), al = sd(base + F::HALF);
+#pragma unroll
+                    for (int kk = 0; kk < F::KSTEPS; ++kk) {
+                        const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                        // the two correction products first, the main one last
+                        umma<4>(acc, ah + adv, bl + adv, idesc, kk > 0 ? 1u : 0u);
+                        umma<4>(acc, al + adv, bh + adv, idesc, 1u);
+                        umma<4>(acc, ah + adv, bh + adv, idesc, 1u);
+                    }
+                    umma_commit(&cempty[cs]);
+                    any = true;
+                }
+                if (!ok) break;
+                umma_commit(&tfull[buf]);
+            }
+            if (any) {
+                umma_commit(mdone);
+                mbar_wait(mdone, 0, globaltimer() + limit);
+            }
+        }
+    } else if (warp >= 8) {
+        // split warps: B' of the current slice (hi / lo), then every half's hi / lo parts
+        const int ts = threadIdx.x - 256;
+        int it = 0, i = 0;
+        int64_t cur = -1;
+        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const uint32_t s = t / tps;
+            const int64_t bs = g.sB ? (int64_t)s : 0;
+            bool ok = !*(volatile int *)aborted;
+            if (ok && bs != cur) {
+                // B' is rewritten only after every MMA that read it has completed (the MMAs of
+                // tile i - 1; those of tile i wait for this group's arrivals below)
+                if (i > 0)
+                    ok = mbar_wait(&tfull[(i - 1) & 1], (uint32_t)((i - 1) >> 1) & 1u,
+                                   globaltimer() + limit);
+                if (ok) {
+                    const float2 *Bs = g.B + bs * g.sB;
+                    for (int e = ts; e < F::NP * 2 * KC; e += 128) {
+                        const int nr = e / (2 * KC), kf = e % (2 * KC);
+                        float v = 0.f;
+                        if (nr < F::NR) {
+                            const float2 b = Bs[(nr >> 1) * KC + (kf >> 1)];
+                            const int c = nr & 1, cp = kf & 1;
+                            v = c == cp ? b.x : (c == 0 ? -b.y : b.y);
+                        }
+                        const float hi = tf32_rna(v);
+                        const uint32_t o = swizzled<F::RB>((uint32_t)(nr * F::RB + kf * 4));
+                        *reinterpret_cast<float *>(bhi + o) = hi;
+                        *reinterpret_cast<float *>(blo + o) = v - hi;
+                    }
+                    cur = bs;
+                }
+            }
+            for (int h = 0; h < 2 && ok; ++h, ++it) {
+                const int rs = it % RS, cs = it % CS;
+                // every thread waits itself: it reads what the TMA wrote, and rewrites a slot
+                // the tensor cores read before
+                ok = mbar_wait(&rfull[rs], (uint32_t)(it / RS) & 1u, globaltimer() + limit);
+                if (ok && it >= CS)
+                    ok = mbar_wait(&cempty[cs], ((uint32_t)(it / CS) & 1u) ^ 1u,
+                                   globaltimer() + limit);
+                if (!ok) break;
+                const float4 *r4 = reinterpret_cast<const float4 *>(raw + rs * F::HALF);
+                float4 *hi4 = reinterpret_cast<float4 *>(slots + cs * F::SLOT);
+                float4 *lo4 = reinterpret_cast<float4 *>(slots + cs * F::SLOT + F::HALF);
+                constexpr int U = F::HALF / 16 / 128;  // 16-byte words per thread
+                float4 v[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) v[q] = r4[ts + 128 * q];
+                mbar_arrive(&rempty[rs]);  // the raw stage may be refilled
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const float4 hv = make_float4(tf32_rna(v[q].x), tf32_rna(v[q].y),
+                                                  tf32_rna(v[q].z), tf32_rna(v[q].w));
+                    hi4[ts + 128 * q] = hv;
+                    lo4[ts + 128 * q] = make_float4(v[q].x - hv.x, v[q].y - hv.y,
+                                                    v[q].z - hv.z, v[q].w - hv.w);
+                }
+                // generic-proxy writes, then the tensor cores (async proxy) read them
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&cfull[cs]);
+            }
+            // the group leaves together once any of its waits ran out
+            if (!named_and(3, 128, ok)) {
+                if (ts == 0) *aborted = 1;
+                break;
+            }
+        }
+    } else {
+        // drain warps: thread tid holds row tid of the tile (TMEM lane 32 (warp % 4) + lane of
+        // half warp / 4) and writes the tile in C's order, 8 consecutive elements per task
+        const int tid = threadIdx.x;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const int half = warp >> 2;
+        auto soff = [&](int sq) { return (sq & 128) ? (LD << (sq & 127)) : (1 << sq); };
+        int w8[8];
+        {
+            const int d0 = soff(g.tb_src[0]), d1 = soff(g.tb_src[1]), d2 = soff(g.tb_src[2]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
+        }
+        // two lanes share each run of 8 (complex64: lane half h writes elements 4j + 2h and
+        // 4j + 2h + 1 in its store j; planar 16-bit results: the even lane alone)
+        constexpr int TASKS = 256 * NT / 8, SUBS = TASKS * 2, SPT = (SUBS + 255) / 256;
+        int ws[SPT];
+        uint64_t os[SPT];
+        const int d0 = w8[1], d1 = w8[2], d2 = w8[4];
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+            const int u = tid + 256 * q, r = u >> 1, h = u & 1;
+            ws[q] = h ? d1 : 0;
+            os[q] = h ? 2 : 0;
+            for (int b = 3; b < g.tile_bits; ++b)
+                if ((r >> (b - 3)) & 1) {
+                    ws[q] += soff(g.tb_src[b]);
+                    os[q] |= 1ull << g.tb_pos[b];
+                }
+        }
+        // C offset of tile t of a slice: deposit(t * 256); the warp's lanes take one bit each
+        auto tile_base = [&](uint32_t t) {
+            uint64_t r = 0;
+            for (int b = 8 + lane; b < g.lm; b += 32)
+                if ((t >> (b - 8)) & 1u) r |= 1ull << g.posC_m[b];
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)r);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(r >> 32));
+            return ((uint64_t)hi << 32) | lo;
+        };
+        float cr[NT], ci[NT];
+        float amx = 0.f;
+        int cur_s = -1, eo = 0, i = 0;
+        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            bool ok = true;
+            if (lane == 0)
+                ok = mbar_wait(&tfull[buf], (uint32_t)(i >> 1) & 1u, globaltimer() + limit) &&
+                     !*(volatile int *)aborted;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!named_and(2, 256, ok)) {
+                if (tid == 0) *aborted = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t v[F::NR < 16 ? 8 : F::NR];
+            tmem_ld_cols(tmem + lane_base + (uint32_t)((2 * buf + half) * F::NP), v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                cr[n] = __uint_as_float(v[2 * n]);
+                ci[n] = __uint_as_float(v[2 * n + 1]);
+            }
+            const uint32_t s = t / tps, tile = t - s * tps;
+            if ((int)s != cur_s) {
+                if (cur_s >= 0 && g.amax_out) amax_publish(g.amax_out + cur_s, amx);
+                amx = 0.f;
+                cur_s = (int)s;
+                eo = g.planar_out ? planar_out_exponent(g.pout, s) : 0;
+            }
+            if (g.planar_out && tile == 0 && tid == 0) g.pout.exps[s] = eo;
+            // stage buffer i & 1 was last read two tiles ago, before every thread passed the
+            // barrier of the previous tile
+            float2 *stage = estage + (size_t)buf * 256 * LD;
+#pragma unroll
+            for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
+            named_sync(1, 256);
+            const uint64_t cbase = tile_base(tile);
+            if (g.planar_out) {
+                if ((tid & 1) == 0) {
+#pragma unroll
+                    for (int q = 0; q < SPT; ++q) {
+                        if (SUBS % 256 != 0 && tid + 256 * q >= SUBS) break;
+                        float2 w[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            w[j] = stage[ws[q] + w8[j]];
+                            amx = fmaxf(amx, fmaxf(fabsf(w[j].x), fabsf(w[j].y)));
+                        }
+                        planar_out_store8(g.pout, s, cbase | os[q], w, eo);
+                    }
+                }
+            } else {
+                float2 *C = g.C + (int64_t)s * g.sC + cbase;
+#pragma unroll
+                for (int q = 0; q < SPT; ++q) {
+                    if (SUBS % 256 != 0 && tid + 256 * q >= SUBS) break;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int w = ws[q] + (j ? d2 : 0);
+                        const float2 v0 = stage[w], v1 = stage[w + d0];
+                        amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
+                                               fmaxf(fabsf(v1.x), fabsf(v1.y))));
+                        *reinterpret_cast<float4 *>(C + (os[q] + 4 * j)) =
+                            make_float4(v0.x, v0.y, v1.x, v1.y);
+                    }
+                }
+            }
+        }
+        if (cur_s >= 0 && g.amax_out) amax_publish(g.amax_out + cur_s, amx);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(F::TMEM_COLS));
+}
+
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -1330,7 +1741,7 @@ template <int ESZ, int RB, int BNP, int NPL>
 cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     using F = PersCfg<ESZ, RB, BNP, NPL>;
     // tile rows and columns index the deposit tables with 24 bits each; tiles count in 32 bits
-    if (d.ln < F::LBN || d.lk < 3 || d.lk > 9 || d.lm > 31 || d.ln > 31 ||
+    if (d.ln < F::LBN || d.lk < 3 || d.lk > (NPL == 4 ? 9 : 12) || d.lm > 31 || d.ln > 31 ||
         (d.dtype == 2) != (ESZ == 4))
         return cudaErrorInvalidValue;
     const int64_t tiles_n = (1ll << d.ln) / BNP;
@@ -1345,6 +1756,23 @@ cudaError_t launch_pers(const TcGemmDesc &d, int64_t slices, cudaStream_t st) {
     else
         k_gemm_tc_pers<ESZ, RB, false, BNP, NPL>
             <<<(unsigned)grid, PERS_THREADS, F::SMEM_BYTES, st>>>(d, tiles_n, slices);
+    return cudaGetLastError();
+}
+
+template <int NT, int KC>
+cudaError_t configure_thin_tc() {
+    return cudaFuncSetAttribute(k_gemm_thin_tc<NT, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                ThinTcCfg<NT, KC>::SMEM_BYTES);
+}
+
+template <int NT, int KC>
+cudaError_t launch_thin_tc_t(const ThinTcDesc &d, int64_t slices, cudaStream_t st) {
+    using F = ThinTcCfg<NT, KC>;
+    const int64_t total = ((1ll << d.g.lm) / 256) * slices;
+    if (total > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+    int64_t grid = sm_count();
+    if (grid > total) grid = total;
+    k_gemm_thin_tc<NT, KC><<<(unsigned)grid, F::THREADS, F::SMEM_BYTES, st>>>(d, slices);
     return cudaGetLastError();
 }
 
@@ -1415,6 +1843,15 @@ cudaError_t tc_prepare() {
     if (e == cudaSuccess) e = configure_pers_bn<128, 4>();
     if (e == cudaSuccess) e = configure_pers_bn<64, 4>();
     if (e == cudaSuccess) e = configure_pers_bn<32, 4>();
+    if (e == cudaSuccess) e = configure_thin_tc<4, 4>();
+    if (e == cudaSuccess) e = configure_thin_tc<4, 8>();
+    if (e == cudaSuccess) e = configure_thin_tc<4, 16>();
+    if (e == cudaSuccess) e = configure_thin_tc<8, 4>();
+    if (e == cudaSuccess) e = configure_thin_tc<8, 8>();
+    if (e == cudaSuccess) e = configure_thin_tc<8, 16>();
+    if (e == cudaSuccess) e = configure_thin_tc<16, 4>();
+    if (e == cudaSuccess) e = configure_thin_tc<16, 8>();
+    if (e == cudaSuccess) e = configure_thin_tc<16, 16>();
 #define TN_TC_CONFIGURE(id, npl, bk, bn, stg, minb, esz) \
     if (e == cudaSuccess) e = configure_variant<npl, bk, bn, stg, minb, esz>();
     TN_TC_VARIANTS(TN_TC_CONFIGURE)
@@ -1530,8 +1967,12 @@ void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits) {
 
 bool tc_variant_fits(int variant, int lk, int ln) {
     if (is_pers(variant)) {
-        const int bn = pers_bn(variant);
-        return lk >= 3 && lk <= 9 && (bn == 128 ? ln >= 7 : (bn == 64 ? ln == 6 : ln == 5));
+        // K up to 512 in every form; the 4M forms with 64-byte rows also take K up to 4096
+        // (candidates of the autotuner: with K of 1024 the one-tile kernel's epilogue, not
+        // overlapped with the next tile's products, costs ~20% of a 128 x 256 tile)
+        const int bn = pers_bn(variant), base = pers_base(variant);
+        const int kmax = (!pers_split(variant) && (base == kPersFp16 || base == kPersTf32)) ? 12 : 9;
+        return lk >= 3 && lk <= kmax && (bn == 128 ? ln >= 7 : (bn == 64 ? ln == 6 : ln == 5));
     }
     const int bk = tc_variant_bk(variant), bn = tc_variant_bn(variant);
     if (bk == 0) return false;
@@ -1601,6 +2042,34 @@ cudaError_t launch_gemm_tc(const TcGemmDesc &d, int64_t slices, cudaStream_t st)
     case id: return launch_variant<npl, bk, bn, stg, minb, esz>(d, slices, st);
         TN_TC_VARIANTS(TN_TC_LAUNCH)
 #undef TN_TC_LAUNCH
+    }
+    return cudaErrorInvalidValue;
+}
+
+
+bool thin_tc_fits(int lm, int ln, int lk) {
+    return lm >= 8 && lm <= 30 && ln >= 2 && ln <= 4 && lk >= 2 && lk <= 4;
+}
+
+int encode_tmap_thin(void *tmap_host, const void *A, int lm, int lk, int64_t depth) {
+    // A as [depth][2^lm rows][2 KC floats], one 128-row half per box
+    return encode_tmap_planar(tmap_host, A, 2ll << lk, 1ll << lm, depth, 2, 2 << lk, 128);
+}
+
+cudaError_t launch_gemm_thin_tc(const ThinTcDesc &d, int64_t slices, cudaStream_t st) {
+    const GemmDesc &g = d.g;
+    if (!thin_tc_fits(g.lm, g.ln, g.lk) || g.tile_bits != 8 + g.ln || slices < 1)
+        return cudaErrorInvalidValue;
+    switch (g.ln * 8 + g.lk) {
+        case 2 * 8 + 2: return launch_thin_tc_t<4, 4>(d, slices, st);
+        case 2 * 8 + 3: return launch_thin_tc_t<4, 8>(d, slices, st);
+        case 2 * 8 + 4: return launch_thin_tc_t<4, 16>(d, slices, st);
+        case 3 * 8 + 2: return launch_thin_tc_t<8, 4>(d, slices, st);
+        case 3 * 8 + 3: return launch_thin_tc_t<8, 8>(d, slices, st);
+        case 3 * 8 + 4: return launch_thin_tc_t<8, 16>(d, slices, st);
+        case 4 * 8 + 2: return launch_thin_tc_t<16, 4>(d, slices, st);
+        case 4 * 8 + 3: return launch_thin_tc_t<16, 8>(d, slices, st);
+        case 4 * 8 + 4: return launch_thin_tc_t<16, 16>(d, slices, st);
     }
     return cudaErrorInvalidValue;
 }

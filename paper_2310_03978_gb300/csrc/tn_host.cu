@@ -158,6 +158,7 @@ struct Step {
     int form = TN_GEMM_4M;
     int splits = 1;              // K_GEMM split-K factor
     bool tune_form = false;      // autotune: 3M is still a candidate for this K_TC step
+    bool thin_tc = false;        // K_STREAM on the tensor cores (k_gemm_thin_tc)
     int variant = -1;            // K_TC kernel variant
     int out_meta = -1;           // meta block whose per-slice max-abs this step's epilogue records
     int direct_planar = -1;      // planar copy this step writes directly instead of complex64
@@ -659,6 +660,19 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
         st.kernel = route(st, mode, p->tc_ok);
         // slice-independent steps run once per call; they stay on the CUDA cores
         if (!st.dep && st.kernel == K_TC) st.kernel = K_GEMM;
+        // a streaming step with K = 16 takes the tensor cores (compensated TF32, FP32-level
+        // accuracy) in the tensor-core modes: on the CUDA cores its 4 * NT * 16 multiply-adds
+        // per row and their operand reads keep it below memory speed (measured on GB300 at
+        // 2^24-2^26 rows: 4, 8, 16 columns 3.6, 2.8, 3.3 TB/s there against 3.8, 4.2, 5.3 on
+        // the tensor cores); with K <= 8 the CUDA-core kernel is the faster one (3.9-6.7 TB/s
+        // against 2.7-4.1).  opts.thin_tc > 0 sends every step that fits, < 0 none
+        if (st.kernel == K_STREAM && mode != TN_PREC_C64 && p->tc_ok && st.dep) {
+            const int wide = (int)std::max(st.M.size(), st.N.size());
+            const int narrow = (int)std::min(st.M.size(), st.N.size());
+            const int lk = (int)st.K.size();
+            st.thin_tc = tn::thin_tc_fits(wide, narrow, lk) &&
+                         (p->opts.thin_tc > 0 || (p->opts.thin_tc == 0 && lk == 4));
+        }
         if (mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 ||
             mode == TN_PREC_SPLIT_TF32 || mode == TN_PREC_MIXED)
             st.form = kFormSplit;
@@ -1448,9 +1462,21 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
             return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the thin tile",
                         (int)(&st - &p->steps[0]));
-        if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
-        e = tn::launch_gemm_thin(d, slices, stream);
-        if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
+        if (st.thin_tc) {
+            tn::ThinTcDesc td;
+            memset(&td, 0, sizeof td);
+            td.g = d;
+            if (tn::encode_tmap_thin(&td.tmA, d.A, d.lm, d.lk, d.sA ? slices : 1) != 0)
+                return fail(TN_ERR_CUDA, "step %d: tensor map of the thin operand",
+                            (int)(&st - &p->steps[0]));
+            if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
+            e = tn::launch_gemm_thin_tc(td, slices, stream);
+            if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
+        } else {
+            if (ev) TN_CUDA(cudaEventRecord(ev->first, stream));
+            e = tn::launch_gemm_thin(d, slices, stream);
+            if (ev) TN_CUDA(cudaEventRecord(ev->second, stream));
+        }
         p->launches += 1;
     } else if (st.kernel == K_GEMM) {
         tn::GemmDesc d{};
@@ -1559,7 +1585,7 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
         return fail(TN_ERR_INVALID_ARG, "bad step index");
     const Step &st = p->steps[(size_t)step];
     memset(out, 0, sizeof *out);
-    out->kernel = st.kernel;
+    out->kernel = st.thin_tc ? 4 : st.kernel;
     out->slice_dependent = st.dep ? 1 : 0;
     out->log2_m = (int)st.M.size();
     out->log2_n = (int)st.N.size();

@@ -321,6 +321,20 @@ bool tc_variant_is_pers(int variant);  // the persistent short-K kernel (one CTA
 // staging) or 32 four-byte banks (bits = 5, packed 16-bit re / im).
 void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits);
 
+// Thin step on the tensor cores (k_gemm_thin_tc): the streaming step of GemmDesc g (A the large
+// complex64 operand [slices][2^lm][2^lk], B the small one [slices][2^ln][2^lk], tiles of 256
+// rows and 2^ln columns staged like the CUDA-core thin kernel's) as one real TF32 product with
+// compensated (hi / lo) operands.  tmA: A as [depth][2^lm rows][2^(lk+1) floats] with boxes of
+// 128 rows (encode_tmap_thin; depth = slices when A depends on the slice, else 1).
+struct ThinTcDesc {
+    CUtensorMap tmA;
+    GemmDesc g;
+    uint64_t wait_limit_ns;    // bound of every mbarrier wait (0 = 4 s)
+};
+bool thin_tc_fits(int lm, int ln, int lk);  // 2^8 <= M <= 2^30 rows, 4-16 columns, 4-16 terms
+int encode_tmap_thin(void *tmap_host, const void *A, int lm, int lk, int64_t depth);
+cudaError_t launch_gemm_thin_tc(const ThinTcDesc &d, int64_t slices, cudaStream_t st);
+
 }  // namespace tn
 
 // A loaded network (tn_network_load): labels and offsets on the host, the complex128 data on the

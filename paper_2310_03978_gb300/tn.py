@@ -21,7 +21,7 @@ STATUS = {0: "TN_OK", 1: "TN_ERR_INVALID_ARG", 2: "TN_ERR_SHAPE", 3: "TN_ERR_PAT
 PRECISION = {"c64": 0, "tf32": 1, "split_tf32": 2, "fp16_scaled": 3, "bf16_scaled": 4,
              "split_bf16": 5, "split_fp16": 6, "mixed": 7}
 GEMM_FORM = {"auto": 0, "4m": 1, "3m": 2}
-KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc"}
+KERNELS = {0: "generic", 1: "stream", 2: "gemm_simt", 3: "gemm_tc", 4: "thin_tc"}
 
 # Every symbol declared in include/tn.h.
 EXPORTS = ("tn_network_load", "tn_network_set_data", "tn_plan", "tn_plan_get_info",
@@ -36,7 +36,7 @@ class PlanOptions(C.Structure):
                 ("workspace", C.c_void_p), ("gemm_form", C.c_int32),
                 ("sync_each_call", C.c_int32), ("use_graph", C.c_int32),
                 ("profile", C.c_int32), ("tc_bk", C.c_int32), ("tc_bn", C.c_int32),
-                ("autotune", C.c_int32), ("mixed_topk", C.c_int32), ("reserved0", C.c_int32),
+                ("autotune", C.c_int32), ("mixed_topk", C.c_int32), ("thin_tc", C.c_int32),
                 ("eps_budget", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
@@ -265,7 +265,7 @@ class Plan:
     def __init__(self, network: Network, path, sliced=(), mode="c64", max_slices_in_flight=0,
                  workspace_limit=0, workspace=None, gemm_form="auto", sync_each_call=False,
                  profile=False, use_graph=False, tc_bk=0, tc_bn=0, autotune=False,
-                 mixed_topk=0, eps_budget=0.0):
+                 mixed_topk=0, eps_budget=0.0, thin_tc=0):
         self.network = network
         opts = PlanOptions()
         opts.max_slices_in_flight = int(max_slices_in_flight)
@@ -283,6 +283,7 @@ class Plan:
         opts.autotune = 1 if autotune else 0
         opts.mixed_topk = int(mixed_topk)
         opts.eps_budget = float(eps_budget)
+        opts.thin_tc = int(thin_tc)
         pp = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1))
         sl = np.ascontiguousarray(np.asarray(list(sliced), dtype=np.int32))
         h = C.c_void_p()

@@ -267,8 +267,85 @@ def test_thin_steps_stream_kernel(tn, shape):
     ref2 = O.contract(t2, l2, out, [(0, 1), (0, 2)])
     for mode in ("c64", "fp16_scaled"):
         got2, info, k2 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode=mode)
-        assert info["slices_in_flight"] == 2 and k2[0] == "stream"
+        assert info["slices_in_flight"] == 2 and k2[0] == thin_kernel(shape, mode)
         check(got2, ref2, 1e-5)
+
+
+def thin_kernel(shape, mode, thin_tc=0):
+    """The kernel a slice-dependent streaming step of GEMM extents (lm, ln, lk) runs on: the
+    tensor cores in the tensor-core modes for 4-16 columns and 4-16 terms (by default with 16
+    terms), else the CUDA cores."""
+    lm, ln, lk = shape
+    wide, narrow = max(lm, ln), min(lm, ln)
+    fits = 8 <= wide <= 30 and 2 <= narrow <= 4 and 2 <= lk <= 4
+    on = thin_tc > 0 or (thin_tc == 0 and lk == 4)
+    return "thin_tc" if mode != "c64" and fits and on else "stream"
+
+
+# (lm, ln, lk): every column / term count of the tensor-core thin kernel, the small operand on
+# either side, 4 tiles (2^10 rows) up to a ragged multiple of the SM count of tiles
+THIN_TC_SHAPES = [(12, 2, 2), (11, 2, 3), (13, 2, 4), (12, 3, 2), (3, 12, 3), (12, 3, 4),
+                  (12, 4, 2), (11, 4, 3), (4, 12, 4), (10, 4, 4), (16, 4, 4), (17, 3, 3)]
+
+
+@pytest.mark.parametrize("shape", THIN_TC_SHAPES)
+def test_thin_steps_on_the_tensor_cores(tn, shape):
+    # the streaming step as one real TF32 product with compensated operands (Sec. 4.2's 3xTF32):
+    # FP32-level accuracy against the oracle, one slice and 2 slices in flight (the large
+    # operand sliced; the small one sliced too); the CUDA-core form of the same step agrees
+    rng = np.random.default_rng(700 + 3 * shape[0] + 5 * shape[1] + shape[2])
+    tensors, labels, out = single_step(rng, *shape)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    A, B = tensors
+    v = crandn(rng, 1)
+    big = 0 if shape[0] >= shape[1] else 1
+    t2 = [A, B, np.ones(2, complex)]
+    t2[big] = tensors[big][None] * v.reshape(2, *([1] * tensors[big].ndim))
+    l2 = [list(labels[0]), list(labels[1]), [900]]
+    l2[big] = [900] + l2[big]
+    ref2 = O.contract(t2, l2, out, [(0, 1), (0, 2)])
+    # both operands sliced: the small one varies with the slice too
+    w = crandn(rng, 1)
+    t3 = list(t2)
+    t3[1 - big] = tensors[1 - big][None] * w.reshape(2, *([1] * tensors[1 - big].ndim))
+    l3 = [list(l2[0]), list(l2[1]), [900]]
+    l3[1 - big] = [900] + l3[1 - big]
+    ref3 = O.contract(t3, l3, out, [(0, 1), (0, 2)])
+    for mode in ("fp16_scaled", "tf32"):
+        for flag in (1, -1):
+            kind = "thin_tc" if flag > 0 else "stream"
+            got2, info, k2 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode=mode,
+                                      thin_tc=flag)
+            assert info["slices_in_flight"] == 2 and k2[0] == kind
+            check(got2, ref2, 1e-5)
+            got3, _, k3 = gpu_amps(tn, t3, l3, out, [(0, 1), (0, 2)], [900], mode=mode,
+                                   thin_tc=flag)
+            assert k3[0] == kind
+            check(got3, ref3, 1e-5)
+        # the automatic choice
+        _, _, k4 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode=mode)
+        assert k4[0] == thin_kernel(shape, mode)
+    # the complex64 mode keeps the CUDA cores whatever the option says
+    _, _, k5 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode="c64", thin_tc=1)
+    assert k5[0] == "stream"
+
+
+def test_thin_tensor_core_step_far_magnitudes(tn):
+    # operands near 2^-60 and 2^+40 (FP32 range, far from 1): the hi / lo split is relative, so
+    # the compensated products keep their accuracy at any scale
+    rng = np.random.default_rng(777)
+    for sa, sb in ((2.0 ** -60, 2.0 ** -50), (2.0 ** 40, 2.0 ** -30)):
+        tensors, labels, out = single_step(rng, 14, 4, 4)
+        tensors = [tensors[0] * sa, tensors[1] * sb]
+        v = crandn(rng, 1)
+        t2 = [tensors[0][None] * v.reshape(2, *([1] * tensors[0].ndim)), tensors[1],
+              np.ones(2, complex)]
+        l2 = [[900] + labels[0], labels[1], [900]]
+        ref = O.contract(t2, l2, out, [(0, 1), (0, 2)])
+        got, _, k = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode="fp16_scaled",
+                             thin_tc=1)
+        assert k[0] == "thin_tc"
+        check(got, ref, 1e-5)
 
 
 # (form, K-tile preference, N-tile preference): every tensor-core kernel variant
@@ -615,7 +692,8 @@ def test_chained_steps_feed_the_tensor_cores(tn, lk1, first, mode):
 
 @pytest.mark.parametrize("mode", ["fp16_scaled", "bf16_scaled", "split_fp16", "tf32"])
 @pytest.mark.parametrize("nsl", [0, 1])
-def test_thin_step_feeds_the_tensor_cores(tn, mode, nsl):
+@pytest.mark.parametrize("thin_tc", [1, -1])
+def test_thin_step_feeds_the_tensor_cores(tn, mode, nsl, thin_tc):
     # step 1 is thin (2^11 x 8, k = 4: the streaming kernel) and its result is an operand of
     # the tensor-core step 2 (m = 2^7, n = 2^8, k = 2^7): for single-pass consumers it writes
     # the planar 16-bit copy itself, with an exponent bounded from its inputs' max-abs (its
@@ -633,8 +711,10 @@ def test_thin_step_feeds_the_tensor_cores(tn, mode, nsl):
     path = [(0, 1), (0, 2)]
     sliced = [a[9]] if nsl else []
     ref = O.contract(tensors, labels, out, path)
-    got, info, kernels = gpu_amps(tn, tensors, labels, out, path, sliced, mode=mode)
-    assert kernels == ["stream", "gemm_tc"]
+    got, info, kernels = gpu_amps(tn, tensors, labels, out, path, sliced, mode=mode,
+                                  thin_tc=thin_tc)
+    first = "thin_tc" if thin_tc > 0 else "stream"
+    assert kernels == [first, "gemm_tc"]
     check(got, ref, TOL[mode])
 
 
