@@ -423,16 +423,18 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
     // a tile has 256 * NT elements (tile_bits = 8 + log2 NT): 32 * NT runs of 8 consecutive
     // elements of C; their stage and C offsets are the same for every tile, so they are set once
     constexpr int TASKS = kThinRows * NT / 8;
-    // two lanes share each run of 8: for complex64 results lane half h writes elements 4j + 2h
-    // and 4j + 2h + 1 in its store j, so each store instruction fills whole 32-byte sectors; a
-    // planar 16-bit result (16 bytes per plane and run) is written by the even lane alone
-    constexpr int SUBS = TASKS * 2, SPT = (SUBS + 255) / 256;
+    // complex64 results: two lanes share each run of 8 (lane half h writes elements 4j + 2h and
+    // 4j + 2h + 1 in its store j, so each store instruction fills whole 32-byte sectors); planar
+    // 16-bit results (16 bytes per plane and run): a lane writes whole runs, consecutive lanes
+    // consecutive runs
+    constexpr int SUBS = TASKS * 2, SPT = (SUBS + 255) / 256, SPTP = (TASKS + 255) / 256;
     int ws[SPT];
     uint64_t os[SPT];
     const int d0 = w8[1], d1 = w8[2], d2 = w8[4];
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-        const int u = tid + 256 * i, r = u >> 1, h = u & 1;
+        const int u = tid + 256 * i;
+        const int r = d.planar_out ? u : u >> 1, h = d.planar_out ? 0 : u & 1;
         ws[i] = h ? d1 : 0;
         os[i] = h ? 2 : 0;
         for (int q = 3; q < d.tile_bits; ++q)
@@ -454,18 +456,16 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         __syncthreads();
         float2 *C = d.C + s * d.sC + cbase;
         if (d.planar_out) {
-            if ((tid & 1) == 0) {
 #pragma unroll
-                for (int i = 0; i < SPT; ++i) {
-                    if (SUBS % 256 != 0 && tid + 256 * i >= SUBS) break;
-                    float2 v[8];
+            for (int i = 0; i < SPTP; ++i) {
+                if (TASKS % 256 != 0 && tid + 256 * i >= TASKS) break;
+                float2 v[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        v[j] = stage[ws[i] + w8[j]];
-                        amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
-                    }
-                    planar_out_store8(d.pout, s, cbase | os[i], v, eo);
+                for (int j = 0; j < 8; ++j) {
+                    v[j] = stage[ws[i] + w8[j]];
+                    amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
                 }
+                planar_out_store8(d.pout, s, cbase | os[i], v, eo);
             }
         } else {
 #pragma unroll

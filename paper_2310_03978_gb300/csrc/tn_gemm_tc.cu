@@ -1203,8 +1203,9 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
 // 2 NT).  Warps 0-7 drain the accumulator (warp w reads TMEM lanes 32 (w % 4).. of half w / 4,
 // so thread t holds row t of the tile) and write the tile in C's order through a shared-memory
 // stage, 8 consecutive elements of C per task as the CUDA-core thin kernel does; warps 8-11
-// split the halves and build B' hi / lo when the slice changes; warp 12 issues the TMA loads,
-// warp 13 the MMAs.  Every wait is bounded; a wait that runs out sets the status word and the
+// split the halves; warp 12 issues the TMA loads, warp 13 the MMAs; B' hi / lo is built by all
+// threads before the roles start.
+// Grid row y is slice y (about one CTA per SM in all); its CTAs walk the slice's tiles.  Every wait is bounded; a wait that runs out sets the status word and the
 // abort flag, and every role leaves its loop.
 template <int NT, int KC>
 struct ThinTcCfg {
@@ -1295,8 +1296,9 @@ __global__ void __launch_bounds__(448, 1)
     int *aborted = reinterpret_cast<int *>(tmem_slot + 1);
     const GemmDesc &g = d.g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // grid row y = slice s; the CTAs of a row walk the slice's 256-row tiles
+    const uint32_t s = blockIdx.y;
     const uint32_t tps = (uint32_t)((1ll << g.lm) / 256);  // tiles per slice
-    const uint32_t total = tps * (uint32_t)slices;
     const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
 
     if (threadIdx.x == 0) {
@@ -1324,6 +1326,25 @@ __global__ void __launch_bounds__(448, 1)
                      "r"(F::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // B' of the slice (hi / lo parts), written by every thread before the roles start
+    {
+        const float2 *Bs = g.B + (g.sB ? (int64_t)s : 0) * g.sB;
+        for (int e = threadIdx.x; e < F::NP * 2 * KC; e += F::THREADS) {
+            const int nr = e / (2 * KC), kf = e % (2 * KC);
+            float v = 0.f;
+            if (nr < F::NR) {
+                const float2 b = Bs[(nr >> 1) * KC + (kf >> 1)];
+                const int c = nr & 1, cp = kf & 1;
+                v = c == cp ? b.x : (c == 0 ? -b.y : b.y);
+            }
+            const float hi = tf32_rna(v);
+            const uint32_t o = swizzled<F::RB>((uint32_t)(nr * F::RB + kf * 4));
+            *reinterpret_cast<float *>(bhi + o) = hi;
+            *reinterpret_cast<float *>(blo + o) = v - hi;
+        }
+        // generic-proxy writes, read by the tensor cores (async proxy) after the barrier
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1333,9 +1354,9 @@ __global__ void __launch_bounds__(448, 1)
         // TMA producer: the two halves of every tile of this CTA through the raw ring
         if (lane == 0) {
             int it = 0, issued = 0;
-            for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted; t += gridDim.x) {
-                const uint32_t s = t / tps, tile = t - s * tps;
-                const int z = g.sA ? (int)s : 0;
+            const int z = g.sA ? (int)s : 0;
+            for (uint32_t tile = blockIdx.x; tile < tps && !*(volatile int *)aborted;
+                 tile += gridDim.x) {
                 bool ok = true;
                 for (int h = 0; h < 2; ++h, ++it) {
                     const int rs = it % RS;
@@ -1367,8 +1388,8 @@ __global__ void __launch_bounds__(448, 1)
             const uint64_t bh = sd(smem_u32(bhi)), bl = sd(smem_u32(blo));
             int it = 0, i = 0;
             bool any = false;
-            for (uint32_t t = blockIdx.x; t < total && !*(volatile int *)aborted;
-                 t += gridDim.x, ++i) {
+            for (uint32_t tile = blockIdx.x; tile < tps && !*(volatile int *)aborted;
+                 tile += gridDim.x, ++i) {
                 const int buf = i & 1;
                 if (i >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((i >> 1) - 1) & 1u,
                                          globaltimer() + limit)) {
@@ -1408,38 +1429,11 @@ __global__ void __launch_bounds__(448, 1)
             }
         }
     } else if (warp >= 8) {
-        // split warps: B' of the current slice (hi / lo), then every half's hi / lo parts
+        // split warps: every half's hi / lo parts
         const int ts = threadIdx.x - 256;
-        int it = 0, i = 0;
-        int64_t cur = -1;
-        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const uint32_t s = t / tps;
-            const int64_t bs = g.sB ? (int64_t)s : 0;
+        int it = 0;
+        for (uint32_t tile = blockIdx.x; tile < tps; tile += gridDim.x) {
             bool ok = !*(volatile int *)aborted;
-            if (ok && bs != cur) {
-                // B' is rewritten only after every MMA that read it has completed (the MMAs of
-                // tile i - 1; those of tile i wait for this group's arrivals below)
-                if (i > 0)
-                    ok = mbar_wait(&tfull[(i - 1) & 1], (uint32_t)((i - 1) >> 1) & 1u,
-                                   globaltimer() + limit);
-                if (ok) {
-                    const float2 *Bs = g.B + bs * g.sB;
-                    for (int e = ts; e < F::NP * 2 * KC; e += 128) {
-                        const int nr = e / (2 * KC), kf = e % (2 * KC);
-                        float v = 0.f;
-                        if (nr < F::NR) {
-                            const float2 b = Bs[(nr >> 1) * KC + (kf >> 1)];
-                            const int c = nr & 1, cp = kf & 1;
-                            v = c == cp ? b.x : (c == 0 ? -b.y : b.y);
-                        }
-                        const float hi = tf32_rna(v);
-                        const uint32_t o = swizzled<F::RB>((uint32_t)(nr * F::RB + kf * 4));
-                        *reinterpret_cast<float *>(bhi + o) = hi;
-                        *reinterpret_cast<float *>(blo + o) = v - hi;
-                    }
-                    cur = bs;
-                }
-            }
             for (int h = 0; h < 2 && ok; ++h, ++it) {
                 const int rs = it % RS, cs = it % CS;
                 // every thread waits itself: it reads what the TMA wrote, and rewrites a slot
@@ -1453,20 +1447,22 @@ __global__ void __launch_bounds__(448, 1)
                 float4 *hi4 = reinterpret_cast<float4 *>(slots + cs * F::SLOT);
                 float4 *lo4 = reinterpret_cast<float4 *>(slots + cs * F::SLOT + F::HALF);
                 constexpr int U = F::HALF / 16 / 128;  // 16-byte words per thread
-                float4 v[U];
-#pragma unroll
-                for (int q = 0; q < U; ++q) v[q] = r4[ts + 128 * q];
-                mbar_arrive(&rempty[rs]);  // the raw stage may be refilled
 #pragma unroll
                 for (int q = 0; q < U; ++q) {
-                    const float4 hv = make_float4(tf32_rna(v[q].x), tf32_rna(v[q].y),
-                                                  tf32_rna(v[q].z), tf32_rna(v[q].w));
+                    const float4 v = r4[ts + 128 * q];
+                    const float4 hv = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z),
+                                                  tf32_rna(v.w));
                     hi4[ts + 128 * q] = hv;
-                    lo4[ts + 128 * q] = make_float4(v[q].x - hv.x, v[q].y - hv.y,
-                                                    v[q].z - hv.z, v[q].w - hv.w);
+                    lo4[ts + 128 * q] = make_float4(v.x - hv.x, v.y - hv.y, v.z - hv.z,
+                                                    v.w - hv.w);
                 }
-                // generic-proxy writes, then the tensor cores (async proxy) read them
+                // the slot's generic-proxy writes, then the tensor cores (async proxy) read them;
+                // the raw stage is released only now, after every value read from it has been
+                // used: an arrive right after the loads let the next TMA write (fast when the
+                // rows come from L2, as when all slices share the large operand) overtake
+                // loads still queued, and a few rows of a tile came out wrong
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&rempty[rs]);
                 mbar_arrive(&cfull[cs]);
             }
             // the group leaves together once any of its waits ran out
@@ -1489,15 +1485,17 @@ __global__ void __launch_bounds__(448, 1)
             for (int j = 0; j < 8; ++j)
                 w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
         }
-        // two lanes share each run of 8 (complex64: lane half h writes elements 4j + 2h and
-        // 4j + 2h + 1 in its store j; planar 16-bit results: the even lane alone)
+        // complex64: two lanes share each run of 8 (lane half h writes elements 4j + 2h and
+        // 4j + 2h + 1 in its store j); planar 16-bit results: a lane writes whole runs
         constexpr int TASKS = 256 * NT / 8, SUBS = TASKS * 2, SPT = (SUBS + 255) / 256;
+        constexpr int SPTP = (TASKS + 255) / 256;
         int ws[SPT];
         uint64_t os[SPT];
         const int d0 = w8[1], d1 = w8[2], d2 = w8[4];
 #pragma unroll
         for (int q = 0; q < SPT; ++q) {
-            const int u = tid + 256 * q, r = u >> 1, h = u & 1;
+            const int u = tid + 256 * q;
+            const int r = g.planar_out ? u : u >> 1, h = g.planar_out ? 0 : u & 1;
             ws[q] = h ? d1 : 0;
             os[q] = h ? 2 : 0;
             for (int b = 3; b < g.tile_bits; ++b)
@@ -1517,8 +1515,10 @@ __global__ void __launch_bounds__(448, 1)
         };
         float cr[NT], ci[NT];
         float amx = 0.f;
-        int cur_s = -1, eo = 0, i = 0;
-        for (uint32_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+        const int eo = g.planar_out ? planar_out_exponent(g.pout, s) : 0;
+        if (g.planar_out && blockIdx.x == 0 && tid == 0) g.pout.exps[s] = eo;
+        int i = 0;
+        for (uint32_t tile = blockIdx.x; tile < tps; tile += gridDim.x, ++i) {
             const int buf = i & 1;
             bool ok = true;
             if (lane == 0)
@@ -1541,14 +1541,6 @@ __global__ void __launch_bounds__(448, 1)
                 cr[n] = __uint_as_float(v[2 * n]);
                 ci[n] = __uint_as_float(v[2 * n + 1]);
             }
-            const uint32_t s = t / tps, tile = t - s * tps;
-            if ((int)s != cur_s) {
-                if (cur_s >= 0 && g.amax_out) amax_publish(g.amax_out + cur_s, amx);
-                amx = 0.f;
-                cur_s = (int)s;
-                eo = g.planar_out ? planar_out_exponent(g.pout, s) : 0;
-            }
-            if (g.planar_out && tile == 0 && tid == 0) g.pout.exps[s] = eo;
             // stage buffer i & 1 was last read two tiles ago, before every thread passed the
             // barrier of the previous tile
             float2 *stage = estage + (size_t)buf * 256 * LD;
@@ -1557,18 +1549,16 @@ __global__ void __launch_bounds__(448, 1)
             named_sync(1, 256);
             const uint64_t cbase = tile_base(tile);
             if (g.planar_out) {
-                if ((tid & 1) == 0) {
 #pragma unroll
-                    for (int q = 0; q < SPT; ++q) {
-                        if (SUBS % 256 != 0 && tid + 256 * q >= SUBS) break;
-                        float2 w[8];
+                for (int q = 0; q < SPTP; ++q) {
+                    if (TASKS % 256 != 0 && tid + 256 * q >= TASKS) break;
+                    float2 w[8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            w[j] = stage[ws[q] + w8[j]];
-                            amx = fmaxf(amx, fmaxf(fabsf(w[j].x), fabsf(w[j].y)));
-                        }
-                        planar_out_store8(g.pout, s, cbase | os[q], w, eo);
+                    for (int j = 0; j < 8; ++j) {
+                        w[j] = stage[ws[q] + w8[j]];
+                        amx = fmaxf(amx, fmaxf(fabsf(w[j].x), fabsf(w[j].y)));
                     }
+                    planar_out_store8(g.pout, s, cbase | os[q], w, eo);
                 }
             } else {
                 float2 *C = g.C + (int64_t)s * g.sC + cbase;
@@ -1587,7 +1577,7 @@ __global__ void __launch_bounds__(448, 1)
                 }
             }
         }
-        if (cur_s >= 0 && g.amax_out) amax_publish(g.amax_out + cur_s, amx);
+        if (g.amax_out) amax_publish(g.amax_out + s, amx);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1768,11 +1758,13 @@ cudaError_t configure_thin_tc() {
 template <int NT, int KC>
 cudaError_t launch_thin_tc_t(const ThinTcDesc &d, int64_t slices, cudaStream_t st) {
     using F = ThinTcCfg<NT, KC>;
-    const int64_t total = ((1ll << d.g.lm) / 256) * slices;
-    if (total > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-    int64_t grid = sm_count();
-    if (grid > total) grid = total;
-    k_gemm_thin_tc<NT, KC><<<(unsigned)grid, F::THREADS, F::SMEM_BYTES, st>>>(d, slices);
+    // one CTA per SM in all, spread over the slices (grid row y = slice), at most one per tile
+    const int64_t tps = (1ll << d.g.lm) / 256;
+    int64_t per_slice = sm_count() / slices;
+    if (per_slice < 1) per_slice = 1;
+    if (per_slice > tps) per_slice = tps;
+    k_gemm_thin_tc<NT, KC><<<dim3((unsigned)per_slice, (unsigned)slices), F::THREADS,
+                             F::SMEM_BYTES, st>>>(d, slices);
     return cudaGetLastError();
 }
 

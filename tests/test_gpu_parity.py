@@ -330,6 +330,40 @@ def test_thin_steps_on_the_tensor_cores(tn, shape):
     assert k5[0] == "stream"
 
 
+@pytest.mark.parametrize("shape", [(19, 4, 3), (20, 4, 4), (19, 2, 2)])
+@pytest.mark.parametrize("cfg", ["A", "B", "AB"])
+def test_thin_tensor_core_slices_and_many_tiles(tn, shape, cfg):
+    # 4 slices in flight (two sliced labels) on the large operand, the small one or both, with
+    # 2^11-2^12 tiles per slice, so every CTA walks dozens of tiles (the raw ring, the hi / lo
+    # slots and both accumulator buffers are reused many times): against the oracle, and the
+    # same result bit for bit on a second call
+    lm, ln, lk = shape
+    rng = np.random.default_rng(800 + 7 * lm + 3 * ln + lk + len(cfg))
+    M, N, K = list(range(0, lm)), list(range(100, 100 + ln)), list(range(200, 200 + lk))
+    t = [crandn(rng, lm + lk), crandn(rng, ln + lk)]
+    lab = [[int(x) for x in rng.permutation(M + K)], [int(x) for x in rng.permutation(N + K)]]
+    extra = [900, 901]
+    for x in extra:
+        for side in (0, 1):
+            if "AB"[side] in cfg:
+                v = crandn(rng, 1)
+                t[side] = t[side][None] * v.reshape(2, *([1] * t[side].ndim))
+                lab[side] = [x] + lab[side]
+    tensors = t + [np.ones(2, complex) for _ in extra]
+    labels = lab + [[x] for x in extra]
+    out = [int(x) for x in rng.permutation(M + N)]
+    path = [(0, 1)] + [(0, 2 + j) for j in range(len(extra))]
+    ref = O.contract(tensors, labels, out, path)
+    net = tn.Network(tensors, labels, out)
+    plan = tn.Plan(net, path, extra, mode="fp16_scaled", sync_each_call=True, thin_tc=1)
+    assert plan.step_info(0)["kernel_name"] == "thin_tc" and plan.info()["slices_in_flight"] == 4
+    first = plan.contract_host()
+    check(first, ref, 1e-5)
+    assert np.array_equal(plan.contract_host(), first)
+    plan.close()
+    net.close()
+
+
 def test_thin_tensor_core_step_far_magnitudes(tn):
     # operands near 2^-60 and 2^+40 (FP32 range, far from 1): the hi / lo split is relative, so
     # the compensated products keep their accuracy at any scale
