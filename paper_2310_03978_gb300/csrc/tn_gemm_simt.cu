@@ -956,6 +956,80 @@ void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, 
     }
 }
 
+namespace {
+// rank over GF(2) of n 4-bit vectors
+int rank4(const int *v, int n) {
+    int b[4] = {0, 0, 0, 0};  // b[i]: a reduced vector with leading bit i
+    int r = 0;
+    for (int k = 0; k < n; ++k) {
+        int x = v[k] & 15;
+        for (int i = 3; i >= 0 && x; --i)
+            if ((x >> i) & 1) {
+                if (!b[i]) {
+                    b[i] = x;
+                    ++r;
+                    x = 0;
+                } else {
+                    x ^= b[i];
+                }
+            }
+    }
+    return r;
+}
+}  // namespace
+
+int thin_choose_swizzle(const int8_t *tb_src, int lnt, bool planar, int8_t *phi) {
+    // the 8-byte bank pair (0..15) of element (r, c) is ((r << lnt) & 15) | (c ^ phi(r)): a row
+    // bit i adds bit lnt + i (when below 4) and phi[i]; a column bit k adds bit k
+    const int nt = 1 << lnt;
+    int ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < lnt; ++k) ph[4 - lnt + k] = 1 << k;  // rows 0-3 spread over the banks
+    auto vec = [&](int sq, const int *f) {
+        if (sq & 128) {
+            const int i = sq & 127;
+            return (lnt + i < 4 ? 1 << (lnt + i) : 0) | (i < 8 ? f[i] : 0);
+        }
+        return 1 << sq;
+    };
+    const int rbits[4] = {128, 129, 130, 131};
+    const int rd[4] = {planar ? tb_src[3] : tb_src[1], tb_src[planar ? 4 : 3],
+                       tb_src[planar ? 5 : 4], tb_src[planar ? 6 : 5]};
+    auto score = [&](const int *f) {
+        int w[4], r[4];
+        for (int q = 0; q < 4; ++q) {
+            w[q] = vec(rbits[q], f);
+            r[q] = vec(rd[q], f);
+        }
+        return (rank4(w, 4) == 4 ? 1 : 0) + (rank4(r, 4) == 4 ? 1 : 0);
+    };
+    int best = score(ph), best_ph[8];
+    for (int i = 0; i < 8; ++i) best_ph[i] = ph[i];
+    if (best < 2 && lnt > 0) {
+        // try every phi on the row bits the reads span (at most 4 of them, 16^4 cases)
+        int rows[4], nr = 0;
+        for (int q = 0; q < 4; ++q)
+            if ((rd[q] & 128) && (rd[q] & 127) < 8) rows[nr++] = rd[q] & 127;
+        int total = 1;
+        for (int q = 0; q < nr; ++q) total *= nt;
+        for (int code = 0; code < total && best < 2; ++code) {
+            int f[8];
+            for (int i = 0; i < 8; ++i) f[i] = ph[i];
+            int c = code;
+            for (int q = 0; q < nr; ++q) {
+                f[rows[q]] = c % nt;
+                c /= nt;
+            }
+            const int sc = score(f);
+            if (sc > best) {
+                best = sc;
+                for (int i = 0; i < 8; ++i) best_ph[i] = f[i];
+            }
+        }
+    }
+    for (int i = 0; i < 8; ++i) phi[i] = (int8_t)best_ph[i];
+    return best;
+}
+
 // Number of K splits for a CUDA-core GEMM step: enough CTAs to fill the GPU a few times when
 // the output tiles alone cannot, with at least 256 contracted elements per split.
 int gemm_simt_splits(int lm, int ln, int lk, int64_t slices) {

@@ -30,6 +30,7 @@
 
 #include "tn_internal.h"
 #include "tn_planar_out.cuh"
+#include "tn_thin_stage.cuh"
 
 namespace tn {
 
@@ -1217,8 +1218,7 @@ struct ThinTcCfg {
     static constexpr int CS = 2;                  // hi / lo slots the MMAs read
     static constexpr int SLOT = 2 * HALF;         // hi, then lo
     static constexpr int BPL = ((NP * RB + 1023) / 1024) * 1024;  // one plane of B'
-    static constexpr int LD = NT + 1;             // row stride of the output stage (float2)
-    static constexpr int ESTAGE = 256 * LD * 8;   // one output stage
+    static constexpr int ESTAGE = 256 * NT * 8;   // one output stage (ThinStage)
     static constexpr int FIXED = CS * SLOT + 2 * BPL + 2 * ESTAGE;
     // raw TMA stages: what is left of shared memory, at most 32 and 128 KB
     static constexpr int RS_FIT = (232448 - 2048 - FIXED) / HALF;
@@ -1277,7 +1277,7 @@ template <int NT, int KC>
 __global__ void __launch_bounds__(448, 1)
     k_gemm_thin_tc(const __grid_constant__ ThinTcDesc d, int64_t slices) {
     using F = ThinTcCfg<NT, KC>;
-    constexpr int RS = F::RS, CS = F::CS, LD = F::LD;
+    constexpr int RS = F::RS, CS = F::CS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -1477,33 +1477,10 @@ __global__ void __launch_bounds__(448, 1)
         const int tid = threadIdx.x;
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const int half = warp >> 2;
-        auto soff = [&](int sq) { return (sq & 128) ? (LD << (sq & 127)) : (1 << sq); };
-        int w8[8];
-        {
-            const int d0 = soff(g.tb_src[0]), d1 = soff(g.tb_src[1]), d2 = soff(g.tb_src[2]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                w8[j] = ((j & 1) ? d0 : 0) + ((j & 2) ? d1 : 0) + ((j & 4) ? d2 : 0);
-        }
-        // complex64: two lanes share each run of 8 (lane half h writes elements 4j + 2h and
-        // 4j + 2h + 1 in its store j); planar 16-bit results: a lane writes whole runs
-        constexpr int TASKS = 256 * NT / 8, SUBS = TASKS * 2, SPT = (SUBS + 255) / 256;
-        constexpr int SPTP = (TASKS + 255) / 256;
-        int ws[SPT];
-        uint64_t os[SPT];
-        const int d0 = w8[1], d1 = w8[2], d2 = w8[4];
-#pragma unroll
-        for (int q = 0; q < SPT; ++q) {
-            const int u = tid + 256 * q;
-            const int r = g.planar_out ? u : u >> 1, h = g.planar_out ? 0 : u & 1;
-            ws[q] = h ? d1 : 0;
-            os[q] = h ? 2 : 0;
-            for (int b = 3; b < g.tile_bits; ++b)
-                if ((r >> (b - 3)) & 1) {
-                    ws[q] += soff(g.tb_src[b]);
-                    os[q] |= 1ull << g.tb_pos[b];
-                }
-        }
+        ThinStage<NT> stg;
+        stg.init(g, tid);
+        constexpr int TASKS = ThinStage<NT>::TASKS, SUBS = ThinStage<NT>::SUBS;
+        constexpr int SPT = ThinStage<NT>::SPT, SPTP = ThinStage<NT>::SPTP;
         // C offset of tile t of a slice: deposit(t * 256); the warp's lanes take one bit each
         auto tile_base = [&](uint32_t t) {
             uint64_t r = 0;
@@ -1543,9 +1520,8 @@ __global__ void __launch_bounds__(448, 1)
             }
             // stage buffer i & 1 was last read two tiles ago, before every thread passed the
             // barrier of the previous tile
-            float2 *stage = estage + (size_t)buf * 256 * LD;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
+            float2 *stage = estage + (size_t)buf * 256 * NT;
+            stg.put(stage, tid, cr, ci);
             named_sync(1, 256);
             const uint64_t cbase = tile_base(tile);
             if (g.planar_out) {
@@ -1555,10 +1531,10 @@ __global__ void __launch_bounds__(448, 1)
                     float2 w[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        w[j] = stage[ws[q] + w8[j]];
+                        w[j] = stg.at(stage, q, j);
                         amx = fmaxf(amx, fmaxf(fabsf(w[j].x), fabsf(w[j].y)));
                     }
-                    planar_out_store8(g.pout, s, cbase | os[q], w, eo);
+                    planar_out_store8(g.pout, s, cbase | stg.os[q], w, eo);
                 }
             } else {
                 float2 *C = g.C + (int64_t)s * g.sC + cbase;
@@ -1567,11 +1543,11 @@ __global__ void __launch_bounds__(448, 1)
                     if (SUBS % 256 != 0 && tid + 256 * q >= SUBS) break;
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        const int w = ws[q] + (j ? d2 : 0);
-                        const float2 v0 = stage[w], v1 = stage[w + d0];
+                        const float2 v0 = stg.at(stage, q, j ? 4 : 0);
+                        const float2 v1 = stg.at(stage, q, j ? 5 : 1);
                         amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
                                                fmaxf(fabsf(v1.x), fabsf(v1.y))));
-                        *reinterpret_cast<float4 *>(C + (os[q] + 4 * j)) =
+                        *reinterpret_cast<float4 *>(C + (stg.os[q] + 4 * j)) =
                             make_float4(v0.x, v0.y, v1.x, v1.y);
                     }
                 }

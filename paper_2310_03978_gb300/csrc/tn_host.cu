@@ -159,6 +159,10 @@ struct Step {
     int splits = 1;              // K_GEMM split-K factor
     bool tune_form = false;      // autotune: 3M is still a candidate for this K_TC step
     bool thin_tc = false;        // K_STREAM on the tensor cores (k_gemm_thin_tc)
+    // K_STREAM on the tensor cores: the output stage's swizzle (thin_choose_swizzle), chosen at
+    // the first launch
+    mutable int8_t thin_phi[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    mutable bool thin_phi_set = false;
     int variant = -1;            // K_TC kernel variant
     int out_meta = -1;           // meta block whose per-slice max-abs this step's epilogue records
     int direct_planar = -1;      // planar copy this step writes directly instead of complex64
@@ -1462,6 +1466,11 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
             return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the thin tile",
                         (int)(&st - &p->steps[0]));
+        if (st.thin_tc && !st.thin_phi_set) {
+            tn::thin_choose_swizzle(d.tb_src, d.ln, d.planar_out != 0, st.thin_phi);
+            st.thin_phi_set = true;
+        }
+        memcpy(d.phi, st.thin_phi, sizeof d.phi);
         if (st.thin_tc) {
             tn::ThinTcDesc td;
             memset(&td, 0, sizeof td);

@@ -100,6 +100,8 @@ struct GemmDesc {
     int8_t tb_pos[16];         //   (n: 0..5, m: 6..11) and its position in C
     int8_t posC_m[TN_MAXR];    // bit i of m (0 = least significant) -> bit of C's index
     int8_t posC_n[TN_MAXR];
+    int8_t phi[8];             // tensor-core thin kernel: XOR swizzle of the output stage by
+                               //   row bit (thin_choose_swizzle)
 };
 
 // Slice binding and conversion of a leaf (Sec. 3.2): dst[s][i] (complex64, plan order) =
@@ -142,6 +144,14 @@ struct BindTiled {
 
 // Sort the bits of an output tile (tm row bits, tn column bits) by their position in C:
 // src[q] = row_tag | i for row bit i, or j for column bit j; pos[q] = position in C.
+// Output stage of the tensor-core thin kernel (256 rows x NT = 2^lnt columns of complex64): element
+// (r, c) sits at r * NT + (c ^ phi(r)), phi(r) the XOR of phi[b] over the set bits b of r
+// (each below NT).  Chosen so that the staging writes (a half-warp: 16 consecutive rows, one
+// column) and the reads in C's order (tile bits sorted by position in C, tb_src as
+// sort_tile_bits writes them with row tag 128; a half-warp spans tile bits 1, 3, 4, 5 for
+// complex64 results, 3-6 for planar ones) each touch 16 distinct 8-byte bank pairs where the
+// layout allows; returns how many of the two patterns are conflict-free.
+int thin_choose_swizzle(const int8_t *tb_src, int lnt, bool planar, int8_t *phi);
 void sort_tile_bits(int tm, int tn, const int8_t *posC_m, const int8_t *posC_n, int row_tag,
                     int8_t *src, int8_t *pos);
 
