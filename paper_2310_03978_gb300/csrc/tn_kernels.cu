@@ -77,6 +77,59 @@ __global__ void __launch_bounds__(256) k_generic(GenericDesc d, int64_t total) {
     }
 }
 
+// Steps with nothing contracted (outer products, with or without batch labels): C[c] = A[a(c)]
+// B[b(c)].  Pure streams of stores, so the per-output work is cut to the bone: a thread keeps
+// the operand offsets of its 4 outputs in each 1024-output chunk in registers (the same in every
+// chunk), the chunk's high-bit offsets come from a warp-parallel deposit (lane i takes output
+// bit 10 + i), and the max-abs is published once per slice a block touches rather than per
+// chunk.
+__global__ void __launch_bounds__(256) k_generic_k1(GenericDesc d, int64_t total) {
+    constexpr int LB = 10, PER = (1 << LB) / 256;
+    const int lane = threadIdx.x & 31;
+    uint64_t oa[PER], ob[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const uint64_t j = (uint64_t)threadIdx.x + 256 * t;
+        oa[t] = deposit(j, LB, d.posA_c);
+        ob[t] = deposit(j, LB, d.posB_c);
+    }
+    const uint64_t cmask = (d.rank_c >= 63) ? ~0ull : ((1ull << d.rank_c) - 1);
+    const int64_t nchunks = total >> LB;
+    int64_t cur_s = -1;
+    float amx = 0.f;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int64_t base = ch << LB;
+        const int64_t s = base >> d.rank_c;
+        const uint64_t c0 = (uint64_t)base & cmask;
+        if (s != cur_s) {
+            if (cur_s >= 0 && d.amax_out) amax_publish(d.amax_out + cur_s, amx);
+            amx = 0.f;
+            cur_s = s;
+        }
+        uint64_t ha = 0, hb = 0;
+        for (int i = LB + lane; i < d.rank_c; i += 32)
+            if ((c0 >> i) & 1ull) {
+                if (d.posA_c[i] >= 0) ha |= 1ull << d.posA_c[i];
+                if (d.posB_c[i] >= 0) hb |= 1ull << d.posB_c[i];
+            }
+        ha = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(ha >> 32)) << 32) |
+             __reduce_or_sync(0xffffffffu, (uint32_t)ha);
+        hb = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(hb >> 32)) << 32) |
+             __reduce_or_sync(0xffffffffu, (uint32_t)hb);
+        const float2 *Ab = d.A + s * d.sA + ha;
+        const float2 *Bb = d.B + s * d.sB + hb;
+        float2 *Cb = d.C + s * d.sC + (int64_t)c0;
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const float2 a = Ab[oa[t]], b = Bb[ob[t]];
+            const float re = fmaf(a.x, b.x, -a.y * b.y), im = fmaf(a.x, b.y, a.y * b.x);
+            Cb[threadIdx.x + 256 * t] = make_float2(re, im);
+            amx = fmaxf(amx, fmaxf(fabsf(re), fabsf(im)));
+        }
+    }
+    if (cur_s >= 0 && d.amax_out) amax_publish(d.amax_out + cur_s, amx);
+}
+
 // A run of consecutive small element-wise steps in one launch: block s executes every step of
 // the run for slice s in order, one thread per output element as in k_generic, with a block
 // barrier between steps (a step's outputs are read by later steps of the same block only).  The
@@ -465,7 +518,10 @@ cudaError_t launch_generic(const GenericDesc &d, int64_t slices, cudaStream_t st
     const int lb = d.rank_c < 10 ? d.rank_c : 10;
     int64_t blocks = total >> lb;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_generic<<<(unsigned)blocks, 256, 0, st>>>(d, total);
+    if (d.nk == 0 && d.rank_c >= 10)
+        k_generic_k1<<<(unsigned)blocks, 256, 0, st>>>(d, total);
+    else
+        k_generic<<<(unsigned)blocks, 256, 0, st>>>(d, total);
     return cudaGetLastError();
 }
 

@@ -246,6 +246,37 @@ def test_long_contraction_with_a_batch_label_on_the_elementwise_kernel(tn):
     check(got, ref, 1e-5)
 
 
+@pytest.mark.parametrize("shape", [(12, 6, 0), (14, 2, 0), (3, 12, 0), (10, 0, 0)])
+def test_outer_product_steps(tn, shape):
+    # nothing contracted (an outer product; C's order scrambled): the element-wise kernel's
+    # store-stream path, one slice and 2 slices in flight, and with a batch label (a hyperedge
+    # that two operands and a third tensor share)
+    rng = np.random.default_rng(600 + 3 * shape[0] + 5 * shape[1])
+    tensors, labels, out = single_step(rng, *shape)
+    ref = O.contract(tensors, labels, out, [(0, 1)])
+    got, _, kernels = gpu_amps(tn, tensors, labels, out, [(0, 1)])
+    assert kernels == ["generic"]
+    check(got, ref, 1e-5)
+    A, B = tensors
+    v = crandn(rng, 1)
+    t2 = [A[None] * v.reshape(2, *([1] * A.ndim)), B, np.ones(2, complex)]
+    l2 = [[900] + labels[0], labels[1], [900]]
+    ref2 = O.contract(t2, l2, out, [(0, 1), (0, 2)])
+    for mode in ("c64", "fp16_scaled"):
+        got2, info, k2 = gpu_amps(tn, t2, l2, out, [(0, 1), (0, 2)], [900], mode=mode)
+        assert info["slices_in_flight"] == 2 and k2[0] == "generic"
+        check(got2, ref2, 1e-5)
+    # a batch label b on A, B and a vector: C[b, m, n] = A[b, m] B[b, n], then summed over b
+    w = crandn(rng, 1)
+    t3 = [A[None] * v.reshape(2, *([1] * A.ndim)), B[None] * w.reshape(2, *([1] * B.ndim)),
+          crandn(rng, 1)]
+    l3 = [[950] + labels[0], [950] + labels[1], [950]]
+    ref3 = O.contract(t3, l3, out, [(0, 1), (0, 2)])
+    got3, _, k3 = gpu_amps(tn, t3, l3, out, [(0, 1), (0, 2)])
+    assert k3[0] == "generic"
+    check(got3, ref3, 1e-5)
+
+
 @pytest.mark.parametrize("shape", [(12, 4, 4), (10, 2, 6), (4, 11, 3), (13, 0, 2), (11, 3, 1),
                                    (1, 12, 5), (14, 2, 2), (12, 1, 3), (10, 4, 1), (18, 2, 2),
                                    (3, 17, 1), (12, 3, 8), (10, 4, 10), (3, 13, 9), (11, 0, 7)])
