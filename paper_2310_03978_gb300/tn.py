@@ -222,9 +222,12 @@ class Network:
     def __init__(self, tensors, labels, open_labels):
         self._keep = []
         n = len(tensors)
-        arrs = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+        # np.array keeps rank-0 tensors 0-d (np.ascontiguousarray would make them 1-d)
+        arrs = [np.array(t, dtype=np.complex128, order="C") for t in tensors]
         ranks = np.array([a.ndim for a in arrs], dtype=np.int32)
-        labs = [np.ascontiguousarray(np.asarray(l, dtype=np.int32)) for l in labels]
+        labs = [np.ascontiguousarray(np.asarray(l, dtype=np.int32).reshape(-1)) for l in labels]
+        if len(labels) != n or any(len(l) != a.ndim for l, a in zip(labs, arrs)):
+            raise ValueError("every tensor needs one label per axis")
         dims = [np.ascontiguousarray(np.asarray(a.shape, dtype=np.int64)) for a in arrs]
         lab_p = (C.c_void_p * n)(*[l.ctypes.data for l in labs])
         dim_p = (C.c_void_p * n)(*[d.ctypes.data for d in dims])
@@ -243,7 +246,7 @@ class Network:
         return cls(net.tensors, net.labels, net.open_labels)
 
     def set_data(self, tensors):
-        arrs = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+        arrs = [np.array(t, dtype=np.complex128, order="C") for t in tensors]
         dat_p = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
         _check(lib().tn_network_set_data(self.handle, dat_p))
 

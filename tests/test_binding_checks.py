@@ -64,3 +64,14 @@ def test_contract_host_rejects_bad_output_arrays():
                 np.zeros(32, np.complex128)[::2]):
         with pytest.raises(ValueError):
             p.contract_host(0, 1, out=out)
+
+
+def test_network_rejects_label_counts_that_do_not_match_ranks():
+    # one label per axis, rank-0 tensors included (no labels); checked before libtn.so is called
+    import numpy as np
+    with pytest.raises(ValueError, match="one label per axis"):
+        T.Network([np.ones((2, 2), complex)], [[0]], [0])
+    with pytest.raises(ValueError, match="one label per axis"):
+        T.Network([np.complex128(1.0)], [[0]], [])
+    with pytest.raises(ValueError, match="one label per axis"):
+        T.Network([np.ones(2, complex), np.ones(2, complex)], [[0]], [])
