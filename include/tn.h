@@ -118,8 +118,8 @@ typedef struct {
     int32_t thin_tc;               /* streaming (thin-operand) steps with 4-16 columns and
                                       4-16 terms on the tensor cores (compensated TF32,
                                       FP32-level accuracy) in the tensor-core modes: 0 =
-                                      those with 16 terms, 1 = all of them, -1 = none (CUDA
-                                      cores)                                                  */
+                                      those with 16 terms or with 16 columns and 8 terms, 1 =
+                                      all of them, -1 = none (CUDA cores)                     */
     double eps_budget;             /* > 0: largest predicted amplitude relative L2 error the
                                       precision policy may reach (error model above); 0 = none,
                                       except TN_PREC_BF16_SCALED (5e-3)                      */

@@ -1197,28 +1197,31 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
 // A B' ~ Ahi B'lo + Alo B'hi + Ahi B'hi: Sec. 4.2's 3xTF32 scheme), which keeps the result at
 // FP32-level accuracy while the tensor cores take the 4 NT KC multiply-adds per row that bound
 // the CUDA-core form once NT and KC reach 8-16.
-// A 256-row tile is loaded by TMA as two 128-row halves into a ring of raw stages (rows of
-// 8 KC bytes with the matching swizzle; as many stages as shared memory holds, so enough reads
-// stay in flight), split into hi / lo parts in one of two slots the MMAs read (which frees the
-// raw stage at once), and accumulated in TMEM as two 128 x 32 blocks (B' has zero rows beyond
-// 2 NT).  Warps 0-7 drain the accumulator (warp w reads TMEM lanes 32 (w % 4).. of half w / 4,
-// so thread t holds row t of the tile) and write the tile in C's order through a shared-memory
-// stage, 8 consecutive elements of C per task as the CUDA-core thin kernel does; warps 8-11
-// split the halves; warp 12 issues the TMA loads, warp 13 the MMAs; B' hi / lo is built by all
-// threads before the roles start.
-// Grid row y is slice y (about one CTA per SM in all); its CTAs walk the slice's tiles.  Every wait is bounded; a wait that runs out sets the status word and the
-// abort flag, and every role leaves its loop.
+// A 128-row tile is loaded by TMA into a ring of raw stages (rows of 8 KC bytes with the
+// matching swizzle; as many stages as shared memory holds, so enough reads stay in flight),
+// split into hi / lo parts in one of two slots the MMAs read (which frees the raw stage at once),
+// and accumulated in TMEM as a 128 x 32 block (B' has zero rows beyond 2 NT), four such buffers
+// in turn.  Two drain groups of 4 warps take the tiles in turn (warp w reads TMEM lanes
+// 32 (w % 4).., so thread t of a group holds row t of its tile) and write them in C's order
+// through shared-memory stages, 8 consecutive elements of C per task as the CUDA-core thin
+// kernel does; with two groups one tile's stores overlap the next tile's TMEM reads and
+// staging.  Warps 8-11 split the tiles; warp 12 issues the TMA loads, warp 13 the MMAs; B'
+// hi / lo is built by all threads before the roles start.
+// Grid row y is slice y (about one CTA per SM in all); its CTAs walk the slice's tiles.  Every
+// wait is bounded; a wait that runs out sets the status word and the abort flag, and every role
+// leaves its loop.
 template <int NT, int KC>
 struct ThinTcCfg {
     static constexpr int RB = 8 * KC;             // bytes of one row of A (2 KC floats)
     static constexpr int NR = 2 * NT;             // real result columns
     static constexpr int NP = 32;                 // MMA N (the 32-column shape of the
                                                   // narrow tiles; B' rows past NR are zero)
-    static constexpr int HALF = BM * RB;          // one 128-row half of a tile
+    static constexpr int HALF = BM * RB;          // one 128-row tile of A
     static constexpr int CS = 2;                  // hi / lo slots the MMAs read
     static constexpr int SLOT = 2 * HALF;         // hi, then lo
     static constexpr int BPL = ((NP * RB + 1023) / 1024) * 1024;  // one plane of B'
-    static constexpr int ESTAGE = 256 * NT * 8;   // one output stage (ThinStage)
+    static constexpr int NB = 4;                  // TMEM accumulator buffers (2 per drain group)
+    static constexpr int ESTAGE = 256 * NT * 8;   // two output stages of 128 rows (one group)
     static constexpr int FIXED = CS * SLOT + 2 * BPL + 2 * ESTAGE;
     // raw TMA stages: what is left of shared memory, at most 32 and 128 KB
     static constexpr int RS_FIT = (232448 - 2048 - FIXED) / HALF;
@@ -1229,13 +1232,13 @@ struct ThinTcCfg {
     static constexpr int SMEM_BYTES = BODY + 1024 + 1024;
     static constexpr int SBO = 8 * RB;            // next 8-row group
     static constexpr uint64_t LAYOUT = RB == 128 ? 2 : (RB == 64 ? 4 : 6);
-    static constexpr int KSTEPS = RB / 32;        // MMAs (8 TF32 of K) per half
-    static constexpr int TMEM_COLS = 4 * NP;      // 2 buffers x 2 halves
+    static constexpr int KSTEPS = RB / 32;        // MMAs (8 TF32 of K) per tile
+    static constexpr int TMEM_COLS = NB * NP;
     static constexpr int THREADS = 448;
     static_assert(NT == 4 || NT == 8 || NT == 16, "columns");
     static_assert(KC == 4 || KC == 8 || KC == 16, "terms");
     static_assert(RS >= 4, "raw stages");
-    static_assert((2 * RS + 2 * CS + 5) * 8 + 8 <= 1024, "barriers");
+    static_assert((2 * RS + 2 * CS + 2 * NB + 1) * 8 + 8 <= 1024, "barriers");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
@@ -1277,28 +1280,28 @@ template <int NT, int KC>
 __global__ void __launch_bounds__(448, 1)
     k_gemm_thin_tc(const __grid_constant__ ThinTcDesc d, int64_t slices) {
     using F = ThinTcCfg<NT, KC>;
-    constexpr int RS = F::RS, CS = F::CS;
+    constexpr int RS = F::RS, CS = F::CS, NB = F::NB, ROWS = ThinStage<NT>::ROWS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *raw = smem;                   // RS raw stages (TMA)
     uint8_t *slots = smem + F::RAW;        // CS slots: hi, lo (MMA operands)
     uint8_t *bhi = slots + CS * F::SLOT, *blo = bhi + F::BPL;
-    float2 *estage = reinterpret_cast<float2 *>(blo + F::BPL);
+    float2 *estage = reinterpret_cast<float2 *>(blo + F::BPL);  // [group][2][ROWS * NT]
     uint64_t *rfull = reinterpret_cast<uint64_t *>(smem + F::BODY);  // TMA -> split
     uint64_t *rempty = rfull + RS;  // split -> TMA: the raw stage was read (128 arrivals)
-    uint64_t *cfull = rempty + RS;  // split -> MMA: hi / lo (and B') are in place (128)
+    uint64_t *cfull = rempty + RS;  // split -> MMA: hi / lo are in place (128 arrivals)
     uint64_t *cempty = cfull + CS;  // MMA -> split: the slot was consumed
     uint64_t *tfull = cempty + CS;  // MMA -> drain: accumulator buffer b is complete
-    uint64_t *tempty = tfull + 2;   // drain -> MMA: buffer b was read (8 arrivals)
-    uint64_t *mdone = tempty + 2;
+    uint64_t *tempty = tfull + NB;  // drain -> MMA: buffer b was read (4 arrivals)
+    uint64_t *mdone = tempty + NB;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
     int *aborted = reinterpret_cast<int *>(tmem_slot + 1);
     const GemmDesc &g = d.g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // grid row y = slice s; the CTAs of a row walk the slice's 256-row tiles
+    // grid row y = slice s; the CTAs of a row walk the slice's 128-row tiles
     const uint32_t s = blockIdx.y;
-    const uint32_t tps = (uint32_t)((1ll << g.lm) / 256);  // tiles per slice
+    const uint32_t tps = (uint32_t)((1ll << g.lm) / ROWS);  // tiles per slice
     const unsigned long long limit = d.wait_limit_ns ? d.wait_limit_ns : kWaitLimitNs;
 
     if (threadIdx.x == 0) {
@@ -1310,9 +1313,9 @@ __global__ void __launch_bounds__(448, 1)
             mbar_init(&cfull[i], 128);
             mbar_init(&cempty[i], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NB; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 8);
+            mbar_init(&tempty[b], 4);
         }
         mbar_init(mdone, 1);
         *aborted = 0;
@@ -1351,27 +1354,21 @@ __global__ void __launch_bounds__(448, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 12) {
-        // TMA producer: the two halves of every tile of this CTA through the raw ring
+        // TMA producer: every tile of this CTA through the raw ring
         if (lane == 0) {
-            int it = 0, issued = 0;
             const int z = g.sA ? (int)s : 0;
+            int it = 0, issued = 0;
             for (uint32_t tile = blockIdx.x; tile < tps && !*(volatile int *)aborted;
-                 tile += gridDim.x) {
-                bool ok = true;
-                for (int h = 0; h < 2; ++h, ++it) {
-                    const int rs = it % RS;
-                    if (it >= RS && !mbar_wait(&rempty[rs], ((uint32_t)(it / RS) & 1u) ^ 1u,
-                                               globaltimer() + limit)) {
-                        *aborted = 1;
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(&rfull[rs], F::HALF);
-                    tma_load_3d(raw + rs * F::HALF, &d.tmA, &rfull[rs], 0,
-                                (int)(tile * 256u + 128u * (uint32_t)h), z);
-                    issued = it + 1;
+                 tile += gridDim.x, ++it) {
+                const int rs = it % RS;
+                if (it >= RS && !mbar_wait(&rempty[rs], ((uint32_t)(it / RS) & 1u) ^ 1u,
+                                           globaltimer() + limit)) {
+                    *aborted = 1;
+                    break;
                 }
-                if (!ok) break;
+                mbar_expect_tx(&rfull[rs], F::HALF);
+                tma_load_3d(raw + rs * F::HALF, &d.tmA, &rfull[rs], 0, (int)(tile * ROWS), z);
+                issued = it + 1;
             }
             // loads in flight land before the CTA's shared memory is released
             const unsigned long long drain = globaltimer() + limit;
@@ -1381,47 +1378,40 @@ __global__ void __launch_bounds__(448, 1)
             }
         }
     } else if (warp == 13) {
-        // MMA issuer: tile i accumulates into TMEM buffer i & 1, half h into its 32 columns
+        // MMA issuer: tile i accumulates into TMEM buffer i % NB (32 columns each)
         if (lane == 0) {
             const uint32_t idesc = idesc_mma(2u, BM, F::NP, false);
             auto sd = [](uint32_t a) { return sdesc_lbo<F::SBO, 16, F::LAYOUT>(a); };
             const uint64_t bh = sd(smem_u32(bhi)), bl = sd(smem_u32(blo));
-            int it = 0, i = 0;
+            int it = 0;
             bool any = false;
             for (uint32_t tile = blockIdx.x; tile < tps && !*(volatile int *)aborted;
-                 tile += gridDim.x, ++i) {
-                const int buf = i & 1;
-                if (i >= 2 && !mbar_wait(&tempty[buf], (uint32_t)((i >> 1) - 1) & 1u,
-                                         globaltimer() + limit)) {
+                 tile += gridDim.x, ++it) {
+                const int buf = it % NB, cs = it % CS;
+                if (it >= NB && !mbar_wait(&tempty[buf], (uint32_t)((it / NB) - 1) & 1u,
+                                           globaltimer() + limit)) {
+                    *aborted = 1;
+                    break;
+                }
+                if (!mbar_wait(&cfull[cs], (uint32_t)(it / CS) & 1u, globaltimer() + limit)) {
                     *aborted = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                bool ok = true;
-                for (int h = 0; h < 2; ++h, ++it) {
-                    const int cs = it % CS;
-                    if (!mbar_wait(&cfull[cs], (uint32_t)(it / CS) & 1u, globaltimer() + limit)) {
-                        *aborted = 1;
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t acc = tmem + (uint32_t)((2 * buf + h) * F::NP);
-                    const uint32_t base = smem_u32(slots + cs * F::SLOT);
-                    const uint64_t ah = sd(base), al = sd(base + F::HALF);
+                const uint32_t acc = tmem + (uint32_t)(buf * F::NP);
+                const uint32_t base = smem_u32(slots + cs * F::SLOT);
+                const uint64_t ah = sd(base), al = sd(base + F::HALF);
 #pragma unroll
-                    for (int kk = 0; kk < F::KSTEPS; ++kk) {
-                        const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                        // the two correction products first, the main one last
-                        umma<4>(acc, ah + adv, bl + adv, idesc, kk > 0 ? 1u : 0u);
-                        umma<4>(acc, al + adv, bh + adv, idesc, 1u);
-                        umma<4>(acc, ah + adv, bh + adv, idesc, 1u);
-                    }
-                    umma_commit(&cempty[cs]);
-                    any = true;
+                for (int kk = 0; kk < F::KSTEPS; ++kk) {
+                    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                    // the two correction products first, the main one last
+                    umma<4>(acc, ah + adv, bl + adv, idesc, kk > 0 ? 1u : 0u);
+                    umma<4>(acc, al + adv, bh + adv, idesc, 1u);
+                    umma<4>(acc, ah + adv, bh + adv, idesc, 1u);
                 }
-                if (!ok) break;
+                umma_commit(&cempty[cs]);
                 umma_commit(&tfull[buf]);
+                any = true;
             }
             if (any) {
                 umma_commit(mdone);
@@ -1429,20 +1419,19 @@ __global__ void __launch_bounds__(448, 1)
             }
         }
     } else if (warp >= 8) {
-        // split warps: every half's hi / lo parts
+        // split warps: every tile's hi / lo parts
         const int ts = threadIdx.x - 256;
         int it = 0;
-        for (uint32_t tile = blockIdx.x; tile < tps; tile += gridDim.x) {
-            bool ok = !*(volatile int *)aborted;
-            for (int h = 0; h < 2 && ok; ++h, ++it) {
-                const int rs = it % RS, cs = it % CS;
-                // every thread waits itself: it reads what the TMA wrote, and rewrites a slot
-                // the tensor cores read before
-                ok = mbar_wait(&rfull[rs], (uint32_t)(it / RS) & 1u, globaltimer() + limit);
-                if (ok && it >= CS)
-                    ok = mbar_wait(&cempty[cs], ((uint32_t)(it / CS) & 1u) ^ 1u,
-                                   globaltimer() + limit);
-                if (!ok) break;
+        for (uint32_t tile = blockIdx.x; tile < tps; tile += gridDim.x, ++it) {
+            const int rs = it % RS, cs = it % CS;
+            // every thread waits itself: it reads what the TMA wrote, and rewrites a slot the
+            // tensor cores read before
+            bool ok = !*(volatile int *)aborted &&
+                      mbar_wait(&rfull[rs], (uint32_t)(it / RS) & 1u, globaltimer() + limit);
+            if (ok && it >= CS)
+                ok = mbar_wait(&cempty[cs], ((uint32_t)(it / CS) & 1u) ^ 1u,
+                               globaltimer() + limit);
+            if (ok) {
                 const float4 *r4 = reinterpret_cast<const float4 *>(raw + rs * F::HALF);
                 float4 *hi4 = reinterpret_cast<float4 *>(slots + cs * F::SLOT);
                 float4 *lo4 = reinterpret_cast<float4 *>(slots + cs * F::SLOT + F::HALF);
@@ -1456,36 +1445,36 @@ __global__ void __launch_bounds__(448, 1)
                     lo4[ts + 128 * q] = make_float4(v.x - hv.x, v.y - hv.y, v.z - hv.z,
                                                     v.w - hv.w);
                 }
-                // the slot's generic-proxy writes, then the tensor cores (async proxy) read them;
-                // the raw stage is released only now, after every value read from it has been
-                // used: an arrive right after the loads let the next TMA write (fast when the
-                // rows come from L2, as when all slices share the large operand) overtake
+                // the slot's generic-proxy writes, then the tensor cores (async proxy) read
+                // them; the raw stage is released only now, after every value read from it has
+                // been used: an arrive right after the loads let the next TMA write (fast when
+                // the rows come from L2, as when all slices share the large operand) overtake
                 // loads still queued, and a few rows of a tile came out wrong
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&rempty[rs]);
                 mbar_arrive(&cfull[cs]);
             }
             // the group leaves together once any of its waits ran out
-            if (!named_and(3, 128, ok)) {
+            if (!named_and(5, 128, ok)) {
                 if (ts == 0) *aborted = 1;
                 break;
             }
         }
     } else {
-        // drain warps: thread tid holds row tid of the tile (TMEM lane 32 (warp % 4) + lane of
-        // half warp / 4) and writes the tile in C's order, 8 consecutive elements per task
-        const int tid = threadIdx.x;
+        // two drain groups (warps 0-3 and 4-7) take the CTA's tiles in turn, each with its own
+        // barriers and stages, so one group's stores overlap the other's TMEM reads; thread
+        // gt of a group holds row gt of its tile (TMEM lane 32 (warp % 4) + lane)
+        const int grp = warp >> 2, gt = threadIdx.x - ROWS * grp;
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        const int half = warp >> 2;
         ThinStage<NT> stg;
-        stg.init(g, tid);
+        stg.init(g, gt);
         constexpr int TASKS = ThinStage<NT>::TASKS, SUBS = ThinStage<NT>::SUBS;
         constexpr int SPT = ThinStage<NT>::SPT, SPTP = ThinStage<NT>::SPTP;
-        // C offset of tile t of a slice: deposit(t * 256); the warp's lanes take one bit each
+        // C offset of tile t of a slice: deposit(t * ROWS); the warp's lanes take one bit each
         auto tile_base = [&](uint32_t t) {
             uint64_t r = 0;
-            for (int b = 8 + lane; b < g.lm; b += 32)
-                if ((t >> (b - 8)) & 1u) r |= 1ull << g.posC_m[b];
+            for (int b = ThinStage<NT>::LR + lane; b < g.lm; b += 32)
+                if ((t >> (b - ThinStage<NT>::LR)) & 1u) r |= 1ull << g.posC_m[b];
             const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)r);
             const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(r >> 32));
             return ((uint64_t)hi << 32) | lo;
@@ -1493,22 +1482,23 @@ __global__ void __launch_bounds__(448, 1)
         float cr[NT], ci[NT];
         float amx = 0.f;
         const int eo = g.planar_out ? planar_out_exponent(g.pout, s) : 0;
-        if (g.planar_out && blockIdx.x == 0 && tid == 0) g.pout.exps[s] = eo;
-        int i = 0;
-        for (uint32_t tile = blockIdx.x; tile < tps; tile += gridDim.x, ++i) {
-            const int buf = i & 1;
+        if (g.planar_out && blockIdx.x == 0 && threadIdx.x == 0) g.pout.exps[s] = eo;
+        int j = 0;  // tiles this group has drained
+        for (uint32_t tile = blockIdx.x + grp * gridDim.x; tile < tps;
+             tile += 2 * gridDim.x, ++j) {
+            const int it = 2 * j + grp, buf = it % NB;
             bool ok = true;
             if (lane == 0)
-                ok = mbar_wait(&tfull[buf], (uint32_t)(i >> 1) & 1u, globaltimer() + limit) &&
+                ok = mbar_wait(&tfull[buf], (uint32_t)(it / NB) & 1u, globaltimer() + limit) &&
                      !*(volatile int *)aborted;
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!named_and(2, 256, ok)) {
-                if (tid == 0) *aborted = 1;
+            if (!named_and(1 + grp, ROWS, ok)) {
+                if (gt == 0) *aborted = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t v[F::NR < 16 ? 8 : F::NR];
-            tmem_ld_cols(tmem + lane_base + (uint32_t)((2 * buf + half) * F::NP), v);
+            tmem_ld_cols(tmem + lane_base + (uint32_t)(buf * F::NP), v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -1518,21 +1508,21 @@ __global__ void __launch_bounds__(448, 1)
                 cr[n] = __uint_as_float(v[2 * n]);
                 ci[n] = __uint_as_float(v[2 * n + 1]);
             }
-            // stage buffer i & 1 was last read two tiles ago, before every thread passed the
-            // barrier of the previous tile
-            float2 *stage = estage + (size_t)buf * 256 * NT;
-            stg.put(stage, tid, cr, ci);
-            named_sync(1, 256);
+            // the group's stage j & 1 was last read two of its tiles ago, before every thread
+            // of the group passed the barrier of its previous tile
+            float2 *stage = estage + (size_t)(2 * grp + (j & 1)) * ROWS * NT;
+            stg.put(stage, gt, cr, ci);
+            named_sync(3 + grp, ROWS);
             const uint64_t cbase = tile_base(tile);
             if (g.planar_out) {
 #pragma unroll
                 for (int q = 0; q < SPTP; ++q) {
-                    if (TASKS % 256 != 0 && tid + 256 * q >= TASKS) break;
+                    if (TASKS % ROWS != 0 && gt + ROWS * q >= TASKS) break;
                     float2 w[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        w[j] = stg.at(stage, q, j);
-                        amx = fmaxf(amx, fmaxf(fabsf(w[j].x), fabsf(w[j].y)));
+                    for (int e = 0; e < 8; ++e) {
+                        w[e] = stg.at(stage, q, e);
+                        amx = fmaxf(amx, fmaxf(fabsf(w[e].x), fabsf(w[e].y)));
                     }
                     planar_out_store8(g.pout, s, cbase | stg.os[q], w, eo);
                 }
@@ -1540,14 +1530,14 @@ __global__ void __launch_bounds__(448, 1)
                 float2 *C = g.C + (int64_t)s * g.sC + cbase;
 #pragma unroll
                 for (int q = 0; q < SPT; ++q) {
-                    if (SUBS % 256 != 0 && tid + 256 * q >= SUBS) break;
+                    if (SUBS % ROWS != 0 && gt + ROWS * q >= SUBS) break;
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const float2 v0 = stg.at(stage, q, j ? 4 : 0);
-                        const float2 v1 = stg.at(stage, q, j ? 5 : 1);
+                    for (int e = 0; e < 2; ++e) {
+                        const float2 v0 = stg.at(stage, q, e ? 4 : 0);
+                        const float2 v1 = stg.at(stage, q, e ? 5 : 1);
                         amx = fmaxf(amx, fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)),
                                                fmaxf(fabsf(v1.x), fabsf(v1.y))));
-                        *reinterpret_cast<float4 *>(C + (stg.os[q] + 4 * j)) =
+                        *reinterpret_cast<float4 *>(C + (stg.os[q] + 4 * e)) =
                             make_float4(v0.x, v0.y, v1.x, v1.y);
                     }
                 }
@@ -1735,7 +1725,7 @@ template <int NT, int KC>
 cudaError_t launch_thin_tc_t(const ThinTcDesc &d, int64_t slices, cudaStream_t st) {
     using F = ThinTcCfg<NT, KC>;
     // one CTA per SM in all, spread over the slices (grid row y = slice), at most one per tile
-    const int64_t tps = (1ll << d.g.lm) / 256;
+    const int64_t tps = (1ll << d.g.lm) / 128;
     int64_t per_slice = sm_count() / slices;
     if (per_slice < 1) per_slice = 1;
     if (per_slice > tps) per_slice = tps;
@@ -2026,7 +2016,7 @@ int encode_tmap_thin(void *tmap_host, const void *A, int lm, int lk, int64_t dep
 
 cudaError_t launch_gemm_thin_tc(const ThinTcDesc &d, int64_t slices, cudaStream_t st) {
     const GemmDesc &g = d.g;
-    if (!thin_tc_fits(g.lm, g.ln, g.lk) || g.tile_bits != 8 + g.ln || slices < 1)
+    if (!thin_tc_fits(g.lm, g.ln, g.lk) || g.tile_bits != 7 + g.ln || slices < 1)
         return cudaErrorInvalidValue;
     switch (g.ln * 8 + g.lk) {
         case 2 * 8 + 2: return launch_thin_tc_t<4, 4>(d, slices, st);

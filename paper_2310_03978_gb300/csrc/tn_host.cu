@@ -163,6 +163,7 @@ struct Step {
     // the first launch
     mutable int8_t thin_phi[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     mutable bool thin_phi_set = false;
+    mutable bool thin_tc_off = false;  // its result order does not fit the 128-row tile
     int variant = -1;            // K_TC kernel variant
     int out_meta = -1;           // meta block whose per-slice max-abs this step's epilogue records
     int direct_planar = -1;      // planar copy this step writes directly instead of complex64
@@ -664,18 +665,20 @@ static tn_status plan_impl(const tn_network_t *net, int32_t path_len, const int3
         st.kernel = route(st, mode, p->tc_ok);
         // slice-independent steps run once per call; they stay on the CUDA cores
         if (!st.dep && st.kernel == K_TC) st.kernel = K_GEMM;
-        // a streaming step with K = 16 takes the tensor cores (compensated TF32, FP32-level
-        // accuracy) in the tensor-core modes: on the CUDA cores its 4 * NT * 16 multiply-adds
-        // per row and their operand reads keep it below memory speed (measured on GB300 at
-        // 2^24-2^26 rows: 4, 8, 16 columns 3.6, 2.8, 3.3 TB/s there against 3.8, 4.2, 5.3 on
-        // the tensor cores); with K <= 8 the CUDA-core kernel is the faster one (3.9-6.7 TB/s
-        // against 2.7-4.1).  opts.thin_tc > 0 sends every step that fits, < 0 none
+        // a streaming step with K = 16, or with 16 columns and K = 8, takes the tensor cores
+        // (compensated TF32, FP32-level accuracy) in the tensor-core modes: on the CUDA cores
+        // its 4 * NT * K multiply-adds per row and their operand reads keep it below memory
+        // speed (measured on GB300 at 2^24-2^26 rows: K = 16 with 4, 8, 16 columns 3.6, 2.9,
+        // 3.3 TB/s there against 3.6, 3.9, 4.6 on the tensor cores; 16 columns and K = 8 3.9
+        // against 4.6); the other shapes are faster on the CUDA cores (4.2-6.7 TB/s against
+        // 2.4-3.9).  opts.thin_tc > 0 sends every step that fits, < 0 none
         if (st.kernel == K_STREAM && mode != TN_PREC_C64 && p->tc_ok && st.dep) {
             const int wide = (int)std::max(st.M.size(), st.N.size());
             const int narrow = (int)std::min(st.M.size(), st.N.size());
             const int lk = (int)st.K.size();
             st.thin_tc = tn::thin_tc_fits(wide, narrow, lk) &&
-                         (p->opts.thin_tc > 0 || (p->opts.thin_tc == 0 && lk == 4));
+                         (p->opts.thin_tc > 0 ||
+                          (p->opts.thin_tc == 0 && (lk == 4 || (narrow == 4 && lk == 3))));
         }
         if (mode == TN_PREC_SPLIT_FP16 || mode == TN_PREC_SPLIT_BF16 ||
             mode == TN_PREC_SPLIT_TF32 || mode == TN_PREC_MIXED)
@@ -1461,17 +1464,30 @@ tn_status run_step_inner(tn_plan_t *p, const Step &st, int64_t slices, cudaStrea
         fill_pos(d.posC_n, TN_MAXR, -1);
         for (int i = 0; i < d.lm; ++i) d.posC_m[i] = (int8_t)C.pos(Rl[Rl.size() - 1 - i]);
         for (int i = 0; i < d.ln; ++i) d.posC_n[i] = (int8_t)C.pos(Ql[Ql.size() - 1 - i]);
-        d.tile_bits = 8 + d.ln;
-        tn::sort_tile_bits(8, d.ln, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
-        if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
-            return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the thin tile",
-                        (int)(&st - &p->steps[0]));
-        if (st.thin_tc && !st.thin_phi_set) {
+        // tiles of 256 rows on the CUDA cores, of 128 rows on the tensor cores; C's three lowest
+        // positions must lie in the tile (else the step stays on the CUDA cores)
+        bool on_tc = st.thin_tc && !st.thin_tc_off;
+        if (on_tc) {
+            d.tile_bits = 7 + d.ln;
+            tn::sort_tile_bits(7, d.ln, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+            if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2) {
+                st.thin_tc_off = true;
+                on_tc = false;
+            }
+        }
+        if (!on_tc) {
+            d.tile_bits = 8 + d.ln;
+            tn::sort_tile_bits(8, d.ln, d.posC_m, d.posC_n, 128, d.tb_src, d.tb_pos);
+            if (d.tb_pos[0] != 0 || d.tb_pos[1] != 1 || d.tb_pos[2] != 2)
+                return fail(TN_ERR_UNSUPPORTED, "step %d: result bits 0-2 outside the thin tile",
+                            (int)(&st - &p->steps[0]));
+        }
+        if (on_tc && !st.thin_phi_set) {
             tn::thin_choose_swizzle(d.tb_src, d.ln, d.planar_out != 0, st.thin_phi);
             st.thin_phi_set = true;
         }
         memcpy(d.phi, st.thin_phi, sizeof d.phi);
-        if (st.thin_tc) {
+        if (on_tc) {
             tn::ThinTcDesc td;
             memset(&td, 0, sizeof td);
             td.g = d;
@@ -1594,7 +1610,7 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
         return fail(TN_ERR_INVALID_ARG, "bad step index");
     const Step &st = p->steps[(size_t)step];
     memset(out, 0, sizeof *out);
-    out->kernel = st.thin_tc ? 4 : st.kernel;
+    out->kernel = st.thin_tc && !st.thin_tc_off ? 4 : st.kernel;
     out->slice_dependent = st.dep ? 1 : 0;
     out->log2_m = (int)st.M.size();
     out->log2_n = (int)st.N.size();
@@ -1619,7 +1635,7 @@ tn_status tn_plan_get_step_info(const tn_plan_t *p, int64_t step, tn_step_info *
             tn_ = std::min((int)st.N.size(), 6);
         } else if (st.kernel == K_STREAM) {
             if (st.N.size() > st.M.size()) std::swap(Ms, Ns);
-            tm = 8;
+            tm = st.thin_tc && !st.thin_tc_off ? 7 : 8;
             tn_ = (int)Ns->size();
         }
         int run = 0;

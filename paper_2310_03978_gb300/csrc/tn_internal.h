@@ -144,7 +144,7 @@ struct BindTiled {
 
 // Sort the bits of an output tile (tm row bits, tn column bits) by their position in C:
 // src[q] = row_tag | i for row bit i, or j for column bit j; pos[q] = position in C.
-// Output stage of the tensor-core thin kernel (256 rows x NT = 2^lnt columns of complex64): element
+// Output stage of the tensor-core thin kernel (128 rows x NT = 2^lnt columns of complex64): element
 // (r, c) sits at r * NT + (c ^ phi(r)), phi(r) the XOR of phi[b] over the set bits b of r
 // (each below NT).  Chosen so that the staging writes (a half-warp: 16 consecutive rows, one
 // column) and the reads in C's order (tile bits sorted by position in C, tb_src as
@@ -332,9 +332,9 @@ bool tc_variant_is_pers(int variant);  // the persistent short-K kernel (one CTA
 void tc_choose_swizzle(const int8_t *tb_src, int8_t *phi, int bits);
 
 // Thin step on the tensor cores (k_gemm_thin_tc): the streaming step of GemmDesc g (A the large
-// complex64 operand [slices][2^lm][2^lk], B the small one [slices][2^ln][2^lk], tiles of 256
-// rows and 2^ln columns staged like the CUDA-core thin kernel's) as one real TF32 product with
-// compensated (hi / lo) operands.  tmA: A as [depth][2^lm rows][2^(lk+1) floats] with boxes of
+// complex64 operand [slices][2^lm][2^lk], B the small one [slices][2^ln][2^lk], tiles of 128
+// rows and 2^ln columns: tile_bits = 7 + ln, tb_src / tb_pos from sort_tile_bits(7, ...)) as
+// one real TF32 product with compensated (hi / lo) operands.  tmA: A as [depth][2^lm rows][2^(lk+1) floats] with boxes of
 // 128 rows (encode_tmap_thin; depth = slices when A depends on the slice, else 1).
 struct ThinTcDesc {
     CUtensorMap tmA;

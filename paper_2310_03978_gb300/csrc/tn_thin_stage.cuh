@@ -1,6 +1,6 @@
-// Output stage of the tensor-core thin kernel (k_gemm_thin_tc): a tile of 256 rows and NT columns
-// of complex64, thread t holding row t, is staged in shared memory and written in the order of
-// C's memory index, 8 consecutive elements of C per task.  (The CUDA-core thin kernel keeps a
+// Output stage of the tensor-core thin kernel (k_gemm_thin_tc): a tile of 128 rows and NT columns
+// of complex64, thread t of a drain group holding row t, is staged in shared memory and written
+// in the order of C's memory index, 8 consecutive elements of C per task.  (The CUDA-core thin kernel keeps a
 // padded stage, rows NT + 1 apart: the swizzle's extra address arithmetic and registers cost
 // it more than the bank conflicts it removes.)
 //
@@ -20,12 +20,13 @@ namespace tn {
 
 template <int NT>
 struct ThinStage {
-    // a tile has 256 * NT elements: 32 * NT runs of 8.  Complex64 results: two lanes share each
-    // run (lane half h writes elements 4j + 2h and 4j + 2h + 1 in its store j, so each store
-    // fills whole 32-byte sectors); planar 16-bit results (16 bytes per plane and run): a lane
-    // writes whole runs, consecutive lanes consecutive runs
-    static constexpr int TASKS = 256 * NT / 8, SUBS = 2 * TASKS;
-    static constexpr int SPT = (SUBS + 255) / 256, SPTP = (TASKS + 255) / 256;
+    static constexpr int LR = 7, ROWS = 1 << LR;  // rows of a tile (= threads of a group)
+    // a tile has ROWS * NT elements: ROWS * NT / 8 runs of 8.  Complex64 results: two lanes
+    // share each run (lane half h writes elements 4j + 2h and 4j + 2h + 1 in its store j, so
+    // each store fills whole 32-byte sectors); planar 16-bit results (16 bytes per plane and
+    // run): a lane writes whole runs, consecutive lanes consecutive runs
+    static constexpr int TASKS = ROWS * NT / 8, SUBS = 2 * TASKS;
+    static constexpr int SPT = (SUBS + ROWS - 1) / ROWS, SPTP = (TASKS + ROWS - 1) / ROWS;
     int phr;                  // column XOR of this thread's own row
     int r0, r1, r2, x0, x1, x2;  // tile bits 0-2: row part * NT, column part ^ phi(row part)
     int qr[SPT], qx[SPT];     // task q of this thread: the same for its run bits
@@ -53,7 +54,7 @@ struct ThinStage {
         x0 = xx[0], x1 = xx[1], x2 = xx[2];
 #pragma unroll
         for (int i = 0; i < SPT; ++i) {
-            const int u = tid + 256 * i;
+            const int u = tid + ROWS * i;
             const int r = d.planar_out ? u : u >> 1, h = d.planar_out ? 0 : u & 1;
             int R = 0, Cc = 0;
             uint64_t o = h ? 2 : 0;

@@ -305,11 +305,11 @@ def test_thin_steps_stream_kernel(tn, shape):
 def thin_kernel(shape, mode, thin_tc=0):
     """The kernel a slice-dependent streaming step of GEMM extents (lm, ln, lk) runs on: the
     tensor cores in the tensor-core modes for 4-16 columns and 4-16 terms (by default with 16
-    terms), else the CUDA cores."""
+    terms, or 16 columns and 8 terms), else the CUDA cores."""
     lm, ln, lk = shape
     wide, narrow = max(lm, ln), min(lm, ln)
     fits = 8 <= wide <= 30 and 2 <= narrow <= 4 and 2 <= lk <= 4
-    on = thin_tc > 0 or (thin_tc == 0 and lk == 4)
+    on = thin_tc > 0 or (thin_tc == 0 and (lk == 4 or (narrow == 4 and lk == 3)))
     return "thin_tc" if mode != "c64" and fits and on else "stream"
 
 
