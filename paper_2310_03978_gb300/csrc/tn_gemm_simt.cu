@@ -369,7 +369,7 @@ constexpr bool thin_b_in_regs(int nt, int ks) { return ks != 0 && nt * ks <= 16;
 constexpr bool thin_dyn_smem(int nt, int ks) { return ks != 0 && nt == 16; }
 constexpr int thin_dyn_bytes(int nt) { return 2 * kThinRows * (nt + 1) * 8; }
 
-template <int NT, int KS>
+template <int NT, int KS, bool PL>
 __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(GemmDesc d) {
     constexpr int NB = NT < 2 ? 2 : NT;  // row stride of sB (pairs stay 16-byte aligned)
     constexpr int LD = NT + 1;           // row stride of the output stage
@@ -423,20 +423,20 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
     // a tile has 256 * NT elements (tile_bits = 8 + log2 NT): 32 * NT runs of 8 consecutive
     // elements of C; their stage and C offsets are the same for every tile, so they are set once
     constexpr int TASKS = kThinRows * NT / 8;
-    // complex64 results: two lanes share each run of 8 (lane half h writes elements 4j + 2h and
-    // 4j + 2h + 1 in its store j, so each store instruction fills whole 32-byte sectors); planar
-    // 16-bit results (16 bytes per plane and run): a lane writes whole runs, consecutive lanes
-    // consecutive runs
-    constexpr int SUBS = TASKS * 2, SPT = (SUBS + 255) / 256, SPTP = (TASKS + 255) / 256;
+    // two lanes share each run of 8, so every thread has stores to make: for complex64 results
+    // lane half h writes elements 4j + 2h and 4j + 2h + 1 in its store j (each store instruction
+    // fills whole 32-byte sectors); for planar 16-bit results (PL, a separate instantiation)
+    // lane half h writes elements 4h .. 4h + 3, 8 bytes per plane (a warp's stores cover 256
+    // contiguous bytes of each plane)
+    constexpr int SUBS = TASKS * 2, SPT = (SUBS + 255) / 256;
     int ws[SPT];
     uint64_t os[SPT];
     const int d0 = w8[1], d1 = w8[2], d2 = w8[4];
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-        const int u = tid + 256 * i;
-        const int r = d.planar_out ? u : u >> 1, h = d.planar_out ? 0 : u & 1;
-        ws[i] = h ? d1 : 0;
-        os[i] = h ? 2 : 0;
+        const int u = tid + 256 * i, r = u >> 1, h = u & 1;
+        ws[i] = h ? (PL ? d2 : d1) : 0;
+        os[i] = h ? (PL ? 4 : 2) : 0;
         for (int q = 3; q < d.tile_bits; ++q)
             if ((r >> (q - 3)) & 1) {
                 ws[i] += soff(d.tb_src[q]);
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
     float amx = 0.f;
     // a result that feeds a tensor-core step is written as its scaled planar 16-bit copy, with
     // the exponent bounded from the inputs' max-abs (as in the other epilogues)
-    const int eo = d.planar_out ? planar_out_exponent(d.pout, s) : 0;
-    if (d.planar_out && blockIdx.x == 0 && tid == 0) d.pout.exps[s] = eo;
+    const int eo = PL ? planar_out_exponent(d.pout, s) : 0;
+    if (PL && blockIdx.x == 0 && tid == 0) d.pout.exps[s] = eo;
     // write the tile whose C offset (its rows' deposit) is cbase through `stage`; callers make
     // sure no thread still reads `stage` from an earlier tile
     auto emit = [&](float2 *stage, uint64_t cbase) {
@@ -455,17 +455,17 @@ __global__ void __launch_bounds__(256, thin_min_blocks(NT, KS)) k_gemm_thin(Gemm
         for (int n = 0; n < NT; ++n) stage[tid * LD + n] = make_float2(cr[n], ci[n]);
         __syncthreads();
         float2 *C = d.C + s * d.sC + cbase;
-        if (d.planar_out) {
+        if constexpr (PL) {
 #pragma unroll
-            for (int i = 0; i < SPTP; ++i) {
-                if (TASKS % 256 != 0 && tid + 256 * i >= TASKS) break;
-                float2 v[8];
+            for (int i = 0; i < SPT; ++i) {
+                if (SUBS % 256 != 0 && tid + 256 * i >= SUBS) break;
+                float2 v[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < 4; ++j) {
                     v[j] = stage[ws[i] + w8[j]];
                     amx = fmaxf(amx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
                 }
-                planar_out_store8(d.pout, s, cbase | os[i], v, eo);
+                planar_out_store4(d.pout, s, cbase | os[i], v, eo);
             }
         } else {
 #pragma unroll
@@ -857,7 +857,9 @@ __global__ void __launch_bounds__(256) k_sparse_gemm(GenericDesc d, int32_t ln, 
 
 cudaError_t simt_prepare() {
     cudaError_t e = cudaSuccess;
-    for (auto f : {k_gemm_thin<16, 2>, k_gemm_thin<16, 4>, k_gemm_thin<16, 8>, k_gemm_thin<16, 16>})
+    for (auto f : {k_gemm_thin<16, 2, false>, k_gemm_thin<16, 4, false>, k_gemm_thin<16, 8, false>,
+                   k_gemm_thin<16, 16, false>, k_gemm_thin<16, 2, true>, k_gemm_thin<16, 4, true>,
+                   k_gemm_thin<16, 8, true>, k_gemm_thin<16, 16, true>})
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      thin_dyn_bytes(16));
@@ -1066,7 +1068,15 @@ void launch_thin_walk(const GemmDesc &d, dim3 grid, cudaStream_t st) {
     const int64_t resident = (int64_t)sms * thin_min_blocks(NT, KS);
     const int64_t per_slice = (resident + grid.y - 1) / grid.y;
     if (per_slice < (int64_t)grid.x) grid.x = (unsigned)per_slice;
-    k_gemm_thin<NT, KS><<<grid, 256, thin_dyn_smem(NT, KS) ? thin_dyn_bytes(NT) : 0, st>>>(d);
+    const int dyn = thin_dyn_smem(NT, KS) ? thin_dyn_bytes(NT) : 0;
+    if (d.planar_out) k_gemm_thin<NT, KS, true><<<grid, 256, dyn, st>>>(d);
+    else k_gemm_thin<NT, KS, false><<<grid, 256, dyn, st>>>(d);
+}
+
+template <int NT>
+void launch_thin_long(const GemmDesc &d, dim3 grid, cudaStream_t st) {
+    if (d.planar_out) k_gemm_thin<NT, 0, true><<<grid, 256, 0, st>>>(d);
+    else k_gemm_thin<NT, 0, false><<<grid, 256, 0, st>>>(d);
 }
 
 template <int NT>
@@ -1077,14 +1087,14 @@ void launch_thin_n(const GemmDesc &d, dim3 grid, cudaStream_t st) {
             case 2: launch_thin_walk<NT, 4>(d, grid, st); break;
             case 3: launch_thin_walk<NT, 8>(d, grid, st); break;
             case 4: launch_thin_walk<NT, 16>(d, grid, st); break;
-            default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
+            default: launch_thin_long<NT>(d, grid, st); break;
         }
     } else {
         switch (d.lk) {
             case 1: launch_thin_walk<NT, 2>(d, grid, st); break;
             case 2: launch_thin_walk<NT, 4>(d, grid, st); break;
             case 3: launch_thin_walk<NT, 8>(d, grid, st); break;
-            default: k_gemm_thin<NT, 0><<<grid, 256, 0, st>>>(d); break;
+            default: launch_thin_long<NT>(d, grid, st); break;
         }
     }
 }

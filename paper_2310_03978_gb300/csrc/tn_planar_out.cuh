@@ -116,6 +116,42 @@ __device__ __forceinline__ void planar_out_store8_t(const PlanarOut &o, int64_t 
     if (o.planes == 4) *reinterpret_cast<uint4 *>(base + 3 * o.plane_stride) = p3.u;
 }
 
+// Store four consecutive complex values (offsets off .. off + 3, off a multiple of 4) into the
+// planar output as one 8-byte word (4 x 16 bits) per plane.
+template <typename T2>
+__device__ __forceinline__ void planar_out_store4_t(const PlanarOut &o, int64_t s, uint64_t off,
+                                                    const float2 (&v)[4], int e) {
+    union Half {
+        uint2 u;
+        T2 h[2];
+    } re, im, p2, p3;
+    const Pow2 pe = pow2_of(-e);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float r0 = scale_pow2(v[2 * j].x, pe), i0 = scale_pow2(v[2 * j].y, pe);
+        const float r1 = scale_pow2(v[2 * j + 1].x, pe), i1 = scale_pow2(v[2 * j + 1].y, pe);
+        re.h[j] = pack_pair<T2>(r0, r1);
+        im.h[j] = pack_pair<T2>(i0, i1);
+        if (o.planes == 3) p2.h[j] = pack_pair<T2>(r0 + i0, r1 + i1);
+        if (o.planes == 4) {
+            const float2 rf = unpack_pair(re.h[j]), jf = unpack_pair(im.h[j]);
+            p2.h[j] = pack_pair<T2>(r0 - rf.x, r1 - rf.y);
+            p3.h[j] = pack_pair<T2>(i0 - jf.x, i1 - jf.y);
+        }
+    }
+    uint16_t *base = static_cast<uint16_t *>(o.base) + s * o.sstride + (int64_t)off;
+    *reinterpret_cast<uint2 *>(base) = re.u;
+    *reinterpret_cast<uint2 *>(base + o.plane_stride) = im.u;
+    if (o.planes >= 3) *reinterpret_cast<uint2 *>(base + 2 * o.plane_stride) = p2.u;
+    if (o.planes == 4) *reinterpret_cast<uint2 *>(base + 3 * o.plane_stride) = p3.u;
+}
+
+__device__ __forceinline__ void planar_out_store4(const PlanarOut &o, int64_t s, uint64_t off,
+                                                  const float2 (&v)[4], int e) {
+    if (o.bf16) planar_out_store4_t<__nv_bfloat162>(o, s, off, v, e);
+    else planar_out_store4_t<__half2>(o, s, off, v, e);
+}
+
 __device__ __forceinline__ void planar_out_store8(const PlanarOut &o, int64_t s, uint64_t off,
                                                   const float2 (&v)[8], int e) {
     if (o.bf16) planar_out_store8_t<__nv_bfloat162, true>(o, s, off, v, e);
